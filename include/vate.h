@@ -1,0 +1,201 @@
+/*
+ * vate.h -- C ABI of the B300 (sm_103a) VATE library.
+ *
+ * VATE (virtual asynchronous timestamp estimator, arXiv 1812.00282) estimates,
+ * at the end of every time slice t, the number of distinct opposite hosts bip
+ * that each host aip has exchanged packets with during the last k' <= k
+ * slices, |OP(aip, t-k'+1, k')| (Sec. 1, Def. 1).  Each host owns g virtual
+ * asynchronous timestamps (ATs) drawn from one shared pool of 2^c ATs
+ * (Sec. 4.1); an AT stores the asynchronous current timestamp (ACT) of the
+ * slice in which it was last set, and value 2k means "inactive" (Sec. 3).
+ *
+ * Conventions for every entry point below
+ *   - Pointers named d_* are DEVICE pointers (cudaMalloc / torch CUDA
+ *     tensors) on the device that was current at vate_create; h_* are HOST
+ *     pointers (page-locked memory gives copy/compute overlap; pageable
+ *     memory works but the copies become synchronous).
+ *   - Caller-owned buffers stay owned by the caller and must stay valid until
+ *     the work queued on `stream` has finished.  The library owns the AT pool,
+ *     BACT^0, the census and its staging buffers.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  All device work is queued asynchronously on it, in
+ *     call order.  Calls on one handle must be made from one host thread at a
+ *     time, in slice order (the slice state machine lives on the host).
+ *   - Every function returns VATE_OK (0) or one of the VATE_E* codes;
+ *     argument and state checks are made on the host before anything is
+ *     queued, so an error return leaves the handle unchanged.
+ *     vate_last_error() gives a message for the calling thread.
+ *   - Numbers follow the paper's notation: c (log2 of the pool size P),
+ *     k (longest window), k' (window of one estimate), g (VATs per host).
+ *
+ * Byte-per-AT layout: the pool is uint8_t[P], one AT value (0..2k) per byte,
+ * so k <= 63 (2k+1 values below 128; the device compares 4 ATs per 32-bit
+ * word).  The paper packs ceil(log2(2k+1)) bits per AT (Sec. 4.2); the state
+ * is the same AT value per index.
+ */
+#ifndef VATE_H
+#define VATE_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes --------------------------------------------------- */
+#define VATE_OK        0
+#define VATE_EINVAL    1   /* bad argument (range, alignment, NULL)            */
+#define VATE_ENOMEM    2   /* device or host allocation failed                 */
+#define VATE_ESLICE    3   /* slice out of order, slice already closed, or an
+                              estimate before any close                        */
+#define VATE_ECUDA     4   /* a CUDA runtime call failed (no device, bad stream,
+                              launch failure); see vate_last_error()           */
+#define VATE_ETIMEOUT  5   /* a bounded device-side wait gave up               */
+
+/* ---- per-host flags written by vate_estimate ------------------------- */
+#define VATE_FLAG_SAT       1u  /* every VAT of the host active: V0 read as 1  */
+#define VATE_FLAG_POOLFULL  2u  /* no inactive AT in the pool: N0 read as 1    */
+
+/* One IPv4 address pair <aip, bip> extracted from a packet: 8 bytes, aip
+ * first (Sec. 4.2: the host-to-GPU buffers hold r such pairs). */
+typedef struct {
+    uint32_t aip;
+    uint32_t bip;
+} vate_pair;
+
+/* Construction parameters.
+ *   log2_pool  c: the pool holds P = 2^c ATs, 12 <= c <= 32 (Sec. 4.1).
+ *   k          longest window in slices, 1 <= k <= 63; ATs hold 0..2k (Sec. 3).
+ *   g          virtual ATs per host, 1 <= g <= 65536, a multiple of seg_len.
+ *   seg_len    L: VAT i of a host lives at offset (i mod L) of the pool segment
+ *              chosen for (aip, floor(i/L)).  L = 1 is fully random placement
+ *              (the paper's H); L = 32 puts 32 VATs in one 32-byte L2 sector.
+ *              Power of two, 1 <= L <= 64, and c - log2(L) >= 1.
+ *   partition  0: blocks of Eq. 9-10 (2k-1 blocks of a = floor(P/(2k-1)) ATs
+ *              and a last block of b = P mod (2k-1)); 1: the low-deviation
+ *              partition of Sec. 4.1 (block sizes P/(2k) or P/(2k)+1).
+ *              Either way every block must hold at least 32 ATs.
+ *   seed       keys the hash functions H and BH.
+ * The hash functions (Sec. 4.1 leaves them open):
+ *   mix(x)   = SplitMix64 output function (Steele, Lea & Flood 2014)
+ *   BH(bip)  = ((mix(mix(seed+2) ^ bip) >> 32) * g) >> 32
+ *   seg      = mix(mix(seed+1) ^ (aip << 32) ^ floor(i/L)) >> (64 - (c - log2 L))
+ *   H(aip,i) = seg * L + (i mod L)                                          */
+typedef struct {
+    uint32_t log2_pool;
+    uint32_t k;
+    uint32_t g;
+    uint32_t seg_len;
+    uint32_t partition;
+    uint32_t reserved;   /* must be 0 */
+    uint64_t seed;
+} vate_params;
+
+/* Read-only view of a handle's geometry and slice state. */
+typedef struct {
+    uint64_t pool_size;      /* P = 2^c                                       */
+    uint64_t block_a;        /* a (Eq. 9) or a' (low-deviation)               */
+    uint64_t block_b;        /* b (Eq. 10) or b'                              */
+    int64_t  slice;          /* current slice, -1 before the first call       */
+    uint32_t bact0;          /* BACT^0 of the current slice (Eq. 7)           */
+    uint32_t closed;         /* 1 when the current slice has been closed      */
+} vate_info;
+
+typedef struct vate_handle vate_handle;
+
+/* Allocate the AT pool (P bytes of device memory, 256-byte aligned) and run
+ * InitAT on every AT: all values become 2k, BACT^0 = 0 (Algorithm 4, start).
+ * The first slice number passed to vate_ingest/vate_close_slice becomes
+ * slice 0 of Algorithm 4.  Errors: VATE_EINVAL (parameters), VATE_ENOMEM,
+ * VATE_ECUDA.  *out is set only on success. */
+int vate_create(const vate_params *params, void *stream, vate_handle **out);
+
+/* Free the pool and every buffer of the handle (synchronises the device work
+ * of the handle first).  NULL is accepted. */
+int vate_destroy(vate_handle *h);
+
+/* Scan n pairs of slice `slice` (Algorithm 4, scan loop; Sec. 4.2 "scanning
+ * IP address pairs"): for each pair, vid = BH(bip), pid = H(aip, vid), and
+ * SetAT(ATP[pid]) writes the ACT of pid's block, (BACT^0 + block) mod 2k.
+ *   d_pairs  device array of n vate_pair (8-byte aligned); n = 0 is allowed.
+ *   slice    >= the current slice.  Moving to a later slice first slides the
+ *            window once per slice passed (BACT^0 + 1, then PreserveAT on the
+ *            two blocks whose ACT became 0 or k: Algorithm 4, Algorithm 3),
+ *            so no maintenance point is skipped (Corollary 1).
+ * Several calls per slice are allowed.  Concurrent SetATs on one AT write the
+ * same value, so the pool does not depend on pair order (Sec. 4.2).
+ * Errors: VATE_ESLICE if slice < current, or == current after it was closed. */
+int vate_ingest(vate_handle *h, const vate_pair *d_pairs, uint64_t n, int64_t slice, void *stream);
+
+/* Close slice `slice` (sliding first, as in vate_ingest, if it is later than
+ * the current one) and take the pool census used by Z_p (Eq. 11): the number
+ * of pool ATs at each distance d = (ACT + 2k - value) mod 2k, 0 <= d < 2k,
+ * and the number of inactive ATs.  After a close, vate_estimate may be called
+ * any number of times until the next ingest/close moves to a later slice.
+ * Errors: VATE_ESLICE if slice < current or already closed. */
+int vate_close_slice(vate_handle *h, int64_t slice, void *stream);
+
+/* Estimate |OP(aip, t-k'+1, k')| for n hosts at the end of the closed slice t
+ * (Algorithm 4, estimation loop; Eq. 11 read as g ln Z_p - g ln Z_v):
+ *   A   = #{ i < g : CheckAT(ATP[H(aip, i)], k') }          (Algorithm 1)
+ *   Z_v = (g - A) / g,  Z_p = N0 / P, N0 = inactive pool ATs for k'
+ *   out = g * log1p((N0*g - V0*P) / (V0*P)), V0 = g - A, evaluated in FP32
+ *         from exact integers (V0 = 0 -> 1 with VATE_FLAG_SAT, N0 = 0 -> 1
+ *         with VATE_FLAG_POOLFULL).
+ *   d_aips   device uint32[n] host addresses; d_out device float[n];
+ *   d_flags  device uint8[n] or NULL.  1 <= kprime <= k.
+ * Errors: VATE_ESLICE if the current slice has not been closed. */
+int vate_estimate(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint32_t kprime,
+                  float *d_out, uint8_t *d_flags, void *stream);
+
+/* Same gather as vate_estimate, returning the active VAT count A of each host
+ * (d_active device uint32[n]) instead of the estimate. */
+int vate_active_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint32_t kprime,
+                       uint32_t *d_active, void *stream);
+
+/* Per-age VAT counts of each host at the end of the closed slice:
+ * d_counts[i*k + d] = number of host i's g VATs whose distance is exactly d
+ * (last set d slices ago), 0 <= d < k; the active count for window k' is the
+ * sum of the first k' entries.  d_counts is device uint16[n*k] (g <= 65535
+ * is required here). */
+int vate_age_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint16_t *d_counts, void *stream);
+
+/* Copy the census of the last close into d_hist (device uint64[2k+1]):
+ * d_hist[d] for distances 0 <= d < 2k, d_hist[2k] = inactive ATs. */
+int vate_census(vate_handle *h, uint64_t *d_hist, void *stream);
+
+/* Copy the AT pool (P bytes) to d_dst, or overwrite it from d_src. */
+int vate_copy_pool(vate_handle *h, uint8_t *d_dst, void *stream);
+int vate_load_pool(vate_handle *h, const uint8_t *d_src, void *stream);
+
+/* End-to-end forms with host buffers: the pairs (or hosts) are copied to the
+ * device in chunks of up to 2^20 records through two device staging buffers
+ * on an internal copy stream, overlapping the copy of chunk i+1 with the
+ * kernel of chunk i (the double buffer of Sec. 4.2, with larger chunks).
+ * The staging buffers are allocated on the first call.  vate_estimate_host
+ * also copies the estimates (and flags, if h_flags is not NULL) back; they
+ * are valid once `stream` has been synchronised. */
+int vate_ingest_host(vate_handle *h, const vate_pair *h_pairs, uint64_t n, int64_t slice, void *stream);
+int vate_estimate_host(vate_handle *h, const uint32_t *h_aips, uint64_t n, uint32_t kprime,
+                       float *h_out, uint8_t *h_flags, void *stream);
+
+/* Geometry and slice state of a handle (host only, never blocks). */
+int vate_get_info(const vate_handle *h, vate_info *out);
+
+/* Host-side evaluation of the mapping the device uses, for checks without a
+ * GPU: H(aip, i), BH(bip) and the block of a pool position for `params`. */
+int vate_host_h(const vate_params *params, uint32_t aip, uint32_t i, uint64_t *pid);
+int vate_host_bh(const vate_params *params, uint32_t bip, uint32_t *vid);
+int vate_host_block(const vate_params *params, uint64_t pid, uint32_t *block);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *vate_last_error(void);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t vate_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VATE_H */

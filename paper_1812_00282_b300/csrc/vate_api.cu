@@ -1,0 +1,428 @@
+// vate_api.cu -- C ABI of the VATE library: argument checks, the slice state
+// machine of Algorithm 4 on the host, device buffers, kernel launches.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "vate.h"
+#include "vate_internal.h"
+
+using vate::Geom;
+
+namespace {
+thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
+constexpr uint64_t STAGE_RECORDS = 1ull << 20;   // records per host-copy chunk
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(VATE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Parameter checks and derived geometry; no device needed.
+int make_geom(const vate_params *p, Geom *G) {
+    if (!p) return fail(VATE_EINVAL, "params is NULL");
+    if (p->reserved != 0) return fail(VATE_EINVAL, "params.reserved must be 0");
+    if (p->log2_pool < 12 || p->log2_pool > 32) return fail(VATE_EINVAL, "log2_pool (c) must be in [12, 32], got %u", p->log2_pool);
+    if (p->k < 1 || p->k > 63) return fail(VATE_EINVAL, "k must be in [1, 63] for byte ATs, got %u", p->k);
+    if (p->g < 1 || p->g > 65536) return fail(VATE_EINVAL, "g must be in [1, 65536], got %u", p->g);
+    uint32_t L = p->seg_len;
+    if (L < 1 || L > 64 || (L & (L - 1)) != 0) return fail(VATE_EINVAL, "seg_len must be a power of two in [1, 64], got %u", L);
+    if (p->g % L != 0) return fail(VATE_EINVAL, "g (%u) must be a multiple of seg_len (%u)", p->g, L);
+    if (p->partition > 1) return fail(VATE_EINVAL, "partition must be 0 or 1, got %u", p->partition);
+    uint32_t log2L = 0;
+    while ((1u << log2L) < L) log2L++;
+    if (p->log2_pool <= log2L) return fail(VATE_EINVAL, "log2_pool must exceed log2(seg_len)");
+    memset(G, 0, sizeof *G);
+    G->c = p->log2_pool;
+    G->k = p->k;
+    G->twok = 2 * p->k;
+    G->g = p->g;
+    G->L = L;
+    G->log2L = log2L;
+    G->segbits = p->log2_pool - log2L;
+    G->partition = p->partition;
+    G->P = 1ull << p->log2_pool;
+    G->key_h = vate::mix64(p->seed + 1);
+    G->key_bh = vate::mix64(p->seed + 2);
+    uint64_t twok = G->twok;
+    if (p->partition == 0) {               // Eq. 9, Eq. 10
+        G->a = G->P / (twok - 1);
+        G->b = G->P % (twok - 1);
+        G->first = G->P;
+    } else {                               // low-deviation partition
+        G->a = G->P / twok;
+        G->b = G->P % twok;
+        G->first = G->a * (twok - G->b);
+    }
+    if (G->a < 32) return fail(VATE_EINVAL, "blocks must hold at least 32 ATs (a = %llu)", (unsigned long long)G->a);
+    G->ma = vate::magic_for(G->a);
+    G->ma1 = vate::magic_for(G->a + 1);
+    return VATE_OK;
+}
+
+// [start, end) of block i
+void block_range(const Geom &G, uint32_t i, uint64_t *s, uint64_t *e) {
+    if (G.partition == 0) {
+        *s = (uint64_t)i * G.a;
+        *e = (i + 1 < G.twok) ? *s + G.a : G.P;
+        return;
+    }
+    uint64_t nsmall = G.twok - G.b;
+    if (i < nsmall) {
+        *s = (uint64_t)i * G.a;
+        *e = *s + G.a;
+    } else {
+        *s = nsmall * G.a + (uint64_t)(i - nsmall) * (G.a + 1);
+        *e = *s + G.a + 1;
+    }
+}
+
+}  // namespace
+
+void vate::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct vate_handle {
+    vate_params prm;
+    Geom G;
+    int device = 0;
+    int sms = 148;
+    int64_t slice = -1;
+    bool closed = false;
+    uint32_t bact0 = 0;
+    uint64_t *d_hist = nullptr;       // census of the last close, 2k+1 counters
+    uint64_t *d_partial = nullptr;    // census scratch: one row per block
+    unsigned int *d_ticket = nullptr; // census scratch: blocks finished
+    int census_grid = 0;
+    // host-copy staging (allocated on first use)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr};
+    cudaEvent_t ev_free[2] = {nullptr, nullptr};
+    void *d_stage[2] = {nullptr, nullptr};       // pairs or hosts in
+    float *d_stage_out[2] = {nullptr, nullptr};  // estimates out
+    uint8_t *d_stage_flags[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+int check_handle(const vate_handle *h) {
+    if (!h) return fail(VATE_EINVAL, "handle is NULL");
+    return VATE_OK;
+}
+
+// Slide the window until `slice` is the current slice: each step is
+// BACT^0 <- BACT^0 + 1 and PreserveAT on the blocks whose ACT became 0 or k
+// (Algorithm 4, last lines).  After 2k steps with no SetAT every AT is
+// inactive, which every further step leaves unchanged, so longer gaps only
+// advance BACT^0.
+int advance_to(vate_handle *h, int64_t slice, cudaStream_t st) {
+    if (h->slice < 0) {            // first call fixes the origin (slice 0 of Algorithm 4)
+        h->slice = slice;
+        h->closed = false;
+        return VATE_OK;
+    }
+    const Geom &G = h->G;
+    int64_t steps = slice - h->slice;
+    int64_t run = steps > (int64_t)G.twok ? (int64_t)G.twok : steps;
+    for (int64_t s = 0; s < run; s++) {
+        h->bact0 = (h->bact0 + 1) % G.twok;
+        uint32_t i0 = (G.twok - h->bact0) % G.twok;          // BACT = 0
+        uint32_t i1 = (G.k + G.twok - h->bact0) % G.twok;    // BACT = k
+        uint64_t s0, e0, s1, e1;
+        block_range(G, i0, &s0, &e0);
+        block_range(G, i1, &s1, &e1);
+        cudaError_t e = vate::launch_preserve(G.pool, G.k, s0, e0, s1, e1, st, h->sms);
+        if (e != cudaSuccess) return cuda_fail(e, "preserve launch");
+    }
+    if (steps > run) h->bact0 = (uint32_t)((h->bact0 + (uint64_t)(steps - run)) % G.twok);
+    h->slice = slice;
+    h->closed = false;
+    return VATE_OK;
+}
+
+int check_slice(const vate_handle *h, int64_t slice) {
+    if (slice < 0) return fail(VATE_ESLICE, "slice numbers start at 0 (got %lld)", (long long)slice);
+    if (h->slice >= 0 && slice < h->slice)
+        return fail(VATE_ESLICE, "slice %lld is before the current slice %lld", (long long)slice, (long long)h->slice);
+    if (h->slice >= 0 && slice == h->slice && h->closed)
+        return fail(VATE_ESLICE, "slice %lld is already closed", (long long)slice);
+    return VATE_OK;
+}
+
+int ensure_staging(vate_handle *h) {
+    if (h->copy_stream) return VATE_OK;
+    CU(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
+    for (int i = 0; i < 2; i++) {
+        CU(cudaEventCreateWithFlags(&h->ev_ready[i], cudaEventDisableTiming), "event");
+        CU(cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming), "event");
+        if (cudaMalloc(&h->d_stage[i], STAGE_RECORDS * sizeof(vate_pair)) != cudaSuccess ||
+            cudaMalloc(&h->d_stage_out[i], STAGE_RECORDS * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&h->d_stage_flags[i], STAGE_RECORDS) != cudaSuccess)
+            return fail(VATE_ENOMEM, "staging buffers: out of device memory");
+    }
+    return VATE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vate_last_error(void) { return g_err.c_str(); }
+
+uint64_t vate_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int vate_host_h(const vate_params *params, uint32_t aip, uint32_t i, uint64_t *pid) {
+    Geom G;
+    int rc = make_geom(params, &G);
+    if (rc) return rc;
+    if (!pid || i >= G.g) return fail(VATE_EINVAL, "bad pid pointer or i >= g");
+    *pid = vate::vat_pid(G, aip, i);
+    return VATE_OK;
+}
+
+int vate_host_bh(const vate_params *params, uint32_t bip, uint32_t *vid) {
+    Geom G;
+    int rc = make_geom(params, &G);
+    if (rc) return rc;
+    if (!vid) return fail(VATE_EINVAL, "vid is NULL");
+    *vid = vate::bh(G, bip);
+    return VATE_OK;
+}
+
+int vate_host_block(const vate_params *params, uint64_t pid, uint32_t *block) {
+    Geom G;
+    int rc = make_geom(params, &G);
+    if (rc) return rc;
+    if (!block || pid >= G.P) return fail(VATE_EINVAL, "bad block pointer or pid >= P");
+    *block = vate::block_of(G, (uint32_t)pid);
+    return VATE_OK;
+}
+
+int vate_create(const vate_params *params, void *stream, vate_handle **out) {
+    if (!out) return fail(VATE_EINVAL, "out is NULL");
+    Geom G;
+    int rc = make_geom(params, &G);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    vate_handle *h = new (std::nothrow) vate_handle();
+    if (!h) return fail(VATE_ENOMEM, "host allocation failed");
+    h->prm = *params;
+    h->G = G;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "no usable CUDA device");
+    }
+    static bool prepared = false;
+    if (!prepared) {
+        e = vate::census_prepare(126);
+        if (e == cudaSuccess) e = vate::age_prepare(63);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "kernel attributes");
+        }
+        prepared = true;
+    }
+    h->census_grid = h->sms * 4;
+    size_t nbins = G.twok + 1;
+    if (cudaMalloc(&h->G.pool, G.P) != cudaSuccess || cudaMalloc(&h->d_hist, nbins * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_partial, (size_t)h->census_grid * nbins * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_ticket, sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        vate_destroy(h);
+        return fail(VATE_ENOMEM, "out of device memory for a pool of 2^%u ATs", G.c);
+    }
+    e = cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_hist, 0, nbins * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = vate::launch_init(h->G, st, h->sms);
+    if (e != cudaSuccess) {
+        vate_destroy(h);
+        return cuda_fail(e, "pool initialisation");
+    }
+    *out = h;
+    return VATE_OK;
+}
+
+int vate_destroy(vate_handle *h) {
+    if (!h) return VATE_OK;
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    cudaFree(h->G.pool);
+    cudaFree(h->d_hist);
+    cudaFree(h->d_partial);
+    cudaFree(h->d_ticket);
+    for (int i = 0; i < 2; i++) {
+        cudaFree(h->d_stage[i]);
+        cudaFree(h->d_stage_out[i]);
+        cudaFree(h->d_stage_flags[i]);
+        if (h->ev_ready[i]) cudaEventDestroy(h->ev_ready[i]);
+        if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    delete h;
+    return VATE_OK;
+}
+
+int vate_get_info(const vate_handle *h, vate_info *out) {
+    if (int rc = check_handle(h)) return rc;
+    if (!out) return fail(VATE_EINVAL, "out is NULL");
+    out->pool_size = h->G.P;
+    out->block_a = h->G.a;
+    out->block_b = h->G.b;
+    out->slice = h->slice;
+    out->bact0 = h->bact0;
+    out->closed = h->closed ? 1u : 0u;
+    return VATE_OK;
+}
+
+int vate_ingest(vate_handle *h, const vate_pair *d_pairs, uint64_t n, int64_t slice, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (n && !d_pairs) return fail(VATE_EINVAL, "d_pairs is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_pairs) & 7u) != 0) return fail(VATE_EINVAL, "d_pairs must be 8-byte aligned");
+    if (int rc = check_slice(h, slice)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = advance_to(h, slice, st)) return rc;
+    cudaError_t e = vate::launch_ingest(h->G, h->bact0, reinterpret_cast<const uint32_t *>(d_pairs), n, st, h->sms);
+    if (e != cudaSuccess) return cuda_fail(e, "ingest launch");
+    return VATE_OK;
+}
+
+int vate_close_slice(vate_handle *h, int64_t slice, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (int rc = check_slice(h, slice)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = advance_to(h, slice, st)) return rc;
+    cudaError_t e = vate::launch_census(h->G, h->bact0, h->d_partial, h->census_grid, h->d_hist, h->d_ticket, st);
+    if (e != cudaSuccess) return cuda_fail(e, "census launch");
+    h->closed = true;
+    return VATE_OK;
+}
+
+static int gather_common(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint32_t kprime) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->closed) return fail(VATE_ESLICE, "the current slice has not been closed");
+    if (kprime < 1 || kprime > h->G.k) return fail(VATE_EINVAL, "kprime must be in [1, k=%u], got %u", h->G.k, kprime);
+    if (n && !d_aips) return fail(VATE_EINVAL, "d_aips is NULL");
+    return VATE_OK;
+}
+
+int vate_estimate(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint32_t kprime, float *d_out,
+                  uint8_t *d_flags, void *stream) {
+    if (int rc = gather_common(h, d_aips, n, kprime)) return rc;
+    if (n && !d_out) return fail(VATE_EINVAL, "d_out is NULL");
+    cudaError_t e = vate::launch_gather(vate::GATHER_ESTIMATE, h->G, h->bact0, kprime, h->d_hist, d_aips, n, d_out,
+                                        d_flags, nullptr, (cudaStream_t)stream, h->sms);
+    if (e != cudaSuccess) return cuda_fail(e, "estimate launch");
+    return VATE_OK;
+}
+
+int vate_active_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint32_t kprime, uint32_t *d_active,
+                       void *stream) {
+    if (int rc = gather_common(h, d_aips, n, kprime)) return rc;
+    if (n && !d_active) return fail(VATE_EINVAL, "d_active is NULL");
+    cudaError_t e = vate::launch_gather(vate::GATHER_ACTIVE, h->G, h->bact0, kprime, h->d_hist, d_aips, n, nullptr,
+                                        nullptr, d_active, (cudaStream_t)stream, h->sms);
+    if (e != cudaSuccess) return cuda_fail(e, "active-count launch");
+    return VATE_OK;
+}
+
+int vate_age_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint16_t *d_counts, void *stream) {
+    if (int rc = gather_common(h, d_aips, n, 1)) return rc;
+    if (h->G.g > 65535) return fail(VATE_EINVAL, "vate_age_counts needs g <= 65535");
+    if (n && !d_counts) return fail(VATE_EINVAL, "d_counts is NULL");
+    cudaError_t e = vate::launch_age_counts(h->G, h->bact0, d_aips, n, d_counts, (cudaStream_t)stream, h->sms);
+    if (e != cudaSuccess) return cuda_fail(e, "age-count launch");
+    return VATE_OK;
+}
+
+int vate_census(vate_handle *h, uint64_t *d_hist, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h->closed) return fail(VATE_ESLICE, "the current slice has not been closed");
+    if (!d_hist) return fail(VATE_EINVAL, "d_hist is NULL");
+    CU(cudaMemcpyAsync(d_hist, h->d_hist, (h->G.twok + 1) * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream), "census copy");
+    return VATE_OK;
+}
+
+int vate_copy_pool(vate_handle *h, uint8_t *d_dst, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!d_dst) return fail(VATE_EINVAL, "d_dst is NULL");
+    CU(cudaMemcpyAsync(d_dst, h->G.pool, h->G.P, cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "pool copy");
+    return VATE_OK;
+}
+
+int vate_load_pool(vate_handle *h, const uint8_t *d_src, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!d_src) return fail(VATE_EINVAL, "d_src is NULL");
+    CU(cudaMemcpyAsync(h->G.pool, d_src, h->G.P, cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "pool load");
+    return VATE_OK;
+}
+
+int vate_ingest_host(vate_handle *h, const vate_pair *h_pairs, uint64_t n, int64_t slice, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (n && !h_pairs) return fail(VATE_EINVAL, "h_pairs is NULL");
+    if (int rc = check_slice(h, slice)) return rc;
+    if (int rc = ensure_staging(h)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = advance_to(h, slice, st)) return rc;
+    for (uint64_t off = 0, i = 0; off < n; off += STAGE_RECORDS, i++) {
+        int b = (int)(i & 1);
+        uint64_t m = (n - off) < STAGE_RECORDS ? (n - off) : STAGE_RECORDS;
+        CU(cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0), "wait");
+        CU(cudaMemcpyAsync(h->d_stage[b], h_pairs + off, m * sizeof(vate_pair), cudaMemcpyHostToDevice, h->copy_stream),
+           "pairs H2D");
+        CU(cudaEventRecord(h->ev_ready[b], h->copy_stream), "record");
+        CU(cudaStreamWaitEvent(st, h->ev_ready[b], 0), "wait");
+        cudaError_t e = vate::launch_ingest(h->G, h->bact0, reinterpret_cast<const uint32_t *>(h->d_stage[b]), m, st,
+                                            h->sms);
+        if (e != cudaSuccess) return cuda_fail(e, "ingest launch");
+        CU(cudaEventRecord(h->ev_free[b], st), "record");
+    }
+    return VATE_OK;
+}
+
+int vate_estimate_host(vate_handle *h, const uint32_t *h_aips, uint64_t n, uint32_t kprime, float *h_out,
+                       uint8_t *h_flags, void *stream) {
+    if (int rc = gather_common(h, h_aips, n, kprime)) return rc;
+    if (n && !h_out) return fail(VATE_EINVAL, "h_out is NULL");
+    if (int rc = ensure_staging(h)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (uint64_t off = 0, i = 0; off < n; off += STAGE_RECORDS, i++) {
+        int b = (int)(i & 1);
+        uint64_t m = (n - off) < STAGE_RECORDS ? (n - off) : STAGE_RECORDS;
+        uint32_t *din = reinterpret_cast<uint32_t *>(h->d_stage[b]);
+        CU(cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0), "wait");
+        CU(cudaMemcpyAsync(din, h_aips + off, m * sizeof(uint32_t), cudaMemcpyHostToDevice, h->copy_stream), "hosts H2D");
+        CU(cudaEventRecord(h->ev_ready[b], h->copy_stream), "record");
+        CU(cudaStreamWaitEvent(st, h->ev_ready[b], 0), "wait");
+        cudaError_t e = vate::launch_gather(vate::GATHER_ESTIMATE, h->G, h->bact0, kprime, h->d_hist, din, m,
+                                            h->d_stage_out[b], h_flags ? h->d_stage_flags[b] : nullptr, nullptr, st,
+                                            h->sms);
+        if (e != cudaSuccess) return cuda_fail(e, "estimate launch");
+        CU(cudaMemcpyAsync(h_out + off, h->d_stage_out[b], m * sizeof(float), cudaMemcpyDeviceToHost, st), "D2H");
+        if (h_flags)
+            CU(cudaMemcpyAsync(h_flags + off, h->d_stage_flags[b], m, cudaMemcpyDeviceToHost, st), "D2H");
+        CU(cudaEventRecord(h->ev_free[b], st), "record");
+    }
+    return VATE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,32 @@
+// vate_internal.h -- declarations shared by the kernel file and the C-ABI file.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "vate_device.cuh"
+
+namespace vate {
+
+constexpr int GATHER_THREADS = 256;
+constexpr int CENSUS_THREADS = 256;
+constexpr int AGE_THREADS = 256;
+constexpr int GATHER_ESTIMATE = 0;
+constexpr int GATHER_ACTIVE = 1;
+
+void count_launch();
+
+cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms);
+cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, uint64_t n, cudaStream_t st, int sms);
+cudaError_t launch_preserve(uint8_t *pool, uint32_t k, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
+                            cudaStream_t st, int sms);
+size_t census_smem_bytes(uint32_t twok);
+cudaError_t census_prepare(uint32_t twok);
+cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,
+                          unsigned int *ticket, cudaStream_t st);
+cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kprime, const uint64_t *hist,
+                          const uint32_t *aips, uint64_t n, float *out, uint8_t *flags, uint32_t *active,
+                          cudaStream_t st, int sms);
+cudaError_t age_prepare(uint32_t k);
+cudaError_t launch_age_counts(const Geom &G, uint32_t bact0, const uint32_t *aips, uint64_t n, uint16_t *counts,
+                              cudaStream_t st, int sms);
+
+}  // namespace vate

@@ -1,0 +1,308 @@
+"""Python binding of the VATE C ABI (include/vate.h): argument marshalling only.
+
+Every function carries the C name and forwards to ``libvate.so`` through
+ctypes; all work happens in the library's CUDA kernels.  Device arguments are
+torch CUDA tensors (their ``data_ptr()`` is passed), host arguments of the
+``*_host`` forms are numpy arrays or CPU tensors (page-locked memory gives
+copy/compute overlap).  ``stream`` defaults to torch's current stream.
+
+There is no fallback: if the library is missing or fails to load, importing
+the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvate.so")
+
+VATE_OK, VATE_EINVAL, VATE_ENOMEM, VATE_ESLICE, VATE_ECUDA, VATE_ETIMEOUT = 0, 1, 2, 3, 4, 5
+VATE_FLAG_SAT, VATE_FLAG_POOLFULL = 1, 2
+ERROR_NAMES = {1: "VATE_EINVAL", 2: "VATE_ENOMEM", 3: "VATE_ESLICE", 4: "VATE_ECUDA", 5: "VATE_ETIMEOUT"}
+
+
+class VateError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (ERROR_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+class vate_params(C.Structure):
+    _fields_ = [("log2_pool", C.c_uint32), ("k", C.c_uint32), ("g", C.c_uint32), ("seg_len", C.c_uint32),
+                ("partition", C.c_uint32), ("reserved", C.c_uint32), ("seed", C.c_uint64)]
+
+
+class vate_info(C.Structure):
+    _fields_ = [("pool_size", C.c_uint64), ("block_a", C.c_uint64), ("block_b", C.c_uint64),
+                ("slice", C.c_int64), ("bact0", C.c_uint32), ("closed", C.c_uint32)]
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libvate.so is not built (run `python -m paper_1812_00282_b300.build`): " + LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    vp, u32, u64, i64, i = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64, C.c_int
+    P = C.POINTER
+    sig = {
+        "vate_create": (i, [P(vate_params), vp, P(vp)]),
+        "vate_destroy": (i, [vp]),
+        "vate_ingest": (i, [vp, vp, u64, i64, vp]),
+        "vate_close_slice": (i, [vp, i64, vp]),
+        "vate_estimate": (i, [vp, vp, u64, u32, vp, vp, vp]),
+        "vate_active_counts": (i, [vp, vp, u64, u32, vp, vp]),
+        "vate_age_counts": (i, [vp, vp, u64, vp, vp]),
+        "vate_census": (i, [vp, vp, vp]),
+        "vate_copy_pool": (i, [vp, vp, vp]),
+        "vate_load_pool": (i, [vp, vp, vp]),
+        "vate_ingest_host": (i, [vp, vp, u64, i64, vp]),
+        "vate_estimate_host": (i, [vp, vp, u64, u32, vp, vp, vp]),
+        "vate_get_info": (i, [vp, P(vate_info)]),
+        "vate_host_h": (i, [P(vate_params), u32, u32, P(u64)]),
+        "vate_host_bh": (i, [P(vate_params), u32, P(u32)]),
+        "vate_host_block": (i, [P(vate_params), u64, P(u32)]),
+        "vate_last_error": (C.c_char_p, []),
+        "vate_launch_count": (u64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _check(rc: int) -> None:
+    if rc != VATE_OK:
+        raise VateError(rc, _lib.vate_last_error().decode())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev(t, dtype, name: str, count: Optional[int] = None) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if count is not None and t.numel() < count:
+        raise ValueError("%s holds %d elements, %d needed" % (name, t.numel(), count))
+    return t.data_ptr()
+
+
+def _host(a, dtype, name: str, output: bool = False):
+    """(pointer, keep-alive object, element count) of a host array.  Outputs
+    must already have the right dtype and layout (no converting copy)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda:
+                raise TypeError("%s must be a host array" % name)
+            if not a.is_contiguous():
+                raise ValueError("%s must be contiguous" % name)
+            if a.element_size() != np.dtype(dtype).itemsize:
+                raise TypeError("%s must have %d-byte elements" % (name, np.dtype(dtype).itemsize))
+            return a.data_ptr(), a, a.numel()
+    except ImportError:
+        pass
+    if output:
+        if not isinstance(a, np.ndarray) or a.dtype != np.dtype(dtype) or not a.flags.c_contiguous:
+            raise TypeError("%s must be a C-contiguous numpy array of %s" % (name, np.dtype(dtype)))
+        return a.ctypes.data, a, a.size
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, arr, arr.size
+
+
+def make_params(log2_pool: int, k: int, g: int, seg_len: int = 1, partition: int = 0, seed: int = 0) -> vate_params:
+    return vate_params(log2_pool, k, g, seg_len, partition, 0, seed & 0xFFFFFFFFFFFFFFFF)
+
+
+# ---- the C ABI, one function per entry point --------------------------------
+
+def vate_create(params: vate_params, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(_lib.vate_create(C.byref(params), _stream(stream), C.byref(h)))
+    _k_of[h.value] = int(params.k)
+    return h
+
+
+def vate_destroy(h) -> None:
+    _k_of.pop(h.value if isinstance(h, C.c_void_p) else h, None)
+    _check(_lib.vate_destroy(h))
+
+
+def vate_ingest(h, pairs, slice: int, stream=None) -> None:
+    """pairs: CUDA tensor of shape (n, 2), dtype int32/uint32 (aip, bip)."""
+    import torch
+    n = pairs.shape[0] if pairs.dim() == 2 else pairs.numel() // 2
+    ptr = _dev(pairs, pairs.dtype if pairs.dtype in (torch.int32, torch.uint32) else torch.int32, "pairs")
+    _check(_lib.vate_ingest(h, ptr if n else None, n, slice, _stream(stream)))
+
+
+def vate_close_slice(h, slice: int, stream=None) -> None:
+    _check(_lib.vate_close_slice(h, slice, _stream(stream)))
+
+
+def vate_estimate(h, aips, kprime: int, out, flags=None, stream=None) -> None:
+    import torch
+    n = aips.numel()
+    pa = _dev(aips, aips.dtype if aips.dtype in (torch.int32, torch.uint32) else torch.int32, "aips")
+    po = _dev(out, torch.float32, "out", n)
+    pf = _dev(flags, torch.uint8, "flags", n) if flags is not None else None
+    _check(_lib.vate_estimate(h, pa, n, kprime, po, pf, _stream(stream)))
+
+
+def vate_active_counts(h, aips, kprime: int, active, stream=None) -> None:
+    import torch
+    n = aips.numel()
+    pa = _dev(aips, aips.dtype if aips.dtype in (torch.int32, torch.uint32) else torch.int32, "aips")
+    pc = _dev(active, active.dtype if active.dtype in (torch.int32, torch.uint32) else torch.int32, "active", n)
+    _check(_lib.vate_active_counts(h, pa, n, kprime, pc, _stream(stream)))
+
+
+def vate_age_counts(h, aips, counts, stream=None) -> None:
+    import torch
+    n = aips.numel()
+    pa = _dev(aips, aips.dtype if aips.dtype in (torch.int32, torch.uint32) else torch.int32, "aips")
+    k = vate_get_info_k(h)
+    pc = _dev(counts, counts.dtype if counts.dtype in (torch.int16, torch.uint16) else torch.int16, "counts", n * k)
+    _check(_lib.vate_age_counts(h, pa, n, pc, _stream(stream)))
+
+
+def vate_census(h, hist, stream=None) -> None:
+    import torch
+    k = vate_get_info_k(h)
+    _check(_lib.vate_census(h, _dev(hist, hist.dtype if hist.dtype in (torch.int64, torch.uint64) else torch.int64,
+                                    "hist", 2 * k + 1), _stream(stream)))
+
+
+def vate_copy_pool(h, dst, stream=None) -> None:
+    import torch
+    _check(_lib.vate_copy_pool(h, _dev(dst, torch.uint8, "dst"), _stream(stream)))
+
+
+def vate_load_pool(h, src, stream=None) -> None:
+    import torch
+    _check(_lib.vate_load_pool(h, _dev(src, torch.uint8, "src"), _stream(stream)))
+
+
+def vate_ingest_host(h, pairs, slice: int, stream=None) -> None:
+    ptr, keep, cnt = _host(pairs, np.uint32, "pairs")
+    n = cnt // 2
+    _check(_lib.vate_ingest_host(h, ptr if n else None, n, slice, _stream(stream)))
+    return keep
+
+
+def vate_estimate_host(h, aips, kprime: int, out, flags=None, stream=None) -> None:
+    pa, ka, n = _host(aips, np.uint32, "aips")
+    po, ko, no = _host(out, np.float32, "out", output=True)
+    if no < n:
+        raise ValueError("out is too small")
+    pf = None
+    if flags is not None:
+        pf, kf, nf = _host(flags, np.uint8, "flags", output=True)
+        if nf < n:
+            raise ValueError("flags is too small")
+    _check(_lib.vate_estimate_host(h, pa, n, kprime, po, pf, _stream(stream)))
+
+
+_k_of = {}
+
+
+def vate_get_info_k(h) -> int:
+    """k of a handle (kept by the binding at creation, for buffer-size checks)."""
+    return _k_of[h.value if isinstance(h, C.c_void_p) else int(h)]
+
+
+def vate_get_info(h) -> vate_info:
+    info = vate_info()
+    _check(_lib.vate_get_info(h, C.byref(info)))
+    return info
+
+
+def vate_host_h(params: vate_params, aip: int, i: int) -> int:
+    out = C.c_uint64()
+    _check(_lib.vate_host_h(C.byref(params), aip, i, C.byref(out)))
+    return int(out.value)
+
+
+def vate_host_bh(params: vate_params, bip: int) -> int:
+    out = C.c_uint32()
+    _check(_lib.vate_host_bh(C.byref(params), bip, C.byref(out)))
+    return int(out.value)
+
+
+def vate_host_block(params: vate_params, pid: int) -> int:
+    out = C.c_uint32()
+    _check(_lib.vate_host_block(C.byref(params), pid, C.byref(out)))
+    return int(out.value)
+
+
+def vate_last_error() -> str:
+    return _lib.vate_last_error().decode()
+
+
+def vate_launch_count() -> int:
+    return int(_lib.vate_launch_count())
+
+
+class Vate:
+    """Owns one handle; methods forward to the functions above."""
+
+    def __init__(self, log2_pool: int, k: int, g: int, seg_len: int = 1, partition: int = 0, seed: int = 0,
+                 stream=None):
+        self.params = make_params(log2_pool, k, g, seg_len, partition, seed)
+        self.k, self.g, self.P = k, g, 1 << log2_pool
+        self.h = vate_create(self.params, stream)
+
+    def close(self) -> None:
+        if self.h:
+            vate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ingest(self, pairs, slice, stream=None):
+        vate_ingest(self.h, pairs, slice, stream)
+
+    def close_slice(self, slice, stream=None):
+        vate_close_slice(self.h, slice, stream)
+
+    def estimate(self, aips, kprime, out, flags=None, stream=None):
+        vate_estimate(self.h, aips, kprime, out, flags, stream)
+
+    def active_counts(self, aips, kprime, active, stream=None):
+        vate_active_counts(self.h, aips, kprime, active, stream)
+
+    def age_counts(self, aips, counts, stream=None):
+        vate_age_counts(self.h, aips, counts, stream)
+
+    def census(self, hist, stream=None):
+        vate_census(self.h, hist, stream)
+
+    def copy_pool(self, dst, stream=None):
+        vate_copy_pool(self.h, dst, stream)
+
+    def load_pool(self, src, stream=None):
+        vate_load_pool(self.h, src, stream)
+
+    def info(self) -> vate_info:
+        return vate_get_info(self.h)

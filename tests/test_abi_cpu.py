@@ -1,0 +1,127 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every symbol
+that include/vate.h declares, validates arguments on the host, and its
+host-side mapping (H, BH, block of Eq. 9-10 / low-deviation partition) agrees
+with the oracle.  No kernel is launched here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_1812_00282_b300 import build
+    build.build()
+    import paper_1812_00282_b300 as V
+    return V
+
+
+def declared_functions():
+    names = []
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(vate_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(V):
+    names = declared_functions()
+    assert "vate_create" in names and "vate_estimate" in names and len(names) >= 18
+    lib = ctypes.CDLL(V.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+        assert hasattr(V, n), "binding lacks " + n
+
+
+@pytest.mark.parametrize("bad", [
+    dict(log2_pool=11), dict(log2_pool=33), dict(k=0), dict(k=64), dict(g=0), dict(g=65537),
+    dict(seg_len=3), dict(seg_len=128), dict(g=1000, seg_len=32), dict(partition=2),
+])
+def test_invalid_parameters_rejected_on_host(V, bad):
+    p = dict(log2_pool=20, k=5, g=1024, seg_len=32, partition=0, seed=1)
+    p.update(bad)
+    params = V.make_params(**p)
+    with pytest.raises(V.VateError) as ei:
+        V.vate_create(params, stream=0)
+    assert ei.value.code == V.VATE_EINVAL
+
+
+def test_reserved_field_must_be_zero(V):
+    params = V.make_params(20, 5, 1024)
+    params.reserved = 1
+    with pytest.raises(V.VateError) as ei:
+        V.vate_create(params, stream=0)
+    assert ei.value.code == V.VATE_EINVAL
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU error path")
+def test_create_without_gpu_reports_cuda_error(V):
+    with pytest.raises(V.VateError) as ei:
+        V.vate_create(V.make_params(20, 5, 1024), stream=0)
+    assert ei.value.code == V.VATE_ECUDA
+    assert "device" in V.vate_last_error().lower() or "driver" in V.vate_last_error().lower()
+
+
+CASES = [(20, 5, 1024, 1, 0, 1), (20, 5, 1024, 32, 0, 2), (26, 10, 4096, 32, 0, 0xC2), (24, 10, 4096, 32, 1, 3),
+         (14, 63, 256, 16, 0, 4), (13, 1, 64, 64, 1, 5), (32, 10, 512, 8, 0, 6), (16, 7, 96, 2, 1, 7)]
+
+
+@pytest.mark.parametrize("c,k,g,L,part,seed", CASES)
+def test_host_mapping_matches_oracle(V, c, k, g, L, part, seed):
+    params = V.make_params(c, k, g, L, part, seed)
+    o = oracle.Oracle(c=c, k=k, g=g, seg_len=L, partition=part, seed=seed) if c <= 26 else None
+    rng = np.random.default_rng(seed)
+    if o is None:
+        # the oracle allocates the pool; for 2^32 compare the mixer-level spec instead
+        key_h, key_bh = oracle.mix64(seed + 1), oracle.mix64(seed + 2)
+        for _ in range(200):
+            aip, i = int(rng.integers(0, 2**32)), int(rng.integers(0, g))
+            j, off = i // L, i % L
+            seg = oracle.mix64(key_h ^ (aip << 32) ^ j) >> (64 - (c - int(np.log2(L))))
+            assert V.vate_host_h(params, aip, i) == seg * L + off
+            bip = int(rng.integers(0, 2**32))
+            assert V.vate_host_bh(params, bip) == ((oracle.mix64(key_bh ^ bip) >> 32) * g) >> 32
+        return
+    for _ in range(300):
+        aip, i, bip = int(rng.integers(0, 2**32)), int(rng.integers(0, g)), int(rng.integers(0, 2**32))
+        assert V.vate_host_h(params, aip, i) == o.h(aip, i)
+        assert V.vate_host_bh(params, bip) == o.bh(bip)
+    P = 1 << c
+    probes = set(int(x) for x in rng.integers(0, P, size=500))
+    for i in range(2 * k + 1):          # every block boundary and its neighbours
+        for base in (i * o.a, i * (o.a + 1), o.a * (2 * k - o.b) + (i - (2 * k - o.b)) * (o.a + 1)):
+            for d in (-1, 0, 1):
+                if 0 <= base + d < P:
+                    probes.add(base + d)
+    probes.add(P - 1)
+    for pid in probes:
+        assert V.vate_host_block(params, pid) == o.block(pid), pid
+
+
+def test_block_division_exact_near_2_32(V):
+    # c = 32: pool positions up to 2^32 - 1 go through the 64-bit multiply-high
+    # division; compare with exact integer division at the extremes.
+    for k, part in ((10, 0), (10, 1), (1, 0), (63, 1)):
+        params = V.make_params(32, k, 64, 1, part, 0)
+        P, twok = 1 << 32, 2 * k
+        if part == 0:
+            a = P // (twok - 1)
+            ref = lambda pid: pid // a
+        else:
+            a, b = P // twok, P % twok
+            first = a * (twok - b)
+            ref = lambda pid: pid // a if pid < first else (pid + twok - b) // (a + 1)
+        for pid in [0, 1, a - 1, a, a + 1, P - 2, P - 1] + [P - 1 - 7919 * j for j in range(200)]:
+            if pid >= P:
+                continue
+            assert V.vate_host_block(params, pid) == ref(pid), (k, part, pid)

@@ -1,0 +1,270 @@
+"""Parity of the CUDA path with the CPU oracle, element by element.
+
+Every test drives the device through the C ABI (Python binding) and the
+oracle through Algorithm 4 on the same seeded inputs and compares:
+  - the AT pool, byte for byte, after every slice (bit-exact);
+  - the pool census (bit-exact);
+  - the active VAT count A of every host and window k' (bit-exact);
+  - the per-age VAT counts (bit-exact);
+  - the estimates of Eq. 11: |device - oracle| <= 1e-5 * max(|oracle|, 1)
+    (FP32 on the device, FP64 in the oracle; the FP32 path evaluates
+    g*log1p(x) from exact integers, a few ulp from the FP64 value);
+  - the SAT / POOLFULL flags (bit-exact).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import Oracle
+from traffic import LINK40G, SMALL, Traffic, mixed_hosts
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1812_00282_b300 as V
+    return V
+
+
+def dev_pairs(pairs):
+    return torch.from_numpy(np.ascontiguousarray(pairs, np.uint32).view(np.int32)).cuda()
+
+
+def dev_u32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.uint32).view(np.int32)).cuda()
+
+
+def compare_close(V, d, o, hosts, kps, check_pool=True, check_ages=True):
+    """Compare device handle d (a Vate) and oracle o at a closed slice."""
+    k = o.k
+    if check_pool:
+        pool = torch.empty(o.P, dtype=torch.uint8, device="cuda")
+        d.copy_pool(pool)
+        dp = pool.cpu().numpy()
+        op = o.pool()
+        if not np.array_equal(dp, op):
+            bad = np.nonzero(dp != op)[0]
+            raise AssertionError("pool differs at %d positions, first %s: dev %s oracle %s"
+                                 % (bad.size, bad[:5], dp[bad[:5]], op[bad[:5]]))
+    hist = torch.empty(2 * k + 1, dtype=torch.int64, device="cuda")
+    d.census(hist)
+    np.testing.assert_array_equal(hist.cpu().numpy().astype(np.uint64), o.census())
+    dh = dev_u32(hosts)
+    n = len(hosts)
+    for kp in kps:
+        est = torch.empty(n, dtype=torch.float32, device="cuda")
+        fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+        act = torch.empty(n, dtype=torch.int32, device="cuda")
+        d.estimate(dh, kp, est, fl)
+        d.active_counts(dh, kp, act)
+        oe, oa, of = o.estimate(hosts, kp)
+        np.testing.assert_array_equal(act.cpu().numpy().view(np.uint32), oa, err_msg="A, k'=%d" % kp)
+        np.testing.assert_array_equal(fl.cpu().numpy(), of, err_msg="flags, k'=%d" % kp)
+        de = est.cpu().numpy().astype(np.float64)
+        err = np.abs(de - oe) / np.maximum(np.abs(oe), 1.0)
+        assert err.max() <= RTOL, "k'=%d max rel err %.3g at host %d (dev %r, oracle %r)" % (
+            kp, err.max(), int(err.argmax()), de[err.argmax()], oe[err.argmax()])
+    if check_ages and o.g <= 65535:
+        ages = torch.empty(n * k, dtype=torch.int16, device="cuda")
+        d.age_counts(dh, ages)
+        np.testing.assert_array_equal(ages.cpu().numpy().view(np.uint16).reshape(n, k).astype(np.uint32),
+                                      o.age_counts(hosts))
+
+
+def run_stream(V, params, slices, hosts, kps, slice_ids=None, check_every=1, **kw):
+    c, k, g, L, part, seed = params
+    d = V.Vate(c, k, g, L, part, seed)
+    o = Oracle(c=c, k=k, g=g, seg_len=L, partition=part, seed=seed)
+    ids = list(range(len(slices))) if slice_ids is None else slice_ids
+    prev = None
+    for j, (sid, arr) in enumerate(zip(ids, slices)):
+        if prev is not None:
+            for _ in range(sid - prev):
+                o.advance()
+        prev = sid
+        d.ingest(dev_pairs(arr), sid)
+        o.ingest(arr)
+        d.close_slice(sid)
+        if j % check_every == 0 or j == len(slices) - 1:
+            compare_close(V, d, o, hosts, kps, **kw)
+    torch.cuda.synchronize()
+    d.close()
+    return o
+
+
+@pytest.mark.parametrize("L", [1, 32])
+@pytest.mark.parametrize("partition", [0, 1])
+def test_small_traffic_parity(V, L, partition):
+    tr = Traffic(SMALL, pkts_per_slice=20_000)
+    k = 5
+    slices = [tr.slice_pairs(s) for s in range(2 * k + 3)]
+    run_stream(V, (16, k, 1024, L, partition, 0xC1), slices, tr.aips, kps=(1, 3, k))
+
+
+@pytest.mark.parametrize("L", [2, 4, 8, 16, 64])
+def test_other_segment_lengths(V, L):
+    tr = Traffic(SMALL, pkts_per_slice=15_000)
+    k = 4
+    slices = [tr.slice_pairs(s) for s in range(2 * k + 2)]
+    run_stream(V, (15, k, 256, L, 0, 11), slices, tr.aips[:1500], kps=(1, k), check_every=3)
+
+
+@pytest.mark.parametrize("k,c,g", [(1, 12, 64), (2, 13, 96), (10, 16, 4096), (63, 14, 512)])
+def test_window_lengths(V, k, c, g):
+    tr = Traffic(SMALL, pkts_per_slice=8_000)
+    slices = [tr.slice_pairs(s) for s in range(2 * k + 3 if k < 20 else 20)]
+    run_stream(V, (c, k, g, 32 if g % 32 == 0 else 1, 0, k), slices, tr.aips[:800], kps=sorted({1, (k + 1) // 2, k}),
+               check_every=2 if k < 20 else 5)
+
+
+def test_ragged_gaps_and_empty_slices(V):
+    # odd batch sizes, an 8-byte aligned (not 16) pointer, empty slices, several
+    # ingests per slice, and slice gaps shorter and longer than 2k
+    tr = Traffic(SMALL, pkts_per_slice=9_999)
+    k = 3
+    params = (14, k, 128, 1, 1, 5)
+    c, _, g, L, part, seed = params
+    d = V.Vate(c, k, g, L, part, seed)
+    o = Oracle(c=c, k=k, g=g, seg_len=L, partition=part, seed=seed)
+    ids = [4, 5, 6, 8, 9, 17, 18, 19, 21, 40, 41]
+    prev = None
+    for j, sid in enumerate(ids):
+        if prev is not None:
+            for _ in range(sid - prev):
+                o.advance()
+        prev = sid
+        arr = tr.slice_pairs(sid, n=0 if sid in (8, 19) else 9_999 - 2 * j)
+        buf = dev_pairs(np.concatenate([np.zeros((1, 2), np.uint32), arr]))   # offset by one pair (8 B)
+        half = len(arr) // 3
+        d.ingest(buf[1:1 + half], sid)
+        d.ingest(buf[1 + half:], sid)
+        d.ingest(buf[:0], sid)
+        o.ingest(arr)
+        d.close_slice(sid)
+        compare_close(V, d, o, tr.aips[:700], kps=(1, 2, 3))
+    d.close()
+
+
+def test_constructed_pools_straddling_segments(V):
+    # Random AT values everywhere (loaded through the ABI) on a small pool, so
+    # that many 32-AT segments straddle a block boundary; census, active counts,
+    # estimates and ages must still match the oracle on the same pool.
+    rng = np.random.default_rng(3)
+    for (c, k, g, L, part) in ((12, 5, 1024, 32, 0), (12, 4, 512, 64, 1), (13, 7, 256, 16, 0), (12, 3, 200, 8, 1)):
+        d = V.Vate(c, k, g, L, part, 9)
+        o = Oracle(c=c, k=k, g=g, seg_len=L, partition=part, seed=9)
+        hosts = rng.integers(0, 2**32, size=600, dtype=np.uint64).astype(np.uint32)
+        for t in range(3):
+            pool = rng.integers(0, 2 * k + 1, size=1 << c).astype(np.uint8)
+            pool[rng.random(1 << c) < 0.3] = 2 * k
+            d.ingest(dev_pairs(np.zeros((0, 2), np.uint32)), t)
+            if t:
+                o.advance()
+            d.load_pool(torch.from_numpy(pool).cuda())
+            o.load_pool(pool)
+            d.close_slice(t)
+            compare_close(V, d, o, hosts, kps=range(1, k + 1))
+        d.close()
+
+
+def test_saturation_and_pool_full_flags(V):
+    # every pool AT set in the current slice (value = ACT of its block): every
+    # VAT of every host is active (SAT) and no pool AT is inactive (POOLFULL)
+    c, k, g = 12, 2, 64
+    d = V.Vate(c, k, g, 1, 0, 1)
+    o = Oracle(c=c, k=k, g=g, seed=1)
+    pool = np.array([o.act_of(p) for p in range(1 << c)], np.uint8)
+    d.ingest(dev_pairs(np.zeros((0, 2), np.uint32)), 0)
+    d.load_pool(torch.from_numpy(pool).cuda())
+    o.load_pool(pool)
+    d.close_slice(0)
+    hosts = np.arange(1, 50, dtype=np.uint32)
+    compare_close(V, d, o, hosts, kps=(1, 2), check_ages=False)
+    est = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+    fl = torch.empty(len(hosts), dtype=torch.uint8, device="cuda")
+    d.estimate(dev_u32(hosts), 2, est, fl)
+    assert np.all(fl.cpu().numpy() == V.VATE_FLAG_SAT | V.VATE_FLAG_POOLFULL)
+    assert np.all(np.isfinite(est.cpu().numpy()))
+    d.close()
+
+
+def test_state_machine_errors(V):
+    d = V.Vate(14, 3, 64, 1, 0, 1)
+    hosts = dev_u32(np.arange(10, dtype=np.uint32))
+    out = torch.empty(10, dtype=torch.float32, device="cuda")
+    with pytest.raises(V.VateError) as e:
+        d.estimate(hosts, 1, out)                 # no slice closed yet
+    assert e.value.code == V.VATE_ESLICE
+    d.ingest(dev_pairs(np.array([[1, 2]], np.uint32)), 7)
+    with pytest.raises(V.VateError) as e:
+        d.ingest(dev_pairs(np.array([[1, 2]], np.uint32)), 6)   # past slice
+    assert e.value.code == V.VATE_ESLICE
+    d.close_slice(7)
+    with pytest.raises(V.VateError) as e:
+        d.ingest(dev_pairs(np.array([[1, 2]], np.uint32)), 7)   # closed slice
+    assert e.value.code == V.VATE_ESLICE
+    with pytest.raises(V.VateError) as e:
+        d.close_slice(7)
+    assert e.value.code == V.VATE_ESLICE
+    for bad_kp in (0, 4):
+        with pytest.raises(V.VateError) as e:
+            d.estimate(hosts, bad_kp, out)
+        assert e.value.code == V.VATE_EINVAL
+    d.estimate(hosts, 3, out)                      # repeated estimates are fine
+    d.estimate(hosts, 1, out)
+    info = d.info()
+    assert (info.slice, info.closed, info.bact0) == (7, 1, 0)
+    d.ingest(dev_pairs(np.array([[1, 2]], np.uint32)), 9)
+    info = d.info()
+    assert (info.slice, info.closed, info.bact0) == (9, 0, 2)
+    d.close()
+
+
+def test_host_buffer_entry_points_match_device_ones(V):
+    tr = Traffic(SMALL, pkts_per_slice=(1 << 20) + 12345)   # more than one staging chunk
+    k = 5
+    params = (18, k, 1024, 32, 0, 2)
+    d1, d2 = V.Vate(*params), V.Vate(*params)
+    hosts = tr.aips
+    for s in range(3):
+        arr = tr.slice_pairs(s)
+        d1.ingest(dev_pairs(arr), s)
+        pinned = torch.from_numpy(arr.view(np.int32)).pin_memory()
+        V.vate_ingest_host(d2.h, pinned, s)
+        d1.close_slice(s)
+        d2.close_slice(s)
+        p1 = torch.empty(d1.P, dtype=torch.uint8, device="cuda")
+        p2 = torch.empty(d2.P, dtype=torch.uint8, device="cuda")
+        d1.copy_pool(p1)
+        d2.copy_pool(p2)
+        assert torch.equal(p1, p2)
+        e1 = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+        f1 = torch.empty(len(hosts), dtype=torch.uint8, device="cuda")
+        d1.estimate(dev_u32(hosts), k, e1, f1)
+        e2 = np.empty(len(hosts), np.float32)
+        f2 = np.empty(len(hosts), np.uint8)
+        V.vate_estimate_host(d2.h, hosts, k, e2, f2)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(e1.cpu().numpy(), e2)
+        np.testing.assert_array_equal(f1.cpu().numpy(), f2)
+    d1.close()
+    d2.close()
+
+
+@pytest.mark.slow
+def test_full_size_40g_shape_sampled(V):
+    # The 40 Gb/s workload at full size -- 2^26-AT pool, g = 4096, L = 32,
+    # k = 10, 5M pairs per slice -- through the same entry points and launch
+    # configuration as the benchmark.  The whole pool and census are compared
+    # every slice; estimates on a seeded sample of hosts plus every
+    # super-spreader (the oracle computes them one by one).
+    tr = Traffic(LINK40G)
+    hosts = mixed_hosts(tr, 2048)
+    k = 10
+    slices = [tr.slice_pairs(s) for s in range(k + 2)]
+    run_stream(V, (26, k, 4096, 32, 0, 0xC2), slices, hosts, kps=(1, k), check_every=4, check_ages=True)
