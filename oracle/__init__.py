@@ -80,6 +80,7 @@ def _load():
             "vo_check_all": (None, [vp, u32, u8p]),
             "vo_census": (None, [vp, u64p]),
             "vo_pool_inactive": (u64, [vp, u32]),
+            "vo_pool_inactive_range": (u64, [vp, u32, u64, u64]),
             "vo_estimate_from_counts": (C.c_double, [u32, u64, u64, u32, C.POINTER(C.c_uint8)]),
             "vo_active_vats": (u32, [vp, u32, u32]),
             "vo_estimate": (None, [vp, u32p, u64, u32, f64p, u32p, u8p]),
@@ -228,6 +229,9 @@ class Oracle:
 
     def pool_inactive(self, kprime: int) -> int:
         return int(self._lib.vo_pool_inactive(self._s, kprime))
+
+    def pool_inactive_range(self, kprime: int, start: int, end: int) -> int:
+        return int(self._lib.vo_pool_inactive_range(self._s, kprime, start, end))
 
     def active_vats(self, aip: int, kprime: int) -> int:
         return int(self._lib.vo_active_vats(self._s, aip, kprime))

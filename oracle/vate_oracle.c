@@ -347,6 +347,17 @@ uint64_t vo_pool_inactive(const vo_state *s, uint32_t kprime)
     return n0;
 }
 
+/* Inactive ATs for window k' among pool positions [start, end) (a bounded
+ * sample of the census, for timing on a slice of the pool). */
+uint64_t vo_pool_inactive_range(const vo_state *s, uint32_t kprime, uint64_t start, uint64_t end)
+{
+    uint64_t n0 = 0;
+    if (end > s->P) end = s->P;
+    for (uint64_t q = start; q < end; q++)
+        if (!vo_check_at(s->pool[q], vo_act_of(s, q), s->k, kprime)) n0++;
+    return n0;
+}
+
 /* Eq. 11 for one host, given the host's active VAT count A (out of g)
  * and the pool's inactive count N0 (out of P).  Reading R1 for the sign,
  * R10 for the two degenerate cases.  flags bit 0 = SAT, bit 1 = POOLFULL. */

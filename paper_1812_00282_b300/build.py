@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libvate.so")
-SOURCES = ["vate_api.cu", "vate_kernels.cu"]
+SOURCES = ["vate_api.cu", "vate_kernels.cu", "vate_probe.cu"]
 HEADERS = ["vate_device.cuh", "vate_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,7 +33,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, "vate.h")]
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + \
+        [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -66,6 +66,8 @@ def _load() -> C.CDLL:
         "vate_host_block": (i, [P(vate_params), u64, P(u32)]),
         "vate_last_error": (C.c_char_p, []),
         "vate_launch_count": (u64, []),
+        "vate_probe_sector_read": (i, [vp, u64, u64, vp, vp]),
+        "vate_probe_byte_write": (i, [vp, u64, u64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -258,6 +260,19 @@ def vate_last_error() -> str:
 
 def vate_launch_count() -> int:
     return int(_lib.vate_launch_count())
+
+
+def vate_probe_sector_read(buf, n_sectors: int, sink, stream=None) -> None:
+    """Random 32-byte sector reads from a CUDA uint8 buffer (include/vate_probe.h)."""
+    import torch
+    _check(_lib.vate_probe_sector_read(_dev(buf, torch.uint8, "buf"), buf.numel(), n_sectors,
+                                       _dev(sink, sink.dtype, "sink"), _stream(stream)))
+
+
+def vate_probe_byte_write(buf, n_writes: int, stream=None) -> None:
+    """Random 1-byte stores into a CUDA uint8 buffer (include/vate_probe.h)."""
+    import torch
+    _check(_lib.vate_probe_byte_write(_dev(buf, torch.uint8, "buf"), buf.numel(), n_writes, _stream(stream)))
 
 
 class Vate:

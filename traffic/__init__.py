@@ -111,3 +111,41 @@ def mixed_hosts(tr: Traffic, n: int, seed: int = 7) -> np.ndarray:
     idx = rng.choice(tr.spec.n_aips, size=min(n, tr.spec.n_aips), replace=False)
     idx = np.union1d(idx, tr.super_hosts)
     return tr.aips[idx]
+
+
+class DeviceTraffic:
+    """The same traffic model drawn on a CUDA device with torch's Philox
+    generator (a different random stream from ``Traffic.slice_pairs``, the same
+    distribution), for benchmarks that need hundreds of 5M-pair slices
+    resident in device memory.  Host table = ``tr``'s."""
+
+    def __init__(self, tr: Traffic, device="cuda"):
+        import torch
+        self.tr, self.device = tr, device
+        self.rank_cdf = torch.from_numpy(tr.rank_cdf).to(device)
+        self.rank_host = torch.from_numpy(tr.rank_host).to(device)
+        self.pool_size = torch.from_numpy(tr.pool_size.astype(np.float64)).to(device)
+        self.peer_base = torch.from_numpy(tr.peer_base.astype(np.int64)).to(device)
+        self.aips = torch.from_numpy(tr.aips.astype(np.int64)).to(device)
+        self.gen = torch.Generator(device=device)
+
+    def slice_pairs(self, s: int, n: Optional[int] = None):
+        """(n, 2) int32 CUDA tensor holding the uint32 bit patterns of (aip, bip)."""
+        import torch
+        n = self.tr.pkts_per_slice if n is None else int(n)
+        self.gen.manual_seed((self.tr.spec.seed * 1_000_003 + 7919 * int(s) + 1) & 0x7FFFFFFFFFFFFFFF)
+        u = torch.rand(n, generator=self.gen, device=self.device, dtype=torch.float64)
+        rank = torch.searchsorted(self.rank_cdf, u, right=True).clamp_(max=self.tr.spec.n_aips - 1)
+        host = self.rank_host[rank]
+        j = torch.floor(torch.rand(n, generator=self.gen, device=self.device, dtype=torch.float64)
+                        * self.pool_size[host]).to(torch.int64)
+        bip = (self.peer_base[host] + j * 0x9E3779B1) & 0xFFFFFFFF
+        out = torch.stack([self.aips[host], bip], dim=1)
+        out = torch.where(out >= 2**31, out - 2**32, out).to(torch.int32).contiguous()
+        return out
+
+    def hosts(self):
+        """All host addresses as an int32 CUDA tensor (uint32 bit patterns)."""
+        import torch
+        a = self.aips
+        return torch.where(a >= 2**31, a - 2**32, a).to(torch.int32).contiguous()
