@@ -189,6 +189,33 @@ int vate_host_h(const vate_params *params, uint32_t aip, uint32_t i, uint64_t *p
 int vate_host_bh(const vate_params *params, uint32_t bip, uint32_t *vid);
 int vate_host_block(const vate_params *params, uint64_t pid, uint32_t *block);
 
+/* Pool census into caller-owned buffers, allocating no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let a library call cudaMalloc -- a packet-processing loop with a
+ * latency budget (cudaMalloc can synchronise the device and its duration is
+ * unbounded), or an application whose device memory is owned entirely by its
+ * own allocator (a caching allocator or a fixed arena), so that nothing is
+ * left for a library to request.  It needs no handle either.
+ *   params   geometry of the pool (log2_pool, k and partition are used; the
+ *            whole struct is validated as for vate_create).
+ *   d_pool   device uint8[P], 16-byte aligned, AT values in [0, 2k].
+ *   bact0    BACT^0 of the slice the pool belongs to, 0 <= bact0 < 2k.
+ *   d_hist   device uint64[2k+1]: receives the same census as vate_census
+ *            (d_hist[d] for distances 0 <= d < 2k, d_hist[2k] inactive).
+ * Scratch: the per-block partial histograms and a "blocks finished" counter
+ * live in one static device array of 300,992 bytes (296 blocks x 127 bins x
+ * 8 bytes + 256), which every GPU that loads the library holds until the
+ * process exits.  A request needing more (more than 127 bins) is rejected with
+ * VATE_EINVAL and a message giving both sizes.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call reuses the same array and
+ * clears its counter first, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race: order them on one stream.  No
+ * cudaMalloc, cudaFree or allocating library routine is called. */
+int vate_census_noalloc(const vate_params *params, const uint8_t *d_pool, uint32_t bact0, uint64_t *d_hist,
+                        void *stream);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *vate_last_error(void);
 

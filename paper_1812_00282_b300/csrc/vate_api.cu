@@ -100,6 +100,12 @@ void block_range(const Geom &G, uint32_t i, uint64_t *s, uint64_t *e) {
 
 void vate::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace vate {
+// parameter checks and error reporting for entry points without a handle
+int make_geom_checked(const vate_params *p, Geom *G) { return make_geom(p, G); }
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace vate
+
 struct vate_handle {
     vate_params prm;
     Geom G;

@@ -66,6 +66,7 @@ def _load() -> C.CDLL:
         "vate_host_block": (i, [P(vate_params), u64, P(u32)]),
         "vate_last_error": (C.c_char_p, []),
         "vate_launch_count": (u64, []),
+        "vate_census_noalloc": (i, [P(vate_params), vp, u32, vp, vp]),
         "vate_probe_sector_read": (i, [vp, u64, u64, vp, vp]),
         "vate_probe_byte_write": (i, [vp, u64, u64, vp]),
     }
@@ -260,6 +261,16 @@ def vate_last_error() -> str:
 
 def vate_launch_count() -> int:
     return int(_lib.vate_launch_count())
+
+
+def vate_census_noalloc(params: vate_params, pool, bact0: int, hist, stream=None) -> None:
+    """Census of a caller-owned pool into a caller-owned histogram; the library
+    allocates no device memory for it (include/vate.h)."""
+    import torch
+    pp = _dev(pool, torch.uint8, "pool", 1 << params.log2_pool)
+    ph = _dev(hist, hist.dtype if hist.dtype in (torch.int64, torch.uint64) else torch.int64, "hist",
+              2 * params.k + 1)
+    _check(_lib.vate_census_noalloc(C.byref(params), pp, bact0, ph, _stream(stream)))
 
 
 def vate_probe_sector_read(buf, n_sectors: int, sink, stream=None) -> None:
