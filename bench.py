@@ -314,7 +314,8 @@ def run_ours(args, rank, world, local):
         "config": {"workload": WORKLOAD, "aips": n_h, "pkts_per_slice": args.pkts, "k": K_WIN, "kprime": K_WIN,
                    "log2_pool": C, "g": G, "seg_len": args.seg_len, "partition": args.partition,
                    "link_gbps_equivalent": round(args.pkts * MEAN_PKT_BYTES * 8 / 1e9, 2),
-                   "l2": "flushed before every timed step (256 MiB write, outside the step events)"
+                   "l2": "flushed before every timed step (256 MiB write, outside the step events); the 64 MiB "
+                         "AT pool is state kept from slice to slice and its kernels mark it L2-persisting"
                    if not args.no_flush else "not flushed", "parallelism": "replicas" if world > 1 else "single"},
         "close_p50_ms": round(float(np.percentile(close_ms, 50)), 4),
         "close_p99_ms": round(float(np.percentile(close_ms, 99)), 4),

@@ -155,7 +155,7 @@ int advance_to(vate_handle *h, int64_t slice, cudaStream_t st) {
         uint64_t s0, e0, s1, e1;
         block_range(G, i0, &s0, &e0);
         block_range(G, i1, &s1, &e1);
-        cudaError_t e = vate::launch_preserve(G.pool, G.k, s0, e0, s1, e1, st, h->sms);
+        cudaError_t e = vate::launch_preserve(G, s0, e0, s1, e1, st, h->sms);
         if (e != cudaSuccess) return cuda_fail(e, "preserve launch");
     }
     if (steps > run) h->bact0 = (uint32_t)((h->bact0 + (uint64_t)(steps - run)) % G.twok);
@@ -248,6 +248,21 @@ int vate_create(const vate_params *params, void *stream, vate_handle **out) {
         }
         prepared = true;
     }
+    // Keep the pool resident in L2: its kernels launch with a persisting
+    // access-policy window over it (hit ratio = persisting capacity / pool).
+    {
+        int persist_max = 0, window_max = 0;
+        cudaDeviceGetAttribute(&persist_max, cudaDevAttrMaxPersistingL2CacheSize, h->device);
+        cudaDeviceGetAttribute(&window_max, cudaDevAttrMaxAccessPolicyWindowSize, h->device);
+        size_t cur = 0;
+        if (persist_max > 0 && window_max > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
+            if (cur < (size_t)persist_max) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist_max);
+            cudaGetLastError();
+            h->G.l2_window_bytes = G.P < (uint64_t)window_max ? G.P : (uint64_t)window_max;
+            double ratio = (double)persist_max / (double)h->G.l2_window_bytes;
+            h->G.l2_hit_ratio = ratio >= 1.0 ? 1.0f : (float)ratio;
+        }
+    }
     h->census_grid = h->sms * 4;
     size_t nbins = G.twok + 1;
     if (cudaMalloc(&h->G.pool, G.P) != cudaSuccess || cudaMalloc(&h->d_hist, nbins * sizeof(uint64_t)) != cudaSuccess ||
@@ -271,6 +286,12 @@ int vate_create(const vate_params *params, void *stream, vate_handle **out) {
 int vate_destroy(vate_handle *h) {
     if (!h) return VATE_OK;
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    if (h->G.l2_window_bytes) {
+        // lines of the freed pool must not keep the persisting carve-out
+        cudaDeviceSynchronize();
+        cudaCtxResetPersistingL2Cache();
+        cudaGetLastError();
+    }
     cudaFree(h->G.pool);
     cudaFree(h->d_hist);
     cudaFree(h->d_partial);

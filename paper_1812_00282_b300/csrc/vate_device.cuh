@@ -34,6 +34,10 @@ struct Geom {
     uint64_t ma1;        // ceil(2^64 / (a + 1)) (low-deviation partition)
     uint64_t first;      // low-deviation: ATs below this index are in blocks of size a
     uint32_t c, k, twok, g, L, log2L, segbits, partition;
+    // host side only: L2 access-policy window over the pool for every launch
+    // that touches it (l2_window_bytes = 0: none)
+    uint64_t l2_window_bytes;
+    float l2_hit_ratio;
 };
 
 VATE_HD uint64_t mix64(uint64_t x) {
@@ -87,39 +91,62 @@ VATE_HD uint32_t act_of_block(uint32_t bact0, uint32_t blk, uint32_t twok) {
 constexpr uint32_t ONES = 0x01010101u;
 constexpr uint32_t HIGH = 0x80808080u;
 
-// Constants selecting the ATs active in W(t-k'+1, k') for an AT whose ACT is
-// act: the active values are {act, act-1, ..., act-k'+1} mod 2k.  They form
-// one range [act-k'+1, act] or, when that wraps below 0, the two ranges
-// [0, act] and [act-k'+1+2k, 2k-1].  A range [lo, hi] is tested per byte as
-// "bit 7 of (v + 128 - lo)" and not "bit 7 of (v + 127 - hi)"; an empty
-// range uses lo = 128.
-struct CheckConsts {
-    uint32_t ge1, gt1, ge2, gt2;
+// Algorithm 1 on four ATs of one word.  For an AT whose ACT is act, the
+// values active in W(t-k'+1, k') are {act, act-1, ..., act-k'+1} mod 2k.
+// Either that set is one range [act-k'+1, act], or (when it wraps below 0)
+// its complement within [0, 2k-1] is the one range [act+1, act+2k-k'].  So
+// one range test per byte suffices: bit 7 of (v + 128 - lo) and not bit 7 of
+// (v + 127 - hi) says lo <= v <= hi; f flips the result for the complement
+// case, and bit 7 of (v + 128 - 2k) removes the inactive value 2k.
+struct RangeConsts {
+    uint32_t a1, b1, f, pad;
 };
 
-VATE_HD CheckConsts check_consts(uint32_t act, uint32_t kprime, uint32_t twok) {
-    CheckConsts cc;
+VATE_HD RangeConsts range_consts(uint32_t act, uint32_t kprime, uint32_t twok) {
+    RangeConsts rc;
     int lo = (int)act - (int)kprime + 1;
+    uint32_t rlo, rhi;
     if (lo >= 0) {
-        cc.ge1 = (128u - (uint32_t)lo) * ONES;
-        cc.gt1 = (127u - act) * ONES;
-        cc.ge2 = 0u;                  // lo = 128: never
-        cc.gt2 = 0u;
+        rlo = (uint32_t)lo;
+        rhi = act;
+        rc.f = 0u;
     } else {
-        cc.ge1 = 128u * ONES;         // lo = 0: always
-        cc.gt1 = (127u - act) * ONES;
-        uint32_t lo2 = (uint32_t)(lo + (int)twok);
-        cc.ge2 = (128u - lo2) * ONES;
-        cc.gt2 = (127u - (twok - 1u)) * ONES;
+        rlo = act + 1u;
+        rhi = act + twok - kprime;
+        rc.f = HIGH;
     }
-    return cc;
+    rc.a1 = (128u - rlo) * ONES;
+    rc.b1 = (127u - rhi) * ONES;
+    rc.pad = 0u;
+    return rc;
 }
 
-// bit 7 set in each byte of w holding an active AT (Algorithm 1 on 4 ATs)
-VATE_HD uint32_t swar_active(uint32_t w, const CheckConsts &cc) {
-    uint32_t r1 = (w + cc.ge1) & ~(w + cc.gt1);
-    uint32_t r2 = (w + cc.ge2) & ~(w + cc.gt2);
-    return (r1 | r2) & HIGH;
+// bit 7 set in each byte of w holding an active AT; c2k = (128 - 2k) * ONES
+VATE_HD uint32_t swar_active(uint32_t w, const RangeConsts &rc, uint32_t c2k) {
+    uint32_t r = ((w + rc.a1) & ~(w + rc.b1)) ^ rc.f;
+    return r & ~(w + c2k) & HIGH;
+}
+
+// swar_active with its three byte-wise additions written as multiply-adds by
+// run-time ones (u1..u3, all 1): the same arithmetic, issued on the
+// multiply-add pipe instead of the integer-logic pipe that the two LOP3s
+// already load.
+__device__ __forceinline__ uint32_t swar_active_fma(uint32_t w, const RangeConsts &rc, uint32_t c2k, uint32_t u1,
+                                                    uint32_t u2, uint32_t u3) {
+    uint32_t r = ((w * u1 + rc.a1) & ~(w * u2 + rc.b1)) ^ rc.f;
+    return r & ~(w * u3 + c2k) & HIGH;
+}
+
+// Census bin of four ATs whose ACT is act: byte = (act + 2k - v) mod 2k, the
+// distance of Eq. 5, or 2k for an inactive AT.  Valid values (v <= 2k) never
+// borrow across bytes; callers clamp each byte to 2k anyway.
+VATE_HD uint32_t swar_bins(uint32_t w, uint32_t act, uint32_t twok) {
+    uint32_t t = (act + twok) * ONES - w;
+    uint32_t ge = (t + (128u - twok) * ONES) & HIGH;          // t >= 2k
+    uint32_t d = t - (ge >> 7) * twok;
+    uint32_t e = (w + (128u - twok) * ONES) & HIGH;           // v >= 2k: inactive
+    uint32_t E = (e >> 7) * 0xFFu;
+    return (d & ~E) | ((twok * ONES) & E);
 }
 
 // Algorithm 3 on 4 ATs: at ACT 0 values 0..k become 2k; at ACT k values k..2k-1

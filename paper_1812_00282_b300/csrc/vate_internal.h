@@ -16,8 +16,8 @@ void count_launch();
 
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms);
 cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, uint64_t n, cudaStream_t st, int sms);
-cudaError_t launch_preserve(uint8_t *pool, uint32_t k, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
-                            cudaStream_t st, int sms);
+cudaError_t launch_preserve(const Geom &G, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1, cudaStream_t st,
+                            int sms);
 size_t census_smem_bytes(uint32_t twok);
 cudaError_t census_prepare(uint32_t twok);
 cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,

@@ -15,6 +15,8 @@
 #include "vate_device.cuh"
 #include "vate_internal.h"
 
+#include <utility>
+
 namespace vate {
 
 // --------------------------------------------------------------------------
@@ -103,10 +105,43 @@ __global__ void __launch_bounds__(256) preserve_kernel(uint8_t *__restrict__ poo
 // --------------------------------------------------------------------------
 // Census: hist[d] = ATs at distance d (d < 2k), hist[2k] = inactive ATs.
 // Each lane keeps a private column of the block's shared histogram
-// (bin * 32 + lane: no bank conflicts, no atomics); runs of 16 inactive ATs
-// are counted in a register.  Block rows go to `partial`; the last block to
-// finish adds the rows up into `hist` and re-arms `ticket` for the next call.
+// (bin * 32 + lane: no bank conflicts, no atomics).  A chunk of 16 inactive
+// ATs is counted in a register; otherwise the four words are turned into bin
+// bytes with SWAR (one ACT per chunk when the chunk lies in one block).
+// Block rows go to `partial`; the last block to finish adds the rows up into
+// `hist` and re-arms `ticket` for the next call.
 // --------------------------------------------------------------------------
+__device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint32_t pid0, uint4 w, uint32_t pat,
+                                             uint32_t *col, uint32_t &inactive_runs) {
+    if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
+        inactive_runs++;
+        return;
+    }
+    uint32_t b0 = block_of(G, pid0);
+    if (b0 == block_of(G, pid0 + 15u)) {
+        uint32_t act = act_of_block(bact0, b0, G.twok);
+        uint32_t words[4] = {swar_bins(w.x, act, G.twok), swar_bins(w.y, act, G.twok), swar_bins(w.z, act, G.twok),
+                             swar_bins(w.w, act, G.twok)};
+#pragma unroll
+        for (int b = 0; b < 16; b++) {
+            uint32_t bin = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, G.twok);
+            col[bin * 32u] += 1u;
+        }
+    } else {
+        uint32_t words[4] = {w.x, w.y, w.z, w.w};
+        for (int b = 0; b < 16; b++) {
+            uint32_t v = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+            uint32_t bin = G.twok;
+            if (v < G.twok) {
+                uint32_t act = act_of_block(bact0, block_of(G, pid0 + b), G.twok);
+                uint32_t d = act + G.twok - v;
+                bin = d >= G.twok ? d - G.twok : d;
+            }
+            col[bin * 32u] += 1u;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ partial,
                                                                 uint64_t *__restrict__ hist,
                                                                 unsigned int *__restrict__ ticket) {
@@ -121,42 +156,25 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
     const uint32_t pat = G.twok * ONES;
     uint32_t inactive_runs = 0;   // chunks of 16 inactive ATs
     const uint64_t n16 = G.P >> 4;
-    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n16;
-         q += (uint64_t)gridDim.x * blockDim.x) {
-        uint4 w = __ldcg(reinterpret_cast<const uint4 *>(G.pool) + q);
-        if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
-            inactive_runs++;
-            continue;
-        }
-        uint32_t pid0 = (uint32_t)(q << 4);
-        uint32_t b0 = block_of(G, pid0), b15 = block_of(G, pid0 + 15u);
-        uint32_t act0 = act_of_block(bact0, b0, G.twok);
-        uint32_t words[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int b = 0; b < 16; b++) {
-            uint32_t v = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-            uint32_t bin;
-            if (v >= G.twok) {   // 2k = inactive (larger values never arise from the ABI)
-                bin = G.twok;
-            } else {
-                uint32_t act = (b0 == b15) ? act0 : act_of_block(bact0, block_of(G, pid0 + b), G.twok);
-                uint32_t d = act + G.twok - v;
-                bin = d >= G.twok ? d - G.twok : d;
-            }
-            col[bin * 32u] += 1u;
-        }
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n16; q += 2 * stride) {
+        uint64_t q2 = q + stride;
+        uint4 w0 = __ldcg(pool16 + q);
+        uint4 w1 = make_uint4(pat, pat, pat, pat);
+        if (q2 < n16) w1 = __ldcg(pool16 + q2);
+        census_chunk(G, bact0, (uint32_t)(q << 4), w0, pat, col, inactive_runs);
+        if (q2 < n16) census_chunk(G, bact0, (uint32_t)(q2 << 4), w1, pat, col, inactive_runs);
     }
     col[G.twok * 32u] += 16u * inactive_runs;
     __syncthreads();
 
-    // block row: sum every lane column of every warp
-    for (uint32_t bin = threadIdx.x; bin < nbins; bin += blockDim.x) {
-        uint64_t s = 0;
-        for (uint32_t wv = 0; wv < nwarps; wv++) {
-            const uint32_t *c = sh + ((size_t)wv * nbins + bin) * 32u;
-            for (uint32_t l = 0; l < 32u; l++) s += c[l];
-        }
-        partial[(uint64_t)blockIdx.x * nbins + bin] = s;
+    // block row: warp w sums bins w, w + nwarps, ... over every warp's lane columns
+    for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
+        uint32_t s = 0;
+        for (uint32_t wv = 0; wv < nwarps; wv++) s += sh[((size_t)wv * nbins + bin) * 32u + lane];
+        s = __reduce_add_sync(0xFFFFFFFFu, s);
+        if (lane == 0) partial[(uint64_t)blockIdx.x * nbins + bin] = s;
     }
     __threadfence();
     __shared__ bool last;
@@ -168,10 +186,12 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (uint32_t bin = threadIdx.x; bin < nbins; bin += blockDim.x) {
+    for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
         uint64_t s = 0;
-        for (uint32_t blk = 0; blk < gridDim.x; blk++) s += __ldcg(partial + (uint64_t)blk * nbins + bin);
-        hist[bin] = s;
+        for (uint32_t blk = lane; blk < gridDim.x; blk += 32u) s += __ldcg(partial + (uint64_t)blk * nbins + bin);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+        if (lane == 0) hist[bin] = s;
     }
     if (threadIdx.x == 0) *ticket = 0u;
 }
@@ -223,65 +243,111 @@ __device__ __forceinline__ uint32_t count_chunk_bytes(const Geom &G, uint32_t ba
     return n;
 }
 
-// Warp per host; L >= 16.  In each round the 32 lanes hash 32 consecutive
+// Warp per host; L = 16 << CPSL (16, 32 or 64).  Work goes in batches of RB
+// rounds of 32 segments.  In each round the 32 lanes hash 32 consecutive
 // segments; the segments' 16-byte chunks are then read by consecutive lanes
 // (for L = 32, lanes 2j and 2j+1 read the two halves of one 32-byte sector),
-// the segment base and ACT coming from the hashing lane by shuffle.
-template <int MODE>
-__global__ void __launch_bounds__(GATHER_THREADS) gather_vec_kernel(Geom G, uint32_t bact0, uint32_t kprime,
+// the segment base and ACT coming from the hashing lane by shuffle.  All
+// RB * CPS loads of a batch are issued before any is tested, so that several
+// sectors are in flight per lane.  FULL: every batch is complete (the number
+// of segments is a multiple of 32 * RB), so no lane needs a bounds test.
+// Active ATs are counted per byte lane in a SWAR accumulator (at most
+// RB * CPS * 4 <= 32 per byte lane per batch) and folded after each batch.
+// 5 blocks of 256 threads per SM (at most 51 registers a thread): measured
+// best for L = 32, g = 4096 on B300 among 2-8 blocks per SM and 1-4 rounds
+// per batch (fewer registers spill, more leave too few warps to hide the L2
+// latency of the sector loads).
+#ifndef VATE_GATHER_MINB
+#define VATE_GATHER_MINB 5
+#endif
+template <int MODE, int CPSL, int RB, bool FULL>
+__global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_kernel(Geom G, uint32_t bact0, uint32_t kprime,
                                                                     const uint64_t *__restrict__ hist,
                                                                     const uint32_t *__restrict__ aips, uint64_t n,
                                                                     float *__restrict__ out,
                                                                     uint8_t *__restrict__ flags,
-                                                                    uint32_t *__restrict__ active) {
-    __shared__ CheckConsts tbl[128];
+                                                                    uint32_t *__restrict__ active, uint32_t u1,
+                                                                    uint32_t u2, uint32_t u3) {
+    constexpr int CPS = 1 << CPSL;                      // 16-byte chunks per segment
+    constexpr int NL = RB * CPS;                        // loads per lane per batch
+    __shared__ RangeConsts tbl[128];
     __shared__ uint64_t sN0;
-    for (uint32_t a = threadIdx.x; a < G.twok; a += blockDim.x) tbl[a] = check_consts(a, kprime, G.twok);
+    for (uint32_t a = threadIdx.x; a < G.twok; a += blockDim.x) tbl[a] = range_consts(a, kprime, G.twok);
     if (MODE == GATHER_ESTIMATE && threadIdx.x == 0) sN0 = pool_inactive(hist, G.P, kprime);
     __syncthreads();
     const uint64_t N0 = (MODE == GATHER_ESTIMATE) ? sN0 : 0;
+    const uint32_t c2k = (128u - G.twok) * ONES;
 
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nseg = G.g >> G.log2L;              // segments per host
-    const uint32_t cps_log2 = G.log2L - 4u;             // log2(16-byte chunks per segment)
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
+    const uint32_t a32 = (uint32_t)min(G.a, (uint64_t)0xFFFFFFFFu);
 
+    uint32_t next_aip = warp0 < n ? aips[warp0] : 0u;    // host addresses are fetched one host ahead
     for (uint64_t h = warp0; h < n; h += nwarps) {
-        const uint32_t aip = aips[h];
+        const uint32_t aip = next_aip;
+        if (h + nwarps < n) next_aip = aips[h + nwarps];
         uint32_t cnt = 0;
-        for (uint32_t r0 = 0; r0 < nseg; r0 += 32u) {
-            // hash one segment per lane
-            uint32_t s = r0 + lane;
-            uint32_t base = 0, act = 0;
-            bool straddle = false;
-            if (s < nseg) {
-                base = seg_base(G, aip, s);
-                uint32_t b0 = block_of(G, base), b1 = block_of(G, base + G.L - 1u);
-                act = act_of_block(bact0, b0, G.twok);
-                straddle = (b0 != b1);
-            }
-            uint32_t segs_here = min(32u, nseg - r0);
-            uint32_t chunks = segs_here << cps_log2;
-            unsigned straddle_mask = __ballot_sync(0xFFFFFFFFu, straddle);
-            for (uint32_t c0 = 0; c0 < chunks; c0 += 32u) {
-                uint32_t c = c0 + lane;
-                uint32_t src = c >> cps_log2;            // lane that hashed this chunk's segment
-                uint32_t sbase = __shfl_sync(0xFFFFFFFFu, base, src & 31u);
-                uint32_t sact = __shfl_sync(0xFFFFFFFFu, act, src & 31u);
-                if (c < chunks) {
-                    uint32_t pid = sbase + ((c & ((1u << cps_log2) - 1u)) << 4);
-                    uint4 w = __ldg(pool16 + (pid >> 4));
-                    if (straddle_mask & (1u << src)) {
-                        cnt += count_chunk_bytes(G, bact0, kprime, pid, w);
-                    } else {
-                        CheckConsts cc = tbl[sact];
-                        cnt += __popc(swar_active(w.x, cc)) + __popc(swar_active(w.y, cc)) +
-                               __popc(swar_active(w.z, cc)) + __popc(swar_active(w.w, cc));
-                    }
+        for (uint32_t r0 = 0; r0 < nseg; r0 += 32u * RB) {
+            // hash: one segment per lane and round; ACT and "straddles a block
+            // boundary" packed as act | flag << 8
+            uint32_t base[RB], actf[RB];
+#pragma unroll
+            for (int rb = 0; rb < RB; rb++) {
+                uint32_t s = r0 + 32u * rb + lane;
+                base[rb] = 0;
+                actf[rb] = 0;
+                if (FULL || s < nseg) {
+                    base[rb] = seg_base(G, aip, s);
+                    uint32_t b0 = block_of(G, base[rb]);
+                    bool straddle;
+                    if (G.partition == 0)       // offset inside a block of size a (the last block may be smaller:
+                        straddle = base[rb] - b0 * a32 > a32 - G.L;   // then this errs towards the exact slow path)
+                    else
+                        straddle = b0 != block_of(G, base[rb] + G.L - 1u);
+                    actf[rb] = act_of_block(bact0, b0, G.twok) | (straddle ? 0x100u : 0u);
                 }
             }
+            // loads
+            uint4 w[NL];
+            uint32_t pid[NL], sact[NL];
+            bool valid[NL];
+#pragma unroll
+            for (int rb = 0; rb < RB; rb++) {
+                const uint32_t segs_here = FULL ? 32u : ((r0 + 32u * rb < nseg) ? min(32u, nseg - r0 - 32u * rb) : 0u);
+#pragma unroll
+                for (int it = 0; it < CPS; it++) {
+                    const int j = rb * CPS + it;
+                    uint32_t c = it * 32u + lane;
+                    uint32_t src = (c >> CPSL) & 31u;
+                    uint32_t sbase = __shfl_sync(0xFFFFFFFFu, base[rb], src);
+                    sact[j] = __shfl_sync(0xFFFFFFFFu, actf[rb], src);
+                    pid[j] = sbase + ((c & (CPS - 1u)) << 4);
+                    valid[j] = FULL || c < (segs_here << CPSL);
+                    w[j] = make_uint4(0u, 0u, 0u, 0u);
+                    if (valid[j]) w[j] = __ldg(pool16 + (pid[j] >> 4));
+                }
+            }
+            // CheckAT on every loaded chunk
+            uint32_t acc = 0;
+#pragma unroll
+            for (int j = 0; j < NL; j++) {
+                if (!valid[j]) continue;
+                if (sact[j] & 0x100u) {
+                    cnt += count_chunk_bytes(G, bact0, kprime, pid[j], w[j]);
+                } else {
+                    const RangeConsts rc = tbl[sact[j]];
+                    // (m >> 7) added as a multiply-high by 2^25 (multiply-add pipe)
+                    acc = __umulhi(swar_active_fma(w[j].x, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                    acc = __umulhi(swar_active_fma(w[j].y, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                    acc = __umulhi(swar_active_fma(w[j].z, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                    acc = __umulhi(swar_active_fma(w[j].w, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                }
+            }
+            uint32_t t = (acc & 0x00FF00FFu) + ((acc >> 8) & 0x00FF00FFu);
+            cnt += (t & 0xFFFFu) + (t >> 16);
         }
         uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
         if (lane == 0) write_result<MODE>(G, N0, h, A, out, flags, active);
@@ -357,6 +423,34 @@ __global__ void __launch_bounds__(AGE_THREADS) age_counts_kernel(Geom G, uint32_
 // --------------------------------------------------------------------------
 // Launchers (host side).  Each returns cudaGetLastError() of its launch.
 // --------------------------------------------------------------------------
+// Launch a kernel that reads or writes the AT pool.  When the handle asked for
+// it, the launch carries an L2 access-policy window over the pool: hits are
+// kept as persisting lines, so the pool (state kept from slice to slice)
+// stays in L2 while the pairs and host lists stream through it.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pool(const Geom &G, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                               cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (G.l2_window_bytes) {
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[0].val.accessPolicyWindow.base_ptr = G.pool;
+        attr[0].val.accessPolicyWindow.num_bytes = G.l2_window_bytes;
+        attr[0].val.accessPolicyWindow.hitRatio = G.l2_hit_ratio;
+        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    count_launch();
+    return e;
+}
+
 static int grid_for(uint64_t work_items, int threads, int max_blocks) {
     uint64_t b = (work_items + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -365,34 +459,26 @@ static int grid_for(uint64_t work_items, int threads, int max_blocks) {
 }
 
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms) {
-    init_pool_kernel<<<grid_for(G.P >> 4, 256, sms * 8), 256, 0, st>>>(G.pool, G.P, G.twok);
-    count_launch();
-    return cudaGetLastError();
+    return launch_pool(G, init_pool_kernel, grid_for(G.P >> 4, 256, sms * 8), 256, 0, st, G.pool, G.P, G.twok);
 }
 
 cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, uint64_t n, cudaStream_t st, int sms) {
     if (n == 0) return cudaSuccess;
     if ((reinterpret_cast<uintptr_t>(pairs) & 15u) != 0) {
         // 8-byte aligned only: the first pair alone, then the 16-byte aligned rest
-        ingest_kernel<<<1, 32, 0, st>>>(G, bact0, pairs, 1);
-        count_launch();
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pool(G, ingest_kernel, 1, 32, 0, st, G, bact0, pairs, (uint64_t)1);
         if (e != cudaSuccess) return e;
         pairs += 2;
         n -= 1;
         if (n == 0) return cudaSuccess;
     }
-    ingest_kernel<<<grid_for((n + 1) / 2, 256, sms * 16), 256, 0, st>>>(G, bact0, pairs, n);
-    count_launch();
-    return cudaGetLastError();
+    return launch_pool(G, ingest_kernel, grid_for((n + 1) / 2, 256, sms * 16), 256, 0, st, G, bact0, pairs, n);
 }
 
-cudaError_t launch_preserve(uint8_t *pool, uint32_t k, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
-                            cudaStream_t st, int sms) {
+cudaError_t launch_preserve(const Geom &G, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1, cudaStream_t st,
+                            int sms) {
     uint64_t chunks = ((e0 - s0) >> 4) + ((e1 - s1) >> 4) + 4;
-    preserve_kernel<<<grid_for(chunks, 256, sms * 8), 256, 0, st>>>(pool, k, s0, e0, s1, e1);
-    count_launch();
-    return cudaGetLastError();
+    return launch_pool(G, preserve_kernel, grid_for(chunks, 256, sms * 8), 256, 0, st, G.pool, G.k, s0, e0, s1, e1);
 }
 
 size_t census_smem_bytes(uint32_t twok) { return (size_t)(CENSUS_THREADS / 32) * (twok + 1) * 32 * sizeof(uint32_t); }
@@ -404,9 +490,8 @@ cudaError_t census_prepare(uint32_t twok) {
 
 cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,
                           unsigned int *ticket, cudaStream_t st) {
-    census_kernel<<<grid, CENSUS_THREADS, census_smem_bytes(G.twok), st>>>(G, bact0, partial, hist, ticket);
-    count_launch();
-    return cudaGetLastError();
+    return launch_pool(G, census_kernel, grid, CENSUS_THREADS, census_smem_bytes(G.twok), st, G, bact0, partial, hist,
+                       ticket);
 }
 
 cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kprime, const uint64_t *hist,
@@ -415,19 +500,49 @@ cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kpri
     if (n == 0) return cudaSuccess;
     int warps_per_block = GATHER_THREADS / 32;
     int grid = grid_for(n, warps_per_block, sms * 64);
+    cudaError_t e = cudaSuccess;
     if (G.L >= 16) {
-        if (mode == GATHER_ESTIMATE)
-            gather_vec_kernel<GATHER_ESTIMATE><<<grid, GATHER_THREADS, 0, st>>>(G, bact0, kprime, hist, aips, n, out, flags, active);
-        else
-            gather_vec_kernel<GATHER_ACTIVE><<<grid, GATHER_THREADS, 0, st>>>(G, bact0, kprime, hist, aips, n, out, flags, active);
+        const uint32_t nseg = G.g >> G.log2L;
+        const uint32_t rounds = (nseg + 31u) / 32u;
+#define VATE_GATHER_LAUNCH(CPSL, RB, FULL)                                                                        \
+    do {                                                                                                          \
+        if (mode == GATHER_ESTIMATE)                                                                              \
+            e = launch_pool(G, gather_vec_kernel<GATHER_ESTIMATE, CPSL, RB, FULL>, grid, GATHER_THREADS, 0, st, G,  \
+                            bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);                        \
+        else                                                                                                      \
+            e = launch_pool(G, gather_vec_kernel<GATHER_ACTIVE, CPSL, RB, FULL>, grid, GATHER_THREADS, 0, st, G,    \
+                            bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);                        \
+    } while (0)
+#define VATE_GATHER_VEC(CPSL, RB)                                                                                 \
+    do {                                                                                                          \
+        if (nseg % (32u * RB) == 0) VATE_GATHER_LAUNCH(CPSL, RB, true);                                           \
+        else VATE_GATHER_LAUNCH(CPSL, RB, false);                                                                 \
+    } while (0)
+        // batches of up to 8 loads per lane: RB rounds x 2^CPSL chunks
+#ifndef VATE_GATHER_RB
+#define VATE_GATHER_RB 2
+#endif
+        if (G.L == 16) {
+            if (rounds >= 2) VATE_GATHER_VEC(0, VATE_GATHER_RB);
+            else VATE_GATHER_VEC(0, 1);
+        } else if (G.L == 32) {
+            if (rounds >= 2) VATE_GATHER_VEC(1, VATE_GATHER_RB);
+            else VATE_GATHER_VEC(1, 1);
+        } else {
+            if (rounds >= 2) VATE_GATHER_VEC(2, VATE_GATHER_RB);
+            else VATE_GATHER_VEC(2, 1);
+        }
+#undef VATE_GATHER_LAUNCH
+#undef VATE_GATHER_VEC
     } else {
         if (mode == GATHER_ESTIMATE)
-            gather_scalar_kernel<GATHER_ESTIMATE><<<grid, GATHER_THREADS, 0, st>>>(G, bact0, kprime, hist, aips, n, out, flags, active);
+            e = launch_pool(G, gather_scalar_kernel<GATHER_ESTIMATE>, grid, GATHER_THREADS, 0, st, G, bact0, kprime, hist,
+                            aips, n, out, flags, active);
         else
-            gather_scalar_kernel<GATHER_ACTIVE><<<grid, GATHER_THREADS, 0, st>>>(G, bact0, kprime, hist, aips, n, out, flags, active);
+            e = launch_pool(G, gather_scalar_kernel<GATHER_ACTIVE>, grid, GATHER_THREADS, 0, st, G, bact0, kprime, hist,
+                            aips, n, out, flags, active);
     }
-    count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t age_prepare(uint32_t k) {
@@ -440,9 +555,7 @@ cudaError_t launch_age_counts(const Geom &G, uint32_t bact0, const uint32_t *aip
     if (n == 0) return cudaSuccess;
     size_t smem = (size_t)(AGE_THREADS / 32) * G.k * 32 * sizeof(uint32_t);
     int grid = grid_for(n, AGE_THREADS / 32, sms * 32);
-    age_counts_kernel<<<grid, AGE_THREADS, smem, st>>>(G, bact0, aips, n, counts);
-    count_launch();
-    return cudaGetLastError();
+    return launch_pool(G, age_counts_kernel, grid, AGE_THREADS, smem, st, G, bact0, aips, n, counts);
 }
 
 }  // namespace vate

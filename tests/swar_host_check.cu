@@ -1,0 +1,67 @@
+// Host-only check of the SWAR AT arithmetic in vate_device.cuh against the
+// scalar forms of Algorithm 1 (CheckAT), Eq. 5 (distance) and Algorithm 3
+// (fast PreserveAT): every k <= 63, every ACT, every k' <= k, every AT value
+// 0..2k in every byte position, plus random mixed words.  Prints "OK".
+#include <cstdio>
+#include <cstdlib>
+#include "vate_device.cuh"
+
+using namespace vate;
+
+static uint32_t rng_state = 12345u;
+static uint32_t rnd() { rng_state = rng_state * 1664525u + 1013904223u; return rng_state >> 8; }
+
+int main() {
+    long checked = 0;
+    for (uint32_t k = 1; k <= 63; k++) {
+        uint32_t twok = 2 * k;
+        uint32_t c2k = (128u - twok) * ONES;
+        for (uint32_t act = 0; act < twok; act++) {
+            for (uint32_t kp = 1; kp <= k; kp++) {
+                RangeConsts rc = range_consts(act, kp, twok);
+                for (int trial = 0; trial < 64 + (int)(twok + 1) * 4; trial++) {
+                    uint32_t v[4];
+                    for (int b = 0; b < 4; b++) v[b] = rnd() % (twok + 1);
+                    if (trial < (int)(twok + 1) * 4) {          // every value in every position
+                        for (int b = 0; b < 4; b++) v[b] = twok;
+                        v[trial & 3] = (uint32_t)(trial >> 2);
+                    }
+                    uint32_t w = v[0] | v[1] << 8 | v[2] << 16 | v[3] << 24;
+                    uint32_t m = swar_active(w, rc, c2k);
+                    uint32_t bins = swar_bins(w, act, twok);
+                    for (int b = 0; b < 4; b++) {
+                        bool want = check_at(v[b], act, kp, twok);
+                        bool got = (m >> (8 * b + 7)) & 1u;
+                        if (want != got || (m >> (8 * b)) & 0x7Fu) {
+                            printf("FAIL active k=%u act=%u k'=%u v=%u\n", k, act, kp, v[b]);
+                            return 1;
+                        }
+                        uint32_t wantbin = v[b] == twok ? twok : (act + twok - v[b]) % twok;
+                        if (((bins >> (8 * b)) & 0xFFu) != wantbin) {
+                            printf("FAIL bins k=%u act=%u v=%u got %u want %u\n", k, act, v[b], (bins >> (8 * b)) & 0xFFu,
+                                   wantbin);
+                            return 1;
+                        }
+                    }
+                    checked++;
+                }
+            }
+        }
+        for (int z = 0; z < 2; z++) {
+            uint32_t act = z ? k : 0;
+            for (int trial = 0; trial < 2000; trial++) {
+                uint32_t v[4];
+                for (int b = 0; b < 4; b++) v[b] = rnd() % (twok + 1);
+                uint32_t w = v[0] | v[1] << 8 | v[2] << 16 | v[3] << 24;
+                uint32_t r = swar_preserve(w, act == 0, k);
+                for (int b = 0; b < 4; b++)
+                    if (((r >> (8 * b)) & 0xFFu) != preserve_at(v[b], act, k)) {
+                        printf("FAIL preserve k=%u act=%u v=%u\n", k, act, v[b]);
+                        return 1;
+                    }
+            }
+        }
+    }
+    printf("OK %ld words\n", checked);
+    return 0;
+}
