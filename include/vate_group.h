@@ -1,0 +1,117 @@
+/*
+ * vate_group.h -- many independent VATE monitors advanced together.
+ *
+ * A group holds M independent monitors (for instance one per router or link),
+ * each with its own pool size 2^c, window k, virtual-vector length g and hash
+ * seed, and runs the per-slice pipeline of Algorithm 4 -- slide (BACT^0 + 1,
+ * PreserveAT on the two blocks whose ACT became 0 or k), SetAT for every pair,
+ * pool census, CheckAT gather and Eq. 11 for every host -- for all of them in
+ * five launches per slice, each a persistent grid working through a table of
+ * (monitor, tile) work items.  Every monitor computes exactly what a single
+ * vate_handle with the same parameters computes (the same device arithmetic);
+ * a monitor's result does not depend on the other monitors in the group.
+ *
+ * All monitors advance in lock step, one slice per vate_group_step call: the
+ * first step is slice 0 (BACT^0 = 0 for every monitor), step s is slice s.
+ * Everything a step reads that changes from slice to slice -- the slice
+ * number, the per-monitor batch boundaries, k' -- lives in device memory, so a
+ * step can be captured once as a CUDA graph and replayed every slice
+ * (vate_group_step_graph) while batch sizes vary.
+ *
+ * Conventions are those of vate.h (device pointers d_*, asynchronous on
+ * `stream`, VATE_* return codes, vate_last_error()).  Values that live in
+ * device memory cannot be checked on the host: a step clamps them to the
+ * capacities it was given and records what it found in a status word
+ * (vate_group_status); it never reads or writes outside the caller's buffers.
+ */
+#ifndef VATE_GROUP_H
+#define VATE_GROUP_H
+
+#include <stdint.h>
+#include "vate.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vate_group vate_group;
+
+/* Status bits recorded by a step (sticky until read with clear = 1). */
+#define VATE_GROUP_BAD_OFFSETS  1u   /* pair or host offsets decreasing or beyond capacity (clamped) */
+#define VATE_GROUP_BAD_KPRIME   2u   /* k' outside [1, k] for some monitor (k used instead)          */
+
+/* Tiling of the group kernels, chosen by vate_group_autotune or set by hand.
+ *   census_tile_chunks  16-byte chunks per census work item (power of two, 256..65536)
+ *   gather_blocks_per_sm, ingest_blocks_per_sm, preserve_blocks_per_sm
+ *                       persistent grid sizes, in blocks of 256 threads per SM (1..32)
+ *   gather_hosts_per_grab  hosts a warp takes from the work queue at a time (1..64) */
+typedef struct {
+    uint32_t census_tile_chunks;
+    uint32_t gather_blocks_per_sm;
+    uint32_t gather_hosts_per_grab;
+    uint32_t ingest_blocks_per_sm;
+    uint32_t preserve_blocks_per_sm;
+    uint32_t reserved;
+} vate_group_tuning;
+
+/* Create a group of n_monitors (1..256) monitors; params[m] as for
+ * vate_create, all with the same seg_len.  The pools live in one device
+ * allocation (each 256-byte aligned) and are initialised (InitAT) on `stream`.
+ * Errors: VATE_EINVAL (any parameter, mixed seg_len), VATE_ENOMEM, VATE_ECUDA. */
+int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stream, vate_group **out);
+
+/* Free everything of the group (synchronises its device work first).  NULL is accepted. */
+int vate_group_destroy(vate_group *g);
+
+/* One slice for every monitor.
+ *   d_pairs         device vate_pair[pair_capacity]: the pairs of monitor m are
+ *                   d_pairs[d_pair_offsets[m] .. d_pair_offsets[m+1]).
+ *   d_pair_offsets  device uint64[M+1], non-decreasing, last <= pair_capacity.
+ *   d_hosts         device uint32[host_capacity]: hosts of monitor m at
+ *                   d_hosts[d_host_offsets[m] .. d_host_offsets[m+1]).
+ *   d_host_offsets  device uint64[M+1], non-decreasing, last <= host_capacity.
+ *   d_kprime        device uint32[M]: window k' of each monitor's estimates.
+ *   d_out, d_flags  device float[host_capacity], uint8[host_capacity] (flags may
+ *                   be NULL): estimate and VATE_FLAG_* of each host, same index.
+ * Capacities are host values (buffer sizes); the offsets are read on the device. */
+int vate_group_step(vate_group *g, const vate_pair *d_pairs, const uint64_t *d_pair_offsets, uint64_t pair_capacity,
+                    const uint32_t *d_hosts, const uint64_t *d_host_offsets, uint64_t host_capacity,
+                    const uint32_t *d_kprime, float *d_out, uint8_t *d_flags, void *stream);
+
+/* The same step as a CUDA graph: the first call (and any call whose buffers or
+ * tuning differ from the previous one) captures the five launches on an
+ * internal stream and instantiates the graph; every call launches the graph on
+ * `stream`.  Refill the same buffers (pairs, offsets, hosts, k') between
+ * slices to keep replaying one graph. */
+int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_t *d_pair_offsets,
+                          uint64_t pair_capacity, const uint32_t *d_hosts, const uint64_t *d_host_offsets,
+                          uint64_t host_capacity, const uint32_t *d_kprime, float *d_out, uint8_t *d_flags,
+                          void *stream);
+
+/* Project-written autotuner: after at least one step, re-runs the ingest (a
+ * repeat of the same slice's SetATs writes the same values), the census and
+ * the gather of that slice on the given inputs under candidate tilings, times
+ * each with CUDA events on `stream` (synchronising it), keeps the fastest per
+ * kernel, and writes the choice to *chosen (may be NULL).  The monitors' state
+ * and the outputs end exactly as the last step left them. */
+int vate_group_autotune(vate_group *g, const vate_pair *d_pairs, const uint64_t *d_pair_offsets,
+                        uint64_t pair_capacity, const uint32_t *d_hosts, const uint64_t *d_host_offsets,
+                        uint64_t host_capacity, const uint32_t *d_kprime, float *d_out, uint8_t *d_flags,
+                        vate_group_tuning *chosen, void *stream);
+
+int vate_group_set_tuning(vate_group *g, const vate_group_tuning *t);
+int vate_group_get_tuning(const vate_group *g, vate_group_tuning *t);
+
+/* Status bits of the steps since the last clear (synchronises `stream`). */
+int vate_group_status(vate_group *g, uint32_t *status, int clear, void *stream);
+
+/* Per-monitor views for checking: the pool (P_m bytes), the census of the last
+ * step (uint64[2k_m+1]), and geometry + slice (slice from the device; synchronises `stream`). */
+int vate_group_copy_pool(vate_group *g, uint32_t m, uint8_t *d_dst, void *stream);
+int vate_group_census(vate_group *g, uint32_t m, uint64_t *d_hist, void *stream);
+int vate_group_monitor_info(vate_group *g, uint32_t m, vate_info *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VATE_GROUP_H */

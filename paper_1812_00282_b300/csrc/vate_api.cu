@@ -79,23 +79,6 @@ int make_geom(const vate_params *p, Geom *G) {
     return VATE_OK;
 }
 
-// [start, end) of block i
-void block_range(const Geom &G, uint32_t i, uint64_t *s, uint64_t *e) {
-    if (G.partition == 0) {
-        *s = (uint64_t)i * G.a;
-        *e = (i + 1 < G.twok) ? *s + G.a : G.P;
-        return;
-    }
-    uint64_t nsmall = G.twok - G.b;
-    if (i < nsmall) {
-        *s = (uint64_t)i * G.a;
-        *e = *s + G.a;
-    } else {
-        *s = nsmall * G.a + (uint64_t)(i - nsmall) * (G.a + 1);
-        *e = *s + G.a + 1;
-    }
-}
-
 }  // namespace
 
 void vate::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -153,8 +136,8 @@ int advance_to(vate_handle *h, int64_t slice, cudaStream_t st) {
         uint32_t i0 = (G.twok - h->bact0) % G.twok;          // BACT = 0
         uint32_t i1 = (G.k + G.twok - h->bact0) % G.twok;    // BACT = k
         uint64_t s0, e0, s1, e1;
-        block_range(G, i0, &s0, &e0);
-        block_range(G, i1, &s1, &e1);
+        vate::block_range_of(G, i0, &s0, &e0);
+        vate::block_range_of(G, i1, &s1, &e1);
         cudaError_t e = vate::launch_preserve(G, s0, e0, s1, e1, st, h->sms);
         if (e != cudaSuccess) return cuda_fail(e, "preserve launch");
     }

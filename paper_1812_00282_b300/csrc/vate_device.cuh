@@ -81,6 +81,23 @@ VATE_HD uint32_t block_of(const Geom &G, uint32_t pid) {
     return (uint32_t)mulhi64(G.ma1, (uint64_t)pid + G.twok - G.b);
 }
 
+// [start, end) of block i (Eq. 9-10, or the low-deviation partition)
+VATE_HD void block_range_of(const Geom &G, uint32_t i, uint64_t *s, uint64_t *e) {
+    if (G.partition == 0) {
+        *s = (uint64_t)i * G.a;
+        *e = (i + 1 < G.twok) ? *s + G.a : G.P;
+        return;
+    }
+    uint64_t nsmall = G.twok - G.b;
+    if (i < nsmall) {
+        *s = (uint64_t)i * G.a;
+        *e = *s + G.a;
+    } else {
+        *s = nsmall * G.a + (uint64_t)(i - nsmall) * (G.a + 1);
+        *e = *s + G.a + 1;
+    }
+}
+
 // ACT of block blk when BACT^0 = bact0 (Eq. 8)
 VATE_HD uint32_t act_of_block(uint32_t bact0, uint32_t blk, uint32_t twok) {
     uint32_t s = bact0 + blk;

@@ -14,6 +14,8 @@
 // traffic and integer ALU, so no tensor cores are used.
 #include "vate_device.cuh"
 #include "vate_internal.h"
+#include "vate_device_ops.cuh"
+#include "vate_launch.cuh"
 
 #include <utility>
 
@@ -74,31 +76,7 @@ __global__ void __launch_bounds__(256) preserve_kernel(uint8_t *__restrict__ poo
          t += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t chunk = t < n0 ? c0s + t : c1s + (t - n0);
         if (t >= n0 && n0 && chunk >= c0s && chunk < c0e) continue;   // enumerated by range 0
-        uint64_t base = chunk << 4;
-        uint4 *p = reinterpret_cast<uint4 *>(pool + base);
-        uint4 w = *p;
-        uint4 r = w;
-        bool full0 = base >= s0 && base + 16 <= e0;
-        bool full1 = base >= s1 && base + 16 <= e1;
-        if (full0 || full1) {
-            r.x = swar_preserve(w.x, full0, k);
-            r.y = swar_preserve(w.y, full0, k);
-            r.z = swar_preserve(w.z, full0, k);
-            r.w = swar_preserve(w.w, full0, k);
-        } else {
-            uint32_t words[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int b = 0; b < 16; b++) {
-                uint64_t pos = base + b;
-                uint32_t v = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-                uint32_t nv = v;
-                if (pos >= s0 && pos < e0) nv = preserve_at(v, 0u, k);
-                else if (pos >= s1 && pos < e1) nv = preserve_at(v, k, k);
-                words[b >> 2] = (words[b >> 2] & ~(0xFFu << (8 * (b & 3)))) | (nv << (8 * (b & 3)));
-            }
-            r.x = words[0]; r.y = words[1]; r.z = words[2]; r.w = words[3];
-        }
-        if (r.x != w.x || r.y != w.y || r.z != w.z || r.w != w.w) *p = r;
+        preserve_chunk(pool, chunk << 4, k, s0, e0, s1, e1);
     }
 }
 
@@ -111,37 +89,6 @@ __global__ void __launch_bounds__(256) preserve_kernel(uint8_t *__restrict__ poo
 // Block rows go to `partial`; the last block to finish adds the rows up into
 // `hist` and re-arms `ticket` for the next call.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint32_t pid0, uint4 w, uint32_t pat,
-                                             uint32_t *col, uint32_t &inactive_runs) {
-    if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
-        inactive_runs++;
-        return;
-    }
-    uint32_t b0 = block_of(G, pid0);
-    if (b0 == block_of(G, pid0 + 15u)) {
-        uint32_t act = act_of_block(bact0, b0, G.twok);
-        uint32_t words[4] = {swar_bins(w.x, act, G.twok), swar_bins(w.y, act, G.twok), swar_bins(w.z, act, G.twok),
-                             swar_bins(w.w, act, G.twok)};
-#pragma unroll
-        for (int b = 0; b < 16; b++) {
-            uint32_t bin = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, G.twok);
-            col[bin * 32u] += 1u;
-        }
-    } else {
-        uint32_t words[4] = {w.x, w.y, w.z, w.w};
-        for (int b = 0; b < 16; b++) {
-            uint32_t v = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-            uint32_t bin = G.twok;
-            if (v < G.twok) {
-                uint32_t act = act_of_block(bact0, block_of(G, pid0 + b), G.twok);
-                uint32_t d = act + G.twok - v;
-                bin = d >= G.twok ? d - G.twok : d;
-            }
-            col[bin * 32u] += 1u;
-        }
-    }
-}
-
 __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ partial,
                                                                 uint64_t *__restrict__ hist,
                                                                 unsigned int *__restrict__ ticket) {
@@ -199,24 +146,6 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
 // --------------------------------------------------------------------------
 // Gather + estimate.
 // --------------------------------------------------------------------------
-// Eq. 11 in FP32 from exact integers: g * log1p((N0*g - V0*P) / (V0*P)).
-__device__ __forceinline__ float estimate_eq11(uint32_t g, uint64_t P, uint64_t N0, uint32_t A, uint8_t &flags) {
-    flags = 0;
-    uint64_t V0 = (uint64_t)g - A;
-    if (V0 == 0) { V0 = 1; flags |= 1u; }
-    if (N0 == 0) { N0 = 1; flags |= 2u; }
-    long long num = (long long)(N0 * (uint64_t)g) - (long long)(V0 * P);
-    float x = (float)num / (float)(V0 * P);
-    return (float)g * log1pf(x);
-}
-
-// N0 for window k' from the census of the last close
-__device__ __forceinline__ uint64_t pool_inactive(const uint64_t *hist, uint64_t P, uint32_t kprime) {
-    uint64_t active = 0;
-    for (uint32_t d = 0; d < kprime; d++) active += hist[d];
-    return P - active;
-}
-
 template <int MODE>
 __device__ __forceinline__ void write_result(const Geom &G, uint64_t N0, uint64_t idx, uint32_t A, float *out,
                                              uint8_t *flags, uint32_t *active) {
@@ -228,19 +157,6 @@ __device__ __forceinline__ void write_result(const Geom &G, uint64_t N0, uint64_
     } else {
         active[idx] = A;
     }
-}
-
-// Per-byte CheckAT of one 16-byte chunk whose bytes may lie in two blocks.
-__device__ __forceinline__ uint32_t count_chunk_bytes(const Geom &G, uint32_t bact0, uint32_t kprime, uint32_t pid,
-                                                   uint4 w) {
-    uint32_t words[4] = {w.x, w.y, w.z, w.w};
-    uint32_t n = 0;
-    for (int b = 0; b < 16; b++) {
-        uint32_t v = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-        uint32_t act = act_of_block(bact0, block_of(G, pid + b), G.twok);
-        n += check_at(v, act, kprime, G.twok) ? 1u : 0u;
-    }
-    return n;
 }
 
 // Warp per host; L = 16 << CPSL (16, 32 or 64).  Work goes in batches of RB
@@ -268,8 +184,6 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
                                                                     uint8_t *__restrict__ flags,
                                                                     uint32_t *__restrict__ active, uint32_t u1,
                                                                     uint32_t u2, uint32_t u3) {
-    constexpr int CPS = 1 << CPSL;                      // 16-byte chunks per segment
-    constexpr int NL = RB * CPS;                        // loads per lane per batch
     __shared__ RangeConsts tbl[128];
     __shared__ uint64_t sN0;
     for (uint32_t a = threadIdx.x; a < G.twok; a += blockDim.x) tbl[a] = range_consts(a, kprime, G.twok);
@@ -279,76 +193,15 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
     const uint32_t c2k = (128u - G.twok) * ONES;
 
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t nseg = G.g >> G.log2L;              // segments per host
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
     const uint32_t a32 = (uint32_t)min(G.a, (uint64_t)0xFFFFFFFFu);
 
     uint32_t next_aip = warp0 < n ? aips[warp0] : 0u;    // host addresses are fetched one host ahead
     for (uint64_t h = warp0; h < n; h += nwarps) {
         const uint32_t aip = next_aip;
         if (h + nwarps < n) next_aip = aips[h + nwarps];
-        uint32_t cnt = 0;
-        for (uint32_t r0 = 0; r0 < nseg; r0 += 32u * RB) {
-            // hash: one segment per lane and round; ACT and "straddles a block
-            // boundary" packed as act | flag << 8
-            uint32_t base[RB], actf[RB];
-#pragma unroll
-            for (int rb = 0; rb < RB; rb++) {
-                uint32_t s = r0 + 32u * rb + lane;
-                base[rb] = 0;
-                actf[rb] = 0;
-                if (FULL || s < nseg) {
-                    base[rb] = seg_base(G, aip, s);
-                    uint32_t b0 = block_of(G, base[rb]);
-                    bool straddle;
-                    if (G.partition == 0)       // offset inside a block of size a (the last block may be smaller:
-                        straddle = base[rb] - b0 * a32 > a32 - G.L;   // then this errs towards the exact slow path)
-                    else
-                        straddle = b0 != block_of(G, base[rb] + G.L - 1u);
-                    actf[rb] = act_of_block(bact0, b0, G.twok) | (straddle ? 0x100u : 0u);
-                }
-            }
-            // loads
-            uint4 w[NL];
-            uint32_t pid[NL], sact[NL];
-            bool valid[NL];
-#pragma unroll
-            for (int rb = 0; rb < RB; rb++) {
-                const uint32_t segs_here = FULL ? 32u : ((r0 + 32u * rb < nseg) ? min(32u, nseg - r0 - 32u * rb) : 0u);
-#pragma unroll
-                for (int it = 0; it < CPS; it++) {
-                    const int j = rb * CPS + it;
-                    uint32_t c = it * 32u + lane;
-                    uint32_t src = (c >> CPSL) & 31u;
-                    uint32_t sbase = __shfl_sync(0xFFFFFFFFu, base[rb], src);
-                    sact[j] = __shfl_sync(0xFFFFFFFFu, actf[rb], src);
-                    pid[j] = sbase + ((c & (CPS - 1u)) << 4);
-                    valid[j] = FULL || c < (segs_here << CPSL);
-                    w[j] = make_uint4(0u, 0u, 0u, 0u);
-                    if (valid[j]) w[j] = __ldg(pool16 + (pid[j] >> 4));
-                }
-            }
-            // CheckAT on every loaded chunk
-            uint32_t acc = 0;
-#pragma unroll
-            for (int j = 0; j < NL; j++) {
-                if (!valid[j]) continue;
-                if (sact[j] & 0x100u) {
-                    cnt += count_chunk_bytes(G, bact0, kprime, pid[j], w[j]);
-                } else {
-                    const RangeConsts rc = tbl[sact[j]];
-                    // (m >> 7) added as a multiply-high by 2^25 (multiply-add pipe)
-                    acc = __umulhi(swar_active_fma(w[j].x, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                    acc = __umulhi(swar_active_fma(w[j].y, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                    acc = __umulhi(swar_active_fma(w[j].z, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                    acc = __umulhi(swar_active_fma(w[j].w, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                }
-            }
-            uint32_t t = (acc & 0x00FF00FFu) + ((acc >> 8) & 0x00FF00FFu);
-            cnt += (t & 0xFFFFu) + (t >> 16);
-        }
+        uint32_t cnt = gather_host_vec<CPSL, RB, FULL>(G, bact0, kprime, aip, tbl, c2k, a32, u1, u2, u3, lane);
         uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
         if (lane == 0) write_result<MODE>(G, N0, h, A, out, flags, active);
     }
@@ -371,14 +224,7 @@ __global__ void __launch_bounds__(GATHER_THREADS) gather_scalar_kernel(Geom G, u
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t h = warp0; h < n; h += nwarps) {
         const uint32_t aip = aips[h];
-        uint32_t cnt = 0;
-#pragma unroll 4
-        for (uint32_t i = lane; i < G.g; i += 32u) {
-            uint32_t pid = vat_pid(G, aip, i);
-            uint32_t v = __ldg(G.pool + pid);
-            uint32_t act = act_of_block(bact0, block_of(G, pid), G.twok);
-            cnt += check_at(v, act, kprime, G.twok) ? 1u : 0u;
-        }
+        uint32_t cnt = gather_host_scalar(G, bact0, kprime, aip, lane);
         uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
         if (lane == 0) write_result<MODE>(G, N0, h, A, out, flags, active);
     }
@@ -423,34 +269,6 @@ __global__ void __launch_bounds__(AGE_THREADS) age_counts_kernel(Geom G, uint32_
 // --------------------------------------------------------------------------
 // Launchers (host side).  Each returns cudaGetLastError() of its launch.
 // --------------------------------------------------------------------------
-// Launch a kernel that reads or writes the AT pool.  When the handle asked for
-// it, the launch carries an L2 access-policy window over the pool: hits are
-// kept as persisting lines, so the pool (state kept from slice to slice)
-// stays in L2 while the pairs and host lists stream through it.
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_pool(const Geom &G, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                               cudaStream_t st, Args &&...args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    if (G.l2_window_bytes) {
-        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-        attr[0].val.accessPolicyWindow.base_ptr = G.pool;
-        attr[0].val.accessPolicyWindow.num_bytes = G.l2_window_bytes;
-        attr[0].val.accessPolicyWindow.hitRatio = G.l2_hit_ratio;
-        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-    }
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-    count_launch();
-    return e;
-}
-
 static int grid_for(uint64_t work_items, int threads, int max_blocks) {
     uint64_t b = (work_items + threads - 1) / threads;
     if (b < 1) b = 1;

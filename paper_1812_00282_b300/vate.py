@@ -41,6 +41,18 @@ class vate_info(C.Structure):
                 ("slice", C.c_int64), ("bact0", C.c_uint32), ("closed", C.c_uint32)]
 
 
+class vate_group_tuning(C.Structure):
+    _fields_ = [("census_tile_chunks", C.c_uint32), ("gather_blocks_per_sm", C.c_uint32),
+                ("gather_hosts_per_grab", C.c_uint32), ("ingest_blocks_per_sm", C.c_uint32),
+                ("preserve_blocks_per_sm", C.c_uint32), ("reserved", C.c_uint32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+
+
+VATE_GROUP_BAD_OFFSETS, VATE_GROUP_BAD_KPRIME = 1, 2
+
+
 def _load() -> C.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError("libvate.so is not built (run `python -m paper_1812_00282_b300.build`): " + LIB_PATH)
@@ -67,6 +79,17 @@ def _load() -> C.CDLL:
         "vate_last_error": (C.c_char_p, []),
         "vate_launch_count": (u64, []),
         "vate_census_noalloc": (i, [P(vate_params), vp, u32, vp, vp]),
+        "vate_group_create": (i, [vp, u32, vp, P(vp)]),
+        "vate_group_destroy": (i, [vp]),
+        "vate_group_step": (i, [vp, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp]),
+        "vate_group_step_graph": (i, [vp, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp]),
+        "vate_group_autotune": (i, [vp, vp, vp, u64, vp, vp, u64, vp, vp, vp, P(vate_group_tuning), vp]),
+        "vate_group_set_tuning": (i, [vp, P(vate_group_tuning)]),
+        "vate_group_get_tuning": (i, [vp, P(vate_group_tuning)]),
+        "vate_group_status": (i, [vp, P(u32), i, vp]),
+        "vate_group_copy_pool": (i, [vp, u32, vp, vp]),
+        "vate_group_census": (i, [vp, u32, vp, vp]),
+        "vate_group_monitor_info": (i, [vp, u32, P(vate_info), vp]),
         "vate_probe_sector_read": (i, [vp, u64, u64, vp, vp]),
         "vate_probe_byte_write": (i, [vp, u64, u64, vp]),
     }
@@ -284,6 +307,121 @@ def vate_probe_byte_write(buf, n_writes: int, stream=None) -> None:
     """Random 1-byte stores into a CUDA uint8 buffer (include/vate_probe.h)."""
     import torch
     _check(_lib.vate_probe_byte_write(_dev(buf, torch.uint8, "buf"), buf.numel(), n_writes, _stream(stream)))
+
+
+# ---- monitor groups (include/vate_group.h) -----------------------------------
+
+def _group_args(pairs, pair_offsets, hosts, host_offsets, kprime, out, flags):
+    import torch
+    i32 = lambda t: t.dtype if t.dtype in (torch.int32, torch.uint32) else torch.int32
+    i64 = lambda t: t.dtype if t.dtype in (torch.int64, torch.uint64) else torch.int64
+    npairs = pairs.shape[0] if pairs.dim() == 2 else pairs.numel() // 2
+    pp = _dev(pairs, i32(pairs), "pairs") if npairs else None
+    po = _dev(pair_offsets, i64(pair_offsets), "pair_offsets")
+    nh = hosts.numel()
+    ph = _dev(hosts, i32(hosts), "hosts") if nh else None
+    ho = _dev(host_offsets, i64(host_offsets), "host_offsets")
+    kp = _dev(kprime, i32(kprime), "kprime")
+    pout = _dev(out, torch.float32, "out", nh) if nh else None
+    pf = _dev(flags, torch.uint8, "flags", nh) if (flags is not None and nh) else None
+    return pp, po, npairs, ph, ho, nh, kp, pout, pf
+
+
+def vate_group_create(params_list, stream=None) -> C.c_void_p:
+    arr = (vate_params * len(params_list))(*params_list)
+    g = C.c_void_p()
+    _check(_lib.vate_group_create(C.cast(arr, C.c_void_p), len(params_list), _stream(stream), C.byref(g)))
+    return g
+
+
+def vate_group_destroy(g) -> None:
+    _check(_lib.vate_group_destroy(g))
+
+
+def vate_group_step(g, pairs, pair_offsets, hosts, host_offsets, kprime, out, flags=None, stream=None) -> None:
+    a = _group_args(pairs, pair_offsets, hosts, host_offsets, kprime, out, flags)
+    _check(_lib.vate_group_step(g, *a, _stream(stream)))
+
+
+def vate_group_step_graph(g, pairs, pair_offsets, hosts, host_offsets, kprime, out, flags=None, stream=None) -> None:
+    a = _group_args(pairs, pair_offsets, hosts, host_offsets, kprime, out, flags)
+    _check(_lib.vate_group_step_graph(g, *a, _stream(stream)))
+
+
+def vate_group_autotune(g, pairs, pair_offsets, hosts, host_offsets, kprime, out, flags=None,
+                        stream=None) -> vate_group_tuning:
+    a = _group_args(pairs, pair_offsets, hosts, host_offsets, kprime, out, flags)
+    t = vate_group_tuning()
+    _check(_lib.vate_group_autotune(g, *a, C.byref(t), _stream(stream)))
+    return t
+
+
+def vate_group_set_tuning(g, t: vate_group_tuning) -> None:
+    _check(_lib.vate_group_set_tuning(g, C.byref(t)))
+
+
+def vate_group_get_tuning(g) -> vate_group_tuning:
+    t = vate_group_tuning()
+    _check(_lib.vate_group_get_tuning(g, C.byref(t)))
+    return t
+
+
+def vate_group_status(g, clear: bool = False, stream=None) -> int:
+    s = C.c_uint32()
+    _check(_lib.vate_group_status(g, C.byref(s), 1 if clear else 0, _stream(stream)))
+    return int(s.value)
+
+
+def vate_group_copy_pool(g, m: int, dst, stream=None) -> None:
+    import torch
+    _check(_lib.vate_group_copy_pool(g, m, _dev(dst, torch.uint8, "dst"), _stream(stream)))
+
+
+def vate_group_census(g, m: int, hist, stream=None) -> None:
+    import torch
+    _check(_lib.vate_group_census(g, m, _dev(hist, hist.dtype if hist.dtype in (torch.int64, torch.uint64)
+                                                else torch.int64, "hist"), _stream(stream)))
+
+
+def vate_group_monitor_info(g, m: int, stream=None) -> vate_info:
+    info = vate_info()
+    _check(_lib.vate_group_monitor_info(g, m, C.byref(info), _stream(stream)))
+    return info
+
+
+class VateGroup:
+    """Owns one monitor group; methods forward to the vate_group_* functions."""
+
+    def __init__(self, params_list, stream=None):
+        self.params = list(params_list)
+        self.M = len(self.params)
+        self.g = vate_group_create(self.params, stream)
+
+    def close(self) -> None:
+        if self.g:
+            vate_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, *a, graph: bool = False, **kw):
+        (vate_group_step_graph if graph else vate_group_step)(self.g, *a, **kw)
+
+    def autotune(self, *a, **kw) -> vate_group_tuning:
+        return vate_group_autotune(self.g, *a, **kw)
+
+    def status(self, clear: bool = False) -> int:
+        return vate_group_status(self.g, clear)
+
+    def copy_pool(self, m, dst, stream=None):
+        vate_group_copy_pool(self.g, m, dst, stream)
+
+    def census(self, m, hist, stream=None):
+        vate_group_census(self.g, m, hist, stream)
 
 
 class Vate:

@@ -1,0 +1,198 @@
+"""Monitor groups (include/vate_group.h): many independent VATE monitors
+advanced together in one set of persistent launches per slice.
+
+Every monitor of a group must compute exactly what a single vate_handle with
+the same parameters computes on the same pairs and hosts: the pool byte for
+byte, the census, and the estimates and flags bit for bit (same device
+arithmetic).  One monitor is also checked against the CPU oracle.  The CUDA
+graph form must equal the plain form, the autotuner must leave state and
+outputs unchanged, and malformed device-side offsets and k' must be clamped
+and reported, never read out of bounds.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import Oracle
+from traffic import SMALL, Traffic
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1812_00282_b300 as V
+    return V
+
+
+def as_i32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.uint32).view(np.int32)).cuda()
+
+
+MONITORS_L32 = [(14, 1, 64, 32, 0, 1), (16, 5, 1024, 32, 0, 2), (15, 3, 96, 32, 1, 3), (17, 10, 512, 32, 0, 4),
+                (16, 30, 256, 32, 1, 5), (14, 2, 1024, 32, 0, 6), (18, 10, 4096, 32, 0, 7)]
+
+
+def make_slice(trs, s, rng, empty_every=3):
+    """Per-monitor pairs and hosts of slice s (some monitors idle in some slices)."""
+    pairs, hosts = [], []
+    for m, tr in enumerate(trs):
+        n = 0 if (s + m) % empty_every == 0 else int(rng.integers(200, 6000))
+        pairs.append(tr.slice_pairs(s, n=n))
+        nh = 0 if (s * 7 + m) % 5 == 0 else int(rng.integers(1, 700))
+        hosts.append(tr.aips[:nh])
+    return pairs, hosts
+
+
+def pack(pairs, hosts, kprime):
+    po = np.zeros(len(pairs) + 1, np.int64)
+    po[1:] = np.cumsum([len(p) for p in pairs])
+    ho = np.zeros(len(hosts) + 1, np.int64)
+    ho[1:] = np.cumsum([len(h) for h in hosts])
+    P = np.concatenate(pairs) if po[-1] else np.zeros((0, 2), np.uint32)
+    H = np.concatenate(hosts) if ho[-1] else np.zeros(0, np.uint32)
+    return (as_i32(P), torch.from_numpy(po).cuda(), as_i32(H), torch.from_numpy(ho).cuda(),
+            torch.tensor(np.asarray(kprime, np.int32)).cuda())
+
+
+def run_group_vs_single(V, monitors, nslices, graph=False, autotune_at=None):
+    rng = np.random.default_rng(len(monitors) * 31 + nslices)
+    trs = [Traffic(SMALL, pkts_per_slice=5000) for _ in monitors]
+    params = [V.make_params(*m) for m in monitors]
+    grp = V.VateGroup(params)
+    singles = [V.Vate(*m) for m in monitors]
+    kprime = [max(1, (m[1] + 1) // 2) if i % 2 else m[1] for i, m in enumerate(monitors)]
+    cap_p, cap_h = 6000 * len(monitors), 700 * len(monitors)
+    bufs = None
+    for s in range(nslices):
+        pairs, hosts = make_slice(trs, s, rng)
+        P, PO, H, HO, KP = pack(pairs, hosts, kprime)
+        if graph:
+            if bufs is None:
+                bufs = (torch.zeros(cap_p, 2, dtype=torch.int32, device="cuda"), torch.zeros_like(PO),
+                        torch.zeros(cap_h, dtype=torch.int32, device="cuda"), torch.zeros_like(HO), KP.clone(),
+                        torch.zeros(cap_h, dtype=torch.float32, device="cuda"),
+                        torch.zeros(cap_h, dtype=torch.uint8, device="cuda"))
+            bp, bpo, bh, bho, bkp, out, fl = bufs
+            bp[:len(P)].copy_(P)
+            bpo.copy_(PO)
+            bh[:len(H)].copy_(H)
+            bho.copy_(HO)
+            grp.step(bp, bpo, bh, bho, bkp, out, fl, graph=True)
+        else:
+            out = torch.zeros(max(1, len(H)), dtype=torch.float32, device="cuda")
+            fl = torch.zeros(max(1, len(H)), dtype=torch.uint8, device="cuda")
+            grp.step(P, PO, H, HO, KP, out, fl)
+            if autotune_at is not None and s == autotune_at:
+                out0, fl0 = out.clone(), fl.clone()
+                pools0 = []
+                for m, mon in enumerate(monitors):
+                    t = torch.empty(1 << mon[0], dtype=torch.uint8, device="cuda")
+                    grp.copy_pool(m, t)
+                    pools0.append(t)
+                tun = grp.autotune(P, PO, H, HO, KP, out, fl)
+                assert tun.census_tile_chunks >= 256
+                assert torch.equal(out, out0) and torch.equal(fl, fl0)
+                for m, mon in enumerate(monitors):
+                    t = torch.empty(1 << mon[0], dtype=torch.uint8, device="cuda")
+                    grp.copy_pool(m, t)
+                    assert torch.equal(t, pools0[m]), "autotune changed monitor %d's pool" % m
+        ho = HO.cpu().numpy()
+        for m, mon in enumerate(monitors):
+            d = singles[m]
+            d.ingest(as_i32(pairs[m]).reshape(-1, 2), s)
+            d.close_slice(s)
+            pa = torch.empty(1 << mon[0], dtype=torch.uint8, device="cuda")
+            pb = torch.empty_like(pa)
+            grp.copy_pool(m, pa)
+            d.copy_pool(pb)
+            assert torch.equal(pa, pb), "slice %d monitor %d: pool differs from a single handle" % (s, m)
+            ha = torch.empty(2 * mon[1] + 1, dtype=torch.int64, device="cuda")
+            hb = torch.empty_like(ha)
+            grp.census(m, ha)
+            d.census(hb)
+            assert torch.equal(ha, hb), "slice %d monitor %d: census differs" % (s, m)
+            n = len(hosts[m])
+            if n:
+                e = torch.empty(n, dtype=torch.float32, device="cuda")
+                f = torch.empty(n, dtype=torch.uint8, device="cuda")
+                d.estimate(as_i32(hosts[m]), kprime[m], e, f)
+                lo = int(ho[m])
+                assert torch.equal(out[lo:lo + n], e), "slice %d monitor %d: estimates differ" % (s, m)
+                assert torch.equal(fl[lo:lo + n], f)
+    assert grp.status() == 0
+    grp.close()
+    for d in singles:
+        d.close()
+
+
+def test_group_equals_single_handles(V):
+    run_group_vs_single(V, MONITORS_L32, nslices=14)
+
+
+@pytest.mark.parametrize("L", [1, 16, 64])
+def test_group_other_segment_lengths(V, L):
+    mons = [(14, 2, 128, L, 0, 11), (15, 5, 256, L, 1, 12), (16, 7, 64 * max(1, L // 16), L, 0, 13)]
+    run_group_vs_single(V, mons, nslices=12)
+
+
+def test_group_graph_replay_equals_single_handles(V):
+    run_group_vs_single(V, MONITORS_L32[:5], nslices=12, graph=True)
+
+
+def test_group_autotune_keeps_state_and_outputs(V):
+    run_group_vs_single(V, MONITORS_L32[:4], nslices=6, autotune_at=2)
+
+
+def test_group_monitor_against_oracle(V):
+    mons = [(15, 4, 256, 32, 0, 21), (14, 3, 128, 32, 1, 22)]
+    trs = [Traffic(SMALL, pkts_per_slice=4000) for _ in mons]
+    grp = V.VateGroup([V.make_params(*m) for m in mons])
+    oras = [Oracle(c=m[0], k=m[1], g=m[2], seg_len=m[3], partition=m[4], seed=m[5]) for m in mons]
+    rng = np.random.default_rng(5)
+    for s in range(10):
+        pairs, hosts = make_slice(trs, s, rng, empty_every=4)
+        P, PO, H, HO, KP = pack(pairs, hosts, [m[1] for m in mons])
+        out = torch.zeros(max(1, len(H)), dtype=torch.float32, device="cuda")
+        grp.step(P, PO, H, HO, KP, out)
+        ho = HO.cpu().numpy()
+        for m, o in enumerate(oras):
+            if s:
+                o.advance()
+            o.ingest(pairs[m])
+            pool = torch.empty(o.P, dtype=torch.uint8, device="cuda")
+            grp.copy_pool(m, pool)
+            assert np.array_equal(pool.cpu().numpy(), o.pool())
+            if len(hosts[m]):
+                oe, _, _ = o.estimate(hosts[m], o.k)
+                de = out[int(ho[m]):int(ho[m]) + len(hosts[m])].cpu().numpy().astype(np.float64)
+                assert (np.abs(de - oe) / np.maximum(np.abs(oe), 1)).max() <= RTOL
+        info = V.vate_group_monitor_info(grp.g, 0)
+        assert info.slice == s and info.bact0 == s % (2 * mons[0][1])
+    grp.close()
+
+
+def test_group_bad_device_inputs_are_clamped_and_reported(V):
+    mons = [(14, 3, 64, 32, 0, 1), (14, 3, 64, 32, 0, 2), (14, 3, 64, 32, 0, 3)]
+    grp = V.VateGroup([V.make_params(*m) for m in mons])
+    tr = Traffic(SMALL, pkts_per_slice=100)
+    P = as_i32(tr.slice_pairs(0, n=30))
+    H = as_i32(tr.aips[:12])
+    out = torch.zeros(12, dtype=torch.float32, device="cuda")
+    # decreasing pair offsets and a host offset past the buffer
+    PO = torch.tensor([0, 20, 10, 30], dtype=torch.int64, device="cuda")
+    HO = torch.tensor([0, 4, 8, 99], dtype=torch.int64, device="cuda")
+    grp.step(P, PO, H, HO, torch.tensor([3, 3, 3], dtype=torch.int32, device="cuda"), out)
+    assert grp.status(clear=True) == V.VATE_GROUP_BAD_OFFSETS
+    PO = torch.tensor([0, 10, 20, 30], dtype=torch.int64, device="cuda")
+    HO = torch.tensor([0, 4, 8, 12], dtype=torch.int64, device="cuda")
+    grp.step(P, PO, H, HO, torch.tensor([0, 3, 7], dtype=torch.int32, device="cuda"), out)
+    assert grp.status(clear=True) == V.VATE_GROUP_BAD_KPRIME
+    grp.step(P, PO, H, HO, torch.tensor([3, 1, 2], dtype=torch.int32, device="cuda"), out)
+    assert grp.status() == 0
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
+    grp.close()
