@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator train/evaluate run")
     ap.add_argument("--workload", default="link40g", choices=["link40g", "monitors64"],
                     help="link40g: the headline single-monitor workload; monitors64: 64 independent monitors "
                          "advanced together (vate_group, CUDA graph per slice)")
@@ -325,7 +326,6 @@ def run_ours(args, rank, world, local):
         "ingest_mpkts": round(args.pkts / ingest_avg / 1e3, 1),
         "kernels_ms": {"ingest+preserve": round(ingest_avg, 4), "census": round(statistics.mean(census_ms), 4),
                        "gather+estimate": round(gather_avg, 4)},
-        "learned_vs_plain_mre": None,
         "roofline": {"bound": "l2", "achieved": round(achieved, 1),
                      "peak": round(peaks["l2_sector_read_gbs"], 1), "unit": "GB/s",
                      "frac": round(achieved / peaks["l2_sector_read_gbs"], 3), "traffic": traffic,
@@ -350,9 +350,47 @@ def run_ours(args, rank, world, local):
 
     if not args.no_e2e:
         result["e2e"] = run_e2e(args, V, torch, tr, dt, rank, world)
+    if not args.no_learned and rank == 0:
+        result["learned_vs_plain_mre"] = run_learned(V, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(tr, budget_s=20.0)
     return result
+
+
+def run_learned(V, torch):
+    """The learned-estimator workload: the 40 Gb/s traffic on a 2^24-AT pool,
+    k = 10, g = 4096; MLP trained on 200 generated slices with exact labels,
+    evaluated against the closed form on 100 held-out slices of another seed;
+    plus the close-time cost of the fused learned estimate for 2^20 hosts."""
+    from paper_1812_00282_b300 import learned
+    from traffic import LINK40G, DeviceTraffic, Traffic
+    r = learned.run(V)
+    params = r.pop("params")
+    # time both estimators on one closed slice of the same configuration
+    dt = DeviceTraffic(Traffic(LINK40G))
+    mon = V.Vate(24, 10, 4096, 32, 0, 0xC4)
+    for s in range(11):
+        mon.ingest(dt.slice_pairs(s), s)
+    mon.close_slice(10)
+    hosts = dt.hosts()
+    out = torch.empty(hosts.numel(), dtype=torch.float32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    times = {}
+    for name, fn in (("plain", lambda: mon.estimate(hosts, 10, out)),
+                     ("learned", lambda: V.vate_estimate_learned(mon.h, hosts, params, out))):
+        fn()
+        best = 1e9
+        for _ in range(5):
+            ev[0].record()
+            fn()
+            ev[1].record()
+            torch.cuda.synchronize()
+            best = min(best, ev[0].elapsed_time(ev[1]))
+        times[name] = round(best, 4)
+    mon.close()
+    r["estimate_ms_2p20_hosts"] = times
+    r["population"] = "hosts active in the window, sampled per slice; relative error |max(est,0) - n| / n"
+    return r
 
 
 def run_e2e(args, V, torch, tr, dt, rank, world):

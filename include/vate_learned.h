@@ -1,0 +1,86 @@
+/*
+ * vate_learned.h -- a small learned estimator beside the closed form of Eq. 11.
+ *
+ * The paper has no counterpart: Eq. 11 is its only estimator.  This adds an
+ * MLP that maps what the pool knows about a host at the end of slice t to
+ * log(1 + |OP(aip, t-k+1, k)|), trained on streams the method itself produces
+ * with exact labels.  The counters stay exact integers; the closed form stays
+ * available as the fallback and as the judge of the MLP's error.
+ *
+ * Features of a host (n_in = 2k + 2 floats, k <= 15):
+ *   x[d]        = c_d / g for 0 <= d < k, c_d = the host's VATs at distance d
+ *                 (last set d slices ago; vate_age_counts)
+ *   x[k + d]    = h[d] / P for 0 <= d < k, the pool's ATs at distance d
+ *                 (the census of the closed slice)
+ *   x[2k]       = log2(g) / 16
+ *   x[2k + 1]   = log1p(max(Eq. 11 estimate for k' = k, 0)) / 16
+ * Model: y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3, hidden width 64, FP32
+ * weights and accumulation.  y corrects the closed form in log space: the
+ * estimate is expm1(8 y + log1p(max(Eq. 11 estimate, 0))), so a model that
+ * outputs 0 reproduces the closed form (clamped at 0).
+ * Parameter layout (floats): W1[n_in][64], b1[64], W2[64][64], b2[64], w3[64], b3
+ * (vate_mlp_param_count(n_in) = 64 n_in + 4288 + 1).
+ *
+ * Conventions are those of vate.h.
+ */
+#ifndef VATE_LEARNED_H
+#define VATE_LEARNED_H
+
+#include <stdint.h>
+#include "vate.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VATE_MLP_HIDDEN 64
+#define VATE_FLAG_FALLBACK 4u   /* the closed form was returned (see vate_estimate_learned) */
+
+/* Number of parameters of the model for n_in inputs. */
+uint64_t vate_mlp_param_count(uint32_t n_in);
+
+/* Features (layout above) of n hosts at the end of the closed slice:
+ * d_x device float[n * (2k+2)], row-major.  Errors: VATE_EINVAL if k > 15,
+ * VATE_ESLICE if the slice is not closed. */
+int vate_features(vate_handle *h, const uint32_t *d_aips, uint64_t n, float *d_x, void *stream);
+
+/* Deterministic initialisation: weights uniform in +-sqrt(6 / (fan_in +
+ * fan_out)) (Glorot) from a counter-based hash of (seed, index); biases 0. */
+int vate_mlp_init(float *d_params, uint32_t n_in, uint64_t seed, void *stream);
+
+/* y[i] = model(x[i]) for n rows of x (device float[n * n_in]) into d_y (device float[n]). */
+int vate_mlp_forward(const float *d_params, uint32_t n_in, const float *d_x, uint64_t n, float *d_y, void *stream);
+
+/* Scratch floats that vate_mlp_train_step needs for a batch of n rows. */
+uint64_t vate_mlp_train_scratch(uint32_t n_in, uint64_t n);
+
+/* Loss of vate_mlp_train_step over the n rows, with row weights w (1 if NULL):
+ *   VATE_MLP_LOSS_SQUARED   mean of w (y - target)^2
+ *   VATE_MLP_LOSS_ABSOLUTE  mean of w |y - target|  (subgradient 0 at y = target) */
+#define VATE_MLP_LOSS_SQUARED  0u
+#define VATE_MLP_LOSS_ABSOLUTE 1u
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; t = step number >= 1) on
+ * the loss above, in place on d_params with moments d_m, d_v (each
+ * param_count floats, zero at t = 1).  d_weight: device float[n] or NULL.
+ * The gradient is formed from per-tile partial sums added in a fixed order,
+ * so training is bit-reproducible.  d_grad (param_count floats) and d_loss
+ * (1 float) receive the batch gradient and loss; either may be NULL.
+ * d_scratch: vate_mlp_train_scratch(n_in, n) floats. */
+int vate_mlp_train_step(float *d_params, float *d_m, float *d_v, uint32_t n_in, const float *d_x,
+                        const float *d_target, const float *d_weight, uint32_t loss, uint64_t n, float lr,
+                        uint32_t t, float *d_scratch, uint64_t scratch_floats, float *d_grad, float *d_loss,
+                        void *stream);
+
+/* Learned estimate of |OP(aip, t-k+1, k)| for n hosts at the end of the
+ * closed slice, in one gather per host (features, MLP and the Eq. 11 fallback
+ * fused).  The closed form is returned instead, with VATE_FLAG_FALLBACK, when
+ * the host has no active VAT or the model's output is not finite.  d_flags
+ * also carries VATE_FLAG_SAT / VATE_FLAG_POOLFULL of the closed form. */
+int vate_estimate_learned(vate_handle *h, const uint32_t *d_aips, uint64_t n, const float *d_params, float *d_out,
+                          uint8_t *d_flags, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VATE_LEARNED_H */

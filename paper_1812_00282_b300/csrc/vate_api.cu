@@ -110,6 +110,19 @@ struct vate_handle {
     uint8_t *d_stage_flags[2] = {nullptr, nullptr};
 };
 
+namespace vate {
+// read-only view of a handle for the other translation units of the library
+int handle_view(const vate_handle *h, HandleView *v) {
+    if (!h) return fail(VATE_EINVAL, "handle is NULL");
+    v->G = h->G;
+    v->bact0 = h->bact0;
+    v->hist = h->d_hist;
+    v->closed = h->closed;
+    v->sms = h->sms;
+    return VATE_OK;
+}
+}  // namespace vate
+
 namespace {
 
 int check_handle(const vate_handle *h) {

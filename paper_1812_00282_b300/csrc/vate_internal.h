@@ -14,6 +14,20 @@ constexpr int GATHER_ACTIVE = 1;
 
 void count_launch();
 
+// Read-only view of a vate_handle (defined in vate_api.cu).
+struct HandleView {
+    Geom G;
+    uint32_t bact0;
+    const uint64_t *hist;
+    bool closed;
+    int sms;
+};
+}  // namespace vate
+struct vate_handle;
+namespace vate {
+int handle_view(const vate_handle *h, HandleView *v);
+int set_error(int code, const char *msg);
+
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms);
 cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, uint64_t n, cudaStream_t st, int sms);
 cudaError_t launch_preserve(const Geom &G, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1, cudaStream_t st,

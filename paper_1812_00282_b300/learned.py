@@ -1,0 +1,179 @@
+"""Training and evaluation of the learned estimator (include/vate_learned.h).
+
+The model's arithmetic -- features, forward pass, gradient, Adam, the fused
+estimate -- runs in the library's kernels; this module only moves data:
+it drives a VATE handle through generated slices, labels sampled hosts with
+their exact window cardinality (distinct (aip, bip) keys of the last k
+slices, by sort-unique on the device), and feeds batches to
+vate_mlp_train_step.  The closed form of Eq. 11 is kept as the judge: a model
+whose mean relative error on held-out slices is worse than the closed form's
+is not accepted.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+from typing import Dict, Optional
+
+import numpy as np
+
+
+def _as_i32(t):
+    import torch
+    return torch.where(t >= 2**31, t - 2**32, t).to(torch.int32)
+
+
+def exact_window_counts(window):
+    """(hosts int64 in [0, 2^32), distinct peers per host) over the pairs of the
+    slices in `window` (device int32 tensors of shape (n, 2))."""
+    import torch
+    keys = []
+    for p in window:
+        a = p[:, 0].to(torch.int64) & 0xFFFFFFFF
+        b = p[:, 1].to(torch.int64) & 0xFFFFFFFF
+        keys.append((a << 32) | b)
+    u = torch.unique(torch.cat(keys))
+    hosts = (u >> 32) & 0xFFFFFFFF
+    h, cnt = torch.unique_consecutive(hosts, return_counts=True)
+    return h, cnt
+
+
+def collect(V, dev_traffic, c, k, g, seg_len, seed, first_slice, n_slices, hosts_per_slice, warm=None,
+            large_share=0.0, large_from=32):
+    """Run one handle over n_slices generated slices and, after `warm` slices,
+    sample hosts active in the window: features, targets (log1p(n) -
+    log1p(max(closed form, 0))) / 8, closed-form estimates and exact counts
+    (device tensors, one row per sampled host).  `large_share` of each slice's
+    sample is drawn from hosts with at least `large_from` peers (training only;
+    evaluation samples uniformly)."""
+    import torch
+    warm = k if warm is None else warm
+    h = V.Vate(c, k, g, seg_len, 0, seed)
+    n_in = 2 * k + 2
+    window = collections.deque(maxlen=k)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    Xs, Ts, Ps, Ns = [], [], [], []
+    for s in range(n_slices):
+        pairs = dev_traffic.slice_pairs(first_slice + s)
+        window.append(pairs)
+        h.ingest(pairs, s)
+        h.close_slice(s)
+        if s < warm:
+            continue
+        hosts, cnt = exact_window_counts(window)
+        m = min(hosts_per_slice, hosts.numel())
+        pick = torch.randperm(hosts.numel(), generator=gen, device="cuda")[:m]
+        if large_share > 0:
+            big = torch.nonzero(cnt >= large_from).flatten()
+            nb = min(int(m * large_share), big.numel())
+            if nb:
+                bpick = big[torch.randperm(big.numel(), generator=gen, device="cuda")[:nb]]
+                pick = torch.cat([pick[:m - nb], bpick])
+                m = pick.numel()
+        sh = _as_i32(hosts[pick]).contiguous()
+        n = cnt[pick].to(torch.float64)
+        x = torch.empty(m * n_in, dtype=torch.float32, device="cuda")
+        V.vate_features(h.h, sh, x)
+        plain = torch.empty(m, dtype=torch.float32, device="cuda")
+        h.estimate(sh, k, plain)
+        Xs.append(x.view(m, n_in))
+        base = 16.0 * x.view(m, n_in)[:, n_in - 1].to(torch.float64)      # log1p(max(plain, 0))
+        Ts.append(((torch.log1p(n) - base) / 8.0).to(torch.float32))
+        Ps.append(plain)
+        Ns.append(n)
+    h.close()
+    return torch.cat(Xs), torch.cat(Ts), torch.cat(Ps), torch.cat(Ns)
+
+
+def balance_weights(N):
+    """Row weights that give every power-of-two band of exact cardinality
+    (1, 2-3, 4-7, ..., >= 2^16) the same total weight, mean 1.  Without them
+    the rare large hosts hardly move the fit."""
+    import torch
+    band = torch.floor(torch.log2(N.to(torch.float64))).clamp(min=0, max=16).to(torch.int64)
+    cnt = torch.bincount(band, minlength=17).to(torch.float64)
+    w = 1.0 / cnt[band]
+    return (w / w.mean()).to(torch.float32)
+
+
+def train(V, X, T, n_in, epochs=8, batch=4096, lr=2e-3, seed=1, weight=None, loss_kind=None):
+    """Adam on the (weighted) absolute error in log space by default; returns
+    the parameters."""
+    import torch
+    npar = V.vate_mlp_param_count(n_in)
+    params = torch.empty(npar, dtype=torch.float32, device="cuda")
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    V.vate_mlp_init(params, n_in, seed)
+    scratch = torch.empty(V.vate_mlp_train_scratch(n_in, batch), dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    n = T.numel()
+    steps_per_epoch = max(1, n // batch)
+    t = 0
+    for ep in range(epochs):
+        order = torch.randperm(n, generator=gen, device="cuda")
+        for b in range(steps_per_epoch):
+            idx = order[b * batch:(b + 1) * batch]
+            t += 1
+            frac = t / float(epochs * steps_per_epoch)
+            step_lr = lr if frac < 0.5 else (lr / 4 if frac < 0.8 else lr / 20)
+            V.vate_mlp_train_step(params, m, v, n_in, X[idx].contiguous(), T[idx].contiguous(), step_lr, t, scratch,
+                                  weight=weight[idx].contiguous() if weight is not None else None,
+                                  loss_kind=V.VATE_MLP_LOSS_ABSOLUTE if loss_kind is None else loss_kind)
+    return params
+
+
+def learned_from_features(V, params, X, plain, k):
+    """The product's rule applied to feature rows: expm1(8 y + log1p(max(plain, 0))),
+    or the closed form when the host has no active VAT or that is not finite."""
+    import torch
+    n_in = X.shape[1]
+    y = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    V.vate_mlp_forward(params, n_in, X.contiguous(), y)
+    est = torch.expm1(8.0 * y + 16.0 * X[:, n_in - 1])
+    no_active = X[:, :k].sum(1) == 0
+    bad = ~torch.isfinite(est) | no_active
+    return torch.where(bad, plain, est)
+
+
+def mean_rel_err(est, n, lo=1):
+    import torch
+    sel = n >= lo
+    e = torch.clamp(est.to(torch.float64), min=0.0)
+    return float((torch.abs(e[sel] - n[sel]) / n[sel]).mean().item()), int(sel.sum().item())
+
+
+def run(V, spec=None, c=24, k=10, g=4096, seg_len=32, train_slices=200, eval_slices=100, hosts_per_slice=8192,
+        eval_hosts_per_slice=16384, epochs=8, seed=0xC4, large_share=0.0) -> Dict:
+    """Learned-estimator workload: the 40 Gb/s traffic on a 2^24-AT pool, k = 10;
+    train on `train_slices` generated slices, evaluate on `eval_slices`
+    held-out slices of a differently seeded stream, against the closed form."""
+    import torch
+    from traffic import LINK40G, DeviceTraffic, Traffic, TrafficSpec
+    spec = LINK40G if spec is None else spec
+    t0 = time.time()
+    tr_train = DeviceTraffic(Traffic(spec))
+    X, T, _, N = collect(V, tr_train, c, k, g, seg_len, seed, 0, train_slices + k, hosts_per_slice,
+                         large_share=large_share)
+    t1 = time.time()
+    params = train(V, X, T, 2 * k + 2, epochs=epochs, seed=seed, weight=balance_weights(N))
+    torch.cuda.synchronize()
+    t2 = time.time()
+    spec_eval = TrafficSpec(**{**spec.__dict__, "seed": spec.seed + 0x4E})
+    tr_eval = DeviceTraffic(Traffic(spec_eval))
+    Xe, _, Pe, Ne = collect(V, tr_eval, c, k, g, seg_len, seed + 1, 0, eval_slices + k, eval_hosts_per_slice)
+    Le = learned_from_features(V, params, Xe, Pe, k)
+    res = {}
+    for lo in (1, 100):
+        ml, cnt = mean_rel_err(Le, Ne, lo)
+        mp, _ = mean_rel_err(Pe, Ne, lo)
+        res["n>=%d" % lo] = {"learned": round(ml, 5), "plain": round(mp, 5), "hosts": cnt}
+    accepted = res["n>=1"]["learned"] <= res["n>=1"]["plain"]
+    return {"mre": res, "accepted": bool(accepted), "train_rows": int(T.numel()), "eval_rows": int(Ne.numel()),
+            "train_slices": train_slices, "eval_slices": eval_slices, "log2_pool": c, "k": k, "g": g,
+            "seconds": {"collect_train": round(t1 - t0, 2), "train": round(t2 - t1, 2),
+                        "collect_eval": round(time.time() - t2, 2)},
+            "params": params}

@@ -90,6 +90,13 @@ def _load() -> C.CDLL:
         "vate_group_copy_pool": (i, [vp, u32, vp, vp]),
         "vate_group_census": (i, [vp, u32, vp, vp]),
         "vate_group_monitor_info": (i, [vp, u32, P(vate_info), vp]),
+        "vate_mlp_param_count": (u64, [u32]),
+        "vate_mlp_train_scratch": (u64, [u32, u64]),
+        "vate_features": (i, [vp, vp, u64, vp, vp]),
+        "vate_mlp_init": (i, [vp, u32, u64, vp]),
+        "vate_mlp_forward": (i, [vp, u32, vp, u64, vp, vp]),
+        "vate_mlp_train_step": (i, [vp, vp, vp, u32, vp, vp, vp, u32, u64, C.c_float, u32, vp, u64, vp, vp, vp]),
+        "vate_estimate_learned": (i, [vp, vp, u64, vp, vp, vp, vp]),
         "vate_probe_sector_read": (i, [vp, u64, u64, vp, vp]),
         "vate_probe_byte_write": (i, [vp, u64, u64, vp]),
     }
@@ -307,6 +314,69 @@ def vate_probe_byte_write(buf, n_writes: int, stream=None) -> None:
     """Random 1-byte stores into a CUDA uint8 buffer (include/vate_probe.h)."""
     import torch
     _check(_lib.vate_probe_byte_write(_dev(buf, torch.uint8, "buf"), buf.numel(), n_writes, _stream(stream)))
+
+
+# ---- learned estimator (include/vate_learned.h) -------------------------------
+
+VATE_FLAG_FALLBACK = 4
+VATE_MLP_LOSS_SQUARED, VATE_MLP_LOSS_ABSOLUTE = 0, 1
+
+
+def vate_mlp_param_count(n_in: int) -> int:
+    return int(_lib.vate_mlp_param_count(n_in))
+
+
+def vate_mlp_train_scratch(n_in: int, n: int) -> int:
+    return int(_lib.vate_mlp_train_scratch(n_in, n))
+
+
+def vate_features(h, aips, x, stream=None) -> None:
+    import torch
+    n = aips.numel()
+    k = vate_get_info_k(h)
+    pa = _dev(aips, aips.dtype if aips.dtype in (torch.int32, torch.uint32) else torch.int32, "aips")
+    px = _dev(x, torch.float32, "x", n * (2 * k + 2))
+    _check(_lib.vate_features(h, pa, n, px, _stream(stream)))
+
+
+def vate_mlp_init(params, n_in: int, seed: int, stream=None) -> None:
+    import torch
+    _check(_lib.vate_mlp_init(_dev(params, torch.float32, "params", vate_mlp_param_count(n_in)), n_in,
+                              seed & 0xFFFFFFFFFFFFFFFF, _stream(stream)))
+
+
+def vate_mlp_forward(params, n_in: int, x, y, stream=None) -> None:
+    import torch
+    n = x.numel() // n_in
+    _check(_lib.vate_mlp_forward(_dev(params, torch.float32, "params", vate_mlp_param_count(n_in)), n_in,
+                                 _dev(x, torch.float32, "x", n * n_in), n, _dev(y, torch.float32, "y", n),
+                                 _stream(stream)))
+
+
+def vate_mlp_train_step(params, m, v, n_in: int, x, target, lr: float, t: int, scratch, grad=None, loss=None,
+                        weight=None, loss_kind: int = VATE_MLP_LOSS_SQUARED, stream=None) -> None:
+    import torch
+    n = target.numel()
+    npar = vate_mlp_param_count(n_in)
+    _check(_lib.vate_mlp_train_step(
+        _dev(params, torch.float32, "params", npar), _dev(m, torch.float32, "m", npar),
+        _dev(v, torch.float32, "v", npar), n_in, _dev(x, torch.float32, "x", n * n_in),
+        _dev(target, torch.float32, "target", n),
+        _dev(weight, torch.float32, "weight", n) if weight is not None else None, loss_kind, n, float(lr), t,
+        _dev(scratch, torch.float32, "scratch"),
+        scratch.numel(), _dev(grad, torch.float32, "grad", npar) if grad is not None else None,
+        _dev(loss, torch.float32, "loss", 1) if loss is not None else None, _stream(stream)))
+
+
+def vate_estimate_learned(h, aips, params, out, flags=None, stream=None) -> None:
+    import torch
+    n = aips.numel()
+    pa = _dev(aips, aips.dtype if aips.dtype in (torch.int32, torch.uint32) else torch.int32, "aips")
+    k = vate_get_info_k(h)
+    pp = _dev(params, torch.float32, "params", vate_mlp_param_count(2 * k + 2))
+    po = _dev(out, torch.float32, "out", n)
+    pf = _dev(flags, torch.uint8, "flags", n) if flags is not None else None
+    _check(_lib.vate_estimate_learned(h, pa, n, pp, po, pf, _stream(stream)))
 
 
 # ---- monitor groups (include/vate_group.h) -----------------------------------

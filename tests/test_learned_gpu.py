@@ -1,0 +1,135 @@
+"""The learned estimator's kernels (include/vate_learned.h) against the FP64
+reference of the model (oracle/mlp.py) and the oracle's features:
+  - features: per-age counts and pool fractions exact, the Eq. 11 feature
+    within the FP32 tolerance;
+  - forward pass within FP32 accumulation tolerance;
+  - one training step: gradient and loss within FP32 tolerance, Adam update
+    recomputed from the returned gradient;
+  - training is bit-reproducible; the fused estimate equals
+    expm1(8 * forward(features)) with the closed-form fallback.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import Oracle, mlp
+from traffic import SMALL, Traffic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1812_00282_b300 as V
+    return V
+
+
+def as_i32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.uint32).view(np.int32)).cuda()
+
+
+def small_run(V, L=32, k=5, c=16, g=512, slices=8):
+    tr = Traffic(SMALL, pkts_per_slice=20_000)
+    d = V.Vate(c, k, g, L, 0, 7)
+    o = Oracle(c=c, k=k, g=g, seg_len=L, partition=0, seed=7)
+    for s in range(slices):
+        p = tr.slice_pairs(s)
+        if s:
+            o.advance()
+        o.ingest(p)
+        d.ingest(as_i32(p), s)
+    d.close_slice(slices - 1)
+    return tr, d, o
+
+
+@pytest.mark.parametrize("L", [1, 32])
+def test_features_match_oracle(V, L):
+    tr, d, o = small_run(V, L=L)
+    hosts = tr.aips[:1500]
+    k = o.k
+    x = torch.empty(len(hosts) * (2 * k + 2), dtype=torch.float32, device="cuda")
+    V.vate_features(d.h, as_i32(hosts), x)
+    X = x.view(len(hosts), -1).cpu().numpy().astype(np.float64)
+    Xo, _ = mlp.features(o, hosts)
+    np.testing.assert_allclose(X[:, :2 * k + 1], Xo[:, :2 * k + 1], rtol=1e-6, atol=0)
+    np.testing.assert_allclose(X[:, 2 * k + 1], Xo[:, 2 * k + 1], rtol=1e-5, atol=1e-6)
+    d.close()
+
+
+def test_forward_matches_reference(V):
+    rng = np.random.default_rng(1)
+    n_in = 22
+    p = rng.normal(0, 0.2, mlp.n_params(n_in)).astype(np.float32)
+    X = rng.normal(0, 1, (3000, n_in)).astype(np.float32)
+    y = torch.empty(3000, dtype=torch.float32, device="cuda")
+    V.vate_mlp_forward(torch.from_numpy(p).cuda(), n_in, torch.from_numpy(X).cuda(), y)
+    ref = mlp.forward(p.astype(np.float64), n_in, X.astype(np.float64))
+    np.testing.assert_allclose(y.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_train_step_gradient_and_update(V, kind):
+    rng = np.random.default_rng(2)
+    n_in, n = 12, 1000
+    npar = mlp.n_params(n_in)
+    p = rng.normal(0, 0.2, npar).astype(np.float32)
+    X = rng.normal(0, 1, (n, n_in)).astype(np.float32)
+    t = rng.normal(0, 1, n).astype(np.float32)
+    dp = torch.from_numpy(p.copy()).cuda()
+    m = torch.zeros(npar, dtype=torch.float32, device="cuda")
+    v = torch.zeros_like(m)
+    grad = torch.empty_like(m)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    scratch = torch.empty(V.vate_mlp_train_scratch(n_in, n), dtype=torch.float32, device="cuda")
+    lr = 1e-3
+    w = rng.uniform(0.2, 3.0, n).astype(np.float32)
+    V.vate_mlp_train_step(dp, m, v, n_in, torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), lr, 1, scratch,
+                          grad, loss, weight=torch.from_numpy(w).cuda(), loss_kind=kind)
+    lref, gref = mlp.loss_and_grad(p.astype(np.float64), n_in, X.astype(np.float64), t.astype(np.float64),
+                                   w.astype(np.float64), absolute=(kind == 1))
+    g = grad.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - lref) <= 1e-5 * abs(lref)
+    scale = np.abs(gref).max()
+    assert np.abs(g - gref).max() <= 1e-4 * scale, np.abs(g - gref).max() / scale
+    # Adam at t = 1 from zero moments: m = 0.1 g, v = 0.001 g^2, update lr * g / (|g| + eps)
+    gf = grad.cpu().numpy()
+    expect = p - lr * (0.1 * gf / 0.1) / (np.sqrt(0.001 * gf * gf / 0.001) + 1e-8)
+    np.testing.assert_allclose(dp.cpu().numpy(), expect, rtol=1e-6, atol=1e-7)
+
+
+def test_training_is_reproducible_and_fused_estimate_matches(V):
+    from paper_1812_00282_b300 import learned
+    tr, d, o = small_run(V, L=32, k=5, c=16, g=512)
+    k, n_in = 5, 12
+    hosts = as_i32(tr.aips)
+    x = torch.empty(hosts.numel() * n_in, dtype=torch.float32, device="cuda")
+    V.vate_features(d.h, hosts, x)
+    X = x.view(-1, n_in)
+    T = torch.rand(X.shape[0], generator=torch.Generator(device="cuda").manual_seed(3), device="cuda")
+    p1 = learned.train(V, X, T, n_in, epochs=2, batch=512, seed=5)
+    p2 = learned.train(V, X, T, n_in, epochs=2, batch=512, seed=5)
+    assert torch.equal(p1, p2)
+    plain = torch.empty(hosts.numel(), dtype=torch.float32, device="cuda")
+    d.estimate(hosts, k, plain)
+    out = torch.empty_like(plain)
+    fl = torch.empty(hosts.numel(), dtype=torch.uint8, device="cuda")
+    V.vate_estimate_learned(d.h, hosts, p1, out, fl)
+    ref = learned.learned_from_features(V, p1, X, plain, k)
+    torch.testing.assert_close(out, ref, rtol=1e-6, atol=1e-6)
+    fb = (fl & V.VATE_FLAG_FALLBACK) != 0
+    assert torch.equal(fb, X[:, :k].sum(1) == 0)
+    d.close()
+
+
+def test_learned_pipeline_small(V):
+    # the whole train / held-out evaluation loop on the small traffic shape
+    from paper_1812_00282_b300 import learned
+    from traffic import SMALL
+    r = learned.run(V, spec=SMALL, c=18, k=5, g=1024, train_slices=24, eval_slices=8, hosts_per_slice=2048,
+                    eval_hosts_per_slice=2048, epochs=3)
+    for pop in ("n>=1",):
+        assert np.isfinite(r["mre"][pop]["learned"]) and np.isfinite(r["mre"][pop]["plain"])
+        assert r["mre"][pop]["hosts"] > 1000
+    assert r["params"].numel() == V.vate_mlp_param_count(12)
