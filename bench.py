@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator train/evaluate run")
-    ap.add_argument("--workload", default="link40g", choices=["link40g", "monitors64"],
+    ap.add_argument("--workload", default="link40g", choices=["link40g", "monitors64", "serving"],
                     help="link40g: the headline single-monitor workload; monitors64: 64 independent monitors "
                          "advanced together (vate_group, CUDA graph per slice)")
     return ap.parse_args()
@@ -605,8 +605,33 @@ def run_monitors64(args):
             "modes": res}
 
 
+def run_serving(args):
+    """Config 5: monitors admitted by an 8 GB AT-memory budget, Poisson batches
+    of 1k..1M pairs (mean 8 Mpkt/s, bursts to 30 Mpkt/s), 1 s slices, k = 10,
+    learned estimator (trained here on the 2^24-pool configuration) with the
+    closed form as fallback; real-time paced and all-at-once runs."""
+    import torch
+    import paper_1812_00282_b300 as V
+    from paper_1812_00282_b300 import learned, serving
+    torch.cuda.set_device(0)
+    lr = learned.run(V, train_slices=60, eval_slices=20)
+    model = lr.pop("params")
+    paced = serving.run(V, duration=5.0, paced=True, model=model)
+    flood = serving.run(V, duration=5.0, paced=False, model=model)
+    return {"metric": METRIC, "value": flood["mpkts"], "unit": "Mpkt/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": round(flood["wall_s"] * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "serving loop: candidate monitors (pools 2^24..2^31, k=10, g=4096) admitted by an "
+                                   "8 GB AT budget up to 16, Poisson batches 1k-1M pairs, mean 8 Mpkt/s, bursts to "
+                                   "30 Mpkt/s, 1 s slices, learned estimator with closed-form fallback"},
+            "paced": paced, "flood": flood, "model_mre": lr["mre"]}
+
+
 def main():
     args = parse()
+    if args.workload == "serving":
+        print(json.dumps(run_serving(args)), flush=True)
+        return
     if args.workload == "monitors64":
         print(json.dumps(run_monitors64(args)), flush=True)
         return

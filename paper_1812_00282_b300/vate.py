@@ -53,6 +53,24 @@ class vate_group_tuning(C.Structure):
 VATE_GROUP_BAD_OFFSETS, VATE_GROUP_BAD_KPRIME = 1, 2
 
 
+class vate_server_config(C.Structure):
+    _fields_ = [("memory_budget_bytes", C.c_uint64), ("slots", C.c_uint32), ("slot_records", C.c_uint32)]
+
+
+class vate_server_stats(C.Structure):
+    _fields_ = [("ingests_done", C.c_uint64), ("closes_done", C.c_uint64), ("pairs_done", C.c_uint64),
+                ("hosts_done", C.c_uint64), ("merged_ingests", C.c_uint64), ("ingest_p50_ms", C.c_double),
+                ("ingest_p99_ms", C.c_double), ("close_p50_ms", C.c_double), ("close_p99_ms", C.c_double),
+                ("memory_in_use", C.c_uint64), ("monitors", C.c_uint32), ("max_in_flight", C.c_uint32)]
+
+    def as_dict(self):
+        return {f: (round(v, 4) if isinstance(v, float) else int(v)) for f, _ in self._fields_
+                for v in [getattr(self, f)]}
+
+
+VATE_SUBMIT_PINNED = 1
+
+
 def _load() -> C.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError("libvate.so is not built (run `python -m paper_1812_00282_b300.build`): " + LIB_PATH)
@@ -97,6 +115,16 @@ def _load() -> C.CDLL:
         "vate_mlp_forward": (i, [vp, u32, vp, u64, vp, vp]),
         "vate_mlp_train_step": (i, [vp, vp, vp, u32, vp, vp, vp, u32, u64, C.c_float, u32, vp, u64, vp, vp, vp]),
         "vate_estimate_learned": (i, [vp, vp, u64, vp, vp, vp, vp]),
+        "vate_server_create": (i, [P(vate_server_config), P(vp)]),
+        "vate_server_destroy": (i, [vp]),
+        "vate_server_admit": (i, [vp, P(vate_params), P(C.c_int32)]),
+        "vate_server_release": (i, [vp, C.c_int32]),
+        "vate_server_set_model": (i, [vp, C.c_int32, vp]),
+        "vate_server_submit_ingest": (i, [vp, C.c_int32, vp, u64, i64, u32, P(u64)]),
+        "vate_server_submit_close": (i, [vp, C.c_int32, i64, vp, u64, u32, vp, vp, u32, P(u64)]),
+        "vate_server_wait": (i, [vp, u64, u32]),
+        "vate_server_drain": (i, [vp, u32]),
+        "vate_server_get_stats": (i, [vp, P(vate_server_stats), i]),
         "vate_probe_sector_read": (i, [vp, u64, u64, vp, vp]),
         "vate_probe_byte_write": (i, [vp, u64, u64, vp]),
     }
@@ -492,6 +520,82 @@ class VateGroup:
 
     def census(self, m, hist, stream=None):
         vate_group_census(self.g, m, hist, stream)
+
+
+# ---- serving loop (include/vate_server.h) -------------------------------------
+
+def vate_server_create(memory_budget_bytes: int, slots: int = 8, slot_records: int = 1 << 20) -> C.c_void_p:
+    cfg = vate_server_config(memory_budget_bytes, slots, slot_records)
+    s = C.c_void_p()
+    _check(_lib.vate_server_create(C.byref(cfg), C.byref(s)))
+    return s
+
+
+def vate_server_destroy(s) -> None:
+    _check(_lib.vate_server_destroy(s))
+
+
+def vate_server_admit(s, params: vate_params) -> int:
+    i = C.c_int32()
+    _check(_lib.vate_server_admit(s, C.byref(params), C.byref(i)))
+    return int(i.value)
+
+
+def vate_server_release(s, mid: int) -> None:
+    _check(_lib.vate_server_release(s, mid))
+
+
+def vate_server_set_model(s, mid: int, params=None) -> None:
+    import torch
+    _check(_lib.vate_server_set_model(s, mid, _dev(params, torch.float32, "params") if params is not None else None))
+
+
+def _host_ptr(a, nbytes_per, name):
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or not a.is_contiguous():
+            raise TypeError("%s must be a contiguous host tensor" % name)
+        return a.data_ptr(), a.numel() * a.element_size() // nbytes_per
+    if not isinstance(a, np.ndarray) or not a.flags.c_contiguous:
+        raise TypeError("%s must be a C-contiguous numpy array or host tensor" % name)
+    return a.ctypes.data, a.nbytes // nbytes_per
+
+
+def vate_server_submit_ingest(s, mid: int, pairs, slice: int, flags: int = 0) -> int:
+    """pairs: host buffer of (aip, bip) uint32 pairs; keep it alive until wait()."""
+    ptr, n = _host_ptr(pairs, 8, "pairs")
+    t = C.c_uint64()
+    _check(_lib.vate_server_submit_ingest(s, mid, ptr if n else None, n, slice, flags, C.byref(t)))
+    return int(t.value)
+
+
+def vate_server_submit_close(s, mid: int, slice: int, hosts, kprime: int, out, flags_out=None, flags: int = 0) -> int:
+    ph, n = _host_ptr(hosts, 4, "hosts")
+    po, no = _host_ptr(out, 4, "out")
+    if no < n:
+        raise ValueError("out is too small")
+    pf = None
+    if flags_out is not None:
+        pf, nf = _host_ptr(flags_out, 1, "flags_out")
+        if nf < n:
+            raise ValueError("flags_out is too small")
+    t = C.c_uint64()
+    _check(_lib.vate_server_submit_close(s, mid, slice, ph if n else None, n, kprime, po, pf, flags, C.byref(t)))
+    return int(t.value)
+
+
+def vate_server_wait(s, ticket: int, timeout_ms: int = 60000) -> None:
+    _check(_lib.vate_server_wait(s, ticket, timeout_ms))
+
+
+def vate_server_drain(s, timeout_ms: int = 60000) -> None:
+    _check(_lib.vate_server_drain(s, timeout_ms))
+
+
+def vate_server_get_stats(s, reset: bool = False) -> vate_server_stats:
+    st = vate_server_stats()
+    _check(_lib.vate_server_get_stats(s, C.byref(st), 1 if reset else 0))
+    return st
 
 
 class Vate:
