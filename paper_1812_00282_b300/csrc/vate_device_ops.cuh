@@ -157,20 +157,36 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, uint32_t bact
                 if (valid[j]) w[j] = __ldg(pool16 + (pid[j] >> 4));
             }
         }
-        // CheckAT on every loaded chunk
+        // CheckAT on every loaded chunk; the per-chunk straddle test only runs
+        // when some segment of the batch straddles a block boundary (rare)
         uint32_t acc = 0;
+        bool any_straddle = false;
 #pragma unroll
-        for (int j = 0; j < NL; j++) {
-            if (!valid[j]) continue;
-            if (sact[j] & 0x100u) {
-                cnt += count_chunk_bytes(G, bact0, kprime, pid[j], w[j]);
-            } else {
+        for (int rb = 0; rb < RB; rb++) any_straddle |= __any_sync(0xFFFFFFFFu, (actf[rb] & 0x100u) != 0u);
+        if (!any_straddle) {
+#pragma unroll
+            for (int j = 0; j < NL; j++) {
+                if (!valid[j]) continue;
                 const RangeConsts rc = tbl[sact[j]];
                 // (m >> 7) added as a multiply-high by 2^25 (multiply-add pipe)
                 acc = __umulhi(swar_active_fma(w[j].x, rc, c2k, u1, u2, u3), 1u << 25) + acc;
                 acc = __umulhi(swar_active_fma(w[j].y, rc, c2k, u1, u2, u3), 1u << 25) + acc;
                 acc = __umulhi(swar_active_fma(w[j].z, rc, c2k, u1, u2, u3), 1u << 25) + acc;
                 acc = __umulhi(swar_active_fma(w[j].w, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NL; j++) {
+                if (!valid[j]) continue;
+                if (sact[j] & 0x100u) {
+                    cnt += count_chunk_bytes(G, bact0, kprime, pid[j], w[j]);
+                } else {
+                    const RangeConsts rc = tbl[sact[j]];
+                    acc = __umulhi(swar_active_fma(w[j].x, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                    acc = __umulhi(swar_active_fma(w[j].y, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                    acc = __umulhi(swar_active_fma(w[j].z, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                    acc = __umulhi(swar_active_fma(w[j].w, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                }
             }
         }
         uint32_t t = (acc & 0x00FF00FFu) + ((acc >> 8) & 0x00FF00FFu);

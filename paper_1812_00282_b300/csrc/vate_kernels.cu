@@ -197,13 +197,22 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t a32 = (uint32_t)min(G.a, (uint64_t)0xFFFFFFFFu);
 
-    uint32_t next_aip = warp0 < n ? aips[warp0] : 0u;    // host addresses are fetched one host ahead
-    for (uint64_t h = warp0; h < n; h += nwarps) {
-        const uint32_t aip = next_aip;
-        if (h + nwarps < n) next_aip = aips[h + nwarps];
-        uint32_t cnt = gather_host_vec<CPSL, RB, FULL>(G, bact0, kprime, aip, tbl, c2k, a32, u1, u2, u3, lane);
-        uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
-        if (lane == 0) write_result<MODE>(G, N0, h, A, out, flags, active);
+    // The warp takes its hosts 32 at a time (hosts g0 + j * nwarps, j < 32):
+    // lane j loads host j's address up front, the warp gathers the hosts one
+    // by one, lane j keeps host j's count, and the 32 Eq. 11 epilogues then
+    // run side by side, one per lane.
+    for (uint64_t g0 = warp0; g0 < n; g0 += 32 * nwarps) {
+        const uint64_t mine = g0 + (uint64_t)lane * nwarps;
+        const uint32_t my_aip = mine < n ? aips[mine] : 0u;
+        uint32_t my_A = 0;
+        for (uint32_t j = 0; j < 32u; j++) {
+            if (g0 + (uint64_t)j * nwarps >= n) break;
+            const uint32_t aip = __shfl_sync(0xFFFFFFFFu, my_aip, j);
+            uint32_t cnt = gather_host_vec<CPSL, RB, FULL>(G, bact0, kprime, aip, tbl, c2k, a32, u1, u2, u3, lane);
+            uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
+            if (lane == j) my_A = A;
+        }
+        if (mine < n) write_result<MODE>(G, N0, mine, my_A, out, flags, active);
     }
 }
 
