@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator train/evaluate run")
-    ap.add_argument("--workload", default="link40g", choices=["link40g", "monitors64", "serving"],
+    ap.add_argument("--workload", default="link40g", choices=["link40g", "monitors64", "serving", "pt"],
                     help="link40g: the headline single-monitor workload; monitors64: 64 independent monitors "
                          "advanced together (vate_group, CUDA graph per slice)")
     return ap.parse_args()
@@ -627,8 +627,53 @@ def run_serving(args):
             "paced": paced, "flood": flood, "model_mre": lr["mre"]}
 
 
+def run_pt(args):
+    """Maintenance time per slide (the paper's PT, Sec. 5): asynchronous
+    timestamps (PreserveAT on the two blocks whose ACT became 0 or k) against
+    distance recorders (every recorder aged each slide), pools of 2^23..2^32
+    counters, the 40 Gb/s traffic ingested between slides.  PT of a slide =
+    CUDA-event time of vate_ingest with no pairs into the next slice."""
+    import torch
+    import paper_1812_00282_b300 as V
+    from traffic import LINK40G, DeviceTraffic, Traffic
+    torch.cuda.set_device(0)
+    dt = DeviceTraffic(Traffic(LINK40G))
+    empty = torch.zeros(0, 2, dtype=torch.int32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    hbm = measured_peaks().get("hbm_gbs", 6400.0)
+    rows = []
+    for k in (10, 63):
+        for c in range(23, 33):
+            res = {"k": k, "log2_counters": c}
+            for name, counter in (("vate", V.VATE_COUNTER_AT), ("vdre", V.VATE_COUNTER_DR)):
+                h = V.Vate(c, k, 1024, 32, 0, 0xD7, counter=counter)
+                times = []
+                for s in range(2 * k + 4):
+                    h.ingest(dt.slice_pairs(s % 40), s)
+                    ev[0].record()
+                    h.ingest(empty, s + 1)          # the slide into slice s+1: maintenance only
+                    ev[1].record()
+                    torch.cuda.synchronize()
+                    if s >= 2:
+                        times.append(ev[0].elapsed_time(ev[1]))
+                h.close()
+                res[name + "_pt_ms"] = round(statistics.mean(times), 4)
+                res[name + "_pt_max_ms"] = round(max(times), 4)
+            res["speedup"] = round(res["vdre_pt_ms"] / res["vate_pt_ms"], 1)
+            # bytes a slide must read: the whole pool (VDRE) or the two maintained blocks (VATE)
+            res["vdre_read_gbs"] = round((1 << c) / res["vdre_pt_ms"] / 1e6, 1)
+            res["vate_read_gbs"] = round(2 * (1 << c) / (2 * k - 1) / res["vate_pt_ms"] / 1e6, 1)
+            rows.append(res)
+            torch.cuda.empty_cache()
+    return {"workload": "maintenance time per slide (PT), VATE vs VDRE, 40 Gb/s traffic between slides, g = 1024",
+            "hbm_peak_gbs": hbm, "rows": rows}
+
+
 def main():
     args = parse()
+    if args.workload == "pt":
+        print(json.dumps(run_pt(args)), flush=True)
+        return
     if args.workload == "serving":
         print(json.dumps(run_serving(args)), flush=True)
         return

@@ -76,6 +76,13 @@ typedef struct {
  *              and a last block of b = P mod (2k-1)); 1: the low-deviation
  *              partition of Sec. 4.1 (block sizes P/(2k) or P/(2k)+1).
  *              Either way every block must hold at least 32 ATs.
+ *   counter    0 (VATE_COUNTER_AT): asynchronous timestamps, values 0..2k,
+ *              maintained once every k slices per block (Sec. 3, Algorithm 3);
+ *              1 (VATE_COUNTER_DR): distance recorders, values 0..k (k =
+ *              inactive), reset to 0 by SetAT and aged by one in every slide,
+ *              the whole pool each slice (Sec. 1; the VDRE of Sec. 5).  Both
+ *              give the same active sets, censuses and estimates; they differ
+ *              in the maintenance work per slide.
  *   seed       keys the hash functions H and BH.
  * The hash functions (Sec. 4.1 leaves them open):
  *   mix(x)   = SplitMix64 output function (Steele, Lea & Flood 2014)
@@ -88,9 +95,12 @@ typedef struct {
     uint32_t g;
     uint32_t seg_len;
     uint32_t partition;
-    uint32_t reserved;   /* must be 0 */
+    uint32_t counter;    /* VATE_COUNTER_AT (0) or VATE_COUNTER_DR (1) */
     uint64_t seed;
 } vate_params;
+
+#define VATE_COUNTER_AT 0u
+#define VATE_COUNTER_DR 1u
 
 /* Read-only view of a handle's geometry and slice state. */
 typedef struct {

@@ -40,7 +40,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 // Parameter checks and derived geometry; no device needed.
 int make_geom(const vate_params *p, Geom *G) {
     if (!p) return fail(VATE_EINVAL, "params is NULL");
-    if (p->reserved != 0) return fail(VATE_EINVAL, "params.reserved must be 0");
+    if (p->counter > 1) return fail(VATE_EINVAL, "params.counter must be VATE_COUNTER_AT (0) or VATE_COUNTER_DR (1)");
     if (p->log2_pool < 12 || p->log2_pool > 32) return fail(VATE_EINVAL, "log2_pool (c) must be in [12, 32], got %u", p->log2_pool);
     if (p->k < 1 || p->k > 63) return fail(VATE_EINVAL, "k must be in [1, 63] for byte ATs, got %u", p->k);
     if (p->g < 1 || p->g > 65536) return fail(VATE_EINVAL, "g must be in [1, 65536], got %u", p->g);
@@ -60,6 +60,7 @@ int make_geom(const vate_params *p, Geom *G) {
     G->log2L = log2L;
     G->segbits = p->log2_pool - log2L;
     G->partition = p->partition;
+    G->counter = p->counter;
     G->P = 1ull << p->log2_pool;
     G->key_h = vate::mix64(p->seed + 1);
     G->key_bh = vate::mix64(p->seed + 2);
@@ -143,16 +144,23 @@ int advance_to(vate_handle *h, int64_t slice, cudaStream_t st) {
     }
     const Geom &G = h->G;
     int64_t steps = slice - h->slice;
-    int64_t run = steps > (int64_t)G.twok ? (int64_t)G.twok : steps;
+    // distance recorders all reach k (inactive) after k slides, timestamps after 2k
+    const int64_t settle = G.counter == 1u ? (int64_t)G.k : (int64_t)G.twok;
+    int64_t run = steps > settle ? settle : steps;
     for (int64_t s = 0; s < run; s++) {
         h->bact0 = (h->bact0 + 1) % G.twok;
-        uint32_t i0 = (G.twok - h->bact0) % G.twok;          // BACT = 0
-        uint32_t i1 = (G.k + G.twok - h->bact0) % G.twok;    // BACT = k
-        uint64_t s0, e0, s1, e1;
-        vate::block_range_of(G, i0, &s0, &e0);
-        vate::block_range_of(G, i1, &s1, &e1);
-        cudaError_t e = vate::launch_preserve(G, s0, e0, s1, e1, st, h->sms);
-        if (e != cudaSuccess) return cuda_fail(e, "preserve launch");
+        cudaError_t e;
+        if (G.counter == 1u) {
+            e = vate::launch_dr_age(G, st, h->sms);                // VDRE: age the whole pool
+        } else {
+            uint32_t i0 = (G.twok - h->bact0) % G.twok;          // BACT = 0
+            uint32_t i1 = (G.k + G.twok - h->bact0) % G.twok;    // BACT = k
+            uint64_t s0, e0, s1, e1;
+            vate::block_range_of(G, i0, &s0, &e0);
+            vate::block_range_of(G, i1, &s1, &e1);
+            e = vate::launch_preserve(G, s0, e0, s1, e1, st, h->sms);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "maintenance launch");
     }
     if (steps > run) h->bact0 = (uint32_t)((h->bact0 + (uint64_t)(steps - run)) % G.twok);
     h->slice = slice;

@@ -34,6 +34,7 @@ struct Geom {
     uint64_t ma1;        // ceil(2^64 / (a + 1)) (low-deviation partition)
     uint64_t first;      // low-deviation: ATs below this index are in blocks of size a
     uint32_t c, k, twok, g, L, log2L, segbits, partition;
+    uint32_t counter;    // 0: asynchronous timestamps; 1: distance recorders
     // host side only: L2 access-policy window over the pool for every launch
     // that touches it (l2_window_bytes = 0: none)
     uint64_t l2_window_bytes;
@@ -182,7 +183,35 @@ VATE_HD uint32_t swar_preserve(uint32_t w, bool act_is_zero, uint32_t k) {
     return (w & ~bytes) | ((twok * ONES) & bytes);
 }
 
+// Distance recorders (VDRE): value 0..k, k = inactive; one slide adds 1 to
+// every recorder below k (four recorders per word; values <= 126).
+VATE_HD uint32_t swar_dr_age(uint32_t w, uint32_t k) {
+    uint32_t t = w + ONES;
+    uint32_t over = (t + (127u - k) * ONES) & HIGH;          // t > k
+    uint32_t bytes = (over >> 7) * 0xFFu;
+    return (t & ~bytes) | ((k * ONES) & bytes);
+}
+
+// Census bin of four recorders: the value itself when below k, else 2k.
+VATE_HD uint32_t swar_dr_bins(uint32_t w, uint32_t k, uint32_t twok) {
+    uint32_t ge = (w + (128u - k) * ONES) & HIGH;            // v >= k: inactive
+    uint32_t bytes = (ge >> 7) * 0xFFu;
+    return (w & ~bytes) | ((twok * ONES) & bytes);
+}
+
+// Range constants of CheckDR for window k': active iff 0 <= v <= k'-1.
+VATE_HD RangeConsts dr_range_consts(uint32_t kprime) {
+    RangeConsts rc;
+    rc.a1 = 128u * ONES;
+    rc.b1 = (127u - (kprime - 1u)) * ONES;
+    rc.f = 0u;
+    rc.pad = 0u;
+    return rc;
+}
+
 // Scalar forms (boundary bytes, small L)
+VATE_HD bool check_dr(uint32_t v, uint32_t kprime) { return v < kprime; }
+
 VATE_HD bool check_at(uint32_t v, uint32_t act, uint32_t kprime, uint32_t twok) {
     if (v == twok) return false;
     uint32_t d = act + twok - v;

@@ -42,28 +42,38 @@ __device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint
         inactive_runs++;
         return;
     }
-    uint32_t b0 = block_of(G, pid0);
-    if (b0 == block_of(G, pid0 + 15u)) {
-        uint32_t act = act_of_block(bact0, b0, G.twok);
-        uint32_t words[4] = {swar_bins(w.x, act, G.twok), swar_bins(w.y, act, G.twok), swar_bins(w.z, act, G.twok),
-                             swar_bins(w.w, act, G.twok)};
-#pragma unroll
-        for (int b = 0; b < 16; b++) {
-            uint32_t bin = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, G.twok);
-            col[bin * 32u] += 1u;
-        }
+    uint32_t words[4];
+    if (G.counter == 1u) {                 // distance recorders: the value is the distance
+        words[0] = swar_dr_bins(w.x, G.k, G.twok);
+        words[1] = swar_dr_bins(w.y, G.k, G.twok);
+        words[2] = swar_dr_bins(w.z, G.k, G.twok);
+        words[3] = swar_dr_bins(w.w, G.k, G.twok);
     } else {
-        uint32_t words[4] = {w.x, w.y, w.z, w.w};
-        for (int b = 0; b < 16; b++) {
-            uint32_t v = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-            uint32_t bin = G.twok;
-            if (v < G.twok) {
-                uint32_t act = act_of_block(bact0, block_of(G, pid0 + b), G.twok);
-                uint32_t d = act + G.twok - v;
-                bin = d >= G.twok ? d - G.twok : d;
+        uint32_t b0 = block_of(G, pid0);
+        if (b0 != block_of(G, pid0 + 15u)) {
+            uint32_t raw[4] = {w.x, w.y, w.z, w.w};
+            for (int b = 0; b < 16; b++) {
+                uint32_t v = (raw[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+                uint32_t bin = G.twok;
+                if (v < G.twok) {
+                    uint32_t act = act_of_block(bact0, block_of(G, pid0 + b), G.twok);
+                    uint32_t d = act + G.twok - v;
+                    bin = d >= G.twok ? d - G.twok : d;
+                }
+                col[bin * 32u] += 1u;
             }
-            col[bin * 32u] += 1u;
+            return;
         }
+        uint32_t act = act_of_block(bact0, b0, G.twok);
+        words[0] = swar_bins(w.x, act, G.twok);
+        words[1] = swar_bins(w.y, act, G.twok);
+        words[2] = swar_bins(w.z, act, G.twok);
+        words[3] = swar_bins(w.w, act, G.twok);
+    }
+#pragma unroll
+    for (int b = 0; b < 16; b++) {
+        uint32_t bin = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, G.twok);
+        col[bin * 32u] += 1u;
     }
 }
 
@@ -92,6 +102,10 @@ __device__ __forceinline__ uint32_t count_chunk_bytes(const Geom &G, uint32_t ba
     uint32_t n = 0;
     for (int b = 0; b < 16; b++) {
         uint32_t v = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+        if (G.counter == 1u) {
+            n += check_dr(v, kprime) ? 1u : 0u;
+            continue;
+        }
         uint32_t act = act_of_block(bact0, block_of(G, pid + b), G.twok);
         n += check_at(v, act, kprime, G.twok) ? 1u : 0u;
     }
@@ -203,6 +217,10 @@ __device__ __forceinline__ uint32_t gather_host_scalar(const Geom &G, uint32_t b
     for (uint32_t i = lane; i < G.g; i += 32u) {
         uint32_t pid = vat_pid(G, aip, i);
         uint32_t v = __ldg(G.pool + pid);
+        if (G.counter == 1u) {
+            cnt += check_dr(v, kprime) ? 1u : 0u;
+            continue;
+        }
         uint32_t act = act_of_block(bact0, block_of(G, pid), G.twok);
         cnt += check_at(v, act, kprime, G.twok) ? 1u : 0u;
     }

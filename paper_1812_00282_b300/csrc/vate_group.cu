@@ -427,6 +427,10 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
     for (uint32_t m = 0; m < n_monitors; m++) {
         int rc = vate::make_geom_checked(&params[m], &g->geoms[m]);
         if (rc) { delete g; return rc; }
+        if (params[m].counter != VATE_COUNTER_AT) {
+            delete g;
+            return vate::set_error(VATE_EINVAL, "groups run asynchronous timestamps (counter 0)");
+        }
         if (m && params[m].seg_len != params[0].seg_len) {
             delete g;
             return vate::set_error(VATE_EINVAL, "all monitors of a group must use the same seg_len");

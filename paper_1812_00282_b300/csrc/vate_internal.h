@@ -30,6 +30,7 @@ int set_error(int code, const char *msg);
 
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms);
 cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, uint64_t n, cudaStream_t st, int sms);
+cudaError_t launch_dr_age(const Geom &G, cudaStream_t st, int sms);
 cudaError_t launch_preserve(const Geom &G, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1, cudaStream_t st,
                             int sms);
 size_t census_smem_bytes(uint32_t twok);

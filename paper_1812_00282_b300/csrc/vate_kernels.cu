@@ -36,11 +36,12 @@ __global__ void init_pool_kernel(uint8_t *__restrict__ pool, uint64_t P, uint32_
 // --------------------------------------------------------------------------
 // Ingest: one thread per two pairs (one 16-byte streaming load).
 // --------------------------------------------------------------------------
+// SetAT writes the ACT of the AT's block; a distance recorder is reset to 0.
 __device__ __forceinline__ void set_at(const Geom &G, uint32_t bact0, uint32_t aip, uint32_t bip) {
     uint32_t vid = bh(G, bip);
     uint32_t pid = vat_pid(G, aip, vid);
-    uint32_t act = act_of_block(bact0, block_of(G, pid), G.twok);
-    G.pool[pid] = (uint8_t)act;
+    uint32_t v = G.counter == 1u ? 0u : act_of_block(bact0, block_of(G, pid), G.twok);
+    G.pool[pid] = (uint8_t)v;
 }
 
 __global__ void __launch_bounds__(256) ingest_kernel(Geom G, uint32_t bact0, const uint32_t *__restrict__ pairs,
@@ -81,6 +82,25 @@ __global__ void __launch_bounds__(256) preserve_kernel(uint8_t *__restrict__ poo
 }
 
 // --------------------------------------------------------------------------
+// Distance recorders: one slide ages every recorder of the pool by one
+// (saturating at k, the inactive value).  16 bytes per thread.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) dr_age_kernel(uint8_t *__restrict__ pool, uint64_t P, uint32_t k) {
+    const uint64_t n16 = P >> 4;
+    uint4 *p = reinterpret_cast<uint4 *>(pool);
+    const uint32_t pat = k * ONES;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n16; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint4 w = p[i];
+        if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) continue;   // all inactive already
+        w.x = swar_dr_age(w.x, k);
+        w.y = swar_dr_age(w.y, k);
+        w.z = swar_dr_age(w.z, k);
+        w.w = swar_dr_age(w.w, k);
+        p[i] = w;
+    }
+}
+
+// --------------------------------------------------------------------------
 // Census: hist[d] = ATs at distance d (d < 2k), hist[2k] = inactive ATs.
 // Each lane keeps a private column of the block's shared histogram
 // (bin * 32 + lane: no bank conflicts, no atomics).  A chunk of 16 inactive
@@ -100,7 +120,7 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
     for (uint32_t i = threadIdx.x; i < nwarps * nbins * 32u; i += blockDim.x) sh[i] = 0;
     __syncthreads();
 
-    const uint32_t pat = G.twok * ONES;
+    const uint32_t pat = (G.counter == 1u ? G.k : G.twok) * ONES;   // 16 inactive counters
     uint32_t inactive_runs = 0;   // chunks of 16 inactive ATs
     const uint64_t n16 = G.P >> 4;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -186,7 +206,8 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
                                                                     uint32_t u2, uint32_t u3) {
     __shared__ RangeConsts tbl[128];
     __shared__ uint64_t sN0;
-    for (uint32_t a = threadIdx.x; a < G.twok; a += blockDim.x) tbl[a] = range_consts(a, kprime, G.twok);
+    for (uint32_t a = threadIdx.x; a < G.twok; a += blockDim.x)    // distance recorders: the same test for every ACT
+        tbl[a] = G.counter == 1u ? dr_range_consts(kprime) : range_consts(a, kprime, G.twok);
     if (MODE == GATHER_ESTIMATE && threadIdx.x == 0) sN0 = pool_inactive(hist, G.P, kprime);
     __syncthreads();
     const uint64_t N0 = (MODE == GATHER_ESTIMATE) ? sN0 : 0;
@@ -258,6 +279,10 @@ __global__ void __launch_bounds__(AGE_THREADS) age_counts_kernel(Geom G, uint32_
         for (uint32_t i = lane; i < G.g; i += 32u) {
             uint32_t pid = vat_pid(G, aip, i);
             uint32_t v = __ldg(G.pool + pid);
+            if (G.counter == 1u) {
+                if (v < G.k) col[v * 32u] += 1u;
+                continue;
+            }
             if (v == G.twok) continue;
             uint32_t act = act_of_block(bact0, block_of(G, pid), G.twok);
             uint32_t d = act + G.twok - v;
@@ -286,7 +311,9 @@ static int grid_for(uint64_t work_items, int threads, int max_blocks) {
 }
 
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms) {
-    return launch_pool(G, init_pool_kernel, grid_for(G.P >> 4, 256, sms * 8), 256, 0, st, G.pool, G.P, G.twok);
+    // InitAT: 2k; a distance recorder starts at k (inactive)
+    return launch_pool(G, init_pool_kernel, grid_for(G.P >> 4, 256, sms * 8), 256, 0, st, G.pool, G.P,
+                       G.counter == 1u ? G.k : G.twok);
 }
 
 cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, uint64_t n, cudaStream_t st, int sms) {
@@ -300,6 +327,10 @@ cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, 
         if (n == 0) return cudaSuccess;
     }
     return launch_pool(G, ingest_kernel, grid_for((n + 1) / 2, 256, sms * 16), 256, 0, st, G, bact0, pairs, n);
+}
+
+cudaError_t launch_dr_age(const Geom &G, cudaStream_t st, int sms) {
+    return launch_pool(G, dr_age_kernel, grid_for(G.P >> 4, 256, sms * 8), 256, 0, st, G.pool, G.P, G.k);
 }
 
 cudaError_t launch_preserve(const Geom &G, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1, cudaStream_t st,

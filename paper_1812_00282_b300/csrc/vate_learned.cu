@@ -368,6 +368,7 @@ int check_learned_handle(const vate_handle *h, HandleView *v) {
     if (int rc = handle_view(h, v)) return rc;
     if (!v->closed) return set_error(VATE_ESLICE, "the current slice has not been closed");
     if (v->G.k > 15) return set_error(VATE_EINVAL, "the learned estimator needs k <= 15 (2k + 2 <= 32 inputs)");
+    if (v->G.counter != VATE_COUNTER_AT) return set_error(VATE_EINVAL, "the learned estimator runs on asynchronous timestamps");
     return VATE_OK;
 }
 

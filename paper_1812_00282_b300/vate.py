@@ -33,7 +33,7 @@ class VateError(RuntimeError):
 
 class vate_params(C.Structure):
     _fields_ = [("log2_pool", C.c_uint32), ("k", C.c_uint32), ("g", C.c_uint32), ("seg_len", C.c_uint32),
-                ("partition", C.c_uint32), ("reserved", C.c_uint32), ("seed", C.c_uint64)]
+                ("partition", C.c_uint32), ("counter", C.c_uint32), ("seed", C.c_uint64)]
 
 
 class vate_info(C.Structure):
@@ -188,8 +188,12 @@ def _host(a, dtype, name: str, output: bool = False):
     return arr.ctypes.data, arr, arr.size
 
 
-def make_params(log2_pool: int, k: int, g: int, seg_len: int = 1, partition: int = 0, seed: int = 0) -> vate_params:
-    return vate_params(log2_pool, k, g, seg_len, partition, 0, seed & 0xFFFFFFFFFFFFFFFF)
+VATE_COUNTER_AT, VATE_COUNTER_DR = 0, 1
+
+
+def make_params(log2_pool: int, k: int, g: int, seg_len: int = 1, partition: int = 0, seed: int = 0,
+                counter: int = 0) -> vate_params:
+    return vate_params(log2_pool, k, g, seg_len, partition, counter, seed & 0xFFFFFFFFFFFFFFFF)
 
 
 # ---- the C ABI, one function per entry point --------------------------------
@@ -602,8 +606,8 @@ class Vate:
     """Owns one handle; methods forward to the functions above."""
 
     def __init__(self, log2_pool: int, k: int, g: int, seg_len: int = 1, partition: int = 0, seed: int = 0,
-                 stream=None):
-        self.params = make_params(log2_pool, k, g, seg_len, partition, seed)
+                 stream=None, counter: int = 0):
+        self.params = make_params(log2_pool, k, g, seg_len, partition, seed, counter)
         self.k, self.g, self.P = k, g, 1 << log2_pool
         self.h = vate_create(self.params, stream)
 

@@ -56,9 +56,9 @@ def test_invalid_parameters_rejected_on_host(V, bad):
     assert ei.value.code == V.VATE_EINVAL
 
 
-def test_reserved_field_must_be_zero(V):
+def test_counter_kind_must_be_known(V):
     params = V.make_params(20, 5, 1024)
-    params.reserved = 1
+    params.counter = 2
     with pytest.raises(V.VateError) as ei:
         V.vate_create(params, stream=0)
     assert ei.value.code == V.VATE_EINVAL

@@ -268,3 +268,51 @@ def test_full_size_40g_shape_sampled(V):
     k = 10
     slices = [tr.slice_pairs(s) for s in range(k + 2)]
     run_stream(V, (26, k, 4096, 32, 0, 0xC2), slices, hosts, kps=(1, k), check_every=4, check_ages=True)
+
+
+@pytest.mark.parametrize("L", [1, 32])
+def test_distance_recorders_match_oracle_and_timestamps(V, L):
+    # VDRE (distance recorders aged every slide, Sec. 1 / Sec. 5) on the same
+    # stream as VATE: the recorder pool equals the oracle's DR pool, and the
+    # active counts, censuses and estimates equal those of the timestamps.
+    tr = Traffic(SMALL, pkts_per_slice=15_000)
+    k, c, g = 4, 16, 512
+    dr = V.Vate(c, k, g, L, 0, 21, counter=V.VATE_COUNTER_DR)
+    at = V.Vate(c, k, g, L, 0, 21)
+    o = Oracle(c=c, k=k, g=g, seg_len=L, partition=0, seed=21)
+    hosts = tr.aips[:1200]
+    dh = dev_u32(hosts)
+    ids = [0, 1, 2, 3, 5, 6, 9, 10, 11, 20, 21, 22]
+    prev = None
+    for sid in ids:
+        if prev is not None:
+            for _ in range(sid - prev):
+                o.advance()
+        prev = sid
+        p = tr.slice_pairs(sid)
+        o.ingest(p)
+        for d in (dr, at):
+            d.ingest(dev_pairs(p), sid)
+            d.close_slice(sid)
+        pool = torch.empty(o.P, dtype=torch.uint8, device="cuda")
+        dr.copy_pool(pool)
+        np.testing.assert_array_equal(pool.cpu().numpy(), o.dr())
+        h_dr = torch.empty(2 * k + 1, dtype=torch.int64, device="cuda")
+        h_at = torch.empty_like(h_dr)
+        dr.census(h_dr)
+        at.census(h_at)
+        a, b = h_dr.cpu().numpy(), h_at.cpu().numpy()
+        np.testing.assert_array_equal(a[:k], b[:k])
+        assert a[k:2 * k].sum() == 0 and a[2 * k] == b[k:].sum()
+        for kp in (1, 2, k):
+            e1 = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+            e2 = torch.empty_like(e1)
+            a1 = torch.empty(len(hosts), dtype=torch.int32, device="cuda")
+            dr.estimate(dh, kp, e1)
+            at.estimate(dh, kp, e2)
+            dr.active_counts(dh, kp, a1)
+            assert torch.equal(e1, e2)
+            _, oa, _ = o.estimate(hosts, kp)
+            np.testing.assert_array_equal(a1.cpu().numpy().view(np.uint32), oa)
+    dr.close()
+    at.close()
