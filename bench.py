@@ -632,7 +632,10 @@ def run_pt(args):
     timestamps (PreserveAT on the two blocks whose ACT became 0 or k) against
     distance recorders (every recorder aged each slide), pools of 2^23..2^32
     counters, the 40 Gb/s traffic ingested between slides.  PT of a slide =
-    CUDA-event time of vate_ingest with no pairs into the next slice."""
+    CUDA-event time of vate_ingest with no pairs into the next slice.  The
+    timestamps run with both partitions: Eq. 9-10 (2k-1 blocks of a and a
+    last block of b < 2k-1) and the low-deviation one (blocks of a' or a'+1),
+    whose per-slide PT should spread less (Sec. 4.1)."""
     import torch
     import paper_1812_00282_b300 as V
     from traffic import LINK40G, DeviceTraffic, Traffic
@@ -642,11 +645,12 @@ def run_pt(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     hbm = measured_peaks().get("hbm_gbs", 6400.0)
     rows = []
+    arms = (("vate", V.VATE_COUNTER_AT, 0), ("vate_lowdev", V.VATE_COUNTER_AT, 1), ("vdre", V.VATE_COUNTER_DR, 0))
     for k in (10, 63):
         for c in range(23, 33):
             res = {"k": k, "log2_counters": c}
-            for name, counter in (("vate", V.VATE_COUNTER_AT), ("vdre", V.VATE_COUNTER_DR)):
-                h = V.Vate(c, k, 1024, 32, 0, 0xD7, counter=counter)
+            for name, counter, part in arms:
+                h = V.Vate(c, k, 1024, 32, part, 0xD7, counter=counter)
                 times = []
                 for s in range(2 * k + 4):
                     h.ingest(dt.slice_pairs(s % 40), s)
@@ -658,6 +662,7 @@ def run_pt(args):
                         times.append(ev[0].elapsed_time(ev[1]))
                 h.close()
                 res[name + "_pt_ms"] = round(statistics.mean(times), 4)
+                res[name + "_pt_std_ms"] = round(statistics.pstdev(times), 4)
                 res[name + "_pt_max_ms"] = round(max(times), 4)
             res["speedup"] = round(res["vdre_pt_ms"] / res["vate_pt_ms"], 1)
             # bytes a slide must read: the whole pool (VDRE) or the two maintained blocks (VATE)
@@ -665,8 +670,8 @@ def run_pt(args):
             res["vate_read_gbs"] = round(2 * (1 << c) / (2 * k - 1) / res["vate_pt_ms"] / 1e6, 1)
             rows.append(res)
             torch.cuda.empty_cache()
-    return {"workload": "maintenance time per slide (PT), VATE vs VDRE, 40 Gb/s traffic between slides, g = 1024",
-            "hbm_peak_gbs": hbm, "rows": rows}
+    return {"workload": "maintenance time per slide (PT), VATE (both partitions) vs VDRE, 40 Gb/s traffic "
+                        "between slides, g = 1024", "hbm_peak_gbs": hbm, "rows": rows}
 
 
 def main():

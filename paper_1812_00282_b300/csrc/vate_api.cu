@@ -1,12 +1,14 @@
 // vate_api.cu -- C ABI of the VATE library: argument checks, the slice state
 // machine of Algorithm 4 on the host, device buffers, kernel launches.
 #include <atomic>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
 
 #include "vate.h"
+#include "vate_checkpoint.h"
 #include "vate_internal.h"
 
 using vate::Geom;
@@ -453,6 +455,124 @@ int vate_estimate_host(vate_handle *h, const uint32_t *h_aips, uint64_t n, uint3
             CU(cudaMemcpyAsync(h_flags + off, h->d_stage_flags[b], m, cudaMemcpyDeviceToHost, st), "D2H");
         CU(cudaEventRecord(h->ev_free[b], st), "record");
     }
+    return VATE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoint and resume (include/vate_checkpoint.h)
+// ---------------------------------------------------------------------------
+namespace {
+
+static_assert(sizeof(vate_checkpoint_header) % 8 == 0, "the image is hashed 8 bytes at a time");
+
+// FNV-1a (Fowler/Noll/Vo), 64-bit offset basis and prime, one 8-byte word per
+// round.  `skip` is the byte offset of a word read as zero (the checksum).
+struct Fnv {
+    uint64_t h = 0xcbf29ce484222325ull;
+    void words(const uint8_t *p, uint64_t n_bytes, uint64_t base, uint64_t skip) {
+        for (uint64_t o = 0; o < n_bytes; o += 8) {
+            uint64_t w;
+            std::memcpy(&w, p + o, 8);
+            if (base + o == skip) w = 0;
+            h = (h ^ w) * 0x100000001b3ull;
+        }
+    }
+};
+
+uint64_t image_bytes(uint32_t twok, uint64_t P) {
+    return sizeof(vate_checkpoint_header) + (uint64_t)(twok + 1) * sizeof(uint64_t) + P;
+}
+
+constexpr uint64_t CHECKSUM_AT = offsetof(vate_checkpoint_header, checksum);
+
+}  // namespace
+
+extern "C" {
+
+int vate_checkpoint_size(const vate_handle *h, uint64_t *bytes) {
+    if (int rc = check_handle(h)) return rc;
+    if (!bytes) return fail(VATE_EINVAL, "bytes is NULL");
+    *bytes = image_bytes(h->G.twok, h->G.P);
+    return VATE_OK;
+}
+
+int vate_checkpoint(vate_handle *h, void *h_buf, uint64_t bytes, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!h_buf) return fail(VATE_EINVAL, "h_buf is NULL");
+    const uint64_t need = image_bytes(h->G.twok, h->G.P);
+    if (bytes < need) return fail(VATE_EINVAL, "checkpoint buffer holds %llu bytes, %llu needed",
+                                  (unsigned long long)bytes, (unsigned long long)need);
+    uint8_t *img = static_cast<uint8_t *>(h_buf);
+    vate_checkpoint_header hd;
+    std::memset(&hd, 0, sizeof hd);
+    hd.magic = VATE_CHECKPOINT_MAGIC;
+    hd.version = VATE_CHECKPOINT_VERSION;
+    hd.header_bytes = (uint32_t)sizeof hd;
+    hd.params = h->prm;
+    hd.slice = h->slice;
+    hd.bact0 = h->bact0;
+    hd.closed = h->closed ? 1u : 0u;
+    hd.hist_bytes = (uint64_t)(h->G.twok + 1) * sizeof(uint64_t);
+    hd.pool_bytes = h->G.P;
+    uint8_t *hist = img + sizeof hd, *pool = hist + hd.hist_bytes;
+    cudaStream_t st = (cudaStream_t)stream;
+    CU(cudaMemcpyAsync(hist, h->d_hist, hd.hist_bytes, cudaMemcpyDeviceToHost, st), "census D2H");
+    CU(cudaMemcpyAsync(pool, h->G.pool, hd.pool_bytes, cudaMemcpyDeviceToHost, st), "pool D2H");
+    CU(cudaStreamSynchronize(st), "checkpoint");
+    std::memcpy(img, &hd, sizeof hd);
+    Fnv f;
+    f.words(img, need, 0, CHECKSUM_AT);
+    hd.checksum = f.h;
+    std::memcpy(img, &hd, sizeof hd);
+    return VATE_OK;
+}
+
+int vate_restore(const void *h_buf, uint64_t bytes, void *stream, vate_handle **out) {
+    if (!out) return fail(VATE_EINVAL, "out is NULL");
+    if (!h_buf) return fail(VATE_EINVAL, "h_buf is NULL");
+    if (bytes < sizeof(vate_checkpoint_header))
+        return fail(VATE_EINVAL, "checkpoint image of %llu bytes is shorter than its header", (unsigned long long)bytes);
+    const uint8_t *img = static_cast<const uint8_t *>(h_buf);
+    vate_checkpoint_header hd;
+    std::memcpy(&hd, img, sizeof hd);
+    if (hd.magic != VATE_CHECKPOINT_MAGIC) return fail(VATE_EINVAL, "not a VATE checkpoint (bad magic)");
+    if (hd.version != VATE_CHECKPOINT_VERSION || hd.header_bytes != sizeof hd)
+        return fail(VATE_EINVAL, "checkpoint version %u / header of %u bytes is not supported", hd.version,
+                    hd.header_bytes);
+    Geom G;
+    if (int rc = make_geom(&hd.params, &G)) return rc;
+    if (hd.pool_bytes != G.P || hd.hist_bytes != (uint64_t)(G.twok + 1) * sizeof(uint64_t))
+        return fail(VATE_EINVAL, "checkpoint sizes do not match its parameters");
+    const uint64_t need = image_bytes(G.twok, G.P);
+    if (bytes < need)
+        return fail(VATE_EINVAL, "checkpoint image truncated: %llu of %llu bytes", (unsigned long long)bytes,
+                    (unsigned long long)need);
+    if (hd.slice < -1 || hd.bact0 >= G.twok || hd.closed > 1u || (hd.slice < 0 && (hd.bact0 != 0 || hd.closed)))
+        return fail(VATE_EINVAL, "checkpoint slice state is inconsistent");
+    Fnv f;
+    f.words(img, need, 0, CHECKSUM_AT);
+    if (f.h != hd.checksum) return fail(VATE_EINVAL, "checkpoint checksum mismatch");
+    // AT values beyond the counter's range would index past the census bins
+    const uint8_t *hist = img + sizeof hd, *pool = hist + hd.hist_bytes;
+    const uint8_t vmax = (uint8_t)(G.counter == VATE_COUNTER_DR ? G.k : G.twok);
+    uint8_t worst = 0;
+    for (uint64_t i = 0; i < G.P; i++) worst = pool[i] > worst ? pool[i] : worst;
+    if (worst > vmax) return fail(VATE_EINVAL, "checkpoint pool holds the value %u, above %u", worst, vmax);
+    vate_handle *h = nullptr;
+    if (int rc = vate_create(&hd.params, stream, &h)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h->G.pool, pool, G.P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_hist, hist, hd.hist_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        vate_destroy(h);
+        return cuda_fail(e, "checkpoint H2D");
+    }
+    h->slice = hd.slice;
+    h->bact0 = hd.bact0;
+    h->closed = hd.closed != 0;
+    *out = h;
     return VATE_OK;
 }
 

@@ -127,6 +127,9 @@ def _load() -> C.CDLL:
         "vate_server_get_stats": (i, [vp, P(vate_server_stats), i]),
         "vate_probe_sector_read": (i, [vp, u64, u64, vp, vp]),
         "vate_probe_byte_write": (i, [vp, u64, u64, vp]),
+        "vate_checkpoint_size": (i, [vp, P(u64)]),
+        "vate_checkpoint": (i, [vp, vp, u64, vp]),
+        "vate_restore": (i, [vp, u64, vp, P(vp)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -602,6 +605,40 @@ def vate_server_get_stats(s, reset: bool = False) -> vate_server_stats:
     return st
 
 
+VATE_CHECKPOINT_MAGIC, VATE_CHECKPOINT_VERSION = 0x31544B4345544156, 1
+
+
+class vate_checkpoint_header(C.Structure):
+    _fields_ = [("magic", C.c_uint64), ("version", C.c_uint32), ("header_bytes", C.c_uint32),
+                ("params", vate_params), ("slice", C.c_int64), ("bact0", C.c_uint32), ("closed", C.c_uint32),
+                ("hist_bytes", C.c_uint64), ("pool_bytes", C.c_uint64), ("checksum", C.c_uint64)]
+
+
+def vate_checkpoint_size(h) -> int:
+    n = C.c_uint64()
+    _check(_lib.vate_checkpoint_size(h, C.byref(n)))
+    return n.value
+
+
+def vate_checkpoint(h, buf=None, stream=None) -> np.ndarray:
+    """The handle's state as a uint8 host array (written into `buf` if given)."""
+    n = vate_checkpoint_size(h)
+    if buf is None:
+        buf = np.empty(n, np.uint8)
+    ptr, keep, cnt = _host(buf, np.uint8, "buf", output=True)
+    _check(_lib.vate_checkpoint(h, ptr, cnt, _stream(stream)))
+    return buf
+
+
+def vate_restore(buf, stream=None) -> C.c_void_p:
+    ptr, keep, cnt = _host(buf, np.uint8, "buf")
+    h = C.c_void_p()
+    _check(_lib.vate_restore(ptr, cnt, _stream(stream), C.byref(h)))
+    hd = vate_checkpoint_header.from_buffer_copy(C.string_at(ptr, C.sizeof(vate_checkpoint_header)))
+    _k_of[h.value] = int(hd.params.k)
+    return h
+
+
 class Vate:
     """Owns one handle; methods forward to the functions above."""
 
@@ -648,3 +685,24 @@ class Vate:
 
     def info(self) -> vate_info:
         return vate_get_info(self.h)
+
+    def checkpoint(self, buf=None, stream=None) -> np.ndarray:
+        return vate_checkpoint(self.h, buf, stream)
+
+    @classmethod
+    def restore(cls, buf, stream=None) -> "Vate":
+        obj = cls.__new__(cls)
+        obj.h = None
+        obj.h = vate_restore(buf, stream)          # validates the image first
+        ptr, keep, _ = _host(buf, np.uint8, "buf")
+        hd = vate_checkpoint_header.from_buffer_copy(C.string_at(ptr, C.sizeof(vate_checkpoint_header)))
+        obj.params = hd.params
+        obj.k, obj.g, obj.P = hd.params.k, hd.params.g, 1 << hd.params.log2_pool
+        return obj
+
+    def save(self, path: str, stream=None) -> None:
+        self.checkpoint(stream=stream).tofile(path)
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Vate":
+        return cls.restore(np.fromfile(path, dtype=np.uint8), stream)

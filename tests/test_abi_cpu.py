@@ -125,3 +125,77 @@ def test_block_division_exact_near_2_32(V):
             if pid >= P:
                 continue
             assert V.vate_host_block(params, pid) == ref(pid), (k, part, pid)
+
+
+# ---- checkpoint images: every check runs on the host before any device call --
+def _fnv1a_words(b: bytes) -> int:
+    """FNV-1a, 64-bit (Fowler/Noll/Vo published offset basis and prime), over
+    little-endian 8-byte words."""
+    h = 0xcbf29ce484222325
+    for (w,) in np.frombuffer(b, dtype="<u8").reshape(-1, 1):
+        h = ((h ^ int(w)) * 0x100000001b3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _image(V, c=12, k=3, slice_=4, bact0=2, closed=1, pool_value=None, counter=0, fix_checksum=True):
+    hd = V.vate_checkpoint_header()
+    hd.magic, hd.version, hd.header_bytes = V.VATE_CHECKPOINT_MAGIC, V.VATE_CHECKPOINT_VERSION, 88
+    hd.params = V.make_params(c, k, 64, 1, 0, 9, counter)
+    hd.slice, hd.bact0, hd.closed = slice_, bact0, closed
+    hd.hist_bytes, hd.pool_bytes = (2 * k + 1) * 8, 1 << c
+    pool = np.full(1 << c, 2 * k if pool_value is None else pool_value, np.uint8)
+    pool[:7] = [0, 1, 2, 3, 4, 5, 6][: 7] if pool_value is None else pool_value
+    body = bytes(hd) + np.zeros(2 * k + 1, np.uint64).tobytes() + pool.tobytes()
+    if fix_checksum:
+        hd.checksum = _fnv1a_words(body)
+    return np.frombuffer(bytes(hd) + body[88:], np.uint8).copy()
+
+
+def test_checkpoint_header_layout(V):
+    import ctypes as C
+    assert C.sizeof(V.vate_checkpoint_header) == 88
+    assert V.vate_checkpoint_header.checksum.offset == 80
+    assert V.VATE_CHECKPOINT_MAGIC.to_bytes(8, "little") == b"VATECKT1"
+
+
+def test_valid_checkpoint_passes_every_host_check(V):
+    # with no device the image is accepted up to the handle's creation
+    if torch.cuda.is_available():
+        pytest.skip("checks the no-GPU path")
+    with pytest.raises(V.VateError) as ei:
+        V.vate_restore(_image(V), stream=0)
+    assert ei.value.code == V.VATE_ECUDA
+
+
+@pytest.mark.parametrize("damage", ["short", "truncated", "magic", "version", "checksum", "value", "dr_value",
+                                    "bact0", "closed", "before_first", "sizes", "params"])
+def test_damaged_checkpoint_rejected_on_host(V, damage):
+    img = _image(V)
+    if damage == "short":
+        img = img[:40]
+    elif damage == "truncated":
+        img = img[:-8]
+    elif damage == "magic":
+        img[0] ^= 0xFF
+    elif damage == "version":
+        img[8] = 7
+    elif damage == "checksum":
+        img[200] ^= 1
+    elif damage == "value":
+        img = _image(V, pool_value=7)                     # 2k + 1
+    elif damage == "dr_value":
+        img = _image(V, pool_value=4, counter=1)          # k + 1
+    elif damage == "bact0":
+        img = _image(V, bact0=6)
+    elif damage == "closed":
+        img = _image(V, closed=2)
+    elif damage == "before_first":
+        img = _image(V, slice_=-1, bact0=1, closed=0)
+    elif damage == "sizes":
+        img = _image(V)
+        img[64] = 9                                       # hist_bytes
+    elif damage == "params":
+        img = _image(V, k=0)
+    with pytest.raises(V.VateError) as ei:
+        V.vate_restore(img, stream=0)
+    assert ei.value.code == V.VATE_EINVAL, V.vate_last_error()
