@@ -85,10 +85,13 @@ typedef struct {
  *              in the maintenance work per slide.
  *   seed       keys the hash functions H and BH.
  * The hash functions (Sec. 4.1 leaves them open):
- *   mix(x)   = SplitMix64 output function (Steele, Lea & Flood 2014)
- *   BH(bip)  = ((mix(mix(seed+2) ^ bip) >> 32) * g) >> 32
- *   seg      = mix(mix(seed+1) ^ (aip << 32) ^ floor(i/L)) >> (64 - (c - log2 L))
- *   H(aip,i) = seg * L + (i mod L)                                          */
+ *   mix(x)    = SplitMix64 output function (Steele, Lea & Flood 2014)
+ *   fmix32(x) = MurmurHash3's 32-bit finalizer (Appleby)
+ *   BH(bip)   = ((mix(mix(seed+2) ^ bip) >> 32) * g) >> 32
+ *   K         = mix(mix(seed+1) ^ (aip << 32))            (one key per host)
+ *   seg       = (fmix32(lo32(K) ^ j * 0x9E3779B9) ^ hi32(K)) >> (32 - (c - log2 L)),
+ *               j = floor(i/L), arithmetic on 32-bit words
+ *   H(aip,i)  = seg * L + (i mod L)                                          */
 typedef struct {
     uint32_t log2_pool;
     uint32_t k;

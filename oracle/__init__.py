@@ -53,6 +53,7 @@ def _load():
         vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
         sig = {
             "vo_mix64": (u64, [u64]),
+            "vo_fmix32": (u32, [u32]),
             "vo_create": (vp, [u32, u32, u32, u32, u32, u64]),
             "vo_destroy": (None, [vp]),
             "vo_bh": (u32, [vp, u32]),
@@ -93,6 +94,10 @@ def _load():
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+def fmix32(x: int) -> int:
+    return int(_load().vo_fmix32(x & 0xFFFFFFFF))
 
 
 def mix64(x: int) -> int:

@@ -34,9 +34,11 @@
  *       differ only when Value == ACT at a maintenance point, a state no run
  *       from InitAT can reach).
  *   R7  H and BH are "random hash functions" in the paper; this build fixes
- *       them to the SplitMix64 output function (Steele, Lea & Flood 2014)
- *       with Lemire's multiply-shift range reduction, and optionally places
- *       the g virtual ATs of a host in segments of L consecutive pool ATs.
+ *       them to published mixers: BH is the SplitMix64 output function
+ *       (Steele, Lea & Flood 2014) with Lemire's multiply-shift range
+ *       reduction; H places the g virtual ATs of a host in segments of L
+ *       consecutive pool ATs, segment j at the top bits of MurmurHash3's
+ *       32-bit finalizer (Appleby) of the host's SplitMix64 key mixed with j.
  *   R10 saturation: V0 = g - A == 0 is replaced by 1 (flag SAT); a pool
  *       census with N0 == 0 is replaced by 1 (flag POOLFULL).
  *
@@ -59,6 +61,18 @@ uint64_t vo_mix64(uint64_t x)
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
+}
+
+/* MurmurHash3's 32-bit finalizer (fmix32, Appleby): xor-shift-multiply
+ * twice and a final xor-shift; a bijection on 32-bit words. */
+uint32_t vo_fmix32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x85EBCA6BU;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35U;
+    x ^= x >> 16;
+    return x;
 }
 
 typedef struct {
@@ -91,7 +105,9 @@ uint32_t vo_bh(const vo_state *s, uint32_t bip)
 
 /* H(aip, i) in [0, P): the i-th virtual AT of host aip.  With segment
  * length L, VAT i lives at offset (i mod L) inside pool segment
- * seg(aip, floor(i / L)); seg is the top (c - log2 L) bits of the mix. */
+ * seg(aip, j), j = floor(i / L).  The host's key is the 64-bit mix
+ * K = mix64(key_h ^ aip << 32); seg(aip, j) is the top (c - log2 L) bits of
+ * fmix32(low32(K) ^ j * 0x9E3779B9) ^ high32(K). */
 uint64_t vo_h(const vo_state *s, uint32_t aip, uint32_t i)
 {
     uint32_t log2L = 0;
@@ -99,8 +115,9 @@ uint64_t vo_h(const vo_state *s, uint32_t aip, uint32_t i)
     uint32_t j = i / s->L;
     uint32_t o = i % s->L;
     uint32_t segbits = s->c - log2L;
-    uint64_t m = vo_mix64(s->key_h ^ (((uint64_t)aip) << 32) ^ (uint64_t)j);
-    uint64_t seg = m >> (64 - segbits);
+    uint64_t K = vo_mix64(s->key_h ^ (((uint64_t)aip) << 32));
+    uint32_t x = vo_fmix32((uint32_t)K ^ (uint32_t)(j * 0x9E3779B9U)) ^ (uint32_t)(K >> 32);
+    uint64_t seg = (uint64_t)x >> (32 - segbits);
     return seg * (uint64_t)s->L + (uint64_t)o;
 }
 

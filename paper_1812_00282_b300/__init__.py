@@ -11,9 +11,14 @@ import importlib
 _BINDING = "paper_1812_00282_b300.vate"
 
 
+_SUBMODULES = ("build", "vate", "learned", "serving")
+
+
 def __getattr__(name):
     if name.startswith("__"):
         raise AttributeError(name)
+    if name in _SUBMODULES:               # `from paper_1812_00282_b300 import build` before the library exists
+        return importlib.import_module(__name__ + "." + name)
     mod = importlib.import_module(_BINDING)
     try:
         return getattr(mod, name)

@@ -65,16 +65,35 @@ VATE_HD uint32_t bh(const Geom &G, uint32_t bip) {
     return (uint32_t)(((m >> 32) * (uint64_t)G.g) >> 32);
 }
 
-// first pool position of segment j of host aip: seg(aip, j) * L
-VATE_HD uint32_t seg_base(const Geom &G, uint32_t aip, uint32_t j) {
-    uint64_t m = mix64(G.key_h ^ ((uint64_t)aip << 32) ^ (uint64_t)j);
-    return (uint32_t)(m >> (64 - G.segbits)) << G.log2L;
+// MurmurHash3's 32-bit finalizer (Appleby), a bijection on 32-bit words
+VATE_HD uint32_t fmix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+
+// the 64-bit key of host aip from which all its segments are drawn
+VATE_HD uint64_t host_key(const Geom &G, uint32_t aip) { return mix64(G.key_h ^ ((uint64_t)aip << 32)); }
+
+// first pool position of segment j of the host with key hk: seg * L, seg the
+// top c - log2 L bits of fmix32(low32(hk) ^ j * 0x9E3779B9) ^ high32(hk)
+VATE_HD uint32_t seg_base_k(const Geom &G, uint64_t hk, uint32_t j) {
+    uint32_t x = fmix32((uint32_t)hk ^ (j * 0x9E3779B9u)) ^ (uint32_t)(hk >> 32);
+    return (x >> (32u - G.segbits)) << G.log2L;
+}
+
+VATE_HD uint32_t seg_base(const Geom &G, uint32_t aip, uint32_t j) { return seg_base_k(G, host_key(G, aip), j); }
+
+// pid = H(aip, i), for the host with key hk = host_key(G, aip)
+VATE_HD uint32_t vat_pid_k(const Geom &G, uint64_t hk, uint32_t i) {
+    return seg_base_k(G, hk, i >> G.log2L) + (i & (G.L - 1));
 }
 
 // pid = H(aip, i)
-VATE_HD uint32_t vat_pid(const Geom &G, uint32_t aip, uint32_t i) {
-    return seg_base(G, aip, i >> G.log2L) + (i & (G.L - 1));
-}
+VATE_HD uint32_t vat_pid(const Geom &G, uint32_t aip, uint32_t i) { return vat_pid_k(G, host_key(G, aip), i); }
 
 // block index of pool position pid
 VATE_HD uint32_t block_of(const Geom &G, uint32_t pid) {

@@ -131,6 +131,7 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, uint32_t bact
     const uint32_t nseg = G.g >> G.log2L;              // segments per host
     const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
     uint32_t cnt = 0;
+    const uint64_t hk = host_key(G, aip);
     for (uint32_t r0 = 0; r0 < nseg; r0 += 32u * RB) {
         // hash: one segment per lane and round; ACT and "straddles a block
         // boundary" packed as act | flag << 8
@@ -141,7 +142,7 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, uint32_t bact
             base[rb] = 0;
             actf[rb] = 0;
             if (FULL || s < nseg) {
-                base[rb] = seg_base(G, aip, s);
+                base[rb] = seg_base_k(G, hk, s);
                 uint32_t b0 = block_of(G, base[rb]);
                 bool straddle;
                 if (G.partition == 0)       // offset inside a block of size a (the last block may be smaller:
@@ -213,9 +214,10 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, uint32_t bact
 __device__ __forceinline__ uint32_t gather_host_scalar(const Geom &G, uint32_t bact0, uint32_t kprime, uint32_t aip,
                                                        uint32_t lane) {
     uint32_t cnt = 0;
+    const uint64_t hk = host_key(G, aip);
 #pragma unroll 4
     for (uint32_t i = lane; i < G.g; i += 32u) {
-        uint32_t pid = vat_pid(G, aip, i);
+        uint32_t pid = vat_pid_k(G, hk, i);
         uint32_t v = __ldg(G.pool + pid);
         if (G.counter == 1u) {
             cnt += check_dr(v, kprime) ? 1u : 0u;

@@ -275,9 +275,9 @@ __global__ void __launch_bounds__(AGE_THREADS) age_counts_kernel(Geom G, uint32_
     for (uint64_t h = warp0; h < n; h += nwarps) {
         for (uint32_t d = 0; d < G.k; d++) col[d * 32u] = 0;
         __syncwarp();
-        const uint32_t aip = aips[h];
+        const uint64_t hk = host_key(G, aips[h]);
         for (uint32_t i = lane; i < G.g; i += 32u) {
-            uint32_t pid = vat_pid(G, aip, i);
+            uint32_t pid = vat_pid_k(G, hk, i);
             uint32_t v = __ldg(G.pool + pid);
             if (G.counter == 1u) {
                 if (v < G.k) col[v * 32u] += 1u;

@@ -42,12 +42,13 @@ __host__ __device__ inline Layout layout(uint32_t n_in) {
 // (col[d * 32], d < k); 16-byte chunks when L >= 16, one byte per VAT otherwise.
 __device__ __forceinline__ void host_age_columns(const Geom &G, uint32_t bact0, uint32_t aip, uint32_t lane,
                                                  uint32_t *col) {
+    const uint64_t hk = host_key(G, aip);
     if (G.L >= 16) {
         const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
         const uint32_t nchunks = G.g >> 4;
         for (uint32_t c = lane; c < nchunks; c += 32u) {
             const uint32_t i = c << 4;                       // first VAT of the chunk
-            const uint32_t pid = seg_base(G, aip, i >> G.log2L) + (i & (G.L - 1u));
+            const uint32_t pid = vat_pid_k(G, hk, i);
             const uint4 w = __ldg(pool16 + (pid >> 4));
             const uint32_t b0 = block_of(G, pid);
             uint32_t words[4] = {w.x, w.y, w.z, w.w};
@@ -72,7 +73,7 @@ __device__ __forceinline__ void host_age_columns(const Geom &G, uint32_t bact0, 
         }
     } else {
         for (uint32_t i = lane; i < G.g; i += 32u) {
-            uint32_t pid = vat_pid(G, aip, i);
+            uint32_t pid = vat_pid_k(G, hk, i);
             uint32_t v = __ldg(G.pool + pid);
             if (v >= G.twok) continue;
             uint32_t d = act_of_block(bact0, block_of(G, pid), G.twok) + G.twok - v;

@@ -87,7 +87,9 @@ def test_host_mapping_matches_oracle(V, c, k, g, L, part, seed):
         for _ in range(200):
             aip, i = int(rng.integers(0, 2**32)), int(rng.integers(0, g))
             j, off = i // L, i % L
-            seg = oracle.mix64(key_h ^ (aip << 32) ^ j) >> (64 - (c - int(np.log2(L))))
+            K = oracle.mix64(key_h ^ (aip << 32))
+            x = oracle.fmix32((K & 0xFFFFFFFF) ^ ((j * 0x9E3779B9) & 0xFFFFFFFF)) ^ (K >> 32)
+            seg = x >> (32 - (c - int(np.log2(L))))
             assert V.vate_host_h(params, aip, i) == seg * L + off
             bip = int(rng.integers(0, 2**32))
             assert V.vate_host_bh(params, bip) == ((oracle.mix64(key_bh ^ bip) >> 32) * g) >> 32

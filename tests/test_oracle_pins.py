@@ -19,7 +19,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 # --------------------------------------------------------------------------
-# Hash functions (reading: SplitMix64 output function + Lemire reduction)
+# Hash functions (reading: SplitMix64 output function + Lemire reduction for BH;
+# a per-host SplitMix64 key and MurmurHash3's finalizer per segment for H)
 # --------------------------------------------------------------------------
 
 def test_mix64_matches_published_splitmix64_sequence():
@@ -30,6 +31,36 @@ def test_mix64_matches_published_splitmix64_sequence():
     assert oracle.mix64(0) == 0xE220A8397B1DCDAF
     assert oracle.mix64(gamma) == 0x6E789E6AA1B965F4
     assert oracle.mix64((2 * gamma) & (2**64 - 1)) == 0x06C45D188009454F
+
+
+def test_fmix32_is_murmurhash3_of_the_empty_input():
+    # MurmurHash3_x86_32 of a zero-length key with seed s is the finalizer
+    # applied to s (no blocks, no tail, length 0 xored in), so the finalizer is
+    # pinned by an independent implementation of the whole hash
+    # (scikit-learn's) and by the published vector for seed 1.
+    from sklearn.utils import murmurhash3_32
+    assert oracle.fmix32(1) == 0x514E28B7
+    rng = np.random.default_rng(3)
+    for s in [0, 1, 2, 0xFFFFFFFF, 0x9E3779B9] + [int(x) for x in rng.integers(0, 2**32, 200)]:
+        assert oracle.fmix32(s) == murmurhash3_32(b"", seed=s, positive=True)
+
+
+@pytest.mark.parametrize("c,L", [(18, 1), (18, 32), (32, 1), (26, 32), (12, 64)])
+def test_h_is_the_documented_composition(c, L):
+    # H(aip, i) = L * top_{c - log2 L}(fmix32(lo32(K) ^ j * 0x9E3779B9) ^ hi32(K)) + i mod L,
+    # K = mix64(mix64(seed + 1) ^ aip << 32), j = i div L; both mixers pinned above
+    from sklearn.utils import murmurhash3_32
+    seed = 0xC2
+    o = Oracle(c=c, k=3, g=256, seg_len=L, seed=seed)
+    segbits = c - (L.bit_length() - 1)
+    key_h = oracle.mix64(seed + 1)
+    for aip in (0, 1, 0xDEADBEEF, 0xFFFFFFFF, 123456):
+        K = oracle.mix64(key_h ^ (aip << 32))
+        for i in (0, 1, 31, 32, 33, 255):
+            j = i // L
+            x = murmurhash3_32(b"", seed=(K & 0xFFFFFFFF) ^ ((j * 0x9E3779B9) & 0xFFFFFFFF), positive=True)
+            x ^= K >> 32
+            assert o.h(aip, i) == L * (x >> (32 - segbits)) + i % L
 
 
 def test_bh_range_and_uniformity():
@@ -418,9 +449,12 @@ def test_exact_counts_brute_force():
 @pytest.mark.slow
 def test_error_falls_with_pool_size_and_vector_length():
     # Sec. 5: with g fixed, a larger pool brings the estimates closer to the
-    # truth; with the pool fixed, a larger g lets the high-cardinality hosts be
-    # estimated (a small g saturates on them), at the price of more sharing
-    # noise on the small hosts.
+    # truth; with the pool fixed, a g too small for the high-cardinality hosts
+    # (n near or above g ln g, the saturation point of Eq. 1) estimates them
+    # worse than any larger g.  Between two g well above that point the
+    # ordering is not fixed: a larger g also takes in more sharing noise from
+    # the pool, and on these hosts (n <= 900) g = 512 and g = 2048 are
+    # statistically tied.
     from traffic import SMALL, Traffic
     tr = Traffic(SMALL, pkts_per_slice=50_000)
     slices = [tr.slice_pairs(s) for s in range(8)]
@@ -443,4 +477,5 @@ def test_error_falls_with_pool_size_and_vector_length():
     top = np.zeros_like(small)
     top[np.argsort(exact)[-16:]] = True
     by_g = [mre(21, g, top) for g in (128, 512, 2048)]
-    assert by_g[0] > by_g[1] > by_g[2], by_g
+    assert exact[top].max() > 128 * math.log(128)           # the largest top host saturates g = 128
+    assert by_g[0] > by_g[1] and by_g[0] > by_g[2], by_g
