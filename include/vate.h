@@ -178,7 +178,13 @@ int vate_age_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint16_t
  * d_hist[d] for distances 0 <= d < 2k, d_hist[2k] = inactive ATs. */
 int vate_census(vate_handle *h, uint64_t *d_hist, void *stream);
 
-/* Copy the AT pool (P bytes) to d_dst, or overwrite it from d_src. */
+/* Copy the AT pool (P bytes, device, any alignment) to d_dst, or overwrite
+ * it from d_src, in the paper's form: byte pid holds the AT value of pool
+ * position pid (an ACT of its block, Sec. 3, or 2k when inactive; a distance
+ * recorder's value for VATE_COUNTER_DR).  Inside the library a timestamp pool
+ * is kept in the frame of block 0 -- value minus block index, mod 2k -- so
+ * that every AT is read with ACT = BACT^0; these calls convert.  Values above
+ * the counter's range in d_src are loaded as inactive. */
 int vate_copy_pool(vate_handle *h, uint8_t *d_dst, void *stream);
 int vate_load_pool(vate_handle *h, const uint8_t *d_src, void *stream);
 

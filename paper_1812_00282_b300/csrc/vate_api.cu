@@ -160,7 +160,7 @@ int advance_to(vate_handle *h, int64_t slice, cudaStream_t st) {
             uint64_t s0, e0, s1, e1;
             vate::block_range_of(G, i0, &s0, &e0);
             vate::block_range_of(G, i1, &s1, &e1);
-            e = vate::launch_preserve(G, s0, e0, s1, e1, st, h->sms);
+            e = vate::launch_preserve(G, h->bact0, s0, e0, s1, e1, st, h->sms);
         }
         if (e != cudaSuccess) return cuda_fail(e, "maintenance launch");
     }
@@ -238,6 +238,7 @@ int vate_create(const vate_params *params, void *stream, vate_handle **out) {
     if (!h) return fail(VATE_ENOMEM, "host allocation failed");
     h->prm = *params;
     h->G = G;
+    h->G.frame0 = G.counter == VATE_COUNTER_AT ? 1u : 0u;    // timestamps kept in the frame of block 0
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) {
@@ -398,14 +399,17 @@ int vate_census(vate_handle *h, uint64_t *d_hist, void *stream) {
 int vate_copy_pool(vate_handle *h, uint8_t *d_dst, void *stream) {
     if (int rc = check_handle(h)) return rc;
     if (!d_dst) return fail(VATE_EINVAL, "d_dst is NULL");
-    CU(cudaMemcpyAsync(d_dst, h->G.pool, h->G.P, cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "pool copy");
+    cudaStream_t st = (cudaStream_t)stream;
+    CU(cudaMemcpyAsync(d_dst, h->G.pool, h->G.P, cudaMemcpyDeviceToDevice, st), "pool copy");
+    if (h->G.frame0) CU(vate::launch_frame_convert(h->G, d_dst, d_dst, 0, h->G.P, true, st, h->sms), "pool convert");
     return VATE_OK;
 }
 
 int vate_load_pool(vate_handle *h, const uint8_t *d_src, void *stream) {
     if (int rc = check_handle(h)) return rc;
     if (!d_src) return fail(VATE_EINVAL, "d_src is NULL");
-    CU(cudaMemcpyAsync(h->G.pool, d_src, h->G.P, cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "pool load");
+    cudaStream_t st = (cudaStream_t)stream;
+    CU(vate::launch_frame_convert(h->G, d_src, h->G.pool, 0, h->G.P, false, st, h->sms), "pool load");
     return VATE_OK;
 }
 
@@ -519,7 +523,20 @@ int vate_checkpoint(vate_handle *h, void *h_buf, uint64_t bytes, void *stream) {
     uint8_t *hist = img + sizeof hd, *pool = hist + hd.hist_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     CU(cudaMemcpyAsync(hist, h->d_hist, hd.hist_bytes, cudaMemcpyDeviceToHost, st), "census D2H");
-    CU(cudaMemcpyAsync(pool, h->G.pool, hd.pool_bytes, cudaMemcpyDeviceToHost, st), "pool D2H");
+    if (!h->G.frame0) {
+        CU(cudaMemcpyAsync(pool, h->G.pool, hd.pool_bytes, cudaMemcpyDeviceToHost, st), "pool D2H");
+    } else {                   // the image holds the paper's form: convert piece by piece through a staging buffer
+        if (int rc = ensure_staging(h)) return rc;
+        const uint64_t piece = STAGE_RECORDS * sizeof(vate_pair);
+        uint8_t *stage = static_cast<uint8_t *>(h->d_stage[0]);
+        CU(cudaStreamWaitEvent(st, h->ev_free[0], 0), "wait");
+        for (uint64_t off = 0; off < hd.pool_bytes; off += piece) {
+            const uint64_t n = hd.pool_bytes - off < piece ? hd.pool_bytes - off : piece;
+            CU(vate::launch_frame_convert(h->G, h->G.pool + off, stage, off, n, true, st, h->sms), "pool convert");
+            CU(cudaMemcpyAsync(pool + off, stage, n, cudaMemcpyDeviceToHost, st), "pool D2H");
+            CU(cudaStreamSynchronize(st), "checkpoint");
+        }
+    }
     CU(cudaStreamSynchronize(st), "checkpoint");
     std::memcpy(img, &hd, sizeof hd);
     Fnv f;
@@ -564,6 +581,8 @@ int vate_restore(const void *h_buf, uint64_t bytes, void *stream, vate_handle **
     if (int rc = vate_create(&hd.params, stream, &h)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(h->G.pool, pool, G.P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && h->G.frame0)          // the image holds the paper's form
+        e = vate::launch_frame_convert(h->G, h->G.pool, h->G.pool, 0, G.P, false, st, h->sms);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_hist, hist, hd.hist_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
         vate_destroy(h);

@@ -11,6 +11,15 @@
 //                   multiply-high by ceil(2^64 / d) (Lemire, Kaser & Kurz 2019,
 //                   exact for 32-bit numerators).
 //   act             ACT of block i: (BACT^0 + i) mod 2k (Eq. 8).
+//   frame 0         how a handle's pool stores its ATs: the value v of an AT
+//                   of block i (an ACT of that block, Sec. 3) is kept as
+//                   u = (v - i) mod 2k, the value it would have in block 0;
+//                   the inactive value 2k is kept as 2k.  Since block i's
+//                   ACT is (BACT^0 + i) mod 2k, CheckAT, the distance of Eq. 5
+//                   and SetAT read the same for every AT with ACT = BACT^0, and
+//                   both cases of Algorithm 3 clear the same values.  The map
+//                   is a bijection per position; pools leave and enter the
+//                   library in the paper's form (to_canonical, from_canonical).
 //   swar_*          CheckAT (Algorithm 1) and fast PreserveAT (Algorithm 3) on
 //                   four ATs of one 32-bit word at once; every AT value is at
 //                   most 2k <= 126, so bit 7 of each byte is free to carry the
@@ -35,6 +44,8 @@ struct Geom {
     uint64_t first;      // low-deviation: ATs below this index are in blocks of size a
     uint32_t c, k, twok, g, L, log2L, segbits, partition;
     uint32_t counter;    // 0: asynchronous timestamps; 1: distance recorders
+    uint32_t frame0;     // 1: timestamps stored in the frame of block 0 (every handle and group pool);
+                         // 0: the paper's per-block values (pools handed in by a caller)
     // host side only: L2 access-policy window over the pool for every launch
     // that touches it (l2_window_bytes = 0: none)
     uint64_t l2_window_bytes;
@@ -186,22 +197,6 @@ VATE_HD uint32_t swar_bins(uint32_t w, uint32_t act, uint32_t twok) {
     return (d & ~E) | ((twok * ONES) & E);
 }
 
-// Algorithm 3 on 4 ATs: at ACT 0 values 0..k become 2k; at ACT k values k..2k-1
-// and 0 become 2k.  Bytes whose ACT is neither 0 nor k must not be passed here.
-VATE_HD uint32_t swar_preserve(uint32_t w, bool act_is_zero, uint32_t k) {
-    uint32_t twok = 2u * k;
-    uint32_t clear;
-    if (act_is_zero) {
-        clear = ~(w + (127u - k) * ONES) & HIGH;                          // v <= k
-    } else {
-        uint32_t in_k_2k1 = (w + (128u - k) * ONES) & ~(w + (127u - (twok - 1u)) * ONES);  // k <= v <= 2k-1
-        uint32_t is_zero = ~(w + 127u * ONES);                             // v <= 0
-        clear = (in_k_2k1 | is_zero) & HIGH;
-    }
-    uint32_t bytes = (clear >> 7) * 0xFFu;    // 0xFF in each cleared byte
-    return (w & ~bytes) | ((twok * ONES) & bytes);
-}
-
 // Distance recorders (VDRE): value 0..k, k = inactive; one slide adds 1 to
 // every recorder below k (four recorders per word; values <= 126).
 VATE_HD uint32_t swar_dr_age(uint32_t w, uint32_t k) {
@@ -243,6 +238,61 @@ VATE_HD uint32_t preserve_at(uint32_t v, uint32_t act, uint32_t k) {
     if (act == 0u && v <= k) return twok;
     if (act == k && ((v >= k && v <= twok - 1u) || v == 0u)) return twok;
     return v;
+}
+
+// ---- frame 0 ---------------------------------------------------------------
+// Algorithm 3 in frame 0.  With B = BACT^0 after the slide, the block whose
+// ACT became 0 has index i = -B and the one whose ACT became k has i = k - B
+// (mod 2k).  At ACT 0 values 0..k are cleared, i.e. u = v - i in B..B+k; at
+// ACT k values k..2k-1 and 0 (= 2k) are cleared, i.e. u = v - i in B..B+k as
+// well.  Both blocks clear the cyclic range [B, B + k] (mod 2k).
+VATE_HD uint32_t preserve_frame0(uint32_t u, uint32_t B, uint32_t k) {
+    uint32_t twok = 2u * k;
+    if (u >= twok) return twok;
+    uint32_t d = u + twok - B;
+    if (d >= twok) d -= twok;
+    return d <= k ? twok : u;
+}
+
+// Range constants (as for CheckAT) selecting the cyclic range [B, B + k]: one
+// range [B, B + k] when it does not wrap, else the complement of
+// [B + k - 2k + 1, B - 1] (that complement also takes in 2k, which a clear
+// leaves unchanged).
+VATE_HD RangeConsts preserve_consts_frame0(uint32_t B, uint32_t k) {
+    uint32_t twok = 2u * k, hi = B + k;
+    RangeConsts rc;
+    if (hi < twok) {
+        rc.a1 = (128u - B) * ONES;
+        rc.b1 = (127u - hi) * ONES;
+        rc.f = 0u;
+    } else {
+        rc.a1 = (128u - (hi - twok + 1u)) * ONES;
+        rc.b1 = (127u - (B - 1u)) * ONES;
+        rc.f = HIGH;
+    }
+    rc.pad = 0u;
+    return rc;
+}
+
+// preserve_frame0 on four ATs of one word
+VATE_HD uint32_t swar_preserve_frame0(uint32_t w, const RangeConsts &pc, uint32_t twok) {
+    uint32_t clear = (((w + pc.a1) & ~(w + pc.b1)) ^ pc.f) & HIGH;
+    uint32_t bytes = (clear >> 7) * 0xFFu;
+    return (w & ~bytes) | ((twok * ONES) & bytes);
+}
+
+// The paper's value of a frame-0 AT of block blk, and back.  Values above 2k
+// (not produced by the library) are taken as inactive.
+VATE_HD uint32_t to_canonical(uint32_t u, uint32_t blk, uint32_t twok) {
+    if (u >= twok) return twok;
+    uint32_t v = u + blk;
+    return v >= twok ? v - twok : v;
+}
+
+VATE_HD uint32_t from_canonical(uint32_t v, uint32_t blk, uint32_t twok) {
+    if (v >= twok) return twok;
+    uint32_t u = v + twok - blk;
+    return u >= twok ? u - twok : u;
 }
 
 }  // namespace vate

@@ -6,36 +6,38 @@
 
 namespace vate {
 
-// PreserveAT (Algorithm 3) on the 16-byte chunk at pool offset `base` for the
-// bytes inside [s0, e0) (block with ACT 0) or [s1, e1) (block with ACT k).
-__device__ __forceinline__ void preserve_chunk(uint8_t *pool, uint64_t base, uint32_t k, uint64_t s0, uint64_t e0,
-                                               uint64_t s1, uint64_t e1) {
+// PreserveAT (Algorithm 3) on the 16-byte chunk at pool offset `base` of a
+// frame-0 pool, for the bytes inside [s0, e0) (block with ACT 0) or [s1, e1)
+// (block with ACT k): both clear the values selected by pc
+// (preserve_consts_frame0 of the new BACT^0).
+__device__ __forceinline__ void preserve_chunk(uint8_t *pool, uint64_t base, const RangeConsts &pc, uint32_t twok,
+                                               uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1) {
     uint4 *p = reinterpret_cast<uint4 *>(pool + base);
     uint4 w = *p;
-    uint4 r = w;
-    bool full0 = base >= s0 && base + 16 <= e0;
-    bool full1 = base >= s1 && base + 16 <= e1;
-    if (full0 || full1) {
-        r.x = swar_preserve(w.x, full0, k);
-        r.y = swar_preserve(w.y, full0, k);
-        r.z = swar_preserve(w.z, full0, k);
-        r.w = swar_preserve(w.w, full0, k);
-    } else {
-        uint32_t words[4] = {w.x, w.y, w.z, w.w};
+    uint4 r;
+    r.x = swar_preserve_frame0(w.x, pc, twok);
+    r.y = swar_preserve_frame0(w.y, pc, twok);
+    r.z = swar_preserve_frame0(w.z, pc, twok);
+    r.w = swar_preserve_frame0(w.w, pc, twok);
+    bool full = (base >= s0 && base + 16 <= e0) || (base >= s1 && base + 16 <= e1);
+    if (!full) {            // keep the bytes outside both blocks
+        uint32_t in[4] = {w.x, w.y, w.z, w.w}, out[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
         for (int b = 0; b < 16; b++) {
             uint64_t pos = base + b;
-            uint32_t v = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-            uint32_t nv = v;
-            if (pos >= s0 && pos < e0) nv = preserve_at(v, 0u, k);
-            else if (pos >= s1 && pos < e1) nv = preserve_at(v, k, k);
-            words[b >> 2] = (words[b >> 2] & ~(0xFFu << (8 * (b & 3)))) | (nv << (8 * (b & 3)));
+            if ((pos >= s0 && pos < e0) || (pos >= s1 && pos < e1)) continue;
+            uint32_t m = 0xFFu << (8 * (b & 3));
+            out[b >> 2] = (out[b >> 2] & ~m) | (in[b >> 2] & m);
         }
-        r.x = words[0]; r.y = words[1]; r.z = words[2]; r.w = words[3];
+        r.x = out[0]; r.y = out[1]; r.z = out[2]; r.w = out[3];
     }
     if (r.x != w.x || r.y != w.y || r.z != w.z || r.w != w.w) *p = r;
 }
 
+// Census of one 16-byte chunk into this lane's column (col[bin * 32]): the
+// distance of Eq. 5 for active values, 2k for inactive ones.  A frame-0 pool
+// reads every AT with ACT = BACT^0; a pool in the paper's form reads each AT
+// with the ACT of its block.
 __device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint32_t pid0, uint4 w, uint32_t pat,
                                              uint32_t *col, uint32_t &inactive_runs) {
     if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
@@ -48,6 +50,11 @@ __device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint
         words[1] = swar_dr_bins(w.y, G.k, G.twok);
         words[2] = swar_dr_bins(w.z, G.k, G.twok);
         words[3] = swar_dr_bins(w.w, G.k, G.twok);
+    } else if (G.frame0) {
+        words[0] = swar_bins(w.x, bact0, G.twok);
+        words[1] = swar_bins(w.y, bact0, G.twok);
+        words[2] = swar_bins(w.z, bact0, G.twok);
+        words[3] = swar_bins(w.w, bact0, G.twok);
     } else {
         uint32_t b0 = block_of(G, pid0);
         if (b0 != block_of(G, pid0 + 15u)) {
@@ -95,37 +102,20 @@ __device__ __forceinline__ uint64_t pool_inactive(const uint64_t *hist, uint64_t
     return P - active;
 }
 
-// Per-byte CheckAT of one 16-byte chunk whose bytes may lie in two blocks.
-__device__ __forceinline__ uint32_t count_chunk_bytes(const Geom &G, uint32_t bact0, uint32_t kprime, uint32_t pid,
-                                                   uint4 w) {
-    uint32_t words[4] = {w.x, w.y, w.z, w.w};
-    uint32_t n = 0;
-    for (int b = 0; b < 16; b++) {
-        uint32_t v = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-        if (G.counter == 1u) {
-            n += check_dr(v, kprime) ? 1u : 0u;
-            continue;
-        }
-        uint32_t act = act_of_block(bact0, block_of(G, pid + b), G.twok);
-        n += check_at(v, act, kprime, G.twok) ? 1u : 0u;
-    }
-    return n;
-}
-
-
-// Active VATs seen by this lane for one host (warp per host, L = 16 << CPSL):
-// in each round the 32 lanes hash 32 consecutive segments; the segments'
-// 16-byte chunks are then read by consecutive lanes (for L = 32, lanes 2j and
-// 2j+1 read the two halves of one 32-byte sector), the segment base and ACT
-// coming from the hashing lane by shuffle.  All RB * CPS loads of a batch are
-// issued before any is tested.  FULL: the number of segments is a multiple of
-// 32 * RB.  Active ATs are counted per byte lane in a SWAR accumulator (at
-// most RB * CPS * 4 <= 32 per byte lane per batch), folded after each batch.
-// tbl[act] holds range_consts(act, k', 2k); u1..u3 are run-time ones.
+// Active VATs seen by this lane for one host of a frame-0 pool (warp per
+// host, L = 16 << CPSL): in each round the 32 lanes hash 32 consecutive
+// segments; the segments' 16-byte chunks are then read by consecutive lanes
+// (for L = 32, lanes 2j and 2j+1 read the two halves of one 32-byte sector),
+// the segment base coming from the hashing lane by shuffle.  All RB * CPS
+// loads of a batch are issued before any is tested.  FULL: the number of
+// segments is a multiple of 32 * RB.  Every AT is tested with the same range
+// constants rc (CheckAT with ACT = BACT^0, or CheckDR), so no block is looked
+// up.  Active ATs are counted per byte lane in a SWAR accumulator (at most
+// RB * CPS * 4 <= 32 per byte lane per batch), folded after each batch.
+// u1..u3 are run-time ones.
 template <int CPSL, int RB, bool FULL>
-__device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, uint32_t bact0, uint32_t kprime, uint32_t aip,
-                                                    const RangeConsts *tbl, uint32_t c2k, uint32_t a32, uint32_t u1,
-                                                    uint32_t u2, uint32_t u3, uint32_t lane) {
+__device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, const RangeConsts &rc, uint32_t c2k, uint32_t aip,
+                                                    uint32_t u1, uint32_t u2, uint32_t u3, uint32_t lane) {
     constexpr int CPS = 1 << CPSL;                      // 16-byte chunks per segment
     constexpr int NL = RB * CPS;                        // loads per lane per batch
     const uint32_t nseg = G.g >> G.log2L;              // segments per host
@@ -133,28 +123,13 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, uint32_t bact
     uint32_t cnt = 0;
     const uint64_t hk = host_key(G, aip);
     for (uint32_t r0 = 0; r0 < nseg; r0 += 32u * RB) {
-        // hash: one segment per lane and round; ACT and "straddles a block
-        // boundary" packed as act | flag << 8
-        uint32_t base[RB], actf[RB];
+        uint32_t base[RB];
 #pragma unroll
         for (int rb = 0; rb < RB; rb++) {
             uint32_t s = r0 + 32u * rb + lane;
-            base[rb] = 0;
-            actf[rb] = 0;
-            if (FULL || s < nseg) {
-                base[rb] = seg_base_k(G, hk, s);
-                uint32_t b0 = block_of(G, base[rb]);
-                bool straddle;
-                if (G.partition == 0)       // offset inside a block of size a (the last block may be smaller:
-                    straddle = base[rb] - b0 * a32 > a32 - G.L;   // then this errs towards the exact slow path)
-                else
-                    straddle = b0 != block_of(G, base[rb] + G.L - 1u);
-                actf[rb] = act_of_block(bact0, b0, G.twok) | (straddle ? 0x100u : 0u);
-            }
+            base[rb] = (FULL || s < nseg) ? seg_base_k(G, hk, s) : 0u;
         }
-        // loads
         uint4 w[NL];
-        uint32_t pid[NL], sact[NL];
         bool valid[NL];
 #pragma unroll
         for (int rb = 0; rb < RB; rb++) {
@@ -164,45 +139,21 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, uint32_t bact
                 const int j = rb * CPS + it;
                 uint32_t c = it * 32u + lane;
                 uint32_t src = (c >> CPSL) & 31u;
-                uint32_t sbase = __shfl_sync(0xFFFFFFFFu, base[rb], src);
-                sact[j] = __shfl_sync(0xFFFFFFFFu, actf[rb], src);
-                pid[j] = sbase + ((c & (CPS - 1u)) << 4);
+                uint32_t pid = __shfl_sync(0xFFFFFFFFu, base[rb], src) + ((c & (CPS - 1u)) << 4);
                 valid[j] = FULL || c < (segs_here << CPSL);
                 w[j] = make_uint4(0u, 0u, 0u, 0u);
-                if (valid[j]) w[j] = __ldg(pool16 + (pid[j] >> 4));
+                if (valid[j]) w[j] = __ldg(pool16 + (pid >> 4));
             }
         }
-        // CheckAT on every loaded chunk; the per-chunk straddle test only runs
-        // when some segment of the batch straddles a block boundary (rare)
         uint32_t acc = 0;
-        bool any_straddle = false;
 #pragma unroll
-        for (int rb = 0; rb < RB; rb++) any_straddle |= __any_sync(0xFFFFFFFFu, (actf[rb] & 0x100u) != 0u);
-        if (!any_straddle) {
-#pragma unroll
-            for (int j = 0; j < NL; j++) {
-                if (!valid[j]) continue;
-                const RangeConsts rc = tbl[sact[j]];
-                // (m >> 7) added as a multiply-high by 2^25 (multiply-add pipe)
-                acc = __umulhi(swar_active_fma(w[j].x, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                acc = __umulhi(swar_active_fma(w[j].y, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                acc = __umulhi(swar_active_fma(w[j].z, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                acc = __umulhi(swar_active_fma(w[j].w, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < NL; j++) {
-                if (!valid[j]) continue;
-                if (sact[j] & 0x100u) {
-                    cnt += count_chunk_bytes(G, bact0, kprime, pid[j], w[j]);
-                } else {
-                    const RangeConsts rc = tbl[sact[j]];
-                    acc = __umulhi(swar_active_fma(w[j].x, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                    acc = __umulhi(swar_active_fma(w[j].y, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                    acc = __umulhi(swar_active_fma(w[j].z, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                    acc = __umulhi(swar_active_fma(w[j].w, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-                }
-            }
+        for (int j = 0; j < NL; j++) {
+            if (!valid[j]) continue;
+            // (m >> 7) added as a multiply-high by 2^25 (multiply-add pipe)
+            acc = __umulhi(swar_active_fma(w[j].x, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+            acc = __umulhi(swar_active_fma(w[j].y, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+            acc = __umulhi(swar_active_fma(w[j].z, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+            acc = __umulhi(swar_active_fma(w[j].w, rc, c2k, u1, u2, u3), 1u << 25) + acc;
         }
         uint32_t t = (acc & 0x00FF00FFu) + ((acc >> 8) & 0x00FF00FFu);
         cnt += (t & 0xFFFFu) + (t >> 16);
@@ -210,7 +161,8 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, uint32_t bact
     return cnt;
 }
 
-// Active VATs seen by this lane for one host, one byte per VAT (any L).
+// Active VATs seen by this lane for one host of a frame-0 pool, one byte per
+// VAT (any L).
 __device__ __forceinline__ uint32_t gather_host_scalar(const Geom &G, uint32_t bact0, uint32_t kprime, uint32_t aip,
                                                        uint32_t lane) {
     uint32_t cnt = 0;
@@ -223,8 +175,7 @@ __device__ __forceinline__ uint32_t gather_host_scalar(const Geom &G, uint32_t b
             cnt += check_dr(v, kprime) ? 1u : 0u;
             continue;
         }
-        uint32_t act = act_of_block(bact0, block_of(G, pid), G.twok);
-        cnt += check_at(v, act, kprime, G.twok) ? 1u : 0u;
+        cnt += check_at(v, bact0, kprime, G.twok) ? 1u : 0u;
     }
     return cnt;
 }

@@ -144,7 +144,9 @@ __global__ void __launch_bounds__(G_THREADS) group_preserve_kernel(const Geom *_
         uint64_t n0 = n0s[m];
         uint64_t chunk = local < n0 ? c0s + local : c1s + (local - n0);
         if (local >= n0 && n0 && chunk >= c0s && chunk < c0e) continue;   // enumerated with range 0
-        preserve_chunk(descs[m].pool, chunk << 4, descs[m].k, s0, e0, s1, e1);
+        const uint32_t k = descs[m].k;
+        preserve_chunk(descs[m].pool, chunk << 4, preserve_consts_frame0(bact0_of(step, 2u * k), k), 2u * k, s0, e0,
+                       s1, e1);
     }
 }
 
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(G_THREADS) group_ingest_kernel(const Geom *__r
         const Geom &G = sd[m];
         uint32_t aip = __ldcs(pairs + 2 * i), bip = __ldcs(pairs + 2 * i + 1);
         uint32_t pid = vat_pid(G, aip, bh(G, bip));
-        G.pool[pid] = (uint8_t)act_of_block(bact0_of(step, G.twok), block_of(G, pid), G.twok);
+        G.pool[pid] = (uint8_t)bact0_of(step, G.twok);        // SetAT in frame 0
     }
 }
 
@@ -224,7 +226,6 @@ __global__ void __launch_bounds__(G_THREADS) group_gather_kernel(const Geom *__r
     uint64_t *n0 = so + M + 1;                                   // N0 per monitor
     uint32_t *kp = reinterpret_cast<uint32_t *>(n0 + M);         // k' per monitor
     Geom *sd = reinterpret_cast<Geom *>(so + ((2 * M + 1 + (M + 1) / 2 + 1) & ~1u));
-    __shared__ RangeConsts tbl[G_THREADS / 32][128];
     load_offsets(off, M, cap, so, st, VATE_GROUP_BAD_OFFSETS);
     for (uint32_t m = threadIdx.x; m < M; m += blockDim.x) {
         sd[m] = descs[m];
@@ -238,9 +239,10 @@ __global__ void __launch_bounds__(G_THREADS) group_gather_kernel(const Geom *__r
     }
     __syncthreads();
     const unsigned long long step = st->step;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
     const uint64_t lo = so[0], hi = so[M];
     uint32_t cur = 0xFFFFFFFFu;
+    RangeConsts rc = {};
     for (;;) {
         uint64_t base = 0;
         if (lane == 0) base = lo + (uint64_t)atomicAdd(&st->q_gather, grab);
@@ -250,24 +252,20 @@ __global__ void __launch_bounds__(G_THREADS) group_gather_kernel(const Geom *__r
         for (uint64_t h = base; h < end; h++) {
             const uint32_t m = find_monitor(so, M, h);
             const Geom &G = sd[m];
-            if (m != cur) {                      // this warp's CheckAT table for monitor m
-                for (uint32_t a = lane; a < G.twok; a += 32u) tbl[warp][a] = range_consts(a, kp[m], G.twok);
-                __syncwarp();
+            const uint32_t bact0 = bact0_of(step, G.twok);
+            if (m != cur) {                      // CheckAT of monitor m: ACT = BACT^0 for every AT in frame 0
+                rc = range_consts(bact0, kp[m], G.twok);
                 cur = m;
             }
-            const uint32_t bact0 = bact0_of(step, G.twok);
             const uint32_t aip = hosts[h];
             uint32_t cnt;
             if (CPSL >= 0) {
                 const uint32_t nseg = G.g >> G.log2L;
-                const uint32_t a32 = (uint32_t)min(G.a, (uint64_t)0xFFFFFFFFu);
                 const uint32_t c2k = (128u - G.twok) * ONES;
                 if (nseg % (32u * RB) == 0)
-                    cnt = gather_host_vec<(CPSL < 0 ? 0 : CPSL), RB, true>(G, bact0, kp[m], aip, tbl[warp], c2k, a32,
-                                                                           u1, u2, u3, lane);
+                    cnt = gather_host_vec<(CPSL < 0 ? 0 : CPSL), RB, true>(G, rc, c2k, aip, u1, u2, u3, lane);
                 else
-                    cnt = gather_host_vec<(CPSL < 0 ? 0 : CPSL), RB, false>(G, bact0, kp[m], aip, tbl[warp], c2k, a32,
-                                                                            u1, u2, u3, lane);
+                    cnt = gather_host_vec<(CPSL < 0 ? 0 : CPSL), RB, false>(G, rc, c2k, aip, u1, u2, u3, lane);
             } else {
                 cnt = gather_host_scalar(G, bact0, kp[m], aip, lane);
             }
@@ -435,6 +433,7 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
             delete g;
             return vate::set_error(VATE_EINVAL, "all monitors of a group must use the same seg_len");
         }
+        g->geoms[m].frame0 = 1u;                 // pools keep timestamps in the frame of block 0
         g->maxbins = std::max(g->maxbins, g->geoms[m].twok + 1);
         off = (off + 255) & ~255ull;
         off += g->geoms[m].P;
@@ -684,7 +683,10 @@ int vate_group_status(vate_group *g, uint32_t *status, int clear, void *stream) 
 
 int vate_group_copy_pool(vate_group *g, uint32_t m, uint8_t *d_dst, void *stream) {
     if (!g || m >= g->M || !d_dst) return vate::set_error(VATE_EINVAL, "bad group, monitor or destination");
-    cudaError_t e = cudaMemcpyAsync(d_dst, g->geoms[m].pool, g->geoms[m].P, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    const Geom &G = g->geoms[m];
+    cudaError_t e = cudaMemcpyAsync(d_dst, G.pool, G.P, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = vate::launch_frame_convert(G, d_dst, d_dst, 0, G.P, true, st, g->sms);   // paper's form
     if (e != cudaSuccess) return vate::set_error(VATE_ECUDA, cudaGetErrorString(e));
     return VATE_OK;
 }

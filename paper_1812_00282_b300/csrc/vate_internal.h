@@ -31,8 +31,11 @@ int set_error(int code, const char *msg);
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms);
 cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, uint64_t n, cudaStream_t st, int sms);
 cudaError_t launch_dr_age(const Geom &G, cudaStream_t st, int sms);
-cudaError_t launch_preserve(const Geom &G, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1, cudaStream_t st,
-                            int sms);
+cudaError_t launch_preserve(const Geom &G, uint32_t bact0, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
+                            cudaStream_t st, int sms);
+// frame 0 -> the paper's per-block values (to_paper) or back, for pool positions pid0 .. pid0 + n - 1
+cudaError_t launch_frame_convert(const Geom &G, const uint8_t *src, uint8_t *dst, uint64_t pid0, uint64_t n,
+                                 bool to_paper, cudaStream_t st, int sms);
 size_t census_smem_bytes(uint32_t twok);
 cudaError_t census_prepare(uint32_t twok);
 cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,

@@ -9,6 +9,13 @@
 //                         segment lengths L >= 16 (16-byte loads)       (Algorithm 1, Algorithm 4)
 //   gather_scalar_kernel  the same for L < 16 (one byte per VAT)
 //   age_counts_kernel     per-host counts of VATs by distance d < k
+//   frame_convert_kernel  a pool to / from the paper's per-block values
+//
+// A handle's timestamp pool is kept in the frame of block 0 (each value minus
+// its block's index, mod 2k; see vate_device.cuh), so SetAT, CheckAT, the
+// census and PreserveAT use constants shared by every AT of a launch and no
+// kernel of the slice step looks up a block except to bound the two
+// maintained ranges.
 //
 // Nothing here is a dense contraction: the path is bound by L2/HBM sector
 // traffic and integer ALU, so no tensor cores are used.
@@ -36,12 +43,12 @@ __global__ void init_pool_kernel(uint8_t *__restrict__ pool, uint64_t P, uint32_
 // --------------------------------------------------------------------------
 // Ingest: one thread per two pairs (one 16-byte streaming load).
 // --------------------------------------------------------------------------
-// SetAT writes the ACT of the AT's block; a distance recorder is reset to 0.
+// SetAT writes the ACT of the AT's block, which in frame 0 is BACT^0 for every
+// AT; a distance recorder is reset to 0.
 __device__ __forceinline__ void set_at(const Geom &G, uint32_t bact0, uint32_t aip, uint32_t bip) {
     uint32_t vid = bh(G, bip);
     uint32_t pid = vat_pid(G, aip, vid);
-    uint32_t v = G.counter == 1u ? 0u : act_of_block(bact0, block_of(G, pid), G.twok);
-    G.pool[pid] = (uint8_t)v;
+    G.pool[pid] = (uint8_t)(G.counter == 1u ? 0u : bact0);
 }
 
 __global__ void __launch_bounds__(256) ingest_kernel(Geom G, uint32_t bact0, const uint32_t *__restrict__ pairs,
@@ -61,13 +68,13 @@ __global__ void __launch_bounds__(256) ingest_kernel(Geom G, uint32_t bact0, con
 }
 
 // --------------------------------------------------------------------------
-// PreserveAT on blocks i0 (ACT 0) and i1 (ACT k).  Work is enumerated in
-// 16-byte chunks covering [s0, e0) and then [s1, e1); a chunk shared by the
-// two ranges (only possible for k = 1) belongs to range 0's enumeration and
-// each byte decides by its own position.
+// PreserveAT on blocks i0 (ACT 0) and i1 (ACT k) of a frame-0 pool.  Work is
+// enumerated in 16-byte chunks covering [s0, e0) and then [s1, e1); a chunk
+// shared by the two ranges (only possible for k = 1) belongs to range 0's
+// enumeration and each byte decides by its own position.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) preserve_kernel(uint8_t *__restrict__ pool, uint32_t k, uint64_t s0,
-                                                       uint64_t e0, uint64_t s1, uint64_t e1) {
+__global__ void __launch_bounds__(256) preserve_kernel(uint8_t *__restrict__ pool, RangeConsts pc, uint32_t twok,
+                                                       uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1) {
     uint64_t c0s = s0 >> 4, c0e = (e0 + 15) >> 4;
     uint64_t c1s = s1 >> 4, c1e = (e1 + 15) >> 4;
     uint64_t n0 = (e0 > s0) ? c0e - c0s : 0;
@@ -77,7 +84,32 @@ __global__ void __launch_bounds__(256) preserve_kernel(uint8_t *__restrict__ poo
          t += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t chunk = t < n0 ? c0s + t : c1s + (t - n0);
         if (t >= n0 && n0 && chunk >= c0s && chunk < c0e) continue;   // enumerated by range 0
-        preserve_chunk(pool, chunk << 4, k, s0, e0, s1, e1);
+        preserve_chunk(pool, chunk << 4, pc, twok, s0, e0, s1, e1);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Frame 0 <-> the paper's per-block values, for n bytes of pool positions
+// pid0 .. pid0 + n - 1 (src and dst may be the same buffer; any alignment).
+// Distance recorders are copied, values above k clamped to k.
+// 16 bytes per thread; the block is looked up once unless the 16 straddle a
+// block boundary.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) frame_convert_kernel(Geom G, const uint8_t *src, uint8_t *dst, uint64_t pid0,
+                                                            uint64_t n, int to_paper) {
+    const uint64_t nq = (n + 15) >> 4;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nq; q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t o0 = q << 4, o1 = min(o0 + 16, n);
+        const uint32_t b0 = block_of(G, (uint32_t)(pid0 + o0));
+        const bool one = b0 == block_of(G, (uint32_t)(pid0 + o1 - 1));
+        for (uint64_t o = o0; o < o1; o++) {
+            const uint32_t blk = one ? b0 : block_of(G, (uint32_t)(pid0 + o));
+            const uint32_t x = src[o];
+            if (G.counter == 1u)          // distance recorders have one frame; out-of-range values become inactive
+                dst[o] = (uint8_t)min(x, G.k);
+            else
+                dst[o] = (uint8_t)(to_paper ? to_canonical(x, blk, G.twok) : from_canonical(x, blk, G.twok));
+        }
     }
 }
 
@@ -183,7 +215,8 @@ __device__ __forceinline__ void write_result(const Geom &G, uint64_t N0, uint64_
 // rounds of 32 segments.  In each round the 32 lanes hash 32 consecutive
 // segments; the segments' 16-byte chunks are then read by consecutive lanes
 // (for L = 32, lanes 2j and 2j+1 read the two halves of one 32-byte sector),
-// the segment base and ACT coming from the hashing lane by shuffle.  All
+// the segment base coming from the hashing lane by shuffle; one CheckAT
+// (ACT = BACT^0 in frame 0) serves every AT of the launch.  All
 // RB * CPS loads of a batch are issued before any is tested, so that several
 // sectors are in flight per lane.  FULL: every batch is complete (the number
 // of segments is a multiple of 32 * RB), so no lane needs a bounds test.
@@ -204,10 +237,9 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
                                                                     uint8_t *__restrict__ flags,
                                                                     uint32_t *__restrict__ active, uint32_t u1,
                                                                     uint32_t u2, uint32_t u3) {
-    __shared__ RangeConsts tbl[128];
     __shared__ uint64_t sN0;
-    for (uint32_t a = threadIdx.x; a < G.twok; a += blockDim.x)    // distance recorders: the same test for every ACT
-        tbl[a] = G.counter == 1u ? dr_range_consts(kprime) : range_consts(a, kprime, G.twok);
+    // one CheckAT for every AT of the frame-0 pool (ACT = BACT^0), or CheckDR
+    const RangeConsts rc = G.counter == 1u ? dr_range_consts(kprime) : range_consts(bact0, kprime, G.twok);
     if (MODE == GATHER_ESTIMATE && threadIdx.x == 0) sN0 = pool_inactive(hist, G.P, kprime);
     __syncthreads();
     const uint64_t N0 = (MODE == GATHER_ESTIMATE) ? sN0 : 0;
@@ -216,7 +248,6 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t a32 = (uint32_t)min(G.a, (uint64_t)0xFFFFFFFFu);
 
     // The warp takes its hosts 32 at a time (hosts g0 + j * nwarps, j < 32):
     // lane j loads host j's address up front, the warp gathers the hosts one
@@ -229,7 +260,7 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
         for (uint32_t j = 0; j < 32u; j++) {
             if (g0 + (uint64_t)j * nwarps >= n) break;
             const uint32_t aip = __shfl_sync(0xFFFFFFFFu, my_aip, j);
-            uint32_t cnt = gather_host_vec<CPSL, RB, FULL>(G, bact0, kprime, aip, tbl, c2k, a32, u1, u2, u3, lane);
+            uint32_t cnt = gather_host_vec<CPSL, RB, FULL>(G, rc, c2k, aip, u1, u2, u3, lane);
             uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
             if (lane == j) my_A = A;
         }
@@ -284,8 +315,7 @@ __global__ void __launch_bounds__(AGE_THREADS) age_counts_kernel(Geom G, uint32_
                 continue;
             }
             if (v == G.twok) continue;
-            uint32_t act = act_of_block(bact0, block_of(G, pid), G.twok);
-            uint32_t d = act + G.twok - v;
+            uint32_t d = bact0 + G.twok - v;          // frame 0: ACT = BACT^0
             if (d >= G.twok) d -= G.twok;
             if (d < G.k) col[d * 32u] += 1u;
         }
@@ -333,10 +363,19 @@ cudaError_t launch_dr_age(const Geom &G, cudaStream_t st, int sms) {
     return launch_pool(G, dr_age_kernel, grid_for(G.P >> 4, 256, sms * 8), 256, 0, st, G.pool, G.P, G.k);
 }
 
-cudaError_t launch_preserve(const Geom &G, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1, cudaStream_t st,
-                            int sms) {
+cudaError_t launch_preserve(const Geom &G, uint32_t bact0, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
+                            cudaStream_t st, int sms) {
     uint64_t chunks = ((e0 - s0) >> 4) + ((e1 - s1) >> 4) + 4;
-    return launch_pool(G, preserve_kernel, grid_for(chunks, 256, sms * 8), 256, 0, st, G.pool, G.k, s0, e0, s1, e1);
+    return launch_pool(G, preserve_kernel, grid_for(chunks, 256, sms * 8), 256, 0, st, G.pool,
+                       preserve_consts_frame0(bact0, G.k), G.twok, s0, e0, s1, e1);
+}
+
+cudaError_t launch_frame_convert(const Geom &G, const uint8_t *src, uint8_t *dst, uint64_t pid0, uint64_t n,
+                                 bool to_paper, cudaStream_t st, int sms) {
+    if (n == 0) return cudaSuccess;
+    frame_convert_kernel<<<grid_for((n + 15) >> 4, 256, sms * 8), 256, 0, st>>>(G, src, dst, pid0, n, to_paper ? 1 : 0);
+    count_launch();
+    return cudaGetLastError();
 }
 
 size_t census_smem_bytes(uint32_t twok) { return (size_t)(CENSUS_THREADS / 32) * (twok + 1) * 32 * sizeof(uint32_t); }

@@ -39,7 +39,8 @@ __host__ __device__ inline Layout layout(uint32_t n_in) {
 }
 
 // Per-age counts of one host's VATs accumulated into this lane's column
-// (col[d * 32], d < k); 16-byte chunks when L >= 16, one byte per VAT otherwise.
+// (col[d * 32], d < k) from a frame-0 pool, where every AT has ACT = BACT^0;
+// 16-byte chunks when L >= 16, one byte per VAT otherwise.
 __device__ __forceinline__ void host_age_columns(const Geom &G, uint32_t bact0, uint32_t aip, uint32_t lane,
                                                  uint32_t *col) {
     const uint64_t hk = host_key(G, aip);
@@ -47,36 +48,21 @@ __device__ __forceinline__ void host_age_columns(const Geom &G, uint32_t bact0, 
         const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
         const uint32_t nchunks = G.g >> 4;
         for (uint32_t c = lane; c < nchunks; c += 32u) {
-            const uint32_t i = c << 4;                       // first VAT of the chunk
-            const uint32_t pid = vat_pid_k(G, hk, i);
+            const uint32_t pid = vat_pid_k(G, hk, c << 4);   // first VAT of the chunk
             const uint4 w = __ldg(pool16 + (pid >> 4));
-            const uint32_t b0 = block_of(G, pid);
-            uint32_t words[4] = {w.x, w.y, w.z, w.w};
-            if (b0 == block_of(G, pid + 15u)) {
-                const uint32_t act = act_of_block(bact0, b0, G.twok);
+            uint32_t words[4] = {swar_bins(w.x, bact0, G.twok), swar_bins(w.y, bact0, G.twok),
+                                 swar_bins(w.z, bact0, G.twok), swar_bins(w.w, bact0, G.twok)};
 #pragma unroll
-                for (int q = 0; q < 4; q++) words[q] = swar_bins(words[q], act, G.twok);
-#pragma unroll
-                for (int b = 0; b < 16; b++) {
-                    uint32_t d = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-                    if (d < G.k) col[d * 32u] += 1u;
-                }
-            } else {
-                for (int b = 0; b < 16; b++) {
-                    uint32_t v = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-                    if (v >= G.twok) continue;
-                    uint32_t d = act_of_block(bact0, block_of(G, pid + b), G.twok) + G.twok - v;
-                    if (d >= G.twok) d -= G.twok;
-                    if (d < G.k) col[d * 32u] += 1u;
-                }
+            for (int b = 0; b < 16; b++) {
+                uint32_t d = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+                if (d < G.k) col[d * 32u] += 1u;
             }
         }
     } else {
         for (uint32_t i = lane; i < G.g; i += 32u) {
-            uint32_t pid = vat_pid_k(G, hk, i);
-            uint32_t v = __ldg(G.pool + pid);
+            uint32_t v = __ldg(G.pool + vat_pid_k(G, hk, i));
             if (v >= G.twok) continue;
-            uint32_t d = act_of_block(bact0, block_of(G, pid), G.twok) + G.twok - v;
+            uint32_t d = bact0 + G.twok - v;
             if (d >= G.twok) d -= G.twok;
             if (d < G.k) col[d * 32u] += 1u;
         }

@@ -1,7 +1,9 @@
 // Host-only check of the SWAR AT arithmetic in vate_device.cuh against the
 // scalar forms of Algorithm 1 (CheckAT), Eq. 5 (distance) and Algorithm 3
 // (fast PreserveAT): every k <= 63, every ACT, every k' <= k, every AT value
-// 0..2k in every byte position, plus random mixed words.  Prints "OK".
+// 0..2k in every byte position, plus random mixed words.  The frame-0 forms
+// (values kept as value minus block index, mod 2k) are tied to the paper's
+// through the per-block map.  Prints "OK".
 #include <cstdio>
 #include <cstdlib>
 #include "vate_device.cuh"
@@ -47,19 +49,47 @@ int main() {
                 }
             }
         }
-        for (int z = 0; z < 2; z++) {
-            uint32_t act = z ? k : 0;
-            for (int trial = 0; trial < 2000; trial++) {
+        // Algorithm 3 in frame 0: the SWAR form against the scalar one, and the
+        // scalar one against the paper's Algorithm 3 on the two maintained
+        // blocks (ACT 0: i = -B, ACT k: i = k - B), through the per-block map.
+        for (uint32_t B = 0; B < twok; B++) {
+            const RangeConsts pc = preserve_consts_frame0(B, k);
+            const uint32_t blk[2] = {(twok - B) % twok, (k + twok - B) % twok}, act[2] = {0u, k};
+            for (uint32_t u = 0; u <= twok; u++)
+                for (int z = 0; z < 2; z++) {
+                    uint32_t got = to_canonical(preserve_frame0(u, B, k), blk[z], twok);
+                    uint32_t want = preserve_at(to_canonical(u, blk[z], twok), act[z], k);
+                    if (got != want || from_canonical(to_canonical(u, blk[z], twok), blk[z], twok) != u) {
+                        printf("FAIL frame-0 preserve k=%u B=%u u=%u block=%u\n", k, B, u, blk[z]);
+                        return 1;
+                    }
+                }
+            for (int trial = 0; trial < 300; trial++) {
                 uint32_t v[4];
                 for (int b = 0; b < 4; b++) v[b] = rnd() % (twok + 1);
                 uint32_t w = v[0] | v[1] << 8 | v[2] << 16 | v[3] << 24;
-                uint32_t r = swar_preserve(w, act == 0, k);
+                uint32_t r = swar_preserve_frame0(w, pc, twok);
                 for (int b = 0; b < 4; b++)
-                    if (((r >> (8 * b)) & 0xFFu) != preserve_at(v[b], act, k)) {
-                        printf("FAIL preserve k=%u act=%u v=%u\n", k, act, v[b]);
+                    if (((r >> (8 * b)) & 0xFFu) != preserve_frame0(v[b], B, k)) {
+                        printf("FAIL swar frame-0 preserve k=%u B=%u v=%u\n", k, B, v[b]);
                         return 1;
                     }
+                checked++;
             }
+        }
+        // CheckAT and the distance of Eq. 5 read a frame-0 value with ACT = BACT^0
+        // exactly as the paper's value with its block's ACT (Eq. 8)
+        if (k == 1 || k == 2 || k == 5 || k == 10 || k == 33 || k == 63) {
+            for (uint32_t B = 0; B < twok; B++)
+                for (uint32_t i = 0; i < twok; i++)
+                    for (uint32_t u = 0; u <= twok; u++)
+                        for (uint32_t kp = 1; kp <= k; kp++) {
+                            uint32_t v = to_canonical(u, i, twok), a = (B + i) % twok;
+                            if (check_at(u, B, kp, twok) != check_at(v, a, kp, twok)) {
+                                printf("FAIL frame-0 CheckAT k=%u B=%u i=%u u=%u k'=%u\n", k, B, i, u, kp);
+                                return 1;
+                            }
+                        }
         }
     }
     printf("OK %ld words\n", checked);
