@@ -189,12 +189,15 @@ int vate_copy_pool(vate_handle *h, uint8_t *d_dst, void *stream);
 int vate_load_pool(vate_handle *h, const uint8_t *d_src, void *stream);
 
 /* End-to-end forms with host buffers: the pairs (or hosts) are copied to the
- * device in chunks of up to 2^20 records through two device staging buffers
- * on an internal copy stream, overlapping the copy of chunk i+1 with the
- * kernel of chunk i (the double buffer of Sec. 4.2, with larger chunks).
- * The staging buffers are allocated on the first call.  vate_estimate_host
- * also copies the estimates (and flags, if h_flags is not NULL) back; they
- * are valid once `stream` has been synchronised. */
+ * device in chunks through two device staging buffers on an internal copy
+ * stream, overlapping the copy of chunk i+1 with the kernel of chunk i (the
+ * double buffer of Sec. 4.2, with larger chunks): 2^20 pairs per chunk for
+ * vate_ingest_host; 2^18 hosts per chunk for vate_estimate_host, which also
+ * copies the estimates (and flags, if h_flags is not NULL) back on a second
+ * internal stream, overlapping the gather of chunk i.  The staging buffers are
+ * allocated on the first call.  Results are valid once `stream` has been
+ * synchronised; host buffers in page-locked memory let the copies run
+ * asynchronously. */
 int vate_ingest_host(vate_handle *h, const vate_pair *h_pairs, uint64_t n, int64_t slice, void *stream);
 int vate_estimate_host(vate_handle *h, const uint32_t *h_aips, uint64_t n, uint32_t kprime,
                        float *h_out, uint8_t *h_flags, void *stream);

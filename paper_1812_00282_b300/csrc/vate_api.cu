@@ -16,7 +16,8 @@ using vate::Geom;
 namespace {
 thread_local std::string g_err;
 std::atomic<uint64_t> g_launches{0};
-constexpr uint64_t STAGE_RECORDS = 1ull << 20;   // records per host-copy chunk
+constexpr uint64_t STAGE_RECORDS = 1ull << 20;   // records per host-copy chunk (staging buffer size)
+constexpr uint64_t EST_RECORDS = 1ull << 18;     // hosts per chunk of vate_estimate_host's pipeline
 
 int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 int fail(int code, const char *fmt, ...) {
@@ -105,9 +106,11 @@ struct vate_handle {
     unsigned int *d_ticket = nullptr; // census scratch: blocks finished
     int census_grid = 0;
     // host-copy staging (allocated on first use)
-    cudaStream_t copy_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;      // host -> device
+    cudaStream_t d2h_stream = nullptr;       // device -> host (estimates)
     cudaEvent_t ev_ready[2] = {nullptr, nullptr};
     cudaEvent_t ev_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_done[2] = {nullptr, nullptr};
     void *d_stage[2] = {nullptr, nullptr};       // pairs or hosts in
     float *d_stage_out[2] = {nullptr, nullptr};  // estimates out
     uint8_t *d_stage_flags[2] = {nullptr, nullptr};
@@ -182,9 +185,11 @@ int check_slice(const vate_handle *h, int64_t slice) {
 int ensure_staging(vate_handle *h) {
     if (h->copy_stream) return VATE_OK;
     CU(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
+    CU(cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking), "copy stream");
     for (int i = 0; i < 2; i++) {
         CU(cudaEventCreateWithFlags(&h->ev_ready[i], cudaEventDisableTiming), "event");
         CU(cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming), "event");
+        CU(cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming), "event");
         if (cudaMalloc(&h->d_stage[i], STAGE_RECORDS * sizeof(vate_pair)) != cudaSuccess ||
             cudaMalloc(&h->d_stage_out[i], STAGE_RECORDS * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&h->d_stage_flags[i], STAGE_RECORDS) != cudaSuccess)
@@ -293,6 +298,7 @@ int vate_create(const vate_params *params, void *stream, vate_handle **out) {
 int vate_destroy(vate_handle *h) {
     if (!h) return VATE_OK;
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    if (h->d2h_stream) cudaStreamSynchronize(h->d2h_stream);
     if (h->G.l2_window_bytes) {
         // lines of the freed pool must not keep the persisting carve-out
         cudaDeviceSynchronize();
@@ -309,8 +315,10 @@ int vate_destroy(vate_handle *h) {
         cudaFree(h->d_stage_flags[i]);
         if (h->ev_ready[i]) cudaEventDestroy(h->ev_ready[i]);
         if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
+        if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
     delete h;
     return VATE_OK;
 }
@@ -442,9 +450,14 @@ int vate_estimate_host(vate_handle *h, const uint32_t *h_aips, uint64_t n, uint3
     if (n && !h_out) return fail(VATE_EINVAL, "h_out is NULL");
     if (int rc = ensure_staging(h)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    for (uint64_t off = 0, i = 0; off < n; off += STAGE_RECORDS, i++) {
+    // Three-stage pipeline over chunks of EST_RECORDS hosts and two staging
+    // buffers: hosts in on the copy stream, gather + Eq. 11 on `stream`,
+    // estimates out on the D2H stream, so that the copies of chunks i+1 and
+    // i-1 overlap the gather of chunk i.
+    int used = 0;
+    for (uint64_t off = 0, i = 0; off < n; off += EST_RECORDS, i++) {
         int b = (int)(i & 1);
-        uint64_t m = (n - off) < STAGE_RECORDS ? (n - off) : STAGE_RECORDS;
+        uint64_t m = (n - off) < EST_RECORDS ? (n - off) : EST_RECORDS;
         uint32_t *din = reinterpret_cast<uint32_t *>(h->d_stage[b]);
         CU(cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0), "wait");
         CU(cudaMemcpyAsync(din, h_aips + off, m * sizeof(uint32_t), cudaMemcpyHostToDevice, h->copy_stream), "hosts H2D");
@@ -454,11 +467,17 @@ int vate_estimate_host(vate_handle *h, const uint32_t *h_aips, uint64_t n, uint3
                                             h->d_stage_out[b], h_flags ? h->d_stage_flags[b] : nullptr, nullptr, st,
                                             h->sms);
         if (e != cudaSuccess) return cuda_fail(e, "estimate launch");
-        CU(cudaMemcpyAsync(h_out + off, h->d_stage_out[b], m * sizeof(float), cudaMemcpyDeviceToHost, st), "D2H");
+        CU(cudaEventRecord(h->ev_done[b], st), "record");
+        CU(cudaStreamWaitEvent(h->d2h_stream, h->ev_done[b], 0), "wait");
+        CU(cudaMemcpyAsync(h_out + off, h->d_stage_out[b], m * sizeof(float), cudaMemcpyDeviceToHost, h->d2h_stream),
+           "D2H");
         if (h_flags)
-            CU(cudaMemcpyAsync(h_flags + off, h->d_stage_flags[b], m, cudaMemcpyDeviceToHost, st), "D2H");
-        CU(cudaEventRecord(h->ev_free[b], st), "record");
+            CU(cudaMemcpyAsync(h_flags + off, h->d_stage_flags[b], m, cudaMemcpyDeviceToHost, h->d2h_stream), "D2H");
+        CU(cudaEventRecord(h->ev_free[b], h->d2h_stream), "record");
+        used |= 1 << b;
     }
+    for (int b = 0; b < 2; b++)            // the caller's stream completes after the last copy out
+        if (used & (1 << b)) CU(cudaStreamWaitEvent(st, h->ev_free[b], 0), "wait");
     return VATE_OK;
 }
 

@@ -230,7 +230,8 @@ def test_host_buffer_entry_points_match_device_ones(V):
     k = 5
     params = (18, k, 1024, 32, 0, 2)
     d1, d2 = V.Vate(*params), V.Vate(*params)
-    hosts = tr.aips
+    # more hosts than one chunk of the estimate pipeline (2^18), ragged tail
+    hosts = np.resize(tr.aips, (1 << 19) + 777)
     for s in range(3):
         arr = tr.slice_pairs(s)
         d1.ingest(dev_pairs(arr), s)
@@ -246,8 +247,12 @@ def test_host_buffer_entry_points_match_device_ones(V):
         e1 = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
         f1 = torch.empty(len(hosts), dtype=torch.uint8, device="cuda")
         d1.estimate(dev_u32(hosts), k, e1, f1)
-        e2 = np.empty(len(hosts), np.float32)
-        f2 = np.empty(len(hosts), np.uint8)
+        if s == 1:                      # page-locked outputs: the copies run asynchronously
+            e2 = torch.empty(len(hosts), dtype=torch.float32).pin_memory().numpy()
+            f2 = torch.empty(len(hosts), dtype=torch.uint8).pin_memory().numpy()
+        else:
+            e2 = np.empty(len(hosts), np.float32)
+            f2 = np.empty(len(hosts), np.uint8)
         V.vate_estimate_host(d2.h, hosts, k, e2, f2)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(e1.cpu().numpy(), e2)
