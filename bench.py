@@ -646,7 +646,7 @@ def run_pt(args):
     hbm = measured_peaks().get("hbm_gbs", 6400.0)
     rows = []
     arms = (("vate", V.VATE_COUNTER_AT, 0), ("vate_lowdev", V.VATE_COUNTER_AT, 1), ("vdre", V.VATE_COUNTER_DR, 0))
-    for k in (10, 63):
+    for k in (10, 63, 300):                        # 300: the paper's k' (16-bit counters here)
         for c in range(23, 33):
             res = {"k": k, "log2_counters": c}
             for name, counter, part in arms:
@@ -666,8 +666,10 @@ def run_pt(args):
                 res[name + "_pt_max_ms"] = round(max(times), 4)
             res["speedup"] = round(res["vdre_pt_ms"] / res["vate_pt_ms"], 1)
             # bytes a slide must read: the whole pool (VDRE) or the two maintained blocks (VATE)
-            res["vdre_read_gbs"] = round((1 << c) / res["vdre_pt_ms"] / 1e6, 1)
-            res["vate_read_gbs"] = round(2 * (1 << c) / (2 * k - 1) / res["vate_pt_ms"] / 1e6, 1)
+            w = 1 if k <= 63 else 2                    # bytes per counter
+            res["counter_bytes"] = w
+            res["vdre_read_gbs"] = round(w * (1 << c) / res["vdre_pt_ms"] / 1e6, 1)
+            res["vate_read_gbs"] = round(w * 2 * (1 << c) / (2 * k - 1) / res["vate_pt_ms"] / 1e6, 1)
             rows.append(res)
             torch.cuda.empty_cache()
     return {"workload": "maintenance time per slide (PT), VATE (both partitions) vs VDRE, 40 Gb/s traffic "

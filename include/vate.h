@@ -28,10 +28,11 @@
  *   - Numbers follow the paper's notation: c (log2 of the pool size P),
  *     k (longest window), k' (window of one estimate), g (VATs per host).
  *
- * Byte-per-AT layout: the pool is uint8_t[P], one AT value (0..2k) per byte,
- * so k <= 63 (2k+1 values below 128; the device compares 4 ATs per 32-bit
- * word).  The paper packs ceil(log2(2k+1)) bits per AT (Sec. 4.2); the state
- * is the same AT value per index.
+ * AT width: for k <= 63 the pool is uint8_t[P], one AT value (0..2k) per
+ * byte (2k+1 values below 128; the device compares 4 ATs per 32-bit word);
+ * for 64 <= k <= 1023 (e.g. the paper's k' = 300, Sec. 5) it is uint16_t[P]
+ * (two ATs per word).  The paper packs ceil(log2(2k+1)) bits per AT
+ * (Sec. 4.2); the state is the same AT value per index.
  */
 #ifndef VATE_H
 #define VATE_H
@@ -66,7 +67,8 @@ typedef struct {
 
 /* Construction parameters.
  *   log2_pool  c: the pool holds P = 2^c ATs, 12 <= c <= 32 (Sec. 4.1).
- *   k          longest window in slices, 1 <= k <= 63; ATs hold 0..2k (Sec. 3).
+ *   k          longest window in slices, 1 <= k <= 1023; ATs hold 0..2k (Sec. 3),
+ *              one byte each for k <= 63, two bytes beyond.
  *   g          virtual ATs per host, 1 <= g <= 65536, a multiple of seg_len.
  *   seg_len    L: VAT i of a host lives at offset (i mod L) of the pool segment
  *              chosen for (aip, floor(i/L)).  L = 1 is fully random placement
@@ -171,15 +173,15 @@ int vate_active_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint3
  * d_counts[i*k + d] = number of host i's g VATs whose distance is exactly d
  * (last set d slices ago), 0 <= d < k; the active count for window k' is the
  * sum of the first k' entries.  d_counts is device uint16[n*k] (g <= 65535
- * is required here). */
+ * and k <= 63 are required here). */
 int vate_age_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint16_t *d_counts, void *stream);
 
 /* Copy the census of the last close into d_hist (device uint64[2k+1]):
  * d_hist[d] for distances 0 <= d < 2k, d_hist[2k] = inactive ATs. */
 int vate_census(vate_handle *h, uint64_t *d_hist, void *stream);
 
-/* Copy the AT pool (P bytes, device, any alignment) to d_dst, or overwrite
- * it from d_src, in the paper's form: byte pid holds the AT value of pool
+/* Copy the AT pool (device uint8[P] for k <= 63, else uint16[P], 2-byte
+ * aligned) to d_dst, or overwrite it from d_src, in the paper's form: byte pid holds the AT value of pool
  * position pid (an ACT of its block, Sec. 3, or 2k when inactive; a distance
  * recorder's value for VATE_COUNTER_DR).  Inside the library a timestamp pool
  * is kept in the frame of block 0 -- value minus block index, mod 2k -- so

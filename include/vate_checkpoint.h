@@ -14,7 +14,8 @@
  * Image layout (little-endian, as written by this library on x86-64/aarch64):
  *   vate_checkpoint_header   (fixed size, header_bytes)
  *   uint64_t hist[2k+1]      census of the last close (zeros before any close)
- *   uint8_t  pool[2^c]       AT values, pool position order
+ *   pool[2^c]                AT values in the paper's form, pool position
+ *                            order: uint8 for k <= 63, uint16 beyond
  * The checksum is FNV-1a (64-bit, Fowler/Noll/Vo) taken over the whole image
  * 8 bytes at a time with the checksum field read as zero.
  */
@@ -40,7 +41,7 @@ typedef struct {
     uint32_t   bact0;          /* BACT^0 of the current slice                             */
     uint32_t   closed;         /* 1 when the current slice has been closed                */
     uint64_t   hist_bytes;     /* (2k+1) * 8                                              */
-    uint64_t   pool_bytes;     /* 2^c                                                     */
+    uint64_t   pool_bytes;     /* 2^c times the AT width (1 or 2 bytes)                   */
     uint64_t   checksum;       /* FNV-1a over the image with this field taken as zero     */
 } vate_checkpoint_header;
 

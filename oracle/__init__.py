@@ -47,6 +47,7 @@ def _load():
             return _lib
         lib = C.CDLL(build())
         u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+        u16p = np.ctypeslib.ndpointer(np.uint16, flags="C_CONTIGUOUS")
         u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
         u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
         f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -69,9 +70,9 @@ def _load():
             "vo_slice": (C.c_int64, [vp]),
             "vo_block_a": (u64, [vp]),
             "vo_block_b": (u64, [vp]),
-            "vo_copy_pool": (None, [vp, u8p]),
-            "vo_copy_dr": (None, [vp, u8p]),
-            "vo_load_pool": (None, [vp, u8p]),
+            "vo_copy_pool": (None, [vp, u16p]),
+            "vo_copy_dr": (None, [vp, u16p]),
+            "vo_load_pool": (None, [vp, u16p]),
             "vo_set_pid": (None, [vp, u64]),
             "vo_set_pids": (None, [vp, u64p, u64]),
             "vo_ingest": (None, [vp, u32p, u64]),
@@ -171,17 +172,18 @@ class Oracle:
         return int(self._lib.vo_block_b(self._s))
 
     def pool(self) -> np.ndarray:
-        out = np.empty(self.P, np.uint8)
+        """AT values (uint16; at most 2k)."""
+        out = np.empty(self.P, np.uint16)
         self._lib.vo_copy_pool(self._s, out)
         return out
 
     def dr(self) -> np.ndarray:
-        out = np.empty(self.P, np.uint8)
+        out = np.empty(self.P, np.uint16)
         self._lib.vo_copy_dr(self._s, out)
         return out
 
     def load_pool(self, pool: np.ndarray) -> None:
-        pool = np.ascontiguousarray(pool, np.uint8)
+        pool = np.ascontiguousarray(pool, np.uint16)
         assert pool.shape == (self.P,)
         self._lib.vo_load_pool(self._s, pool)
 

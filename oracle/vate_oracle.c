@@ -88,11 +88,11 @@ typedef struct {
     uint64_t key_h, key_bh;
     uint64_t a, b;       /* Eq. 9-10 (partition 0) or a', b' (partition 1)  */
     /* state */
-    uint8_t *pool;       /* ATP: one AT value per byte                      */
+    uint16_t *pool;      /* ATP: one AT value per element (values <= 2k)    */
     uint32_t bact0;      /* BACT^0 (Eq. 7)                                  */
     int64_t  t;          /* current slice number, origin 0                  */
     /* VDRE cross-check: one DR per pool position (Sec. 1, Sec. 5) */
-    uint8_t *dr;
+    uint16_t *dr;
 } vo_state;
 
 /* BH(bip) in [0, g): high 32 bits of the mix, scaled by g (Lemire). */
@@ -213,7 +213,7 @@ uint32_t vo_preserve_fast(uint32_t v, uint32_t act, uint32_t k)
 vo_state *vo_create(uint32_t c, uint32_t k, uint32_t g, uint32_t L,
                     uint32_t partition, uint64_t seed)
 {
-    if (c < 1 || c > 32 || k < 1 || k > 127 || g < 1 || L < 1) return NULL;
+    if (c < 1 || c > 32 || k < 1 || k > 1023 || g < 1 || L < 1) return NULL;
     if ((L & (L - 1)) != 0 || g % L != 0 || partition > 1) return NULL;
     uint32_t log2L = 0;
     while ((1u << log2L) < L) log2L++;
@@ -235,13 +235,13 @@ vo_state *vo_create(uint32_t c, uint32_t k, uint32_t g, uint32_t L,
         s->a = P / twok;
         s->b = P % twok;
     }
-    s->pool = (uint8_t *)malloc(P);
-    s->dr = (uint8_t *)malloc(P);
+    s->pool = (uint16_t *)malloc(P * sizeof(uint16_t));
+    s->dr = (uint16_t *)malloc(P * sizeof(uint16_t));
     if (!s->pool || !s->dr) { free(s->pool); free(s->dr); free(s); return NULL; }
     /* InitAT on every AT of the pool; BACT^0 = 0; t = 0. */
-    for (uint64_t i = 0; i < P; i++) s->pool[i] = (uint8_t)(2 * k);
+    for (uint64_t i = 0; i < P; i++) s->pool[i] = (uint16_t)(2 * k);
     /* DR counters start "all ones", i.e. inactive; k or more is inactive. */
-    for (uint64_t i = 0; i < P; i++) s->dr[i] = (uint8_t)k;
+    for (uint64_t i = 0; i < P; i++) s->dr[i] = (uint16_t)k;
     s->bact0 = 0;
     s->t = 0;
     return s;
@@ -260,13 +260,13 @@ uint32_t vo_bact0(const vo_state *s) { return s->bact0; }
 int64_t vo_slice(const vo_state *s) { return s->t; }
 uint64_t vo_block_a(const vo_state *s) { return s->a; }
 uint64_t vo_block_b(const vo_state *s) { return s->b; }
-void vo_copy_pool(const vo_state *s, uint8_t *dst) { memcpy(dst, s->pool, s->P); }
-void vo_copy_dr(const vo_state *s, uint8_t *dst) { memcpy(dst, s->dr, s->P); }
+void vo_copy_pool(const vo_state *s, uint16_t *dst) { memcpy(dst, s->pool, s->P * sizeof(uint16_t)); }
+void vo_copy_dr(const vo_state *s, uint16_t *dst) { memcpy(dst, s->dr, s->P * sizeof(uint16_t)); }
 
 /* SetAT on one pool AT: its value becomes the ACT of its block. */
 void vo_set_pid(vo_state *s, uint64_t pid)
 {
-    s->pool[pid] = (uint8_t)vo_act_of(s, pid);
+    s->pool[pid] = (uint16_t)vo_act_of(s, pid);
     s->dr[pid] = 0;   /* the DR of the same position records distance 0 */
 }
 
@@ -313,7 +313,7 @@ void vo_advance(vo_state *s)
             uint64_t start, count;
             vo_block_range(s, i, &start, &count);
             for (uint64_t q = start; q < start + count; q++)
-                s->pool[q] = (uint8_t)vo_preserve_fast(s->pool[q], bact, s->k);
+                s->pool[q] = (uint16_t)vo_preserve_fast(s->pool[q], bact, s->k);
         }
     }
     for (uint64_t q = 0; q < s->P; q++)
@@ -328,7 +328,7 @@ void vo_advance_general_every_slice(vo_state *s)
     s->bact0 = (s->bact0 + 1) % twok;
     s->t += 1;
     for (uint64_t q = 0; q < s->P; q++)
-        s->pool[q] = (uint8_t)vo_preserve_general(s->pool[q], vo_act_of(s, q), s->k);
+        s->pool[q] = (uint16_t)vo_preserve_general(s->pool[q], vo_act_of(s, q), s->k);
     for (uint64_t q = 0; q < s->P; q++)
         if (s->dr[q] < s->k) s->dr[q] += 1;
 }
@@ -447,4 +447,4 @@ uint32_t vo_active_vats_dr(const vo_state *s, uint32_t aip, uint32_t kprime)
 }
 
 /* Overwrite the pool (tests that construct states by hand). */
-void vo_load_pool(vo_state *s, const uint8_t *src) { memcpy(s->pool, src, s->P); }
+void vo_load_pool(vo_state *s, const uint16_t *src) { memcpy(s->pool, src, s->P * sizeof(uint16_t)); }

@@ -45,7 +45,7 @@ int make_geom(const vate_params *p, Geom *G) {
     if (!p) return fail(VATE_EINVAL, "params is NULL");
     if (p->counter > 1) return fail(VATE_EINVAL, "params.counter must be VATE_COUNTER_AT (0) or VATE_COUNTER_DR (1)");
     if (p->log2_pool < 12 || p->log2_pool > 32) return fail(VATE_EINVAL, "log2_pool (c) must be in [12, 32], got %u", p->log2_pool);
-    if (p->k < 1 || p->k > 63) return fail(VATE_EINVAL, "k must be in [1, 63] for byte ATs, got %u", p->k);
+    if (p->k < 1 || p->k > 1023) return fail(VATE_EINVAL, "k must be in [1, 1023], got %u", p->k);
     if (p->g < 1 || p->g > 65536) return fail(VATE_EINVAL, "g must be in [1, 65536], got %u", p->g);
     uint32_t L = p->seg_len;
     if (L < 1 || L > 64 || (L & (L - 1)) != 0) return fail(VATE_EINVAL, "seg_len must be a power of two in [1, 64], got %u", L);
@@ -64,6 +64,7 @@ int make_geom(const vate_params *p, Geom *G) {
     G->segbits = p->log2_pool - log2L;
     G->partition = p->partition;
     G->counter = p->counter;
+    G->atw = p->k <= 63 ? 1u : 2u;             // byte ATs up to k = 63, 16-bit ones beyond
     G->P = 1ull << p->log2_pool;
     G->key_h = vate::mix64(p->seed + 1);
     G->key_bh = vate::mix64(p->seed + 2);
@@ -270,14 +271,15 @@ int vate_create(const vate_params *params, void *stream, vate_handle **out) {
         if (persist_max > 0 && window_max > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
             if (cur < (size_t)persist_max) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist_max);
             cudaGetLastError();
-            h->G.l2_window_bytes = G.P < (uint64_t)window_max ? G.P : (uint64_t)window_max;
+            const uint64_t pool_bytes = G.P * G.atw;
+            h->G.l2_window_bytes = pool_bytes < (uint64_t)window_max ? pool_bytes : (uint64_t)window_max;
             double ratio = (double)persist_max / (double)h->G.l2_window_bytes;
             h->G.l2_hit_ratio = ratio >= 1.0 ? 1.0f : (float)ratio;
         }
     }
     h->census_grid = h->sms * 4;
     size_t nbins = G.twok + 1;
-    if (cudaMalloc(&h->G.pool, G.P) != cudaSuccess || cudaMalloc(&h->d_hist, nbins * sizeof(uint64_t)) != cudaSuccess ||
+    if (cudaMalloc(&h->G.pool, G.P * G.atw) != cudaSuccess || cudaMalloc(&h->d_hist, nbins * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&h->d_partial, (size_t)h->census_grid * nbins * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&h->d_ticket, sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
@@ -389,6 +391,7 @@ int vate_active_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint3
 int vate_age_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint16_t *d_counts, void *stream) {
     if (int rc = gather_common(h, d_aips, n, 1)) return rc;
     if (h->G.g > 65535) return fail(VATE_EINVAL, "vate_age_counts needs g <= 65535");
+    if (h->G.atw != 1u) return fail(VATE_EINVAL, "vate_age_counts needs k <= 63 (byte ATs)");
     if (n && !d_counts) return fail(VATE_EINVAL, "d_counts is NULL");
     cudaError_t e = vate::launch_age_counts(h->G, h->bact0, d_aips, n, d_counts, (cudaStream_t)stream, h->sms);
     if (e != cudaSuccess) return cuda_fail(e, "age-count launch");
@@ -408,7 +411,8 @@ int vate_copy_pool(vate_handle *h, uint8_t *d_dst, void *stream) {
     if (int rc = check_handle(h)) return rc;
     if (!d_dst) return fail(VATE_EINVAL, "d_dst is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    CU(cudaMemcpyAsync(d_dst, h->G.pool, h->G.P, cudaMemcpyDeviceToDevice, st), "pool copy");
+    if ((reinterpret_cast<uintptr_t>(d_dst) & (h->G.atw - 1u)) != 0) return fail(VATE_EINVAL, "d_dst must be 2-byte aligned");
+    CU(cudaMemcpyAsync(d_dst, h->G.pool, h->G.P * h->G.atw, cudaMemcpyDeviceToDevice, st), "pool copy");
     if (h->G.frame0) CU(vate::launch_frame_convert(h->G, d_dst, d_dst, 0, h->G.P, true, st, h->sms), "pool convert");
     return VATE_OK;
 }
@@ -417,6 +421,7 @@ int vate_load_pool(vate_handle *h, const uint8_t *d_src, void *stream) {
     if (int rc = check_handle(h)) return rc;
     if (!d_src) return fail(VATE_EINVAL, "d_src is NULL");
     cudaStream_t st = (cudaStream_t)stream;
+    if ((reinterpret_cast<uintptr_t>(d_src) & (h->G.atw - 1u)) != 0) return fail(VATE_EINVAL, "d_src must be 2-byte aligned");
     CU(vate::launch_frame_convert(h->G, d_src, h->G.pool, 0, h->G.P, false, st, h->sms), "pool load");
     return VATE_OK;
 }
@@ -517,14 +522,14 @@ extern "C" {
 int vate_checkpoint_size(const vate_handle *h, uint64_t *bytes) {
     if (int rc = check_handle(h)) return rc;
     if (!bytes) return fail(VATE_EINVAL, "bytes is NULL");
-    *bytes = image_bytes(h->G.twok, h->G.P);
+    *bytes = image_bytes(h->G.twok, h->G.P * h->G.atw);
     return VATE_OK;
 }
 
 int vate_checkpoint(vate_handle *h, void *h_buf, uint64_t bytes, void *stream) {
     if (int rc = check_handle(h)) return rc;
     if (!h_buf) return fail(VATE_EINVAL, "h_buf is NULL");
-    const uint64_t need = image_bytes(h->G.twok, h->G.P);
+    const uint64_t need = image_bytes(h->G.twok, h->G.P * h->G.atw);
     if (bytes < need) return fail(VATE_EINVAL, "checkpoint buffer holds %llu bytes, %llu needed",
                                   (unsigned long long)bytes, (unsigned long long)need);
     uint8_t *img = static_cast<uint8_t *>(h_buf);
@@ -538,7 +543,7 @@ int vate_checkpoint(vate_handle *h, void *h_buf, uint64_t bytes, void *stream) {
     hd.bact0 = h->bact0;
     hd.closed = h->closed ? 1u : 0u;
     hd.hist_bytes = (uint64_t)(h->G.twok + 1) * sizeof(uint64_t);
-    hd.pool_bytes = h->G.P;
+    hd.pool_bytes = h->G.P * h->G.atw;
     uint8_t *hist = img + sizeof hd, *pool = hist + hd.hist_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     CU(cudaMemcpyAsync(hist, h->d_hist, hd.hist_bytes, cudaMemcpyDeviceToHost, st), "census D2H");
@@ -551,7 +556,8 @@ int vate_checkpoint(vate_handle *h, void *h_buf, uint64_t bytes, void *stream) {
         CU(cudaStreamWaitEvent(st, h->ev_free[0], 0), "wait");
         for (uint64_t off = 0; off < hd.pool_bytes; off += piece) {
             const uint64_t n = hd.pool_bytes - off < piece ? hd.pool_bytes - off : piece;
-            CU(vate::launch_frame_convert(h->G, h->G.pool + off, stage, off, n, true, st, h->sms), "pool convert");
+            CU(vate::launch_frame_convert(h->G, h->G.pool + off, stage, off / h->G.atw, n / h->G.atw, true, st,
+                                          h->sms), "pool convert");
             CU(cudaMemcpyAsync(pool + off, stage, n, cudaMemcpyDeviceToHost, st), "pool D2H");
             CU(cudaStreamSynchronize(st), "checkpoint");
         }
@@ -579,9 +585,9 @@ int vate_restore(const void *h_buf, uint64_t bytes, void *stream, vate_handle **
                     hd.header_bytes);
     Geom G;
     if (int rc = make_geom(&hd.params, &G)) return rc;
-    if (hd.pool_bytes != G.P || hd.hist_bytes != (uint64_t)(G.twok + 1) * sizeof(uint64_t))
+    if (hd.pool_bytes != G.P * G.atw || hd.hist_bytes != (uint64_t)(G.twok + 1) * sizeof(uint64_t))
         return fail(VATE_EINVAL, "checkpoint sizes do not match its parameters");
-    const uint64_t need = image_bytes(G.twok, G.P);
+    const uint64_t need = image_bytes(G.twok, G.P * G.atw);
     if (bytes < need)
         return fail(VATE_EINVAL, "checkpoint image truncated: %llu of %llu bytes", (unsigned long long)bytes,
                     (unsigned long long)need);
@@ -592,14 +598,22 @@ int vate_restore(const void *h_buf, uint64_t bytes, void *stream, vate_handle **
     if (f.h != hd.checksum) return fail(VATE_EINVAL, "checkpoint checksum mismatch");
     // AT values beyond the counter's range would index past the census bins
     const uint8_t *hist = img + sizeof hd, *pool = hist + hd.hist_bytes;
-    const uint8_t vmax = (uint8_t)(G.counter == VATE_COUNTER_DR ? G.k : G.twok);
-    uint8_t worst = 0;
-    for (uint64_t i = 0; i < G.P; i++) worst = pool[i] > worst ? pool[i] : worst;
+    const uint32_t vmax = G.counter == VATE_COUNTER_DR ? G.k : G.twok;
+    uint32_t worst = 0;
+    if (G.atw == 1u) {
+        for (uint64_t i = 0; i < G.P; i++) worst = pool[i] > worst ? pool[i] : worst;
+    } else {
+        for (uint64_t i = 0; i < G.P; i++) {
+            uint16_t v;
+            std::memcpy(&v, pool + 2 * i, 2);
+            worst = v > worst ? v : worst;
+        }
+    }
     if (worst > vmax) return fail(VATE_EINVAL, "checkpoint pool holds the value %u, above %u", worst, vmax);
     vate_handle *h = nullptr;
     if (int rc = vate_create(&hd.params, stream, &h)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(h->G.pool, pool, G.P, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(h->G.pool, pool, G.P * G.atw, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && h->G.frame0)          // the image holds the paper's form
         e = vate::launch_frame_convert(h->G, h->G.pool, h->G.pool, 0, G.P, false, st, h->sms);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_hist, hist, hd.hist_bytes, cudaMemcpyHostToDevice, st);

@@ -46,6 +46,7 @@ struct Geom {
     uint32_t counter;    // 0: asynchronous timestamps; 1: distance recorders
     uint32_t frame0;     // 1: timestamps stored in the frame of block 0 (every handle and group pool);
                          // 0: the paper's per-block values (pools handed in by a caller)
+    uint32_t atw;        // bytes per AT: 1 for k <= 63, 2 (uint16) for 64 <= k <= 1023
     // host side only: L2 access-policy window over the pool for every launch
     // that touches it (l2_window_bytes = 0: none)
     uint64_t l2_window_bytes;
@@ -238,6 +239,45 @@ VATE_HD uint32_t preserve_at(uint32_t v, uint32_t act, uint32_t k) {
     if (act == 0u && v <= k) return twok;
     if (act == k && ((v >= k && v <= twok - 1u) || v == 0u)) return twok;
     return v;
+}
+
+// ---- 16-bit ATs (k >= 64): two per 32-bit word, bit 15 of each half free ----
+constexpr uint32_t ONES16 = 0x00010001u;
+constexpr uint32_t HIGH16 = 0x80008000u;
+
+// range_consts for 16-bit lanes (values <= 2k <= 2046)
+VATE_HD RangeConsts range_consts16(uint32_t act, uint32_t kprime, uint32_t twok) {
+    RangeConsts rc;
+    int lo = (int)act - (int)kprime + 1;
+    uint32_t rlo, rhi;
+    if (lo >= 0) {
+        rlo = (uint32_t)lo;
+        rhi = act;
+        rc.f = 0u;
+    } else {
+        rlo = act + 1u;
+        rhi = act + twok - kprime;
+        rc.f = HIGH16;
+    }
+    rc.a1 = (0x8000u - rlo) * ONES16;
+    rc.b1 = (0x7FFFu - rhi) * ONES16;
+    rc.pad = 0u;
+    return rc;
+}
+
+VATE_HD RangeConsts dr_range_consts16(uint32_t kprime) {
+    RangeConsts rc;
+    rc.a1 = 0x8000u * ONES16;
+    rc.b1 = (0x7FFFu - (kprime - 1u)) * ONES16;
+    rc.f = 0u;
+    rc.pad = 0u;
+    return rc;
+}
+
+// bit 15 set in each half of w holding an active AT; c2k = (0x8000 - 2k) * ONES16
+VATE_HD uint32_t swar16_active(uint32_t w, const RangeConsts &rc, uint32_t c2k) {
+    uint32_t r = ((w + rc.a1) & ~(w + rc.b1)) ^ rc.f;
+    return r & ~(w + c2k) & HIGH16;
 }
 
 // ---- frame 0 ---------------------------------------------------------------

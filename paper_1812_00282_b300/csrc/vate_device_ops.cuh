@@ -103,31 +103,32 @@ __device__ __forceinline__ uint64_t pool_inactive(const uint64_t *hist, uint64_t
 }
 
 // Active VATs seen by this lane for one host of a frame-0 pool (warp per
-// host, L = 16 << CPSL): in each round the 32 lanes hash 32 consecutive
-// segments; the segments' 16-byte chunks are then read by consecutive lanes
-// (for L = 32, lanes 2j and 2j+1 read the two halves of one 32-byte sector),
-// the segment base coming from the hashing lane by shuffle.  All RB * CPS
-// loads of a batch are issued before any is tested.  FULL: the number of
-// segments is a multiple of 32 * RB.  Every AT is tested with the same range
-// constants rc (CheckAT with ACT = BACT^0, or CheckDR), so no block is looked
-// up.  Active ATs are counted per byte lane in a SWAR accumulator (at most
-// RB * CPS * 4 <= 32 per byte lane per batch), folded after each batch.
-// u1..u3 are run-time ones.
-template <int CPSL, int RB, bool FULL>
+// host; a segment of L ATs of W bytes each spans 16 << CPSL bytes): in each
+// round the 32 lanes hash 32 consecutive segments; the segments' 16-byte
+// chunks are then read by consecutive lanes (for byte ATs and L = 32, lanes
+// 2j and 2j+1 read the two halves of one 32-byte sector), the segment base
+// coming from the hashing lane by shuffle.  All RB * CPS loads of a batch are
+// issued before any is tested.  FULL: the number of segments is a multiple of
+// 32 * RB.  Every AT is tested with the same range constants rc (CheckAT with
+// ACT = BACT^0, or CheckDR), so no block is looked up.  Active ATs are counted
+// per lane of the SWAR word (4 bytes or 2 halves) in an accumulator folded
+// after each batch.  u1..u3 are run-time ones.
+template <int CPSL, int RB, bool FULL, int W = 1>
 __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, const RangeConsts &rc, uint32_t c2k, uint32_t aip,
                                                     uint32_t u1, uint32_t u2, uint32_t u3, uint32_t lane) {
     constexpr int CPS = 1 << CPSL;                      // 16-byte chunks per segment
     constexpr int NL = RB * CPS;                        // loads per lane per batch
+    constexpr uint32_t ATS_PER_CHUNK_LOG2 = W == 1 ? 4 : 3;
     const uint32_t nseg = G.g >> G.log2L;              // segments per host
     const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
     uint32_t cnt = 0;
     const uint64_t hk = host_key(G, aip);
     for (uint32_t r0 = 0; r0 < nseg; r0 += 32u * RB) {
-        uint32_t base[RB];
+        uint32_t base[RB];                              // first chunk of the segment
 #pragma unroll
         for (int rb = 0; rb < RB; rb++) {
             uint32_t s = r0 + 32u * rb + lane;
-            base[rb] = (FULL || s < nseg) ? seg_base_k(G, hk, s) : 0u;
+            base[rb] = (FULL || s < nseg) ? (seg_base_k(G, hk, s) >> ATS_PER_CHUNK_LOG2) : 0u;
         }
         uint4 w[NL];
         bool valid[NL];
@@ -139,30 +140,45 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, const RangeCo
                 const int j = rb * CPS + it;
                 uint32_t c = it * 32u + lane;
                 uint32_t src = (c >> CPSL) & 31u;
-                uint32_t pid = __shfl_sync(0xFFFFFFFFu, base[rb], src) + ((c & (CPS - 1u)) << 4);
+                uint32_t q = __shfl_sync(0xFFFFFFFFu, base[rb], src) + (c & (CPS - 1u));
                 valid[j] = FULL || c < (segs_here << CPSL);
                 w[j] = make_uint4(0u, 0u, 0u, 0u);
-                if (valid[j]) w[j] = __ldg(pool16 + (pid >> 4));
+                if (valid[j]) w[j] = __ldg(pool16 + q);
             }
         }
         uint32_t acc = 0;
 #pragma unroll
         for (int j = 0; j < NL; j++) {
             if (!valid[j]) continue;
-            // (m >> 7) added as a multiply-high by 2^25 (multiply-add pipe)
-            acc = __umulhi(swar_active_fma(w[j].x, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-            acc = __umulhi(swar_active_fma(w[j].y, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-            acc = __umulhi(swar_active_fma(w[j].z, rc, c2k, u1, u2, u3), 1u << 25) + acc;
-            acc = __umulhi(swar_active_fma(w[j].w, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+            if (W == 1) {
+                // (m >> 7) added as a multiply-high by 2^25 (multiply-add pipe)
+                acc = __umulhi(swar_active_fma(w[j].x, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                acc = __umulhi(swar_active_fma(w[j].y, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                acc = __umulhi(swar_active_fma(w[j].z, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+                acc = __umulhi(swar_active_fma(w[j].w, rc, c2k, u1, u2, u3), 1u << 25) + acc;
+            } else {
+                acc = __umulhi(swar16_active(w[j].x, rc, c2k), 1u << 17) + acc;
+                acc = __umulhi(swar16_active(w[j].y, rc, c2k), 1u << 17) + acc;
+                acc = __umulhi(swar16_active(w[j].z, rc, c2k), 1u << 17) + acc;
+                acc = __umulhi(swar16_active(w[j].w, rc, c2k), 1u << 17) + acc;
+            }
         }
-        uint32_t t = (acc & 0x00FF00FFu) + ((acc >> 8) & 0x00FF00FFu);
-        cnt += (t & 0xFFFFu) + (t >> 16);
+        if (W == 1) {
+            uint32_t t = (acc & 0x00FF00FFu) + ((acc >> 8) & 0x00FF00FFu);
+            cnt += (t & 0xFFFFu) + (t >> 16);
+        } else {
+            cnt += (acc & 0xFFFFu) + (acc >> 16);
+        }
     }
     return cnt;
 }
 
-// Active VATs seen by this lane for one host of a frame-0 pool, one byte per
-// VAT (any L).
+// Active VATs seen by this lane for one host of a frame-0 pool, one AT per
+// load (any L).
+__device__ __forceinline__ uint32_t load_at(const Geom &G, uint32_t pid) {
+    return G.atw == 1u ? (uint32_t)__ldg(G.pool + pid) : (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(G.pool) + pid);
+}
+
 __device__ __forceinline__ uint32_t gather_host_scalar(const Geom &G, uint32_t bact0, uint32_t kprime, uint32_t aip,
                                                        uint32_t lane) {
     uint32_t cnt = 0;
@@ -170,7 +186,7 @@ __device__ __forceinline__ uint32_t gather_host_scalar(const Geom &G, uint32_t b
 #pragma unroll 4
     for (uint32_t i = lane; i < G.g; i += 32u) {
         uint32_t pid = vat_pid_k(G, hk, i);
-        uint32_t v = __ldg(G.pool + pid);
+        uint32_t v = load_at(G, pid);
         if (G.counter == 1u) {
             cnt += check_dr(v, kprime) ? 1u : 0u;
             continue;

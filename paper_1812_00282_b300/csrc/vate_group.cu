@@ -429,6 +429,10 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
             delete g;
             return vate::set_error(VATE_EINVAL, "groups run asynchronous timestamps (counter 0)");
         }
+        if (g->geoms[m].atw != 1u) {
+            delete g;
+            return vate::set_error(VATE_EINVAL, "groups hold byte ATs (k <= 63)");
+        }
         if (m && params[m].seg_len != params[0].seg_len) {
             delete g;
             return vate::set_error(VATE_EINVAL, "all monitors of a group must use the same seg_len");

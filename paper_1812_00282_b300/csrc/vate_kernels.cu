@@ -29,12 +29,12 @@
 namespace vate {
 
 // --------------------------------------------------------------------------
-// InitAT: every AT becomes 2k.
+// InitAT: every AT becomes 2k (a distance recorder k).
 // --------------------------------------------------------------------------
-__global__ void init_pool_kernel(uint8_t *__restrict__ pool, uint64_t P, uint32_t twok) {
+__global__ void init_pool_kernel(uint8_t *__restrict__ pool, uint64_t nbytes, uint32_t pat) {
     uint4 v;
-    v.x = v.y = v.z = v.w = twok * ONES;
-    uint64_t n16 = P >> 4;   // P is a power of two >= 4096
+    v.x = v.y = v.z = v.w = pat;   // the inactive value in every AT of the word
+    uint64_t n16 = nbytes >> 4;    // P * AT width, a multiple of 4096
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n16;
          i += (uint64_t)gridDim.x * blockDim.x)
         reinterpret_cast<uint4 *>(pool)[i] = v;
@@ -48,7 +48,11 @@ __global__ void init_pool_kernel(uint8_t *__restrict__ pool, uint64_t P, uint32_
 __device__ __forceinline__ void set_at(const Geom &G, uint32_t bact0, uint32_t aip, uint32_t bip) {
     uint32_t vid = bh(G, bip);
     uint32_t pid = vat_pid(G, aip, vid);
-    G.pool[pid] = (uint8_t)(G.counter == 1u ? 0u : bact0);
+    uint32_t v = G.counter == 1u ? 0u : bact0;
+    if (G.atw == 1u)
+        G.pool[pid] = (uint8_t)v;
+    else
+        reinterpret_cast<uint16_t *>(G.pool)[pid] = (uint16_t)v;
 }
 
 __global__ void __launch_bounds__(256) ingest_kernel(Geom G, uint32_t bact0, const uint32_t *__restrict__ pairs,
@@ -89,26 +93,32 @@ __global__ void __launch_bounds__(256) preserve_kernel(uint8_t *__restrict__ poo
 }
 
 // --------------------------------------------------------------------------
-// Frame 0 <-> the paper's per-block values, for n bytes of pool positions
-// pid0 .. pid0 + n - 1 (src and dst may be the same buffer; any alignment).
-// Distance recorders are copied, values above k clamped to k.
-// 16 bytes per thread; the block is looked up once unless the 16 straddle a
+// Frame 0 <-> the paper's per-block values, for the n ATs of pool positions
+// pid0 .. pid0 + n - 1 (src and dst may be the same buffer; aligned to the AT
+// width).  Distance recorders are copied, values above k clamped to k.
+// 16 ATs per thread; the block is looked up once unless the 16 straddle a
 // block boundary.
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) frame_convert_kernel(Geom G, const uint8_t *src, uint8_t *dst, uint64_t pid0,
                                                             uint64_t n, int to_paper) {
     const uint64_t nq = (n + 15) >> 4;
+    const uint32_t W = G.atw;
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nq; q += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t o0 = q << 4, o1 = min(o0 + 16, n);
         const uint32_t b0 = block_of(G, (uint32_t)(pid0 + o0));
         const bool one = b0 == block_of(G, (uint32_t)(pid0 + o1 - 1));
         for (uint64_t o = o0; o < o1; o++) {
             const uint32_t blk = one ? b0 : block_of(G, (uint32_t)(pid0 + o));
-            const uint32_t x = src[o];
+            const uint32_t x = W == 1u ? (uint32_t)src[o] : (uint32_t)reinterpret_cast<const uint16_t *>(src)[o];
+            uint32_t y;
             if (G.counter == 1u)          // distance recorders have one frame; out-of-range values become inactive
-                dst[o] = (uint8_t)min(x, G.k);
+                y = min(x, G.k);
             else
-                dst[o] = (uint8_t)(to_paper ? to_canonical(x, blk, G.twok) : from_canonical(x, blk, G.twok));
+                y = to_paper ? to_canonical(x, blk, G.twok) : from_canonical(x, blk, G.twok);
+            if (W == 1u)
+                dst[o] = (uint8_t)y;
+            else
+                reinterpret_cast<uint16_t *>(dst)[o] = (uint16_t)y;
         }
     }
 }
@@ -130,6 +140,122 @@ __global__ void __launch_bounds__(256) dr_age_kernel(uint8_t *__restrict__ pool,
         w.w = swar_dr_age(w.w, k);
         p[i] = w;
     }
+}
+
+// --------------------------------------------------------------------------
+// 16-bit ATs (k >= 64): PreserveAT in frame 0 and the recorders' slide, eight
+// ATs per 16-byte chunk, one scalar step per AT (both are bound by memory).
+// Chunks cover the AT positions [s0, e0) and [s1, e1); positions outside both
+// are left alone.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) preserve16_kernel(uint16_t *__restrict__ pool, uint32_t B, uint32_t k,
+                                                         uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1) {
+    uint64_t c0s = s0 >> 3, c0e = (e0 + 7) >> 3;
+    uint64_t c1s = s1 >> 3, c1e = (e1 + 7) >> 3;
+    uint64_t n0 = (e0 > s0) ? c0e - c0s : 0;
+    uint64_t n1 = (e1 > s1) ? c1e - c1s : 0;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n0 + n1;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t chunk = t < n0 ? c0s + t : c1s + (t - n0);
+        if (t >= n0 && n0 && chunk >= c0s && chunk < c0e) continue;   // enumerated by range 0
+        uint4 *p = reinterpret_cast<uint4 *>(pool) + chunk;
+        uint4 w = *p;
+        uint32_t words[4] = {w.x, w.y, w.z, w.w};
+        bool changed = false;
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            uint64_t pos = (chunk << 3) + e;
+            if (!((pos >= s0 && pos < e0) || (pos >= s1 && pos < e1))) continue;
+            uint32_t sh = 16 * (e & 1);
+            uint32_t u = (words[e >> 1] >> sh) & 0xFFFFu;
+            uint32_t nu = preserve_frame0(u, B, k);
+            if (nu != u) {
+                words[e >> 1] = (words[e >> 1] & ~(0xFFFFu << sh)) | (nu << sh);
+                changed = true;
+            }
+        }
+        if (changed) *p = make_uint4(words[0], words[1], words[2], words[3]);
+    }
+}
+
+__global__ void __launch_bounds__(256) dr_age16_kernel(uint16_t *__restrict__ pool, uint64_t P, uint32_t k) {
+    const uint32_t pat = k * ONES16;
+    uint4 *p = reinterpret_cast<uint4 *>(pool);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (P >> 3); i += (uint64_t)gridDim.x * blockDim.x) {
+        uint4 w = p[i];
+        if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) continue;   // all inactive already
+        uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            uint32_t lo = words[q] & 0xFFFFu, hi = words[q] >> 16;
+            lo = lo < k ? lo + 1u : k;
+            hi = hi < k ? hi + 1u : k;
+            words[q] = lo | (hi << 16);
+        }
+        p[i] = make_uint4(words[0], words[1], words[2], words[3]);
+    }
+}
+
+// Census of a 16-bit pool (k >= 64): one shared histogram per block (2k + 1
+// bins, shared-memory atomics; inactive ATs are counted in a register), the
+// same block rows and last-block reduction as census_kernel.
+__global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ partial,
+                                                                  uint64_t *__restrict__ hist,
+                                                                  unsigned int *__restrict__ ticket) {
+    extern __shared__ uint32_t hsh[];   // [nbins]
+    const uint32_t nbins = G.twok + 1u;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) hsh[i] = 0;
+    __syncthreads();
+    const uint32_t inact = G.counter == 1u ? G.k : G.twok;
+    const uint32_t pat = inact * ONES16;
+    uint32_t inactive = 0;
+    const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < (G.P >> 3); q += (uint64_t)gridDim.x * blockDim.x) {
+        uint4 w = __ldcg(pool16 + q);
+        if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
+            inactive += 8u;
+            continue;
+        }
+        uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            uint32_t v = (words[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+            if (v >= inact) {
+                inactive++;
+                continue;
+            }
+            uint32_t d = v;                               // a recorder's value is its distance
+            if (G.counter != 1u) {                        // frame 0: ACT = BACT^0 for every AT
+                d = bact0 + G.twok - v;
+                if (d >= G.twok) d -= G.twok;
+            }
+            atomicAdd(&hsh[d], 1u);
+        }
+    }
+    inactive = __reduce_add_sync(0xFFFFFFFFu, inactive);
+    if (lane == 0) atomicAdd(&hsh[G.twok], inactive);
+    __syncthreads();
+    for (uint32_t bin = threadIdx.x; bin < nbins; bin += blockDim.x)
+        partial[(uint64_t)blockIdx.x * nbins + bin] = hsh[bin];
+    __threadfence();
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1u);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
+        uint64_t s = 0;
+        for (uint32_t blk = lane; blk < gridDim.x; blk += 32u) s += __ldcg(partial + (uint64_t)blk * nbins + bin);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+        if (lane == 0) hist[bin] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // --------------------------------------------------------------------------
@@ -229,7 +355,7 @@ __device__ __forceinline__ void write_result(const Geom &G, uint64_t N0, uint64_
 #ifndef VATE_GATHER_MINB
 #define VATE_GATHER_MINB 5
 #endif
-template <int MODE, int CPSL, int RB, bool FULL>
+template <int MODE, int CPSL, int RB, bool FULL, int W>
 __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_kernel(Geom G, uint32_t bact0, uint32_t kprime,
                                                                     const uint64_t *__restrict__ hist,
                                                                     const uint32_t *__restrict__ aips, uint64_t n,
@@ -239,11 +365,13 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
                                                                     uint32_t u2, uint32_t u3) {
     __shared__ uint64_t sN0;
     // one CheckAT for every AT of the frame-0 pool (ACT = BACT^0), or CheckDR
-    const RangeConsts rc = G.counter == 1u ? dr_range_consts(kprime) : range_consts(bact0, kprime, G.twok);
+    const RangeConsts rc = W == 1 ? (G.counter == 1u ? dr_range_consts(kprime) : range_consts(bact0, kprime, G.twok))
+                                  : (G.counter == 1u ? dr_range_consts16(kprime)
+                                                     : range_consts16(bact0, kprime, G.twok));
     if (MODE == GATHER_ESTIMATE && threadIdx.x == 0) sN0 = pool_inactive(hist, G.P, kprime);
     __syncthreads();
     const uint64_t N0 = (MODE == GATHER_ESTIMATE) ? sN0 : 0;
-    const uint32_t c2k = (128u - G.twok) * ONES;
+    const uint32_t c2k = W == 1 ? (128u - G.twok) * ONES : (0x8000u - G.twok) * ONES16;
 
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -260,7 +388,7 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
         for (uint32_t j = 0; j < 32u; j++) {
             if (g0 + (uint64_t)j * nwarps >= n) break;
             const uint32_t aip = __shfl_sync(0xFFFFFFFFu, my_aip, j);
-            uint32_t cnt = gather_host_vec<CPSL, RB, FULL>(G, rc, c2k, aip, u1, u2, u3, lane);
+            uint32_t cnt = gather_host_vec<CPSL, RB, FULL, W>(G, rc, c2k, aip, u1, u2, u3, lane);
             uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
             if (lane == j) my_A = A;
         }
@@ -342,8 +470,10 @@ static int grid_for(uint64_t work_items, int threads, int max_blocks) {
 
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms) {
     // InitAT: 2k; a distance recorder starts at k (inactive)
-    return launch_pool(G, init_pool_kernel, grid_for(G.P >> 4, 256, sms * 8), 256, 0, st, G.pool, G.P,
-                       G.counter == 1u ? G.k : G.twok);
+    const uint32_t v = G.counter == 1u ? G.k : G.twok;
+    const uint64_t nbytes = G.P * G.atw;
+    return launch_pool(G, init_pool_kernel, grid_for(nbytes >> 4, 256, sms * 8), 256, 0, st, G.pool, nbytes,
+                       G.atw == 1u ? v * ONES : v * ONES16);
 }
 
 cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, uint64_t n, cudaStream_t st, int sms) {
@@ -360,11 +490,19 @@ cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, 
 }
 
 cudaError_t launch_dr_age(const Geom &G, cudaStream_t st, int sms) {
+    if (G.atw == 2u)
+        return launch_pool(G, dr_age16_kernel, grid_for(G.P >> 3, 256, sms * 8), 256, 0, st,
+                           reinterpret_cast<uint16_t *>(G.pool), G.P, G.k);
     return launch_pool(G, dr_age_kernel, grid_for(G.P >> 4, 256, sms * 8), 256, 0, st, G.pool, G.P, G.k);
 }
 
 cudaError_t launch_preserve(const Geom &G, uint32_t bact0, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
                             cudaStream_t st, int sms) {
+    if (G.atw == 2u) {
+        uint64_t chunks = ((e0 - s0) >> 3) + ((e1 - s1) >> 3) + 4;
+        return launch_pool(G, preserve16_kernel, grid_for(chunks, 256, sms * 8), 256, 0, st,
+                           reinterpret_cast<uint16_t *>(G.pool), bact0, G.k, s0, e0, s1, e1);
+    }
     uint64_t chunks = ((e0 - s0) >> 4) + ((e1 - s1) >> 4) + 4;
     return launch_pool(G, preserve_kernel, grid_for(chunks, 256, sms * 8), 256, 0, st, G.pool,
                        preserve_consts_frame0(bact0, G.k), G.twok, s0, e0, s1, e1);
@@ -387,6 +525,9 @@ cudaError_t census_prepare(uint32_t twok) {
 
 cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,
                           unsigned int *ticket, cudaStream_t st) {
+    if (G.atw == 2u)
+        return launch_pool(G, census16_kernel, grid, CENSUS_THREADS, (size_t)(G.twok + 1) * sizeof(uint32_t), st, G,
+                           bact0, partial, hist, ticket);
     return launch_pool(G, census_kernel, grid, CENSUS_THREADS, census_smem_bytes(G.twok), st, G, bact0, partial, hist,
                        ticket);
 }
@@ -398,36 +539,44 @@ cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kpri
     int warps_per_block = GATHER_THREADS / 32;
     int grid = grid_for(n, warps_per_block, sms * 64);
     cudaError_t e = cudaSuccess;
-    if (G.L >= 16) {
+    const uint32_t seg_bytes = G.L * G.atw;
+    if (seg_bytes >= 16) {
         const uint32_t nseg = G.g >> G.log2L;
         const uint32_t rounds = (nseg + 31u) / 32u;
-#define VATE_GATHER_LAUNCH(CPSL, RB, FULL)                                                                        \
+#define VATE_GATHER_LAUNCH(CPSL, RB, FULL, W)                                                                     \
     do {                                                                                                          \
         if (mode == GATHER_ESTIMATE)                                                                              \
-            e = launch_pool(G, gather_vec_kernel<GATHER_ESTIMATE, CPSL, RB, FULL>, grid, GATHER_THREADS, 0, st, G,  \
-                            bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);                        \
+            e = launch_pool(G, gather_vec_kernel<GATHER_ESTIMATE, CPSL, RB, FULL, W>, grid, GATHER_THREADS, 0, st, \
+                            G, bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);                     \
         else                                                                                                      \
-            e = launch_pool(G, gather_vec_kernel<GATHER_ACTIVE, CPSL, RB, FULL>, grid, GATHER_THREADS, 0, st, G,    \
-                            bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);                        \
+            e = launch_pool(G, gather_vec_kernel<GATHER_ACTIVE, CPSL, RB, FULL, W>, grid, GATHER_THREADS, 0, st,   \
+                            G, bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);                     \
     } while (0)
-#define VATE_GATHER_VEC(CPSL, RB)                                                                                 \
+#define VATE_GATHER_VEC(CPSL, RB, W)                                                                              \
     do {                                                                                                          \
-        if (nseg % (32u * RB) == 0) VATE_GATHER_LAUNCH(CPSL, RB, true);                                           \
-        else VATE_GATHER_LAUNCH(CPSL, RB, false);                                                                 \
+        if (nseg % (32u * RB) == 0) VATE_GATHER_LAUNCH(CPSL, RB, true, W);                                        \
+        else VATE_GATHER_LAUNCH(CPSL, RB, false, W);                                                              \
     } while (0)
         // batches of up to 8 loads per lane: RB rounds x 2^CPSL chunks
 #ifndef VATE_GATHER_RB
 #define VATE_GATHER_RB 2
 #endif
-        if (G.L == 16) {
-            if (rounds >= 2) VATE_GATHER_VEC(0, VATE_GATHER_RB);
-            else VATE_GATHER_VEC(0, 1);
-        } else if (G.L == 32) {
-            if (rounds >= 2) VATE_GATHER_VEC(1, VATE_GATHER_RB);
-            else VATE_GATHER_VEC(1, 1);
-        } else {
-            if (rounds >= 2) VATE_GATHER_VEC(2, VATE_GATHER_RB);
-            else VATE_GATHER_VEC(2, 1);
+        if (G.atw == 1u) {
+            if (seg_bytes == 16) {
+                if (rounds >= 2) VATE_GATHER_VEC(0, VATE_GATHER_RB, 1);
+                else VATE_GATHER_VEC(0, 1, 1);
+            } else if (seg_bytes == 32) {
+                if (rounds >= 2) VATE_GATHER_VEC(1, VATE_GATHER_RB, 1);
+                else VATE_GATHER_VEC(1, 1, 1);
+            } else {
+                if (rounds >= 2) VATE_GATHER_VEC(2, VATE_GATHER_RB, 1);
+                else VATE_GATHER_VEC(2, 1, 1);
+            }
+        } else {                       // 16-bit ATs: one round per batch (a segment is 16-128 bytes)
+            if (seg_bytes == 16) VATE_GATHER_VEC(0, 1, 2);
+            else if (seg_bytes == 32) VATE_GATHER_VEC(1, 1, 2);
+            else if (seg_bytes == 64) VATE_GATHER_VEC(2, 1, 2);
+            else VATE_GATHER_VEC(3, 1, 2);
         }
 #undef VATE_GATHER_LAUNCH
 #undef VATE_GATHER_VEC

@@ -258,14 +258,20 @@ def vate_census(h, hist, stream=None) -> None:
                                     "hist", 2 * k + 1), _stream(stream)))
 
 
-def vate_copy_pool(h, dst, stream=None) -> None:
+def pool_dtype(k: int):
+    """torch dtype of a pool copy: uint8 ATs for k <= 63, 16-bit ones (int16 in torch) beyond."""
     import torch
-    _check(_lib.vate_copy_pool(h, _dev(dst, torch.uint8, "dst"), _stream(stream)))
+    return torch.uint8 if k <= 63 else torch.int16
+
+
+def vate_copy_pool(h, dst, stream=None) -> None:
+    n = vate_get_info(h).pool_size
+    _check(_lib.vate_copy_pool(h, _dev(dst, pool_dtype(vate_get_info_k(h)), "dst", n), _stream(stream)))
 
 
 def vate_load_pool(h, src, stream=None) -> None:
-    import torch
-    _check(_lib.vate_load_pool(h, _dev(src, torch.uint8, "src"), _stream(stream)))
+    n = vate_get_info(h).pool_size
+    _check(_lib.vate_load_pool(h, _dev(src, pool_dtype(vate_get_info_k(h)), "src", n), _stream(stream)))
 
 
 def vate_ingest_host(h, pairs, slice: int, stream=None) -> None:

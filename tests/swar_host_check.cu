@@ -92,6 +92,29 @@ int main() {
                         }
         }
     }
+    // 16-bit ATs (k >= 64): CheckAT and CheckDR on two values per word
+    const uint32_t wide[] = {64, 100, 300, 1023};
+    for (uint32_t k : wide) {
+        uint32_t twok = 2 * k, c2k = (0x8000u - twok) * ONES16;
+        for (uint32_t act = 0; act < twok; act += (k > 100 ? 7 : 1)) {
+            for (uint32_t kp = 1; kp <= k; kp += (k > 100 ? 13 : 1)) {
+                RangeConsts rc = range_consts16(act, kp, twok), dc = dr_range_consts16(kp);
+                for (int trial = 0; trial < 24; trial++) {
+                    uint32_t v0 = rnd() % (twok + 1), v1 = rnd() % (twok + 1);
+                    if (trial < 4) { v0 = trial & 1 ? twok : act; v1 = trial & 2 ? 0u : twok - 1u; }
+                    uint32_t w = v0 | (v1 << 16);
+                    uint32_t m = swar16_active(w, rc, c2k), d = swar16_active(w, dc, c2k);
+                    bool g0 = (m >> 15) & 1u, g1 = (m >> 31) & 1u;
+                    if (g0 != check_at(v0, act, kp, twok) || g1 != check_at(v1, act, kp, twok) ||
+                        (((d >> 15) & 1u) != 0) != (v0 < kp && v0 <= k) || (((d >> 31) & 1u) != 0) != (v1 < kp && v1 <= k)) {
+                        printf("FAIL swar16 k=%u act=%u k'=%u v=%u,%u\n", k, act, kp, v0, v1);
+                        return 1;
+                    }
+                    checked++;
+                }
+            }
+        }
+    }
     printf("OK %ld words\n", checked);
     return 0;
 }

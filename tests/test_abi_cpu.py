@@ -44,7 +44,8 @@ def test_library_exports_every_declared_symbol(V):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(log2_pool=11), dict(log2_pool=33), dict(k=0), dict(k=64), dict(g=0), dict(g=65537),
+    dict(log2_pool=11), dict(log2_pool=33), dict(k=0), dict(k=1024), dict(g=0), dict(g=65537),
+    dict(log2_pool=14, k=300),                                   # blocks of fewer than 32 ATs
     dict(seg_len=3), dict(seg_len=128), dict(g=1000, seg_len=32), dict(partition=2),
 ])
 def test_invalid_parameters_rejected_on_host(V, bad):

@@ -32,7 +32,7 @@ def dev_u32(a):
 def state(V, d, hosts, kps):
     """Everything a caller can observe of a closed handle."""
     info = d.info()
-    pool = torch.empty(d.P, dtype=torch.uint8, device="cuda")
+    pool = torch.empty(d.P, dtype=V.pool_dtype(d.k), device="cuda")
     d.copy_pool(pool)
     hist = torch.empty(2 * d.k + 1, dtype=torch.int64, device="cuda")
     d.census(hist)
@@ -126,3 +126,27 @@ def test_checkpoint_image_describes_the_handle(V):
         V.Vate.restore(bad)
     assert e.value.code == V.VATE_EINVAL and "checksum" in V.vate_last_error()
     d.close()
+
+
+def test_wide_resume_continues_bit_exactly(V):
+    c, k, g, L, seed = 18, 150, 512, 32, 0x77
+    tr = Traffic(SMALL, pkts_per_slice=4000)
+    hosts = tr.aips[:500]
+    ref = V.Vate(c, k, g, L, 0, seed)
+    cur = V.Vate(c, k, g, L, 0, seed)
+    ids = [0, 1, 2, 100, 149, 150, 151, 300, 301, 302, 460]
+    for j, sid in enumerate(ids):
+        dp = torch.from_numpy(tr.slice_pairs(sid % 64).view(np.int32)).cuda()
+        ref.ingest(dp, sid)
+        cur.ingest(dp, sid)
+        ref.close_slice(sid)
+        cur.close_slice(sid)
+        if j in (2, 6):
+            img = cur.checkpoint()
+            assert img.size == 88 + (2 * k + 1) * 8 + 2 * (1 << c)
+            cur.close()
+            cur = V.Vate.restore(img)
+        a, b = state(V, ref, hosts, (1, k)), state(V, cur, hosts, (1, k))
+        assert_same(a, b, "slice %d" % sid)
+    ref.close()
+    cur.close()

@@ -400,6 +400,31 @@ def test_pool_equals_timestamp_closed_form_with_collisions(L, partition):
         np.testing.assert_array_equal(hist.astype(np.int64), expect)
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("c,k,every", [(16, 100, 5), (19, 300, 17)])
+def test_wide_timestamps_equal_closed_form(c, k, every):
+    # k beyond one byte (values up to 2k = 600, the paper's k' = 300 of Sec. 5):
+    # the pool still equals the closed form of the last-set shadow, through
+    # more than one full 2k cycle of every block's ACT.
+    o = Oracle(c=c, k=k, g=64, seg_len=1, partition=0, seed=k)
+    rng = np.random.default_rng(k)
+    hosts, slices = _small_stream(o, 2 * k + 3, 400, 30, rng)
+    block = np.array([o.block(p) for p in range(o.P)], np.int64)
+    last = np.full(o.P, -1, np.int64)
+    for t, arr in enumerate(slices):
+        if t > 0:
+            o.advance()
+        o.ingest(arr)
+        last[o.pids_of_pairs(arr).astype(np.int64)] = t
+        if t % every == 0 or t >= 2 * k:
+            pool = o.pool().astype(np.int64)
+            assert pool.max() <= 2 * k
+            np.testing.assert_array_equal(pool, _closed_form_pool(last, block, t, k), err_msg="t=%d" % t)
+    for kp in (1, k // 2, k):
+        for h in hosts[:10]:
+            assert o.active_vats(int(h), kp) == o.active_vats_dr(int(h), kp)
+
+
 def test_vate_equals_vdre():
     # Sec. 5: with the same mapping, VATE (AT pool) and VDRE (DR pool aged every
     # slice) give identical estimates.

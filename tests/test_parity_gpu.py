@@ -43,9 +43,9 @@ def compare_close(V, d, o, hosts, kps, check_pool=True, check_ages=True):
     """Compare device handle d (a Vate) and oracle o at a closed slice."""
     k = o.k
     if check_pool:
-        pool = torch.empty(o.P, dtype=torch.uint8, device="cuda")
+        pool = torch.empty(o.P, dtype=V.pool_dtype(k), device="cuda")
         d.copy_pool(pool)
-        dp = pool.cpu().numpy()
+        dp = pool.cpu().numpy().astype(np.int64)
         op = o.pool()
         if not np.array_equal(dp, op):
             bad = np.nonzero(dp != op)[0]
@@ -321,3 +321,90 @@ def test_distance_recorders_match_oracle_and_timestamps(V, L):
             np.testing.assert_array_equal(a1.cpu().numpy().view(np.uint32), oa)
     dr.close()
     at.close()
+
+
+# ---- 16-bit ATs (64 <= k <= 1023; the paper's k' = 300 of Sec. 5) ----------
+WIDE = [
+    (17, 100, 1024, 32, 0, 31),     # 64-byte segments
+    (19, 300, 1024, 32, 0, 32),     # the paper's k' = 300
+    (17, 64, 512, 8, 1, 33),        # 16-byte segments, low-deviation partition
+    (17, 80, 512, 16, 0, 34),       # 32-byte segments
+    (18, 70, 1024, 64, 0, 35),      # 128-byte segments
+    (17, 100, 256, 1, 0, 36),       # one AT per load
+]
+
+
+@pytest.mark.parametrize("params", WIDE, ids=lambda p: "c%d-k%d-L%d-p%d" % (p[0], p[1], p[3], p[4]))
+def test_wide_timestamps_parity(V, params):
+    c, k, g, L, part, seed = params
+    tr = Traffic(SMALL, pkts_per_slice=4000)
+    # runs of consecutive slices with gaps, past 2k so that every block is maintained at ACT 0 and k
+    ids = sorted(set(list(range(0, 6)) + list(range(k - 3, k + 4)) + list(range(2 * k - 2, 2 * k + 5))
+                     + [3 * k + 1, 5 * k + 7, 5 * k + 8]))
+    slices = [tr.slice_pairs(i % 64) for i in ids]
+    run_stream(V, params, slices, tr.aips[:700], kps=(1, k // 3, k), slice_ids=ids, check_ages=False)
+
+
+@pytest.mark.parametrize("L", [1, 32])
+def test_wide_distance_recorders_match_oracle(V, L):
+    tr = Traffic(SMALL, pkts_per_slice=5000)
+    k, c, g = 120, 18, 512
+    dr = V.Vate(c, k, g, L, 0, 41, counter=V.VATE_COUNTER_DR)
+    at = V.Vate(c, k, g, L, 0, 41)
+    o = Oracle(c=c, k=k, g=g, seg_len=L, partition=0, seed=41)
+    hosts = tr.aips[:600]
+    dh = dev_u32(hosts)
+    ids = [0, 1, 2, 60, 119, 120, 121, 125, 240, 241]
+    prev = None
+    for sid in ids:
+        if prev is not None:
+            for _ in range(sid - prev):
+                o.advance()
+        prev = sid
+        p = tr.slice_pairs(sid % 64)
+        o.ingest(p)
+        for d in (dr, at):
+            d.ingest(dev_pairs(p), sid)
+            d.close_slice(sid)
+        pool = torch.empty(o.P, dtype=torch.int16, device="cuda")
+        dr.copy_pool(pool)
+        np.testing.assert_array_equal(pool.cpu().numpy().astype(np.uint16), o.dr())
+        h_dr = torch.empty(2 * k + 1, dtype=torch.int64, device="cuda")
+        h_at = torch.empty_like(h_dr)
+        dr.census(h_dr)
+        at.census(h_at)
+        a, b = h_dr.cpu().numpy(), h_at.cpu().numpy()
+        np.testing.assert_array_equal(a[:k], b[:k])
+        assert a[k:2 * k].sum() == 0 and a[2 * k] == b[k:].sum()
+        for kp in (1, 7, k):
+            e1 = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+            e2 = torch.empty_like(e1)
+            a1 = torch.empty(len(hosts), dtype=torch.int32, device="cuda")
+            dr.estimate(dh, kp, e1)
+            at.estimate(dh, kp, e2)
+            dr.active_counts(dh, kp, a1)
+            assert torch.equal(e1, e2)
+            _, oa, _ = o.estimate(hosts, kp)
+            np.testing.assert_array_equal(a1.cpu().numpy().view(np.uint32), oa)
+    dr.close()
+    at.close()
+
+
+def test_wide_pool_load_and_age_counts_limits(V):
+    d = V.Vate(17, 100, 512, 32, 0, 3)
+    tr = Traffic(SMALL, pkts_per_slice=3000)
+    d.ingest(dev_pairs(tr.slice_pairs(0)), 0)
+    d.close_slice(0)
+    pool = torch.empty(d.P, dtype=torch.int16, device="cuda")
+    d.copy_pool(pool)
+    d2 = V.Vate(17, 100, 512, 32, 0, 3)
+    d2.ingest(torch.zeros(0, 2, dtype=torch.int32, device="cuda"), 0)
+    d2.load_pool(pool)                              # the paper's form round-trips
+    back = torch.empty_like(pool)
+    d2.copy_pool(back)
+    assert torch.equal(back, pool)
+    with pytest.raises(V.VateError) as e:
+        d.age_counts(dev_u32(tr.aips[:4]), torch.empty(400, dtype=torch.int16, device="cuda"))
+    assert e.value.code == V.VATE_EINVAL
+    d.close()
+    d2.close()
