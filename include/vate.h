@@ -115,6 +115,7 @@ typedef struct {
     int64_t  slice;          /* current slice, -1 before the first call       */
     uint32_t bact0;          /* BACT^0 of the current slice (Eq. 7)           */
     uint32_t closed;         /* 1 when the current slice has been closed      */
+    uint64_t pid_lo, pid_hi; /* positions held: [0, P), or a shard's range    */
 } vate_info;
 
 typedef struct vate_handle vate_handle;

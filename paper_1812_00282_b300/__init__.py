@@ -11,7 +11,7 @@ import importlib
 _BINDING = "paper_1812_00282_b300.vate"
 
 
-_SUBMODULES = ("build", "vate", "learned", "serving")
+_SUBMODULES = ("build", "vate", "learned", "serving", "sharded")
 
 
 def __getattr__(name):

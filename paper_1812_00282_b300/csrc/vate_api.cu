@@ -9,6 +9,7 @@
 
 #include "vate.h"
 #include "vate_checkpoint.h"
+#include "vate_shard.h"
 #include "vate_internal.h"
 
 using vate::Geom;
@@ -79,6 +80,8 @@ int make_geom(const vate_params *p, Geom *G) {
         G->first = G->a * (twok - G->b);
     }
     if (G->a < 32) return fail(VATE_EINVAL, "blocks must hold at least 32 ATs (a = %llu)", (unsigned long long)G->a);
+    G->lo = 0;
+    G->hi = G->P;
     G->ma = vate::magic_for(G->a);
     G->ma1 = vate::magic_for(G->a + 1);
     return VATE_OK;
@@ -137,6 +140,16 @@ int check_handle(const vate_handle *h) {
     return VATE_OK;
 }
 
+// [s, e) intersected with the positions the handle holds (empty: s = e)
+void clip(const Geom &G, uint64_t *s, uint64_t *e) {
+    uint64_t a = *s > G.lo ? *s : G.lo, b = *e < G.hi ? *e : G.hi;
+    if (a >= b) a = b = G.lo;
+    *s = a;
+    *e = b;
+}
+
+bool is_shard(const vate_handle *h) { return h->G.lo != 0 || h->G.hi != h->G.P; }
+
 // Slide the window until `slice` is the current slice: each step is
 // BACT^0 <- BACT^0 + 1 and PreserveAT on the blocks whose ACT became 0 or k
 // (Algorithm 4, last lines).  After 2k steps with no SetAT every AT is
@@ -164,6 +177,8 @@ int advance_to(vate_handle *h, int64_t slice, cudaStream_t st) {
             uint64_t s0, e0, s1, e1;
             vate::block_range_of(G, i0, &s0, &e0);
             vate::block_range_of(G, i1, &s1, &e1);
+            clip(G, &s0, &e0);                                 // a shard maintains its part of each block
+            clip(G, &s1, &e1);
             e = vate::launch_preserve(G, h->bact0, s0, e0, s1, e1, st, h->sms);
         }
         if (e != cudaSuccess) return cuda_fail(e, "maintenance launch");
@@ -234,11 +249,17 @@ int vate_host_block(const vate_params *params, uint64_t pid, uint32_t *block) {
     return VATE_OK;
 }
 
-int vate_create(const vate_params *params, void *stream, vate_handle **out) {
+// The handle of a whole pool (hi = ~0: up to P) or of the shard that holds
+// the positions [lo, hi).
+static int create_range(const vate_params *params, uint64_t lo, uint64_t hi, void *stream, vate_handle **out) {
     if (!out) return fail(VATE_EINVAL, "out is NULL");
     Geom G;
     int rc = make_geom(params, &G);
     if (rc) return rc;
+    G.lo = lo;
+    G.hi = hi > G.P ? G.P : hi;
+    const uint64_t held_bytes = (G.hi - G.lo) * G.atw;
+
     cudaStream_t st = (cudaStream_t)stream;
     vate_handle *h = new (std::nothrow) vate_handle();
     if (!h) return fail(VATE_ENOMEM, "host allocation failed");
@@ -271,15 +292,16 @@ int vate_create(const vate_params *params, void *stream, vate_handle **out) {
         if (persist_max > 0 && window_max > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
             if (cur < (size_t)persist_max) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist_max);
             cudaGetLastError();
-            const uint64_t pool_bytes = G.P * G.atw;
-            h->G.l2_window_bytes = pool_bytes < (uint64_t)window_max ? pool_bytes : (uint64_t)window_max;
+            h->G.l2_window_bytes = held_bytes < (uint64_t)window_max ? held_bytes : (uint64_t)window_max;
             double ratio = (double)persist_max / (double)h->G.l2_window_bytes;
             h->G.l2_hit_ratio = ratio >= 1.0 ? 1.0f : (float)ratio;
         }
     }
     h->census_grid = h->sms * 4;
     size_t nbins = G.twok + 1;
-    if (cudaMalloc(&h->G.pool, G.P * G.atw) != cudaSuccess || cudaMalloc(&h->d_hist, nbins * sizeof(uint64_t)) != cudaSuccess ||
+    uint8_t *mem = nullptr;
+    if (cudaMalloc(&mem, held_bytes) == cudaSuccess) h->G.pool = mem - G.lo * G.atw;   // position 0's address
+    if (!mem || cudaMalloc(&h->d_hist, nbins * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&h->d_partial, (size_t)h->census_grid * nbins * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&h->d_ticket, sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
@@ -297,6 +319,21 @@ int vate_create(const vate_params *params, void *stream, vate_handle **out) {
     return VATE_OK;
 }
 
+
+int vate_create(const vate_params *params, void *stream, vate_handle **out) {
+    return create_range(params, 0, ~0ull, stream, out);
+}
+
+int vate_create_shard(const vate_params *params, uint64_t pid_lo, uint64_t pid_hi, void *stream, vate_handle **out) {
+    Geom G;
+    if (int rc = make_geom(params, &G)) return rc;
+    if (pid_lo >= pid_hi || pid_hi > G.P || (pid_lo & 63u) != 0 || ((pid_hi & 63u) != 0 && pid_hi != G.P))
+        return fail(VATE_EINVAL, "a shard holds positions [lo, hi) with lo < hi <= P, both multiples of 64 "
+                                 "(got [%llu, %llu), P = %llu)", (unsigned long long)pid_lo,
+                    (unsigned long long)pid_hi, (unsigned long long)G.P);
+    return create_range(params, pid_lo, pid_hi, stream, out);
+}
+
 int vate_destroy(vate_handle *h) {
     if (!h) return VATE_OK;
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
@@ -307,7 +344,7 @@ int vate_destroy(vate_handle *h) {
         cudaCtxResetPersistingL2Cache();
         cudaGetLastError();
     }
-    cudaFree(h->G.pool);
+    if (h->G.pool) cudaFree(vate::pool_mem(h->G));
     cudaFree(h->d_hist);
     cudaFree(h->d_partial);
     cudaFree(h->d_ticket);
@@ -334,6 +371,8 @@ int vate_get_info(const vate_handle *h, vate_info *out) {
     out->slice = h->slice;
     out->bact0 = h->bact0;
     out->closed = h->closed ? 1u : 0u;
+    out->pid_lo = h->G.lo;
+    out->pid_hi = h->G.hi;
     return VATE_OK;
 }
 
@@ -368,9 +407,17 @@ static int gather_common(vate_handle *h, const uint32_t *d_aips, uint64_t n, uin
     return VATE_OK;
 }
 
+static int whole_pool_only(const vate_handle *h, const char *what) {
+    if (is_shard(h))
+        return fail(VATE_EINVAL, "%s needs the whole pool; a shard gives vate_active_counts and vate_census, "
+                                 "summed over the shards and passed to vate_estimate_from_counts", what);
+    return VATE_OK;
+}
+
 int vate_estimate(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint32_t kprime, float *d_out,
                   uint8_t *d_flags, void *stream) {
     if (int rc = gather_common(h, d_aips, n, kprime)) return rc;
+    if (int rc = whole_pool_only(h, "vate_estimate")) return rc;
     if (n && !d_out) return fail(VATE_EINVAL, "d_out is NULL");
     cudaError_t e = vate::launch_gather(vate::GATHER_ESTIMATE, h->G, h->bact0, kprime, h->d_hist, d_aips, n, d_out,
                                         d_flags, nullptr, (cudaStream_t)stream, h->sms);
@@ -392,9 +439,24 @@ int vate_age_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint16_t
     if (int rc = gather_common(h, d_aips, n, 1)) return rc;
     if (h->G.g > 65535) return fail(VATE_EINVAL, "vate_age_counts needs g <= 65535");
     if (h->G.atw != 1u) return fail(VATE_EINVAL, "vate_age_counts needs k <= 63 (byte ATs)");
+    if (int rc = whole_pool_only(h, "vate_age_counts")) return rc;
     if (n && !d_counts) return fail(VATE_EINVAL, "d_counts is NULL");
     cudaError_t e = vate::launch_age_counts(h->G, h->bact0, d_aips, n, d_counts, (cudaStream_t)stream, h->sms);
     if (e != cudaSuccess) return cuda_fail(e, "age-count launch");
+    return VATE_OK;
+}
+
+int vate_estimate_from_counts(const vate_params *params, const uint32_t *d_active, const uint64_t *d_hist, uint64_t n,
+                              uint32_t kprime, float *d_out, uint8_t *d_flags, void *stream) {
+    Geom G;
+    if (int rc = make_geom(params, &G)) return rc;
+    if (kprime < 1 || kprime > G.k) return fail(VATE_EINVAL, "kprime must be in [1, k=%u], got %u", G.k, kprime);
+    if (!d_hist) return fail(VATE_EINVAL, "d_hist is NULL");
+    if (n && (!d_active || !d_out)) return fail(VATE_EINVAL, "d_active and d_out must not be NULL");
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    CU(vate::launch_estimate_from_counts(G, kprime, d_hist, d_active, n, d_out, d_flags, (cudaStream_t)stream, sms),
+       "estimate launch");
     return VATE_OK;
 }
 
@@ -412,8 +474,9 @@ int vate_copy_pool(vate_handle *h, uint8_t *d_dst, void *stream) {
     if (!d_dst) return fail(VATE_EINVAL, "d_dst is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((reinterpret_cast<uintptr_t>(d_dst) & (h->G.atw - 1u)) != 0) return fail(VATE_EINVAL, "d_dst must be 2-byte aligned");
-    CU(cudaMemcpyAsync(d_dst, h->G.pool, h->G.P * h->G.atw, cudaMemcpyDeviceToDevice, st), "pool copy");
-    if (h->G.frame0) CU(vate::launch_frame_convert(h->G, d_dst, d_dst, 0, h->G.P, true, st, h->sms), "pool convert");
+    const uint64_t n = h->G.hi - h->G.lo;
+    CU(cudaMemcpyAsync(d_dst, vate::pool_mem(h->G), n * h->G.atw, cudaMemcpyDeviceToDevice, st), "pool copy");
+    if (h->G.frame0) CU(vate::launch_frame_convert(h->G, d_dst, d_dst, h->G.lo, n, true, st, h->sms), "pool convert");
     return VATE_OK;
 }
 
@@ -422,7 +485,8 @@ int vate_load_pool(vate_handle *h, const uint8_t *d_src, void *stream) {
     if (!d_src) return fail(VATE_EINVAL, "d_src is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((reinterpret_cast<uintptr_t>(d_src) & (h->G.atw - 1u)) != 0) return fail(VATE_EINVAL, "d_src must be 2-byte aligned");
-    CU(vate::launch_frame_convert(h->G, d_src, h->G.pool, 0, h->G.P, false, st, h->sms), "pool load");
+    CU(vate::launch_frame_convert(h->G, d_src, vate::pool_mem(h->G), h->G.lo, h->G.hi - h->G.lo, false, st, h->sms),
+       "pool load");
     return VATE_OK;
 }
 
@@ -452,6 +516,7 @@ int vate_ingest_host(vate_handle *h, const vate_pair *h_pairs, uint64_t n, int64
 int vate_estimate_host(vate_handle *h, const uint32_t *h_aips, uint64_t n, uint32_t kprime, float *h_out,
                        uint8_t *h_flags, void *stream) {
     if (int rc = gather_common(h, h_aips, n, kprime)) return rc;
+    if (int rc = whole_pool_only(h, "vate_estimate_host")) return rc;
     if (n && !h_out) return fail(VATE_EINVAL, "h_out is NULL");
     if (int rc = ensure_staging(h)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -521,6 +586,7 @@ extern "C" {
 
 int vate_checkpoint_size(const vate_handle *h, uint64_t *bytes) {
     if (int rc = check_handle(h)) return rc;
+    if (int rc = whole_pool_only(h, "a checkpoint")) return rc;
     if (!bytes) return fail(VATE_EINVAL, "bytes is NULL");
     *bytes = image_bytes(h->G.twok, h->G.P * h->G.atw);
     return VATE_OK;
@@ -528,6 +594,7 @@ int vate_checkpoint_size(const vate_handle *h, uint64_t *bytes) {
 
 int vate_checkpoint(vate_handle *h, void *h_buf, uint64_t bytes, void *stream) {
     if (int rc = check_handle(h)) return rc;
+    if (int rc = whole_pool_only(h, "a checkpoint")) return rc;
     if (!h_buf) return fail(VATE_EINVAL, "h_buf is NULL");
     const uint64_t need = image_bytes(h->G.twok, h->G.P * h->G.atw);
     if (bytes < need) return fail(VATE_EINVAL, "checkpoint buffer holds %llu bytes, %llu needed",
@@ -548,7 +615,7 @@ int vate_checkpoint(vate_handle *h, void *h_buf, uint64_t bytes, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     CU(cudaMemcpyAsync(hist, h->d_hist, hd.hist_bytes, cudaMemcpyDeviceToHost, st), "census D2H");
     if (!h->G.frame0) {
-        CU(cudaMemcpyAsync(pool, h->G.pool, hd.pool_bytes, cudaMemcpyDeviceToHost, st), "pool D2H");
+        CU(cudaMemcpyAsync(pool, vate::pool_mem(h->G), hd.pool_bytes, cudaMemcpyDeviceToHost, st), "pool D2H");
     } else {                   // the image holds the paper's form: convert piece by piece through a staging buffer
         if (int rc = ensure_staging(h)) return rc;
         const uint64_t piece = STAGE_RECORDS * sizeof(vate_pair);

@@ -34,7 +34,8 @@ namespace vate {
 
 // Geometry of one AT pool, passed by value to every kernel.
 struct Geom {
-    uint8_t *pool;
+    uint8_t *pool;       // base of pool position 0: pool + pid * atw addresses position pid for lo <= pid < hi
+                         // (a shard's allocation starts at position lo; nothing outside [lo, hi) is touched)
     uint64_t P;          // 2^c ATs
     uint64_t key_h;      // key of H
     uint64_t key_bh;     // key of BH
@@ -47,6 +48,7 @@ struct Geom {
     uint32_t frame0;     // 1: timestamps stored in the frame of block 0 (every handle and group pool);
                          // 0: the paper's per-block values (pools handed in by a caller)
     uint32_t atw;        // bytes per AT: 1 for k <= 63, 2 (uint16) for 64 <= k <= 1023
+    uint64_t lo, hi;     // pool positions held: [0, P) for a whole pool, a 64-aligned range for a shard
     // host side only: L2 access-policy window over the pool for every launch
     // that touches it (l2_window_bytes = 0: none)
     uint64_t l2_window_bytes;
@@ -129,6 +131,9 @@ VATE_HD void block_range_of(const Geom &G, uint32_t i, uint64_t *s, uint64_t *e)
         *e = *s + G.a + 1;
     }
 }
+
+// first byte of the memory that holds positions [lo, hi)
+VATE_HD uint8_t *pool_mem(const Geom &G) { return G.pool + G.lo * G.atw; }
 
 // ACT of block blk when BACT^0 = bact0 (Eq. 8)
 VATE_HD uint32_t act_of_block(uint32_t bact0, uint32_t blk, uint32_t twok) {

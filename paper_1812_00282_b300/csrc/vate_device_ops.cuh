@@ -113,7 +113,9 @@ __device__ __forceinline__ uint64_t pool_inactive(const uint64_t *hist, uint64_t
 // ACT = BACT^0, or CheckDR), so no block is looked up.  Active ATs are counted
 // per lane of the SWAR word (4 bytes or 2 halves) in an accumulator folded
 // after each batch.  u1..u3 are run-time ones.
-template <int CPSL, int RB, bool FULL, int W = 1>
+// SHARD: the pool holds only the positions [lo, hi) (64-aligned, so a
+// segment is wholly inside or outside); segments outside are not read.
+template <int CPSL, int RB, bool FULL, int W = 1, bool SHARD = false>
 __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, const RangeConsts &rc, uint32_t c2k, uint32_t aip,
                                                     uint32_t u1, uint32_t u2, uint32_t u3, uint32_t lane) {
     constexpr int CPS = 1 << CPSL;                      // 16-byte chunks per segment
@@ -123,6 +125,7 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, const RangeCo
     const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
     uint32_t cnt = 0;
     const uint64_t hk = host_key(G, aip);
+    const uint32_t q_lo = (uint32_t)((G.lo * W) >> 4), q_n = (uint32_t)(((G.hi - G.lo) * W) >> 4);
     for (uint32_t r0 = 0; r0 < nseg; r0 += 32u * RB) {
         uint32_t base[RB];                              // first chunk of the segment
 #pragma unroll
@@ -142,6 +145,7 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, const RangeCo
                 uint32_t src = (c >> CPSL) & 31u;
                 uint32_t q = __shfl_sync(0xFFFFFFFFu, base[rb], src) + (c & (CPS - 1u));
                 valid[j] = FULL || c < (segs_here << CPSL);
+                if (SHARD) valid[j] = valid[j] && (q - q_lo) < q_n;
                 w[j] = make_uint4(0u, 0u, 0u, 0u);
                 if (valid[j]) w[j] = __ldg(pool16 + q);
             }
@@ -186,6 +190,7 @@ __device__ __forceinline__ uint32_t gather_host_scalar(const Geom &G, uint32_t b
 #pragma unroll 4
     for (uint32_t i = lane; i < G.g; i += 32u) {
         uint32_t pid = vat_pid_k(G, hk, i);
+        if (pid < G.lo || pid >= G.hi) continue;             // another shard's AT
         uint32_t v = load_at(G, pid);
         if (G.counter == 1u) {
             cnt += check_dr(v, kprime) ? 1u : 0u;

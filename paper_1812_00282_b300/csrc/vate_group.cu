@@ -718,6 +718,8 @@ int vate_group_monitor_info(vate_group *g, uint32_t m, vate_info *out, void *str
     out->slice = s.started ? (int64_t)s.step : -1;
     out->bact0 = (uint32_t)(s.step % G.twok);
     out->closed = s.started ? 1u : 0u;
+    out->pid_lo = 0;
+    out->pid_hi = G.P;
     return VATE_OK;
 }
 

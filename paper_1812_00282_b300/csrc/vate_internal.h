@@ -44,6 +44,9 @@ cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kpri
                           const uint32_t *aips, uint64_t n, float *out, uint8_t *flags, uint32_t *active,
                           cudaStream_t st, int sms);
 cudaError_t age_prepare(uint32_t k);
+// Eq. 11 from active counts and a census (both summed over the shards of one pool)
+cudaError_t launch_estimate_from_counts(const Geom &G, uint32_t kprime, const uint64_t *hist, const uint32_t *active,
+                                        uint64_t n, float *out, uint8_t *flags, cudaStream_t st, int sms);
 cudaError_t launch_age_counts(const Geom &G, uint32_t bact0, const uint32_t *aips, uint64_t n, uint16_t *counts,
                               cudaStream_t st, int sms);
 

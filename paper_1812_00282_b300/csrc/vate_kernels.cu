@@ -48,6 +48,7 @@ __global__ void init_pool_kernel(uint8_t *__restrict__ pool, uint64_t nbytes, ui
 __device__ __forceinline__ void set_at(const Geom &G, uint32_t bact0, uint32_t aip, uint32_t bip) {
     uint32_t vid = bh(G, bip);
     uint32_t pid = vat_pid(G, aip, vid);
+    if (pid < G.lo || pid >= G.hi) return;              // another shard's AT
     uint32_t v = G.counter == 1u ? 0u : bact0;
     if (G.atw == 1u)
         G.pool[pid] = (uint8_t)v;
@@ -211,7 +212,8 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32
     const uint32_t pat = inact * ONES16;
     uint32_t inactive = 0;
     const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
-    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < (G.P >> 3); q += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t q = (G.lo >> 3) + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < (G.hi >> 3);
+         q += (uint64_t)gridDim.x * blockDim.x) {
         uint4 w = __ldcg(pool16 + q);
         if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
             inactive += 8u;
@@ -280,10 +282,10 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
 
     const uint32_t pat = (G.counter == 1u ? G.k : G.twok) * ONES;   // 16 inactive counters
     uint32_t inactive_runs = 0;   // chunks of 16 inactive ATs
-    const uint64_t n16 = G.P >> 4;
+    const uint64_t n16 = G.hi >> 4;                         // chunks of the positions held, [lo, hi)
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
-    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n16; q += 2 * stride) {
+    for (uint64_t q = (G.lo >> 4) + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n16; q += 2 * stride) {
         uint64_t q2 = q + stride;
         uint4 w0 = __ldcg(pool16 + q);
         uint4 w1 = make_uint4(pat, pat, pat, pat);
@@ -355,7 +357,7 @@ __device__ __forceinline__ void write_result(const Geom &G, uint64_t N0, uint64_
 #ifndef VATE_GATHER_MINB
 #define VATE_GATHER_MINB 5
 #endif
-template <int MODE, int CPSL, int RB, bool FULL, int W>
+template <int MODE, int CPSL, int RB, bool FULL, int W, bool SHARD>
 __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_kernel(Geom G, uint32_t bact0, uint32_t kprime,
                                                                     const uint64_t *__restrict__ hist,
                                                                     const uint32_t *__restrict__ aips, uint64_t n,
@@ -388,11 +390,27 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
         for (uint32_t j = 0; j < 32u; j++) {
             if (g0 + (uint64_t)j * nwarps >= n) break;
             const uint32_t aip = __shfl_sync(0xFFFFFFFFu, my_aip, j);
-            uint32_t cnt = gather_host_vec<CPSL, RB, FULL, W>(G, rc, c2k, aip, u1, u2, u3, lane);
+            uint32_t cnt = gather_host_vec<CPSL, RB, FULL, W, SHARD>(G, rc, c2k, aip, u1, u2, u3, lane);
             uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
             if (lane == j) my_A = A;
         }
         if (mine < n) write_result<MODE>(G, N0, mine, my_A, out, flags, active);
+    }
+}
+
+// Eq. 11 from counts: A per host and the pool census, each summed over the
+// shards that hold one pool.
+__global__ void __launch_bounds__(256) estimate_from_counts_kernel(uint32_t g, uint64_t P, uint32_t kprime,
+                                                                   const uint64_t *__restrict__ hist,
+                                                                   const uint32_t *__restrict__ active, uint64_t n,
+                                                                   float *__restrict__ out, uint8_t *__restrict__ flags) {
+    __shared__ uint64_t sN0;
+    if (threadIdx.x == 0) sN0 = pool_inactive(hist, P, kprime);
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint8_t f;
+        out[i] = estimate_eq11(g, P, sN0, active[i], f);
+        if (flags) flags[i] = f;
     }
 }
 
@@ -471,8 +489,8 @@ static int grid_for(uint64_t work_items, int threads, int max_blocks) {
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms) {
     // InitAT: 2k; a distance recorder starts at k (inactive)
     const uint32_t v = G.counter == 1u ? G.k : G.twok;
-    const uint64_t nbytes = G.P * G.atw;
-    return launch_pool(G, init_pool_kernel, grid_for(nbytes >> 4, 256, sms * 8), 256, 0, st, G.pool, nbytes,
+    const uint64_t nbytes = (G.hi - G.lo) * G.atw;
+    return launch_pool(G, init_pool_kernel, grid_for(nbytes >> 4, 256, sms * 8), 256, 0, st, pool_mem(G), nbytes,
                        G.atw == 1u ? v * ONES : v * ONES16);
 }
 
@@ -490,10 +508,11 @@ cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, 
 }
 
 cudaError_t launch_dr_age(const Geom &G, cudaStream_t st, int sms) {
+    const uint64_t n = G.hi - G.lo;                         // the recorders held
     if (G.atw == 2u)
-        return launch_pool(G, dr_age16_kernel, grid_for(G.P >> 3, 256, sms * 8), 256, 0, st,
-                           reinterpret_cast<uint16_t *>(G.pool), G.P, G.k);
-    return launch_pool(G, dr_age_kernel, grid_for(G.P >> 4, 256, sms * 8), 256, 0, st, G.pool, G.P, G.k);
+        return launch_pool(G, dr_age16_kernel, grid_for(n >> 3, 256, sms * 8), 256, 0, st,
+                           reinterpret_cast<uint16_t *>(pool_mem(G)), n, G.k);
+    return launch_pool(G, dr_age_kernel, grid_for(n >> 4, 256, sms * 8), 256, 0, st, pool_mem(G), n, G.k);
 }
 
 cudaError_t launch_preserve(const Geom &G, uint32_t bact0, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
@@ -540,17 +559,23 @@ cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kpri
     int grid = grid_for(n, warps_per_block, sms * 64);
     cudaError_t e = cudaSuccess;
     const uint32_t seg_bytes = G.L * G.atw;
+    // a shard only counts active VATs (its estimates come from counts summed over the shards)
+    const bool sharded = G.lo != 0 || G.hi != G.P;
+    if (sharded && mode == GATHER_ESTIMATE) return cudaErrorInvalidValue;
     if (seg_bytes >= 16) {
         const uint32_t nseg = G.g >> G.log2L;
         const uint32_t rounds = (nseg + 31u) / 32u;
 #define VATE_GATHER_LAUNCH(CPSL, RB, FULL, W)                                                                     \
     do {                                                                                                          \
-        if (mode == GATHER_ESTIMATE)                                                                              \
-            e = launch_pool(G, gather_vec_kernel<GATHER_ESTIMATE, CPSL, RB, FULL, W>, grid, GATHER_THREADS, 0, st, \
-                            G, bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);                     \
+        if (sharded)                                                                                              \
+            e = launch_pool(G, gather_vec_kernel<GATHER_ACTIVE, CPSL, RB, FULL, W, true>, grid, GATHER_THREADS, 0, \
+                            st, G, bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);                 \
+        else if (mode == GATHER_ESTIMATE)                                                                         \
+            e = launch_pool(G, gather_vec_kernel<GATHER_ESTIMATE, CPSL, RB, FULL, W, false>, grid, GATHER_THREADS, \
+                            0, st, G, bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);              \
         else                                                                                                      \
-            e = launch_pool(G, gather_vec_kernel<GATHER_ACTIVE, CPSL, RB, FULL, W>, grid, GATHER_THREADS, 0, st,   \
-                            G, bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);                     \
+            e = launch_pool(G, gather_vec_kernel<GATHER_ACTIVE, CPSL, RB, FULL, W, false>, grid, GATHER_THREADS,   \
+                            0, st, G, bact0, kprime, hist, aips, n, out, flags, active, 1u, 1u, 1u);              \
     } while (0)
 #define VATE_GATHER_VEC(CPSL, RB, W)                                                                              \
     do {                                                                                                          \
@@ -589,6 +614,14 @@ cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kpri
                             aips, n, out, flags, active);
     }
     return e;
+}
+
+cudaError_t launch_estimate_from_counts(const Geom &G, uint32_t kprime, const uint64_t *hist, const uint32_t *active,
+                                        uint64_t n, float *out, uint8_t *flags, cudaStream_t st, int sms) {
+    if (n == 0) return cudaSuccess;
+    estimate_from_counts_kernel<<<grid_for(n, 256, sms * 8), 256, 0, st>>>(G.g, G.P, kprime, hist, active, n, out, flags);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t age_prepare(uint32_t k) {

@@ -22,7 +22,7 @@ inline cudaError_t launch_pool(const Geom &G, void (*kernel)(KArgs...), dim3 gri
     cudaLaunchAttribute attr[1];
     if (G.l2_window_bytes) {
         attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-        attr[0].val.accessPolicyWindow.base_ptr = G.pool;
+        attr[0].val.accessPolicyWindow.base_ptr = pool_mem(G);
         attr[0].val.accessPolicyWindow.num_bytes = G.l2_window_bytes;
         attr[0].val.accessPolicyWindow.hitRatio = G.l2_hit_ratio;
         attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;

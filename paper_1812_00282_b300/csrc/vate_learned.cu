@@ -356,6 +356,7 @@ int check_learned_handle(const vate_handle *h, HandleView *v) {
     if (!v->closed) return set_error(VATE_ESLICE, "the current slice has not been closed");
     if (v->G.k > 15) return set_error(VATE_EINVAL, "the learned estimator needs k <= 15 (2k + 2 <= 32 inputs)");
     if (v->G.counter != VATE_COUNTER_AT) return set_error(VATE_EINVAL, "the learned estimator runs on asynchronous timestamps");
+    if (v->G.lo != 0 || v->G.hi != v->G.P) return set_error(VATE_EINVAL, "the learned estimator needs the whole pool");
     return VATE_OK;
 }
 

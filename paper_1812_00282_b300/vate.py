@@ -38,7 +38,8 @@ class vate_params(C.Structure):
 
 class vate_info(C.Structure):
     _fields_ = [("pool_size", C.c_uint64), ("block_a", C.c_uint64), ("block_b", C.c_uint64),
-                ("slice", C.c_int64), ("bact0", C.c_uint32), ("closed", C.c_uint32)]
+                ("slice", C.c_int64), ("bact0", C.c_uint32), ("closed", C.c_uint32),
+                ("pid_lo", C.c_uint64), ("pid_hi", C.c_uint64)]
 
 
 class vate_group_tuning(C.Structure):
@@ -127,6 +128,8 @@ def _load() -> C.CDLL:
         "vate_server_get_stats": (i, [vp, P(vate_server_stats), i]),
         "vate_probe_sector_read": (i, [vp, u64, u64, vp, vp]),
         "vate_probe_byte_write": (i, [vp, u64, u64, vp]),
+        "vate_create_shard": (i, [P(vate_params), u64, u64, vp, P(vp)]),
+        "vate_estimate_from_counts": (i, [P(vate_params), vp, vp, u64, u32, vp, vp, vp]),
         "vate_checkpoint_size": (i, [vp, P(u64)]),
         "vate_checkpoint": (i, [vp, vp, u64, vp]),
         "vate_restore": (i, [vp, u64, vp, P(vp)]),
@@ -265,12 +268,14 @@ def pool_dtype(k: int):
 
 
 def vate_copy_pool(h, dst, stream=None) -> None:
-    n = vate_get_info(h).pool_size
+    info = vate_get_info(h)
+    n = info.pid_hi - info.pid_lo
     _check(_lib.vate_copy_pool(h, _dev(dst, pool_dtype(vate_get_info_k(h)), "dst", n), _stream(stream)))
 
 
 def vate_load_pool(h, src, stream=None) -> None:
-    n = vate_get_info(h).pool_size
+    info = vate_get_info(h)
+    n = info.pid_hi - info.pid_lo
     _check(_lib.vate_load_pool(h, _dev(src, pool_dtype(vate_get_info_k(h)), "src", n), _stream(stream)))
 
 
@@ -609,6 +614,22 @@ def vate_server_get_stats(s, reset: bool = False) -> vate_server_stats:
     st = vate_server_stats()
     _check(_lib.vate_server_get_stats(s, C.byref(st), 1 if reset else 0))
     return st
+
+
+def vate_create_shard(params: vate_params, pid_lo: int, pid_hi: int, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(_lib.vate_create_shard(C.byref(params), pid_lo, pid_hi, _stream(stream), C.byref(h)))
+    _k_of[h.value] = int(params.k)
+    return h
+
+
+def vate_estimate_from_counts(params: vate_params, active, hist, kprime: int, out, flags=None, stream=None) -> None:
+    import torch
+    n = active.numel()
+    _check(_lib.vate_estimate_from_counts(
+        C.byref(params), _dev(active, torch.int32, "active"), _dev(hist, torch.int64, "hist", 2 * params.k + 1), n,
+        kprime, _dev(out, torch.float32, "out", n), _dev(flags, torch.uint8, "flags", n) if flags is not None else None,
+        _stream(stream)))
 
 
 VATE_CHECKPOINT_MAGIC, VATE_CHECKPOINT_VERSION = 0x31544B4345544156, 1
