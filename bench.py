@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seg-len", type=int, default=32)
     ap.add_argument("--partition", type=int, default=0)
+    ap.add_argument("--at-bits", type=int, default=0,
+                    help="0: one byte per AT; b: the packed layout with b-bit fields (memory against speed)")
     ap.add_argument("--aips", type=int, default=1 << 20, help="hosts estimated per slice")
     ap.add_argument("--pkts", type=int, default=5_000_000, help="packets per slice")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -251,7 +253,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
 
     peaks = probe_peaks(V, torch, 1 << C)
-    mon = V.Vate(C, K_WIN, G, args.seg_len, args.partition, seed=0xC2 + rank)
+    mon = V.Vate(C, K_WIN, G, args.seg_len, args.partition, seed=0xC2 + rank, at_bits=args.at_bits)
 
     def step(s):
         mon.ingest(pairs[s], s)
@@ -317,6 +319,7 @@ def run_ours(args, rank, world, local):
         "dtype": "u8", "data": "synthetic",
         "config": {"workload": WORKLOAD, "aips": n_h, "pkts_per_slice": args.pkts, "k": K_WIN, "kprime": K_WIN,
                    "log2_pool": C, "g": G, "seg_len": args.seg_len, "partition": args.partition,
+                   "at_bits": args.at_bits or 8,
                    "link_gbps_equivalent": round(args.pkts * MEAN_PKT_BYTES * 8 / 1e9, 2),
                    "l2": "flushed before every timed step (256 MiB write, outside the step events); the 64 MiB "
                          "AT pool is state kept from slice to slice and its kernels mark it L2-persisting"
@@ -403,7 +406,7 @@ def run_e2e(args, V, torch, tr, dt, rank, world):
     hosts = dt.hosts()[: args.aips].cpu().pin_memory()
     out = torch.empty(hosts.numel(), dtype=torch.float32).pin_memory()
     fl = torch.empty(hosts.numel(), dtype=torch.uint8).pin_memory()
-    mon = V.Vate(C, K_WIN, G, args.seg_len, args.partition, seed=0xE2E + rank)
+    mon = V.Vate(C, K_WIN, G, args.seg_len, args.partition, seed=0xE2E + rank, at_bits=args.at_bits)
     st = torch.cuda.current_stream()
 
     def step(s):

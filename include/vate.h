@@ -85,6 +85,16 @@ typedef struct {
  *              the whole pool each slice (Sec. 1; the VDRE of Sec. 5).  Both
  *              give the same active sets, censuses and estimates; they differ
  *              in the maintenance work per slide.
+ *   at_bits    0: one byte per AT for k <= 63, two beyond (the fast layout).
+ *              b with ceil(log2(2k+1)) <= b <= 16: the paper's packed layout
+ *              (Sec. 4.2) -- floor(32/b) b-bit fields per 32-bit word, no field
+ *              across words (5.33 bits per AT for k = 10, 10.67 for k = 300);
+ *              b = 8 and b = 16 are the byte and 16-bit layouts themselves.
+ *              A packed pool takes SetAT as two atomic bit operations per
+ *              pair and reads one field per VAT: less memory, more time.
+ *              Packed pools serve the handle API; shards, groups, per-age
+ *              counts and the learned estimator need b = 8 or 16.
+ *   reserved   0.
  *   seed       keys the hash functions H and BH.
  * The hash functions (Sec. 4.1 leaves them open):
  *   mix(x)    = SplitMix64 output function (Steele, Lea & Flood 2014)
@@ -101,6 +111,8 @@ typedef struct {
     uint32_t seg_len;
     uint32_t partition;
     uint32_t counter;    /* VATE_COUNTER_AT (0) or VATE_COUNTER_DR (1) */
+    uint32_t at_bits;    /* 0: byte / 16-bit ATs by k; else packed b-bit fields */
+    uint32_t reserved;   /* 0 */
     uint64_t seed;
 } vate_params;
 

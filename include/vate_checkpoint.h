@@ -15,7 +15,8 @@
  *   vate_checkpoint_header   (fixed size, header_bytes)
  *   uint64_t hist[2k+1]      census of the last close (zeros before any close)
  *   pool[2^c]                AT values in the paper's form, pool position
- *                            order: uint8 for k <= 63, uint16 beyond
+ *                            order: uint8 for k <= 63, uint16 beyond (also
+ *                            for a packed pool, whose image is unpacked)
  * The checksum is FNV-1a (64-bit, Fowler/Noll/Vo) taken over the whole image
  * 8 bytes at a time with the checksum field read as zero.
  */
@@ -30,7 +31,7 @@ extern "C" {
 #endif
 
 #define VATE_CHECKPOINT_MAGIC   0x31544B4345544156ull   /* "VATECKT1" read as a little-endian uint64 */
-#define VATE_CHECKPOINT_VERSION 1u
+#define VATE_CHECKPOINT_VERSION 2u
 
 typedef struct {
     uint64_t   magic;          /* VATE_CHECKPOINT_MAGIC                                   */

@@ -66,6 +66,19 @@ int make_geom(const vate_params *p, Geom *G) {
     G->partition = p->partition;
     G->counter = p->counter;
     G->atw = p->k <= 63 ? 1u : 2u;             // byte ATs up to k = 63, 16-bit ones beyond
+    if (p->reserved != 0) return fail(VATE_EINVAL, "params.reserved must be 0");
+    if (p->at_bits != 0) {
+        uint32_t bmin = 1;
+        while ((1u << bmin) < 2 * p->k + 1) bmin++;          // ceil(log2(2k + 1))
+        if (p->at_bits < bmin || p->at_bits > 16)
+            return fail(VATE_EINVAL, "at_bits must be 0 or in [%u, 16] for k = %u, got %u", bmin, p->k, p->at_bits);
+        const bool natural = (p->at_bits == 8 && p->k <= 63) || (p->at_bits == 16 && p->k >= 64);
+        if (!natural) {                          // the paper's packed layout (vate_packed.cu)
+            G->packed = 1;
+            G->atb = p->at_bits;
+            G->pn = 32 / p->at_bits;
+        }
+    }
     G->P = 1ull << p->log2_pool;
     G->key_h = vate::mix64(p->seed + 1);
     G->key_bh = vate::mix64(p->seed + 2);
@@ -83,6 +96,7 @@ int make_geom(const vate_params *p, Geom *G) {
     G->lo = 0;
     G->hi = G->P;
     G->ma = vate::magic_for(G->a);
+    if (G->packed) G->mpn = vate::magic_for(G->pn);
     G->ma1 = vate::magic_for(G->a + 1);
     return VATE_OK;
 }
@@ -258,7 +272,7 @@ static int create_range(const vate_params *params, uint64_t lo, uint64_t hi, voi
     if (rc) return rc;
     G.lo = lo;
     G.hi = hi > G.P ? G.P : hi;
-    const uint64_t held_bytes = (G.hi - G.lo) * G.atw;
+    const uint64_t held_bytes = vate::held_bytes(G);
 
     cudaStream_t st = (cudaStream_t)stream;
     vate_handle *h = new (std::nothrow) vate_handle();
@@ -327,6 +341,7 @@ int vate_create(const vate_params *params, void *stream, vate_handle **out) {
 int vate_create_shard(const vate_params *params, uint64_t pid_lo, uint64_t pid_hi, void *stream, vate_handle **out) {
     Geom G;
     if (int rc = make_geom(params, &G)) return rc;
+    if (G.packed) return fail(VATE_EINVAL, "shards hold byte or 16-bit ATs (at_bits 0, 8 or 16)");
     if (pid_lo >= pid_hi || pid_hi > G.P || (pid_lo & 63u) != 0 || ((pid_hi & 63u) != 0 && pid_hi != G.P))
         return fail(VATE_EINVAL, "a shard holds positions [lo, hi) with lo < hi <= P, both multiples of 64 "
                                  "(got [%llu, %llu), P = %llu)", (unsigned long long)pid_lo,
@@ -438,7 +453,7 @@ int vate_active_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint3
 int vate_age_counts(vate_handle *h, const uint32_t *d_aips, uint64_t n, uint16_t *d_counts, void *stream) {
     if (int rc = gather_common(h, d_aips, n, 1)) return rc;
     if (h->G.g > 65535) return fail(VATE_EINVAL, "vate_age_counts needs g <= 65535");
-    if (h->G.atw != 1u) return fail(VATE_EINVAL, "vate_age_counts needs k <= 63 (byte ATs)");
+    if (h->G.atw != 1u || h->G.packed) return fail(VATE_EINVAL, "vate_age_counts needs byte ATs (k <= 63, at_bits 0 or 8)");
     if (int rc = whole_pool_only(h, "vate_age_counts")) return rc;
     if (n && !d_counts) return fail(VATE_EINVAL, "d_counts is NULL");
     cudaError_t e = vate::launch_age_counts(h->G, h->bact0, d_aips, n, d_counts, (cudaStream_t)stream, h->sms);
@@ -475,6 +490,10 @@ int vate_copy_pool(vate_handle *h, uint8_t *d_dst, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if ((reinterpret_cast<uintptr_t>(d_dst) & (h->G.atw - 1u)) != 0) return fail(VATE_EINVAL, "d_dst must be 2-byte aligned");
     const uint64_t n = h->G.hi - h->G.lo;
+    if (h->G.packed) {
+        CU(vate::launch_packed_to_paper(h->G, d_dst, 0, n, st, h->sms), "pool copy");
+        return VATE_OK;
+    }
     CU(cudaMemcpyAsync(d_dst, vate::pool_mem(h->G), n * h->G.atw, cudaMemcpyDeviceToDevice, st), "pool copy");
     if (h->G.frame0) CU(vate::launch_frame_convert(h->G, d_dst, d_dst, h->G.lo, n, true, st, h->sms), "pool convert");
     return VATE_OK;
@@ -485,6 +504,10 @@ int vate_load_pool(vate_handle *h, const uint8_t *d_src, void *stream) {
     if (!d_src) return fail(VATE_EINVAL, "d_src is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((reinterpret_cast<uintptr_t>(d_src) & (h->G.atw - 1u)) != 0) return fail(VATE_EINVAL, "d_src must be 2-byte aligned");
+    if (h->G.packed) {
+        CU(vate::launch_paper_to_packed(h->G, d_src, 0, h->G.P, st, h->sms), "pool load");
+        return VATE_OK;
+    }
     CU(vate::launch_frame_convert(h->G, d_src, vate::pool_mem(h->G), h->G.lo, h->G.hi - h->G.lo, false, st, h->sms),
        "pool load");
     return VATE_OK;
@@ -614,18 +637,22 @@ int vate_checkpoint(vate_handle *h, void *h_buf, uint64_t bytes, void *stream) {
     uint8_t *hist = img + sizeof hd, *pool = hist + hd.hist_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     CU(cudaMemcpyAsync(hist, h->d_hist, hd.hist_bytes, cudaMemcpyDeviceToHost, st), "census D2H");
-    if (!h->G.frame0) {
+    if (!h->G.frame0 && !h->G.packed) {
         CU(cudaMemcpyAsync(pool, vate::pool_mem(h->G), hd.pool_bytes, cudaMemcpyDeviceToHost, st), "pool D2H");
     } else {                   // the image holds the paper's form: convert piece by piece through a staging buffer
         if (int rc = ensure_staging(h)) return rc;
-        const uint64_t piece = STAGE_RECORDS * sizeof(vate_pair);
+        const uint32_t w = h->G.atw;
+        const uint64_t piece = STAGE_RECORDS * sizeof(vate_pair) / w;    // positions per piece
         uint8_t *stage = static_cast<uint8_t *>(h->d_stage[0]);
         CU(cudaStreamWaitEvent(st, h->ev_free[0], 0), "wait");
-        for (uint64_t off = 0; off < hd.pool_bytes; off += piece) {
-            const uint64_t n = hd.pool_bytes - off < piece ? hd.pool_bytes - off : piece;
-            CU(vate::launch_frame_convert(h->G, h->G.pool + off, stage, off / h->G.atw, n / h->G.atw, true, st,
-                                          h->sms), "pool convert");
-            CU(cudaMemcpyAsync(pool + off, stage, n, cudaMemcpyDeviceToHost, st), "pool D2H");
+        for (uint64_t pos = 0; pos < h->G.P; pos += piece) {
+            const uint64_t n = h->G.P - pos < piece ? h->G.P - pos : piece;
+            if (h->G.packed)
+                CU(vate::launch_packed_to_paper(h->G, stage, pos, n, st, h->sms), "pool convert");
+            else
+                CU(vate::launch_frame_convert(h->G, h->G.pool + pos * w, stage, pos, n, true, st, h->sms),
+                   "pool convert");
+            CU(cudaMemcpyAsync(pool + pos * w, stage, n * w, cudaMemcpyDeviceToHost, st), "pool D2H");
             CU(cudaStreamSynchronize(st), "checkpoint");
         }
     }
@@ -680,9 +707,25 @@ int vate_restore(const void *h_buf, uint64_t bytes, void *stream, vate_handle **
     vate_handle *h = nullptr;
     if (int rc = vate_create(&hd.params, stream, &h)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(h->G.pool, pool, G.P * G.atw, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && h->G.frame0)          // the image holds the paper's form
-        e = vate::launch_frame_convert(h->G, h->G.pool, h->G.pool, 0, G.P, false, st, h->sms);
+    cudaError_t e = cudaSuccess;
+    if (!h->G.packed) {
+        e = cudaMemcpyAsync(h->G.pool, pool, G.P * G.atw, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && h->G.frame0)      // the image holds the paper's form
+            e = vate::launch_frame_convert(h->G, h->G.pool, h->G.pool, 0, G.P, false, st, h->sms);
+    } else {                                      // pack piece by piece through a staging buffer
+        if (int rc = ensure_staging(h)) {
+            vate_destroy(h);
+            return rc;
+        }
+        const uint64_t piece = STAGE_RECORDS * sizeof(vate_pair) / G.atw / G.pn * G.pn;   // whole words
+        uint8_t *stage = static_cast<uint8_t *>(h->d_stage[0]);
+        for (uint64_t pos = 0; e == cudaSuccess && pos < G.P; pos += piece) {
+            const uint64_t n = G.P - pos < piece ? G.P - pos : piece;
+            e = cudaMemcpyAsync(stage, pool + pos * G.atw, n * G.atw, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = vate::launch_paper_to_packed(h->G, stage, pos, n, st, h->sms);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        }
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_hist, hist, hd.hist_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
         vate_destroy(h);

@@ -47,7 +47,11 @@ struct Geom {
     uint32_t counter;    // 0: asynchronous timestamps; 1: distance recorders
     uint32_t frame0;     // 1: timestamps stored in the frame of block 0 (every handle and group pool);
                          // 0: the paper's per-block values (pools handed in by a caller)
-    uint32_t atw;        // bytes per AT: 1 for k <= 63, 2 (uint16) for 64 <= k <= 1023
+    uint32_t atw;        // bytes per AT: 1 for k <= 63, 2 (uint16) for 64 <= k <= 1023 (for a packed pool:
+                         // the width of its values in the paper's form)
+    uint32_t packed;     // 1: b-bit fields, pn of them per 32-bit word (vate_packed.cu)
+    uint32_t atb, pn;    // packed: bits per AT and fields per word
+    uint64_t mpn;        // packed: ceil(2^64 / pn)
     uint64_t lo, hi;     // pool positions held: [0, P) for a whole pool, a 64-aligned range for a shard
     // host side only: L2 access-policy window over the pool for every launch
     // that touches it (l2_window_bytes = 0: none)
@@ -133,7 +137,13 @@ VATE_HD void block_range_of(const Geom &G, uint32_t i, uint64_t *s, uint64_t *e)
 }
 
 // first byte of the memory that holds positions [lo, hi)
-VATE_HD uint8_t *pool_mem(const Geom &G) { return G.pool + G.lo * G.atw; }
+VATE_HD uint8_t *pool_mem(const Geom &G) { return G.packed ? G.pool : G.pool + G.lo * G.atw; }
+
+// bytes of a packed pool: whole words, rounded up to 16 bytes
+VATE_HD uint64_t packed_bytes(const Geom &G) { return ((G.P + G.pn - 1) / G.pn * 4 + 15) / 16 * 16; }
+
+// device bytes that hold positions [lo, hi)
+VATE_HD uint64_t held_bytes(const Geom &G) { return G.packed ? packed_bytes(G) : (G.hi - G.lo) * G.atw; }
 
 // ACT of block blk when BACT^0 = bact0 (Eq. 8)
 VATE_HD uint32_t act_of_block(uint32_t bact0, uint32_t blk, uint32_t twok) {

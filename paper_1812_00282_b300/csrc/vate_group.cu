@@ -429,7 +429,7 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
             delete g;
             return vate::set_error(VATE_EINVAL, "groups run asynchronous timestamps (counter 0)");
         }
-        if (g->geoms[m].atw != 1u) {
+        if (g->geoms[m].atw != 1u || g->geoms[m].packed) {
             delete g;
             return vate::set_error(VATE_EINVAL, "groups hold byte ATs (k <= 63)");
         }

@@ -44,6 +44,20 @@ cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kpri
                           const uint32_t *aips, uint64_t n, float *out, uint8_t *flags, uint32_t *active,
                           cudaStream_t st, int sms);
 cudaError_t age_prepare(uint32_t k);
+// packed pools (vate_packed.cu)
+uint32_t packed_pattern(const Geom &G);
+cudaError_t launch_packed_init(const Geom &G, cudaStream_t st, int sms);
+cudaError_t launch_packed_preserve(const Geom &G, uint32_t bact0, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
+                                   cudaStream_t st, int sms);
+cudaError_t launch_packed_dr_age(const Geom &G, cudaStream_t st, int sms);
+cudaError_t launch_packed_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,
+                                 unsigned int *ticket, cudaStream_t st);
+cudaError_t launch_packed_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kprime, const uint64_t *hist,
+                                 const uint32_t *aips, uint64_t n, float *out, uint8_t *flags, uint32_t *active,
+                                 cudaStream_t st, int sms);
+cudaError_t launch_packed_to_paper(const Geom &G, uint8_t *dst, uint64_t pos0, uint64_t n, cudaStream_t st, int sms);
+cudaError_t launch_paper_to_packed(const Geom &G, const uint8_t *src, uint64_t pos0, uint64_t n, cudaStream_t st,
+                                   int sms);
 // Eq. 11 from active counts and a census (both summed over the shards of one pool)
 cudaError_t launch_estimate_from_counts(const Geom &G, uint32_t kprime, const uint64_t *hist, const uint32_t *active,
                                         uint64_t n, float *out, uint8_t *flags, cudaStream_t st, int sms);

@@ -50,10 +50,16 @@ __device__ __forceinline__ void set_at(const Geom &G, uint32_t bact0, uint32_t a
     uint32_t pid = vat_pid(G, aip, vid);
     if (pid < G.lo || pid >= G.hi) return;              // another shard's AT
     uint32_t v = G.counter == 1u ? 0u : bact0;
-    if (G.atw == 1u)
+    if (G.packed) {                  // clear the field, then set it (see vate_packed.cu)
+        uint32_t q = (uint32_t)mulhi64(G.mpn, pid), sh = (pid - q * G.pn) * G.atb;
+        uint32_t *w = reinterpret_cast<uint32_t *>(G.pool) + q;
+        atomicAnd(w, ~(((1u << G.atb) - 1u) << sh));
+        atomicOr(w, v << sh);
+    } else if (G.atw == 1u) {
         G.pool[pid] = (uint8_t)v;
-    else
+    } else {
         reinterpret_cast<uint16_t *>(G.pool)[pid] = (uint16_t)v;
+    }
 }
 
 __global__ void __launch_bounds__(256) ingest_kernel(Geom G, uint32_t bact0, const uint32_t *__restrict__ pairs,
@@ -487,6 +493,7 @@ static int grid_for(uint64_t work_items, int threads, int max_blocks) {
 }
 
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms) {
+    if (G.packed) return launch_packed_init(G, st, sms);
     // InitAT: 2k; a distance recorder starts at k (inactive)
     const uint32_t v = G.counter == 1u ? G.k : G.twok;
     const uint64_t nbytes = (G.hi - G.lo) * G.atw;
@@ -508,6 +515,7 @@ cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, 
 }
 
 cudaError_t launch_dr_age(const Geom &G, cudaStream_t st, int sms) {
+    if (G.packed) return launch_packed_dr_age(G, st, sms);
     const uint64_t n = G.hi - G.lo;                         // the recorders held
     if (G.atw == 2u)
         return launch_pool(G, dr_age16_kernel, grid_for(n >> 3, 256, sms * 8), 256, 0, st,
@@ -517,6 +525,7 @@ cudaError_t launch_dr_age(const Geom &G, cudaStream_t st, int sms) {
 
 cudaError_t launch_preserve(const Geom &G, uint32_t bact0, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
                             cudaStream_t st, int sms) {
+    if (G.packed) return launch_packed_preserve(G, bact0, s0, e0, s1, e1, st, sms);
     if (G.atw == 2u) {
         uint64_t chunks = ((e0 - s0) >> 3) + ((e1 - s1) >> 3) + 4;
         return launch_pool(G, preserve16_kernel, grid_for(chunks, 256, sms * 8), 256, 0, st,
@@ -544,6 +553,7 @@ cudaError_t census_prepare(uint32_t twok) {
 
 cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,
                           unsigned int *ticket, cudaStream_t st) {
+    if (G.packed) return launch_packed_census(G, bact0, partial, grid, hist, ticket, st);
     if (G.atw == 2u)
         return launch_pool(G, census16_kernel, grid, CENSUS_THREADS, (size_t)(G.twok + 1) * sizeof(uint32_t), st, G,
                            bact0, partial, hist, ticket);
@@ -555,6 +565,7 @@ cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kpri
                           const uint32_t *aips, uint64_t n, float *out, uint8_t *flags, uint32_t *active,
                           cudaStream_t st, int sms) {
     if (n == 0) return cudaSuccess;
+    if (G.packed) return launch_packed_gather(mode, G, bact0, kprime, hist, aips, n, out, flags, active, st, sms);
     int warps_per_block = GATHER_THREADS / 32;
     int grid = grid_for(n, warps_per_block, sms * 64);
     cudaError_t e = cudaSuccess;

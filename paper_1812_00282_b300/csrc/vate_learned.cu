@@ -357,6 +357,7 @@ int check_learned_handle(const vate_handle *h, HandleView *v) {
     if (v->G.k > 15) return set_error(VATE_EINVAL, "the learned estimator needs k <= 15 (2k + 2 <= 32 inputs)");
     if (v->G.counter != VATE_COUNTER_AT) return set_error(VATE_EINVAL, "the learned estimator runs on asynchronous timestamps");
     if (v->G.lo != 0 || v->G.hi != v->G.P) return set_error(VATE_EINVAL, "the learned estimator needs the whole pool");
+    if (v->G.packed) return set_error(VATE_EINVAL, "the learned estimator needs byte ATs (at_bits 0 or 8)");
     return VATE_OK;
 }
 

@@ -94,6 +94,7 @@ extern "C" int vate_census_noalloc(const vate_params *params, const uint8_t *d_p
         return vate::set_error(VATE_EINVAL, g_msg);
     }
     G.pool = const_cast<uint8_t *>(d_pool);
+    G.packed = 0;                                // the caller's pool: one byte per AT in the paper's form
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *base = static_cast<unsigned char *>(scratch);
     clear_ticket_kernel<<<1, 1, 0, st>>>();

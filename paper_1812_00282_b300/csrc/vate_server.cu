@@ -250,8 +250,9 @@ void scheduler(vate_server *s) {
 
 uint64_t monitor_bytes(const vate_params *p, int sms) {
     const uint64_t bins = 2ull * p->k + 1;
-    const uint64_t at_bytes = p->k <= 63 ? 1 : 2;    // byte ATs up to k = 63, 16-bit ones beyond
-    return (at_bytes << p->log2_pool) + bins * 8 * (1 + 4ull * sms) + 256;
+    vate::Geom G;
+    const uint64_t pool = vate::make_geom_checked(p, &G) == VATE_OK ? vate::held_bytes(G) : (2ull << p->log2_pool);
+    return pool + bins * 8 * (1 + 4ull * sms) + 256;
 }
 
 int enqueue(vate_server *s, Req *r, uint64_t *ticket) {

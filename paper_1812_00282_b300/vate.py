@@ -33,7 +33,8 @@ class VateError(RuntimeError):
 
 class vate_params(C.Structure):
     _fields_ = [("log2_pool", C.c_uint32), ("k", C.c_uint32), ("g", C.c_uint32), ("seg_len", C.c_uint32),
-                ("partition", C.c_uint32), ("counter", C.c_uint32), ("seed", C.c_uint64)]
+                ("partition", C.c_uint32), ("counter", C.c_uint32), ("at_bits", C.c_uint32),
+                ("reserved", C.c_uint32), ("seed", C.c_uint64)]
 
 
 class vate_info(C.Structure):
@@ -198,8 +199,8 @@ VATE_COUNTER_AT, VATE_COUNTER_DR = 0, 1
 
 
 def make_params(log2_pool: int, k: int, g: int, seg_len: int = 1, partition: int = 0, seed: int = 0,
-                counter: int = 0) -> vate_params:
-    return vate_params(log2_pool, k, g, seg_len, partition, counter, seed & 0xFFFFFFFFFFFFFFFF)
+                counter: int = 0, at_bits: int = 0) -> vate_params:
+    return vate_params(log2_pool, k, g, seg_len, partition, counter, at_bits, 0, seed & 0xFFFFFFFFFFFFFFFF)
 
 
 # ---- the C ABI, one function per entry point --------------------------------
@@ -632,7 +633,7 @@ def vate_estimate_from_counts(params: vate_params, active, hist, kprime: int, ou
         _stream(stream)))
 
 
-VATE_CHECKPOINT_MAGIC, VATE_CHECKPOINT_VERSION = 0x31544B4345544156, 1
+VATE_CHECKPOINT_MAGIC, VATE_CHECKPOINT_VERSION = 0x31544B4345544156, 2
 
 
 class vate_checkpoint_header(C.Structure):
@@ -670,8 +671,8 @@ class Vate:
     """Owns one handle; methods forward to the functions above."""
 
     def __init__(self, log2_pool: int, k: int, g: int, seg_len: int = 1, partition: int = 0, seed: int = 0,
-                 stream=None, counter: int = 0):
-        self.params = make_params(log2_pool, k, g, seg_len, partition, seed, counter)
+                 stream=None, counter: int = 0, at_bits: int = 0):
+        self.params = make_params(log2_pool, k, g, seg_len, partition, seed, counter, at_bits)
         self.k, self.g, self.P = k, g, 1 << log2_pool
         self.h = vate_create(self.params, stream)
 

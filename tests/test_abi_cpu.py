@@ -46,12 +46,21 @@ def test_library_exports_every_declared_symbol(V):
 @pytest.mark.parametrize("bad", [
     dict(log2_pool=11), dict(log2_pool=33), dict(k=0), dict(k=1024), dict(g=0), dict(g=65537),
     dict(log2_pool=14, k=300),                                   # blocks of fewer than 32 ATs
+    dict(k=10, at_bits=4), dict(k=10, at_bits=17), dict(k=300, log2_pool=20, at_bits=9),   # fields too narrow / wide
     dict(seg_len=3), dict(seg_len=128), dict(g=1000, seg_len=32), dict(partition=2),
 ])
 def test_invalid_parameters_rejected_on_host(V, bad):
     p = dict(log2_pool=20, k=5, g=1024, seg_len=32, partition=0, seed=1)
     p.update(bad)
     params = V.make_params(**p)
+    with pytest.raises(V.VateError) as ei:
+        V.vate_create(params, stream=0)
+    assert ei.value.code == V.VATE_EINVAL
+
+
+def test_reserved_must_be_zero(V):
+    params = V.make_params(20, 5, 1024)
+    params.reserved = 1
     with pytest.raises(V.VateError) as ei:
         V.vate_create(params, stream=0)
     assert ei.value.code == V.VATE_EINVAL
@@ -142,7 +151,7 @@ def _fnv1a_words(b: bytes) -> int:
 
 def _image(V, c=12, k=3, slice_=4, bact0=2, closed=1, pool_value=None, counter=0, fix_checksum=True):
     hd = V.vate_checkpoint_header()
-    hd.magic, hd.version, hd.header_bytes = V.VATE_CHECKPOINT_MAGIC, V.VATE_CHECKPOINT_VERSION, 88
+    hd.magic, hd.version, hd.header_bytes = V.VATE_CHECKPOINT_MAGIC, V.VATE_CHECKPOINT_VERSION, 96
     hd.params = V.make_params(c, k, 64, 1, 0, 9, counter)
     hd.slice, hd.bact0, hd.closed = slice_, bact0, closed
     hd.hist_bytes, hd.pool_bytes = (2 * k + 1) * 8, 1 << c
@@ -151,13 +160,13 @@ def _image(V, c=12, k=3, slice_=4, bact0=2, closed=1, pool_value=None, counter=0
     body = bytes(hd) + np.zeros(2 * k + 1, np.uint64).tobytes() + pool.tobytes()
     if fix_checksum:
         hd.checksum = _fnv1a_words(body)
-    return np.frombuffer(bytes(hd) + body[88:], np.uint8).copy()
+    return np.frombuffer(bytes(hd) + body[96:], np.uint8).copy()
 
 
 def test_checkpoint_header_layout(V):
     import ctypes as C
-    assert C.sizeof(V.vate_checkpoint_header) == 88
-    assert V.vate_checkpoint_header.checksum.offset == 80
+    assert C.sizeof(V.vate_checkpoint_header) == 96
+    assert V.vate_checkpoint_header.checksum.offset == 88
     assert V.VATE_CHECKPOINT_MAGIC.to_bytes(8, "little") == b"VATECKT1"
 
 
@@ -196,7 +205,7 @@ def test_damaged_checkpoint_rejected_on_host(V, damage):
         img = _image(V, slice_=-1, bact0=1, closed=0)
     elif damage == "sizes":
         img = _image(V)
-        img[64] = 9                                       # hist_bytes
+        img[72] = 9                                       # hist_bytes
     elif damage == "params":
         img = _image(V, k=0)
     with pytest.raises(V.VateError) as ei:

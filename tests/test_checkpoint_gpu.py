@@ -110,18 +110,18 @@ def test_checkpoint_image_describes_the_handle(V):
     d.ingest(torch.from_numpy(p.view(np.int32)).cuda(), 3)
     d.close_slice(3)
     img = d.checkpoint()
-    assert img.size == V.vate_checkpoint_size(d.h) == 88 + 9 * 8 + (1 << 16)
-    hd = V.vate_checkpoint_header.from_buffer_copy(img[:88].tobytes())
+    assert img.size == V.vate_checkpoint_size(d.h) == 96 + 9 * 8 + (1 << 16)
+    hd = V.vate_checkpoint_header.from_buffer_copy(img[:96].tobytes())
     assert hd.magic == V.VATE_CHECKPOINT_MAGIC and hd.version == V.VATE_CHECKPOINT_VERSION
     assert (hd.slice, hd.bact0, hd.closed, hd.params.partition) == (3, 0, 1, 1)
     pool = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
     d.copy_pool(pool)
-    np.testing.assert_array_equal(img[88 + 72:], pool.cpu().numpy())
+    np.testing.assert_array_equal(img[96 + 72:], pool.cpu().numpy())
     with pytest.raises(V.VateError) as e:
         V.vate_checkpoint(d.h, np.empty(img.size - 1, np.uint8))
     assert e.value.code == V.VATE_EINVAL
     bad = img.copy()
-    bad[88 + 72 + 5] ^= 1                          # one AT flipped: checksum mismatch
+    bad[96 + 72 + 5] ^= 1                          # one AT flipped: checksum mismatch
     with pytest.raises(V.VateError) as e:
         V.Vate.restore(bad)
     assert e.value.code == V.VATE_EINVAL and "checksum" in V.vate_last_error()
@@ -143,10 +143,34 @@ def test_wide_resume_continues_bit_exactly(V):
         cur.close_slice(sid)
         if j in (2, 6):
             img = cur.checkpoint()
-            assert img.size == 88 + (2 * k + 1) * 8 + 2 * (1 << c)
+            assert img.size == 96 + (2 * k + 1) * 8 + 2 * (1 << c)
             cur.close()
             cur = V.Vate.restore(img)
         a, b = state(V, ref, hosts, (1, k)), state(V, cur, hosts, (1, k))
         assert_same(a, b, "slice %d" % sid)
     ref.close()
     cur.close()
+
+
+def test_packed_resume_continues_bit_exactly(V):
+    c, k, g, L, seed = 17, 10, 512, 32, 0x78
+    tr = Traffic(SMALL, pkts_per_slice=5000)
+    hosts = tr.aips[:500]
+    ref = V.Vate(c, k, g, L, 0, seed, at_bits=5)
+    cur = V.Vate(c, k, g, L, 0, seed, at_bits=5)
+    plain = V.Vate(c, k, g, L, 0, seed)
+    for j, sid in enumerate([0, 1, 2, 9, 10, 11, 12, 25, 26]):
+        dp = torch.from_numpy(tr.slice_pairs(sid).view(np.int32)).cuda()
+        for d in (ref, cur, plain):
+            d.ingest(dp, sid)
+            d.close_slice(sid)
+        if j in (2, 5):
+            img = cur.checkpoint()
+            assert img.size == 96 + (2 * k + 1) * 8 + (1 << c)      # unpacked: the paper's form
+            cur.close()
+            cur = V.Vate.restore(img)
+        a, b, p = state(V, ref, hosts, (1, k)), state(V, cur, hosts, (1, k)), state(V, plain, hosts, (1, k))
+        assert_same(a, b, "slice %d" % sid)
+        assert_same(a, p, "packed vs byte, slice %d" % sid)
+    for d in (ref, cur, plain):
+        d.close()

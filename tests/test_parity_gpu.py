@@ -76,9 +76,9 @@ def compare_close(V, d, o, hosts, kps, check_pool=True, check_ages=True):
                                       o.age_counts(hosts))
 
 
-def run_stream(V, params, slices, hosts, kps, slice_ids=None, check_every=1, **kw):
+def run_stream(V, params, slices, hosts, kps, slice_ids=None, check_every=1, at_bits=0, **kw):
     c, k, g, L, part, seed = params
-    d = V.Vate(c, k, g, L, part, seed)
+    d = V.Vate(c, k, g, L, part, seed, at_bits=at_bits)
     o = Oracle(c=c, k=k, g=g, seg_len=L, partition=part, seed=seed)
     ids = list(range(len(slices))) if slice_ids is None else slice_ids
     prev = None
@@ -408,3 +408,68 @@ def test_wide_pool_load_and_age_counts_limits(V):
     assert e.value.code == V.VATE_EINVAL
     d.close()
     d2.close()
+
+
+# ---- packed ATs (the paper's layout: floor(32/b) b-bit fields per word) -------
+PACKED = [
+    ((17, 10, 1024, 32, 0, 71), 5),      # 6 fields per word, the paper's 5 bits for k = 10
+    ((16, 5, 512, 1, 1, 72), 4),         # 8 per word, fully random placement, low-deviation partition
+    ((19, 300, 512, 32, 0, 73), 10),     # 3 per word, the paper's 10 bits for k' = 300
+    ((15, 1, 256, 8, 0, 74), 2),         # 16 per word
+    ((17, 70, 512, 16, 0, 75), 8),       # 4 per word, values up to 140
+    ((17, 10, 512, 64, 0, 76), 7),       # 4 per word, 3 bits left over
+]
+
+
+@pytest.mark.parametrize("params,b", PACKED, ids=lambda x: str(x))
+def test_packed_timestamps_parity(V, params, b):
+    c, k, g, L, part, seed = params
+    tr = Traffic(SMALL, pkts_per_slice=5000)
+    ids = sorted(set(list(range(0, 5)) + list(range(k, k + 3)) + list(range(2 * k, 2 * k + 4)) + [4 * k + 3]))
+    slices = [tr.slice_pairs(i % 64) for i in ids]
+    run_stream(V, params, slices, tr.aips[:700], kps=(1, max(1, k // 2), k), slice_ids=ids, at_bits=b,
+               check_ages=False)
+
+
+def test_packed_recorders_and_pool_round_trip(V):
+    k, c, g, L = 10, 17, 512, 32
+    tr = Traffic(SMALL, pkts_per_slice=5000)
+    dr = V.Vate(c, k, g, L, 0, 81, counter=V.VATE_COUNTER_DR, at_bits=5)
+    at = V.Vate(c, k, g, L, 0, 81)
+    o = Oracle(c=c, k=k, g=g, seg_len=L, partition=0, seed=81)
+    hosts = tr.aips[:500]
+    dh = dev_u32(hosts)
+    prev = None
+    for sid in (0, 1, 2, 9, 10, 11, 30):
+        if prev is not None:
+            for _ in range(sid - prev):
+                o.advance()
+        prev = sid
+        p = tr.slice_pairs(sid)
+        o.ingest(p)
+        for d in (dr, at):
+            d.ingest(dev_pairs(p), sid)
+            d.close_slice(sid)
+        pool = torch.empty(o.P, dtype=torch.uint8, device="cuda")
+        dr.copy_pool(pool)
+        np.testing.assert_array_equal(pool.cpu().numpy(), o.dr())
+        for kp in (1, k):
+            e1 = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+            e2 = torch.empty_like(e1)
+            dr.estimate(dh, kp, e1)
+            at.estimate(dh, kp, e2)
+            assert torch.equal(e1, e2)
+    # the paper's form loads into a packed pool and copies back unchanged
+    d = V.Vate(c, k, g, L, 0, 81, at_bits=5)
+    d.ingest(torch.zeros(0, 2, dtype=torch.int32, device="cuda"), 0)
+    ref = torch.empty(o.P, dtype=torch.uint8, device="cuda")
+    at.copy_pool(ref)
+    d.load_pool(ref)
+    back = torch.empty_like(ref)
+    d.copy_pool(back)
+    assert torch.equal(back, ref)
+    with pytest.raises(V.VateError) as e:
+        V.vate_create_shard(V.make_params(c, k, g, L, 0, 81, 0, 5), 0, 1 << 16)
+    assert e.value.code == V.VATE_EINVAL
+    for h in (dr, at, d):
+        h.close()
