@@ -77,10 +77,12 @@ __device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint
         words[2] = swar_bins(w.z, act, G.twok);
         words[3] = swar_bins(w.w, act, G.twok);
     }
+    // shared-memory atomics without a return value: consecutive bytes of one
+    // bin do not wait for each other's read-modify-write
 #pragma unroll
     for (int b = 0; b < 16; b++) {
         uint32_t bin = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, G.twok);
-        col[bin * 32u] += 1u;
+        atomicAdd(&col[bin * 32u], 1u);
     }
 }
 

@@ -38,49 +38,138 @@ __host__ __device__ inline Layout layout(uint32_t n_in) {
     return L;
 }
 
-// Per-age counts of one host's VATs accumulated into this lane's column
-// (col[d * 32], d < k) from a frame-0 pool, where every AT has ACT = BACT^0;
-// 16-byte chunks when L >= 16, one byte per VAT otherwise.
-__device__ __forceinline__ void host_age_columns(const Geom &G, uint32_t bact0, uint32_t aip, uint32_t lane,
-                                                 uint32_t *col) {
-    const uint64_t hk = host_key(G, aip);
-    if (G.L >= 16) {
-        const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
-        const uint32_t nchunks = G.g >> 4;
-        for (uint32_t c = lane; c < nchunks; c += 32u) {
-            const uint32_t pid = vat_pid_k(G, hk, c << 4);   // first VAT of the chunk
-            const uint4 w = __ldg(pool16 + (pid >> 4));
-            uint32_t words[4] = {swar_bins(w.x, bact0, G.twok), swar_bins(w.y, bact0, G.twok),
-                                 swar_bins(w.z, bact0, G.twok), swar_bins(w.w, bact0, G.twok)};
+// Per-age counts of one host's VATs seen by this lane, in registers, as
+// bit-sliced (vertical) counters over the byte values 0..31 (2k <= 30 here):
+// bit u of plane j is bit j of the number of bytes equal to u, planes 1, 2,
+// ..., 128.  Sixteen bytes at a time enter as one-hot masks 1 << u through a
+// carry-save adder tree (each adder two 3-input logic operations), the
+// sixteens rippling into the high planes.  In frame 0 the age of value u is
+// (BACT^0 - u) mod 2k.  At most 15 chunks (240 bytes) are counted before the
+// planes are folded into the warp's totals (lane d holds age d).
+__device__ __forceinline__ void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+struct AgePlanes {
+    uint32_t p[8] = {0, 0, 0, 0, 0, 0, 0, 0};     // planes of weight 1, 2, 4, ..., 128
+
+    __device__ __forceinline__ void add_chunk(uint4 w) {
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+        uint32_t m[16];
 #pragma unroll
-            for (int b = 0; b < 16; b++) {
-                uint32_t d = (words[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-                if (d < G.k) col[d * 32u] += 1u;
-            }
-        }
-    } else {
-        for (uint32_t i = lane; i < G.g; i += 32u) {
-            uint32_t v = __ldg(G.pool + vat_pid_k(G, hk, i));
-            if (v >= G.twok) continue;
-            uint32_t d = bact0 + G.twok - v;
-            if (d >= G.twok) d -= G.twok;
-            if (d < G.k) col[d * 32u] += 1u;
+        for (int b = 0; b < 16; b++) m[b] = 1u << ((words[b >> 2] >> (8 * (b & 3))) & 31u);
+        uint32_t twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;
+        csa(twosA, p[0], p[0], m[0], m[1]);
+        csa(twosB, p[0], p[0], m[2], m[3]);
+        csa(foursA, p[1], p[1], twosA, twosB);
+        csa(twosA, p[0], p[0], m[4], m[5]);
+        csa(twosB, p[0], p[0], m[6], m[7]);
+        csa(foursB, p[1], p[1], twosA, twosB);
+        csa(eightsA, p[2], p[2], foursA, foursB);
+        csa(twosA, p[0], p[0], m[8], m[9]);
+        csa(twosB, p[0], p[0], m[10], m[11]);
+        csa(foursA, p[1], p[1], twosA, twosB);
+        csa(twosA, p[0], p[0], m[12], m[13]);
+        csa(twosB, p[0], p[0], m[14], m[15]);
+        csa(foursB, p[1], p[1], twosA, twosB);
+        csa(eightsB, p[2], p[2], foursA, foursB);
+        csa(sixteens, p[3], p[3], eightsA, eightsB);
+        uint32_t c = sixteens;                 // ripple into 16, 32, 64, 128
+#pragma unroll
+        for (int j = 4; j < 8; j++) {
+            const uint32_t t = p[j] & c;
+            p[j] ^= c;
+            c = t;
         }
     }
+    __device__ __forceinline__ uint32_t count(uint32_t u) const {
+        uint32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) c |= ((p[j] >> u) & 1u) << j;
+        return c;
+    }
+    // add the warp's counts of ages 0..k-1 to the totals (lane d: age d) and restart
+    __device__ __forceinline__ void fold(uint32_t bact0, uint32_t k, uint32_t lane, uint32_t &cd) {
+        const uint32_t twok = 2u * k;
+        for (uint32_t d = 0; d < k; d++) {
+            uint32_t u = bact0 + twok - d;
+            if (u >= twok) u -= twok;
+            const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, count(u));
+            if (lane == d) cd += c;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) p[j] = 0;
+    }
+};
+
+// The segments' chunks as in gather_host_vec: the lanes hash 32 segments per
+// round, read the round's chunks with the segment base shuffled from the
+// hashing lane, all loads of a round issued before any is counted.
+template <int CPSL>
+__device__ __forceinline__ void age_counts_vec(const Geom &G, uint32_t bact0, uint64_t hk, uint32_t lane,
+                                               AgePlanes &ap, uint32_t &cd) {
+    constexpr int CPS = 1 << CPSL;
+    constexpr uint32_t ROUNDS_PER_FOLD = 15u / CPS;                 // a round gives a lane CPS chunks
+    const uint32_t nseg = G.g >> G.log2L;
+    const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
+    uint32_t since = 0;
+    for (uint32_t r0 = 0; r0 < nseg; r0 += 32u) {
+        if (since++ == ROUNDS_PER_FOLD) {
+            ap.fold(bact0, G.k, lane, cd);
+            since = 1;
+        }
+        const uint32_t s = r0 + lane;
+        const uint32_t base = s < nseg ? (seg_base_k(G, hk, s) >> 4) : 0u;   // first chunk of the segment
+        const uint32_t segs = min(32u, nseg - r0);
+        uint4 w[CPS];
+        bool valid[CPS];
+#pragma unroll
+        for (int it = 0; it < CPS; it++) {
+            const uint32_t c = it * 32u + lane;
+            const uint32_t q = __shfl_sync(0xFFFFFFFFu, base, (c >> CPSL) & 31u) + (c & (CPS - 1u));
+            valid[it] = c < (segs << CPSL);
+            w[it] = make_uint4(0u, 0u, 0u, 0u);
+            if (valid[it]) w[it] = __ldg(pool16 + q);
+        }
+        const uint32_t none = G.twok * ONES;                          // a missing chunk counts as inactive ATs
+#pragma unroll
+        for (int it = 0; it < CPS; it++) ap.add_chunk(valid[it] ? w[it] : make_uint4(none, none, none, none));
+    }
+}
+
+// The count of age d (d < k) of one host's VATs, in lane d; 0 in other lanes.
+__device__ __forceinline__ uint32_t host_age_counts(const Geom &G, uint32_t bact0, uint32_t aip, uint32_t lane) {
+    AgePlanes ap;
+    uint32_t cd = 0;
+    const uint64_t hk = host_key(G, aip);
+    if (G.L == 16) age_counts_vec<0>(G, bact0, hk, lane, ap, cd);
+    else if (G.L == 32) age_counts_vec<1>(G, bact0, hk, lane, ap, cd);
+    else if (G.L == 64) age_counts_vec<2>(G, bact0, hk, lane, ap, cd);
+    else {                      // one byte per VAT: sixteen VATs per lane make a chunk
+        const uint32_t none = G.twok;
+        for (uint32_t i0 = 0; i0 < G.g; i0 += 32u * 16u) {
+            uint32_t words[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int b = 0; b < 16; b++) {
+                const uint32_t i = i0 + 32u * b + lane;
+                const uint32_t v = i < G.g ? (uint32_t)__ldg(G.pool + vat_pid_k(G, hk, i)) : none;
+                words[b >> 2] |= v << (8 * (b & 3));
+            }
+            ap.add_chunk(make_uint4(words[0], words[1], words[2], words[3]));
+            ap.fold(bact0, G.k, lane, cd);
+        }
+    }
+    ap.fold(bact0, G.k, lane, cd);
+    return cd;
 }
 
 // Features of one host into xw[0 .. 2k+2) (shared memory of the warp); returns
 // the closed-form estimate for k' = k and its flags, and the active count.
 __device__ __forceinline__ float host_features(const Geom &G, uint32_t bact0, const uint64_t *hist, uint64_t N0,
-                                               uint32_t aip, uint32_t lane, uint32_t *colw, float *xw,
-                                               uint8_t &flags, uint32_t &A) {
-    uint32_t *col = colw + lane;
-    for (uint32_t d = 0; d < G.k; d++) col[d * 32u] = 0u;
-    host_age_columns(G, bact0, aip, lane, col);
-    __syncwarp();
-    uint32_t cd = 0;
-    if (lane < G.k)
-        for (uint32_t l = 0; l < 32u; l++) cd += colw[lane * 32u + l];
+                                               uint32_t aip, uint32_t lane, float *xw, uint8_t &flags, uint32_t &A) {
+    const uint32_t cd = host_age_counts(G, bact0, aip, lane);
     A = __reduce_add_sync(0xFFFFFFFFu, cd);
     const float plain = estimate_eq11(G.g, G.P, N0, A, flags);
     if (lane < G.k) {
@@ -95,40 +184,66 @@ __device__ __forceinline__ float host_features(const Geom &G, uint32_t bact0, co
     return plain;
 }
 
-// y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 for one input row held in shared
-// memory (xw), lane j computing hidden units j and j + 32.  Summation order is
-// fixed, so the result is deterministic.
-__device__ __forceinline__ float mlp_eval_warp(const float *prm, uint32_t n_in, const float *xw, uint32_t lane) {
+// y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 for one input row x (shared
+// memory), evaluated by one lane.  The lanes of a warp evaluate different rows
+// with the same weights, so every weight read is a shared-memory broadcast;
+// w2t holds W2 transposed (w2t[j * 64 + i] = W2[i][j]) so that unit j reads its
+// 64 inputs contiguously.  Every sum runs in index order (bias first), so the
+// result is deterministic and the same in every kernel that calls this.
+__device__ __forceinline__ float mlp_eval_lane(const float *prm, const float *w2t, uint32_t n_in, const float *x) {
     const Layout L = layout(n_in);
-    float a = prm[L.b1 + lane], b = prm[L.b1 + lane + 32];
-    for (uint32_t i = 0; i < n_in; i++) {
-        const float xi = xw[i];
-        a = fmaf(prm[L.W1 + i * HID + lane], xi, a);
-        b = fmaf(prm[L.W1 + i * HID + lane + 32], xi, b);
-    }
-    a = fmaxf(a, 0.0f);
-    b = fmaxf(b, 0.0f);
-    float c = prm[L.b2 + lane], d = prm[L.b2 + lane + 32];
-#pragma unroll 8
-    for (uint32_t i = 0; i < 32; i++) {
-        const float hi = __shfl_sync(0xFFFFFFFFu, a, i);
-        c = fmaf(prm[L.W2 + i * HID + lane], hi, c);
-        d = fmaf(prm[L.W2 + i * HID + lane + 32], hi, d);
-    }
-#pragma unroll 8
-    for (uint32_t i = 0; i < 32; i++) {
-        const float hi = __shfl_sync(0xFFFFFFFFu, b, i);
-        c = fmaf(prm[L.W2 + (i + 32) * HID + lane], hi, c);
-        d = fmaf(prm[L.W2 + (i + 32) * HID + lane + 32], hi, d);
-    }
-    c = fmaxf(c, 0.0f);
-    d = fmaxf(d, 0.0f);
-    float y = fmaf(prm[L.w3 + lane], c, prm[L.w3 + lane + 32] * d);
+    float h[HID];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xFFFFFFFFu, y, o);
-    y = __shfl_sync(0xFFFFFFFFu, y, 0);
-    return y + prm[L.b3];
+    for (int j = 0; j < HID; j++) h[j] = prm[L.b1 + j];
+    for (uint32_t i = 0; i < n_in; i++) {
+        const float xi = x[i];
+        const float4 *row = reinterpret_cast<const float4 *>(prm + L.W1 + i * HID);
+#pragma unroll
+        for (int j4 = 0; j4 < HID / 4; j4++) {
+            const float4 w = row[j4];
+            h[4 * j4] = fmaf(w.x, xi, h[4 * j4]);
+            h[4 * j4 + 1] = fmaf(w.y, xi, h[4 * j4 + 1]);
+            h[4 * j4 + 2] = fmaf(w.z, xi, h[4 * j4 + 2]);
+            h[4 * j4 + 3] = fmaf(w.w, xi, h[4 * j4 + 3]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < HID; j++) h[j] = fmaxf(h[j], 0.0f);
+    float y = prm[L.b3];
+#pragma unroll 2
+    for (int j = 0; j < HID; j++) {
+        const float4 *col = reinterpret_cast<const float4 *>(w2t + j * HID);
+        float a = prm[L.b2 + j];
+#pragma unroll
+        for (int i4 = 0; i4 < HID / 4; i4++) {
+            const float4 w = col[i4];
+            a = fmaf(w.x, h[4 * i4], a);
+            a = fmaf(w.y, h[4 * i4 + 1], a);
+            a = fmaf(w.z, h[4 * i4 + 2], a);
+            a = fmaf(w.w, h[4 * i4 + 3], a);
+        }
+        y = fmaf(prm[L.w3 + j], fmaxf(a, 0.0f), y);
+    }
+    return y;
 }
+
+// The model in shared memory for mlp_eval_lane: the parameters (padded to a
+// multiple of 4 floats) followed by W2 transposed.  Returns w2t.
+__device__ __forceinline__ float *stage_model(float *sm, const float *params, uint32_t n_in) {
+    const uint64_t np = n_params(n_in), npad = (np + 3) & ~3ull;
+    const Layout L = layout(n_in);
+    float *w2t = sm + npad;
+    for (uint64_t i = threadIdx.x; i < np; i += blockDim.x) sm[i] = params[i];
+    for (uint32_t t = threadIdx.x; t < HID * HID; t += blockDim.x) {
+        const uint32_t j = t / HID, i = t % HID;
+        w2t[t] = params[L.W2 + i * HID + j];
+    }
+    return w2t;
+}
+
+__host__ __device__ inline size_t model_smem_floats(uint32_t n_in) { return ((n_params(n_in) + 3) & ~3ull) + HID * HID; }
+
+constexpr int XS = MAX_IN + 1;           // row stride of the per-warp input rows (no bank conflicts per lane)
 
 __device__ __forceinline__ uint64_t inactive_for_k(const uint64_t *hist, uint64_t P, uint32_t k) {
     uint64_t act = 0;
@@ -139,7 +254,6 @@ __device__ __forceinline__ uint64_t inactive_for_k(const uint64_t *hist, uint64_
 __global__ void __launch_bounds__(WARPS * 32) features_kernel(Geom G, uint32_t bact0, const uint64_t *__restrict__ hist,
                                                               const uint32_t *__restrict__ aips, uint64_t n,
                                                               float *__restrict__ x) {
-    __shared__ uint32_t cols[WARPS][15 * 32];
     __shared__ float xs[WARPS][MAX_IN];
     __shared__ uint64_t sN0;
     if (threadIdx.x == 0) sN0 = inactive_for_k(hist, G.P, G.k);
@@ -150,63 +264,82 @@ __global__ void __launch_bounds__(WARPS * 32) features_kernel(Geom G, uint32_t b
          h += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
         uint8_t f;
         uint32_t A;
-        host_features(G, bact0, hist, sN0, aips[h], lane, cols[warp], xs[warp], f, A);
+        host_features(G, bact0, hist, sN0, aips[h], lane, xs[warp], f, A);
         if (lane < n_in) x[h * n_in + lane] = xs[warp][lane];
         __syncwarp();
     }
 }
 
+// 32 hosts per warp: the warp extracts each host's features into its row of
+// xs (host_features), then lane j evaluates host j's model (mlp_eval_lane)
+// and the fallback.
 __global__ void __launch_bounds__(WARPS * 32) learned_estimate_kernel(Geom G, uint32_t bact0,
                                                                       const uint64_t *__restrict__ hist,
                                                                       const uint32_t *__restrict__ aips, uint64_t n,
                                                                       const float *__restrict__ params,
                                                                       float *__restrict__ out,
                                                                       uint8_t *__restrict__ flags) {
-    extern __shared__ float prm[];           // the model
-    __shared__ uint32_t cols[WARPS][15 * 32];
-    __shared__ float xs[WARPS][MAX_IN];
-    __shared__ uint64_t sN0;
+    extern __shared__ float4 dyn4[];
+    float *prm = reinterpret_cast<float *>(dyn4);
     const uint32_t n_in = 2 * G.k + 2;
-    const uint64_t np = n_params(n_in);
-    for (uint64_t i = threadIdx.x; i < np; i += blockDim.x) prm[i] = params[i];
+    float *w2t = stage_model(prm, params, n_in);
+    float *xs = w2t + HID * HID;                       // [WARPS][32][XS]
+    __shared__ uint64_t sN0;
     if (threadIdx.x == 0) sN0 = inactive_for_k(hist, G.P, G.k);
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    for (uint64_t h = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; h < n;
-         h += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
-        uint8_t f;
-        uint32_t A;
-        const float plain = host_features(G, bact0, hist, sN0, aips[h], lane, cols[warp], xs[warp], f, A);
-        const float y = mlp_eval_warp(prm, n_in, xs[warp], lane);
-        // the model corrects the closed form in log space: x[2k+1] * 16 = log1p(max(plain, 0))
-        float e = expm1f(8.0f * y + 16.0f * xs[warp][n_in - 1]);
-        if (A == 0u || !isfinite(e)) {
-            e = plain;
-            f |= (uint8_t)VATE_FLAG_FALLBACK;
+    float *xw = xs + (size_t)warp * 32 * XS;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t g0 = warp0 * 32; g0 < n; g0 += nwarps * 32) {
+        uint32_t myA = 0;
+        float myplain = 0.0f;
+        uint8_t myf = 0;
+        for (uint32_t j = 0; j < 32u && g0 + j < n; j++) {
+            uint8_t f;
+            uint32_t A;
+            const float plain = host_features(G, bact0, hist, sN0, aips[g0 + j], lane, xw + j * XS, f, A);
+            if (lane == j) {
+                myA = A;
+                myplain = plain;
+                myf = f;
+            }
         }
-        if (lane == 0) {
-            out[h] = e;
-            if (flags) flags[h] = f;
+        __syncwarp();
+        if (g0 + lane < n) {
+            const float *x = xw + lane * XS;
+            const float y = mlp_eval_lane(prm, w2t, n_in, x);
+            // the model corrects the closed form in log space: x[2k+1] * 16 = log1p(max(plain, 0))
+            float e = expm1f(8.0f * y + 16.0f * x[n_in - 1]);
+            if (myA == 0u || !isfinite(e)) {
+                e = myplain;
+                myf |= (uint8_t)VATE_FLAG_FALLBACK;
+            }
+            out[g0 + lane] = e;
+            if (flags) flags[g0 + lane] = myf;
         }
         __syncwarp();
     }
 }
 
+// Lane per row: lane j evaluates row r0 + j.
 __global__ void __launch_bounds__(WARPS * 32) mlp_forward_kernel(const float *__restrict__ params, uint32_t n_in,
                                                                  const float *__restrict__ x, uint64_t n,
                                                                  float *__restrict__ y) {
-    extern __shared__ float prm[];
-    __shared__ float xs[WARPS][MAX_IN];
-    const uint64_t np = n_params(n_in);
-    for (uint64_t i = threadIdx.x; i < np; i += blockDim.x) prm[i] = params[i];
+    extern __shared__ float4 dyn4[];
+    float *prm = reinterpret_cast<float *>(dyn4);
+    float *w2t = stage_model(prm, params, n_in);
+    float *xs = w2t + HID * HID;                       // [WARPS][32][XS]
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    for (uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; r < n;
-         r += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
-        if (lane < n_in) xs[warp][lane] = x[r * n_in + lane];
+    float *xw = xs + (size_t)warp * 32 * XS;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t r0 = warp0 * 32; r0 < n; r0 += nwarps * 32) {
+        const uint64_t rows = n - r0 < 32 ? n - r0 : 32;
+        for (uint32_t t = lane; t < rows * n_in; t += 32u) xw[(t / n_in) * XS + t % n_in] = x[r0 * n_in + t];
         __syncwarp();
-        const float v = mlp_eval_warp(prm, n_in, xs[warp], lane);
-        if (lane == 0) y[r] = v;
+        if (lane < rows) y[r0 + lane] = mlp_eval_lane(prm, w2t, n_in, xw + lane * XS);
         __syncwarp();
     }
 }
@@ -395,9 +528,9 @@ int vate_mlp_forward(const float *d_params, uint32_t n_in, const float *d_x, uin
     if (!d_params || n_in < 1 || n_in > MAX_IN) return set_error(VATE_EINVAL, "bad parameters pointer or n_in (1..32)");
     if (n && (!d_x || !d_y)) return set_error(VATE_EINVAL, "d_x and d_y must not be NULL");
     if (n == 0) return VATE_OK;
-    const size_t smem = sizeof(float) * n_params(n_in);
+    const size_t smem = sizeof(float) * (model_smem_floats(n_in) + (size_t)WARPS * 32 * XS);
     cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int grid = (int)std::min<uint64_t>((n + WARPS - 1) / WARPS, (uint64_t)sms_now() * 8);
+    int grid = (int)std::min<uint64_t>((n + WARPS * 32 - 1) / (WARPS * 32), (uint64_t)sms_now() * 8);
     mlp_forward_kernel<<<grid, WARPS * 32, smem, (cudaStream_t)stream>>>(d_params, n_in, d_x, n, d_y);
     count_launch();
     cudaError_t e = cudaGetLastError();
@@ -437,9 +570,9 @@ int vate_estimate_learned(vate_handle *h, const uint32_t *d_aips, uint64_t n, co
     if (!d_params) return set_error(VATE_EINVAL, "d_params must not be NULL");
     if (n && (!d_aips || !d_out)) return set_error(VATE_EINVAL, "d_aips and d_out must not be NULL");
     if (n == 0) return VATE_OK;
-    const size_t smem = sizeof(float) * n_params(2 * v.G.k + 2);
+    const size_t smem = sizeof(float) * (model_smem_floats(2 * v.G.k + 2) + (size_t)WARPS * 32 * XS);
     cudaFuncSetAttribute(learned_estimate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int grid = (int)std::min<uint64_t>((n + WARPS - 1) / WARPS, (uint64_t)v.sms * 8);
+    int grid = (int)std::min<uint64_t>((n + WARPS * 32 - 1) / (WARPS * 32), (uint64_t)v.sms * 8);
     cudaError_t e = launch_pool(v.G, learned_estimate_kernel, grid, WARPS * 32, smem, (cudaStream_t)stream, v.G,
                                 v.bact0, v.hist, d_aips, n, d_params, d_out, d_flags);
     return e == cudaSuccess ? VATE_OK : set_error(VATE_ECUDA, cudaGetErrorString(e));

@@ -67,7 +67,8 @@ def run(V, duration: float = 5.0, budget_bytes: int = 8 << 30, max_monitors: int
     for i in range(candidates):
         if len(admitted) >= max_monitors:
             break
-        c = int(rng.integers(24, 32))
+        # every fourth candidate has the pool the learned model was trained for
+        c = model_log2_pool if i % 4 == 0 else int(rng.integers(24, 32))
         try:
             mid = V.vate_server_admit(srv, V.make_params(c, 10, 4096, 32, 0, seed * 100 + i))
         except V.VateError as e:
