@@ -180,7 +180,7 @@ class ClockSampler:
 def traffic_sha() -> str:
     """Checksum of the sources a committed ncu traffic figure depends on."""
     h = hashlib.sha256()
-    for f in ("vate_kernels.cu", "vate_device.cuh"):
+    for f in ("vate_kernels.cu", "vate_device.cuh", "vate_device_ops.cuh"):
         with open(os.path.join(ROOT, "paper_1812_00282_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
