@@ -59,6 +59,8 @@ def _load():
             "vo_destroy": (None, [vp]),
             "vo_bh": (u32, [vp, u32]),
             "vo_h": (u64, [vp, u32, u32]),
+            "vo_h_of": (u64, [u32, u32, u64, u32, u32]),
+            "vo_bh_of": (u32, [u32, u64, u32]),
             "vo_block": (u32, [vp, u64]),
             "vo_bact": (u32, [vp, u32]),
             "vo_act_of": (u32, [vp, u64]),
@@ -95,6 +97,15 @@ def _load():
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+def h_of(c: int, L: int, seed: int, aip: int, i: int) -> int:
+    """H(aip, i) for a pool of 2^c ATs without allocating it."""
+    return int(_load().vo_h_of(c, L, seed & 0xFFFFFFFFFFFFFFFF, aip, i))
+
+
+def bh_of(g: int, seed: int, bip: int) -> int:
+    return int(_load().vo_bh_of(g, seed & 0xFFFFFFFFFFFFFFFF, bip))
 
 
 def fmix32(x: int) -> int:

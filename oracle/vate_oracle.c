@@ -121,6 +121,27 @@ uint64_t vo_h(const vo_state *s, uint32_t aip, uint32_t i)
     return seg * (uint64_t)s->L + (uint64_t)o;
 }
 
+/* The same H and BH without a pool, for pools too large to hold here: a
+ * state with only the hash parameters filled in. */
+uint64_t vo_h_of(uint32_t c, uint32_t L, uint64_t seed, uint32_t aip, uint32_t i)
+{
+    vo_state s;
+    memset(&s, 0, sizeof s);
+    s.c = c;
+    s.L = L;
+    s.key_h = vo_mix64(seed + 1);
+    return vo_h(&s, aip, i);
+}
+
+uint32_t vo_bh_of(uint32_t g, uint64_t seed, uint32_t bip)
+{
+    vo_state s;
+    memset(&s, 0, sizeof s);
+    s.g = g;
+    s.key_bh = vo_mix64(seed + 2);
+    return vo_bh(&s, bip);
+}
+
 /* ------------------------------------------------------------------ */
 /* AT blocks (Eq. 6-10).                                               */
 /* ------------------------------------------------------------------ */

@@ -63,6 +63,16 @@ def test_h_is_the_documented_composition(c, L):
             assert o.h(aip, i) == L * (x >> (32 - segbits)) + i % L
 
 
+def test_stateless_mapping_equals_the_pool_state_mapping():
+    for c, L, g, seed in [(18, 32, 1024, 5), (16, 1, 256, 9), (20, 64, 4096, 0xC2)]:
+        o = Oracle(c=c, k=3, g=g, seg_len=L, seed=seed)
+        for aip in (0, 7, 0xDEADBEEF):
+            for i in (0, 1, g // 2, g - 1):
+                assert oracle.h_of(c, L, seed, aip, i) == o.h(aip, i)
+        for bip in (0, 3, 0xFFFFFFFF):
+            assert oracle.bh_of(g, seed, bip) == o.bh(bip)
+
+
 def test_bh_range_and_uniformity():
     o = Oracle(c=16, k=3, g=64, seed=11)
     vals = np.array([o.bh(b) for b in range(20000)])

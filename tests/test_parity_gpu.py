@@ -473,3 +473,45 @@ def test_packed_recorders_and_pool_round_trip(V):
     assert e.value.code == V.VATE_EINVAL
     for h in (dr, at, d):
         h.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("L", [1, 32])
+def test_maximum_pool_2p32_on_sparse_input(V, L):
+    # 2^32 ATs (4 GiB), the largest pool: too large for the oracle's own pool,
+    # but on sparse input the exact answer follows from the mapping alone.
+    # By Corollary 1 an AT is active for window k' iff its position was last
+    # set less than k' slices ago, so the census holds exactly those positions
+    # at distances below k', and a host's A counts its VATs among them.
+    c, k, g, seed = 32, 4, 512, 0x32
+    rng = np.random.default_rng(L)
+    hosts = rng.integers(0, 2**32, 40, dtype=np.uint64).astype(np.uint32)
+    d = V.Vate(c, k, g, L, 0, seed)
+    last = {}                                   # position -> slice of its last SetAT
+    vats = {int(a): [oracle.h_of(c, L, seed, int(a), i) for i in range(g)] for a in hosts}
+    dh = dev_u32(hosts)
+    for s in (0, 1, 2, 5, 6, 7, 13):
+        a = hosts[rng.integers(0, len(hosts), 300)]
+        b = rng.integers(0, 2**32, 300, dtype=np.uint64).astype(np.uint32)
+        pairs = np.stack([a, b], 1)
+        d.ingest(dev_pairs(pairs), s)
+        d.close_slice(s)
+        for x, y in pairs:
+            last[oracle.h_of(c, L, seed, int(x), oracle.bh_of(g, seed, int(y)))] = s
+        hist = torch.empty(2 * k + 1, dtype=torch.int64, device="cuda")
+        d.census(hist)
+        hist = hist.cpu().numpy()
+        for kp in (1, 2, k):
+            live = {p for p, t in last.items() if s - t < kp}
+            assert int(hist[:kp].sum()) == len(live)
+            want = np.array([sum(p in live for p in vats[int(h)]) for h in hosts], np.uint32)
+            act = torch.empty(len(hosts), dtype=torch.int32, device="cuda")
+            d.active_counts(dh, kp, act)
+            np.testing.assert_array_equal(act.cpu().numpy().view(np.uint32), want)
+            est = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+            d.estimate(dh, kp, est)
+            n0 = (1 << c) - len(live)
+            oe = np.array([oracle.estimate_from_counts(g, 1 << c, n0, int(x))[0] for x in want])
+            err = np.abs(est.cpu().numpy().astype(np.float64) - oe) / np.maximum(np.abs(oe), 1.0)
+            assert err.max() <= RTOL
+    d.close()
