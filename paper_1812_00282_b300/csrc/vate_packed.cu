@@ -188,6 +188,79 @@ __global__ void __launch_bounds__(256) gather_packed_kernel(Geom G, uint32_t bac
     }
 }
 
+// Gather for widths B = 4..11 and segments of L <= 32 ATs: lane per segment.
+// In each round the lanes take 32 consecutive segments of the host, one each;
+// a lane loads the words its segment spans (at most MAXW, issued together),
+// then tests every field of them that belongs to the segment.  With
+// 2^B <= 64 the test is a lookup in a 64-bit mask of the active values;
+// wider fields use the distance arithmetic.
+template <int MODE, int B>
+__global__ void __launch_bounds__(256) gather_packed_seg_kernel(Geom G, uint32_t bact0, uint32_t kprime,
+                                                                const uint64_t *__restrict__ hist,
+                                                                const uint32_t *__restrict__ aips, uint64_t n,
+                                                                float *__restrict__ out, uint8_t *__restrict__ flags,
+                                                                uint32_t *__restrict__ active) {
+    constexpr uint32_t PN = 32 / B;                     // fields per word
+    constexpr uint32_t MAXW = (PN - 1 + 32 + PN - 1) / PN;   // words a segment of <= 32 fields can span
+    constexpr uint32_t M = (1u << B) - 1u;
+    __shared__ uint64_t sN0;
+    if (MODE == GATHER_ESTIMATE && threadIdx.x == 0) sN0 = pool_inactive(hist, G.P, kprime);
+    __syncthreads();
+    // the active values: bit u of amask (2^B <= 64)
+    uint64_t amask = 0;
+    if (B <= 6)
+        for (uint32_t u = 0; u < (1u << B); u++)
+            if (G.counter == 1u ? check_dr(u, kprime) : (u <= G.twok && check_at(u, bact0, kprime, G.twok)))
+                amask |= 1ull << u;
+    const uint32_t *words = reinterpret_cast<const uint32_t *>(G.pool);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t nseg = G.g >> G.log2L;
+    for (uint64_t h = warp0; h < n; h += nwarps) {
+        const uint64_t hk = host_key(G, aips[h]);
+        uint32_t cnt = 0;
+        for (uint32_t r0 = 0; r0 < nseg; r0 += 32u) {
+            const uint32_t s = r0 + lane;
+            if (s >= nseg) continue;
+            const uint32_t base = seg_base_k(G, hk, s);
+            const uint32_t q0 = base / PN, f0 = base - q0 * PN;
+            const uint32_t nw = (f0 + G.L + PN - 1) / PN;      // words holding the segment
+            uint32_t w[MAXW];
+#pragma unroll
+            for (uint32_t j = 0; j < MAXW; j++) w[j] = j < nw ? __ldg(words + q0 + j) : 0u;
+#pragma unroll
+            for (uint32_t j = 0; j < MAXW; j++) {
+#pragma unroll
+                for (uint32_t f = 0; f < PN; f++) {
+                    const uint32_t rel = j * PN + f;            // field index counted from the first word
+                    if (rel - f0 >= G.L) continue;              // outside the segment (also rel < f0)
+                    const uint32_t val = (w[j] >> (f * B)) & M;
+                    bool act;
+                    if (B <= 6) {
+                        act = (amask >> val) & 1u;
+                    } else if (G.counter == 1u) {
+                        act = check_dr(val, kprime);
+                    } else {
+                        act = val < G.twok && check_at(val, bact0, kprime, G.twok);
+                    }
+                    cnt += act ? 1u : 0u;
+                }
+            }
+        }
+        const uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
+        if (lane == 0) {
+            if (MODE == GATHER_ESTIMATE) {
+                uint8_t f;
+                out[h] = estimate_eq11(G.g, G.P, sN0, A, f);
+                if (flags) flags[h] = f;
+            } else {
+                active[h] = A;
+            }
+        }
+    }
+}
+
 // The paper's per-position values (uint8 for k <= 63, else uint16) of the n
 // positions from pos0, from the packed pool.
 __global__ void __launch_bounds__(256) packed_to_paper_kernel(Geom G, uint8_t *dst, uint64_t pos0, uint64_t n) {
@@ -273,6 +346,27 @@ cudaError_t launch_packed_gather(int mode, const Geom &G, uint32_t bact0, uint32
     if (n == 0) return cudaSuccess;
     uint64_t blocks = (n + 7) / 8;
     int grid = (int)(blocks < (uint64_t)sms * 64 ? blocks : (uint64_t)sms * 64);
+    if (G.L <= 32) {
+#define VATE_PACKED_SEG(B)                                                                                        \
+    case B:                                                                                                       \
+        return mode == GATHER_ESTIMATE                                                                            \
+                   ? launch_pool(G, gather_packed_seg_kernel<GATHER_ESTIMATE, B>, grid, 256, 0, st, G, bact0,     \
+                                 kprime, hist, aips, n, out, flags, active)                                       \
+                   : launch_pool(G, gather_packed_seg_kernel<GATHER_ACTIVE, B>, grid, 256, 0, st, G, bact0,       \
+                                 kprime, hist, aips, n, out, flags, active);
+        switch (G.atb) {
+            VATE_PACKED_SEG(4)
+            VATE_PACKED_SEG(5)
+            VATE_PACKED_SEG(6)
+            VATE_PACKED_SEG(7)
+            VATE_PACKED_SEG(8)
+            VATE_PACKED_SEG(9)
+            VATE_PACKED_SEG(10)
+            VATE_PACKED_SEG(11)
+            default: break;
+        }
+#undef VATE_PACKED_SEG
+    }
     if (mode == GATHER_ESTIMATE)
         return launch_pool(G, gather_packed_kernel<GATHER_ESTIMATE>, grid, 256, 0, st, G, bact0, kprime, hist, aips, n,
                            out, flags, active);
