@@ -197,8 +197,21 @@ __global__ void __launch_bounds__(G_THREADS) group_census_kernel(const Geom *__r
         const uint32_t bact0 = bact0_of(step, G.twok);
         uint32_t inactive_runs = 0;
         const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
-        for (uint64_t q = tile.chunk0 + threadIdx.x; q < tile.chunk0 + tile.nchunks; q += blockDim.x)
-            census_chunk(G, bact0, (uint32_t)(q << 4), __ldcg(pool16 + q), pat, col, inactive_runs);
+        // four chunks in flight per thread: the pools of a group exceed L2, so the loads wait on memory
+        const uint64_t qend = tile.chunk0 + tile.nchunks;
+        for (uint64_t q = tile.chunk0 + threadIdx.x; q < qend; q += 4ull * blockDim.x) {
+            uint4 w[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint64_t qu = q + (uint64_t)u * blockDim.x;
+                w[u] = qu < qend ? __ldcg(pool16 + qu) : make_uint4(pat, pat, pat, pat);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint64_t qu = q + (uint64_t)u * blockDim.x;
+                if (qu < qend) census_chunk(G, bact0, (uint32_t)(qu << 4), w[u], pat, col, inactive_runs);
+            }
+        }
         col[G.twok * 32u] += 16u * inactive_runs;
         __syncthreads();
         for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
