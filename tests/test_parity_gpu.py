@@ -515,3 +515,27 @@ def test_maximum_pool_2p32_on_sparse_input(V, L):
             err = np.abs(est.cpu().numpy().astype(np.float64) - oe) / np.maximum(np.abs(oe), 1.0)
             assert err.max() <= RTOL
     d.close()
+
+
+def test_empty_host_lists_are_no_ops(V):
+    # n = 0 hosts on every per-host entry point: no error, nothing written
+    d = V.Vate(16, 4, 512, 32, 0, 5)
+    p = Traffic(SMALL, pkts_per_slice=2000).slice_pairs(0)
+    d.ingest(dev_pairs(p), 0)
+    d.close_slice(0)
+    none = torch.zeros(0, dtype=torch.int32, device="cuda")
+    sentinel = torch.full((4,), -7.0, device="cuda")
+    d.estimate(none, 4, sentinel[:0])
+    d.active_counts(none, 4, torch.zeros(0, dtype=torch.int32, device="cuda"))
+    d.age_counts(none, torch.zeros(0, dtype=torch.int16, device="cuda"))
+    V.vate_estimate_host(d.h, np.zeros(0, np.uint32), 4, np.zeros(0, np.float32))
+    V.vate_features(d.h, none, torch.zeros(0, dtype=torch.float32, device="cuda"))
+    model = torch.empty(V.vate_mlp_param_count(10), dtype=torch.float32, device="cuda")
+    V.vate_mlp_init(model, 10, 1)
+    V.vate_estimate_learned(d.h, none, model, sentinel[:0])
+    hist = torch.empty(9, dtype=torch.int64, device="cuda")
+    d.census(hist)
+    V.vate_estimate_from_counts(d.params, none, hist, 4, sentinel[:0])
+    torch.cuda.synchronize()
+    assert torch.all(sentinel == -7.0)
+    d.close()
