@@ -496,8 +496,8 @@ def test_error_falls_with_pool_size_and_vector_length():
     k, t = 5, 7
     exact = window_cardinality(slices, t, k, tr.aips)
 
-    def mre(c, g, sel):
-        o = Oracle(c=c, k=k, g=g, seed=1)
+    def mre(c, g, sel, L=1):
+        o = Oracle(c=c, k=k, g=g, seg_len=L, seed=1)
         for s, arr in enumerate(slices):
             if s > 0:
                 o.advance()
@@ -509,6 +509,10 @@ def test_error_falls_with_pool_size_and_vector_length():
     small = exact >= 20
     by_c = [mre(c, 1024, small) for c in (17, 19, 21)]
     assert by_c[0] > by_c[1] > by_c[2], by_c
+    # the same trend with 32-VAT segments, which cost some accuracy at equal memory (clustered VATs)
+    by_c32 = [mre(c, 1024, small, L=32) for c in (17, 19, 21)]
+    assert by_c32[0] > by_c32[1] > by_c32[2], by_c32
+    assert by_c32[2] > by_c[2]
     top = np.zeros_like(small)
     top[np.argsort(exact)[-16:]] = True
     by_g = [mre(21, g, top) for g in (128, 512, 2048)]
