@@ -138,6 +138,9 @@ typedef struct vate_handle vate_handle;
  * slice 0 of Algorithm 4.  Errors: VATE_EINVAL (parameters), VATE_ENOMEM,
  * VATE_ECUDA.  *out is set only on success. */
 int vate_create(const vate_params *params, void *stream, vate_handle **out);
+/* The handle belongs to the device current at creation: every later call that
+ * queues work on it must be made with that device current (the library never
+ * switches the calling thread's device); otherwise VATE_EINVAL. */
 
 /* Free the pool and every buffer of the handle (synchronises the device work
  * of the handle first).  NULL is accepted. */

@@ -1,6 +1,7 @@
 // vate_api.cu -- C ABI of the VATE library: argument checks, the slice state
 // machine of Algorithm 4 on the host, device buffers, kernel launches.
 #include <atomic>
+#include <mutex>
 #include <cstddef>
 #include <cstdarg>
 #include <cstdio>
@@ -138,6 +139,10 @@ namespace vate {
 // read-only view of a handle for the other translation units of the library
 int handle_view(const vate_handle *h, HandleView *v) {
     if (!h) return fail(VATE_EINVAL, "handle is NULL");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device)
+        return fail(VATE_EINVAL, "the handle lives on device %d but device %d is current (cudaSetDevice first)",
+                    h->device, dev);
     v->G = h->G;
     v->bact0 = h->bact0;
     v->hist = h->d_hist;
@@ -149,8 +154,15 @@ int handle_view(const vate_handle *h, HandleView *v) {
 
 namespace {
 
+// A handle's memory and streams belong to the device it was created on; the
+// library never switches the calling thread's device, so calls that queue
+// work on a handle must be made with that device current.
 int check_handle(const vate_handle *h) {
     if (!h) return fail(VATE_EINVAL, "handle is NULL");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device)
+        return fail(VATE_EINVAL, "the handle lives on device %d but device %d is current (cudaSetDevice first)",
+                    h->device, dev);
     return VATE_OK;
 }
 
@@ -210,6 +222,21 @@ int check_slice(const vate_handle *h, int64_t slice) {
     if (h->slice >= 0 && slice == h->slice && h->closed)
         return fail(VATE_ESLICE, "slice %lld is already closed", (long long)slice);
     return VATE_OK;
+}
+
+// The kernels' shared-memory limits are attributes of the current device:
+// set them once per device, under a lock (handles may be created from
+// several threads and on several devices).
+std::mutex g_prep_mu;
+bool g_prepared[256] = {};
+
+cudaError_t prepare_device(int dev) {
+    std::lock_guard<std::mutex> lock(g_prep_mu);
+    if (dev >= 0 && dev < 256 && g_prepared[dev]) return cudaSuccess;
+    cudaError_t e = vate::census_prepare(126);
+    if (e == cudaSuccess) e = vate::age_prepare(63);
+    if (e == cudaSuccess && dev >= 0 && dev < 256) g_prepared[dev] = true;
+    return e;
 }
 
 int ensure_staging(vate_handle *h) {
@@ -286,15 +313,10 @@ static int create_range(const vate_params *params, uint64_t lo, uint64_t hi, voi
         delete h;
         return cuda_fail(e, "no usable CUDA device");
     }
-    static bool prepared = false;
-    if (!prepared) {
-        e = vate::census_prepare(126);
-        if (e == cudaSuccess) e = vate::age_prepare(63);
-        if (e != cudaSuccess) {
-            delete h;
-            return cuda_fail(e, "kernel attributes");
-        }
-        prepared = true;
+    e = prepare_device(h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "kernel attributes");
     }
     // Keep the pool resident in L2: its kernels launch with a persisting
     // access-policy window over it (hit ratio = persisting capacity / pool).
@@ -378,7 +400,7 @@ int vate_destroy(vate_handle *h) {
 }
 
 int vate_get_info(const vate_handle *h, vate_info *out) {
-    if (int rc = check_handle(h)) return rc;
+    if (!h) return fail(VATE_EINVAL, "handle is NULL");
     if (!out) return fail(VATE_EINVAL, "out is NULL");
     out->pool_size = h->G.P;
     out->block_a = h->G.a;
@@ -608,7 +630,7 @@ constexpr uint64_t CHECKSUM_AT = offsetof(vate_checkpoint_header, checksum);
 extern "C" {
 
 int vate_checkpoint_size(const vate_handle *h, uint64_t *bytes) {
-    if (int rc = check_handle(h)) return rc;
+    if (!h) return fail(VATE_EINVAL, "handle is NULL");
     if (int rc = whole_pool_only(h, "a checkpoint")) return rc;
     if (!bytes) return fail(VATE_EINVAL, "bytes is NULL");
     *bytes = image_bytes(h->G.twok, h->G.P * h->G.atw);
