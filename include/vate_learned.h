@@ -5,7 +5,7 @@
  * MLP that maps what the pool knows about a host at the end of slice t to
  * log(1 + |OP(aip, t-k+1, k)|), trained on streams the method itself produces
  * with exact labels.  The counters stay exact integers; the closed form stays
- * available as the fallback and as the judge of the MLP's error.
+ * available as the fallback and as the yardstick of the MLP's error.
  *
  * Features of a host (n_in = 2k + 2 floats, k <= 15):
  *   x[d]        = c_d / g for 0 <= d < k, c_d = the host's VATs at distance d

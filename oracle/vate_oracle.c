@@ -33,7 +33,7 @@
  *   R5  Algorithm 3 is normative; Algorithm 2 is kept as a cross-check (they
  *       differ only when Value == ACT at a maintenance point, a state no run
  *       from InitAT can reach).
- *   R7  H and BH are "random hash functions" in the paper; this build fixes
+ *   R7  H and BH are "random hash functions" in the paper; the oracle fixes
  *       them to published mixers: BH is the SplitMix64 output function
  *       (Steele, Lea & Flood 2014) with Lemire's multiply-shift range
  *       reduction; H places the g virtual ATs of a host in segments of L

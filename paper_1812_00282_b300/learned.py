@@ -5,7 +5,7 @@ estimate -- runs in the library's kernels; this module only moves data:
 it drives a VATE handle through generated slices, labels sampled hosts with
 their exact window cardinality (distinct (aip, bip) keys of the last k
 slices, by sort-unique on the device), and feeds batches to
-vate_mlp_train_step.  The closed form of Eq. 11 is kept as the judge: a model
+vate_mlp_train_step.  The closed form of Eq. 11 is kept as the yardstick: a model
 whose mean relative error on held-out slices is worse than the closed form's
 is not accepted.
 """
