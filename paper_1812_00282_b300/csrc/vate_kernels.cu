@@ -203,49 +203,65 @@ __global__ void __launch_bounds__(256) dr_age16_kernel(uint16_t *__restrict__ po
     }
 }
 
-// Census of a 16-bit pool (k >= 64): one shared histogram per block (2k + 1
-// bins, shared-memory atomics; inactive ATs are counted in a register), the
-// same block rows and last-block reduction as census_kernel.
+// Census of a 16-bit pool (k >= 64): one shared histogram per warp (2k + 1
+// bins, shared-memory atomics, so that the warps of a block do not contend
+// for the same bins; inactive ATs are counted in a register), two chunks in
+// flight per thread, then the same block rows and last-block reduction as
+// census_kernel.
 __global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ partial,
                                                                   uint64_t *__restrict__ hist,
                                                                   unsigned int *__restrict__ ticket) {
-    extern __shared__ uint32_t hsh[];   // [nbins]
+    extern __shared__ uint32_t hsh_all[];   // [warps][nbins]
     const uint32_t nbins = G.twok + 1u;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) hsh[i] = 0;
+    uint32_t *hsh = hsh_all + (size_t)warp * nbins;
+    for (uint32_t i = threadIdx.x; i < nwarps * nbins; i += blockDim.x) hsh_all[i] = 0;
     __syncthreads();
     const uint32_t inact = G.counter == 1u ? G.k : G.twok;
     const uint32_t pat = inact * ONES16;
     uint32_t inactive = 0;
     const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
-    for (uint64_t q = (G.lo >> 3) + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < (G.hi >> 3);
-         q += (uint64_t)gridDim.x * blockDim.x) {
-        uint4 w = __ldcg(pool16 + q);
-        if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
-            inactive += 8u;
-            continue;
-        }
-        uint32_t words[4] = {w.x, w.y, w.z, w.w};
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t end = G.hi >> 3;
+    // four chunks in flight per thread (a 16-bit pool is usually larger than L2); the per-AT step is
+    // branch-free so that the lanes of a warp stay together
+    constexpr int U = 4;
+    for (uint64_t q = (G.lo >> 3) + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < end; q += U * stride) {
+        uint4 ws[U];
 #pragma unroll
-        for (int e = 0; e < 8; e++) {
-            uint32_t v = (words[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
-            if (v >= inact) {
-                inactive++;
+        for (int c = 0; c < U; c++) {
+            const uint64_t qc = q + (uint64_t)c * stride;
+            ws[c] = qc < end ? __ldcg(pool16 + qc) : make_uint4(pat, pat, pat, pat);
+        }
+#pragma unroll
+        for (int c = 0; c < U; c++) {
+            const uint4 w = ws[c];
+            const bool real = q + (uint64_t)c * stride < end;
+            if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
+                inactive += real ? 8u : 0u;
                 continue;
             }
-            uint32_t d = v;                               // a recorder's value is its distance
-            if (G.counter != 1u) {                        // frame 0: ACT = BACT^0 for every AT
-                d = bact0 + G.twok - v;
-                if (d >= G.twok) d -= G.twok;
+            const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const uint32_t v = (words[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+                const bool act = v < inact;
+                uint32_t d = bact0 + G.twok - v;          // frame 0: ACT = BACT^0 for every AT
+                d = d >= G.twok ? d - G.twok : d;
+                d = G.counter == 1u ? v : d;              // a recorder's value is its distance
+                inactive += act ? 0u : 1u;
+                if (act) atomicAdd(&hsh[d], 1u);
             }
-            atomicAdd(&hsh[d], 1u);
         }
     }
     inactive = __reduce_add_sync(0xFFFFFFFFu, inactive);
     if (lane == 0) atomicAdd(&hsh[G.twok], inactive);
     __syncthreads();
-    for (uint32_t bin = threadIdx.x; bin < nbins; bin += blockDim.x)
-        partial[(uint64_t)blockIdx.x * nbins + bin] = hsh[bin];
+    for (uint32_t bin = threadIdx.x; bin < nbins; bin += blockDim.x) {
+        uint32_t t = 0;
+        for (uint32_t wv = 0; wv < nwarps; wv++) t += hsh_all[(size_t)wv * nbins + bin];
+        partial[(uint64_t)blockIdx.x * nbins + bin] = t;
+    }
     __threadfence();
     __shared__ bool last;
     __syncthreads();
@@ -547,16 +563,21 @@ cudaError_t launch_frame_convert(const Geom &G, const uint8_t *src, uint8_t *dst
 size_t census_smem_bytes(uint32_t twok) { return (size_t)(CENSUS_THREADS / 32) * (twok + 1) * 32 * sizeof(uint32_t); }
 
 cudaError_t census_prepare(uint32_t twok) {
-    return cudaFuncSetAttribute(census_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)census_smem_bytes(twok));
+    cudaError_t e = cudaFuncSetAttribute(census_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)census_smem_bytes(twok));
+    if (e != cudaSuccess) return e;
+    // 16-bit pools: one histogram of up to 2 * 1023 + 1 bins per warp
+    return cudaFuncSetAttribute(census16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((CENSUS_THREADS / 32) * (2 * 1023 + 1) * sizeof(uint32_t)));
 }
 
 cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,
                           unsigned int *ticket, cudaStream_t st) {
     if (G.packed) return launch_packed_census(G, bact0, partial, grid, hist, ticket, st);
     if (G.atw == 2u)
-        return launch_pool(G, census16_kernel, grid, CENSUS_THREADS, (size_t)(G.twok + 1) * sizeof(uint32_t), st, G,
-                           bact0, partial, hist, ticket);
+        return launch_pool(G, census16_kernel, grid, CENSUS_THREADS,
+                           (size_t)(CENSUS_THREADS / 32) * (G.twok + 1) * sizeof(uint32_t), st, G, bact0, partial, hist,
+                           ticket);
     return launch_pool(G, census_kernel, grid, CENSUS_THREADS, census_smem_bytes(G.twok), st, G, bact0, partial, hist,
                        ticket);
 }
