@@ -86,6 +86,40 @@ __device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint
     }
 }
 
+// The end of a census whose block counted into nrows shared-memory rows of
+// nbins bins (rows[r * nbins + b]): the block's sum of the rows goes to its
+// row of partial; the last block to finish adds all rows of partial into hist
+// and re-arms ticket for the next launch.  Called by every thread of the block.
+__device__ __forceinline__ void census_finish(const uint32_t *rows, uint32_t nrows, uint32_t nbins,
+                                              uint64_t *__restrict__ partial, uint64_t *__restrict__ hist,
+                                              unsigned int *__restrict__ ticket) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    __syncthreads();
+    for (uint32_t bin = threadIdx.x; bin < nbins; bin += blockDim.x) {
+        uint32_t t = 0;
+        for (uint32_t r = 0; r < nrows; r++) t += rows[(size_t)r * nbins + bin];
+        partial[(uint64_t)blockIdx.x * nbins + bin] = t;
+    }
+    __threadfence();
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1u);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
+        uint64_t s = 0;
+        for (uint32_t blk = lane; blk < gridDim.x; blk += 32u) s += __ldcg(partial + (uint64_t)blk * nbins + bin);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+        if (lane == 0) hist[bin] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 // Eq. 11 in FP32 from exact integers: g * log1p((N0*g - V0*P) / (V0*P)).
 __device__ __forceinline__ float estimate_eq11(uint32_t g, uint64_t P, uint64_t N0, uint32_t A, uint8_t &flags) {
     flags = 0;

@@ -256,30 +256,7 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32
     }
     inactive = __reduce_add_sync(0xFFFFFFFFu, inactive);
     if (lane == 0) atomicAdd(&hsh[G.twok], inactive);
-    __syncthreads();
-    for (uint32_t bin = threadIdx.x; bin < nbins; bin += blockDim.x) {
-        uint32_t t = 0;
-        for (uint32_t wv = 0; wv < nwarps; wv++) t += hsh_all[(size_t)wv * nbins + bin];
-        partial[(uint64_t)blockIdx.x * nbins + bin] = t;
-    }
-    __threadfence();
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1u);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
-        uint64_t s = 0;
-        for (uint32_t blk = lane; blk < gridDim.x; blk += 32u) s += __ldcg(partial + (uint64_t)blk * nbins + bin);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
-        if (lane == 0) hist[bin] = s;
-    }
-    if (threadIdx.x == 0) *ticket = 0u;
+    census_finish(hsh_all, nwarps, nbins, partial, hist, ticket);
 }
 
 // --------------------------------------------------------------------------

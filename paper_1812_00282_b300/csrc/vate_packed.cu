@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_packed_kernel(Geom G, u
                                                                        unsigned int *__restrict__ ticket) {
     extern __shared__ uint32_t hsh[];   // [nbins]
     const uint32_t nbins = G.twok + 1u;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
     for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) hsh[i] = 0;
     __syncthreads();
     const uint32_t inact = inactive_value(G);
@@ -115,27 +115,7 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_packed_kernel(Geom G, u
     }
     inactive = __reduce_add_sync(0xFFFFFFFFu, inactive);
     if (lane == 0) atomicAdd(&hsh[G.twok], inactive);
-    __syncthreads();
-    for (uint32_t bin = threadIdx.x; bin < nbins; bin += blockDim.x)
-        partial[(uint64_t)blockIdx.x * nbins + bin] = hsh[bin];
-    __threadfence();
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1u);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
-        uint64_t s = 0;
-        for (uint32_t blk = lane; blk < gridDim.x; blk += 32u) s += __ldcg(partial + (uint64_t)blk * nbins + bin);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
-        if (lane == 0) hist[bin] = s;
-    }
-    if (threadIdx.x == 0) *ticket = 0u;
+    census_finish(hsh, 1, nbins, partial, hist, ticket);
 }
 
 // Gather: warp per host.  In each round the lanes hash 32 consecutive
