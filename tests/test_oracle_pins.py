@@ -73,6 +73,20 @@ def test_stateless_mapping_equals_the_pool_state_mapping():
             assert oracle.bh_of(g, seed, bip) == o.bh(bip)
 
 
+@pytest.mark.parametrize("g", [1, 64, 1000, 4096, 65536])
+def test_bh_is_the_documented_composition(g):
+    # BH(bip) = ((mix64(mix64(seed + 2) ^ bip) >> 32) * g) >> 32: Lemire's
+    # multiply-shift range reduction of the high half of the pinned mixer
+    seed = 0xC2
+    o = Oracle(c=16, k=3, g=g, seed=seed) if g <= 4096 else None
+    key_bh = oracle.mix64(seed + 2)
+    for bip in (0, 1, 7, 0x80000000, 0xFFFFFFFF, 123456789):
+        want = ((oracle.mix64(key_bh ^ bip) >> 32) * g) >> 32
+        assert oracle.bh_of(g, seed, bip) == want
+        if o is not None:
+            assert o.bh(bip) == want
+
+
 def test_bh_range_and_uniformity():
     o = Oracle(c=16, k=3, g=64, seed=11)
     vals = np.array([o.bh(b) for b in range(20000)])
