@@ -186,3 +186,32 @@ def test_learned_close_matches_direct_learned_estimate(V):
     for s in range(len(slices)):
         np.testing.assert_array_equal(res[s][0], ref[s][0])
         np.testing.assert_array_equal(res[s][1], ref[s][1])
+
+
+def test_wide_and_packed_monitors_are_served_exactly(V):
+    # 16-bit ATs (k = 100) and the packed layout (5-bit fields) through the
+    # server: the same results as their own handles, and memory counted by layout
+    tr = Traffic(SMALL, pkts_per_slice=8_000)
+    slices = [tr.slice_pairs(s) for s in range(5)]
+    hosts = tr.aips[:800]
+    cases = [((17, 100, 512, 32, 0, 21), 0), ((17, 10, 512, 32, 0, 22), 5)]
+    srv = V.vate_server_create(1 << 30, slots=4, slot_records=4096)
+    for params, bits in cases:
+        ref = []
+        d = V.Vate(*params, at_bits=bits)
+        for s, p in enumerate(slices):
+            d.ingest(as_i32(p), s)
+            d.close_slice(s)
+            e = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+            d.estimate(as_i32(hosts), params[1], e)
+            ref.append(e.cpu().numpy())
+        d.close()
+        before = V.vate_server_get_stats(srv).memory_in_use
+        mid = V.vate_server_admit(srv, V.make_params(*params, at_bits=bits))
+        pool_bytes = V.vate_server_get_stats(srv).memory_in_use - before
+        want = (2 << 17) if params[1] > 63 else (((1 << 17) + 5) // 6 * 4 + 15) // 16 * 16
+        assert pool_bytes >= want and pool_bytes < want + (1 << 20)
+        got = serve_monitor(V, srv, mid, slices, hosts, params[1], np.random.default_rng(bits))
+        for s in range(len(slices)):
+            np.testing.assert_array_equal(got[s][0], ref[s])
+    V.vate_server_destroy(srv)
