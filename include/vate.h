@@ -242,15 +242,14 @@ int vate_host_block(const vate_params *params, uint64_t pid, uint32_t *block);
  *   bact0    BACT^0 of the slice the pool belongs to, 0 <= bact0 < 2k.
  *   d_hist   device uint64[2k+1]: receives the same census as vate_census
  *            (d_hist[d] for distances 0 <= d < 2k, d_hist[2k] inactive).
- * Scratch: the per-block partial histograms and a "blocks finished" counter
- * live in one static device array of 300,992 bytes (296 blocks x 127 bins x
- * 8 bytes + 256), which every GPU that loads the library holds until the
- * process exits.  A request needing more (more than 127 bins) is rejected with
- * VATE_EINVAL and a message giving both sizes.
+ * Scratch: the counters the census blocks add into (127 x 8 bytes) and a
+ * "blocks finished" counter live in one static device array of 1,272 bytes,
+ * which every GPU that loads the library holds until the process exits.  A
+ * request needing more than 127 bins (k > 63) is rejected with VATE_EINVAL.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and caches it; make that
  * first call before any stream capture.  Every call reuses the same array and
- * clears its counter first, so calls whose work overlaps on the GPU (other
+ * clears it first, so calls whose work overlaps on the GPU (other
  * streams, other host threads) race: order them on one stream.  No
  * cudaMalloc, cudaFree or allocating library routine is called. */
 int vate_census_noalloc(const vate_params *params, const uint8_t *d_pool, uint32_t bact0, uint64_t *d_hist,

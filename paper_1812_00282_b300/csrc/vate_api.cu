@@ -121,9 +121,8 @@ struct vate_handle {
     bool closed = false;
     uint32_t bact0 = 0;
     uint64_t *d_hist = nullptr;       // census of the last close, 2k+1 counters
-    uint64_t *d_partial = nullptr;    // census scratch: one row per block
+    uint64_t *d_acc = nullptr;        // census scratch: 2k+1 counters the blocks add into, zero between calls
     unsigned int *d_ticket = nullptr; // census scratch: blocks finished
-    int census_grid = 0;
     // host-copy staging (allocated on first use)
     cudaStream_t copy_stream = nullptr;      // host -> device
     cudaStream_t d2h_stream = nullptr;       // device -> host (estimates)
@@ -333,12 +332,11 @@ static int create_range(const vate_params *params, uint64_t lo, uint64_t hi, voi
             h->G.l2_hit_ratio = ratio >= 1.0 ? 1.0f : (float)ratio;
         }
     }
-    h->census_grid = h->sms * 4;
     size_t nbins = G.twok + 1;
     uint8_t *mem = nullptr;
     if (cudaMalloc(&mem, held_bytes) == cudaSuccess) h->G.pool = mem - G.lo * G.atw;   // position 0's address
     if (!mem || cudaMalloc(&h->d_hist, nbins * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMalloc(&h->d_partial, (size_t)h->census_grid * nbins * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_acc, nbins * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&h->d_ticket, sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
         vate_destroy(h);
@@ -346,6 +344,7 @@ static int create_range(const vate_params *params, uint64_t lo, uint64_t hi, voi
     }
     e = cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_hist, 0, nbins * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc, 0, nbins * sizeof(uint64_t), st);
     if (e == cudaSuccess) e = vate::launch_init(h->G, st, h->sms);
     if (e != cudaSuccess) {
         vate_destroy(h);
@@ -383,7 +382,7 @@ int vate_destroy(vate_handle *h) {
     }
     if (h->G.pool) cudaFree(vate::pool_mem(h->G));
     cudaFree(h->d_hist);
-    cudaFree(h->d_partial);
+    cudaFree(h->d_acc);
     cudaFree(h->d_ticket);
     for (int i = 0; i < 2; i++) {
         cudaFree(h->d_stage[i]);
@@ -430,7 +429,7 @@ int vate_close_slice(vate_handle *h, int64_t slice, void *stream) {
     if (int rc = check_slice(h, slice)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     if (int rc = advance_to(h, slice, st)) return rc;
-    cudaError_t e = vate::launch_census(h->G, h->bact0, h->d_partial, h->census_grid, h->d_hist, h->d_ticket, st);
+    cudaError_t e = vate::launch_census(h->G, h->bact0, h->d_acc, h->sms, h->d_hist, h->d_ticket, st);
     if (e != cudaSuccess) return cuda_fail(e, "census launch");
     h->closed = true;
     return VATE_OK;

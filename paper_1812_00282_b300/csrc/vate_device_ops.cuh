@@ -86,38 +86,43 @@ __device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint
     }
 }
 
+// The end of a census, once a block has added its counts into acc (2k + 1
+// counters that are zero between calls) with 64-bit atomics: the last block to
+// finish copies acc into hist, zeroes acc and re-arms ticket for the next
+// launch.  Called by every thread of the block.
+__device__ __forceinline__ void census_publish(uint64_t *__restrict__ acc, uint64_t *__restrict__ hist,
+                                               unsigned int *__restrict__ ticket, uint32_t nbins) {
+    __threadfence();
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x) {
+        hist[b] = __ldcg(acc + b);
+        acc[b] = 0;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+__device__ __forceinline__ void census_add(uint64_t *acc, uint32_t bin, uint32_t count) {
+    if (count) atomicAdd(reinterpret_cast<unsigned long long *>(acc + bin), (unsigned long long)count);
+}
+
 // The end of a census whose block counted into nrows shared-memory rows of
-// nbins bins (rows[r * nbins + b]): the block's sum of the rows goes to its
-// row of partial; the last block to finish adds all rows of partial into hist
-// and re-arms ticket for the next launch.  Called by every thread of the block.
+// nbins bins (rows[r * nbins + b]): the block's sum of the rows goes into acc,
+// then census_publish.  Called by every thread of the block.
 __device__ __forceinline__ void census_finish(const uint32_t *rows, uint32_t nrows, uint32_t nbins,
-                                              uint64_t *__restrict__ partial, uint64_t *__restrict__ hist,
+                                              uint64_t *__restrict__ acc, uint64_t *__restrict__ hist,
                                               unsigned int *__restrict__ ticket) {
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     __syncthreads();
     for (uint32_t bin = threadIdx.x; bin < nbins; bin += blockDim.x) {
         uint32_t t = 0;
         for (uint32_t r = 0; r < nrows; r++) t += rows[(size_t)r * nbins + bin];
-        partial[(uint64_t)blockIdx.x * nbins + bin] = t;
+        census_add(acc, bin, t);
     }
-    __threadfence();
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1u);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
-        uint64_t s = 0;
-        for (uint32_t blk = lane; blk < gridDim.x; blk += 32u) s += __ldcg(partial + (uint64_t)blk * nbins + bin);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
-        if (lane == 0) hist[bin] = s;
-    }
-    if (threadIdx.x == 0) *ticket = 0u;
+    census_publish(acc, hist, ticket, nbins);
 }
 
 // Eq. 11 in FP32 from exact integers: g * log1p((N0*g - V0*P) / (V0*P)).

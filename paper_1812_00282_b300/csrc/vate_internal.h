@@ -38,7 +38,9 @@ cudaError_t launch_frame_convert(const Geom &G, const uint8_t *src, uint8_t *dst
                                  bool to_paper, cudaStream_t st, int sms);
 size_t census_smem_bytes(uint32_t twok);
 cudaError_t census_prepare(uint32_t twok);
-cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,
+// the pool census into hist (2k + 1 counters); acc (2k + 1 counters) and
+// ticket are scratch that must be zero before the first call and are left zero
+cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *acc, int sms, uint64_t *hist,
                           unsigned int *ticket, cudaStream_t st);
 cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kprime, const uint64_t *hist,
                           const uint32_t *aips, uint64_t n, float *out, uint8_t *flags, uint32_t *active,
@@ -50,7 +52,7 @@ cudaError_t launch_packed_init(const Geom &G, cudaStream_t st, int sms);
 cudaError_t launch_packed_preserve(const Geom &G, uint32_t bact0, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
                                    cudaStream_t st, int sms);
 cudaError_t launch_packed_dr_age(const Geom &G, cudaStream_t st, int sms);
-cudaError_t launch_packed_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,
+cudaError_t launch_packed_census(const Geom &G, uint32_t bact0, uint64_t *acc, int grid, uint64_t *hist,
                                  unsigned int *ticket, cudaStream_t st);
 cudaError_t launch_packed_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kprime, const uint64_t *hist,
                                  const uint32_t *aips, uint64_t n, float *out, uint8_t *flags, uint32_t *active,

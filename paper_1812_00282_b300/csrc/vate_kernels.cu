@@ -206,9 +206,9 @@ __global__ void __launch_bounds__(256) dr_age16_kernel(uint16_t *__restrict__ po
 // Census of a 16-bit pool (k >= 64): one shared histogram per warp (2k + 1
 // bins, shared-memory atomics, so that the warps of a block do not contend
 // for the same bins; inactive ATs are counted in a register), two chunks in
-// flight per thread, then the same block rows and last-block reduction as
+// flight per thread, then the block's sums added into acc and published as in
 // census_kernel.
-__global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ partial,
+__global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ acc,
                                                                   uint64_t *__restrict__ hist,
                                                                   unsigned int *__restrict__ ticket) {
     extern __shared__ uint32_t hsh_all[];   // [warps][nbins]
@@ -256,19 +256,31 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32
     }
     inactive = __reduce_add_sync(0xFFFFFFFFu, inactive);
     if (lane == 0) atomicAdd(&hsh[G.twok], inactive);
-    census_finish(hsh_all, nwarps, nbins, partial, hist, ticket);
+    census_finish(hsh_all, nwarps, nbins, acc, hist, ticket);
 }
 
 // --------------------------------------------------------------------------
 // Census: hist[d] = ATs at distance d (d < 2k), hist[2k] = inactive ATs.
 // Each lane keeps a private column of the block's shared histogram
-// (bin * 32 + lane: no bank conflicts, no atomics).  A chunk of 16 inactive
-// ATs is counted in a register; otherwise the four words are turned into bin
-// bytes with SWAR (one ACT per chunk when the chunk lies in one block).
-// Block rows go to `partial`; the last block to finish adds the rows up into
-// `hist` and re-arms `ticket` for the next call.
+// (bin * 32 + lane: no bank conflicts) and counts with shared-memory atomics
+// that return nothing, so consecutive ATs of one bin do not wait on each
+// other.  A chunk of 16 inactive ATs is counted in a register.
+//
+// RAW (timestamps in the frame of block 0, or distance recorders): every AT
+// of the pool is read with the same ACT, so the census is the histogram of
+// the stored values with its bins relabelled once per block -- value u at
+// distance (BACT^0 - u) mod 2k, a recorder's value its own distance -- and an
+// AT costs one byte extract, one clamp and one atomic.  Values above the
+// inactive one are clamped to it, as the SWAR bins would count them, which
+// also keeps every column index inside the block's histogram.
+// Otherwise (the paper's per-block values of a caller's pool) the chunk's
+// bins are computed with SWAR, one ACT per chunk when it lies in one block.
+//
+// Eight 16-byte chunks are in flight per thread; the block's sums go into acc
+// with 64-bit atomics and the last block publishes them (census_publish).
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ partial,
+template <int RAW>
+__global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ acc,
                                                                 uint64_t *__restrict__ hist,
                                                                 unsigned int *__restrict__ ticket) {
     extern __shared__ uint32_t sh[];   // [warps][nbins][32]
@@ -279,47 +291,60 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
     for (uint32_t i = threadIdx.x; i < nwarps * nbins * 32u; i += blockDim.x) sh[i] = 0;
     __syncthreads();
 
-    const uint32_t pat = (G.counter == 1u ? G.k : G.twok) * ONES;   // 16 inactive counters
-    uint32_t inactive_runs = 0;   // chunks of 16 inactive ATs
-    const uint64_t n16 = G.hi >> 4;                         // chunks of the positions held, [lo, hi)
+    const uint32_t inact = G.counter == 1u ? G.k : G.twok;   // the inactive value, < nbins
+    const uint32_t pat = inact * ONES;                        // 16 inactive counters
+    uint32_t runs = 0;                                        // chunks of 16 inactive ATs
+    const uint64_t n16 = G.hi >> 4;                           // chunks of the positions held, [lo, hi)
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
-    for (uint64_t q = (G.lo >> 4) + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n16; q += 2 * stride) {
-        uint64_t q2 = q + stride;
-        uint4 w0 = __ldcg(pool16 + q);
-        uint4 w1 = make_uint4(pat, pat, pat, pat);
-        if (q2 < n16) w1 = __ldcg(pool16 + q2);
-        census_chunk(G, bact0, (uint32_t)(q << 4), w0, pat, col, inactive_runs);
-        if (q2 < n16) census_chunk(G, bact0, (uint32_t)(q2 << 4), w1, pat, col, inactive_runs);
+    constexpr int U = 8;
+    for (uint64_t q = (G.lo >> 4) + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n16; q += U * stride) {
+        uint4 w[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint64_t qu = q + (uint64_t)u * stride;
+            w[u] = qu < n16 ? __ldcg(pool16 + qu) : make_uint4(pat, pat, pat, pat);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint64_t qu = q + (uint64_t)u * stride;
+            if (qu >= n16) continue;
+            if (!RAW) {
+                census_chunk(G, bact0, (uint32_t)(qu << 4), w[u], pat, col, runs);
+                continue;
+            }
+            if (w[u].x == pat && w[u].y == pat && w[u].z == pat && w[u].w == pat) {
+                runs++;
+                continue;
+            }
+            const uint32_t words[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+            for (int b = 0; b < 16; b++) {
+                const uint32_t v = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, inact);
+                atomicAdd(&col[v * 32u], 1u);
+            }
+        }
     }
-    col[G.twok * 32u] += 16u * inactive_runs;
+    col[(RAW ? inact : G.twok) * 32u] += 16u * runs;
     __syncthreads();
 
-    // block row: warp w sums bins w, w + nwarps, ... over every warp's lane columns
-    for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
+    // warp w sums rows w, w + nwarps, ... over every warp's lane columns
+    for (uint32_t r = warp; r < nbins; r += nwarps) {
         uint32_t s = 0;
-        for (uint32_t wv = 0; wv < nwarps; wv++) s += sh[((size_t)wv * nbins + bin) * 32u + lane];
+        for (uint32_t wv = 0; wv < nwarps; wv++) s += sh[((size_t)wv * nbins + r) * 32u + lane];
         s = __reduce_add_sync(0xFFFFFFFFu, s);
-        if (lane == 0) partial[(uint64_t)blockIdx.x * nbins + bin] = s;
+        uint32_t bin = r;
+        if (RAW) {
+            if (G.counter == 1u) {
+                bin = r < G.k ? r : G.twok;
+            } else if (r < G.twok) {
+                bin = bact0 + G.twok - r;
+                bin = bin >= G.twok ? bin - G.twok : bin;
+            }
+        }
+        if (lane == 0) census_add(acc, bin, s);
     }
-    __threadfence();
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1u);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
-        uint64_t s = 0;
-        for (uint32_t blk = lane; blk < gridDim.x; blk += 32u) s += __ldcg(partial + (uint64_t)blk * nbins + bin);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
-        if (lane == 0) hist[bin] = s;
-    }
-    if (threadIdx.x == 0) *ticket = 0u;
+    census_publish(acc, hist, ticket, nbins);
 }
 
 // --------------------------------------------------------------------------
@@ -540,22 +565,30 @@ cudaError_t launch_frame_convert(const Geom &G, const uint8_t *src, uint8_t *dst
 size_t census_smem_bytes(uint32_t twok) { return (size_t)(CENSUS_THREADS / 32) * (twok + 1) * 32 * sizeof(uint32_t); }
 
 cudaError_t census_prepare(uint32_t twok) {
-    cudaError_t e = cudaFuncSetAttribute(census_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(census_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)census_smem_bytes(twok));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(census_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)census_smem_bytes(twok));
     if (e != cudaSuccess) return e;
     // 16-bit pools: one histogram of up to 2 * 1023 + 1 bins per warp
     return cudaFuncSetAttribute(census16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)((CENSUS_THREADS / 32) * (2 * 1023 + 1) * sizeof(uint32_t)));
 }
 
-cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,
+cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *acc, int sms, uint64_t *hist,
                           unsigned int *ticket, cudaStream_t st) {
-    if (G.packed) return launch_packed_census(G, bact0, partial, grid, hist, ticket, st);
+    if (G.packed) return launch_packed_census(G, bact0, acc, sms * 4, hist, ticket, st);
     if (G.atw == 2u)
-        return launch_pool(G, census16_kernel, grid, CENSUS_THREADS,
-                           (size_t)(CENSUS_THREADS / 32) * (G.twok + 1) * sizeof(uint32_t), st, G, bact0, partial, hist,
+        return launch_pool(G, census16_kernel, sms * 4, CENSUS_THREADS,
+                           (size_t)(CENSUS_THREADS / 32) * (G.twok + 1) * sizeof(uint32_t), st, G, bact0, acc, hist,
                            ticket);
-    return launch_pool(G, census_kernel, grid, CENSUS_THREADS, census_smem_bytes(G.twok), st, G, bact0, partial, hist,
+    // byte pools: two blocks per SM while two histograms fit (2k + 1 <= 63), else one
+    const int grid = sms * (G.twok + 1u <= 63u ? 2 : 1);
+    if (G.frame0 || G.counter == 1u)
+        return launch_pool(G, census_kernel<1>, grid, CENSUS_THREADS, census_smem_bytes(G.twok), st, G, bact0, acc,
+                           hist, ticket);
+    return launch_pool(G, census_kernel<0>, grid, CENSUS_THREADS, census_smem_bytes(G.twok), st, G, bact0, acc, hist,
                        ticket);
 }
 

@@ -6,10 +6,11 @@
 // entirely by its own allocator (a framework's caching allocator or a fixed
 // arena) and which therefore has nothing left for a library to ask the
 // driver for.  vate_census_noalloc serves them: it takes the caller's pool
-// and output buffers and keeps its only scratch -- the per-block partial
-// histograms and the "blocks finished" ticket of the census kernel -- in a
-// file-scope device array of fixed size.  That array exists once on every
-// device that loads the library and stays allocated until the process exits.
+// and output buffers and keeps its only scratch -- the 2k + 1 counters the
+// census blocks add into and the "blocks finished" ticket of the census
+// kernel -- in a file-scope device array of fixed size.  That array exists
+// once on every device that loads the library and stays allocated until the
+// process exits.
 //
 // In host code the array's name is only a host-side stand-in, not a device
 // address.  The first call on each device (with that device current) looks
@@ -25,18 +26,21 @@ using vate::Geom;
 
 namespace {
 
-constexpr int NOALLOC_MAX_BLOCKS = 296;                 // census blocks per call
 constexpr int NOALLOC_MAX_BINS = 127;                   // 2k + 1 with k <= 63
 constexpr size_t NOALLOC_TICKET_BYTES = 256;            // ticket, padded to the alignment
 constexpr size_t NOALLOC_SCRATCH_BYTES =
-    NOALLOC_TICKET_BYTES + (size_t)NOALLOC_MAX_BLOCKS * NOALLOC_MAX_BINS * sizeof(uint64_t);   // 300,992 bytes
+    NOALLOC_TICKET_BYTES + (size_t)NOALLOC_MAX_BINS * sizeof(uint64_t);   // 1,272 bytes
 
 static __device__ __align__(256) unsigned char census_scratch[NOALLOC_SCRATCH_BYTES];
 
-// The ticket must be 0 when the census kernel starts.  A completed call
-// leaves it at 0; it is cleared before every call anyway so that nothing a
-// previous call left behind can leak into this one.
-__global__ void clear_ticket_kernel() { *reinterpret_cast<unsigned int *>(census_scratch) = 0u; }
+// The ticket and the counters must be 0 when the census kernel starts.  A
+// completed call leaves them at 0; they are cleared before every call anyway
+// so that nothing a previous call left behind can leak into this one.
+__global__ void clear_scratch_kernel() {
+    if (threadIdx.x == 0) *reinterpret_cast<unsigned int *>(census_scratch) = 0u;
+    if (threadIdx.x < NOALLOC_MAX_BINS)
+        reinterpret_cast<uint64_t *>(census_scratch + NOALLOC_TICKET_BYTES)[threadIdx.x] = 0u;
+}
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
@@ -86,22 +90,19 @@ extern "C" int vate_census_noalloc(const vate_params *params, const uint8_t *d_p
     void *scratch = nullptr;
     if (setup_device(&scratch, &sms) != VATE_OK)
         return vate::set_error(VATE_ECUDA, "no-alloc census: device set-up (cudaGetSymbolAddress) failed");
-    int grid = sms * 2 < NOALLOC_MAX_BLOCKS ? sms * 2 : NOALLOC_MAX_BLOCKS;
-    size_t need = NOALLOC_TICKET_BYTES + (size_t)grid * (G.twok + 1) * sizeof(uint64_t);
-    if (G.twok + 1 > (uint32_t)NOALLOC_MAX_BINS || need > NOALLOC_SCRATCH_BYTES) {
-        snprintf(g_msg, sizeof g_msg, "no-alloc census needs %zu bytes of scratch; the static scratch holds %zu",
-                 need, NOALLOC_SCRATCH_BYTES);
+    if (G.twok + 1 > (uint32_t)NOALLOC_MAX_BINS) {
+        snprintf(g_msg, sizeof g_msg, "no-alloc census keeps at most %d bins (k <= 63)", NOALLOC_MAX_BINS);
         return vate::set_error(VATE_EINVAL, g_msg);
     }
     G.pool = const_cast<uint8_t *>(d_pool);
     G.packed = 0;                                // the caller's pool: one byte per AT in the paper's form
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *base = static_cast<unsigned char *>(scratch);
-    clear_ticket_kernel<<<1, 1, 0, st>>>();
+    clear_scratch_kernel<<<1, 128, 0, st>>>();
     vate::count_launch();
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = vate::launch_census(G, bact0, reinterpret_cast<uint64_t *>(base + NOALLOC_TICKET_BYTES), grid, d_hist,
+        e = vate::launch_census(G, bact0, reinterpret_cast<uint64_t *>(base + NOALLOC_TICKET_BYTES), sms, d_hist,
                                 reinterpret_cast<unsigned int *>(base), st);
     if (e != cudaSuccess) return vate::set_error(VATE_ECUDA, cudaGetErrorString(e));
     return VATE_OK;

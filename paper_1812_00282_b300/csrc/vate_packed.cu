@@ -76,10 +76,10 @@ __global__ void __launch_bounds__(256) dr_age_packed_kernel(Geom G, uint64_t nwo
     }
 }
 
-// Census: one shared histogram per block (2k + 1 bins), the block rows and
-// last-block reduction of census16_kernel.
+// Census: one shared histogram per block (2k + 1 bins), added into acc and
+// published as in census16_kernel.
 __global__ void __launch_bounds__(CENSUS_THREADS) census_packed_kernel(Geom G, uint32_t bact0, uint32_t pat,
-                                                                       uint64_t *__restrict__ partial,
+                                                                       uint64_t *__restrict__ acc,
                                                                        uint64_t *__restrict__ hist,
                                                                        unsigned int *__restrict__ ticket) {
     extern __shared__ uint32_t hsh[];   // [nbins]
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_packed_kernel(Geom G, u
     }
     inactive = __reduce_add_sync(0xFFFFFFFFu, inactive);
     if (lane == 0) atomicAdd(&hsh[G.twok], inactive);
-    census_finish(hsh, 1, nbins, partial, hist, ticket);
+    census_finish(hsh, 1, nbins, acc, hist, ticket);
 }
 
 // Gather: warp per host.  In each round the lanes hash 32 consecutive
@@ -314,10 +314,10 @@ cudaError_t launch_packed_dr_age(const Geom &G, cudaStream_t st, int sms) {
     return launch_pool(G, dr_age_packed_kernel, grid_for_packed(nwords, sms), 256, 0, st, G, nwords);
 }
 
-cudaError_t launch_packed_census(const Geom &G, uint32_t bact0, uint64_t *partial, int grid, uint64_t *hist,
+cudaError_t launch_packed_census(const Geom &G, uint32_t bact0, uint64_t *acc, int grid, uint64_t *hist,
                                  unsigned int *ticket, cudaStream_t st) {
     return launch_pool(G, census_packed_kernel, grid, CENSUS_THREADS, (size_t)(G.twok + 1) * sizeof(uint32_t), st, G,
-                       bact0, packed_pattern(G), partial, hist, ticket);
+                       bact0, packed_pattern(G), acc, hist, ticket);
 }
 
 cudaError_t launch_packed_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kprime, const uint64_t *hist,
