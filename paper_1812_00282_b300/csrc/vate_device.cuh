@@ -222,13 +222,6 @@ VATE_HD uint32_t swar_dr_age(uint32_t w, uint32_t k) {
     return (t & ~bytes) | ((k * ONES) & bytes);
 }
 
-// Census bin of four recorders: the value itself when below k, else 2k.
-VATE_HD uint32_t swar_dr_bins(uint32_t w, uint32_t k, uint32_t twok) {
-    uint32_t ge = (w + (128u - k) * ONES) & HIGH;            // v >= k: inactive
-    uint32_t bytes = (ge >> 7) * 0xFFu;
-    return (w & ~bytes) | ((twok * ONES) & bytes);
-}
-
 // Range constants of CheckDR for window k': active iff 0 <= v <= k'-1.
 VATE_HD RangeConsts dr_range_consts(uint32_t kprime) {
     RangeConsts rc;

@@ -34,49 +34,33 @@ __device__ __forceinline__ void preserve_chunk(uint8_t *pool, uint64_t base, con
     if (r.x != w.x || r.y != w.y || r.z != w.z || r.w != w.w) *p = r;
 }
 
-// Census of one 16-byte chunk into this lane's column (col[bin * 32]): the
-// distance of Eq. 5 for active values, 2k for inactive ones.  A frame-0 pool
-// reads every AT with ACT = BACT^0; a pool in the paper's form reads each AT
-// with the ACT of its block.
+// Census of one 16-byte chunk of a timestamp pool in the paper's form (each
+// AT read with the ACT of its block) into this lane's column (col[bin * 32]):
+// the distance of Eq. 5 for active values, 2k for inactive ones.
 __device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint32_t pid0, uint4 w, uint32_t pat,
                                              uint32_t *col, uint32_t &inactive_runs) {
     if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
         inactive_runs++;
         return;
     }
-    uint32_t words[4];
-    if (G.counter == 1u) {                 // distance recorders: the value is the distance
-        words[0] = swar_dr_bins(w.x, G.k, G.twok);
-        words[1] = swar_dr_bins(w.y, G.k, G.twok);
-        words[2] = swar_dr_bins(w.z, G.k, G.twok);
-        words[3] = swar_dr_bins(w.w, G.k, G.twok);
-    } else if (G.frame0) {
-        words[0] = swar_bins(w.x, bact0, G.twok);
-        words[1] = swar_bins(w.y, bact0, G.twok);
-        words[2] = swar_bins(w.z, bact0, G.twok);
-        words[3] = swar_bins(w.w, bact0, G.twok);
-    } else {
-        uint32_t b0 = block_of(G, pid0);
-        if (b0 != block_of(G, pid0 + 15u)) {
-            uint32_t raw[4] = {w.x, w.y, w.z, w.w};
-            for (int b = 0; b < 16; b++) {
-                uint32_t v = (raw[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-                uint32_t bin = G.twok;
-                if (v < G.twok) {
-                    uint32_t act = act_of_block(bact0, block_of(G, pid0 + b), G.twok);
-                    uint32_t d = act + G.twok - v;
-                    bin = d >= G.twok ? d - G.twok : d;
-                }
-                col[bin * 32u] += 1u;
+    const uint32_t b0 = block_of(G, pid0);
+    if (b0 != block_of(G, pid0 + 15u)) {       // the chunk straddles two blocks
+        const uint32_t raw[4] = {w.x, w.y, w.z, w.w};
+        for (int b = 0; b < 16; b++) {
+            const uint32_t v = (raw[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+            uint32_t bin = G.twok;
+            if (v < G.twok) {
+                const uint32_t act = act_of_block(bact0, block_of(G, pid0 + b), G.twok);
+                const uint32_t d = act + G.twok - v;
+                bin = d >= G.twok ? d - G.twok : d;
             }
-            return;
+            col[bin * 32u] += 1u;
         }
-        uint32_t act = act_of_block(bact0, b0, G.twok);
-        words[0] = swar_bins(w.x, act, G.twok);
-        words[1] = swar_bins(w.y, act, G.twok);
-        words[2] = swar_bins(w.z, act, G.twok);
-        words[3] = swar_bins(w.w, act, G.twok);
+        return;
     }
+    const uint32_t act = act_of_block(bact0, b0, G.twok);
+    const uint32_t words[4] = {swar_bins(w.x, act, G.twok), swar_bins(w.y, act, G.twok), swar_bins(w.z, act, G.twok),
+                               swar_bins(w.w, act, G.twok)};
     // shared-memory atomics without a return value: consecutive bytes of one
     // bin do not wait for each other's read-modify-write
 #pragma unroll
@@ -84,6 +68,37 @@ __device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint
         uint32_t bin = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, G.twok);
         atomicAdd(&col[bin * 32u], 1u);
     }
+}
+
+// Census of one 16-byte chunk of a pool whose ATs are all read with the same
+// ACT (timestamps in the frame of block 0) or hold their own distance
+// (recorders): the stored values themselves go into this lane's column
+// (col[value * 32]), each clamped to the inactive value inact -- which is how
+// the distance bins count values above it, and keeps every index below
+// inact + 1 -- and a chunk of 16 inactive ATs is counted in inactive_runs.
+// census_raw_bin turns a value's row into its census bin.
+__device__ __forceinline__ void census_chunk_raw(uint4 w, uint32_t pat, uint32_t inact, uint32_t *col,
+                                                 uint32_t &inactive_runs) {
+    if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
+        inactive_runs++;
+        return;
+    }
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int b = 0; b < 16; b++) {
+        const uint32_t v = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, inact);
+        atomicAdd(&col[v * 32u], 1u);
+    }
+}
+
+// Census bin of stored value r (r <= inact): a frame-0 timestamp at distance
+// (BACT^0 - r) mod 2k, 2k inactive; a recorder's value is its distance, k
+// inactive (bin 2k).
+__device__ __forceinline__ uint32_t census_raw_bin(const Geom &G, uint32_t bact0, uint32_t r) {
+    if (G.counter == 1u) return r < G.k ? r : G.twok;
+    if (r >= G.twok) return G.twok;
+    const uint32_t d = bact0 + G.twok - r;
+    return d >= G.twok ? d - G.twok : d;
 }
 
 // The end of a census, once a block has added its counts into acc (2k + 1

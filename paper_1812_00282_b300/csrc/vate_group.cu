@@ -197,29 +197,33 @@ __global__ void __launch_bounds__(G_THREADS) group_census_kernel(const Geom *__r
         const uint32_t bact0 = bact0_of(step, G.twok);
         uint32_t inactive_runs = 0;
         const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
-        // four chunks in flight per thread: the pools of a group exceed L2, so the loads wait on memory
+        // eight chunks in flight per thread: the pools of a group exceed L2, so the loads wait on memory;
+        // frame-0 pools: the stored values are counted and relabelled as bins below
+        constexpr int U = 8;
         const uint64_t qend = tile.chunk0 + tile.nchunks;
-        for (uint64_t q = tile.chunk0 + threadIdx.x; q < qend; q += 4ull * blockDim.x) {
-            uint4 w[4];
+        for (uint64_t q = tile.chunk0 + threadIdx.x; q < qend; q += (uint64_t)U * blockDim.x) {
+            uint4 w[U];
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
+            for (int u = 0; u < U; u++) {
                 const uint64_t qu = q + (uint64_t)u * blockDim.x;
                 w[u] = qu < qend ? __ldcg(pool16 + qu) : make_uint4(pat, pat, pat, pat);
             }
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
+            for (int u = 0; u < U; u++) {
                 const uint64_t qu = q + (uint64_t)u * blockDim.x;
-                if (qu < qend) census_chunk(G, bact0, (uint32_t)(qu << 4), w[u], pat, col, inactive_runs);
+                if (qu < qend) census_chunk_raw(w[u], pat, G.twok, col, inactive_runs);
             }
         }
         col[G.twok * 32u] += 16u * inactive_runs;
         __syncthreads();
-        for (uint32_t bin = warp; bin < nbins; bin += nwarps) {
+        for (uint32_t r = warp; r < nbins; r += nwarps) {
             uint32_t s = 0;
-            for (uint32_t wv = 0; wv < nwarps; wv++) s += sh[((size_t)wv * maxbins + bin) * 32u + lane];
+            for (uint32_t wv = 0; wv < nwarps; wv++) s += sh[((size_t)wv * maxbins + r) * 32u + lane];
             s = __reduce_add_sync(0xFFFFFFFFu, s);
-            if (lane == 0 && s) atomicAdd(reinterpret_cast<unsigned long long *>(hist_all) + (size_t)tile.mon * maxbins + bin,
-                                          (unsigned long long)s);
+            if (lane == 0 && s)
+                atomicAdd(reinterpret_cast<unsigned long long *>(hist_all) + (size_t)tile.mon * maxbins +
+                              census_raw_bin(G, bact0, r),
+                          (unsigned long long)s);
         }
         __syncthreads();
     }

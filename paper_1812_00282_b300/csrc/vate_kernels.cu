@@ -268,12 +268,9 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32
 //
 // RAW (timestamps in the frame of block 0, or distance recorders): every AT
 // of the pool is read with the same ACT, so the census is the histogram of
-// the stored values with its bins relabelled once per block -- value u at
-// distance (BACT^0 - u) mod 2k, a recorder's value its own distance -- and an
-// AT costs one byte extract, one clamp and one atomic.  Values above the
-// inactive one are clamped to it, as the SWAR bins would count them, which
-// also keeps every column index inside the block's histogram.
-// Otherwise (the paper's per-block values of a caller's pool) the chunk's
+// the stored values with its bins relabelled once per block
+// (census_chunk_raw, census_raw_bin), and an AT costs one byte extract, one
+// clamp and one atomic.  Otherwise (the paper's per-block values of a caller's pool) the chunk's
 // bins are computed with SWAR, one ACT per chunk when it lies in one block.
 //
 // Eight 16-byte chunks are in flight per thread; the block's sums go into acc
@@ -309,20 +306,8 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
         for (int u = 0; u < U; u++) {
             const uint64_t qu = q + (uint64_t)u * stride;
             if (qu >= n16) continue;
-            if (!RAW) {
-                census_chunk(G, bact0, (uint32_t)(qu << 4), w[u], pat, col, runs);
-                continue;
-            }
-            if (w[u].x == pat && w[u].y == pat && w[u].z == pat && w[u].w == pat) {
-                runs++;
-                continue;
-            }
-            const uint32_t words[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
-#pragma unroll
-            for (int b = 0; b < 16; b++) {
-                const uint32_t v = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, inact);
-                atomicAdd(&col[v * 32u], 1u);
-            }
+            if (RAW) census_chunk_raw(w[u], pat, inact, col, runs);
+            else census_chunk(G, bact0, (uint32_t)(qu << 4), w[u], pat, col, runs);
         }
     }
     col[(RAW ? inact : G.twok) * 32u] += 16u * runs;
@@ -333,16 +318,7 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
         uint32_t s = 0;
         for (uint32_t wv = 0; wv < nwarps; wv++) s += sh[((size_t)wv * nbins + r) * 32u + lane];
         s = __reduce_add_sync(0xFFFFFFFFu, s);
-        uint32_t bin = r;
-        if (RAW) {
-            if (G.counter == 1u) {
-                bin = r < G.k ? r : G.twok;
-            } else if (r < G.twok) {
-                bin = bact0 + G.twok - r;
-                bin = bin >= G.twok ? bin - G.twok : bin;
-            }
-        }
-        if (lane == 0) census_add(acc, bin, s);
+        if (lane == 0) census_add(acc, RAW ? census_raw_bin(G, bact0, r) : r, s);
     }
     census_publish(acc, hist, ticket, nbins);
 }
