@@ -207,15 +207,19 @@ int vate_copy_pool(vate_handle *h, uint8_t *d_dst, void *stream);
 int vate_load_pool(vate_handle *h, const uint8_t *d_src, void *stream);
 
 /* End-to-end forms with host buffers: the pairs (or hosts) are copied to the
- * device in chunks through two device staging buffers on an internal copy
- * stream, overlapping the copy of chunk i+1 with the kernel of chunk i (the
- * double buffer of Sec. 4.2, with larger chunks): 2^20 pairs per chunk for
- * vate_ingest_host; 2^18 hosts per chunk for vate_estimate_host, which also
- * copies the estimates (and flags, if h_flags is not NULL) back on a second
- * internal stream, overlapping the gather of chunk i.  The staging buffers are
- * allocated on the first call.  Results are valid once `stream` has been
- * synchronised; host buffers in page-locked memory let the copies run
- * asynchronously. */
+ * device in chunks through device staging buffers on internal copy streams,
+ * overlapping the copy of chunk i+1 with the kernel of chunk i (the double
+ * buffer of Sec. 4.2, with larger chunks and more buffers).
+ * vate_ingest_host: 2^20 pairs per chunk, a ring of six 8 MiB buffers on a
+ * stream of their own, so that the pairs of the next slice (up to 6M) are
+ * copied while the current slice is still being estimated.
+ * vate_estimate_host: 2^18 hosts per chunk through two buffers; the estimates
+ * (and flags, if h_flags is not NULL) go back on a third internal stream,
+ * overlapping the gather of the next chunk.
+ * The staging buffers (52 MiB) are allocated on the first call.  Results are
+ * valid once `stream` has been synchronised; host buffers in page-locked
+ * memory let the copies run asynchronously.  The host buffer of a call must
+ * stay unchanged until `stream` reaches the call. */
 int vate_ingest_host(vate_handle *h, const vate_pair *h_pairs, uint64_t n, int64_t slice, void *stream);
 int vate_estimate_host(vate_handle *h, const uint32_t *h_aips, uint64_t n, uint32_t kprime,
                        float *h_out, uint8_t *h_flags, void *stream);

@@ -18,7 +18,8 @@ using vate::Geom;
 namespace {
 thread_local std::string g_err;
 std::atomic<uint64_t> g_launches{0};
-constexpr uint64_t STAGE_RECORDS = 1ull << 20;   // records per host-copy chunk (staging buffer size)
+constexpr uint64_t STAGE_RECORDS = 1ull << 20;   // pairs per chunk of vate_ingest_host (staging buffer size)
+constexpr int INGEST_RING = 6;                   // pair staging buffers: one 6M-pair slice copied ahead
 constexpr uint64_t EST_RECORDS = 1ull << 18;     // hosts per chunk of vate_estimate_host's pipeline
 
 int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -124,12 +125,20 @@ struct vate_handle {
     uint64_t *d_acc = nullptr;        // census scratch: 2k+1 counters the blocks add into, zero between calls
     unsigned int *d_ticket = nullptr; // census scratch: blocks finished
     // host-copy staging (allocated on first use)
-    cudaStream_t copy_stream = nullptr;      // host -> device
+    // pairs: a ring of staging buffers filled on their own stream, so that the
+    // pairs of the next slice are copied while this slice is estimated
+    cudaStream_t pairs_stream = nullptr;                 // host -> device (pairs)
+    cudaEvent_t ev_in_ready[INGEST_RING] = {};           // chunk copied
+    cudaEvent_t ev_in_free[INGEST_RING] = {};            // chunk ingested: the buffer may be refilled
+    vate_pair *d_in[INGEST_RING] = {};
+    uint32_t in_next = 0;                                // next ring slot
+    // estimates: two host-list buffers in, two result buffers out
+    cudaStream_t copy_stream = nullptr;      // host -> device (hosts)
     cudaStream_t d2h_stream = nullptr;       // device -> host (estimates)
     cudaEvent_t ev_ready[2] = {nullptr, nullptr};
     cudaEvent_t ev_free[2] = {nullptr, nullptr};
     cudaEvent_t ev_done[2] = {nullptr, nullptr};
-    void *d_stage[2] = {nullptr, nullptr};       // pairs or hosts in
+    uint32_t *d_stage[2] = {nullptr, nullptr};   // hosts in
     float *d_stage_out[2] = {nullptr, nullptr};  // estimates out
     uint8_t *d_stage_flags[2] = {nullptr, nullptr};
 };
@@ -238,19 +247,38 @@ cudaError_t prepare_device(int dev) {
     return e;
 }
 
+// The staging of the host-buffer entry points (and of checkpoints), created
+// on first use.  Each piece is created only if missing, so a call after a
+// failed one finishes the set-up; copy_stream, created last, marks it done.
 int ensure_staging(vate_handle *h) {
     if (h->copy_stream) return VATE_OK;
-    CU(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
-    CU(cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking), "copy stream");
-    for (int i = 0; i < 2; i++) {
-        CU(cudaEventCreateWithFlags(&h->ev_ready[i], cudaEventDisableTiming), "event");
-        CU(cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming), "event");
-        CU(cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming), "event");
-        if (cudaMalloc(&h->d_stage[i], STAGE_RECORDS * sizeof(vate_pair)) != cudaSuccess ||
-            cudaMalloc(&h->d_stage_out[i], STAGE_RECORDS * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&h->d_stage_flags[i], STAGE_RECORDS) != cudaSuccess)
+    auto stream = [](cudaStream_t *s) { return *s ? cudaSuccess : cudaStreamCreateWithFlags(s, cudaStreamNonBlocking); };
+    auto event = [](cudaEvent_t *e) { return *e ? cudaSuccess : cudaEventCreateWithFlags(e, cudaEventDisableTiming); };
+    auto alloc = [](auto **p, size_t bytes) {
+        return *p ? cudaSuccess : cudaMalloc(reinterpret_cast<void **>(p), bytes);
+    };
+    CU(stream(&h->pairs_stream), "copy stream");
+    CU(stream(&h->d2h_stream), "copy stream");
+    for (int i = 0; i < INGEST_RING; i++) {
+        CU(event(&h->ev_in_ready[i]), "event");
+        CU(event(&h->ev_in_free[i]), "event");
+        if (alloc(&h->d_in[i], STAGE_RECORDS * sizeof(vate_pair)) != cudaSuccess) {
+            cudaGetLastError();
             return fail(VATE_ENOMEM, "staging buffers: out of device memory");
+        }
     }
+    for (int i = 0; i < 2; i++) {
+        CU(event(&h->ev_ready[i]), "event");
+        CU(event(&h->ev_free[i]), "event");
+        CU(event(&h->ev_done[i]), "event");
+        if (alloc(&h->d_stage[i], EST_RECORDS * sizeof(uint32_t)) != cudaSuccess ||
+            alloc(&h->d_stage_out[i], EST_RECORDS * sizeof(float)) != cudaSuccess ||
+            alloc(&h->d_stage_flags[i], EST_RECORDS) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(VATE_ENOMEM, "staging buffers: out of device memory");
+        }
+    }
+    CU(stream(&h->copy_stream), "copy stream");
     return VATE_OK;
 }
 
@@ -372,6 +400,7 @@ int vate_create_shard(const vate_params *params, uint64_t pid_lo, uint64_t pid_h
 
 int vate_destroy(vate_handle *h) {
     if (!h) return VATE_OK;
+    if (h->pairs_stream) cudaStreamSynchronize(h->pairs_stream);
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
     if (h->d2h_stream) cudaStreamSynchronize(h->d2h_stream);
     if (h->G.l2_window_bytes) {
@@ -392,6 +421,12 @@ int vate_destroy(vate_handle *h) {
         if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
         if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
     }
+    for (int i = 0; i < INGEST_RING; i++) {
+        cudaFree(h->d_in[i]);
+        if (h->ev_in_ready[i]) cudaEventDestroy(h->ev_in_ready[i]);
+        if (h->ev_in_free[i]) cudaEventDestroy(h->ev_in_free[i]);
+    }
+    if (h->pairs_stream) cudaStreamDestroy(h->pairs_stream);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
     delete h;
@@ -541,18 +576,22 @@ int vate_ingest_host(vate_handle *h, const vate_pair *h_pairs, uint64_t n, int64
     if (int rc = ensure_staging(h)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     if (int rc = advance_to(h, slice, st)) return rc;
-    for (uint64_t off = 0, i = 0; off < n; off += STAGE_RECORDS, i++) {
-        int b = (int)(i & 1);
+    // chunk copies on the pairs stream into the next free ring buffer; each
+    // chunk's SetAT on `stream` waits for its copy, and a buffer is refilled
+    // only after the kernel that read it
+    for (uint64_t off = 0; off < n; off += STAGE_RECORDS) {
+        const uint32_t b = h->in_next;
+        h->in_next = (b + 1u) % INGEST_RING;
         uint64_t m = (n - off) < STAGE_RECORDS ? (n - off) : STAGE_RECORDS;
-        CU(cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0), "wait");
-        CU(cudaMemcpyAsync(h->d_stage[b], h_pairs + off, m * sizeof(vate_pair), cudaMemcpyHostToDevice, h->copy_stream),
+        CU(cudaStreamWaitEvent(h->pairs_stream, h->ev_in_free[b], 0), "wait");
+        CU(cudaMemcpyAsync(h->d_in[b], h_pairs + off, m * sizeof(vate_pair), cudaMemcpyHostToDevice, h->pairs_stream),
            "pairs H2D");
-        CU(cudaEventRecord(h->ev_ready[b], h->copy_stream), "record");
-        CU(cudaStreamWaitEvent(st, h->ev_ready[b], 0), "wait");
-        cudaError_t e = vate::launch_ingest(h->G, h->bact0, reinterpret_cast<const uint32_t *>(h->d_stage[b]), m, st,
+        CU(cudaEventRecord(h->ev_in_ready[b], h->pairs_stream), "record");
+        CU(cudaStreamWaitEvent(st, h->ev_in_ready[b], 0), "wait");
+        cudaError_t e = vate::launch_ingest(h->G, h->bact0, reinterpret_cast<const uint32_t *>(h->d_in[b]), m, st,
                                             h->sms);
         if (e != cudaSuccess) return cuda_fail(e, "ingest launch");
-        CU(cudaEventRecord(h->ev_free[b], st), "record");
+        CU(cudaEventRecord(h->ev_in_free[b], st), "record");
     }
     return VATE_OK;
 }
@@ -572,7 +611,7 @@ int vate_estimate_host(vate_handle *h, const uint32_t *h_aips, uint64_t n, uint3
     for (uint64_t off = 0, i = 0; off < n; off += EST_RECORDS, i++) {
         int b = (int)(i & 1);
         uint64_t m = (n - off) < EST_RECORDS ? (n - off) : EST_RECORDS;
-        uint32_t *din = reinterpret_cast<uint32_t *>(h->d_stage[b]);
+        uint32_t *din = h->d_stage[b];
         CU(cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0), "wait");
         CU(cudaMemcpyAsync(din, h_aips + off, m * sizeof(uint32_t), cudaMemcpyHostToDevice, h->copy_stream), "hosts H2D");
         CU(cudaEventRecord(h->ev_ready[b], h->copy_stream), "record");
@@ -664,8 +703,8 @@ int vate_checkpoint(vate_handle *h, void *h_buf, uint64_t bytes, void *stream) {
         if (int rc = ensure_staging(h)) return rc;
         const uint32_t w = h->G.atw;
         const uint64_t piece = STAGE_RECORDS * sizeof(vate_pair) / w;    // positions per piece
-        uint8_t *stage = static_cast<uint8_t *>(h->d_stage[0]);
-        CU(cudaStreamWaitEvent(st, h->ev_free[0], 0), "wait");
+        uint8_t *stage = reinterpret_cast<uint8_t *>(h->d_in[0]);          // a pair buffer, once its last reader is done
+        CU(cudaStreamWaitEvent(st, h->ev_in_free[0], 0), "wait");
         for (uint64_t pos = 0; pos < h->G.P; pos += piece) {
             const uint64_t n = h->G.P - pos < piece ? h->G.P - pos : piece;
             if (h->G.packed)
@@ -739,7 +778,7 @@ int vate_restore(const void *h_buf, uint64_t bytes, void *stream, vate_handle **
             return rc;
         }
         const uint64_t piece = STAGE_RECORDS * sizeof(vate_pair) / G.atw / G.pn * G.pn;   // whole words
-        uint8_t *stage = static_cast<uint8_t *>(h->d_stage[0]);
+        uint8_t *stage = reinterpret_cast<uint8_t *>(h->d_in[0]);
         for (uint64_t pos = 0; e == cudaSuccess && pos < G.P; pos += piece) {
             const uint64_t n = G.P - pos < piece ? G.P - pos : piece;
             e = cudaMemcpyAsync(stage, pool + pos * G.atw, n * G.atw, cudaMemcpyHostToDevice, st);
