@@ -242,7 +242,9 @@ int vate_host_block(const vate_params *params, uint64_t pid, uint32_t *block);
  * left for a library to request.  It needs no handle either.
  *   params   geometry of the pool (log2_pool, k and partition are used; the
  *            whole struct is validated as for vate_create).
- *   d_pool   device uint8[P], 16-byte aligned, AT values in [0, 2k].
+ *   d_pool   device uint8[P], 16-byte aligned, in the paper's form: AT values
+ *            in [0, 2k] (a distance recorder's in [0, k]); larger bytes are
+ *            counted as inactive.
  *   bact0    BACT^0 of the slice the pool belongs to, 0 <= bact0 < 2k.
  *   d_hist   device uint64[2k+1]: receives the same census as vate_census
  *            (d_hist[d] for distances 0 <= d < 2k, d_hist[2k] inactive).

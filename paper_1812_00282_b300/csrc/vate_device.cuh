@@ -201,9 +201,20 @@ __device__ __forceinline__ uint32_t swar_active_fma(uint32_t w, const RangeConst
     return r & ~(w * u3 + c2k) & HIGH;
 }
 
+// Four byte values with every byte above top (top <= 126) replaced by top.
+// The high bit of each byte is tested apart from its low seven bits, so no
+// sum crosses into the next byte whatever the bytes hold.
+VATE_HD uint32_t swar_clamp(uint32_t w, uint32_t top) {
+    const uint32_t lo7 = w & ~HIGH;
+    const uint32_t over = ((lo7 + (127u - top) * ONES) | w) & HIGH;   // byte > top
+    const uint32_t mask = (over >> 7) * 0xFFu;
+    return (w & ~mask) | ((top * ONES) & mask);
+}
+
 // Census bin of four ATs whose ACT is act: byte = (act + 2k - v) mod 2k, the
 // distance of Eq. 5, or 2k for an inactive AT.  Valid values (v <= 2k) never
-// borrow across bytes; callers clamp each byte to 2k anyway.
+// borrow across bytes; a pool that may hold others goes through swar_clamp
+// first.
 VATE_HD uint32_t swar_bins(uint32_t w, uint32_t act, uint32_t twok) {
     uint32_t t = (act + twok) * ONES - w;
     uint32_t ge = (t + (128u - twok) * ONES) & HIGH;          // t >= 2k

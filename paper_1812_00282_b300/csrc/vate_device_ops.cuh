@@ -36,7 +36,8 @@ __device__ __forceinline__ void preserve_chunk(uint8_t *pool, uint64_t base, con
 
 // Census of one 16-byte chunk of a timestamp pool in the paper's form (each
 // AT read with the ACT of its block) into this lane's column (col[bin * 32]):
-// the distance of Eq. 5 for active values, 2k for inactive ones.
+// the distance of Eq. 5 for active values, 2k for inactive ones and for any
+// byte above 2k (a caller's pool is not checked).
 __device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint32_t pid0, uint4 w, uint32_t pat,
                                              uint32_t *col, uint32_t &inactive_runs) {
     if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
@@ -59,15 +60,13 @@ __device__ __forceinline__ void census_chunk(const Geom &G, uint32_t bact0, uint
         return;
     }
     const uint32_t act = act_of_block(bact0, b0, G.twok);
-    const uint32_t words[4] = {swar_bins(w.x, act, G.twok), swar_bins(w.y, act, G.twok), swar_bins(w.z, act, G.twok),
-                               swar_bins(w.w, act, G.twok)};
+    const uint32_t words[4] = {
+        swar_bins(swar_clamp(w.x, G.twok), act, G.twok), swar_bins(swar_clamp(w.y, G.twok), act, G.twok),
+        swar_bins(swar_clamp(w.z, G.twok), act, G.twok), swar_bins(swar_clamp(w.w, G.twok), act, G.twok)};
     // shared-memory atomics without a return value: consecutive bytes of one
     // bin do not wait for each other's read-modify-write
 #pragma unroll
-    for (int b = 0; b < 16; b++) {
-        uint32_t bin = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, G.twok);
-        atomicAdd(&col[bin * 32u], 1u);
-    }
+    for (int b = 0; b < 16; b++) atomicAdd(&col[((words[b >> 2] >> (8 * (b & 3))) & 0xFFu) * 32u], 1u);
 }
 
 // Census of one 16-byte chunk of a pool whose ATs are all read with the same

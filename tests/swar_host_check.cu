@@ -1,7 +1,8 @@
 // Host-only check of the SWAR AT arithmetic in vate_device.cuh against the
 // scalar forms of Algorithm 1 (CheckAT), Eq. 5 (distance) and Algorithm 3
 // (fast PreserveAT): every k <= 63, every ACT, every k' <= k, every AT value
-// 0..2k in every byte position, plus random mixed words.  The frame-0 forms
+// 0..2k in every byte position, plus random mixed words; and the byte clamp
+// for every byte value.  The frame-0 forms
 // (values kept as value minus block index, mod 2k) are tied to the paper's
 // through the per-block map.  Prints "OK".
 #include <cstdio>
@@ -15,6 +16,23 @@ static uint32_t rnd() { rng_state = rng_state * 1664525u + 1013904223u; return r
 
 int main() {
     long checked = 0;
+    // swar_clamp: every byte value in every position, every top <= 126, the
+    // other bytes random (so that a carry across bytes would show)
+    for (uint32_t top = 0; top <= 126; top++)
+        for (uint32_t x = 0; x < 256; x++)
+            for (int pos = 0; pos < 4; pos++) {
+                uint32_t v[4];
+                for (int b = 0; b < 4; b++) v[b] = rnd() & 0xFFu;
+                v[pos] = x;
+                const uint32_t w = v[0] | v[1] << 8 | v[2] << 16 | v[3] << 24;
+                const uint32_t r = swar_clamp(w, top);
+                for (int b = 0; b < 4; b++)
+                    if (((r >> (8 * b)) & 0xFFu) != (v[b] > top ? top : v[b])) {
+                        printf("FAIL clamp top=%u v=%u\n", top, v[b]);
+                        return 1;
+                    }
+                checked++;
+            }
     for (uint32_t k = 1; k <= 63; k++) {
         uint32_t twok = 2 * k;
         uint32_t c2k = (128u - twok) * ONES;

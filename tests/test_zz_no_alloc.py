@@ -23,11 +23,12 @@ def V():
     return V
 
 
-@pytest.mark.parametrize("c,k,L,partition", [(20, 5, 32, 0), (26, 10, 32, 0), (16, 63, 1, 1), (14, 1, 8, 1)])
-def test_census_noalloc_matches_regular_census(V, c, k, L, partition):
+@pytest.mark.parametrize("c,k,L,partition,counter", [(20, 5, 32, 0, 0), (26, 10, 32, 0, 0), (16, 63, 1, 1, 0),
+                                                      (14, 1, 8, 1, 0), (20, 10, 32, 0, 1), (16, 63, 1, 1, 1)])
+def test_census_noalloc_matches_regular_census(V, c, k, L, partition, counter):
     from traffic import SMALL, Traffic
     tr = Traffic(SMALL, pkts_per_slice=30_000)
-    d = V.Vate(c, k, 64, L, partition, seed=c * 100 + k)
+    d = V.Vate(c, k, 64, L, partition, seed=c * 100 + k, counter=counter)
     pool = torch.empty(1 << c, dtype=torch.uint8, device="cuda")
     ref = torch.empty(2 * k + 1, dtype=torch.int64, device="cuda")
     for s in range(3):
@@ -63,3 +64,36 @@ def test_census_noalloc_rejects_bad_arguments(V):
     expect = np.zeros(2 * k + 1, np.int64)
     expect[2 * k] = 1 << 16
     np.testing.assert_array_equal(hist.cpu().numpy(), expect)
+
+
+@pytest.mark.parametrize("counter", [0, 1])
+def test_census_noalloc_counts_out_of_range_values_as_inactive(V, counter):
+    """Bytes above the counter's range (a caller's pool is not checked) are
+    counted as inactive by both forms of the census -- the timestamp bins of
+    the paper's per-block values and the stored-value count of recorders,
+    which clamps every byte to the inactive value before it indexes the
+    block's histogram."""
+    c, k = 16, 5
+    params = V.make_params(c, k, 64, 1, 0, 1, counter)
+    g = torch.Generator().manual_seed(5)
+    top = k if counter else 2 * k                  # the inactive value
+    pool = torch.randint(0, top + 1, (1 << c,), generator=g, dtype=torch.int32)
+    wild = torch.randint(0, 1 << c, (4096,), generator=g)
+    pool[wild] = torch.randint(top + 1, 256, (4096,), generator=g, dtype=torch.int32)
+    pool_u8 = pool.to(torch.uint8)
+    hist = torch.empty(2 * k + 1, dtype=torch.int64, device="cuda")
+    V.vate_census_noalloc(params, pool_u8.cuda(), 3, hist)
+    torch.cuda.synchronize()
+    v = pool.numpy()
+    want = np.zeros(2 * k + 1, np.int64)
+    want[2 * k] = int((v >= top).sum())
+    active = v[v < top]
+    if counter:                                    # a recorder's value is its distance
+        np.add.at(want, active, 1)
+    else:                                          # Eq. 5 with the ACT of each AT's block
+        from oracle import Oracle
+        o = Oracle(c=c, k=k, g=64, seg_len=1, partition=0, seed=1)
+        pid = np.nonzero(v < top)[0]
+        act = np.array([(3 + o.block(int(p))) % (2 * k) for p in pid])
+        np.add.at(want, (act - active) % (2 * k), 1)
+    np.testing.assert_array_equal(hist.cpu().numpy(), want)
