@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(WARPS * 32) features_kernel(Geom G, uint32_t b
 // 32 hosts per warp: the warp extracts each host's features into its row of
 // xs (host_features), then lane j evaluates host j's model (mlp_eval_lane)
 // and the fallback.
-__global__ void __launch_bounds__(WARPS * 32) learned_estimate_kernel(Geom G, uint32_t bact0,
+__global__ void __launch_bounds__(WARPS * 32, 3) learned_estimate_kernel(Geom G, uint32_t bact0,
                                                                       const uint64_t *__restrict__ hist,
                                                                       const uint32_t *__restrict__ aips, uint64_t n,
                                                                       const float *__restrict__ params,
