@@ -24,6 +24,7 @@
 #include "vate_device_ops.cuh"
 #include "vate_launch.cuh"
 
+#include <algorithm>
 #include <utility>
 
 namespace vate {
@@ -559,13 +560,14 @@ cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *acc, int sms,
         return launch_pool(G, census16_kernel, sms * 4, CENSUS_THREADS,
                            (size_t)(CENSUS_THREADS / 32) * (G.twok + 1) * sizeof(uint32_t), st, G, bact0, acc, hist,
                            ticket);
-    // byte pools: two blocks per SM while two histograms fit (2k + 1 <= 63), else one
-    const int grid = sms * (G.twok + 1u <= 63u ? 2 : 1);
+    // byte pools: up to four blocks per SM, as many as their lane-column
+    // histograms fit in about 200 KiB of shared memory (one for k = 63)
+    const size_t smem = census_smem_bytes(G.twok);
+    const int per_sm = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)(200u << 10) / smem));
+    const int grid = sms * per_sm;
     if (G.frame0 || G.counter == 1u)
-        return launch_pool(G, census_kernel<1>, grid, CENSUS_THREADS, census_smem_bytes(G.twok), st, G, bact0, acc,
-                           hist, ticket);
-    return launch_pool(G, census_kernel<0>, grid, CENSUS_THREADS, census_smem_bytes(G.twok), st, G, bact0, acc, hist,
-                       ticket);
+        return launch_pool(G, census_kernel<1>, grid, CENSUS_THREADS, smem, st, G, bact0, acc, hist, ticket);
+    return launch_pool(G, census_kernel<0>, grid, CENSUS_THREADS, smem, st, G, bact0, acc, hist, ticket);
 }
 
 cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kprime, const uint64_t *hist,
