@@ -63,16 +63,37 @@ __device__ __forceinline__ void set_at(const Geom &G, uint32_t bact0, uint32_t a
     }
 }
 
+// U 16-byte loads (2U pairs) in flight per thread before their SetATs, and
+// up to VATE_INGEST_BPS blocks per SM.  Measured at the 40 Gb/s shape on B300
+// (5M pairs, ingest + slide): U = 1 with 32 blocks/SM 62.5 us, U = 2 with 16
+// 62.7 us, U = 1 with 16 65.1 us, U = 4 with 16 65.4 us; the random byte
+// stores, not the pair loads, bound it.
+#ifndef VATE_INGEST_U
+#define VATE_INGEST_U 1
+#endif
+#ifndef VATE_INGEST_BPS
+#define VATE_INGEST_BPS 32
+#endif
+template <int U>
 __global__ void __launch_bounds__(256) ingest_kernel(Geom G, uint32_t bact0, const uint32_t *__restrict__ pairs,
                                                      uint64_t n) {
     // pairs is 16-byte aligned here; n pairs = n/2 uint4 plus an odd tail
     const uint4 *p4 = reinterpret_cast<const uint4 *>(pairs);
     uint64_t n2 = n >> 1;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n2; i += stride) {
-        uint4 q = __ldcs(p4 + i);
-        set_at(G, bact0, q.x, q.y);
-        set_at(G, bact0, q.z, q.w);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n2; i += U * stride) {
+        uint4 q[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint64_t j = i + (uint64_t)u * stride;
+            q[u] = j < n2 ? __ldcs(p4 + j) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (i + (uint64_t)u * stride >= n2) break;
+            set_at(G, bact0, q[u].x, q[u].y);
+            set_at(G, bact0, q[u].z, q[u].w);
+        }
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         set_at(G, bact0, pairs[2 * (n - 1)], pairs[2 * (n - 1) + 1]);
@@ -500,13 +521,14 @@ cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, 
     if (n == 0) return cudaSuccess;
     if ((reinterpret_cast<uintptr_t>(pairs) & 15u) != 0) {
         // 8-byte aligned only: the first pair alone, then the 16-byte aligned rest
-        cudaError_t e = launch_pool(G, ingest_kernel, 1, 32, 0, st, G, bact0, pairs, (uint64_t)1);
+        cudaError_t e = launch_pool(G, ingest_kernel<1>, 1, 32, 0, st, G, bact0, pairs, (uint64_t)1);
         if (e != cudaSuccess) return e;
         pairs += 2;
         n -= 1;
         if (n == 0) return cudaSuccess;
     }
-    return launch_pool(G, ingest_kernel, grid_for((n + 1) / 2, 256, sms * 16), 256, 0, st, G, bact0, pairs, n);
+    return launch_pool(G, ingest_kernel<VATE_INGEST_U>, grid_for((n + 1) / 2, 256, sms * VATE_INGEST_BPS), 256, 0, st, G,
+                       bact0, pairs, n);
 }
 
 cudaError_t launch_dr_age(const Geom &G, cudaStream_t st, int sms) {
