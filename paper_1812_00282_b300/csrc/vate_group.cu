@@ -162,13 +162,40 @@ __global__ void __launch_bounds__(G_THREADS) group_ingest_kernel(const Geom *__r
     __syncthreads();
     const unsigned long long step = st->step;
     const uint64_t lo = so[0], hi = so[M];
-    for (uint64_t i = lo + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < hi;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t m = find_monitor(so, M, i);
-        const Geom &G = sd[m];
-        uint32_t aip = __ldcs(pairs + 2 * i), bip = __ldcs(pairs + 2 * i + 1);
-        uint32_t pid = vat_pid(G, aip, bh(G, bip));
-        G.pool[pid] = (uint8_t)bact0_of(step, G.twok);        // SetAT in frame 0
+    const uint2 *p2 = reinterpret_cast<const uint2 *>(pairs);          // 8-byte aligned (checked on the host)
+    __shared__ uint32_t tile_mon[2];
+    // Tiles of INGEST_TILE consecutive pairs, in order across the grid, so the
+    // pools being written at any time are those of the few monitors whose
+    // pairs are in flight.  A tile inside one monitor runs with that monitor's
+    // descriptor in registers; only a tile that straddles monitors looks up
+    // the monitor of each pair.
+    constexpr uint32_t INGEST_TILE = G_THREADS * 8;
+    const uint64_t ntiles = (hi - lo + INGEST_TILE - 1) / INGEST_TILE;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t t0 = lo + tile * INGEST_TILE, t1 = min(t0 + INGEST_TILE, hi);
+        __syncthreads();                        // the previous tile's tile_mon has been read
+        if (threadIdx.x == 0) {
+            tile_mon[0] = find_monitor(so, M, t0);
+            tile_mon[1] = find_monitor(so, M, t1 - 1);
+        }
+        __syncthreads();
+        const uint32_t m0 = tile_mon[0];
+        if (m0 == tile_mon[1]) {
+            const Geom G = sd[m0];
+            const uint8_t v = (uint8_t)bact0_of(step, G.twok);        // SetAT in frame 0
+#pragma unroll 4
+            for (uint64_t i = t0 + threadIdx.x; i < t1; i += G_THREADS) {
+                const uint2 q = __ldcs(p2 + i);
+                G.pool[vat_pid(G, q.x, bh(G, q.y))] = v;
+            }
+        } else {
+            for (uint64_t i = t0 + threadIdx.x; i < t1; i += G_THREADS) {
+                const uint32_t m = find_monitor(so, M, i);
+                const Geom &G = sd[m];
+                const uint2 q = __ldcs(p2 + i);
+                G.pool[vat_pid(G, q.x, bh(G, q.y))] = (uint8_t)bact0_of(step, G.twok);
+            }
+        }
     }
 }
 
