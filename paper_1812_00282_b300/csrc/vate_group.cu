@@ -285,7 +285,10 @@ __global__ void __launch_bounds__(G_THREADS) group_gather_kernel(const Geom *__r
     const unsigned long long step = st->step;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t lo = so[0], hi = so[M];
-    uint32_t cur = 0xFFFFFFFFu;
+    // the monitor of the last host and its host range [cur_lo, cur_hi): hosts
+    // come in runs of one monitor, so the binary search runs once per run
+    uint32_t cur = 0;
+    uint64_t cur_lo = 1, cur_hi = 0;
     RangeConsts rc = {};
     for (;;) {
         uint64_t base = 0;
@@ -293,31 +296,42 @@ __global__ void __launch_bounds__(G_THREADS) group_gather_kernel(const Geom *__r
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (base >= hi) break;
         const uint64_t end = min(base + grab, hi);
-        for (uint64_t h = base; h < end; h++) {
-            const uint32_t m = find_monitor(so, M, h);
-            const Geom &G = sd[m];
-            const uint32_t bact0 = bact0_of(step, G.twok);
-            if (m != cur) {                      // CheckAT of monitor m: ACT = BACT^0 for every AT in frame 0
-                rc = range_consts(bact0, kp[m], G.twok);
-                cur = m;
+        // up to 32 hosts at a time: lane j keeps host b0 + j's count and
+        // monitor, and the warp's lanes evaluate their Eq. 11 side by side
+        for (uint64_t b0 = base; b0 < end; b0 += 32) {
+            const uint64_t b1 = min(b0 + 32, end);
+            uint32_t myA = 0, mym = 0;
+            for (uint64_t h = b0; h < b1; h++) {
+                if (h < cur_lo || h >= cur_hi) {   // CheckAT of monitor m: ACT = BACT^0 for every AT in frame 0
+                    cur = find_monitor(so, M, h);
+                    cur_lo = so[cur];
+                    cur_hi = so[cur + 1];
+                    rc = range_consts(bact0_of(step, sd[cur].twok), kp[cur], sd[cur].twok);
+                }
+                const Geom &G = sd[cur];
+                const uint32_t aip = hosts[h];
+                uint32_t cnt;
+                if (CPSL >= 0) {
+                    const uint32_t nseg = G.g >> G.log2L;
+                    const uint32_t c2k = (128u - G.twok) * ONES;
+                    if (nseg % (32u * RB) == 0)
+                        cnt = gather_host_vec<(CPSL < 0 ? 0 : CPSL), RB, true>(G, rc, c2k, aip, u1, u2, u3, lane);
+                    else
+                        cnt = gather_host_vec<(CPSL < 0 ? 0 : CPSL), RB, false>(G, rc, c2k, aip, u1, u2, u3, lane);
+                } else {
+                    cnt = gather_host_scalar(G, bact0_of(step, G.twok), kp[cur], aip, lane);
+                }
+                const uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
+                if (lane == (uint32_t)(h - b0)) {
+                    myA = A;
+                    mym = cur;
+                }
             }
-            const uint32_t aip = hosts[h];
-            uint32_t cnt;
-            if (CPSL >= 0) {
-                const uint32_t nseg = G.g >> G.log2L;
-                const uint32_t c2k = (128u - G.twok) * ONES;
-                if (nseg % (32u * RB) == 0)
-                    cnt = gather_host_vec<(CPSL < 0 ? 0 : CPSL), RB, true>(G, rc, c2k, aip, u1, u2, u3, lane);
-                else
-                    cnt = gather_host_vec<(CPSL < 0 ? 0 : CPSL), RB, false>(G, rc, c2k, aip, u1, u2, u3, lane);
-            } else {
-                cnt = gather_host_scalar(G, bact0, kp[m], aip, lane);
-            }
-            const uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
-            if (lane == 0) {
+            if (b0 + lane < b1) {
+                const Geom &G = sd[mym];
                 uint8_t f;
-                out[h] = estimate_eq11(G.g, G.P, n0[m], A, f);
-                if (flags) flags[h] = f;
+                out[b0 + lane] = estimate_eq11(G.g, G.P, n0[mym], myA, f);
+                if (flags) flags[b0 + lane] = f;
             }
         }
     }
