@@ -4,10 +4,16 @@
 //   ingest_kernel         SetAT for every <aip, bip> pair              (Algorithm 4, scan loop)
 //   preserve_kernel       fast PreserveAT on the two blocks whose ACT
 //                         became 0 or k                                 (Algorithm 3, Corollary 1)
+//   preserve16_kernel     the same for 16-bit ATs (k >= 64)
+//   dr_age_kernel         one slide of distance recorders (VDRE),
+//   dr_age16_kernel       every recorder below k aged by one            (Sec. 1; the baseline of Sec. 5)
 //   census_kernel         histogram of pool distances -> Z_p            (Eq. 11)
+//   census16_kernel       the same for 16-bit ATs
 //   gather_vec_kernel     per-host CheckAT over g VATs + Eq. 11, for
 //                         segment lengths L >= 16 (16-byte loads)       (Algorithm 1, Algorithm 4)
 //   gather_scalar_kernel  the same for L < 16 (one byte per VAT)
+//   estimate_from_counts_kernel  Eq. 11 from active counts and a census
+//                         summed over the shards of one pool            (Eq. 11)
 //   age_counts_kernel     per-host counts of VATs by distance d < k
 //   frame_convert_kernel  a pool to / from the paper's per-block values
 //
