@@ -27,6 +27,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -179,12 +180,23 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def code_of(text: str) -> str:
+    """C/CUDA source without its comments and with whitespace collapsed: what
+    the compiler sees, so that a comment edit leaves a kernel's checksum alone.
+    (Enough for these sources: no string literal in them holds a comment
+    marker.)"""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def traffic_sha() -> str:
-    """Checksum of the sources a committed ncu traffic figure depends on."""
+    """Checksum of the code (comments aside) of the sources a committed ncu
+    traffic figure depends on."""
     h = hashlib.sha256()
     for f in ("vate_kernels.cu", "vate_device.cuh", "vate_device_ops.cuh"):
-        with open(os.path.join(ROOT, "paper_1812_00282_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1812_00282_b300", "csrc", f), encoding="utf-8") as fh:
+            h.update(code_of(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
