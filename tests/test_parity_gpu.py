@@ -266,6 +266,44 @@ def test_host_buffer_entry_points_match_device_ones(V):
     d2.close()
 
 
+def test_host_staging_ring_wraps_and_back_to_back_steps(V):
+    """vate_ingest_host with more chunks in one call than the ring has buffers
+    (a chunk refills the buffer of an earlier chunk of the same call), then
+    slices issued back to back with no synchronisation between them (the
+    pairs of slice s+1 are copied while slice s is estimated): pools, estimates
+    and flags equal those of the device entry points."""
+    k, params = 5, (20, 5, 1024, 32, 0, 7)
+    big = Traffic(SMALL, pkts_per_slice=7 * (1 << 20) + 1001).slice_pairs(0)   # 8 chunks, ring of 6
+    tr = Traffic(SMALL, pkts_per_slice=(1 << 20) + 4321)
+    hosts = np.resize(tr.aips, (1 << 18) + 99)
+    d1, d2 = V.Vate(*params), V.Vate(*params)
+    slices = [(0, big)] + [(s, tr.slice_pairs(s)) for s in (1, 2, 3)]
+    pinned = [torch.from_numpy(arr.view(np.int32)).pin_memory() for _, arr in slices]
+    outs = [(torch.empty(len(hosts), dtype=torch.float32).pin_memory(),
+             torch.empty(len(hosts), dtype=torch.uint8).pin_memory()) for _ in slices]
+    for (s, _), p, (e, f) in zip(slices, pinned, outs):       # issued back to back
+        V.vate_ingest_host(d2.h, p, s)
+        d2.close_slice(s)
+        V.vate_estimate_host(d2.h, hosts, k, e.numpy(), f.numpy())
+    torch.cuda.synchronize()
+    dh = dev_u32(hosts)
+    for (s, arr), (e, f) in zip(slices, outs):
+        d1.ingest(dev_pairs(arr), s)
+        d1.close_slice(s)
+        e1 = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+        f1 = torch.empty(len(hosts), dtype=torch.uint8, device="cuda")
+        d1.estimate(dh, k, e1, f1)
+        np.testing.assert_array_equal(e1.cpu().numpy(), e.numpy())
+        np.testing.assert_array_equal(f1.cpu().numpy(), f.numpy())
+    p1 = torch.empty(d1.P, dtype=torch.uint8, device="cuda")
+    p2 = torch.empty(d2.P, dtype=torch.uint8, device="cuda")
+    d1.copy_pool(p1)
+    d2.copy_pool(p2)
+    assert torch.equal(p1, p2)
+    d1.close()
+    d2.close()
+
+
 @pytest.mark.slow
 def test_full_size_40g_shape_sampled(V):
     # The 40 Gb/s workload at full size -- 2^26-AT pool, g = 4096, L = 32,
