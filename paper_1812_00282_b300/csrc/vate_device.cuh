@@ -354,4 +354,72 @@ VATE_HD uint32_t from_canonical(uint32_t v, uint32_t blk, uint32_t twok) {
     return u >= twok ? u - twok : u;
 }
 
+// ---------------------------------------------------------------------------
+// SWAR tests on bit-packed ATs: B-bit fields, PN = floor(32 / B) per 32-bit
+// word, field f at bits [fB, fB + B).  A word is split into its even fields
+// (left in place) and its odd fields (shifted down by B); either half has its
+// fields at bits 2iB with B free bits above each, so adding a constant c' <=
+// 2^B to the half sets the bit just above a field (its guard, bit 2iB + B) iff
+// field + c' >= 2^B, with no carry into the next field.  With c' = 2^B - c the
+// guard says "field >= c"; the top field's guard stays inside the word for
+// every B in 4..11.
+// ---------------------------------------------------------------------------
+VATE_HD constexpr uint32_t packed_rep(uint32_t B, uint32_t c) {
+    uint32_t r = 0;
+    for (uint32_t i = 0; 2u * i < 32u / B; i++) r |= c << (2u * i * B);
+    return r;
+}
+
+// The constants of one window test: field active iff
+// ((field >= a) & !(field >= b)) ^ complement, and field < 2k.
+struct PackedRange {
+    uint32_t ca, cb, c2k, f;
+};
+
+VATE_HD PackedRange packed_range(uint32_t B, uint32_t a, uint32_t b, uint32_t twok, bool complement) {
+    PackedRange r;
+    r.ca = packed_rep(B, (1u << B) - a);
+    r.cb = packed_rep(B, (1u << B) - b);
+    r.c2k = packed_rep(B, (1u << B) - twok);
+    r.f = complement ? packed_rep(B, 1u << B) : 0u;
+    return r;
+}
+
+// CheckAT of a frame-0 timestamp (ACT = BACT^0 for every AT): active iff
+// v < 2k and (BACT^0 - v) mod 2k < k'.  The window is the cyclic range
+// [lo, BACT^0] with lo = (BACT^0 - k' + 1) mod 2k; when it wraps past 0 it is
+// the complement of [BACT^0 + 1, lo) in [0, 2k).  Needs 1 <= k' <= k.
+VATE_HD PackedRange packed_range_at(uint32_t B, uint32_t bact0, uint32_t kprime, uint32_t twok) {
+    const uint32_t lo = bact0 + 1u >= kprime ? bact0 + 1u - kprime : bact0 + 1u + twok - kprime;
+    return lo <= bact0 ? packed_range(B, lo, bact0 + 1u, twok, false) : packed_range(B, bact0 + 1u, lo, twok, true);
+}
+
+// CheckDR of a recorder: active iff v < k'.
+VATE_HD PackedRange packed_range_dr(uint32_t B, uint32_t kprime, uint32_t twok) {
+    return packed_range(B, 0u, kprime, twok, false);
+}
+
+VATE_HD uint32_t popc32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return (uint32_t)__popc(x);
+#else
+    return (uint32_t)__builtin_popcount(x);
+#endif
+}
+
+// The number of active fields among fields [fa, fb) of word w (0 <= fa <= fb
+// <= PN).  An even field's guard sits B bits above its start, an odd field's
+// (in the shifted half) at its start; the odd guards are moved up one bit so
+// that both halves share one popcount.
+template <int B>
+VATE_HD uint32_t packed_count_word(uint32_t w, const PackedRange &r, uint32_t fa, uint32_t fb) {
+    constexpr uint32_t EVEN = packed_rep(B, (1u << B) - 1u), GUARD = packed_rep(B, 1u << B);
+    const uint32_t he = w & EVEN, ho = (w >> B) & EVEN;
+    const uint32_t ge = ((((he + r.ca) & ~(he + r.cb)) ^ r.f) & ~(he + r.c2k)) & GUARD;
+    const uint32_t go = ((((ho + r.ca) & ~(ho + r.cb)) ^ r.f) & ~(ho + r.c2k)) & GUARD;
+    const uint32_t span_e = (uint32_t)((1ull << (fb * B + B)) - (1ull << (fa * B + B)));
+    const uint32_t span_o = (uint32_t)((1ull << (fb * B)) - (1ull << (fa * B)));
+    return popc32((ge & span_e) | ((go & span_o) << 1));
+}
+
 }  // namespace vate

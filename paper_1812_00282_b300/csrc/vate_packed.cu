@@ -170,10 +170,14 @@ __global__ void __launch_bounds__(256) gather_packed_kernel(Geom G, uint32_t bac
 
 // Gather for widths B = 4..11 and segments of L <= 32 ATs: lane per segment.
 // In each round the lanes take 32 consecutive segments of the host, one each;
-// a lane loads the words its segment spans (at most MAXW, issued together),
-// then tests every field of them that belongs to the segment.  With
-// 2^B <= 64 the test is a lookup in a 64-bit mask of the active values;
-// wider fields use the distance arithmetic.
+// a lane loads the 16-byte chunks holding the words its segment spans (at
+// most NCH, issued together; the pool is padded to whole chunks), moves those
+// words into place by their offset in the first chunk (two rounds of selects),
+// then counts the active fields of each word that belong to the segment with
+// the SWAR test of packed_count_word (the first and last words only in part).
+// Chunks rather than words: the loads are scattered, so the L1 cost is per
+// request, and a segment of 32 fields takes at most 3 chunk loads against up
+// to 7 word loads.
 template <int MODE, int B>
 __global__ void __launch_bounds__(256) gather_packed_seg_kernel(Geom G, uint32_t bact0, uint32_t kprime,
                                                                 const uint64_t *__restrict__ hist,
@@ -182,17 +186,13 @@ __global__ void __launch_bounds__(256) gather_packed_seg_kernel(Geom G, uint32_t
                                                                 uint32_t *__restrict__ active) {
     constexpr uint32_t PN = 32 / B;                     // fields per word
     constexpr uint32_t MAXW = (PN - 1 + 32 + PN - 1) / PN;   // words a segment of <= 32 fields can span
-    constexpr uint32_t M = (1u << B) - 1u;
+    constexpr uint32_t NCH = (3 + MAXW + 3) / 4;        // 16-byte chunks they can span
     __shared__ uint64_t sN0;
     if (MODE == GATHER_ESTIMATE && threadIdx.x == 0) sN0 = pool_inactive(hist, G.P, kprime);
     __syncthreads();
-    // the active values: bit u of amask (2^B <= 64)
-    uint64_t amask = 0;
-    if (B <= 6)
-        for (uint32_t u = 0; u < (1u << B); u++)
-            if (G.counter == 1u ? check_dr(u, kprime) : (u <= G.twok && check_at(u, bact0, kprime, G.twok)))
-                amask |= 1ull << u;
-    const uint32_t *words = reinterpret_cast<const uint32_t *>(G.pool);
+    // frame 0: every AT is read with ACT = BACT^0
+    const PackedRange r = G.counter == 1u ? packed_range_dr(B, kprime, G.twok) : packed_range_at(B, bact0, kprime, G.twok);
+    const uint4 *chunks = reinterpret_cast<const uint4 *>(G.pool);
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -205,28 +205,27 @@ __global__ void __launch_bounds__(256) gather_packed_seg_kernel(Geom G, uint32_t
             if (s >= nseg) continue;
             const uint32_t base = seg_base_k(G, hk, s);
             const uint32_t q0 = base / PN, f0 = base - q0 * PN;
-            const uint32_t nw = (f0 + G.L + PN - 1) / PN;      // words holding the segment
-            uint32_t w[MAXW];
+            const uint32_t end = f0 + G.L;                  // the segment: fields [f0, end) from word q0's first
+            const uint32_t nw = (end + PN - 1) / PN;        // words holding it
+            const uint32_t o = q0 & 3u;                     // q0's place in its chunk
+            const uint32_t nch = (o + nw + 3u) >> 2;        // chunks holding words q0 .. q0 + nw - 1
+            uint32_t v[4 * NCH];
 #pragma unroll
-            for (uint32_t j = 0; j < MAXW; j++) w[j] = j < nw ? __ldg(words + q0 + j) : 0u;
-#pragma unroll
-            for (uint32_t j = 0; j < MAXW; j++) {
-#pragma unroll
-                for (uint32_t f = 0; f < PN; f++) {
-                    const uint32_t rel = j * PN + f;            // field index counted from the first word
-                    if (rel - f0 >= G.L) continue;              // outside the segment (also rel < f0)
-                    const uint32_t val = (w[j] >> (f * B)) & M;
-                    bool act;
-                    if (B <= 6) {
-                        act = (amask >> val) & 1u;
-                    } else if (G.counter == 1u) {
-                        act = check_dr(val, kprime);
-                    } else {
-                        act = val < G.twok && check_at(val, bact0, kprime, G.twok);
-                    }
-                    cnt += act ? 1u : 0u;
-                }
+            for (uint32_t c = 0; c < NCH; c++) {
+                const uint4 x = c < nch ? __ldg(chunks + (q0 >> 2) + c) : make_uint4(0u, 0u, 0u, 0u);
+                v[4 * c] = x.x;
+                v[4 * c + 1] = x.y;
+                v[4 * c + 2] = x.z;
+                v[4 * c + 3] = x.w;
             }
+            uint32_t t[4 * NCH - 1], w[MAXW];               // w[j] = v[o + j]
+#pragma unroll
+            for (uint32_t i = 0; i < 4 * NCH - 1; i++) t[i] = (o & 1u) ? v[i + 1] : v[i];
+#pragma unroll
+            for (uint32_t j = 0; j < MAXW; j++) w[j] = (o & 2u) ? t[j + 2] : t[j];
+#pragma unroll
+            for (uint32_t j = 0; j < MAXW; j++)
+                if (j < nw) cnt += packed_count_word<B>(w[j], r, j == 0 ? f0 : 0u, min(PN, end - j * PN));
         }
         const uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
         if (lane == 0) {

@@ -14,8 +14,51 @@ using namespace vate;
 static uint32_t rng_state = 12345u;
 static uint32_t rnd() { rng_state = rng_state * 1664525u + 1013904223u; return rng_state >> 8; }
 
+// packed_count_word<B> against a field-by-field count, for timestamps in
+// frame 0 (ACT = BACT^0) and recorders: every field range [fa, fb), every
+// BACT^0 and k' (sampled when k is large), words with every value in every
+// field position (B <= 6) or random ones.
+template <int B>
+static bool check_packed(long &checked) {
+    constexpr uint32_t PN = 32u / B, MF = (1u << B) - 1u;
+    const uint32_t kmax = ((1u << B) - 1u) / 2u;              // 2k + 1 <= 2^B
+    for (uint32_t k = 1; k <= kmax; k += (k < 12 ? 1u : 1u + kmax / 7u)) {
+        const uint32_t twok = 2u * k;
+        for (uint32_t dr = 0; dr < 2; dr++)
+            for (uint32_t bact0 = 0; bact0 < twok; bact0 += (twok <= 40 ? 1u : 1u + twok / 13u))
+                for (uint32_t kp = 1; kp <= k; kp += (k <= 20 ? 1u : 1u + k / 9u)) {
+                    const PackedRange r = dr ? packed_range_dr(B, kp, twok) : packed_range_at(B, bact0, kp, twok);
+                    const int nw = B <= 6 ? (int)(PN << B) : 96;
+                    for (int t = 0; t < nw; t++) {
+                        uint32_t v[32];
+                        for (uint32_t f = 0; f < PN; f++) v[f] = rnd() & MF;
+                        if (B <= 6) v[(uint32_t)t >> B] = (uint32_t)t & MF;   // every value in every position
+                        uint32_t w = (uint32_t)((uint64_t)rnd() << (PN * B));   // random unused top bits
+                        for (uint32_t f = 0; f < PN; f++) w |= v[f] << (f * B);
+                        for (uint32_t fa = 0; fa <= PN; fa++)
+                            for (uint32_t fb = fa; fb <= PN; fb++) {
+                                uint32_t want = 0;
+                                for (uint32_t f = fa; f < fb; f++)
+                                    want += dr ? (v[f] < kp) : (v[f] < twok && check_at(v[f], bact0, kp, twok));
+                                if (packed_count_word<B>(w, r, fa, fb) != want) {
+                                    printf("FAIL packed B=%d k=%u dr=%u bact0=%u k'=%u fields [%u,%u) w=%08x\n", B, k,
+                                           dr, bact0, kp, fa, fb, w);
+                                    return false;
+                                }
+                                checked++;
+                            }
+                    }
+                }
+    }
+    return true;
+}
+
 int main() {
     long checked = 0;
+    if (!check_packed<4>(checked) || !check_packed<5>(checked) || !check_packed<6>(checked) ||
+        !check_packed<7>(checked) || !check_packed<8>(checked) || !check_packed<9>(checked) ||
+        !check_packed<10>(checked) || !check_packed<11>(checked))
+        return 1;
     // swar_clamp: every byte value in every position, every top <= 126, the
     // other bytes random (so that a carry across bytes would show)
     for (uint32_t top = 0; top <= 126; top++)
