@@ -52,7 +52,8 @@ cudaError_t launch_packed_init(const Geom &G, cudaStream_t st, int sms);
 cudaError_t launch_packed_preserve(const Geom &G, uint32_t bact0, uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1,
                                    cudaStream_t st, int sms);
 cudaError_t launch_packed_dr_age(const Geom &G, cudaStream_t st, int sms);
-cudaError_t launch_packed_census(const Geom &G, uint32_t bact0, uint64_t *acc, int grid, uint64_t *hist,
+cudaError_t packed_census_prepare(uint32_t twok);   // shared-memory attribute of the lane-column packed census
+cudaError_t launch_packed_census(const Geom &G, uint32_t bact0, uint64_t *acc, int sms, uint64_t *hist,
                                  unsigned int *ticket, cudaStream_t st);
 cudaError_t launch_packed_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kprime, const uint64_t *hist,
                                  const uint32_t *aips, uint64_t n, float *out, uint8_t *flags, uint32_t *active,

@@ -572,6 +572,7 @@ size_t census_smem_bytes(uint32_t twok) { return (size_t)(CENSUS_THREADS / 32) *
 cudaError_t census_prepare(uint32_t twok) {
     cudaError_t e = cudaFuncSetAttribute(census_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)census_smem_bytes(twok));
+    if (e == cudaSuccess) e = packed_census_prepare(twok);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(census_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)census_smem_bytes(twok));
@@ -583,7 +584,7 @@ cudaError_t census_prepare(uint32_t twok) {
 
 cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *acc, int sms, uint64_t *hist,
                           unsigned int *ticket, cudaStream_t st) {
-    if (G.packed) return launch_packed_census(G, bact0, acc, sms * 4, hist, ticket, st);
+    if (G.packed) return launch_packed_census(G, bact0, acc, sms, hist, ticket, st);
     if (G.atw == 2u)
         return launch_pool(G, census16_kernel, sms * 4, CENSUS_THREADS,
                            (size_t)(CENSUS_THREADS / 32) * (G.twok + 1) * sizeof(uint32_t), st, G, bact0, acc, hist,

@@ -21,6 +21,8 @@
 #include "vate_device_ops.cuh"
 #include "vate_launch.cuh"
 
+#include <algorithm>
+
 namespace vate {
 
 namespace {
@@ -76,42 +78,83 @@ __global__ void __launch_bounds__(256) dr_age_packed_kernel(Geom G, uint64_t nwo
     }
 }
 
-// Census: one shared histogram per block (2k + 1 bins), added into acc and
-// published as in census16_kernel.
+// Census.  COLS (2k + 1 <= 127): as the byte census, each lane counts the
+// stored values (clamped to the inactive one) in its own column of the
+// block's shared histogram and the rows are relabelled as distance bins once
+// per block (census_raw_bin).  Otherwise one shared histogram of distance bins
+// per block.  Four 16-byte chunks (4 words each) in flight per thread; the
+// pool is padded to whole chunks, and fields past position P are not counted.
+template <bool COLS>
 __global__ void __launch_bounds__(CENSUS_THREADS) census_packed_kernel(Geom G, uint32_t bact0, uint32_t pat,
                                                                        uint64_t *__restrict__ acc,
                                                                        uint64_t *__restrict__ hist,
                                                                        unsigned int *__restrict__ ticket) {
-    extern __shared__ uint32_t hsh[];   // [nbins]
+    extern __shared__ uint32_t hsh[];   // COLS: [warps][nbins][32]; else [nbins]
     const uint32_t nbins = G.twok + 1u;
-    const uint32_t lane = threadIdx.x & 31u;
-    for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) hsh[i] = 0;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t nsh = COLS ? nwarps * nbins * 32u : nbins;
+    for (uint32_t i = threadIdx.x; i < nsh; i += blockDim.x) hsh[i] = 0;
     __syncthreads();
+    uint32_t *col = hsh + (size_t)warp * nbins * 32u + lane;
     const uint32_t inact = inactive_value(G);
-    const uint32_t *words = reinterpret_cast<const uint32_t *>(G.pool);
-    const uint64_t nwords = (G.P + G.pn - 1) / G.pn;
+    const uint4 *chunks = reinterpret_cast<const uint4 *>(G.pool);
+    const uint64_t nwords = (G.P + G.pn - 1) / G.pn, nchunks = (nwords + 3) / 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint32_t inactive = 0;
-    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nwords; q += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t w = __ldcg(words + q);
-        const uint64_t rest = G.P - q * G.pn;
-        const uint32_t nf = rest < G.pn ? (uint32_t)rest : G.pn;
-        if (w == pat && nf == G.pn) {
-            inactive += nf;
-            continue;
+    constexpr int U = 4;
+    for (uint64_t c0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c0 < nchunks; c0 += U * stride) {
+        uint4 x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint64_t c = c0 + (uint64_t)u * stride;
+            x[u] = c < nchunks ? __ldcg(chunks + c) : make_uint4(pat, pat, pat, pat);
         }
-        for (uint32_t f = 0; f < nf; f++) {
-            const uint32_t v = field(w, f, G.atb);
-            if (v >= inact) {
-                inactive++;
-                continue;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint64_t c = c0 + (uint64_t)u * stride;
+            if (c >= nchunks) continue;
+            const uint32_t ws[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint64_t q = 4 * c + j;
+                const uint64_t first = q * G.pn;                  // position of the word's first field
+                const uint32_t nf = first >= G.P ? 0u : (G.P - first < G.pn ? (uint32_t)(G.P - first) : G.pn);
+                const uint32_t w = ws[j];
+                if (w == pat && nf == G.pn) {
+                    inactive += nf;
+                    continue;
+                }
+                for (uint32_t f = 0; f < nf; f++) {
+                    const uint32_t v = field(w, f, G.atb);
+                    if (COLS) {
+                        atomicAdd(&col[min(v, inact) * 32u], 1u);
+                        continue;
+                    }
+                    if (v >= inact) {
+                        inactive++;
+                        continue;
+                    }
+                    uint32_t d = v;                               // a recorder's value is its distance
+                    if (G.counter != 1u) {                        // frame 0: ACT = BACT^0 for every AT
+                        d = bact0 + G.twok - v;
+                        if (d >= G.twok) d -= G.twok;
+                    }
+                    atomicAdd(&hsh[d], 1u);
+                }
             }
-            uint32_t d = v;                               // a recorder's value is its distance
-            if (G.counter != 1u) {                        // frame 0: ACT = BACT^0 for every AT
-                d = bact0 + G.twok - v;
-                if (d >= G.twok) d -= G.twok;
-            }
-            atomicAdd(&hsh[d], 1u);
         }
+    }
+    if (COLS) {
+        col[inact * 32u] += inactive;
+        __syncthreads();
+        for (uint32_t r = warp; r < nbins; r += nwarps) {
+            uint32_t t = 0;
+            for (uint32_t wv = 0; wv < nwarps; wv++) t += hsh[((size_t)wv * nbins + r) * 32u + lane];
+            t = __reduce_add_sync(0xFFFFFFFFu, t);
+            if (lane == 0) census_add(acc, census_raw_bin(G, bact0, r), t);
+        }
+        census_publish(acc, hist, ticket, nbins);
+        return;
     }
     inactive = __reduce_add_sync(0xFFFFFFFFu, inactive);
     if (lane == 0) atomicAdd(&hsh[G.twok], inactive);
@@ -313,10 +356,21 @@ cudaError_t launch_packed_dr_age(const Geom &G, cudaStream_t st, int sms) {
     return launch_pool(G, dr_age_packed_kernel, grid_for_packed(nwords, sms), 256, 0, st, G, nwords);
 }
 
-cudaError_t launch_packed_census(const Geom &G, uint32_t bact0, uint64_t *acc, int grid, uint64_t *hist,
+cudaError_t packed_census_prepare(uint32_t twok) {
+    return cudaFuncSetAttribute(census_packed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)census_smem_bytes(twok));
+}
+
+cudaError_t launch_packed_census(const Geom &G, uint32_t bact0, uint64_t *acc, int sms, uint64_t *hist,
                                  unsigned int *ticket, cudaStream_t st) {
-    return launch_pool(G, census_packed_kernel, grid, CENSUS_THREADS, (size_t)(G.twok + 1) * sizeof(uint32_t), st, G,
-                       bact0, packed_pattern(G), acc, hist, ticket);
+    if (G.twok + 1u <= 127u) {      // lane columns, as many blocks per SM as fit in about 200 KiB (up to four)
+        const size_t smem = census_smem_bytes(G.twok);
+        const int per_sm = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)(200u << 10) / smem));
+        return launch_pool(G, census_packed_kernel<true>, sms * per_sm, CENSUS_THREADS, smem, st, G, bact0,
+                           packed_pattern(G), acc, hist, ticket);
+    }
+    return launch_pool(G, census_packed_kernel<false>, sms * 4, CENSUS_THREADS, (size_t)(G.twok + 1) * sizeof(uint32_t),
+                       st, G, bact0, packed_pattern(G), acc, hist, ticket);
 }
 
 cudaError_t launch_packed_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kprime, const uint64_t *hist,
