@@ -464,6 +464,9 @@ PACKED = [
     ((15, 1, 256, 8, 0, 74), 2),         # 16 per word
     ((17, 70, 512, 16, 0, 75), 8),       # 4 per word, values up to 140
     ((17, 10, 512, 64, 0, 76), 7),       # 4 per word, 3 bits left over
+    ((16, 15, 512, 32, 0, 77), 6),       # 5 per word: an odd count, the odd half's top field absent
+    ((18, 200, 512, 16, 1, 78), 9),      # 3 per word, 16-bit values in the paper's form
+    ((22, 1000, 256, 32, 0, 79), 11),    # 2 per word, k near the 16-bit limit
 ]
 
 
