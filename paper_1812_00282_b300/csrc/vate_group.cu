@@ -51,6 +51,24 @@ struct CensusTile {
     uint64_t chunk0;
 };
 
+// census_chunk_raw (vate_device_ops.cuh) into columns of counter pairs:
+// values 2j and 2j + 1 share the 32-bit word col[j * 32] as its low and high
+// 16 bits, halving the shared memory.  The caller keeps every count below
+// 2^16 (at most 4,096 ATs per lane between two clearings).
+__device__ __forceinline__ void census_chunk_raw_pairs(uint4 w, uint32_t pat, uint32_t inact, uint32_t *col,
+                                                       uint32_t &inactive_runs) {
+    if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
+        inactive_runs++;
+        return;
+    }
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int b = 0; b < 16; b++) {
+        const uint32_t v = min((words[b >> 2] >> (8 * (b & 3))) & 0xFFu, inact);
+        atomicAdd(&col[(v >> 1) * 32u], 1u << ((v & 1u) << 4));
+    }
+}
+
 __device__ __forceinline__ uint32_t bact0_of(unsigned long long step, uint32_t twok) {
     return (uint32_t)(step % twok);
 }
@@ -202,12 +220,13 @@ __global__ void __launch_bounds__(G_THREADS) group_ingest_kernel(const Geom *__r
 __global__ void __launch_bounds__(G_THREADS) group_census_kernel(const Geom *__restrict__ descs, GroupState *st,
                                                                  const CensusTile *__restrict__ tiles, uint32_t ntiles,
                                                                  uint64_t *__restrict__ hist_all, uint32_t maxbins) {
-    extern __shared__ uint32_t sh[];             // [warps][maxbins][32]
+    extern __shared__ uint32_t sh[];             // [warps][maxpairs][32]: lane columns of 16-bit counter pairs
     __shared__ Geom G;
     __shared__ CensusTile tile;
     __shared__ unsigned int ticket;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    uint32_t *col = sh + (size_t)warp * maxbins * 32u + lane;
+    const uint32_t maxpairs = (maxbins + 1u) / 2u;
+    uint32_t *col = sh + (size_t)warp * maxpairs * 32u + lane;
     const unsigned long long step = st->step;
     for (;;) {
         if (threadIdx.x == 0) ticket = atomicAdd(&st->q_census, 1u);
@@ -218,14 +237,15 @@ __global__ void __launch_bounds__(G_THREADS) group_census_kernel(const Geom *__r
             G = descs[tile.mon];
         }
         __syncthreads();
-        const uint32_t nbins = G.twok + 1u;
-        for (uint32_t b = 0; b < nbins; b++) col[b * 32u] = 0u;
+        const uint32_t nbins = G.twok + 1u, npairs = (nbins + 1u) / 2u;
+        for (uint32_t b = 0; b < npairs; b++) col[b * 32u] = 0u;
         const uint32_t pat = G.twok * ONES;
         const uint32_t bact0 = bact0_of(step, G.twok);
         uint32_t inactive_runs = 0;
         const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
         // eight chunks in flight per thread: the pools of a group exceed L2, so the loads wait on memory;
-        // frame-0 pools: the stored values are counted and relabelled as bins below
+        // frame-0 pools: the stored values are counted and relabelled as bins below.  A tile holds at
+        // most 65,536 chunks, so a lane counts at most 4,096 ATs and every 16-bit counter stays exact.
         constexpr int U = 8;
         const uint64_t qend = tile.chunk0 + tile.nchunks;
         for (uint64_t q = tile.chunk0 + threadIdx.x; q < qend; q += (uint64_t)U * blockDim.x) {
@@ -238,19 +258,24 @@ __global__ void __launch_bounds__(G_THREADS) group_census_kernel(const Geom *__r
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const uint64_t qu = q + (uint64_t)u * blockDim.x;
-                if (qu < qend) census_chunk_raw(w[u], pat, G.twok, col, inactive_runs);
+                if (qu < qend) census_chunk_raw_pairs(w[u], pat, G.twok, col, inactive_runs);
             }
         }
-        col[G.twok * 32u] += 16u * inactive_runs;
+        col[(G.twok >> 1) * 32u] += 16u * inactive_runs;     // 2k is even: the low half of pair k
         __syncthreads();
-        for (uint32_t r = warp; r < nbins; r += nwarps) {
-            uint32_t s = 0;
-            for (uint32_t wv = 0; wv < nwarps; wv++) s += sh[((size_t)wv * maxbins + r) * 32u + lane];
-            s = __reduce_add_sync(0xFFFFFFFFu, s);
-            if (lane == 0 && s)
-                atomicAdd(reinterpret_cast<unsigned long long *>(hist_all) + (size_t)tile.mon * maxbins +
-                              census_raw_bin(G, bact0, r),
-                          (unsigned long long)s);
+        for (uint32_t r = warp; r < npairs; r += nwarps) {
+            uint32_t lo = 0, hi = 0;
+            for (uint32_t wv = 0; wv < nwarps; wv++) {
+                const uint32_t x = sh[((size_t)wv * maxpairs + r) * 32u + lane];
+                lo += x & 0xFFFFu;
+                hi += x >> 16;
+            }
+            lo = __reduce_add_sync(0xFFFFFFFFu, lo);
+            hi = __reduce_add_sync(0xFFFFFFFFu, hi);
+            unsigned long long *h = reinterpret_cast<unsigned long long *>(hist_all) + (size_t)tile.mon * maxbins;
+            if (lane == 0 && lo) atomicAdd(h + census_raw_bin(G, bact0, 2u * r), (unsigned long long)lo);
+            if (lane == 0 && hi && 2u * r + 1u < nbins)
+                atomicAdd(h + census_raw_bin(G, bact0, 2u * r + 1u), (unsigned long long)hi);
         }
         __syncthreads();
     }
@@ -403,7 +428,7 @@ int check_tuning(const vate_group_tuning *t) {
 
 size_t ingest_smem(uint32_t M) { return (size_t)((M + 2) & ~1u) * 8 + (size_t)M * sizeof(Geom); }
 size_t gather_smem(uint32_t M) { return (size_t)((2 * M + 1 + (M + 1) / 2 + 1) & ~1u) * 8 + (size_t)M * sizeof(Geom); }
-size_t census_smem(uint32_t maxbins) { return (size_t)(G_THREADS / 32) * maxbins * 32 * sizeof(uint32_t); }
+size_t census_smem(uint32_t maxbins) { return (size_t)(G_THREADS / 32) * ((maxbins + 1) / 2) * 32 * sizeof(uint32_t); }
 
 template <int CPSL, int RB>
 cudaError_t launch_group_gather(vate_group *g, const uint32_t *hosts, const uint64_t *hoff, uint64_t hcap,
@@ -437,7 +462,9 @@ cudaError_t enqueue_ingest(vate_group *g, const vate_pair *pairs, const uint64_t
 cudaError_t enqueue_census(vate_group *g, cudaStream_t st) {
     size_t smem = census_smem(g->maxbins);
     cudaFuncSetAttribute(group_census_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return vate::launch_pool(g->arena_geom, group_census_kernel, g->sms * 2, G_THREADS, smem, st,
+    // as many blocks per SM as their columns fit in about 200 KiB, up to four
+    const int per_sm = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)(200u << 10) / smem));
+    return vate::launch_pool(g->arena_geom, group_census_kernel, g->sms * per_sm, G_THREADS, smem, st,
                              (const Geom *)g->d_descs, g->d_state, (const CensusTile *)g->d_tiles, g->ntiles, g->d_hist,
                              g->maxbins);
 }
