@@ -64,9 +64,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator train/evaluate run")
-    ap.add_argument("--workload", default="link40g", choices=["link40g", "monitors64", "serving", "pt"],
+    ap.add_argument("--workload", default="link40g",
+                    choices=["link40g", "monitors64", "serving", "pt", "learned-kernels"],
                     help="link40g: the headline single-monitor workload; monitors64: 64 independent monitors "
-                         "advanced together (vate_group, CUDA graph per slice)")
+                         "advanced together (vate_group, CUDA graph per slice); learned-kernels: the learned "
+                         "estimator's kernels timed one by one at 2^20 hosts")
     return ap.parse_args()
 
 
@@ -749,8 +751,57 @@ def run_pt(args):
                         "between slides, g = 1024", "hbm_peak_gbs": hbm, "rows": rows}
 
 
+def run_learned_kernels(args):
+    """The learned estimator's kernels one by one at close, 2^20 hosts: the
+    40 Gb/s traffic on a 2^24-AT pool (k = 10, g = 4096, L = 32) after 12
+    slices, a model of 2k + 2 = 22 inputs with weights from vate_mlp_init (the
+    cost does not depend on them).  CUDA-event mean of 10 calls after 3
+    warm-up calls."""
+    import torch
+    import paper_1812_00282_b300 as V
+    from traffic import LINK40G, DeviceTraffic, Traffic
+    torch.cuda.set_device(0)
+    dt = DeviceTraffic(Traffic(LINK40G))
+    k, c, g = 10, 24, 4096
+    h = V.Vate(c, k, g, 32, 0, 7)
+    for s in range(12):
+        h.ingest(dt.slice_pairs(s), s)
+    h.close_slice(11)
+    hosts = dt.hosts()[: args.aips].contiguous()
+    n, n_in = hosts.numel(), 2 * k + 2
+    params = torch.empty(V.vate_mlp_param_count(n_in), dtype=torch.float32, device="cuda")
+    V.vate_mlp_init(params, n_in, 3)
+    x = torch.empty(n * n_in, dtype=torch.float32, device="cuda")
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return round(ev[0].elapsed_time(ev[1]) / reps, 4)
+
+    ms = {"features": timed(lambda: V.vate_features(h.h, hosts, x)),
+          "forward": timed(lambda: V.vate_mlp_forward(params, n_in, x.view(n, n_in), y)),
+          "fused_learned_estimate": timed(lambda: V.vate_estimate_learned(h.h, hosts, params, out, fl)),
+          "plain_eq11_estimate": timed(lambda: h.estimate(hosts, k, out, fl))}
+    h.close()
+    return {"workload": "learned estimator kernels at close: %d hosts, 2^24-AT pool, k = 10, g = 4096" % n,
+            "unit": "ms per call", "ms": ms}
+
+
 def main():
     args = parse()
+    if args.workload == "learned-kernels":
+        print(json.dumps(run_learned_kernels(args)), flush=True)
+        return
     if args.workload == "pt":
         print(json.dumps(run_pt(args)), flush=True)
         return
