@@ -65,10 +65,11 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator train/evaluate run")
     ap.add_argument("--workload", default="link40g",
-                    choices=["link40g", "monitors64", "serving", "pt", "learned-kernels"],
+                    choices=["link40g", "monitors64", "serving", "pt", "learned-kernels", "probes"],
                     help="link40g: the headline single-monitor workload; monitors64: 64 independent monitors "
                          "advanced together (vate_group, CUDA graph per slice); learned-kernels: the learned "
-                         "estimator's kernels timed one by one at 2^20 hosts")
+                         "estimator's kernels timed one by one at 2^20 hosts; probes: random 32-byte sector "
+                         "reads against the working-set size")
     return ap.parse_args()
 
 
@@ -797,8 +798,40 @@ def run_learned_kernels(args):
             "unit": "ms per call", "ms": ms}
 
 
+def run_probes(args):
+    """Random 32-byte sector reads (vate_probe_sector_read, lane pairs per
+    sector as in the gather) from buffers of 8 MiB to 256 MiB: where the L2
+    rate gives way to the HBM one.  2^27 sectors per launch, best of 5 after
+    2 warm-up launches."""
+    import torch
+    import paper_1812_00282_b300 as V
+    torch.cuda.set_device(0)
+    sink = torch.zeros(4, dtype=torch.int32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    n = 1 << 27
+    rates = {}
+    for mib in (8, 16, 32, 64, 128, 256):
+        buf = torch.zeros(mib << 20, dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            V.vate_probe_sector_read(buf, n, sink)
+        best = float("inf")
+        for _ in range(5):
+            ev[0].record()
+            V.vate_probe_sector_read(buf, n, sink)
+            ev[1].record()
+            torch.cuda.synchronize()
+            best = min(best, ev[0].elapsed_time(ev[1]))
+        rates["%d MiB" % mib] = round(32 * n / best / 1e6, 1)
+        del buf
+    return {"workload": "random 32-byte sector reads against the working-set size", "unit": "GB/s",
+            "sector_read_gbs": rates}
+
+
 def main():
     args = parse()
+    if args.workload == "probes":
+        print(json.dumps(run_probes(args)), flush=True)
+        return
     if args.workload == "learned-kernels":
         print(json.dumps(run_learned_kernels(args)), flush=True)
         return
