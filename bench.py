@@ -65,11 +65,12 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator train/evaluate run")
     ap.add_argument("--workload", default="link40g",
-                    choices=["link40g", "monitors64", "serving", "pt", "learned-kernels", "probes"],
+                    choices=["link40g", "monitors64", "serving", "pt", "learned-kernels", "probes", "ingest-mix"],
                     help="link40g: the headline single-monitor workload; monitors64: 64 independent monitors "
                          "advanced together (vate_group, CUDA graph per slice); learned-kernels: the learned "
                          "estimator's kernels timed one by one at 2^20 hosts; probes: random 32-byte sector "
-                         "reads against the working-set size")
+                         "reads against the working-set size; ingest-mix: vate_ingest of a 40 Gb/s slice "
+                         "against uniform random pairs and against the slice's distinct pairs")
     return ap.parse_args()
 
 
@@ -827,8 +828,54 @@ def run_probes(args):
             "sector_read_gbs": rates}
 
 
+def run_ingest_mix(args):
+    """vate_ingest alone into a 2^26-AT pool (k = 10, g = 4096, L = 32), L2
+    flushed before each launch: one 40 Gb/s slice (5M pairs with the traffic's
+    repeats and heavy hosts), the same number of uniform random pairs, and the
+    slice's distinct pairs only.  CUDA-event mean of 20 launches after 3."""
+    import torch
+    import paper_1812_00282_b300 as V
+    from traffic import LINK40G, DeviceTraffic, Traffic
+    torch.cuda.set_device(0)
+    dt = DeviceTraffic(Traffic(LINK40G))
+    h = V.Vate(C, 10, G, 32, 0, 7)
+    pairs = dt.slice_pairs(5)
+    n = pairs.shape[0]
+    key = (pairs[:, 0].to(torch.int64) & 0xFFFFFFFF) << 32 | (pairs[:, 1].to(torch.int64) & 0xFFFFFFFF)
+    uniq = torch.unique(key)
+    distinct = torch.stack([uniq >> 32, uniq & 0xFFFFFFFF], 1)
+    distinct = torch.where(distinct >= 2**31, distinct - 2**32, distinct).to(torch.int32).contiguous()
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    uniform = torch.randint(-2**31, 2**31 - 1, (n, 2), generator=gen, device="cuda", dtype=torch.int32)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    h.ingest(pairs, 0)
+
+    def timed(p, reps=20):
+        for _ in range(3):
+            V.vate_ingest(h.h, p, 0)
+        tot = 0.0
+        for r in range(reps):
+            flush.fill_(r & 0xFF)
+            torch.cuda.synchronize()
+            ev[0].record()
+            V.vate_ingest(h.h, p, 0)
+            ev[1].record()
+            torch.cuda.synchronize()
+            tot += ev[0].elapsed_time(ev[1])
+        return round(1000 * tot / reps, 1)
+
+    res = {"slice_us": timed(pairs), "distinct_only_us": timed(distinct), "uniform_us": timed(uniform)}
+    h.close()
+    return {"workload": "vate_ingest alone, 2^26-AT pool, k = 10, g = 4096, L = 32, L2 flushed before each launch",
+            "pairs": n, "distinct_pairs": int(uniq.numel()), "unit": "us per launch", "times": res}
+
+
 def main():
     args = parse()
+    if args.workload == "ingest-mix":
+        print(json.dumps(run_ingest_mix(args)), flush=True)
+        return
     if args.workload == "probes":
         print(json.dumps(run_probes(args)), flush=True)
         return
