@@ -1,0 +1,108 @@
+"""Randomised configurations against the oracle.
+
+Each case draws a valid configuration -- pool size, window k (byte ATs up to
+63, 16-bit ATs up to 300), vector length g, segment length L, partition,
+layout (bytes, 16-bit or b-bit packed fields) -- and a slice sequence with
+gaps (some longer than 2k, so that whole windows expire), then compares the
+pool, the census, the active counts, the flags and Eq. 11 with the oracle
+after every close, as the fixed parity cases do.  Distance recorders (VDRE)
+are drawn the same way: their pool equals the oracle's recorder pool, and
+their census, active counts and estimates those of the timestamps.  The
+draws are seeded, so a failing case is reproduced by its id.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import Oracle
+from test_parity_gpu import dev_pairs, dev_u32, run_stream
+from traffic import SMALL, Traffic
+
+pytestmark = pytest.mark.gpu
+
+N_CASES = 64
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1812_00282_b300 as V
+    return V
+
+
+def draw(case):
+    rng = np.random.default_rng(1000 + case)
+    k = int(rng.integers(1, 64)) if rng.random() < 0.7 else int(rng.integers(64, 301))
+    cmin = max(12, math.ceil(math.log2((2 * k - 1) * 2 * k)))   # every block of Eq. 9-10 non-empty
+    c = int(rng.integers(cmin, max(cmin, 18) + 1))
+    L = int(rng.choice([1, 2, 4, 8, 16, 32, 64]))
+    g = int(min(L * rng.integers(2, 65), 4096))
+    part = int(rng.integers(0, 2))
+    bmin = math.ceil(math.log2(2 * k + 1))
+    at_bits = int(rng.integers(bmin, 17)) if rng.random() < 0.3 else 0
+    ids, s = [], 0
+    for _ in range(int(rng.integers(4, 8))):
+        ids.append(s)
+        s += int(rng.choice([1, 1, 2, 3, k, 2 * k + 1]))
+    kps = sorted({1, int(rng.integers(1, k + 1)), k})
+    return (c, k, g, L, part, 500 + case), at_bits, ids, kps, int(rng.integers(2_000, 12_000))
+
+
+@pytest.mark.parametrize("case", range(N_CASES))
+def test_random_configuration_matches_oracle(V, case):
+    params, at_bits, ids, kps, pkts = draw(case)
+    c, k, g, L, part, seed = params
+    tr = Traffic(SMALL, pkts_per_slice=pkts)
+    slices = [tr.slice_pairs(i % 64) for i in ids]
+    hosts = np.concatenate([tr.aips[:300], np.random.default_rng(case).integers(0, 2**32, 50, dtype=np.uint64)
+                            .astype(np.uint32)])
+    run_stream(V, params, slices, hosts, kps=kps, slice_ids=ids, at_bits=at_bits,
+               check_ages=(at_bits == 0 and k <= 63))
+
+
+@pytest.mark.parametrize("case", range(N_CASES // 2))
+def test_random_recorder_configuration_matches_oracle(V, case):
+    params, at_bits, ids, kps, pkts = draw(10_000 + case)
+    c, k, g, L, part, seed = params
+    tr = Traffic(SMALL, pkts_per_slice=pkts)
+    hosts = tr.aips[:300]
+    dh = dev_u32(hosts)
+    dr = V.Vate(c, k, g, L, part, seed, counter=V.VATE_COUNTER_DR, at_bits=at_bits)
+    at = V.Vate(c, k, g, L, part, seed, at_bits=at_bits)
+    o = Oracle(c=c, k=k, g=g, seg_len=L, partition=part, seed=seed)
+    prev = None
+    for sid in ids:
+        if prev is not None:
+            for _ in range(sid - prev):
+                o.advance()
+        prev = sid
+        p = tr.slice_pairs(sid % 64)
+        o.ingest(p)
+        for d in (dr, at):
+            d.ingest(dev_pairs(p), sid)
+            d.close_slice(sid)
+        pool = torch.empty(o.P, dtype=V.pool_dtype(k), device="cuda")
+        dr.copy_pool(pool)
+        np.testing.assert_array_equal(pool.cpu().numpy().astype(np.int64), o.dr().astype(np.int64))
+        h_dr = torch.empty(2 * k + 1, dtype=torch.int64, device="cuda")
+        h_at = torch.empty_like(h_dr)
+        dr.census(h_dr)
+        at.census(h_at)
+        a, b = h_dr.cpu().numpy(), h_at.cpu().numpy()
+        np.testing.assert_array_equal(a[:k], b[:k])
+        assert a[k:2 * k].sum() == 0 and a[2 * k] == b[k:].sum()
+        for kp in kps:
+            e1 = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+            e2 = torch.empty_like(e1)
+            a1 = torch.empty(len(hosts), dtype=torch.int32, device="cuda")
+            dr.estimate(dh, kp, e1)
+            at.estimate(dh, kp, e2)
+            dr.active_counts(dh, kp, a1)
+            assert torch.equal(e1, e2)
+            _, oa, _ = o.estimate(hosts, kp)
+            np.testing.assert_array_equal(a1.cpu().numpy().view(np.uint32), oa)
+    dr.close()
+    at.close()
