@@ -7,8 +7,10 @@ gaps (some longer than 2k, so that whole windows expire), then compares the
 pool, the census, the active counts, the flags and Eq. 11 with the oracle
 after every close, as the fixed parity cases do.  Distance recorders (VDRE)
 are drawn the same way: their pool equals the oracle's recorder pool, and
-their census, active counts and estimates those of the timestamps.  The
-draws are seeded, so a failing case is reproduced by its id.
+their census, active counts and estimates those of the timestamps.  Monitor
+groups of random size and make-up (one segment length per group), stepped
+plainly or by graph replay, equal a single handle per monitor bit for bit.
+The draws are seeded, so a failing case is reproduced by its id.
 """
 import math
 
@@ -17,6 +19,7 @@ import pytest
 import torch
 
 from oracle import Oracle
+from test_group_gpu import run_group_vs_single
 from test_parity_gpu import dev_pairs, dev_u32, run_stream
 from traffic import SMALL, Traffic
 
@@ -106,3 +109,17 @@ def test_random_recorder_configuration_matches_oracle(V, case):
             np.testing.assert_array_equal(a1.cpu().numpy().view(np.uint32), oa)
     dr.close()
     at.close()
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_random_monitor_group_equals_single_handles(V, case):
+    rng = np.random.default_rng(20_000 + case)
+    L = int(rng.choice([1, 2, 8, 16, 32, 64]))
+    monitors = []
+    for m in range(int(rng.integers(1, 25))):
+        k = int(rng.integers(1, 61))
+        cmin = max(12, math.ceil(math.log2((2 * k - 1) * 2 * k)))
+        c = int(rng.integers(cmin, max(cmin, 17) + 1))
+        g = int(min(L * rng.integers(2, 65), 4096))
+        monitors.append((c, k, g, L, int(rng.integers(0, 2)), 30_000 + 100 * case + m))
+    run_group_vs_single(V, monitors, nslices=int(rng.integers(4, 10)), graph=bool(rng.integers(0, 2)))
