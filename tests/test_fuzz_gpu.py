@@ -10,6 +10,8 @@ are drawn the same way: their pool equals the oracle's recorder pool, and
 their census, active counts and estimates those of the timestamps.  Monitor
 groups of random size and make-up (one segment length per group), stepped
 plainly or by graph replay, equal a single handle per monitor bit for bit.
+Position shards at random 64-aligned cut points hold the undivided pool
+between them and reduce to its census and estimates.
 The draws are seeded, so a failing case is reproduced by its id.
 """
 import math
@@ -123,3 +125,61 @@ def test_random_monitor_group_equals_single_handles(V, case):
         g = int(min(L * rng.integers(2, 65), 4096))
         monitors.append((c, k, g, L, int(rng.integers(0, 2)), 30_000 + 100 * case + m))
     run_group_vs_single(V, monitors, nslices=int(rng.integers(4, 10)), graph=bool(rng.integers(0, 2)))
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_random_shards_equal_one_handle(V, case):
+    rng = np.random.default_rng(40_000 + case)
+    params, _, ids, kps, pkts = draw(50_000 + case)
+    c, k, g, L, part, seed = params
+    counter = int(rng.integers(0, 2))
+    P = 1 << c
+    cuts = sorted(set(int(x) * 64 for x in rng.integers(1, P // 64, int(rng.integers(1, 5)))))
+    bounds = [0] + cuts + [P]
+    ranges = list(zip(bounds[:-1], bounds[1:]))
+    vp = V.make_params(c, k, g, L, part, seed, counter)
+    full = V.Vate(c, k, g, L, part, seed, counter=counter)
+    shards = [V.vate_create_shard(vp, lo, hi) for lo, hi in ranges]
+    tr = Traffic(SMALL, pkts_per_slice=pkts)
+    hosts = tr.aips[:300]
+    dh = dev_u32(hosts)
+    dt = V.pool_dtype(k)
+    for sid in ids:
+        dp = dev_pairs(tr.slice_pairs(sid % 64))
+        full.ingest(dp, sid)
+        full.close_slice(sid)
+        for h in shards:
+            V.vate_ingest(h, dp, sid)
+            V.vate_close_slice(h, sid)
+        whole = torch.empty(P, dtype=dt, device="cuda")
+        full.copy_pool(whole)
+        parts = []
+        for h, (lo, hi) in zip(shards, ranges):
+            t = torch.empty(hi - lo, dtype=dt, device="cuda")
+            V.vate_copy_pool(h, t)
+            parts.append(t)
+        assert torch.equal(torch.cat(parts), whole)
+        hist = torch.zeros(2 * k + 1, dtype=torch.int64, device="cuda")
+        for h in shards:
+            t = torch.empty_like(hist)
+            V.vate_census(h, t)
+            hist += t
+        want = torch.empty_like(hist)
+        full.census(want)
+        assert torch.equal(hist, want)
+        for kp in kps:
+            act = torch.zeros(len(hosts), dtype=torch.int32, device="cuda")
+            for h in shards:
+                t = torch.empty_like(act)
+                V.vate_active_counts(h, dh, kp, t)
+                act += t
+            e1 = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+            f1 = torch.empty(len(hosts), dtype=torch.uint8, device="cuda")
+            V.vate_estimate_from_counts(vp, act, hist, kp, e1, f1)
+            e2 = torch.empty_like(e1)
+            f2 = torch.empty_like(f1)
+            full.estimate(dh, kp, e2, f2)
+            assert torch.equal(e1, e2) and torch.equal(f1, f2)
+    for h in shards:
+        V.vate_destroy(h)
+    full.close()
