@@ -11,7 +11,8 @@ their census, active counts and estimates those of the timestamps.  Monitor
 groups of random size and make-up (one segment length per group), stepped
 plainly or by graph replay, equal a single handle per monitor bit for bit.
 Position shards at random 64-aligned cut points hold the undivided pool
-between them and reduce to its census and estimates.
+between them and reduce to its census and estimates.  A handle checkpointed
+after a random slice and restored continues exactly as the original.
 The draws are seeded, so a failing case is reproduced by its id.
 """
 import math
@@ -183,3 +184,41 @@ def test_random_shards_equal_one_handle(V, case):
     for h in shards:
         V.vate_destroy(h)
     full.close()
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_random_checkpoint_resume_continues_exactly(V, case):
+    rng = np.random.default_rng(60_000 + case)
+    params, at_bits, ids, kps, pkts = draw(70_000 + case)
+    c, k, g, L, part, seed = params
+    counter = int(rng.integers(0, 2))
+    cut = int(rng.integers(1, len(ids)))             # checkpoint after the close of slice ids[cut - 1]
+    tr = Traffic(SMALL, pkts_per_slice=pkts)
+    hosts = tr.aips[:300]
+    dh = dev_u32(hosts)
+    a = V.Vate(c, k, g, L, part, seed, counter=counter, at_bits=at_bits)
+    b = None
+    for j, sid in enumerate(ids):
+        if j == cut:
+            b = V.Vate.restore(a.checkpoint())
+        p = dev_pairs(tr.slice_pairs(sid % 64))
+        for d in (a, b):
+            if d is None:
+                continue
+            d.ingest(p, sid)
+            d.close_slice(sid)
+        if b is None:
+            continue
+        pa = torch.empty(1 << c, dtype=V.pool_dtype(k), device="cuda")
+        pb = torch.empty_like(pa)
+        a.copy_pool(pa)
+        b.copy_pool(pb)
+        assert torch.equal(pa, pb)
+        for kp in kps:
+            e1 = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
+            e2 = torch.empty_like(e1)
+            a.estimate(dh, kp, e1)
+            b.estimate(dh, kp, e2)
+            assert torch.equal(e1, e2)
+    a.close()
+    b.close()
