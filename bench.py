@@ -754,7 +754,8 @@ def run_pt(args):
 
 
 def run_learned_kernels(args):
-    """The learned estimator's kernels one by one at close, 2^20 hosts: the
+    """The learned estimator's kernels one by one at close, 2^20 hosts (and
+    the per-age counts of vate_age_counts, which hold the same numbers): the
     40 Gb/s traffic on a 2^24-AT pool (k = 10, g = 4096, L = 32) after 12
     slices, a model of 2k + 2 = 22 inputs with weights from vate_mlp_init (the
     cost does not depend on them).  CUDA-event mean of 10 calls after 3
@@ -790,7 +791,9 @@ def run_learned_kernels(args):
         torch.cuda.synchronize()
         return round(ev[0].elapsed_time(ev[1]) / reps, 4)
 
-    ms = {"features": timed(lambda: V.vate_features(h.h, hosts, x)),
+    ages = torch.empty(n * k, dtype=torch.int16, device="cuda")
+    ms = {"age_counts": timed(lambda: V.vate_age_counts(h.h, hosts, ages)),
+          "features": timed(lambda: V.vate_features(h.h, hosts, x)),
           "forward": timed(lambda: V.vate_mlp_forward(params, n_in, x.view(n, n_in), y)),
           "fused_learned_estimate": timed(lambda: V.vate_estimate_learned(h.h, hosts, params, out, fl)),
           "plain_eq11_estimate": timed(lambda: h.estimate(hosts, k, out, fl))}

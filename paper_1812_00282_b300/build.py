@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libvate.so")
 SOURCES = ["vate_api.cu", "vate_kernels.cu", "vate_packed.cu", "vate_probe.cu", "vate_noalloc.cu", "vate_group.cu", "vate_learned.cu", "vate_server.cu"]
-HEADERS = ["vate_device.cuh", "vate_device_ops.cuh", "vate_launch.cuh", "vate_internal.h"]
+HEADERS = ["vate_device.cuh", "vate_device_ops.cuh", "vate_ages.cuh", "vate_launch.cuh", "vate_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -14,7 +14,8 @@
 //   gather_scalar_kernel  the same for L < 16 (one byte per VAT)
 //   estimate_from_counts_kernel  Eq. 11 from active counts and a census
 //                         summed over the shards of one pool            (Eq. 11)
-//   age_counts_kernel     per-host counts of VATs by distance d < k
+//   age_counts_planes_kernel, age_counts_kernel
+//                         per-host counts of VATs by distance d < k
 //   frame_convert_kernel  a pool to / from the paper's per-block values
 //
 // A handle's timestamp pool is kept in the frame of block 0 (each value minus
@@ -28,6 +29,7 @@
 #include "vate_device.cuh"
 #include "vate_internal.h"
 #include "vate_device_ops.cuh"
+#include "vate_ages.cuh"
 #include "vate_launch.cuh"
 
 #include <algorithm>
@@ -466,9 +468,26 @@ __global__ void __launch_bounds__(GATHER_THREADS) gather_scalar_kernel(Geom G, u
 }
 
 // --------------------------------------------------------------------------
-// Per-age counts: warp per host, each lane a private column of k counters in
-// shared memory ([warp][d][32]); d = distance of the VAT, kept when d < k.
+// Per-age counts (vate_age_counts).
 // --------------------------------------------------------------------------
+// For k <= 15: warp per host, the host's segments read as
+// 16-byte chunks (as in the gather) and counted in bit-sliced registers
+// (host_age_counts, vate_ages.cuh); lane d < k writes the count of age d.
+__global__ void __launch_bounds__(AGE_THREADS) age_counts_planes_kernel(Geom G, uint32_t bact0,
+                                                                        const uint32_t *__restrict__ aips, uint64_t n,
+                                                                        uint16_t *__restrict__ counts) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t h = warp0; h < n; h += nwarps) {
+        const uint32_t cd = host_age_counts(G, bact0, aips[h], lane);
+        if (lane < G.k) counts[h * G.k + lane] = (uint16_t)cd;
+    }
+}
+
+// Per-age counts for 15 < k <= 63: warp per host, one VAT per lane at a time,
+// each lane a private column of k counters in shared memory ([warp][d][32]);
+// d = distance of the VAT, kept when d < k.
 __global__ void __launch_bounds__(AGE_THREADS) age_counts_kernel(Geom G, uint32_t bact0,
                                                                  const uint32_t *__restrict__ aips, uint64_t n,
                                                                  uint16_t *__restrict__ counts) {
@@ -681,8 +700,10 @@ cudaError_t age_prepare(uint32_t k) {
 cudaError_t launch_age_counts(const Geom &G, uint32_t bact0, const uint32_t *aips, uint64_t n, uint16_t *counts,
                               cudaStream_t st, int sms) {
     if (n == 0) return cudaSuccess;
-    size_t smem = (size_t)(AGE_THREADS / 32) * G.k * 32 * sizeof(uint32_t);
     int grid = grid_for(n, AGE_THREADS / 32, sms * 32);
+    if (G.k <= 15u)          // every stored value (at most 2k) fits a 32-bit one-hot mask
+        return launch_pool(G, age_counts_planes_kernel, grid, AGE_THREADS, 0, st, G, bact0, aips, n, counts);
+    size_t smem = (size_t)(AGE_THREADS / 32) * G.k * 32 * sizeof(uint32_t);
     return launch_pool(G, age_counts_kernel, grid, AGE_THREADS, smem, st, G, bact0, aips, n, counts);
 }
 

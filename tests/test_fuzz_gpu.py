@@ -7,7 +7,8 @@ gaps (some longer than 2k, so that whole windows expire), then compares the
 pool, the census, the active counts, the flags and Eq. 11 with the oracle
 after every close, as the fixed parity cases do.  Distance recorders (VDRE)
 are drawn the same way: their pool equals the oracle's recorder pool, and
-their census, active counts and estimates those of the timestamps.  Monitor
+their census, active counts, estimates and per-age counts those of the
+timestamps.  Monitor
 groups of random size and make-up (one segment length per group), stepped
 plainly or by graph replay, equal a single handle per monitor bit for bit.
 Position shards at random 64-aligned cut points hold the undivided pool
@@ -110,6 +111,14 @@ def test_random_recorder_configuration_matches_oracle(V, case):
             assert torch.equal(e1, e2)
             _, oa, _ = o.estimate(hosts, kp)
             np.testing.assert_array_equal(a1.cpu().numpy().view(np.uint32), oa)
+        if at_bits == 0 and k <= 63:               # per-age counts: a recorder's value is its age
+            g1 = torch.empty(len(hosts) * k, dtype=torch.int16, device="cuda")
+            g2 = torch.empty_like(g1)
+            dr.age_counts(dh, g1)
+            at.age_counts(dh, g2)
+            assert torch.equal(g1, g2)
+            np.testing.assert_array_equal(g1.cpu().numpy().view(np.uint16).reshape(len(hosts), k).astype(np.uint32),
+                                          o.age_counts(hosts))
     dr.close()
     at.close()
 
