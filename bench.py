@@ -798,6 +798,14 @@ def run_learned_kernels(args):
           "fused_learned_estimate": timed(lambda: V.vate_estimate_learned(h.h, hosts, params, out, fl)),
           "plain_eq11_estimate": timed(lambda: h.estimate(hosts, k, out, fl))}
     h.close()
+    # per-age counts with a longer window, k = 30 (shared-memory counters instead of bit planes)
+    h30 = V.Vate(c, 30, g, 32, 0, 7)
+    for s in range(12):
+        h30.ingest(dt.slice_pairs(s), s)
+    h30.close_slice(11)
+    ages30 = torch.empty(n * 30, dtype=torch.int16, device="cuda")
+    ms["age_counts_k30"] = timed(lambda: V.vate_age_counts(h30.h, hosts, ages30))
+    h30.close()
     return {"workload": "learned estimator kernels at close: %d hosts, 2^24-AT pool, k = 10, g = 4096" % n,
             "unit": "ms per call", "ms": ms}
 

@@ -1,8 +1,8 @@
 // vate_ages.cuh -- per-age counts of one host's VATs (for d < k, the VATs
-// last set d slices ago), as bit-sliced counters in registers.  Used by the
-// learned estimator's features (vate_learned.cu) and by vate_age_counts
-// (vate_kernels.cu) for k <= 15, where every stored value fits a 32-bit
-// one-hot mask.
+// last set d slices ago).  For k <= 15, where every stored value fits a
+// 32-bit one-hot mask, as bit-sliced counters in registers (the learned
+// estimator's features in vate_learned.cu, and vate_age_counts); for larger k
+// as shared-memory counters (age_columns_vec, vate_age_counts).
 #pragma once
 #include "vate_device.cuh"
 
@@ -135,6 +135,49 @@ __device__ __forceinline__ uint32_t host_age_counts(const Geom &G, uint32_t bact
     }
     ap.fold(bact0, G.k, G.counter, lane, cd);
     return cd;
+}
+
+// Per-age counts for any k <= 63 into this lane's shared-memory column
+// (col[d * 32] for d < k): the host's segments read as 16-byte chunks as in
+// age_counts_vec, each word's distances found with SWAR (swar_bins: the
+// distance of Eq. 5 with ACT = BACT^0 in frame 0, 2k for an inactive AT; a
+// recorder's value is its distance, k when inactive), and every byte with
+// d < k added to its counter with a shared-memory atomic.
+template <int CPSL>
+__device__ __forceinline__ void age_columns_vec(const Geom &G, uint32_t bact0, uint64_t hk, uint32_t lane,
+                                                uint32_t *col) {
+    constexpr int CPS = 1 << CPSL;
+    const uint32_t nseg = G.g >> G.log2L;
+    const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
+    for (uint32_t r0 = 0; r0 < nseg; r0 += 32u) {
+        const uint32_t s = r0 + lane;
+        const uint32_t base = s < nseg ? (seg_base_k(G, hk, s) >> 4) : 0u;   // first chunk of the segment
+        const uint32_t segs = min(32u, nseg - r0);
+        uint4 w[CPS];
+        bool valid[CPS];
+#pragma unroll
+        for (int it = 0; it < CPS; it++) {
+            const uint32_t c = it * 32u + lane;
+            const uint32_t q = __shfl_sync(0xFFFFFFFFu, base, (c >> CPSL) & 31u) + (c & (CPS - 1u));
+            valid[it] = c < (segs << CPSL);
+            w[it] = make_uint4(0u, 0u, 0u, 0u);
+            if (valid[it]) w[it] = __ldg(pool16 + q);
+        }
+#pragma unroll
+        for (int it = 0; it < CPS; it++) {
+            if (!valid[it]) continue;
+            const uint32_t words[4] = {w[it].x, w[it].y, w[it].z, w[it].w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t bins = G.counter == 1u ? words[j] : swar_bins(words[j], bact0, G.twok);
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    const uint32_t d = (bins >> (8 * b)) & 0xFFu;
+                    if (d < G.k) atomicAdd(&col[d * 32u], 1u);
+                }
+            }
+        }
+    }
 }
 
 }  // namespace vate

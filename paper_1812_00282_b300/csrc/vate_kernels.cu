@@ -485,9 +485,10 @@ __global__ void __launch_bounds__(AGE_THREADS) age_counts_planes_kernel(Geom G, 
     }
 }
 
-// Per-age counts for 15 < k <= 63: warp per host, one VAT per lane at a time,
-// each lane a private column of k counters in shared memory ([warp][d][32]);
-// d = distance of the VAT, kept when d < k.
+// Per-age counts for 15 < k <= 63: warp per host, each lane a private column
+// of k counters in shared memory ([warp][d][32]); the host's segments read as
+// 16-byte chunks for L >= 16 (age_columns_vec, vate_ages.cuh), one VAT per lane
+// at a time for shorter segments; d = distance of the VAT, kept when d < k.
 __global__ void __launch_bounds__(AGE_THREADS) age_counts_kernel(Geom G, uint32_t bact0,
                                                                  const uint32_t *__restrict__ aips, uint64_t n,
                                                                  uint16_t *__restrict__ counts) {
@@ -500,17 +501,22 @@ __global__ void __launch_bounds__(AGE_THREADS) age_counts_kernel(Geom G, uint32_
         for (uint32_t d = 0; d < G.k; d++) col[d * 32u] = 0;
         __syncwarp();
         const uint64_t hk = host_key(G, aips[h]);
-        for (uint32_t i = lane; i < G.g; i += 32u) {
-            uint32_t pid = vat_pid_k(G, hk, i);
-            uint32_t v = __ldg(G.pool + pid);
-            if (G.counter == 1u) {
-                if (v < G.k) col[v * 32u] += 1u;
-                continue;
+        if (G.L == 16) age_columns_vec<0>(G, bact0, hk, lane, col);
+        else if (G.L == 32) age_columns_vec<1>(G, bact0, hk, lane, col);
+        else if (G.L == 64) age_columns_vec<2>(G, bact0, hk, lane, col);
+        else {                                        // L < 16: one byte per VAT
+            for (uint32_t i = lane; i < G.g; i += 32u) {
+                uint32_t pid = vat_pid_k(G, hk, i);
+                uint32_t v = __ldg(G.pool + pid);
+                if (G.counter == 1u) {
+                    if (v < G.k) col[v * 32u] += 1u;
+                    continue;
+                }
+                if (v == G.twok) continue;
+                uint32_t d = bact0 + G.twok - v;          // frame 0: ACT = BACT^0
+                if (d >= G.twok) d -= G.twok;
+                if (d < G.k) col[d * 32u] += 1u;
             }
-            if (v == G.twok) continue;
-            uint32_t d = bact0 + G.twok - v;          // frame 0: ACT = BACT^0
-            if (d >= G.twok) d -= G.twok;
-            if (d < G.k) col[d * 32u] += 1u;
         }
         __syncwarp();
         for (uint32_t d = lane; d < G.k; d += 32u) {
