@@ -361,7 +361,11 @@ def run_ours(args, rank, world, local):
                                     "(vate_probe_sector_read); no L2 figure in MEASURED_PEAKS.json",
                      "algorithmic_bytes": "aips x g VATs x AT bytes per launch (%d)" % vat_bytes,
                      "vs_hbm": {"peak": hbm, "frac": round(achieved / hbm, 3),
-                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}},
+                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                     "note": "the 64 MiB pool stays in L2 (persisting window) and the gather reads it 64 times "
+                             "over in random 32-byte sectors, so the bound is L2's random-sector rate, not HBM; "
+                             "traffic = DRAM bytes of one launch with caches flushed first (ncu, "
+                             "profiles/traffic.json), null once the kernel sources change"},
         "roofline_ingest": {"bound": "l2_random_store", "achieved": round(args.pkts / ingest_avg / 1e6, 2),
                             "peak": round(peaks["l2_byte_store_gps"], 2), "unit": "Gstore/s",
                             "frac": round(args.pkts / ingest_avg / 1e6 / peaks["l2_byte_store_gps"], 3),
