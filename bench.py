@@ -335,18 +335,30 @@ def run_ours(args, rank, world, local):
     ingest_avg = statistics.mean(ingest_ms)
     mp = measured_peaks()
     hbm = mp.get("hbm_gbs", 6400.0)
+    at_width = args.at_bits or (8 if args.k <= 63 else 16)                # bits per AT as stored
+    pool_mib = ((1 << C) // (32 // args.at_bits) * 4 if args.at_bits else (1 << C) * at_width // 8) / 2**20
+    if default_shape:
+        roofline_note = ("the 64 MiB pool stays in L2 (persisting window) and the gather reads it 64 times over in "
+                         "random 32-byte sectors, so the bound is L2's random-sector rate, not HBM; traffic = DRAM "
+                         "bytes of one launch with caches flushed first (ncu, profiles/traffic.json), null once the "
+                         "kernel sources change")
+    else:
+        roofline_note = ("the gather reads the %.0f MiB pool in random 32-byte sectors; peak = the L2 random-sector "
+                         "rate on a 64 MiB buffer; a pool larger than the L2's persisting part is read partly from "
+                         "HBM (vs_hbm); traffic is committed for the default shape only" % pool_mib)
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpkt/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(dev_ms_max / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u8", "data": "synthetic",
+        "dtype": "u%d" % at_width if not args.at_bits else "%d-bit fields in u32 words" % args.at_bits,
+        "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("k=10", "k=%d" % args.k), "aips": n_h, "pkts_per_slice": args.pkts,
                    "k": args.k, "kprime": args.k,
                    "log2_pool": C, "g": G, "seg_len": args.seg_len, "partition": args.partition,
-                   "at_bits": args.at_bits or 8,
+                   "at_bits": at_width,
                    "link_gbps_equivalent": round(args.pkts * MEAN_PKT_BYTES * 8 / 1e9, 2),
-                   "l2": "flushed before every timed step (256 MiB write, outside the step events); the 64 MiB "
-                         "AT pool is state kept from slice to slice and its kernels mark it L2-persisting"
+                   "l2": "flushed before every timed step (256 MiB write, outside the step events); the %.0f MiB "
+                         "AT pool is state kept from slice to slice and its kernels mark it L2-persisting" % pool_mib
                    if not args.no_flush else "not flushed", "parallelism": "replicas" if world > 1 else "single"},
         "close_p50_ms": round(float(np.percentile(close_ms, 50)), 4),
         "close_p99_ms": round(float(np.percentile(close_ms, 99)), 4),
@@ -362,10 +374,7 @@ def run_ours(args, rank, world, local):
                      "algorithmic_bytes": "aips x g VATs x AT bytes per launch (%d)" % vat_bytes,
                      "vs_hbm": {"peak": hbm, "frac": round(achieved / hbm, 3),
                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
-                     "note": "the 64 MiB pool stays in L2 (persisting window) and the gather reads it 64 times "
-                             "over in random 32-byte sectors, so the bound is L2's random-sector rate, not HBM; "
-                             "traffic = DRAM bytes of one launch with caches flushed first (ncu, "
-                             "profiles/traffic.json), null once the kernel sources change"},
+                     "note": roofline_note},
         "roofline_ingest": {"bound": "l2_random_store", "achieved": round(args.pkts / ingest_avg / 1e6, 2),
                             "peak": round(peaks["l2_byte_store_gps"], 2), "unit": "Gstore/s",
                             "frac": round(args.pkts / ingest_avg / 1e6 / peaks["l2_byte_store_gps"], 3),
