@@ -40,9 +40,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mpkt/s AT ingest; slice-close p99 ms @1M aips; learned vs plain mean rel. err"
-WORKLOAD = ("plain VATE at 40 Gb/s shape: 1,048,576 aips, 5,000,000 pkts per 1 s slice, k=10, "
-            "AT pool 2^26, virtual vector 4,096 (32-AT segments), Zipf(1.05), 0.1% super-spreaders")
+
 C, K_WIN, G = 26, 10, 4096
+
+
+def workload_name(args, n_h):
+    """The workload as run: the 40 Gb/s traffic shape with this run's hosts,
+    packets per slice, window and segment length."""
+    return ("plain VATE at 40 Gb/s shape: {:,} aips, {:,} pkts per 1 s slice, k={}, AT pool 2^26, virtual vector "
+            "4,096 ({}-AT segments), Zipf(1.05), 0.1% super-spreaders".format(n_h, args.pkts, args.k, args.seg_len))
 
 
 def parse():
@@ -352,7 +358,7 @@ def run_ours(args, rank, world, local):
         "ms_per_step": round(dev_ms_max / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u%d" % at_width if not args.at_bits else "%d-bit fields in u32 words" % args.at_bits,
         "data": "synthetic",
-        "config": {"workload": WORKLOAD.replace("k=10", "k=%d" % args.k), "aips": n_h, "pkts_per_slice": args.pkts,
+        "config": {"workload": workload_name(args, n_h), "aips": n_h, "pkts_per_slice": args.pkts,
                    "k": args.k, "kprime": args.k,
                    "log2_pool": C, "g": G, "seg_len": args.seg_len, "partition": args.partition,
                    "at_bits": at_width,
@@ -393,7 +399,7 @@ def run_ours(args, rank, world, local):
     if not args.no_learned and rank == 0:
         result["learned_vs_plain_mre"] = run_learned(V, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(tr, budget_s=20.0)
+        result["cpu_baseline"] = cpu_baseline(tr, args, budget_s=20.0)
     return result
 
 
@@ -521,7 +527,7 @@ def run_e2e(args, V, torch, tr, dt, rank, world):
 # ---------------------------------------------------------------------------
 # CPU oracle timings (the reference arm and the cpu_baseline field)
 # ---------------------------------------------------------------------------
-def oracle_step_sample(o, pairs, hosts_sample, pool_frac, n_hosts_total, pkts_total, advance=True):
+def oracle_step_sample(o, k, pairs, hosts_sample, pool_frac, n_hosts_total, pkts_total, advance=True):
     """Time one oracle step on a bounded sample and scale it to a full slice:
     the slide, SetAT over the sample pairs, the census over a fraction of the
     pool, and the gather + Eq. 11 of the sample hosts.  Returns
@@ -534,33 +540,35 @@ def oracle_step_sample(o, pairs, hosts_sample, pool_frac, n_hosts_total, pkts_to
     o.ingest(pairs)
     t2 = time.perf_counter()
     end = max(4096, int(o.P * pool_frac))
-    n0_part = o.pool_inactive_range(K_WIN, 0, end)
+    n0_part = o.pool_inactive_range(k, 0, end)
     t3 = time.perf_counter()
     n0 = int(n0_part * o.P / end)
     for h in hosts_sample:
-        oracle.estimate_from_counts(o.g, o.P, n0, o.active_vats(int(h), K_WIN))
+        oracle.estimate_from_counts(o.g, o.P, n0, o.active_vats(int(h), k))
     t4 = time.perf_counter()
     full = ((t1 - t0) + (t2 - t1) / max(1, len(pairs)) * pkts_total + (t3 - t2) * o.P / end
             + (t4 - t3) / max(1, len(hosts_sample)) * n_hosts_total)
     return pkts_total / full / 1e6, t4 - t0
 
 
-def cpu_baseline(tr, budget_s=20.0):
+def cpu_baseline(tr, args, budget_s=20.0):
     import oracle
     from traffic import mixed_hosts
-    o = oracle.Oracle(c=C, k=K_WIN, g=G, seg_len=32, partition=0, seed=0xC2)
+    o = oracle.Oracle(c=C, k=args.k, g=G, seg_len=args.seg_len, partition=args.partition, seed=0xC2)
+    n_h = min(args.aips, tr.spec.n_aips)
     hs = mixed_hosts(tr, 8192)
     vals, spent, s = [], 0.0, 0
     while spent < budget_s and s < 6:
         pairs = tr.slice_pairs(s)
-        v, dt = oracle_step_sample(o, pairs, hs, 1.0, tr.spec.n_aips, len(pairs), advance=s > 0)
+        v, dt = oracle_step_sample(o, args.k, pairs, hs, 1.0, n_h, len(pairs), advance=s > 0)
         vals.append(v)
         spent += dt
         s += 1
     return {"value": round(statistics.median(vals), 5), "unit": "Mpkt/s", "cores": 1, "kind": "oracle",
-            "sample": "%d slices of the workload: the slide, SetAT over all 5M pairs, the census of the whole 2^26 "
+            "sample": "%d slices of the workload: the slide, SetAT over all %d pairs, the census of the whole 2^26 "
                       "pool, and the gather + Eq. 11 of %d hosts (every super-spreader plus a seeded sample), "
-                      "scaled to 2^20 hosts; single-threaded plain C oracle, %.1f s of CPU work" % (s, len(hs), spent)}
+                      "scaled to %d hosts; single-threaded plain C oracle, %.1f s of CPU work"
+                      % (s, args.pkts, len(hs), n_h, spent)}
 
 
 def run_reference(args, rank, world):
@@ -571,13 +579,14 @@ def run_reference(args, rank, world):
     tr = Traffic(LINK40G, pkts_per_slice=args.pkts)
     total = args.steps + args.warmup
     per_step_budget = max(0.15, 120.0 / total)
-    o = oracle.Oracle(c=C, k=K_WIN, g=G, seg_len=32, partition=0, seed=0xC2)
+    o = oracle.Oracle(c=C, k=args.k, g=G, seg_len=args.seg_len, partition=args.partition, seed=0xC2)
+    n_h = min(args.aips, tr.spec.n_aips)
     base_pairs = tr.slice_pairs(0)
     # calibrate the sample so that one step costs about per_step_budget
     n_pk, n_hs, frac = 200_000, 128, 1.0 / 64
     hs_all = mixed_hosts(tr, 4096)
     t0 = time.perf_counter()
-    oracle_step_sample(o, base_pairs[:n_pk], hs_all[:n_hs], frac, tr.spec.n_aips, args.pkts, advance=True)
+    oracle_step_sample(o, args.k, base_pairs[:n_pk], hs_all[:n_hs], frac, n_h, args.pkts, advance=True)
     cal = time.perf_counter() - t0
     scale = max(0.05, min(4.0, per_step_budget / max(cal, 1e-3)))
     n_pk = max(10_000, min(args.pkts, int(n_pk * scale)))
@@ -587,7 +596,7 @@ def run_reference(args, rank, world):
     vals, spent = [], 0.0
     for s in range(total):
         off = (s * 104_729) % max(1, args.pkts - n_pk)
-        v, dt = oracle_step_sample(o, base_pairs[off:off + n_pk], hs, frac, tr.spec.n_aips, args.pkts, advance=True)
+        v, dt = oracle_step_sample(o, args.k, base_pairs[off:off + n_pk], hs, frac, n_h, args.pkts, advance=True)
         spent += dt
         if s >= args.warmup:
             vals.append(v)
@@ -595,14 +604,16 @@ def run_reference(args, rank, world):
     ms = args.pkts / value / 1e3
     return {"metric": METRIC, "impl": "reference", "value": round(value, 5), "unit": "Mpkt/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "aips": tr.spec.n_aips, "pkts_per_slice": args.pkts, "k": K_WIN,
-                       "kprime": K_WIN, "log2_pool": C, "g": G, "seg_len": 32, "partition": 0},
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": workload_name(args, n_h), "aips": n_h,
+                       "pkts_per_slice": args.pkts, "k": args.k, "kprime": args.k, "log2_pool": C, "g": G,
+                       "seg_len": args.seg_len, "partition": args.partition,
+                       "oracle_values": "one uint16 per AT position, Eq. 11 in float64"},
             "cpu_baseline": {"value": round(value, 5), "unit": "Mpkt/s", "cores": 1, "kind": "oracle",
                              "sample": "per step: the slide, SetAT over %d pairs, the census of %.4f of the 2^26 "
-                                       "pool, the gather + Eq. 11 of %d hosts, each scaled to a full slice (5M "
-                                       "pairs, whole pool, 2^20 hosts); %.1f s of CPU work in total"
-                                       % (n_pk, frac, n_hs, spent)},
+                                       "pool, the gather + Eq. 11 of %d hosts, each scaled to a full slice (%d "
+                                       "pairs, whole pool, %d hosts); %.1f s of CPU work in total"
+                                       % (n_pk, frac, n_hs, args.pkts, n_h, spent)},
             "e2e": {"value": round(value, 5), "unit": "Mpkt/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

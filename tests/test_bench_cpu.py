@@ -1,6 +1,7 @@
 """Host logic of bench.py that needs no GPU: the checksum that ties the
 committed ncu traffic figures to the kernel sources follows their code and
-ignores comments and layout."""
+ignores comments and layout; the workload name and the oracle legs follow
+the run's arguments."""
 import os
 import sys
 
@@ -27,3 +28,49 @@ def test_traffic_sha_is_the_committed_one_or_the_figure_is_null():
     assert len(sha) == 16 and all(c in "0123456789abcdef" for c in sha)
     t = bench.committed_traffic("gather_vec_kernel")
     assert t is None or t > 0
+
+
+def _args(*argv):
+    old = sys.argv
+    sys.argv = ["bench.py", *argv]
+    try:
+        return bench.parse()
+    finally:
+        sys.argv = old
+
+
+def test_workload_name_follows_the_arguments():
+    a = _args()
+    assert bench.workload_name(a, 1 << 20).startswith(
+        "plain VATE at 40 Gb/s shape: 1,048,576 aips, 5,000,000 pkts per 1 s slice, k=10, AT pool 2^26")
+    b = _args("--k", "300", "--seg-len", "16", "--pkts", "1000")
+    name = bench.workload_name(b, 4096)
+    assert "4,096 aips, 1,000 pkts" in name and "k=300" in name and "(16-AT segments)" in name
+
+
+def test_oracle_step_sample_uses_the_given_window():
+    # the oracle leg counts with the run's window: every census and gather
+    # call of one step gets k' = k, for the long window as for the short one
+    from oracle import Oracle
+    from traffic import SMALL, Traffic
+
+    class Recording(Oracle):
+        seen = []
+
+        def pool_inactive_range(self, kprime, start, end):
+            self.seen.append(kprime)
+            return super().pool_inactive_range(kprime, start, end)
+
+        def active_vats(self, aip, kprime):
+            self.seen.append(kprime)
+            return super().active_vats(aip, kprime)
+
+    tr = Traffic(SMALL, pkts_per_slice=2000)
+    pairs = tr.slice_pairs(0)
+    hosts = tr.aips[:8]
+    for k in (2, 300):
+        o = Recording(c=19, k=k, g=64, seg_len=8, partition=0, seed=3)   # every block of Eq. 9-10 non-empty
+        o.seen = []
+        v, dt = bench.oracle_step_sample(o, k, pairs, hosts, 1.0, 8, len(pairs), advance=True)
+        assert v > 0 and dt >= 0
+        assert o.seen == [k] * (1 + len(hosts))
