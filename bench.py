@@ -384,7 +384,11 @@ def run_ours(args, rank, world, local):
         "roofline_ingest": {"bound": "l2_random_store", "achieved": round(args.pkts / ingest_avg / 1e6, 2),
                             "peak": round(peaks["l2_byte_store_gps"], 2), "unit": "Gstore/s",
                             "frac": round(args.pkts / ingest_avg / 1e6 / peaks["l2_byte_store_gps"], 3),
-                            "note": "one 1-byte SetAT store per pair; time includes the slide's PreserveAT"},
+                            "note": ("one %s per pair against random 1-byte stores into a 64 MiB buffer; time "
+                                     "includes the slide's PreserveAT"
+                                     % ("1-byte SetAT store" if at_width == 8 and not args.at_bits else
+                                        "2-byte SetAT store" if not args.at_bits else
+                                        "SetAT of a %d-bit field (atomicAnd + atomicOr)" % args.at_bits))},
         "gpu_launches": int(launches),
         "clocks": clock_info,
         "wall_bracket_s": round(t1 - t0, 4),
