@@ -435,7 +435,8 @@ cudaError_t launch_group_gather(vate_group *g, const uint32_t *hosts, const uint
                                 const uint32_t *kprime, float *out, uint8_t *flags, cudaStream_t st) {
     auto kern = group_gather_kernel<CPSL, RB>;
     size_t smem = gather_smem(g->M);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+        return e;
     return vate::launch_pool(g->arena_geom, kern, g->sms * g->tuning.gather_blocks_per_sm, G_THREADS, smem, st,
                              (const Geom *)g->d_descs, g->M, g->d_state, hosts, hoff, hcap, kprime,
                              (const uint64_t *)g->d_hist, g->maxbins, out, flags, g->tuning.gather_hosts_per_grab, 1u,
@@ -453,7 +454,8 @@ cudaError_t enqueue_gather(vate_group *g, const uint32_t *hosts, const uint64_t 
 cudaError_t enqueue_ingest(vate_group *g, const vate_pair *pairs, const uint64_t *poff, uint64_t pcap,
                            cudaStream_t st) {
     size_t smem = ingest_smem(g->M);
-    cudaFuncSetAttribute(group_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaError_t e = cudaFuncSetAttribute(group_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+        return e;
     return vate::launch_pool(g->arena_geom, group_ingest_kernel, g->sms * g->tuning.ingest_blocks_per_sm, G_THREADS,
                              smem, st, (const Geom *)g->d_descs, g->M, g->d_state,
                              reinterpret_cast<const uint32_t *>(pairs), poff, pcap);
@@ -461,7 +463,8 @@ cudaError_t enqueue_ingest(vate_group *g, const vate_pair *pairs, const uint64_t
 
 cudaError_t enqueue_census(vate_group *g, cudaStream_t st) {
     size_t smem = census_smem(g->maxbins);
-    cudaFuncSetAttribute(group_census_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaError_t e = cudaFuncSetAttribute(group_census_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+        return e;
     // as many blocks per SM as their columns fit in about 200 KiB, up to four
     const int per_sm = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)(200u << 10) / smem));
     return vate::launch_pool(g->arena_geom, group_census_kernel, g->sms * per_sm, G_THREADS, smem, st,

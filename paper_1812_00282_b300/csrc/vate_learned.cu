@@ -403,7 +403,8 @@ int vate_mlp_forward(const float *d_params, uint32_t n_in, const float *d_x, uin
     if (n && (!d_x || !d_y)) return set_error(VATE_EINVAL, "d_x and d_y must not be NULL");
     if (n == 0) return VATE_OK;
     const size_t smem = sizeof(float) * (model_smem_floats(n_in) + (size_t)WARPS * 32 * XS);
-    cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+        return set_error(VATE_ECUDA, cudaGetErrorString(e));
     int grid = (int)std::min<uint64_t>((n + WARPS * 32 - 1) / (WARPS * 32), (uint64_t)sms_now() * 8);
     mlp_forward_kernel<<<grid, WARPS * 32, smem, (cudaStream_t)stream>>>(d_params, n_in, d_x, n, d_y);
     count_launch();
@@ -424,7 +425,8 @@ int vate_mlp_train_step(float *d_params, float *d_m, float *d_v, uint32_t n_in, 
     const uint32_t tiles = (uint32_t)((n + TR_ROWS - 1) / TR_ROWS);
     const uint32_t np = (uint32_t)n_params(n_in);
     const size_t smem = train_smem(n_in);
-    cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+        return set_error(VATE_ECUDA, cudaGetErrorString(e));
     float *partial = d_scratch, *loss_partial = d_scratch + (uint64_t)tiles * np;
     mlp_grad_kernel<<<tiles, TR_THREADS, smem, st>>>(d_params, n_in, d_x, d_target, d_weight, loss, n, partial,
                                                      loss_partial);
@@ -445,7 +447,9 @@ int vate_estimate_learned(vate_handle *h, const uint32_t *d_aips, uint64_t n, co
     if (n && (!d_aips || !d_out)) return set_error(VATE_EINVAL, "d_aips and d_out must not be NULL");
     if (n == 0) return VATE_OK;
     const size_t smem = sizeof(float) * (model_smem_floats(2 * v.G.k + 2) + (size_t)WARPS * 32 * XS);
-    cudaFuncSetAttribute(learned_estimate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaError_t e = cudaFuncSetAttribute(learned_estimate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem))
+        return set_error(VATE_ECUDA, cudaGetErrorString(e));
     int grid = (int)std::min<uint64_t>((n + WARPS * 32 - 1) / (WARPS * 32), (uint64_t)v.sms * 8);
     cudaError_t e = launch_pool(v.G, learned_estimate_kernel, grid, WARPS * 32, smem, (cudaStream_t)stream, v.G,
                                 v.bact0, v.hist, d_aips, n, d_params, d_out, d_flags);
