@@ -321,6 +321,46 @@ def test_full_size_40g_shape_sampled(V):
                pool_every_slice=True)
 
 
+@pytest.mark.slow
+def test_full_size_every_host_in_one_launch_sampled(V):
+    # The benchmark's launch configuration: all 2^20 hosts of the 40 Gb/s
+    # workload estimated by one vate_estimate call (so the gather runs on its
+    # full grid), in host-table order, with flags, after 5M-pair slices into
+    # the 2^26-AT pool.  The oracle computes a seeded sample of the outputs
+    # plus every super-spreader one by one; 2k + 3 slices take every block's
+    # ACT through a full cycle.
+    tr = Traffic(LINK40G)
+    k, n = 10, tr.spec.n_aips
+    d = V.Vate(26, k, 4096, 32, 0, 0xC2)
+    o = Oracle(c=26, k=k, g=4096, seg_len=32, partition=0, seed=0xC2)
+    dh = dev_u32(tr.aips)
+    rng = np.random.default_rng(11)
+    idx = np.union1d(rng.choice(n, 4096, replace=False), tr.super_hosts)
+    sample = tr.aips[idx]
+    est = torch.empty(n, dtype=torch.float32, device="cuda")
+    fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+    act = torch.empty(n, dtype=torch.int32, device="cuda")
+    for s in range(2 * k + 3):
+        if s:
+            o.advance()
+        p = tr.slice_pairs(s)
+        d.ingest(dev_pairs(p), s)
+        o.ingest(p)
+        d.close_slice(s)
+        if s not in (0, k + 1, 2 * k + 2):
+            continue
+        for kp in (1, k // 2, k):
+            d.estimate(dh, kp, est, fl)
+            d.active_counts(dh, kp, act)
+            oe, oa, of = o.estimate(sample, kp)
+            np.testing.assert_array_equal(act.cpu().numpy().view(np.uint32)[idx], oa, err_msg="A, k'=%d" % kp)
+            np.testing.assert_array_equal(fl.cpu().numpy()[idx], of, err_msg="flags, k'=%d" % kp)
+            de = est.cpu().numpy()[idx].astype(np.float64)
+            err = np.abs(de - oe) / np.maximum(np.abs(oe), 1.0)
+            assert err.max() <= RTOL, "k'=%d max rel err %.3g" % (kp, err.max())
+    d.close()
+
+
 @pytest.mark.parametrize("L", [1, 32])
 def test_distance_recorders_match_oracle_and_timestamps(V, L):
     # VDRE (distance recorders aged every slide, Sec. 1 / Sec. 5) on the same
