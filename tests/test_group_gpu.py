@@ -7,7 +7,8 @@ byte, the census, and the estimates and flags bit for bit (same device
 arithmetic).  One monitor is also checked against the CPU oracle.  The CUDA
 graph form must equal the plain form, the autotuner must leave state and
 outputs unchanged, and malformed device-side offsets and k' must be clamped
-and reported, never read out of bounds.
+and reported, never read out of bounds.  The 64-monitor configuration is run
+at full size as the benchmark drives it.
 """
 import numpy as np
 import pytest
@@ -196,3 +197,91 @@ def test_group_bad_device_inputs_are_clamped_and_reported(V):
     torch.cuda.synchronize()
     assert torch.isfinite(out).all()
     grp.close()
+
+
+@pytest.mark.slow
+def test_group_full_size_64_monitors(V):
+    # The 64-monitor configuration at full size, driven as the benchmark
+    # drives it (pools 2^20-2^25, k in {5, 10, 30, 60}, g 512-8192, 44 M pairs
+    # and 1.86 M hosts per slice, the tuned tiling, one CUDA graph per slice):
+    # every monitor equals a single handle bit for bit (pool, census, every
+    # host's estimate and flag) over three slices, and the two busiest equal
+    # the oracle (pool, census, a seeded sample of estimates and counts).
+    import bench
+    from traffic import DeviceTraffic, TrafficSpec
+    mons = bench.monitors64_config()
+    dts, params, singles = [], [], []
+    for m in mons:
+        spec = TrafficSpec(n_aips=m["hosts"], pkts_per_slice=m["rate"], zipf_s=1.1, seed=m["seed"])
+        dts.append(DeviceTraffic(Traffic(spec)))
+        params.append(V.make_params(m["c"], m["k"], m["g"], 32, 0, m["seed"]))
+        singles.append(V.Vate(m["c"], m["k"], m["g"], 32, 0, m["seed"]))
+    po = np.zeros(65, np.int64)
+    po[1:] = np.cumsum([m["rate"] for m in mons])
+    ho = np.zeros(65, np.int64)
+    ho[1:] = np.cumsum([m["hosts"] for m in mons])
+    pairs = torch.empty(int(po[-1]), 2, dtype=torch.int32, device="cuda")
+    hosts = torch.cat([d.hosts() for d in dts])
+    PO, HO = torch.from_numpy(po).cuda(), torch.from_numpy(ho).cuda()
+    KP = torch.tensor([m["k"] for m in mons], dtype=torch.int32, device="cuda")
+    out = torch.empty(hosts.numel(), dtype=torch.float32, device="cuda")
+    flags = torch.empty(hosts.numel(), dtype=torch.uint8, device="cuda")
+
+    def fill(s):
+        for i, d in enumerate(dts):
+            pairs[int(po[i]):int(po[i + 1])].copy_(d.slice_pairs(s))
+
+    fill(0)
+    tuner = V.VateGroup(params)
+    tuner.step(pairs, PO, hosts, HO, KP, out, flags)
+    tun = tuner.autotune(pairs, PO, hosts, HO, KP, out, flags)
+    tuner.close()
+    grp = V.VateGroup(params)
+    V.vate_group_set_tuning(grp.g, tun)
+    busiest = [int(i) for i in np.argsort([m["rate"] for m in mons])[-2:]]
+    oras = {i: Oracle(c=mons[i]["c"], k=mons[i]["k"], g=mons[i]["g"], seg_len=32, partition=0,
+                      seed=mons[i]["seed"]) for i in busiest}
+    rng = np.random.default_rng(17)
+    for s in range(3):
+        fill(s)
+        grp.step(pairs, PO, hosts, HO, KP, out, flags, graph=True)
+        for i, (m, d) in enumerate(zip(mons, singles)):
+            p = pairs[int(po[i]):int(po[i + 1])]
+            h = hosts[int(ho[i]):int(ho[i + 1])]
+            d.ingest(p, s)
+            d.close_slice(s)
+            pa = torch.empty(1 << m["c"], dtype=torch.uint8, device="cuda")
+            pb = torch.empty_like(pa)
+            grp.copy_pool(i, pa)
+            d.copy_pool(pb)
+            assert torch.equal(pa, pb), "slice %d monitor %d: pool differs from a single handle" % (s, i)
+            ha = torch.empty(2 * m["k"] + 1, dtype=torch.int64, device="cuda")
+            hb = torch.empty_like(ha)
+            grp.census(i, ha)
+            d.census(hb)
+            assert torch.equal(ha, hb), "slice %d monitor %d: census differs" % (s, i)
+            e = torch.empty(h.numel(), dtype=torch.float32, device="cuda")
+            f = torch.empty(h.numel(), dtype=torch.uint8, device="cuda")
+            d.estimate(h, m["k"], e, f)
+            assert torch.equal(out[int(ho[i]):int(ho[i + 1])], e), "slice %d monitor %d: estimates" % (s, i)
+            assert torch.equal(flags[int(ho[i]):int(ho[i + 1])], f)
+            if i in oras:
+                o = oras[i]
+                if s:
+                    o.advance()
+                o.ingest(p.cpu().numpy().view(np.uint32))
+                assert np.array_equal(pa.cpu().numpy(), o.pool())
+                np.testing.assert_array_equal(hb.cpu().numpy().astype(np.uint64), o.census())
+                idx = rng.choice(h.numel(), 512, replace=False)
+                hs = h.cpu().numpy().view(np.uint32)[idx]
+                oe, oa, of = o.estimate(hs, m["k"])
+                act = torch.empty(h.numel(), dtype=torch.int32, device="cuda")
+                d.active_counts(h, m["k"], act)
+                np.testing.assert_array_equal(act.cpu().numpy().view(np.uint32)[idx], oa)
+                np.testing.assert_array_equal(f.cpu().numpy()[idx], of)
+                de = e.cpu().numpy()[idx].astype(np.float64)
+                assert (np.abs(de - oe) / np.maximum(np.abs(oe), 1)).max() <= RTOL
+    assert grp.status() == 0
+    grp.close()
+    for d in singles:
+        d.close()
