@@ -111,6 +111,20 @@ def test_small_traffic_parity(V, L, partition):
     run_stream(V, (16, k, 1024, L, partition, 0xC1), slices, tr.aips, kps=(1, 3, k))
 
 
+@pytest.mark.parametrize("L", [1, 32])
+def test_small_workload_exact_shape(V, L):
+    # The small workload exactly: 4,096 hosts, 1,000,000 pairs over 20 slices
+    # of 50,000, k = 5, a 2^20-AT pool, g = 1,024.  The pool and census at
+    # every close, and every host's estimate, active count and per-age counts
+    # at k' = 1, 3, 5 at every fourth close and the last, equal the oracle.
+    tr = Traffic(SMALL)
+    k = 5
+    slices = [tr.slice_pairs(s) for s in range(20)]
+    assert sum(len(p) for p in slices) == 1_000_000
+    run_stream(V, (20, k, 1024, L, 0, 0xC1), slices, tr.aips, kps=(1, 3, k), check_every=4,
+               pool_every_slice=True)
+
+
 @pytest.mark.parametrize("L", [2, 4, 8, 16, 64])
 def test_other_segment_lengths(V, L):
     tr = Traffic(SMALL, pkts_per_slice=15_000)
