@@ -133,3 +133,21 @@ def test_learned_pipeline_small(V):
         assert np.isfinite(r["mre"][pop]["learned"]) and np.isfinite(r["mre"][pop]["plain"])
         assert r["mre"][pop]["hosts"] > 1000
     assert r["params"].numel() == V.vate_mlp_param_count(12)
+
+
+@pytest.mark.slow
+def test_learned_full_configuration_no_worse_than_eq11(V):
+    # The learned-estimator workload at full size: the 40 Gb/s traffic on a
+    # 2^24-AT pool, k = 10, g = 4096, trained on 200 generated slices with
+    # exact labels and evaluated on 100 held-out slices of another stream.
+    # At equal AT memory its mean relative error must not exceed the closed
+    # form's (Eq. 11), over all hosts active in the window and over the hosts
+    # with at least 100 peers.
+    from paper_1812_00282_b300 import learned
+    r = learned.run(V)
+    assert r["train_slices"] == 200 and r["eval_slices"] == 100 and r["log2_pool"] == 24
+    assert r["accepted"]
+    for pop in ("n>=1", "n>=100"):
+        m = r["mre"][pop]
+        assert m["hosts"] > 1000 and np.isfinite(m["learned"])
+        assert m["learned"] <= m["plain"], (pop, m)
