@@ -215,3 +215,23 @@ def test_wide_and_packed_monitors_are_served_exactly(V):
         for s in range(len(slices)):
             np.testing.assert_array_equal(got[s][0], ref[s])
     V.vate_server_destroy(srv)
+
+
+@pytest.mark.slow
+def test_serving_workload_full_size(V):
+    # The serving workload as configured: candidate monitors admitted by an
+    # 8 GB AT-memory budget up to 16, Poisson batches of 1k-1M pairs arriving
+    # in real time (mean 8 Mpkt/s, bursts to 30 Mpkt/s), 1 s slices, k = 10.
+    # Every request completes without error (vate_server_wait raises
+    # otherwise), every batch and close is accounted for, the admitted pools
+    # fit the budget, and several requests were in flight at once.
+    from paper_1812_00282_b300 import serving
+    r = serving.run(V, duration=3.0, paced=True)
+    st = r["stats"]
+    assert 1 <= r["monitors_admitted"] <= 16
+    assert sum(1 << c for c in r["log2_pools"]) <= 8 << 30
+    assert st["memory_in_use"] <= 8 << 30
+    assert st["pairs_done"] == r["pairs"] and st["closes_done"] == 3 * r["monitors_admitted"]
+    assert st["max_in_flight"] >= 2
+    assert 0 < st["close_p50_ms"] <= st["close_p99_ms"] < 1000.0
+    assert 0 < r["offered_mpkts"] < 30.0
