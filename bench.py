@@ -277,7 +277,8 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
 
     peaks = probe_peaks(V, torch, 1 << C)
-    mon = V.Vate(C, args.k, G, args.seg_len, args.partition, seed=0xC2 + rank, at_bits=args.at_bits)
+    mon = V.Vate(C, args.k, G, args.seg_len, args.partition, seed=0xC2 + rank, at_bits=args.at_bits,
+                 options=V.VATE_OPT_PERSIST_L2)
 
     def step(s):
         mon.ingest(pairs[s], s)
@@ -455,7 +456,8 @@ def run_e2e(args, V, torch, tr, dt, rank, world):
     hosts = dt.hosts()[: args.aips].cpu().pin_memory()
     out = torch.empty(hosts.numel(), dtype=torch.float32).pin_memory()
     fl = torch.empty(hosts.numel(), dtype=torch.uint8).pin_memory()
-    mon = V.Vate(C, args.k, G, args.seg_len, args.partition, seed=0xE2E + rank, at_bits=args.at_bits)
+    mon = V.Vate(C, args.k, G, args.seg_len, args.partition, seed=0xE2E + rank, at_bits=args.at_bits,
+                 options=V.VATE_OPT_PERSIST_L2)
     st = torch.cuda.current_stream()
 
     def step(s):
@@ -652,7 +654,7 @@ def run_monitors64(args):
     for m in mons:
         spec = TrafficSpec(n_aips=m["hosts"], pkts_per_slice=m["rate"], zipf_s=1.1, seed=m["seed"])
         dts.append(DeviceTraffic(Traffic(spec)))
-        params.append(V.make_params(m["c"], m["k"], m["g"], 32, 0, m["seed"]))
+        params.append(V.make_params(m["c"], m["k"], m["g"], 32, 0, m["seed"], options=V.VATE_OPT_PERSIST_L2))
     grp = V.VateGroup(params)
     po = np.zeros(65, np.int64)
     po[1:] = np.cumsum([m["rate"] for m in mons])

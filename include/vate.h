@@ -94,7 +94,18 @@ typedef struct {
  *              pair and reads one field per VAT: less memory, more time.
  *              Packed pools serve the handle API; shards, groups, per-age
  *              counts and the learned estimator need b = 8 or 16.
- *   reserved   0.
+ *   options    bit set, 0 by default:
+ *              VATE_OPT_PERSIST_L2  keep the pool resident in L2 across
+ *                slices: vate_create raises the PROCESS-WIDE persisting-L2
+ *                limit (cudaLimitPersistingL2CacheSize) to the device maximum
+ *                if it is lower, and vate_destroy resets the persisting lines
+ *                (cudaCtxResetPersistingL2Cache).  Both change L2 behaviour
+ *                for every kernel of the calling process, so the library
+ *                does neither unless asked.  Without the bit no process-wide
+ *                setting is touched; the pool's kernels still carry a
+ *                persisting access-policy window over it, which takes effect
+ *                only if the process has set a persisting limit itself.
+ *              Other bits must be 0.
  *   seed       keys the hash functions H and BH.
  * The hash functions (Sec. 4.1 leaves them open):
  *   mix(x)    = SplitMix64 output function (Steele, Lea & Flood 2014)
@@ -112,12 +123,14 @@ typedef struct {
     uint32_t partition;
     uint32_t counter;    /* VATE_COUNTER_AT (0) or VATE_COUNTER_DR (1) */
     uint32_t at_bits;    /* 0: byte / 16-bit ATs by k; else packed b-bit fields */
-    uint32_t reserved;   /* 0 */
+    uint32_t options;    /* VATE_OPT_* bits, 0 by default */
     uint64_t seed;
 } vate_params;
 
 #define VATE_COUNTER_AT 0u
 #define VATE_COUNTER_DR 1u
+
+#define VATE_OPT_PERSIST_L2 1u  /* vate_params.options: see above */
 
 /* Read-only view of a handle's geometry and slice state. */
 typedef struct {

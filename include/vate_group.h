@@ -93,7 +93,11 @@ int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_
  * the gather of that slice on the given inputs under candidate tilings, times
  * each with CUDA events on `stream` (synchronising it), keeps the fastest per
  * kernel, and writes the choice to *chosen (may be NULL).  The monitors' state
- * and the outputs end exactly as the last step left them. */
+ * and the outputs end exactly as the last step left them.
+ * The inputs MUST be exactly those of the last vate_group_step (same pairs,
+ * offsets, hosts, host offsets and k'): other pairs would be stamped into the
+ * current slice, which is not checked.  On an error the tiling in force on
+ * entry is restored. */
 int vate_group_autotune(vate_group *g, const vate_pair *d_pairs, const uint64_t *d_pair_offsets,
                         uint64_t pair_capacity, const uint32_t *d_hosts, const uint64_t *d_host_offsets,
                         uint64_t host_capacity, const uint32_t *d_kprime, float *d_out, uint8_t *d_flags,

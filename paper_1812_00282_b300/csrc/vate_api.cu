@@ -68,7 +68,8 @@ int make_geom(const vate_params *p, Geom *G) {
     G->partition = p->partition;
     G->counter = p->counter;
     G->atw = p->k <= 63 ? 1u : 2u;             // byte ATs up to k = 63, 16-bit ones beyond
-    if (p->reserved != 0) return fail(VATE_EINVAL, "params.reserved must be 0");
+    if (p->options & ~VATE_OPT_PERSIST_L2)
+        return fail(VATE_EINVAL, "params.options has unknown bits (0x%x)", p->options & ~VATE_OPT_PERSIST_L2);
     if (p->at_bits != 0) {
         uint32_t bmin = 1;
         while ((1u << bmin) < 2 * p->k + 1) bmin++;          // ceil(log2(2k + 1))
@@ -116,6 +117,7 @@ int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
 struct vate_handle {
     vate_params prm;
     Geom G;
+    bool persist_l2 = false;         // this handle raised the process's persisting-L2 limit
     int device = 0;
     int sms = 148;
     int64_t slice = -1;
@@ -345,15 +347,20 @@ static int create_range(const vate_params *params, uint64_t lo, uint64_t hi, voi
         delete h;
         return cuda_fail(e, "kernel attributes");
     }
-    // Keep the pool resident in L2: its kernels launch with a persisting
-    // access-policy window over it (hit ratio = persisting capacity / pool).
+    // The pool's kernels launch with a persisting access-policy window over
+    // it (hit ratio = persisting capacity / pool).  Only with
+    // VATE_OPT_PERSIST_L2 does the handle raise the process-wide persisting
+    // limit that gives the window its effect.
     {
         int persist_max = 0, window_max = 0;
         cudaDeviceGetAttribute(&persist_max, cudaDevAttrMaxPersistingL2CacheSize, h->device);
         cudaDeviceGetAttribute(&window_max, cudaDevAttrMaxAccessPolicyWindowSize, h->device);
         size_t cur = 0;
         if (persist_max > 0 && window_max > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
-            if (cur < (size_t)persist_max) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist_max);
+            if ((params->options & VATE_OPT_PERSIST_L2) && cur < (size_t)persist_max) {
+                cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist_max);
+                h->persist_l2 = true;
+            }
             cudaGetLastError();
             h->G.l2_window_bytes = held_bytes < (uint64_t)window_max ? held_bytes : (uint64_t)window_max;
             double ratio = (double)persist_max / (double)h->G.l2_window_bytes;
@@ -403,7 +410,7 @@ int vate_destroy(vate_handle *h) {
     if (h->pairs_stream) cudaStreamSynchronize(h->pairs_stream);
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
     if (h->d2h_stream) cudaStreamSynchronize(h->d2h_stream);
-    if (h->G.l2_window_bytes) {
+    if (h->G.l2_window_bytes && (h->prm.options & VATE_OPT_PERSIST_L2)) {
         // lines of the freed pool must not keep the persisting carve-out
         cudaDeviceSynchronize();
         cudaCtxResetPersistingL2Cache();

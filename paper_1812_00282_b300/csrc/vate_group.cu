@@ -387,6 +387,7 @@ struct vate_group {
     int sms = 148;
     uint32_t steps = 0;              // steps queued so far (host count)
     vate_group_tuning tuning;
+    bool persist_l2 = false;         // VATE_OPT_PERSIST_L2 in some monitor's options
     // CUDA graph of one step
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -508,6 +509,8 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
     if (!g) return vate::set_error(VATE_ENOMEM, "host allocation failed");
     g->M = n_monitors;
     g->prm.assign(params, params + n_monitors);
+    for (uint32_t m = 0; m < n_monitors; m++)
+        if (params[m].options & VATE_OPT_PERSIST_L2) g->persist_l2 = true;
     g->geoms.resize(n_monitors);
     uint64_t off = 0;
     for (uint32_t m = 0; m < n_monitors; m++) {
@@ -567,7 +570,9 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
         cudaDeviceGetAttribute(&window_max, cudaDevAttrMaxAccessPolicyWindowSize, dev);
         size_t cur = 0;
         if (persist_max > 0 && window_max > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
-            if (cur < (size_t)persist_max) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist_max);
+            // the process-wide limit only on request (VATE_OPT_PERSIST_L2 in any monitor's options)
+            if (g->persist_l2 && cur < (size_t)persist_max)
+                cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist_max);
             cudaGetLastError();
             g->arena_geom.l2_window_bytes = std::min<uint64_t>(g->arena_bytes, (uint64_t)window_max);
             double ratio = (double)persist_max / (double)g->arena_geom.l2_window_bytes;
@@ -601,7 +606,7 @@ int vate_group_destroy(vate_group *g) {
     if (!g) return VATE_OK;
     cudaDeviceSynchronize();
     if (g->exec) cudaGraphExecDestroy(g->exec);
-    if (g->arena_geom.l2_window_bytes) cudaCtxResetPersistingL2Cache();
+    if (g->arena_geom.l2_window_bytes && g->persist_l2) cudaCtxResetPersistingL2Cache();
     cudaFree(g->arena);
     cudaFree(g->d_descs);
     cudaFree(g->d_state);
@@ -691,9 +696,21 @@ int vate_group_autotune(vate_group *g, const vate_pair *d_pairs, const uint64_t 
         return rc;
     if (g->steps == 0) return vate::set_error(VATE_ESLICE, "autotune needs one step of the slice to repeat");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return vate::set_error(VATE_ECUDA, "autotune: cudaEventCreate failed");
+    }
+    const vate_group_tuning entry = g->tuning;
+    // every return after this point destroys the events; an error restores the
+    // tiling the group had on entry
+    auto fail = [&](int rc) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        g->tuning = entry;
+        rebuild_tiles(g, st);
+        return rc;
+    };
     const uint32_t hist_words = g->M * g->maxbins;
     auto reset = [&](bool hist) {
         return vate::launch_pool(g->arena_geom, group_reset_kernel, 8, G_THREADS, 0, st, g->d_state, g->d_hist,
@@ -713,7 +730,8 @@ int vate_group_autotune(vate_group *g, const vate_pair *d_pairs, const uint64_t 
         return best;
     };
     vate_group_tuning best = g->tuning;
-    // ingest (repeating the slice's SetATs rewrites the same values)
+    // ingest: repeating the last step's SetATs rewrites the values they wrote
+    // (d_pairs and d_pair_offsets must be that step's inputs, see the header)
     float bt = 1e30f;
     for (uint32_t b : {4u, 8u, 16u, 24u}) {
         g->tuning.ingest_blocks_per_sm = b;
@@ -725,12 +743,12 @@ int vate_group_autotune(vate_group *g, const vate_pair *d_pairs, const uint64_t 
     bt = 1e30f;
     for (uint32_t c : {1024u, 4096u, 16384u, 65536u}) {
         g->tuning.census_tile_chunks = c;
-        if (int rc = rebuild_tiles(g, st)) return rc;
+        if (int rc = rebuild_tiles(g, st)) return fail(rc);
         float ms = timed([&] { reset(true); enqueue_census(g, st); });
         if (ms < bt) { bt = ms; best.census_tile_chunks = c; }
     }
     g->tuning.census_tile_chunks = best.census_tile_chunks;
-    if (int rc = rebuild_tiles(g, st)) return rc;
+    if (int rc = rebuild_tiles(g, st)) return fail(rc);
     reset(true);
     enqueue_census(g, st);                       // leave the slice's census in place
     // gather (queue counter cleared before each run)
@@ -750,9 +768,9 @@ int vate_group_autotune(vate_group *g, const vate_pair *d_pairs, const uint64_t 
     reset(false);
     cudaError_t e = enqueue_gather(g, d_hosts, d_host_offsets, host_capacity, d_kprime, d_out, d_flags, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(vate::set_error(VATE_ECUDA, cudaGetErrorString(e)));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (e != cudaSuccess) return vate::set_error(VATE_ECUDA, cudaGetErrorString(e));
     if (chosen) *chosen = best;
     return VATE_OK;
 }

@@ -50,9 +50,17 @@ thread_local char g_msg[256];
 
 // Once per device: the device address of the scratch array, the SM count,
 // and the census kernel's shared-memory attribute.
-int setup_device(void **addr_out, int *sms_out) {
+int setup_device(void **addr_out, int *sms_out, const char **why) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return VATE_ECUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+        *why = "no-alloc census: no current CUDA device (cudaGetDevice failed)";
+        return VATE_ECUDA;
+    }
+    if (dev >= MAX_DEVICES) {
+        *why = "no-alloc census: device index beyond the 64 devices this entry point keeps addresses for";
+        return VATE_EINVAL;
+    }
+    *why = "no-alloc census: device set-up (cudaGetSymbolAddress, SM count or kernel attribute) failed";
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_addr[dev]) {
         void *ptr = nullptr;
@@ -86,14 +94,16 @@ extern "C" int vate_census_noalloc(const vate_params *params, const uint8_t *d_p
     if ((reinterpret_cast<uintptr_t>(d_pool) & 15u) != 0)
         return vate::set_error(VATE_EINVAL, "d_pool must be 16-byte aligned");
     if (bact0 >= G.twok) return vate::set_error(VATE_EINVAL, "bact0 must be below 2k");
-    int sms = 0;
-    void *scratch = nullptr;
-    if (setup_device(&scratch, &sms) != VATE_OK)
-        return vate::set_error(VATE_ECUDA, "no-alloc census: device set-up (cudaGetSymbolAddress) failed");
     if (G.twok + 1 > (uint32_t)NOALLOC_MAX_BINS) {
         snprintf(g_msg, sizeof g_msg, "no-alloc census keeps at most %d bins (k <= 63)", NOALLOC_MAX_BINS);
         return vate::set_error(VATE_EINVAL, g_msg);
     }
+    // every argument is checked before the device is touched
+    int sms = 0;
+    void *scratch = nullptr;
+    const char *why = "";
+    rc = setup_device(&scratch, &sms, &why);
+    if (rc != VATE_OK) return vate::set_error(rc, why);
     G.pool = const_cast<uint8_t *>(d_pool);
     G.packed = 0;                                // the caller's pool: one byte per AT in the paper's form
     cudaStream_t st = (cudaStream_t)stream;

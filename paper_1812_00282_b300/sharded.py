@@ -77,23 +77,52 @@ class ShardedVate:
         if t.dtype == torch.int32:
             assert int(t.min()) >= 0, "active counts overflowed"
 
+    @staticmethod
+    def _torch_stream(stream, dev):
+        """The torch stream object for `stream` (None: torch's current stream;
+        an int: a raw cudaStream_t)."""
+        import torch
+        if stream is None:
+            return torch.cuda.current_stream(dev)
+        if isinstance(stream, int):
+            return torch.cuda.ExternalStream(stream, device=dev)
+        return stream
+
     def counts(self, hosts, kprime: int, stream=None):
-        """(A, census) summed over the shards."""
+        """(A, census) summed over the shards.  The counting kernels run on
+        `stream`; the all-reduces see their results (gloo: after a
+        synchronisation of that stream; NCCL: torch's current stream waits on
+        it), and the reduced tensors are ready on torch's current stream."""
         import torch
         dev = hosts.device
         active = torch.empty(hosts.numel(), dtype=torch.int32, device=dev)
         hist = torch.empty(2 * self.k + 1, dtype=torch.int64, device=dev)
-        self.lib.vate_active_counts(self.h, hosts, kprime, active, stream)
-        self.lib.vate_census(self.h, hist, stream)
+        st = self._torch_stream(stream, dev) if dev.type == "cuda" else stream
         if dev.type == "cuda":
-            torch.cuda.current_stream(dev).synchronize()
+            st.wait_stream(torch.cuda.current_stream(dev))   # the buffers were made on the current stream
+            active.record_stream(st)
+            hist.record_stream(st)
+        self.lib.vate_active_counts(self.h, hosts, kprime, active, st)
+        self.lib.vate_census(self.h, hist, st)
+        if dev.type == "cuda":
+            if self._gloo:
+                st.synchronize()
+            else:
+                torch.cuda.current_stream(dev).wait_stream(st)
         self._all_reduce(active)
         self._all_reduce(hist)
         return active, hist
 
     def estimate(self, hosts, kprime: int, out, flags=None, stream=None) -> None:
+        """Eq. 11 on the summed counts, queued on `stream` after the
+        all-reduces (which leave their results on torch's current stream)."""
+        import torch
         active, hist = self.counts(hosts, kprime, stream)
-        self.lib.vate_estimate_from_counts(self.params, active, hist, kprime, out, flags, stream)
+        st = stream
+        if hosts.device.type == "cuda":
+            st = self._torch_stream(stream, hosts.device)
+            st.wait_stream(torch.cuda.current_stream(hosts.device))
+        self.lib.vate_estimate_from_counts(self.params, active, hist, kprime, out, flags, st)
 
     def copy_pool(self, dst, stream=None) -> None:
         """This shard's positions [lo, hi), in the paper's form."""

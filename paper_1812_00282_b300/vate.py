@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libvate.so")
 
 VATE_OK, VATE_EINVAL, VATE_ENOMEM, VATE_ESLICE, VATE_ECUDA, VATE_ETIMEOUT = 0, 1, 2, 3, 4, 5
 VATE_FLAG_SAT, VATE_FLAG_POOLFULL = 1, 2
+VATE_OPT_PERSIST_L2 = 1
 ERROR_NAMES = {1: "VATE_EINVAL", 2: "VATE_ENOMEM", 3: "VATE_ESLICE", 4: "VATE_ECUDA", 5: "VATE_ETIMEOUT"}
 
 
@@ -34,7 +35,7 @@ class VateError(RuntimeError):
 class vate_params(C.Structure):
     _fields_ = [("log2_pool", C.c_uint32), ("k", C.c_uint32), ("g", C.c_uint32), ("seg_len", C.c_uint32),
                 ("partition", C.c_uint32), ("counter", C.c_uint32), ("at_bits", C.c_uint32),
-                ("reserved", C.c_uint32), ("seed", C.c_uint64)]
+                ("options", C.c_uint32), ("seed", C.c_uint64)]
 
 
 class vate_info(C.Structure):
@@ -199,8 +200,8 @@ VATE_COUNTER_AT, VATE_COUNTER_DR = 0, 1
 
 
 def make_params(log2_pool: int, k: int, g: int, seg_len: int = 1, partition: int = 0, seed: int = 0,
-                counter: int = 0, at_bits: int = 0) -> vate_params:
-    return vate_params(log2_pool, k, g, seg_len, partition, counter, at_bits, 0, seed & 0xFFFFFFFFFFFFFFFF)
+                counter: int = 0, at_bits: int = 0, options: int = 0) -> vate_params:
+    return vate_params(log2_pool, k, g, seg_len, partition, counter, at_bits, options, seed & 0xFFFFFFFFFFFFFFFF)
 
 
 # ---- the C ABI, one function per entry point --------------------------------
@@ -671,8 +672,8 @@ class Vate:
     """Owns one handle; methods forward to the functions above."""
 
     def __init__(self, log2_pool: int, k: int, g: int, seg_len: int = 1, partition: int = 0, seed: int = 0,
-                 stream=None, counter: int = 0, at_bits: int = 0):
-        self.params = make_params(log2_pool, k, g, seg_len, partition, seed, counter, at_bits)
+                 stream=None, counter: int = 0, at_bits: int = 0, options: int = 0):
+        self.params = make_params(log2_pool, k, g, seg_len, partition, seed, counter, at_bits, options)
         self.k, self.g, self.P = k, g, 1 << log2_pool
         self.h = vate_create(self.params, stream)
 

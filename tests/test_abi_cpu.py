@@ -58,9 +58,9 @@ def test_invalid_parameters_rejected_on_host(V, bad):
     assert ei.value.code == V.VATE_EINVAL
 
 
-def test_reserved_must_be_zero(V):
+def test_unknown_option_bits_are_rejected(V):
     params = V.make_params(20, 5, 1024)
-    params.reserved = 1
+    params.options = 2
     with pytest.raises(V.VateError) as ei:
         V.vate_create(params, stream=0)
     assert ei.value.code == V.VATE_EINVAL

@@ -18,7 +18,7 @@ from oracle import Oracle
 from traffic import SMALL, Traffic
 
 pytestmark = pytest.mark.gpu
-RTOL = 1e-5
+from eq11_tol import RTOL, assert_eq11_close  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -170,7 +170,7 @@ def test_group_monitor_against_oracle(V):
             if len(hosts[m]):
                 oe, _, _ = o.estimate(hosts[m], o.k)
                 de = out[int(ho[m]):int(ho[m]) + len(hosts[m])].cpu().numpy().astype(np.float64)
-                assert (np.abs(de - oe) / np.maximum(np.abs(oe), 1)).max() <= RTOL
+                assert_eq11_close(de, oe, o.g, "monitor %d" % m)
         info = V.vate_group_monitor_info(grp.g, 0)
         assert info.slice == s and info.bact0 == s % (2 * mons[0][1])
     grp.close()
@@ -280,7 +280,7 @@ def test_group_full_size_64_monitors(V):
                 np.testing.assert_array_equal(act.cpu().numpy().view(np.uint32)[idx], oa)
                 np.testing.assert_array_equal(f.cpu().numpy()[idx], of)
                 de = e.cpu().numpy()[idx].astype(np.float64)
-                assert (np.abs(de - oe) / np.maximum(np.abs(oe), 1)).max() <= RTOL
+                assert_eq11_close(de, oe, m["g"], "monitor")
     assert grp.status() == 0
     grp.close()
     for d in singles:

@@ -20,7 +20,7 @@ from oracle import Oracle
 from traffic import LINK40G, SMALL, Traffic, mixed_hosts
 
 pytestmark = pytest.mark.gpu
-RTOL = 1e-5
+from eq11_tol import RTOL, assert_eq11_close  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -68,9 +68,7 @@ def compare_close(V, d, o, hosts, kps, check_pool=True, check_ages=True, check_e
         np.testing.assert_array_equal(act.cpu().numpy().view(np.uint32), oa, err_msg="A, k'=%d" % kp)
         np.testing.assert_array_equal(fl.cpu().numpy(), of, err_msg="flags, k'=%d" % kp)
         de = est.cpu().numpy().astype(np.float64)
-        err = np.abs(de - oe) / np.maximum(np.abs(oe), 1.0)
-        assert err.max() <= RTOL, "k'=%d max rel err %.3g at host %d (dev %r, oracle %r)" % (
-            kp, err.max(), int(err.argmax()), de[err.argmax()], oe[err.argmax()])
+        assert_eq11_close(de, oe, o.g, "k'=%d" % kp)
     if check_ages and o.g <= 65535:
         ages = torch.empty(n * k, dtype=torch.int16, device="cuda")
         d.age_counts(dh, ages)
@@ -370,8 +368,7 @@ def test_full_size_every_host_in_one_launch_sampled(V):
             np.testing.assert_array_equal(act.cpu().numpy().view(np.uint32)[idx], oa, err_msg="A, k'=%d" % kp)
             np.testing.assert_array_equal(fl.cpu().numpy()[idx], of, err_msg="flags, k'=%d" % kp)
             de = est.cpu().numpy()[idx].astype(np.float64)
-            err = np.abs(de - oe) / np.maximum(np.abs(oe), 1.0)
-            assert err.max() <= RTOL, "k'=%d max rel err %.3g" % (kp, err.max())
+            assert_eq11_close(de, oe, o.g, "k'=%d" % kp)
     d.close()
 
 
@@ -615,8 +612,7 @@ def test_maximum_pool_2p32_on_sparse_input(V, L):
             d.estimate(dh, kp, est)
             n0 = (1 << c) - len(live)
             oe = np.array([oracle.estimate_from_counts(g, 1 << c, n0, int(x))[0] for x in want])
-            err = np.abs(est.cpu().numpy().astype(np.float64) - oe) / np.maximum(np.abs(oe), 1.0)
-            assert err.max() <= RTOL
+            assert_eq11_close(est.cpu().numpy(), oe, g, "k'=%d" % kp)
     d.close()
 
 

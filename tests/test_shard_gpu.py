@@ -149,7 +149,11 @@ def free_port():
         return s.getsockname()[1]
 
 
-def test_two_processes_reduce_to_one_handle(V, tmp_path):
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_two_processes_reduce_to_one_handle(V, tmp_path, side_stream):
+    # side_stream: every shard call is queued on a stream other than torch's
+    # current one, so the all-reduces and Eq. 11 must be ordered after the
+    # counting kernels by the module itself
     c, k, g, L, seed = 17, 5, 1024, 32, 61
     script = tmp_path / "ranks.py"
     script.write_text(textwrap.dedent("""
@@ -165,15 +169,20 @@ def test_two_processes_reduce_to_one_handle(V, tmp_path):
         tr = Traffic(SMALL, pkts_per_slice=6000)
         hosts = torch.from_numpy(np.ascontiguousarray(tr.aips[:800], np.uint32).view(np.int32)).cuda()
         sv = ShardedVate(%(c)d, %(k)d, %(g)d, %(L)d, 0, %(seed)d)
+        st = torch.cuda.Stream() if %(side)r else None
         ref = V.Vate(%(c)d, %(k)d, %(g)d, %(L)d, 0, %(seed)d) if rank == 0 else None
         ok = True
         for s in (0, 1, 2, 7, 8, 20):
             p = torch.from_numpy(tr.slice_pairs(s).view(np.int32)).cuda()
-            sv.ingest(p, s)
-            sv.close_slice(s)
             out = torch.empty(hosts.numel(), dtype=torch.float32, device="cuda")
             fl = torch.empty(hosts.numel(), dtype=torch.uint8, device="cuda")
-            sv.estimate(hosts, %(k)d, out, fl)
+            if st is not None:
+                st.wait_stream(torch.cuda.current_stream())
+            sv.ingest(p, s, stream=st)
+            sv.close_slice(s, stream=st)
+            sv.estimate(hosts, %(k)d, out, fl, stream=st)
+            if st is not None:
+                torch.cuda.current_stream().wait_stream(st)
             if ref is not None:
                 ref.ingest(p, s)
                 ref.close_slice(s)
@@ -186,7 +195,7 @@ def test_two_processes_reduce_to_one_handle(V, tmp_path):
         with open(os.path.join(%(tmp)r, "rank%%d.json" %% rank), "w") as fh:
             json.dump({"ok": bool(ok), "range": [sv.lo, sv.hi]}, fh)
         dist.destroy_process_group()
-    """ % dict(root=ROOT, tmp=str(tmp_path), c=c, k=k, g=g, L=L, seed=seed)))
+    """ % dict(root=ROOT, tmp=str(tmp_path), c=c, k=k, g=g, L=L, seed=seed, side=side_stream)))
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr=127.0.0.1", "--master-port=%d" % free_port(), str(script)]
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)

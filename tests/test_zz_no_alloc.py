@@ -97,3 +97,22 @@ def test_census_noalloc_counts_out_of_range_values_as_inactive(V, counter):
         act = np.array([(3 + o.block(int(p))) % (2 * k) for p in pid])
         np.add.at(want, (act - active) % (2 * k), 1)
     np.testing.assert_array_equal(hist.cpu().numpy(), want)
+
+
+def test_census_noalloc_takes_no_device_memory(V):
+    """The promise itself: after the first call on the device (which looks up
+    the static scratch array's address), further calls leave the device's free
+    memory (cudaMemGetInfo) unchanged -- no cudaMalloc, no library pool."""
+    c, k = 20, 10
+    params = V.make_params(c, k, 64, 32, 0, 3)
+    pool = torch.randint(0, 2 * k + 1, (1 << c,), dtype=torch.uint8, device="cuda")
+    hist = torch.empty(2 * k + 1, dtype=torch.int64, device="cuda")
+    ref = torch.empty_like(hist)
+    V.vate_census_noalloc(params, pool, 1, ref)          # first call on this device: the set-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for call in range(8):
+        V.vate_census_noalloc(params, pool, 1, hist)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.equal(hist, ref)
