@@ -5,14 +5,21 @@ y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 with hidden width 64, parameters
 laid out as W1[n_in][64], b1[64], W2[64][64], b2[64], w3[64], b3.  Loss: mean
 squared error over the rows.  Features of a host: per-age VAT counts / g, the
 pool's per-age fractions, log2(g)/16, log1p(max(Eq. 11 estimate, 0))/16.
+Output rule at slice close (`estimate`): the model corrects the closed form
+of Eq. 11 in log space, estimate = expm1(8 y + log1p(max(Eq. 11, 0))); the
+closed form itself is returned, flagged FALLBACK, when the host has no active
+VAT in the window or the corrected value is not a finite FP32 number.
 Written directly from those definitions with numpy; the gradient is pinned
-by finite differences in the tests.
+by finite differences, the forward pass and the output rule by hand-built
+networks whose outputs are known in closed form.
 """
 from __future__ import annotations
 
 import numpy as np
 
 HID = 64
+FALLBACK = 4          # flag bit: the closed form was returned instead of the model's value
+FLT_MAX = float(np.finfo(np.float32).max)
 
 
 def n_params(n_in: int) -> int:
@@ -84,3 +91,27 @@ def features(o, hosts, k=None):
     X[:, 2 * k] = np.log2(o.g) / 16.0
     X[:, 2 * k + 1] = np.log1p(np.maximum(est, 0.0)) / 16.0
     return X, est
+
+
+def estimate(p, n_in, X, plain, k, plain_flags=None):
+    """The learned estimate of each row and its flags (the closed form's
+    SAT/POOLFULL bits from `plain_flags`, plus FALLBACK).
+
+    y = forward(X); z = 8 y + log1p(max(plain, 0)); estimate = expm1(z).
+    FALLBACK (estimate = plain): the row's per-age counts X[:, :k] are all 0
+    (no active VAT in the window), or expm1(z) is not a finite FP32 number.
+    The finiteness decision is taken in FP32, the precision in which the
+    estimate is delivered."""
+    X = np.asarray(X, np.float64).reshape(-1, n_in)
+    plain = np.asarray(plain, np.float64)
+    y = forward(p, n_in, X)
+    z = 8.0 * y + np.log1p(np.maximum(plain, 0.0))
+    with np.errstate(over="ignore", invalid="ignore"):
+        est = np.expm1(z)
+        finite32 = np.isfinite(est) & (np.abs(est) <= FLT_MAX)
+    no_active = X[:, :k].sum(axis=1) == 0
+    fb = no_active | ~finite32
+    out = np.where(fb, plain, est)
+    flags = np.zeros(len(out), np.uint8) if plain_flags is None else np.asarray(plain_flags, np.uint8).copy()
+    flags[fb] |= FALLBACK
+    return out, flags, z

@@ -1,13 +1,14 @@
 """Training and evaluation of the learned estimator (include/vate_learned.h).
 
 The model's arithmetic -- features, forward pass, gradient, Adam, the fused
-estimate -- runs in the library's kernels; this module only moves data:
-it drives a VATE handle through generated slices, labels sampled hosts with
-their exact window cardinality (distinct (aip, bip) keys of the last k
-slices, by sort-unique on the device), and feeds batches to
-vate_mlp_train_step.  The closed form of Eq. 11 is kept as the yardstick: a model
-whose mean relative error on held-out slices is worse than the closed form's
-is not accepted.
+estimate with its closed-form fallback -- runs in the library's kernels; this
+module only moves data: it drives a VATE handle through generated slices,
+labels sampled hosts with their exact window cardinality (distinct (aip, bip)
+keys of the last k slices, by sort-unique on the device), feeds batches to
+vate_mlp_train_step, and on held-out slices takes the estimates that
+vate_estimate_learned -- the kernel that serves closes -- returns.  The closed
+form of Eq. 11 is kept as the yardstick: a model whose mean relative error on
+held-out slices is worse than the closed form's is not accepted.
 """
 from __future__ import annotations
 
@@ -40,13 +41,14 @@ def exact_window_counts(window):
 
 
 def collect(V, dev_traffic, c, k, g, seg_len, seed, first_slice, n_slices, hosts_per_slice, warm=None,
-            large_share=0.0, large_from=32):
+            large_share=0.0, large_from=32, params=None):
     """Run one handle over n_slices generated slices and, after `warm` slices,
     sample hosts active in the window: features, targets (log1p(n) -
-    log1p(max(closed form, 0))) / 8, closed-form estimates and exact counts
-    (device tensors, one row per sampled host).  `large_share` of each slice's
-    sample is drawn from hosts with at least `large_from` peers (training only;
-    evaluation samples uniformly)."""
+    log1p(max(closed form, 0))) / 8, closed-form estimates, exact counts and,
+    when `params` is given, the fused learned estimates of vate_estimate_learned
+    (device tensors, one row per sampled host; None without params).
+    `large_share` of each slice's sample is drawn from hosts with at least
+    `large_from` peers (training only; evaluation samples uniformly)."""
     import torch
     warm = k if warm is None else warm
     h = V.Vate(c, k, g, seg_len, 0, seed)
@@ -54,7 +56,7 @@ def collect(V, dev_traffic, c, k, g, seg_len, seed, first_slice, n_slices, hosts
     window = collections.deque(maxlen=k)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed)
-    Xs, Ts, Ps, Ns = [], [], [], []
+    Xs, Ts, Ps, Ns, Ls = [], [], [], [], []
     for s in range(n_slices):
         pairs = dev_traffic.slice_pairs(first_slice + s)
         window.append(pairs)
@@ -83,8 +85,12 @@ def collect(V, dev_traffic, c, k, g, seg_len, seed, first_slice, n_slices, hosts
         Ts.append(((torch.log1p(n) - base) / 8.0).to(torch.float32))
         Ps.append(plain)
         Ns.append(n)
+        if params is not None:
+            est = torch.empty(m, dtype=torch.float32, device="cuda")
+            V.vate_estimate_learned(h.h, sh, params, est)
+            Ls.append(est)
     h.close()
-    return torch.cat(Xs), torch.cat(Ts), torch.cat(Ps), torch.cat(Ns)
+    return torch.cat(Xs), torch.cat(Ts), torch.cat(Ps), torch.cat(Ns), (torch.cat(Ls) if Ls else None)
 
 
 def balance_weights(N):
@@ -126,19 +132,6 @@ def train(V, X, T, n_in, epochs=8, batch=4096, lr=2e-3, seed=1, weight=None, los
     return params
 
 
-def learned_from_features(V, params, X, plain, k):
-    """The product's rule applied to feature rows: expm1(8 y + log1p(max(plain, 0))),
-    or the closed form when the host has no active VAT or that is not finite."""
-    import torch
-    n_in = X.shape[1]
-    y = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
-    V.vate_mlp_forward(params, n_in, X.contiguous(), y)
-    est = torch.expm1(8.0 * y + 16.0 * X[:, n_in - 1])
-    no_active = X[:, :k].sum(1) == 0
-    bad = ~torch.isfinite(est) | no_active
-    return torch.where(bad, plain, est)
-
-
 def mean_rel_err(est, n, lo=1):
     import torch
     sel = n >= lo
@@ -150,22 +143,24 @@ def run(V, spec=None, c=24, k=10, g=4096, seg_len=32, train_slices=200, eval_sli
         eval_hosts_per_slice=16384, epochs=8, seed=0xC4, large_share=0.0) -> Dict:
     """Learned-estimator workload: the 40 Gb/s traffic on a 2^24-AT pool, k = 10;
     train on `train_slices` generated slices, evaluate on `eval_slices`
-    held-out slices of a differently seeded stream, against the closed form."""
+    held-out slices of a differently seeded stream, against the closed form.
+    The learned estimates evaluated are those of vate_estimate_learned."""
     import torch
     from traffic import LINK40G, DeviceTraffic, Traffic, TrafficSpec
     spec = LINK40G if spec is None else spec
     t0 = time.time()
     tr_train = DeviceTraffic(Traffic(spec))
-    X, T, _, N = collect(V, tr_train, c, k, g, seg_len, seed, 0, train_slices + k, hosts_per_slice,
-                         large_share=large_share)
+    X, T, _, N, _ = collect(V, tr_train, c, k, g, seg_len, seed, 0, train_slices + k, hosts_per_slice,
+                            large_share=large_share)
     t1 = time.time()
     params = train(V, X, T, 2 * k + 2, epochs=epochs, seed=seed, weight=balance_weights(N))
     torch.cuda.synchronize()
     t2 = time.time()
     spec_eval = TrafficSpec(**{**spec.__dict__, "seed": spec.seed + 0x4E})
     tr_eval = DeviceTraffic(Traffic(spec_eval))
-    Xe, _, Pe, Ne = collect(V, tr_eval, c, k, g, seg_len, seed + 1, 0, eval_slices + k, eval_hosts_per_slice)
-    Le = learned_from_features(V, params, Xe, Pe, k)
+    # held-out slices: the estimates come from the fused kernel that serves closes
+    _, _, Pe, Ne, Le = collect(V, tr_eval, c, k, g, seg_len, seed + 1, 0, eval_slices + k, eval_hosts_per_slice,
+                               params=params)
     res = {}
     for lo in (1, 100):
         ml, cnt = mean_rel_err(Le, Ne, lo)
@@ -174,6 +169,7 @@ def run(V, spec=None, c=24, k=10, g=4096, seg_len=32, train_slices=200, eval_sli
     accepted = res["n>=1"]["learned"] <= res["n>=1"]["plain"]
     return {"mre": res, "accepted": bool(accepted), "train_rows": int(T.numel()), "eval_rows": int(Ne.numel()),
             "train_slices": train_slices, "eval_slices": eval_slices, "log2_pool": c, "k": k, "g": g,
+            "learned_from": "vate_estimate_learned (the fused kernel that serves closes)",
             "seconds": {"collect_train": round(t1 - t0, 2), "train": round(t2 - t1, 2),
                         "collect_eval": round(time.time() - t2, 2)},
             "params": params}

@@ -40,3 +40,54 @@ def test_forward_of_a_hand_built_network():
     p = np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [0.25]])
     X = np.array([[2.0, 5.0, -1.0], [-3.0, 0.0, 0.0], [0.0, 1.0, 1.0]])
     np.testing.assert_allclose(mlp.forward(p, n_in, X), [2.25, 3.25, 0.25])
+
+
+def _abs_net(n_in, b3):
+    # y = relu(x0) + relu(-x0) + b3 = |x0| + b3 (as in the forward pin)
+    W1 = np.zeros((n_in, 64)); W1[0, 0] = 1.0; W1[0, 1] = -1.0
+    W2 = np.zeros((64, 64)); W2[0, 0] = 1.0; W2[1, 1] = 1.0
+    w3 = np.zeros(64); w3[0] = w3[1] = 1.0
+    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [b3]])
+
+
+def test_learned_output_of_a_hand_built_network():
+    # k = 2, n_in = 6: columns 0-1 are per-age counts / g.  y = |x0| + 0.25;
+    # z = 8 y + log1p(max(plain, 0)).
+    k, n_in = 2, 6
+    p = _abs_net(n_in, 0.25)
+    X = np.array([[0.5, 0.0, 0, 0, 0.75, 0.1],      # y = 0.75, plain = e^2 - 1: z = 6 + 2
+                  [0.125, 0.25, 0, 0, 0.75, 0.1],   # y = 0.375, plain negative: z = 3 + 0
+                  [0.0, 0.5, 0, 0, 0.75, 0.1]])     # y = 0.25, plain = 0: z = 2
+    plain = np.array([np.expm1(2.0), -7.5, 0.0])
+    est, fl, z = mlp.estimate(p, n_in, X, plain, k, np.array([1, 0, 2], np.uint8))
+    np.testing.assert_allclose(z, [8.0, 3.0, 2.0], rtol=1e-15)
+    np.testing.assert_allclose(est, [np.expm1(8.0), np.expm1(3.0), np.expm1(2.0)], rtol=1e-15)
+    np.testing.assert_array_equal(fl, [1, 0, 2])          # closed form's flags kept, no fallback
+
+
+def test_learned_output_zero_model_reproduces_the_clamped_closed_form():
+    # a model that outputs 0 everywhere returns max(Eq. 11, 0) (up to the
+    # expm1(log1p(.)) round trip)
+    k, n_in = 3, 8
+    p = np.zeros(mlp.n_params(n_in))
+    rng = np.random.default_rng(4)
+    X = rng.uniform(0.01, 1, (50, n_in))
+    plain = rng.normal(0, 300, 50)
+    est, fl, _ = mlp.estimate(p, n_in, X, plain, k)
+    np.testing.assert_allclose(est, np.maximum(plain, 0.0), rtol=1e-13, atol=1e-12)
+    assert not fl.any()
+
+
+def test_learned_output_falls_back_to_the_closed_form():
+    k, n_in = 2, 6
+    p = _abs_net(n_in, 0.0)
+    X = np.array([[0.0, 0.0, 0, 0, 0.75, 0.1],     # no active VAT: per-age counts all 0
+                  [-12.0, 0.01, 0, 0, 0.75, 0.1],  # y = 12: z = 96 > ln(FLT_MAX) = 88.72
+                  [-11.0, 0.01, 0, 0, 0.75, 0.1],  # y = 11: z = 88, finite in FP32
+                  [0.0, 0.125, 0, 0, 0.75, 0.1]])  # active VATs, y = 0
+    plain = np.array([3.5, 100.0, 0.0, 41.0])
+    est, fl, _ = mlp.estimate(p, n_in, X, plain, k, np.array([0, 1, 0, 0], np.uint8))
+    assert est[0] == 3.5 and fl[0] == mlp.FALLBACK
+    assert est[1] == 100.0 and fl[1] == 1 | mlp.FALLBACK
+    assert np.isclose(est[2], np.expm1(88.0), rtol=1e-15) and fl[2] == 0
+    assert np.isclose(est[3], 41.0, rtol=1e-13) and fl[3] == 0
