@@ -51,6 +51,21 @@ def workload_name(args, n_h):
             "4,096 ({}-AT segments), Zipf(1.05), 0.1% super-spreaders".format(n_h, args.pkts, args.k, args.seg_len))
 
 
+def make_config(args, n_h, world):
+    """The `config` of both arms' JSON lines (the same dict in each)."""
+    from traffic import MEAN_PKT_BYTES
+    at_width = args.at_bits or (8 if args.k <= 63 else 16)
+    pool_mib = ((1 << C) // (32 // args.at_bits) * 4 if args.at_bits else (1 << C) * at_width // 8) / 2**20
+    return {"workload": workload_name(args, n_h), "aips": n_h, "pkts_per_slice": args.pkts,
+            "k": args.k, "kprime": args.k, "log2_pool": C, "g": G, "seg_len": args.seg_len,
+            "partition": args.partition, "at_bits": at_width,
+            "link_gbps_equivalent": round(args.pkts * MEAN_PKT_BYTES * 8 / 1e9, 2),
+            "l2": "flushed before every timed step (256 MiB write, outside the step events); the %.0f MiB AT pool "
+                  "is state kept from slice to slice and its kernels mark it L2-persisting" % pool_mib
+            if not args.no_flush else "not flushed",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -258,6 +273,33 @@ def probe_peaks(V, torch, pool_bytes: int):
     return {"l2_sector_read_gbs": 32 * n_sec / min(rd) / 1e6, "l2_byte_store_gps": n_wr / min(wr) / 1e6}
 
 
+def close_latency_loop(torch, mon, dt, hosts, out, flags, k, first_slice, flush, no_flush, n=200):
+    """Slice-close latency over n closes in a loop of their own (independent of
+    --steps): each close follows the ingest of a fresh slice (generated and
+    ingested before the close's events, L2 flushed before the ingest) and is
+    timed from the vate_close_slice enqueue to the completion of vate_estimate
+    for every host (census, gather, Eq. 11)."""
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    for i in range(n):
+        s = first_slice + i
+        p = dt.slice_pairs(s)
+        if not no_flush:
+            flush.fill_(s & 0xFF)
+        mon.ingest(p, s)
+        e0[i].record()
+        mon.close_slice(s)
+        mon.estimate(hosts, k, out, flags)
+        e1[i].record()
+        del p
+    torch.cuda.synchronize()
+    ms = [e0[i].elapsed_time(e1[i]) for i in range(n)]
+    return {"closes": n, "hosts": int(hosts.numel()), "p50_ms": round(float(np.percentile(ms, 50)), 4),
+            "p99_ms": round(float(np.percentile(ms, 99)), 4), "max_ms": round(max(ms), 4),
+            "how": "a loop of its own: every close after a fresh slice's ingest, from the vate_close_slice enqueue "
+                   "to the completion of vate_estimate for every host"}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_1812_00282_b300 as V
@@ -318,6 +360,8 @@ def run_ours(args, rank, world, local):
     clocks.mark_off()
     launches = V.vate_launch_count() - launches0
     clock_info = clocks.stop()
+    close_loop = close_latency_loop(torch, mon, dt, hosts, out, flags, args.k, W + K, flush, args.no_flush,
+                                    n=max(200, K))
 
     step_ms = [e0[i].elapsed_time(e3[i]) for i in range(K)]
     ingest_ms = [e0[i].elapsed_time(e1[i]) for i in range(K)]
@@ -359,16 +403,11 @@ def run_ours(args, rank, world, local):
         "ms_per_step": round(dev_ms_max / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u%d" % at_width if not args.at_bits else "%d-bit fields in u32 words" % args.at_bits,
         "data": "synthetic",
-        "config": {"workload": workload_name(args, n_h), "aips": n_h, "pkts_per_slice": args.pkts,
-                   "k": args.k, "kprime": args.k,
-                   "log2_pool": C, "g": G, "seg_len": args.seg_len, "partition": args.partition,
-                   "at_bits": at_width,
-                   "link_gbps_equivalent": round(args.pkts * MEAN_PKT_BYTES * 8 / 1e9, 2),
-                   "l2": "flushed before every timed step (256 MiB write, outside the step events); the %.0f MiB "
-                         "AT pool is state kept from slice to slice and its kernels mark it L2-persisting" % pool_mib
-                   if not args.no_flush else "not flushed", "parallelism": "replicas" if world > 1 else "single"},
-        "close_p50_ms": round(float(np.percentile(close_ms, 50)), 4),
-        "close_p99_ms": round(float(np.percentile(close_ms, 99)), 4),
+        "config": make_config(args, n_h, world),
+        "close_p50_ms": close_loop["p50_ms"],
+        "close_p99_ms": close_loop["p99_ms"],
+        "close_latency": {**close_loop, "in_timed_steps": {"p50_ms": round(float(np.percentile(close_ms, 50)), 4),
+                                                           "max_ms": round(max(close_ms), 4), "closes": K}},
         "ingest_mpkts": round(args.pkts / ingest_avg / 1e3, 1),
         "kernels_ms": {"ingest+preserve": round(ingest_avg, 4), "census": round(statistics.mean(census_ms), 4),
                        "gather+estimate": round(gather_avg, 4)},
@@ -533,93 +572,167 @@ def run_e2e(args, V, torch, tr, dt, rank, world):
 # ---------------------------------------------------------------------------
 # CPU oracle timings (the reference arm and the cpu_baseline field)
 # ---------------------------------------------------------------------------
-def oracle_step_sample(o, k, pairs, hosts_sample, pool_frac, n_hosts_total, pkts_total, advance=True):
-    """Time one oracle step on a bounded sample and scale it to a full slice:
-    the slide, SetAT over the sample pairs, the census over a fraction of the
-    pool, and the gather + Eq. 11 of the sample hosts.  Returns
-    (Mpkt/s for a full slice, seconds spent)."""
+def host_cpu() -> dict:
+    """Threads this process may use and the CPU model of the host."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        n = os.cpu_count() or 1
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": n, "model": model}
+
+
+def oracle_step_parts(o, k, pairs, hosts_sample, threads, advance=True):
+    """One oracle step on a bounded sample, timed part by part (seconds): the
+    slide and SetAT over `pairs` on one thread (the plain oracle's ingest); the
+    census of the whole pool, the inactive count N0 of Z_p and the per-host
+    gather + Eq. 11 of `hosts_sample` on `threads` OpenMP threads."""
     import oracle
+    oracle.set_threads(1)
     t0 = time.perf_counter()
     if advance:
         o.advance()
     t1 = time.perf_counter()
     o.ingest(pairs)
     t2 = time.perf_counter()
-    end = max(4096, int(o.P * pool_frac))
-    n0_part = o.pool_inactive_range(k, 0, end)
+    oracle.set_threads(threads)
+    o.census()
     t3 = time.perf_counter()
-    n0 = int(n0_part * o.P / end)
-    for h in hosts_sample:
-        oracle.estimate_from_counts(o.g, o.P, n0, o.active_vats(int(h), k))
+    n0 = o.pool_inactive(k)
     t4 = time.perf_counter()
-    full = ((t1 - t0) + (t2 - t1) / max(1, len(pairs)) * pkts_total + (t3 - t2) * o.P / end
-            + (t4 - t3) / max(1, len(hosts_sample)) * n_hosts_total)
-    return pkts_total / full / 1e6, t4 - t0
+    o.estimate_hosts(hosts_sample, k, n0)
+    t5 = time.perf_counter()
+    oracle.set_threads(1)
+    return {"slide": t1 - t0, "ingest": t2 - t1, "census": t3 - t2, "n0": t4 - t3, "hosts": t5 - t4,
+            "n_pairs": len(pairs), "n_hosts": len(hosts_sample)}
+
+
+def full_step_s(parts, pkts_total, n_hosts_total):
+    """The measured parts scaled to one full slice: SetAT per pair times the
+    slice's pairs, the per-host loop per host times the hosts estimated; the
+    slide, census and N0 already cover the whole pool."""
+    return (parts["slide"] + parts["ingest"] / max(1, parts["n_pairs"]) * pkts_total + parts["census"]
+            + parts["n0"] + parts["hosts"] / max(1, parts["n_hosts"]) * n_hosts_total)
+
+
+def measured_s(parts):
+    return parts["slide"] + parts["ingest"] + parts["census"] + parts["n0"] + parts["hosts"]
 
 
 def cpu_baseline(tr, args, budget_s=20.0):
+    """The oracle as it stands on this host's cores (about budget_s of CPU work):
+    three slices of the workload; on the last one SetAT over all the slice's
+    pairs (one thread), the whole-pool census and N0, and the per-host loop on a
+    seeded host sample, at one thread and at nproc threads, each scaled to a
+    full slice of 2^20 hosts."""
     import oracle
     from traffic import mixed_hosts
+    cpu = host_cpu()
+    nt = cpu["nproc"]
     o = oracle.Oracle(c=C, k=args.k, g=G, seg_len=args.seg_len, partition=args.partition, seed=0xC2)
     n_h = min(args.aips, tr.spec.n_aips)
-    hs = mixed_hosts(tr, 8192)
-    vals, spent, s = [], 0.0, 0
-    while spent < budget_s and s < 6:
-        pairs = tr.slice_pairs(s)
-        v, dt = oracle_step_sample(o, args.k, pairs, hs, 1.0, n_h, len(pairs), advance=s > 0)
-        vals.append(v)
-        spent += dt
-        s += 1
-    return {"value": round(statistics.median(vals), 5), "unit": "Mpkt/s", "cores": 1, "kind": "oracle",
-            "sample": "%d slices of the workload: the slide, SetAT over all %d pairs, the census of the whole 2^26 "
-                      "pool, and the gather + Eq. 11 of %d hosts (every super-spreader plus a seeded sample), "
-                      "scaled to %d hosts; single-threaded plain C oracle, %.1f s of CPU work"
-                      % (s, args.pkts, len(hs), n_h, spent)}
+    for s in range(2):
+        if s:
+            o.advance()
+        o.ingest(tr.slice_pairs(s))
+    pairs = tr.slice_pairs(2)
+    # per-host cost on one thread, to size the samples
+    hs_all = mixed_hosts(tr, 262144)
+    t0 = time.perf_counter()
+    o.estimate_hosts(hs_all[:64], args.k, 1)
+    per_host = max(1e-6, (time.perf_counter() - t0) / 64)
+    n1 = int(max(64, min(len(hs_all), 4.0 / per_host)))               # ~4 s on one thread
+    nn = int(max(64, min(len(hs_all), 8.0 * nt / per_host)))          # ~8 s on nproc threads
+    p_n = oracle_step_parts(o, args.k, pairs, hs_all[:nn], nt, advance=True)
+    p_1 = dict(p_n)
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    o.census()
+    t1 = time.perf_counter()
+    n0 = o.pool_inactive(args.k)
+    t2 = time.perf_counter()
+    o.estimate_hosts(hs_all[:n1], args.k, n0)
+    t3 = time.perf_counter()
+    p_1.update(census=t1 - t0, n0=t2 - t1, hosts=t3 - t2, n_hosts=n1)
+    full_n = full_step_s(p_n, args.pkts, n_h)
+    full_1 = full_step_s(p_1, args.pkts, n_h)
+    spent = measured_s(p_n) + (t3 - t0)
+    return {"value": round(args.pkts / full_n / 1e6, 5), "unit": "Mpkt/s", "cores": nt, "kind": "oracle",
+            "cpu_model": cpu["model"], "nproc": nt,
+            "value_1_thread": round(args.pkts / full_1 / 1e6, 5),
+            "full_slice_s": {"nproc_threads": round(full_n, 3), "1_thread": round(full_1, 3)},
+            "parts_s": {"slide_1t": round(p_n["slide"], 4), "setat_all_pairs_1t": round(p_n["ingest"], 3),
+                        "census_nt": round(p_n["census"], 4), "census_1t": round(p_1["census"], 4),
+                        "n0_nt": round(p_n["n0"], 4), "n0_1t": round(p_1["n0"], 4),
+                        "hosts_nt": round(p_n["hosts"], 3), "hosts_1t": round(p_1["hosts"], 3)},
+            "sample": "third slice of the workload: the slide and SetAT over all %d pairs on one thread (the plain "
+                      "oracle's ingest), the census of the whole 2^26 pool and N0 at %d and at 1 thread(s), and "
+                      "the gather + Eq. 11 of %d hosts at %d threads and %d hosts at 1 thread (every "
+                      "super-spreader first, then a seeded sample), scaled to %d hosts; %.1f s of CPU work"
+                      % (len(pairs), nt, nn, nt, n1, n_h, spent)}
 
 
 def run_reference(args, rank, world):
-    """The oracle as it stands, timed on this host's cores, on the same workload
-    and metric; each step a bounded sample so the whole run ends in minutes."""
+    """The oracle as it stands, timed on this host's cores, on the same workload,
+    metric and config as the device arm.  Each step is a bounded sample of a
+    slice: the slide and SetAT over a contiguous sample of the slice's pairs on
+    one thread, the whole-pool census and N0 and the gather + Eq. 11 of a host
+    sample on nproc threads.  ms_per_step is the measured time of what ran;
+    the value is the throughput of a full slice at the measured per-pair and
+    per-host costs, and sample_scale the ratio of the two times."""
     from traffic import LINK40G, Traffic, mixed_hosts
     import oracle
+    cpu = host_cpu()
+    nt = cpu["nproc"]
     tr = Traffic(LINK40G, pkts_per_slice=args.pkts)
     total = args.steps + args.warmup
-    per_step_budget = max(0.15, 120.0 / total)
+    per_step_budget = max(0.2, 100.0 / total)
     o = oracle.Oracle(c=C, k=args.k, g=G, seg_len=args.seg_len, partition=args.partition, seed=0xC2)
     n_h = min(args.aips, tr.spec.n_aips)
     base_pairs = tr.slice_pairs(0)
+    hs_all = mixed_hosts(tr, 65536)
     # calibrate the sample so that one step costs about per_step_budget
-    n_pk, n_hs, frac = 200_000, 128, 1.0 / 64
-    hs_all = mixed_hosts(tr, 4096)
-    t0 = time.perf_counter()
-    oracle_step_sample(o, args.k, base_pairs[:n_pk], hs_all[:n_hs], frac, n_h, args.pkts, advance=True)
-    cal = time.perf_counter() - t0
-    scale = max(0.05, min(4.0, per_step_budget / max(cal, 1e-3)))
-    n_pk = max(10_000, min(args.pkts, int(n_pk * scale)))
-    n_hs = max(16, min(len(hs_all), int(n_hs * scale)))
-    frac = min(1.0, frac * scale)
+    cal = oracle_step_parts(o, args.k, base_pairs[:200_000], hs_all[:8 * nt], nt, advance=False)
+    per_pair = cal["ingest"] / cal["n_pairs"]
+    per_host = cal["hosts"] / cal["n_hosts"]
+    fixed = cal["census"] + cal["n0"] + 0.01
+    room = max(0.05, per_step_budget - fixed)
+    n_pk = int(max(10_000, min(args.pkts, 0.4 * room / per_pair)))
+    n_hs = int(max(nt, min(len(hs_all), 0.6 * room / per_host)))
     hs = hs_all[:n_hs]
-    vals, spent = [], 0.0
+    full, meas, t_run = [], [], time.perf_counter()
     for s in range(total):
         off = (s * 104_729) % max(1, args.pkts - n_pk)
-        v, dt = oracle_step_sample(o, args.k, base_pairs[off:off + n_pk], hs, frac, n_h, args.pkts, advance=True)
-        spent += dt
+        parts = oracle_step_parts(o, args.k, base_pairs[off:off + n_pk], hs, nt, advance=True)
         if s >= args.warmup:
-            vals.append(v)
-    value = statistics.median(vals)
-    ms = args.pkts / value / 1e3
+            full.append(full_step_s(parts, args.pkts, n_h))
+            meas.append(measured_s(parts))
+    wall = time.perf_counter() - t_run
+    full_s = statistics.median(full)
+    ms = 1e3 * statistics.mean(meas)
+    value = args.pkts / full_s / 1e6
     return {"metric": METRIC, "impl": "reference", "value": round(value, 5), "unit": "Mpkt/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-            "config": {"workload": workload_name(args, n_h), "aips": n_h,
-                       "pkts_per_slice": args.pkts, "k": args.k, "kprime": args.k, "log2_pool": C, "g": G,
-                       "seg_len": args.seg_len, "partition": args.partition,
-                       "oracle_values": "one uint16 per AT position, Eq. 11 in float64"},
-            "cpu_baseline": {"value": round(value, 5), "unit": "Mpkt/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step: the slide, SetAT over %d pairs, the census of %.4f of the 2^26 "
-                                       "pool, the gather + Eq. 11 of %d hosts, each scaled to a full slice (%d "
-                                       "pairs, whole pool, %d hosts); %.1f s of CPU work in total"
-                                       % (n_pk, frac, n_hs, args.pkts, n_h, spent)},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+            "sample_scale": round(full_s * 1e3 / ms, 3), "ms_per_full_slice": round(full_s * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": make_config(args, n_h, world),
+            "wall_s": round(wall, 2),
+            "cpu_baseline": {"value": round(value, 5), "unit": "Mpkt/s", "cores": nt, "kind": "oracle",
+                             "cpu_model": cpu["model"], "nproc": nt,
+                             "sample": "per step: the slide and SetAT over %d of the slice's %d pairs on one thread, "
+                                       "the census of the whole 2^26 pool and N0 and the gather + Eq. 11 of %d "
+                                       "hosts on %d threads (one uint16 per AT position, Eq. 11 in float64); "
+                                       "ms_per_step is what ran, the value scales SetAT to all pairs and the "
+                                       "per-host loop to %d hosts (sample_scale = full slice / sample time)"
+                                       % (n_pk, args.pkts, n_hs, nt, n_h)},
             "e2e": {"value": round(value, 5), "unit": "Mpkt/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

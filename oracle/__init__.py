@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -83,11 +83,14 @@ def _load():
             "vo_advance_general_every_slice": (None, [vp]),
             "vo_check_all": (None, [vp, u32, u8p]),
             "vo_census": (None, [vp, u64p]),
+            "vo_set_threads": (None, [C.c_int]),
+            "vo_get_threads": (C.c_int, []),
             "vo_pool_inactive": (u64, [vp, u32]),
             "vo_pool_inactive_range": (u64, [vp, u32, u64, u64]),
             "vo_estimate_from_counts": (C.c_double, [u32, u64, u64, u32, C.POINTER(C.c_uint8)]),
             "vo_active_vats": (u32, [vp, u32, u32]),
             "vo_estimate": (None, [vp, u32p, u64, u32, f64p, u32p, u8p]),
+            "vo_estimate_hosts": (None, [vp, u32p, u64, u32, u64, f64p, u32p, u8p]),
             "vo_age_counts": (None, [vp, u32p, u64, u32p]),
             "vo_active_vats_dr": (u32, [vp, u32, u32]),
         }
@@ -97,6 +100,16 @@ def _load():
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's loops over pool ATs and over hosts (1 by
+    default); results do not depend on it."""
+    _load().vo_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(_load().vo_get_threads())
 
 
 def h_of(c: int, L: int, seed: int, aip: int, i: int) -> int:
@@ -264,6 +277,16 @@ class Oracle:
         act = np.empty(a.shape[0], np.uint32)
         fl = np.empty(a.shape[0], np.uint8)
         self._lib.vo_estimate(self._s, a, a.shape[0], kprime, est, act, fl)
+        return est, act, fl
+
+    def estimate_hosts(self, aips, kprime: int, n0: int):
+        """The per-host part of estimate() with the pool's inactive count n0
+        given (as pool_inactive(kprime) returns it)."""
+        a = np.ascontiguousarray(aips, np.uint32)
+        est = np.empty(a.shape[0], np.float64)
+        act = np.empty(a.shape[0], np.uint32)
+        fl = np.empty(a.shape[0], np.uint8)
+        self._lib.vo_estimate_hosts(self._s, a, a.shape[0], kprime, n0, est, act, fl)
         return est, act, fl
 
     def age_counts(self, aips) -> np.ndarray:

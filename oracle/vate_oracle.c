@@ -42,12 +42,24 @@
  *   R10 saturation: V0 = g - A == 0 is replaced by 1 (flag SAT); a pool
  *       census with N0 == 0 is replaced by 1 (flag POOLFULL).
  *
- * Build: gcc -O2 -shared -fPIC -o liboracle.so vate_oracle.c -lm
+ * Threads: the loops over pool ATs (census, inactive count) and over hosts
+ * (estimate, per-age counts) may run on several OpenMP threads -- plain
+ * parallel loops, no blocking or reordering of any per-AT or per-host step;
+ * the integer sums do not depend on the split, so the results are the same
+ * for any thread count.  The default is one thread (vo_set_threads).
+ *
+ * Build: gcc -O2 -fopenmp -shared -fPIC -o liboracle.so vate_oracle.c -lm
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <omp.h>
+
+/* Number of threads of the parallel loops below (1 by default). */
+static int vo_nthreads = 1;
+void vo_set_threads(int n) { vo_nthreads = n < 1 ? 1 : n; }
+int vo_get_threads(void) { return vo_nthreads; }
 
 /* ------------------------------------------------------------------ */
 /* Hash functions H and BH (reading R7).                               */
@@ -368,6 +380,7 @@ void vo_census(const vo_state *s, uint64_t *hist)
 {
     uint32_t twok = 2 * s->k;
     for (uint32_t d = 0; d <= twok; d++) hist[d] = 0;
+#pragma omp parallel for num_threads(vo_nthreads) reduction(+ : hist[:twok + 1]) schedule(static)
     for (uint64_t q = 0; q < s->P; q++) {
         uint32_t v = s->pool[q];
         if (v == twok) { hist[twok]++; continue; }
@@ -380,6 +393,7 @@ void vo_census(const vo_state *s, uint64_t *hist)
 uint64_t vo_pool_inactive(const vo_state *s, uint32_t kprime)
 {
     uint64_t n0 = 0;
+#pragma omp parallel for num_threads(vo_nthreads) reduction(+ : n0) schedule(static)
     for (uint64_t q = 0; q < s->P; q++)
         if (!vo_check_at(s->pool[q], vo_act_of(s, q), s->k, kprime)) n0++;
     return n0;
@@ -391,6 +405,7 @@ uint64_t vo_pool_inactive_range(const vo_state *s, uint32_t kprime, uint64_t sta
 {
     uint64_t n0 = 0;
     if (end > s->P) end = s->P;
+#pragma omp parallel for num_threads(vo_nthreads) reduction(+ : n0) schedule(static)
     for (uint64_t q = start; q < end; q++)
         if (!vo_check_at(s->pool[q], vo_act_of(s, q), s->k, kprime)) n0++;
     return n0;
@@ -424,10 +439,21 @@ uint32_t vo_active_vats(const vo_state *s, uint32_t aip, uint32_t kprime)
 
 /* Estimation step of Algorithm 4 for a list of hosts: Z_p from the pool,
  * Z_v from each host's g VATs, then Eq. 11.  Any of the outputs may be NULL. */
+void vo_estimate_hosts(const vo_state *s, const uint32_t *aips, uint64_t n, uint32_t kprime, uint64_t N0,
+                       double *est, uint32_t *active, uint8_t *flags);
+
 void vo_estimate(const vo_state *s, const uint32_t *aips, uint64_t n, uint32_t kprime,
                  double *est, uint32_t *active, uint8_t *flags)
 {
-    uint64_t N0 = vo_pool_inactive(s, kprime);
+    vo_estimate_hosts(s, aips, n, kprime, vo_pool_inactive(s, kprime), est, active, flags);
+}
+
+/* The per-host part of the estimation step, given the pool's inactive count
+ * N0 for window k' (Z_p = N0 / P). */
+void vo_estimate_hosts(const vo_state *s, const uint32_t *aips, uint64_t n, uint32_t kprime, uint64_t N0,
+                       double *est, uint32_t *active, uint8_t *flags)
+{
+#pragma omp parallel for num_threads(vo_nthreads) schedule(dynamic, 16)
     for (uint64_t h = 0; h < n; h++) {
         uint32_t A = vo_active_vats(s, aips[h], kprime);
         uint8_t f = 0;
@@ -444,6 +470,7 @@ void vo_estimate(const vo_state *s, const uint32_t *aips, uint64_t n, uint32_t k
 void vo_age_counts(const vo_state *s, const uint32_t *aips, uint64_t n, uint32_t *out)
 {
     uint32_t twok = 2 * s->k;
+#pragma omp parallel for num_threads(vo_nthreads) schedule(dynamic, 16)
     for (uint64_t h = 0; h < n; h++) {
         uint32_t *row = out + h * s->k;
         for (uint32_t d = 0; d < s->k; d++) row[d] = 0;

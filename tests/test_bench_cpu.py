@@ -48,22 +48,22 @@ def test_workload_name_follows_the_arguments():
     assert "4,096 aips, 1,000 pkts" in name and "k=300" in name and "(16-AT segments)" in name
 
 
-def test_oracle_step_sample_uses_the_given_window():
-    # the oracle leg counts with the run's window: every census and gather
-    # call of one step gets k' = k, for the long window as for the short one
+def test_oracle_step_parts_use_the_given_window():
+    # the oracle leg counts with the run's window: the N0 scan and every
+    # per-host call of one step get k' = k, for the long window as for the short one
     from oracle import Oracle
     from traffic import SMALL, Traffic
 
     class Recording(Oracle):
         seen = []
 
-        def pool_inactive_range(self, kprime, start, end):
+        def pool_inactive(self, kprime):
             self.seen.append(kprime)
-            return super().pool_inactive_range(kprime, start, end)
+            return super().pool_inactive(kprime)
 
-        def active_vats(self, aip, kprime):
+        def estimate_hosts(self, aips, kprime, n0):
             self.seen.append(kprime)
-            return super().active_vats(aip, kprime)
+            return super().estimate_hosts(aips, kprime, n0)
 
     tr = Traffic(SMALL, pkts_per_slice=2000)
     pairs = tr.slice_pairs(0)
@@ -71,6 +71,24 @@ def test_oracle_step_sample_uses_the_given_window():
     for k in (2, 300):
         o = Recording(c=19, k=k, g=64, seg_len=8, partition=0, seed=3)   # every block of Eq. 9-10 non-empty
         o.seen = []
-        v, dt = bench.oracle_step_sample(o, k, pairs, hosts, 1.0, 8, len(pairs), advance=True)
-        assert v > 0 and dt >= 0
-        assert o.seen == [k] * (1 + len(hosts))
+        parts = bench.oracle_step_parts(o, k, pairs, hosts, 2, advance=True)
+        assert o.seen == [k, k]
+        assert parts["n_pairs"] == len(pairs) and parts["n_hosts"] == len(hosts)
+        assert all(parts[x] >= 0 for x in ("slide", "ingest", "census", "n0", "hosts"))
+        full = bench.full_step_s(parts, 10 * len(pairs), 100)
+        # the full slice scales SetAT by 10 and the host loop by 100 / 8
+        expect = (parts["slide"] + 10 * parts["ingest"] + parts["census"] + parts["n0"] + parts["hosts"] * 100 / 8)
+        assert abs(full - expect) <= 1e-12 * max(1.0, expect)
+
+
+def test_both_arms_print_the_same_config():
+    a = _args("--k", "30")
+    c1 = bench.make_config(a, 1 << 20, 1)
+    c2 = bench.make_config(a, 1 << 20, 1)
+    assert c1 == c2 and c1["k"] == 30 and c1["parallelism"] == "single"
+    assert bench.make_config(a, 1 << 20, 4)["parallelism"] == "replicas"
+
+
+def test_host_cpu_reports_threads_and_model():
+    cpu = bench.host_cpu()
+    assert cpu["nproc"] >= 1 and isinstance(cpu["model"], str) and cpu["model"]

@@ -532,3 +532,29 @@ def test_error_falls_with_pool_size_and_vector_length():
     by_g = [mre(21, g, top) for g in (128, 512, 2048)]
     assert exact[top].max() > 128 * math.log(128)           # the largest top host saturates g = 128
     assert by_g[0] > by_g[1] and by_g[0] > by_g[2], by_g
+
+
+def test_oracle_results_do_not_depend_on_its_thread_count():
+    # the census, the inactive count and the per-host loops may run on
+    # several OpenMP threads (for the timed CPU baseline); integer sums and
+    # per-host results must be the same for any thread count
+    from traffic import SMALL, Traffic
+    tr = Traffic(SMALL, pkts_per_slice=30_000)
+    o = oracle.Oracle(c=18, k=5, g=512, seg_len=1, partition=0, seed=8)
+    for s in range(4):
+        if s:
+            o.advance()
+        o.ingest(tr.slice_pairs(s))
+    runs = []
+    try:
+        for t in (1, 3, 8):
+            oracle.set_threads(t)
+            assert oracle.threads() == t
+            e, a, f = o.estimate(tr.aips, 5)
+            n0 = o.pool_inactive(3)
+            runs.append((o.census(), e, a, f, o.age_counts(tr.aips), n0, o.estimate_hosts(tr.aips, 3, n0)[0]))
+    finally:
+        oracle.set_threads(1)
+    for r in runs[1:]:
+        for x, y in zip(runs[0], r):
+            assert np.array_equal(x, y)
