@@ -86,12 +86,15 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator train/evaluate run")
     ap.add_argument("--workload", default="link40g",
-                    choices=["link40g", "monitors64", "serving", "pt", "learned-kernels", "probes", "ingest-mix"],
+                    choices=["link40g", "monitors64", "serving", "pt", "learned-kernels", "probes", "ingest-mix",
+                             "placement"],
                     help="link40g: the headline single-monitor workload; monitors64: 64 independent monitors "
                          "advanced together (vate_group, CUDA graph per slice); learned-kernels: the learned "
                          "estimator's kernels timed one by one at 2^20 hosts; probes: random 32-byte sector "
                          "reads against the working-set size; ingest-mix: vate_ingest of a 40 Gb/s slice "
-                         "against uniform random pairs and against the slice's distinct pairs")
+                         "against uniform random pairs and against the slice's distinct pairs; placement: "
+                         "gather time, close latency and accuracy against exact window counts for segment "
+                         "lengths L = 1 (the paper's random H) to 64 at the 40 Gb/s shape")
     return ap.parse_args()
 
 
@@ -246,31 +249,52 @@ def measured_peaks():
         return {}
 
 
-def probe_peaks(V, torch, pool_bytes: int):
-    """L2 random 32-byte sector reads and random byte stores on a pool-sized
-    (L2-resident) buffer, best of several launches."""
+PROBE_UNROLL = (1, 2, 4, 8)
+PROBE_BLOCKS = (2, 4, 8, 16, 32)
+
+
+def best_of(torch, fn, reps=5, warm=2):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(warm):
+        fn()
+    best = float("inf")
+    for _ in range(reps):
+        ev[0].record()
+        fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        best = min(best, ev[0].elapsed_time(ev[1]))
+    return best
+
+
+def probe_peaks(torch, pool_bytes: int, sweep=True):
+    """Ceilings of the three access patterns on a pool-sized buffer (L2-resident
+    at 64 MiB), each the fastest over accesses in flight per thread (1, 2, 4, 8)
+    x blocks of 256 threads per SM (2..32): random 32-byte sector reads (the
+    gather), random byte stores (the ingest) and one coalesced read of the
+    buffer (the census).  Rates in GB/s (reads) and G stores/s."""
+    from paper_1812_00282_b300 import probe
     buf = torch.zeros(pool_bytes, dtype=torch.uint8, device="cuda")
     sink = torch.zeros(4, dtype=torch.int32, device="cuda")
-    n_sec = 1 << 27
-    n_wr = 1 << 26
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    rd, wr = [], []
-    for _ in range(2):
-        V.vate_probe_sector_read(buf, n_sec, sink)
-        V.vate_probe_byte_write(buf, n_wr)
-    for _ in range(5):
-        ev[0].record()
-        V.vate_probe_sector_read(buf, n_sec, sink)
-        ev[1].record()
-        torch.cuda.synchronize()
-        rd.append(ev[0].elapsed_time(ev[1]))
-        ev[0].record()
-        V.vate_probe_byte_write(buf, n_wr)
-        ev[1].record()
-        torch.cuda.synchronize()
-        wr.append(ev[0].elapsed_time(ev[1]))
+    n_sec, n_wr, passes = 1 << 27, 1 << 26, 16
+    shapes = [(u, b) for u in PROBE_UNROLL for b in PROBE_BLOCKS] if sweep else [(4, 8)]
+    best = {"sector_read": (0.0, None), "byte_store": (0.0, None), "stream_read": (0.0, None)}
+    for u, b in shapes:
+        r = 32 * n_sec / best_of(torch, lambda: probe.sector_read(buf, n_sec, sink, u, b)) / 1e6
+        w = n_wr / best_of(torch, lambda: probe.byte_write(buf, n_wr, u, b)) / 1e6
+
+        def stream():
+            for _ in range(passes):
+                probe.stream_read(buf, sink, u, b)
+        st = passes * pool_bytes / best_of(torch, stream) / 1e6
+        for key, val in (("sector_read", r), ("byte_store", w), ("stream_read", st)):
+            if val > best[key][0]:
+                best[key] = (val, {"in_flight": u, "blocks_per_sm": b})
     del buf
-    return {"l2_sector_read_gbs": 32 * n_sec / min(rd) / 1e6, "l2_byte_store_gps": n_wr / min(wr) / 1e6}
+    return {"l2_sector_read_gbs": best["sector_read"][0], "sector_read_shape": best["sector_read"][1],
+            "l2_byte_store_gps": best["byte_store"][0], "byte_store_shape": best["byte_store"][1],
+            "l2_stream_read_gbs": best["stream_read"][0], "stream_read_shape": best["stream_read"][1],
+            "buffer_mib": pool_bytes >> 20, "shapes_tried": len(shapes)}
 
 
 def close_latency_loop(torch, mon, dt, hosts, out, flags, k, first_slice, flush, no_flush, n=200):
@@ -318,7 +342,7 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
 
-    peaks = probe_peaks(V, torch, 1 << C)
+    peaks = probe_peaks(torch, 1 << C)
     mon = V.Vate(C, args.k, G, args.seg_len, args.partition, seed=0xC2 + rank, at_bits=args.at_bits,
                  options=V.VATE_OPT_PERSIST_L2)
 
@@ -415,8 +439,10 @@ def run_ours(args, rank, world, local):
                      "peak": round(peaks["l2_sector_read_gbs"], 1), "unit": "GB/s",
                      "frac": round(achieved / peaks["l2_sector_read_gbs"], 3), "traffic": traffic,
                      "kernel": "gather_vec_kernel",
-                     "peak_source": "random 32-B sector reads from a 64 MiB L2-resident buffer, measured in this run "
-                                    "(vate_probe_sector_read); no L2 figure in MEASURED_PEAKS.json",
+                     "peak_source": "random 32-B sector reads from a 64 MiB L2-resident buffer, two threads per "
+                                    "sector, measured in this run (vate_probe_sector_read, fastest of %d launch "
+                                    "shapes: %s); no L2 figure in MEASURED_PEAKS.json"
+                                    % (peaks["shapes_tried"], peaks["sector_read_shape"]),
                      "algorithmic_bytes": "aips x g VATs x AT bytes per launch (%d)" % vat_bytes,
                      "vs_hbm": {"peak": hbm, "frac": round(achieved / hbm, 3),
                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
@@ -424,11 +450,21 @@ def run_ours(args, rank, world, local):
         "roofline_ingest": {"bound": "l2_random_store", "achieved": round(args.pkts / ingest_avg / 1e6, 2),
                             "peak": round(peaks["l2_byte_store_gps"], 2), "unit": "Gstore/s",
                             "frac": round(args.pkts / ingest_avg / 1e6 / peaks["l2_byte_store_gps"], 3),
-                            "note": ("one %s per pair against random 1-byte stores into a 64 MiB buffer; time "
-                                     "includes the slide's PreserveAT"
+                            "note": ("one %s per pair against random 1-byte stores into a 64 MiB buffer (fastest of "
+                                     "%d launch shapes: %s); time includes the slide's PreserveAT"
                                      % ("1-byte SetAT store" if at_width == 8 and not args.at_bits else
                                         "2-byte SetAT store" if not args.at_bits else
-                                        "SetAT of a %d-bit field (atomicAnd + atomicOr)" % args.at_bits))},
+                                        "SetAT of a %d-bit field (atomicAnd + atomicOr)" % args.at_bits,
+                                        peaks["shapes_tried"], peaks["byte_store_shape"]))},
+        "roofline_census": {"bound": "l2_stream", "achieved": round(pool_mib * 2**20 / statistics.mean(census_ms)
+                                                                     / 1e6, 1),
+                            "peak": round(peaks["l2_stream_read_gbs"], 1), "unit": "GB/s",
+                            "frac": round(pool_mib * 2**20 / statistics.mean(census_ms) / 1e6
+                                          / peaks["l2_stream_read_gbs"], 3),
+                            "note": "the pool read once per close against one coalesced read of a 64 MiB buffer "
+                                    "(vate_probe_stream_read, fastest of %d launch shapes: %s); time includes the "
+                                    "census's launch and its publication of the 2k + 1 counters"
+                                    % (peaks["shapes_tried"], peaks["stream_read_shape"])},
         "gpu_launches": int(launches),
         "clocks": clock_info,
         "wall_bracket_s": round(t1 - t0, 4),
@@ -954,32 +990,22 @@ def run_learned_kernels(args):
 
 
 def run_probes(args):
-    """Random 32-byte sector reads (vate_probe_sector_read, lane pairs per
-    sector as in the gather) from buffers of 8 MiB to 256 MiB: where the L2
-    rate gives way to the HBM one.  2^27 sectors per launch, best of 5 after
-    2 warm-up launches."""
+    """The three probe patterns (vate_probe_*) against the working-set size, 8 to
+    256 MiB: where the L2 rates give way to the HBM ones.  Each figure is the
+    fastest over accesses in flight per thread x blocks per SM (probe_peaks)."""
     import torch
-    import paper_1812_00282_b300 as V
     torch.cuda.set_device(0)
-    sink = torch.zeros(4, dtype=torch.int32, device="cuda")
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    n = 1 << 27
-    rates = {}
+    out = {}
     for mib in (8, 16, 32, 64, 128, 256):
-        buf = torch.zeros(mib << 20, dtype=torch.uint8, device="cuda")
-        for _ in range(2):
-            V.vate_probe_sector_read(buf, n, sink)
-        best = float("inf")
-        for _ in range(5):
-            ev[0].record()
-            V.vate_probe_sector_read(buf, n, sink)
-            ev[1].record()
-            torch.cuda.synchronize()
-            best = min(best, ev[0].elapsed_time(ev[1]))
-        rates["%d MiB" % mib] = round(32 * n / best / 1e6, 1)
-        del buf
-    return {"workload": "random 32-byte sector reads against the working-set size", "unit": "GB/s",
-            "sector_read_gbs": rates}
+        p = probe_peaks(torch, mib << 20)
+        out["%d MiB" % mib] = {"sector_read_gbs": round(p["l2_sector_read_gbs"], 1),
+                               "sector_read_shape": p["sector_read_shape"],
+                               "byte_store_gps": round(p["l2_byte_store_gps"], 2),
+                               "byte_store_shape": p["byte_store_shape"],
+                               "stream_read_gbs": round(p["l2_stream_read_gbs"], 1),
+                               "stream_read_shape": p["stream_read_shape"]}
+    return {"workload": "memory-system probes against the working-set size (best over 1-8 accesses in flight per "
+                        "thread x 2-32 blocks of 256 threads per SM)", "rates": out}
 
 
 def run_ingest_mix(args):
@@ -1025,8 +1051,88 @@ def run_ingest_mix(args):
             "pairs": n, "distinct_pairs": int(uniq.numel()), "unit": "us per launch", "times": res}
 
 
+def run_placement(args, seg_lens=(1, 4, 8, 16, 32, 64), n_slices=40):
+    """The placement of a host's virtual ATs at the 40 Gb/s shape (2^26-AT pool,
+    g = 4096, k = k' = 10, 5M pairs per slice, all 2^20 hosts estimated per
+    close): for each segment length L, the gather + Eq. 11 time, the close
+    latency (census + gather + Eq. 11) and the ingest time over the closes of
+    slices k..n_slices-1, and the mean relative error |max(est, 0) - n| / n
+    against the exact window cardinality n of every host active in the window
+    (distinct (aip, bip) keys of the last k slices, sort-unique on the device),
+    over n >= 1 and n >= 100, pooled over those closes.  L = 1 is the paper's
+    fully random H (Sec. 4.1); larger L place L consecutive VATs of a host in
+    one pool segment."""
+    import collections
+    import torch
+    import paper_1812_00282_b300 as V
+    from paper_1812_00282_b300.learned import exact_window_counts
+    from traffic import LINK40G, DeviceTraffic, Traffic
+    torch.cuda.set_device(0)
+    k = args.k
+    tr = Traffic(LINK40G, pkts_per_slice=args.pkts)
+    dt = DeviceTraffic(tr)
+    hosts = dt.hosts()
+    hkey = hosts.to(torch.int64) & 0xFFFFFFFF
+    n_h = hosts.numel()
+    out = torch.empty(n_h, dtype=torch.float32, device="cuda")
+    fl = torch.empty(n_h, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    rows = {}
+    for L in seg_lens:
+        mon = V.Vate(C, k, G, L, 0, seed=0xC2, options=V.VATE_OPT_PERSIST_L2)
+        window = collections.deque(maxlen=k)
+        ing, cen, gat, clo = [], [], [], []
+        err = {1: [0.0, 0], 100: [0.0, 0]}
+        sat = 0
+        for s in range(n_slices):
+            p = dt.slice_pairs(s)
+            window.append(p)
+            flush.fill_(s & 0xFF)
+            ev[0].record()
+            mon.ingest(p, s)
+            ev[1].record()
+            mon.close_slice(s)
+            ev[2].record()
+            mon.estimate(hosts, k, out, fl)
+            ev[3].record()
+            torch.cuda.synchronize()
+            if s < k:
+                continue
+            ing.append(ev[0].elapsed_time(ev[1]))
+            cen.append(ev[1].elapsed_time(ev[2]))
+            gat.append(ev[2].elapsed_time(ev[3]))
+            clo.append(ev[1].elapsed_time(ev[3]))
+            uh, cnt = exact_window_counts(window)
+            pos = torch.searchsorted(uh, hkey).clamp_(max=uh.numel() - 1)
+            n = torch.where(uh[pos] == hkey, cnt[pos], torch.zeros_like(cnt[pos])).to(torch.float64)
+            e = torch.clamp(out.to(torch.float64), min=0.0)
+            for lo in (1, 100):
+                m = n >= lo
+                err[lo][0] += float((torch.abs(e[m] - n[m]) / n[m]).sum().item())
+                err[lo][1] += int(m.sum().item())
+            sat += int(((fl & V.VATE_FLAG_SAT) != 0).sum().item())
+        mon.close()
+        rows["L=%d" % L] = {
+            "gather_ms": round(statistics.mean(gat), 4), "census_ms": round(statistics.mean(cen), 4),
+            "ingest_ms": round(statistics.mean(ing), 4),
+            "close_p50_ms": round(float(np.percentile(clo, 50)), 4),
+            "close_p99_ms": round(float(np.percentile(clo, 99)), 4),
+            "mre_n>=1": round(err[1][0] / max(1, err[1][1]), 5), "hosts_n>=1": err[1][1],
+            "mre_n>=100": round(err[100][0] / max(1, err[100][1]), 5), "hosts_n>=100": err[100][1],
+            "saturated_estimates": sat}
+    return {"workload": "VAT placement at the 40 Gb/s shape: 2^26-AT pool, g = 4096, k = k' = %d, %d pkts per slice, "
+                        "all %d hosts estimated at each of %d closes (slices %d..%d)"
+                        % (k, args.pkts, n_h, n_slices - k, k, n_slices - 1),
+            "error": "mean of |max(est, 0) - n| / n over hosts active in the window, pooled over the closes; n = "
+                     "exact distinct peers in the last k slices", "rows": rows}
+
+
 def main():
     args = parse()
+    if args.workload == "placement":
+        print(json.dumps(run_placement(args)), flush=True)
+        return
     if args.workload == "ingest-mix":
         print(json.dumps(run_ingest_mix(args)), flush=True)
         return

@@ -11,7 +11,7 @@ import importlib
 _BINDING = "paper_1812_00282_b300.vate"
 
 
-_SUBMODULES = ("build", "vate", "learned", "serving", "sharded")
+_SUBMODULES = ("build", "vate", "learned", "serving", "sharded", "probe")
 
 
 def __getattr__(name):

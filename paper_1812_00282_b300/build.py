@@ -1,9 +1,10 @@
-"""Build ``libvate.so`` in-tree with nvcc for sm_103a (B300).
+"""Build ``libvate.so`` and the measurement library ``libvate_probe.so``
+in-tree with nvcc for sm_103a (B300).
 
     python -m paper_1812_00282_b300.build [--force] [--verbose]
 
-The library is plain C ABI (include/vate.h); the Python binding loads it with
-ctypes.  Only the sm_103a cubin is generated (no PTX, no other targets).
+The libraries are plain C ABI (include/vate*.h); the Python bindings load them
+with ctypes.  Only the sm_103a cubin is generated (no PTX, no other targets).
 """
 from __future__ import annotations
 
@@ -17,7 +18,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libvate.so")
-SOURCES = ["vate_api.cu", "vate_kernels.cu", "vate_packed.cu", "vate_probe.cu", "vate_noalloc.cu", "vate_group.cu", "vate_learned.cu", "vate_server.cu"]
+SOURCES = ["vate_api.cu", "vate_kernels.cu", "vate_packed.cu", "vate_noalloc.cu", "vate_group.cu", "vate_learned.cu",
+           "vate_server.cu"]
+PROBE_LIB = os.path.join(HERE, "libvate_probe.so")   # memory-system probes for the benchmark (include/vate_probe.h)
+PROBE_SOURCES = ["vate_probe.cu"]
 HEADERS = ["vate_device.cuh", "vate_device_ops.cuh", "vate_ages.cuh", "vate_launch.cuh", "vate_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -29,27 +33,31 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the VATE CUDA library cannot be built")
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib, sources) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + \
+    t = os.path.getmtime(lib)
+    deps = [os.path.join(CSRC, f) for f in sources + HEADERS] + \
         [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
+def _compile(lib, sources, verbose):
+    tmp = lib + ".tmp%d" % os.getpid()
     extra = os.environ.get("VATE_NVCC_DEFINES", "").split()
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-shared", *extra,
-           "-I", INCLUDE, "-I", CSRC, "-o", tmp] + [os.path.join(CSRC, f) for f in SOURCES]
+           "-I", INCLUDE, "-I", CSRC, "-o", tmp] + [os.path.join(CSRC, f) for f in sources]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
         print(" ".join(cmd))
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    for lib, sources in ((LIB, SOURCES), (PROBE_LIB, PROBE_SOURCES)):
+        if force or _stale(lib, sources):
+            _compile(lib, sources, verbose)
     return LIB
 
 

@@ -128,8 +128,6 @@ def _load() -> C.CDLL:
         "vate_server_wait": (i, [vp, u64, u32]),
         "vate_server_drain": (i, [vp, u32]),
         "vate_server_get_stats": (i, [vp, P(vate_server_stats), i]),
-        "vate_probe_sector_read": (i, [vp, u64, u64, vp, vp]),
-        "vate_probe_byte_write": (i, [vp, u64, u64, vp]),
         "vate_create_shard": (i, [P(vate_params), u64, u64, vp, P(vp)]),
         "vate_estimate_from_counts": (i, [P(vate_params), vp, vp, u64, u32, vp, vp, vp]),
         "vate_checkpoint_size": (i, [vp, P(u64)]),
@@ -349,19 +347,6 @@ def vate_census_noalloc(params: vate_params, pool, bact0: int, hist, stream=None
     ph = _dev(hist, hist.dtype if hist.dtype in (torch.int64, torch.uint64) else torch.int64, "hist",
               2 * params.k + 1)
     _check(_lib.vate_census_noalloc(C.byref(params), pp, bact0, ph, _stream(stream)))
-
-
-def vate_probe_sector_read(buf, n_sectors: int, sink, stream=None) -> None:
-    """Random 32-byte sector reads from a CUDA uint8 buffer (include/vate_probe.h)."""
-    import torch
-    _check(_lib.vate_probe_sector_read(_dev(buf, torch.uint8, "buf"), buf.numel(), n_sectors,
-                                       _dev(sink, sink.dtype, "sink"), _stream(stream)))
-
-
-def vate_probe_byte_write(buf, n_writes: int, stream=None) -> None:
-    """Random 1-byte stores into a CUDA uint8 buffer (include/vate_probe.h)."""
-    import torch
-    _check(_lib.vate_probe_byte_write(_dev(buf, torch.uint8, "buf"), buf.numel(), n_writes, _stream(stream)))
 
 
 # ---- learned estimator (include/vate_learned.h) -------------------------------

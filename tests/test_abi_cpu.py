@@ -23,10 +23,12 @@ def V():
     return V
 
 
-def declared_functions():
+def declared_functions(probe=False):
+    """Functions the headers declare: those of include/vate_probe.h (the
+    measurement library) or those of every other header (libvate.so)."""
     names = []
     for hdr in os.listdir(os.path.join(ROOT, "include")):
-        if not hdr.endswith(".h"):
+        if not hdr.endswith(".h") or (hdr == "vate_probe.h") != probe:
             continue
         text = open(os.path.join(ROOT, "include", hdr)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -41,6 +43,19 @@ def test_library_exports_every_declared_symbol(V):
     for n in names:
         assert hasattr(lib, n), n
         assert hasattr(V, n), "binding lacks " + n
+    assert not any(n.startswith("vate_probe") for n in names)
+
+
+def test_probe_library_exports_its_symbols_and_libvate_does_not(V):
+    from paper_1812_00282_b300 import probe
+    names = declared_functions(probe=True)
+    assert names == ["vate_probe_byte_write", "vate_probe_sector_read", "vate_probe_stream_read"]
+    plib = ctypes.CDLL(probe.LIB_PATH)
+    main = ctypes.CDLL(V.LIB_PATH)
+    for n in names:
+        assert hasattr(plib, n), n
+        assert not hasattr(main, n), n + " is a measurement helper, not part of libvate.so"
+        assert hasattr(probe, n[len("vate_probe_"):]), "binding lacks " + n
 
 
 @pytest.mark.parametrize("bad", [
