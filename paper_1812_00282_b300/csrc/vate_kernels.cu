@@ -306,6 +306,10 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32
 // Eight 16-byte chunks are in flight per thread; the block's sums go into acc
 // with 64-bit atomics and the last block publishes them (census_publish).
 // --------------------------------------------------------------------------
+#ifndef VATE_CENSUS_PLANES_BPS
+#define VATE_CENSUS_PLANES_BPS 2
+#endif
+
 template <int RAW>
 __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ acc,
                                                                 uint64_t *__restrict__ hist,
@@ -351,6 +355,176 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
         if (lane == 0) census_add(acc, RAW ? census_raw_bin(G, bact0, r) : r, s);
     }
     census_publish(acc, hist, ticket, nbins);
+}
+
+// --------------------------------------------------------------------------
+// Census of a byte pool whose stored values fit a 32-bit one-hot mask (the
+// inactive value inact <= 31: frame-0 timestamps and recorders with k <= 15),
+// as bit-sliced (vertical) counters in registers: bit u of plane j is bit j of
+// the number of bytes equal to u that this thread has read.  Each 16-byte
+// chunk enters as sixteen one-hot masks 1 << u (a funnel shift whose amount is
+// the byte's low five bits) through a carry-save adder tree into the planes of
+// weight 1, 2, 4 and 8 (the tree of AgePlanes::add_chunk, 15 adders of two
+// 3-input logic operations); the carries of weight 16 of a batch of eight
+// chunks go through a second tree into the planes of weight 16 .. 2048.  An
+// AT so costs about two shifts and two logic operations, where
+// census_kernel<1> spends a byte extract, a clamp and a shared-memory atomic.
+// The planes hold up to 4095 per value; every CP_FOLD_BATCHES batches and at
+// the end the warp sums them (warp_fold: each plane transposed over the warp
+// as a 32 x 32 bit matrix, so that lane u holds bit u of every lane, then one
+// popcount per plane), lane u adds the warp's count of value u to the block's,
+// and the block's counts, relabelled as census bins (census_raw_bin), go into
+// acc; census_publish ends it.  The loop runs the same number of trips in
+// every lane of a warp (lanes past the end count nothing), so that the
+// shuffles of warp_fold see the whole warp.
+// CLAMP: bytes above inact are counted as inact (a recorder pool may come from
+// a caller); a frame-0 timestamp pool of the library never holds them.
+// --------------------------------------------------------------------------
+constexpr int CP_THREADS = 256;
+constexpr int CP_BATCH = 8;                    // chunks loaded per thread per trip (all issued before any use)
+constexpr int CP_FOLD_BATCHES = 31;            // 31 batches x 8 chunks x 16 ATs = 3968 <= 4095 per value
+
+struct CensusPlanes {
+    uint32_t lo[4] = {0, 0, 0, 0};             // weights 1, 2, 4, 8
+    uint32_t hi[8] = {0, 0, 0, 0, 0, 0, 0, 0}; // weights 16, 32, ..., 2048
+
+    // the tree of one chunk into lo; returns the chunk's carry of weight 16
+    __device__ __forceinline__ uint32_t add_chunk(uint4 w) {
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+        uint32_t m[16];
+#pragma unroll
+        for (int b = 0; b < 16; b++) m[b] = __funnelshift_l(0u, 1u, words[b >> 2] >> (8 * (b & 3)));
+        uint32_t twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;
+        csa(twosA, lo[0], lo[0], m[0], m[1]);
+        csa(twosB, lo[0], lo[0], m[2], m[3]);
+        csa(foursA, lo[1], lo[1], twosA, twosB);
+        csa(twosA, lo[0], lo[0], m[4], m[5]);
+        csa(twosB, lo[0], lo[0], m[6], m[7]);
+        csa(foursB, lo[1], lo[1], twosA, twosB);
+        csa(eightsA, lo[2], lo[2], foursA, foursB);
+        csa(twosA, lo[0], lo[0], m[8], m[9]);
+        csa(twosB, lo[0], lo[0], m[10], m[11]);
+        csa(foursA, lo[1], lo[1], twosA, twosB);
+        csa(twosA, lo[0], lo[0], m[12], m[13]);
+        csa(twosB, lo[0], lo[0], m[14], m[15]);
+        csa(foursB, lo[1], lo[1], twosA, twosB);
+        csa(eightsB, lo[2], lo[2], foursA, foursB);
+        csa(sixteens, lo[3], lo[3], eightsA, eightsB);
+        return sixteens;
+    }
+    // the eight carries of weight 16 of one batch into hi
+    __device__ __forceinline__ void add_batch_carries(const uint32_t (&s)[CP_BATCH]) {
+        uint32_t t32A, t32B, t64A, t64B, t128;
+        csa(t32A, hi[0], hi[0], s[0], s[1]);
+        csa(t32B, hi[0], hi[0], s[2], s[3]);
+        csa(t64A, hi[1], hi[1], t32A, t32B);
+        csa(t32A, hi[0], hi[0], s[4], s[5]);
+        csa(t32B, hi[0], hi[0], s[6], s[7]);
+        csa(t64B, hi[1], hi[1], t32A, t32B);
+        csa(t128, hi[2], hi[2], t64A, t64B);
+        uint32_t c = t128;                          // ripple into 128 .. 2048
+#pragma unroll
+        for (int j = 3; j < 8; j++) {
+            const uint32_t t = hi[j] & c;
+            hi[j] ^= c;
+            c = t;
+        }
+    }
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int j = 0; j < 4; j++) lo[j] = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) hi[j] = 0;
+    }
+};
+
+// Transpose of a 32 x 32 bit matrix held one row per lane (row i = lane i's
+// word): afterwards lane u holds column u, bit i = bit u of row i.  Five
+// rounds, each swapping the off-diagonal s x s blocks of lane pairs (lane,
+// lane ^ s).  Called by all 32 lanes.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, uint32_t lane) {
+    const uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int r = 0; r < 5; r++) {
+        const uint32_t sft = 16u >> r;
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, sft);
+        const bool upper = (lane & sft) != 0u;
+        const uint32_t keep = upper ? ~M[r] : M[r];            // the bits this lane keeps
+        const uint32_t t = upper ? (y >> sft) : (y << sft);     // the partner's block moved into place
+        x = (x & keep) | (t & ~keep);
+    }
+    return x;
+}
+
+// The warp's total count of value u (lane u) in the planes of its 32 lanes.
+__device__ __forceinline__ uint32_t warp_fold(const CensusPlanes &cp, uint32_t lane) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) t += (uint32_t)__popc(warp_transpose32(cp.lo[j], lane)) << j;
+#pragma unroll
+    for (int j = 0; j < 8; j++) t += (uint32_t)__popc(warp_transpose32(cp.hi[j], lane)) << (4 + j);
+    return t;
+}
+
+template <bool CLAMP>
+__global__ void __launch_bounds__(CP_THREADS) census_planes_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ acc,
+                                                                   uint64_t *__restrict__ hist,
+                                                                   unsigned int *__restrict__ ticket) {
+    __shared__ uint32_t blk[32];                                // the block's count of each stored value
+    if (threadIdx.x < 32) blk[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t inact = G.counter == 1u ? G.k : G.twok;     // <= 31 here
+    const uint32_t pat = inact * ONES;                          // 16 inactive ATs
+    const uint64_t n16 = G.hi >> 4;                             // chunks of the positions held, [lo, hi)
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
+    CensusPlanes cp;
+    uint32_t runs = 0;                                          // chunks of 16 inactive ATs
+    uint32_t total = 0;                                         // lane u: the warp's folded count of value u
+    uint32_t batches = 0;
+    // lane 0's chunk bounds the loop, so that every lane of the warp makes the same trips
+    for (uint64_t q0 = (G.lo >> 4) + blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); q0 < n16;
+         q0 += CP_BATCH * stride) {
+        const uint64_t q = q0 + lane;
+        uint4 w[CP_BATCH];
+#pragma unroll
+        for (int b = 0; b < CP_BATCH; b++) {
+            const uint64_t qb = q + (uint64_t)b * stride;
+            w[b] = qb < n16 ? __ldcg(pool16 + qb) : make_uint4(pat, pat, pat, pat);
+        }
+        uint32_t s[CP_BATCH];
+#pragma unroll
+        for (int b = 0; b < CP_BATCH; b++) {
+            s[b] = 0u;
+            if (q + (uint64_t)b * stride >= n16) continue;      // beyond the pool: not counted
+            uint4 c = w[b];
+            if (CLAMP) {
+                c.x = swar_clamp(c.x, inact);
+                c.y = swar_clamp(c.y, inact);
+                c.z = swar_clamp(c.z, inact);
+                c.w = swar_clamp(c.w, inact);
+            }
+            if (c.x == pat && c.y == pat && c.z == pat && c.w == pat) {
+                runs++;
+                continue;
+            }
+            s[b] = cp.add_chunk(c);
+        }
+        cp.add_batch_carries(s);
+        if (++batches == CP_FOLD_BATCHES) {                     // the same trip in every lane
+            total += warp_fold(cp, lane);
+            cp.clear();
+            batches = 0;
+        }
+    }
+    total += warp_fold(cp, lane);
+    runs = __reduce_add_sync(0xFFFFFFFFu, runs);
+    if (lane == inact) total += 16u * runs;
+    if (lane <= inact && total) atomicAdd(&blk[lane], total);
+    __syncthreads();
+    if (threadIdx.x <= inact) census_add(acc, census_raw_bin(G, bact0, threadIdx.x), blk[threadIdx.x]);
+    census_publish(acc, hist, ticket, G.twok + 1u);
 }
 
 // --------------------------------------------------------------------------
@@ -422,6 +596,91 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
             const uint32_t aip = __shfl_sync(0xFFFFFFFFu, my_aip, j);
             uint32_t cnt = gather_host_vec<CPSL, RB, FULL, W, SHARD>(G, rc, c2k, aip, u1, u2, u3, lane);
             uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
+            if (lane == j) my_A = A;
+        }
+        if (mine < n) write_result<MODE>(G, N0, mine, my_A, out, flags, active);
+    }
+}
+
+// Warp per host for segments of SB = L x AT-width bytes with SB in {2, 4, 8}
+// (L = 2, 4, 8 with byte ATs; L = 1, 2, 4 with 16-bit ones): lane j of a
+// round hashes segment 32 r + j of the host and loads the whole segment with
+// one 2-, 4- or 8-byte load (a segment is aligned to its size and never
+// crosses a 32-byte sector); RB rounds are loaded before any is tested, so
+// RB random sectors are in flight per lane.  CheckAT (ACT = BACT^0 in frame
+// 0) is the SWAR range test of the vector gather on the segment's word(s); a
+// 2-byte segment is widened to a word with inactive values (2k) in the other
+// half.  For these L a host's g VATs span g / L sectors, and the kernel is
+// bound by the L2's random-sector rate.
+template <int SB, int W, bool SHARD>
+__device__ __forceinline__ uint32_t gather_host_seg(const Geom &G, const RangeConsts &rc, uint32_t c2k, uint32_t pad,
+                                                    uint32_t aip, uint32_t lane) {
+    constexpr int RB = SB == 8 ? 4 : 8;                  // segments in flight per lane
+    constexpr int NW = SB == 8 ? 2 : 1;                  // words per segment
+    const uint32_t nseg = G.g >> G.log2L;
+    const uint64_t hk = host_key(G, aip);
+    uint32_t cnt = 0;
+    for (uint32_t r0 = 0; r0 < nseg; r0 += 32u * RB) {
+        uint32_t w[RB][NW];
+#pragma unroll
+        for (int rb = 0; rb < RB; rb++) {
+            const uint32_t sg = r0 + 32u * rb + lane;
+            bool valid = sg < nseg;
+            const uint32_t pos = valid ? seg_base_k(G, hk, sg) : 0u;      // first AT of the segment
+            if (SHARD) valid = valid && pos >= G.lo && pos < G.hi;        // another shard's segment
+            const uint8_t *at = G.pool + (uint64_t)pos * W;
+#pragma unroll
+            for (int q = 0; q < NW; q++) w[rb][q] = pad;
+            if (valid) {
+                if (SB == 2) {
+                    w[rb][0] = (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(at)) | (pad & 0xFFFF0000u);
+                } else if (SB == 4) {
+                    w[rb][0] = __ldg(reinterpret_cast<const uint32_t *>(at));
+                } else {
+                    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(at));
+                    w[rb][0] = v.x;
+                    w[rb][NW - 1] = v.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int rb = 0; rb < RB; rb++) {
+#pragma unroll
+            for (int q = 0; q < NW; q++)
+                cnt += (uint32_t)__popc(W == 1 ? swar_active(w[rb][q], rc, c2k) : swar16_active(w[rb][q], rc, c2k));
+        }
+    }
+    return cnt;
+}
+
+template <int MODE, int SB, int W, bool SHARD>
+__global__ void __launch_bounds__(GATHER_THREADS) gather_seg_kernel(Geom G, uint32_t bact0, uint32_t kprime,
+                                                                    const uint64_t *__restrict__ hist,
+                                                                    const uint32_t *__restrict__ aips, uint64_t n,
+                                                                    float *__restrict__ out,
+                                                                    uint8_t *__restrict__ flags,
+                                                                    uint32_t *__restrict__ active) {
+    __shared__ uint64_t sN0;
+    const RangeConsts rc = W == 1 ? (G.counter == 1u ? dr_range_consts(kprime) : range_consts(bact0, kprime, G.twok))
+                                  : (G.counter == 1u ? dr_range_consts16(kprime)
+                                                     : range_consts16(bact0, kprime, G.twok));
+    if (MODE == GATHER_ESTIMATE && threadIdx.x == 0) sN0 = pool_inactive(hist, G.P, kprime);
+    __syncthreads();
+    const uint64_t N0 = (MODE == GATHER_ESTIMATE) ? sN0 : 0;
+    const uint32_t c2k = W == 1 ? (128u - G.twok) * ONES : (0x8000u - G.twok) * ONES16;
+    const uint32_t pad = W == 1 ? G.twok * ONES : G.twok * ONES16;   // never active (2k: inactive; above k' for recorders)
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    // 32 hosts per warp at a time, lane j keeping host j's count (as gather_vec_kernel)
+    for (uint64_t g0 = warp0; g0 < n; g0 += 32 * nwarps) {
+        const uint64_t mine = g0 + (uint64_t)lane * nwarps;
+        const uint32_t my_aip = mine < n ? aips[mine] : 0u;
+        uint32_t my_A = 0;
+        for (uint32_t j = 0; j < 32u; j++) {
+            if (g0 + (uint64_t)j * nwarps >= n) break;
+            const uint32_t aip = __shfl_sync(0xFFFFFFFFu, my_aip, j);
+            const uint32_t A = __reduce_add_sync(0xFFFFFFFFu, gather_host_seg<SB, W, SHARD>(G, rc, c2k, pad, aip, lane));
             if (lane == j) my_A = A;
         }
         if (mine < n) write_result<MODE>(G, N0, mine, my_A, out, flags, active);
@@ -614,7 +873,18 @@ cudaError_t launch_census(const Geom &G, uint32_t bact0, uint64_t *acc, int sms,
         return launch_pool(G, census16_kernel, sms * 4, CENSUS_THREADS,
                            (size_t)(CENSUS_THREADS / 32) * (G.twok + 1) * sizeof(uint32_t), st, G, bact0, acc, hist,
                            ticket);
-    // byte pools: up to four blocks per SM, as many as their lane-column
+    // byte pools whose stored values fit a 32-bit one-hot mask (k <= 15):
+    // bit-sliced counters, two blocks of 256 threads per SM so that a thread
+    // reads enough chunks to pay for reading its planes out
+    const uint32_t inact = G.counter == 1u ? G.k : G.twok;
+    if ((G.frame0 || G.counter == 1u) && inact <= 31u) {
+        if (G.counter == 1u)
+            return launch_pool(G, census_planes_kernel<true>, sms * VATE_CENSUS_PLANES_BPS, CP_THREADS, 0, st, G,
+                               bact0, acc, hist, ticket);
+        return launch_pool(G, census_planes_kernel<false>, sms * VATE_CENSUS_PLANES_BPS, CP_THREADS, 0, st, G, bact0,
+                           acc, hist, ticket);
+    }
+    // other byte pools: up to four blocks per SM, as many as their lane-column
     // histograms fit in about 200 KiB of shared memory (one for k = 63)
     const size_t smem = census_smem_bytes(G.twok);
     const int per_sm = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)(200u << 10) / smem));
@@ -679,6 +949,29 @@ cudaError_t launch_gather(int mode, const Geom &G, uint32_t bact0, uint32_t kpri
         }
 #undef VATE_GATHER_LAUNCH
 #undef VATE_GATHER_VEC
+    } else if (seg_bytes == 2 || seg_bytes == 4 || seg_bytes == 8) {
+#define VATE_GATHER_SEG(SB, W)                                                                                    \
+    do {                                                                                                          \
+        if (sharded)                                                                                              \
+            e = launch_pool(G, gather_seg_kernel<GATHER_ACTIVE, SB, W, true>, grid, GATHER_THREADS, 0, st, G, bact0,  \
+                            kprime, hist, aips, n, out, flags, active);                                           \
+        else if (mode == GATHER_ESTIMATE)                                                                         \
+            e = launch_pool(G, gather_seg_kernel<GATHER_ESTIMATE, SB, W, false>, grid, GATHER_THREADS, 0, st, G,      \
+                            bact0, kprime, hist, aips, n, out, flags, active);                                    \
+        else                                                                                                      \
+            e = launch_pool(G, gather_seg_kernel<GATHER_ACTIVE, SB, W, false>, grid, GATHER_THREADS, 0, st, G,        \
+                            bact0, kprime, hist, aips, n, out, flags, active);                                    \
+    } while (0)
+        if (G.atw == 1u) {
+            if (seg_bytes == 2) VATE_GATHER_SEG(2, 1);
+            else if (seg_bytes == 4) VATE_GATHER_SEG(4, 1);
+            else VATE_GATHER_SEG(8, 1);
+        } else {
+            if (seg_bytes == 2) VATE_GATHER_SEG(2, 2);
+            else if (seg_bytes == 4) VATE_GATHER_SEG(4, 2);
+            else VATE_GATHER_SEG(8, 2);
+        }
+#undef VATE_GATHER_SEG
     } else {
         if (mode == GATHER_ESTIMATE)
             e = launch_pool(G, gather_scalar_kernel<GATHER_ESTIMATE>, grid, GATHER_THREADS, 0, st, G, bact0, kprime, hist,
