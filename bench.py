@@ -72,7 +72,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=295)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--seg-len", type=int, default=32)
+    ap.add_argument("--seg-len", type=int, default=2,
+                    help="VATs per pool segment: 2 is the smallest that meets the 10 ms close target at 2^20 "
+                         "hosts (1 is the paper's random H; 32 is 14x faster at 2.4x the error, --workload placement)")
     ap.add_argument("--partition", type=int, default=0)
     ap.add_argument("--k", type=int, default=K_WIN,
                     help="window in slices (the 40 Gb/s workload uses 10; the paper's long window is 300)")
@@ -297,6 +299,52 @@ def probe_peaks(torch, pool_bytes: int, sweep=True):
             "buffer_mib": pool_bytes >> 20, "shapes_tried": len(shapes)}
 
 
+def accuracy_at_closes(torch, V, dt, hosts, args, first_slice, n_closes=3):
+    """Mean relative error |max(est, 0) - n| / n of every host's Eq. 11 estimate
+    against its exact window cardinality n (distinct (aip, bip) keys of the
+    last k slices, sort-unique on the device), over hosts with n >= 1 and
+    n >= 100, pooled over n_closes closes after a full window: for this run's
+    segment length and, on the same slices, for L = 1 (the paper's random H)."""
+    import collections
+    from paper_1812_00282_b300.learned import exact_window_counts
+    k = args.k
+    lens = [args.seg_len] + ([1] if args.seg_len != 1 else [])
+    hs = [V.Vate(C, k, G, L, args.partition, seed=0xACC, at_bits=args.at_bits if L == args.seg_len else 0)
+          for L in lens]
+    out = torch.empty(hosts.numel(), dtype=torch.float32, device="cuda")
+    hkey = hosts.to(torch.int64) & 0xFFFFFFFF
+    err = {L: {1: [0.0, 0], 100: [0.0, 0]} for L in lens}
+    window = collections.deque(maxlen=k)
+    for i in range(k + n_closes - 1):
+        s = first_slice + i
+        p = dt.slice_pairs(s)
+        window.append(p)
+        for h in hs:
+            h.ingest(p, s)
+        if i < k - 1:
+            continue
+        uh, cnt = exact_window_counts(window)
+        pos = torch.searchsorted(uh, hkey).clamp_(max=uh.numel() - 1)
+        n = torch.where(uh[pos] == hkey, cnt[pos], torch.zeros_like(cnt[pos])).to(torch.float64)
+        for L, h in zip(lens, hs):
+            h.close_slice(s)
+            h.estimate(hosts, k, out)
+            e = torch.clamp(out.to(torch.float64), min=0.0)
+            for lo in (1, 100):
+                m = n >= lo
+                err[L][lo][0] += float((torch.abs(e[m] - n[m]) / n[m]).sum().item())
+                err[L][lo][1] += int(m.sum().item())
+    for h in hs:
+        h.close()
+    res = {"closes": n_closes, "how": "|max(est, 0) - n| / n against exact window counts (sort-unique on the "
+                                      "device), every host with n >= 1 (n >= 100), pooled over the closes"}
+    for L in lens:
+        key = "seg_len_%d" % L + (" (this run)" if L == args.seg_len else " (the paper's random H)")
+        res[key] = {"mre_n>=1": round(err[L][1][0] / max(1, err[L][1][1]), 5), "hosts_n>=1": err[L][1][1],
+                    "mre_n>=100": round(err[L][100][0] / max(1, err[L][100][1]), 5), "hosts_n>=100": err[L][100][1]}
+    return res
+
+
 def close_latency_loop(torch, mon, dt, hosts, out, flags, k, first_slice, flush, no_flush, n=200):
     """Slice-close latency over n closes in a loop of their own (independent of
     --steps): each close follows the ingest of a fresh slice (generated and
@@ -386,6 +434,7 @@ def run_ours(args, rank, world, local):
     clock_info = clocks.stop()
     close_loop = close_latency_loop(torch, mon, dt, hosts, out, flags, args.k, W + K, flush, args.no_flush,
                                     n=max(200, K))
+    accuracy = accuracy_at_closes(torch, V, dt, hosts, args, W + K + max(200, K)) if rank == 0 else None
 
     step_ms = [e0[i].elapsed_time(e3[i]) for i in range(K)]
     ingest_ms = [e0[i].elapsed_time(e1[i]) for i in range(K)]
@@ -397,30 +446,36 @@ def run_ours(args, rank, world, local):
     total_pkts = sum_over_ranks(float(K * args.pkts), world)
     value = total_pkts / dev_ms_max / 1e3       # packets per ms / 1e3 = Mpkt/s
 
-    # roofline of the dominant kernel: the gather (one 32-B sector per segment)
+    # roofline of the dominant kernel: the gather.  Its unit of work is one
+    # random segment read, which moves whole 32-byte L2 sectors: g / L segments
+    # per host, ceil(L x AT bytes / 32) sectors each (L <= 32 byte ATs: one)
     gather_avg = statistics.mean(gather_ms)
-    vat_bytes = n_h * G * (1 if args.k <= 63 else 2)          # one or two bytes per AT
+    atb = 1 if args.k <= 63 else 2                            # bytes per AT
+    vat_bytes = n_h * G * atb                                 # the VATs themselves
     if args.at_bits:
         vat_bytes = n_h * G * args.at_bits // 8                  # the packed fields the VATs occupy
-    achieved = vat_bytes / gather_avg / 1e6     # GB/s
+    seg_sectors = max(1, (args.seg_len * atb + 31) // 32)
+    sectors = n_h * (G // args.seg_len) * seg_sectors
+    gkernel = ("gather_seg_kernel" if args.seg_len * atb in (2, 4, 8) else
+               "gather_vec_kernel" if args.seg_len * atb >= 16 else "gather_scalar_kernel")
     # the committed ncu figure is for the default 40 Gb/s workload only
-    default_shape = (args.k == K_WIN and not args.at_bits and args.seg_len == 32 and args.partition == 0
+    default_shape = (args.k == K_WIN and not args.at_bits and args.seg_len == 2 and args.partition == 0
                      and n_h == 1 << 20 and args.pkts == 5_000_000)
-    traffic = committed_traffic("gather_vec_kernel") if default_shape else None
+    traffic = committed_traffic(gkernel) if default_shape else None
     ingest_avg = statistics.mean(ingest_ms)
     mp = measured_peaks()
     hbm = mp.get("hbm_gbs", 6400.0)
     at_width = args.at_bits or (8 if args.k <= 63 else 16)                # bits per AT as stored
     pool_mib = ((1 << C) // (32 // args.at_bits) * 4 if args.at_bits else (1 << C) * at_width // 8) / 2**20
-    if default_shape:
-        roofline_note = ("the 64 MiB pool stays in L2 (persisting window) and the gather reads it 64 times over in "
-                         "random 32-byte sectors, so the bound is L2's random-sector rate, not HBM; traffic = DRAM "
-                         "bytes of one launch with caches flushed first (ncu, profiles/traffic.json), null once the "
-                         "kernel sources change")
-    else:
-        roofline_note = ("the gather reads the %.0f MiB pool in random 32-byte sectors; peak = the L2 random-sector "
-                         "rate on a 64 MiB buffer; a pool larger than the L2's persisting part is read partly from "
-                         "HBM (vs_hbm); traffic is committed for the default shape only" % pool_mib)
+    sector_peak = peaks["l2_sector_read_gbs"] / 32.0           # G sectors/s
+    achieved_sectors = sectors / gather_avg / 1e6              # G sectors/s
+    roofline_note = ("the %.0f MiB pool is state kept in L2 (persisting window); the gather reads it in random "
+                     "32-byte sectors, %d per host (g / L segments of %d sector(s)), so its bound is the L2's random-"
+                     "sector rate, measured by the same access pattern on a 64 MiB buffer; traffic = DRAM bytes "
+                     "of one launch (ncu, profiles/traffic.json) for the default shape, null once the kernel "
+                     "sources change" % (pool_mib, (G // args.seg_len) * seg_sectors, seg_sectors))
+    if args.at_bits:
+        roofline_note += "; packed fields: a segment's words may span more sectors than counted here"
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpkt/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -432,20 +487,24 @@ def run_ours(args, rank, world, local):
         "close_p99_ms": close_loop["p99_ms"],
         "close_latency": {**close_loop, "in_timed_steps": {"p50_ms": round(float(np.percentile(close_ms, 50)), 4),
                                                            "max_ms": round(max(close_ms), 4), "closes": K}},
+        "accuracy": accuracy,
         "ingest_mpkts": round(args.pkts / ingest_avg / 1e3, 1),
         "kernels_ms": {"ingest+preserve": round(ingest_avg, 4), "census": round(statistics.mean(census_ms), 4),
                        "gather+estimate": round(gather_avg, 4)},
-        "roofline": {"bound": "l2", "achieved": round(achieved, 1),
-                     "peak": round(peaks["l2_sector_read_gbs"], 1), "unit": "GB/s",
-                     "frac": round(achieved / peaks["l2_sector_read_gbs"], 3), "traffic": traffic,
-                     "kernel": "gather_vec_kernel",
+        "roofline": {"bound": "l2_sector_rate", "achieved": round(achieved_sectors, 2),
+                     "peak": round(sector_peak, 2), "unit": "Gsector/s",
+                     "frac": round(achieved_sectors / sector_peak, 3), "traffic": traffic, "kernel": gkernel,
                      "peak_source": "random 32-B sector reads from a 64 MiB L2-resident buffer, two threads per "
                                     "sector, measured in this run (vate_probe_sector_read, fastest of %d launch "
-                                    "shapes: %s); no L2 figure in MEASURED_PEAKS.json"
-                                    % (peaks["shapes_tried"], peaks["sector_read_shape"]),
-                     "algorithmic_bytes": "aips x g VATs x AT bytes per launch (%d)" % vat_bytes,
-                     "vs_hbm": {"peak": hbm, "frac": round(achieved / hbm, 3),
-                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                                    "shapes: %s; %.1f GB/s); no L2 figure in MEASURED_PEAKS.json"
+                                    % (peaks["shapes_tried"], peaks["sector_read_shape"],
+                                       peaks["l2_sector_read_gbs"]),
+                     "algorithmic": "aips x g / L segment reads of %d sector(s) per launch (%d sectors); the VATs "
+                                    "themselves are %d bytes" % (seg_sectors, sectors, vat_bytes),
+                     "vs_hbm": {"achieved_gbs": round(vat_bytes / gather_avg / 1e6, 1), "peak": hbm,
+                                "frac": round(vat_bytes / gather_avg / 1e6 / hbm, 3),
+                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured); VAT bytes per launch / "
+                                               "launch time"},
                      "note": roofline_note},
         "roofline_ingest": {"bound": "l2_random_store", "achieved": round(args.pkts / ingest_avg / 1e6, 2),
                             "peak": round(peaks["l2_byte_store_gps"], 2), "unit": "Gstore/s",
@@ -494,7 +553,7 @@ def run_learned(V, torch):
     params = r.pop("params")
     # time both estimators on one closed slice of the same configuration
     dt = DeviceTraffic(Traffic(LINK40G))
-    mon = V.Vate(24, 10, 4096, 32, 0, 0xC4)
+    mon = V.Vate(24, 10, 4096, 2, 0, 0xC4)
     for s in range(11):
         mon.ingest(dt.slice_pairs(s), s)
     mon.close_slice(10)
@@ -935,7 +994,7 @@ def run_pt(args):
 def run_learned_kernels(args):
     """The learned estimator's kernels one by one at close, 2^20 hosts (and
     the per-age counts of vate_age_counts, which hold the same numbers): the
-    40 Gb/s traffic on a 2^24-AT pool (k = 10, g = 4096, L = 32) after 12
+    40 Gb/s traffic on a 2^24-AT pool (k = 10, g = 4096, L = 2) after 12
     slices, a model of 2k + 2 = 22 inputs with weights from vate_mlp_init (the
     cost does not depend on them).  CUDA-event mean of 10 calls after 3
     warm-up calls."""
@@ -945,7 +1004,7 @@ def run_learned_kernels(args):
     torch.cuda.set_device(0)
     dt = DeviceTraffic(Traffic(LINK40G))
     k, c, g = 10, 24, 4096
-    h = V.Vate(c, k, g, 32, 0, 7)
+    h = V.Vate(c, k, g, 2, 0, 7)
     for s in range(12):
         h.ingest(dt.slice_pairs(s), s)
     h.close_slice(11)
@@ -978,7 +1037,7 @@ def run_learned_kernels(args):
           "plain_eq11_estimate": timed(lambda: h.estimate(hosts, k, out, fl))}
     h.close()
     # per-age counts with a longer window, k = 30 (shared-memory counters instead of bit planes)
-    h30 = V.Vate(c, 30, g, 32, 0, 7)
+    h30 = V.Vate(c, 30, g, 2, 0, 7)
     for s in range(12):
         h30.ingest(dt.slice_pairs(s), s)
     h30.close_slice(11)

@@ -6,10 +6,14 @@
  * seed, and runs the per-slice pipeline of Algorithm 4 -- slide (BACT^0 + 1,
  * PreserveAT on the two blocks whose ACT became 0 or k), SetAT for every pair,
  * pool census, CheckAT gather and Eq. 11 for every host -- for all of them in
- * five launches per slice, each a persistent grid working through a table of
- * (monitor, tile) work items.  Every monitor computes exactly what a single
- * vate_handle with the same parameters computes (the same device arithmetic);
- * a monitor's result does not depend on the other monitors in the group.
+ * ONE persistent launch per slice.  Its blocks take (monitor, phase, tile)
+ * work items in order from a device queue, monitor after monitor; an item
+ * starts once the earlier phases of its monitor have finished (a bounded
+ * device-side wait on a per-monitor count of finished items, which can only
+ * wait on items already handed to running blocks).  Every monitor computes
+ * exactly what a single vate_handle with the same parameters computes (the
+ * same device arithmetic); a monitor's result does not depend on the other
+ * monitors in the group.
  *
  * All monitors advance in lock step, one slice per vate_group_step call: the
  * first step is slice 0 (BACT^0 = 0 for every monitor), step s is slice s.
@@ -39,18 +43,22 @@ typedef struct vate_group vate_group;
 /* Status bits recorded by a step (sticky until read with clear = 1). */
 #define VATE_GROUP_BAD_OFFSETS  1u   /* pair or host offsets decreasing or beyond capacity (clamped) */
 #define VATE_GROUP_BAD_KPRIME   2u   /* k' outside [1, k] for some monitor (k used instead)          */
+#define VATE_GROUP_TIMEOUT      4u   /* a device-side wait of a step gave up (see vate_group_set_wait):
+                                        that step is incomplete and the group does no further work --
+                                        destroy it (a checkpoint of each monitor is the way back)      */
 
-/* Tiling of the group kernels, chosen by vate_group_autotune or set by hand.
- *   census_tile_chunks  16-byte chunks per census work item (power of two, 256..65536)
- *   gather_blocks_per_sm, ingest_blocks_per_sm, preserve_blocks_per_sm
- *                       persistent grid sizes, in blocks of 256 threads per SM (1..32)
- *   gather_hosts_per_grab  hosts a warp takes from the work queue at a time (1..64) */
+/* Tiling of the step kernel, chosen by vate_group_autotune or set by hand.
+ *   census_tile_chunks    16-byte chunks per census work item (power of two, 256..65536)
+ *   blocks_per_sm         persistent grid: blocks of 256 threads per SM (1 .. the kernel's occupancy)
+ *   gather_tile_hosts     hosts per gather work item (multiple of 256, 256..65536)
+ *   ingest_tile_pairs     pairs per SetAT work item (multiple of 256, 256..65536)
+ *   preserve_tile_chunks  16-byte chunks per PreserveAT work item (multiple of 256, 256..65536) */
 typedef struct {
     uint32_t census_tile_chunks;
-    uint32_t gather_blocks_per_sm;
-    uint32_t gather_hosts_per_grab;
-    uint32_t ingest_blocks_per_sm;
-    uint32_t preserve_blocks_per_sm;
+    uint32_t blocks_per_sm;
+    uint32_t gather_tile_hosts;
+    uint32_t ingest_tile_pairs;
+    uint32_t preserve_tile_chunks;
     uint32_t reserved;
 } vate_group_tuning;
 
@@ -78,22 +86,23 @@ int vate_group_step(vate_group *g, const vate_pair *d_pairs, const uint64_t *d_p
                     const uint32_t *d_hosts, const uint64_t *d_host_offsets, uint64_t host_capacity,
                     const uint32_t *d_kprime, float *d_out, uint8_t *d_flags, void *stream);
 
-/* The same step as a CUDA graph: the first call (and any call whose buffers or
- * tuning differ from the previous one) captures the five launches on an
- * internal stream and instantiates the graph; every call launches the graph on
- * `stream`.  Refill the same buffers (pairs, offsets, hosts, k') between
- * slices to keep replaying one graph. */
+/* The same step as a CUDA graph: the first call (and any call whose buffers,
+ * tuning or wait settings differ from the previous one) captures the step's
+ * one launch on an internal stream and instantiates the graph; every call
+ * launches the graph on `stream`.  Refill the same buffers (pairs, offsets,
+ * hosts, k') between slices to keep replaying one graph. */
 int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_t *d_pair_offsets,
                           uint64_t pair_capacity, const uint32_t *d_hosts, const uint64_t *d_host_offsets,
                           uint64_t host_capacity, const uint32_t *d_kprime, float *d_out, uint8_t *d_flags,
                           void *stream);
 
-/* Project-written autotuner: after at least one step, re-runs the ingest (a
- * repeat of the same slice's SetATs writes the same values), the census and
- * the gather of that slice on the given inputs under candidate tilings, times
- * each with CUDA events on `stream` (synchronising it), keeps the fastest per
- * kernel, and writes the choice to *chosen (may be NULL).  The monitors' state
- * and the outputs end exactly as the last step left them.
+/* Project-written autotuner: after at least one step, repeats that step (same
+ * slice: a second PreserveAT of the same slide changes nothing, a repeat of
+ * the same SetATs writes the same values, the census and the gather recompute
+ * the same outputs) under candidate tilings -- blocks per SM, census, ingest
+ * and gather tiles -- times each with CUDA events on `stream` (synchronising
+ * it), keeps the fastest and writes it to *chosen (may be NULL).  The
+ * monitors' state and the outputs end exactly as the last step left them.
  * The inputs MUST be exactly those of the last vate_group_step (same pairs,
  * offsets, hosts, host offsets and k'): other pairs would be stamped into the
  * current slice, which is not checked.  On an error the tiling in force on
@@ -106,7 +115,22 @@ int vate_group_autotune(vate_group *g, const vate_pair *d_pairs, const uint64_t 
 int vate_group_set_tuning(vate_group *g, const vate_group_tuning *t);
 int vate_group_get_tuning(const vate_group *g, vate_group_tuning *t);
 
-/* Status bits of the steps since the last clear (synchronises `stream`). */
+/* Bounded waits of the step kernel.  Each work item's wait for the earlier
+ * phases of its monitor sleeps ~128 ns between looks and gives up after
+ * spin_limit looks (default 2^23, about a second; 0 gives up at the first
+ * unsatisfied look): the step then sets VATE_GROUP_TIMEOUT, every later wait
+ * of the launch gives up at once, and the kernel returns instead of hanging.
+ * `missing` > 0 raises every wait's target by that many items, a target no
+ * step can reach: a test of the timeout path that needs no fault.  Both
+ * apply to later steps (a graph is re-captured).  Errors: VATE_EINVAL. */
+int vate_group_set_wait(vate_group *g, uint64_t spin_limit, uint32_t missing);
+
+/* Kernel nodes of the captured step graph (0 before the first
+ * vate_group_step_graph): one, the step's persistent launch. */
+int vate_group_graph_nodes(const vate_group *g, uint32_t *nodes);
+
+/* Status bits of the steps since the last clear (synchronises `stream`);
+ * VATE_GROUP_TIMEOUT is never cleared. */
 int vate_group_status(vate_group *g, uint32_t *status, int clear, void *stream);
 
 /* Per-monitor views for checking: the pool (P_m bytes), the census of the last

@@ -111,6 +111,45 @@ __device__ __forceinline__ void age_counts_vec(const Geom &G, uint32_t bact0, ui
     }
 }
 
+// Segments of SB = 2, 4 or 8 bytes (L = 2, 4, 8 with byte ATs): lane j loads
+// segments 32 q + j of a round with one SB-byte load each (hashing each
+// segment once, as gather_host_seg), 16 / SB of them filling one 16-byte chunk
+// of the planes; missing segments count as inactive ATs.  The rounds are
+// warp-uniform, so the fold (a warp reduction) runs in every lane together.
+template <int SB>
+__device__ __forceinline__ void age_counts_seg(const Geom &G, uint32_t bact0, uint64_t hk, uint32_t lane,
+                                               AgePlanes &ap, uint32_t &cd) {
+    constexpr int SPC = 16 / SB;                                    // segments per chunk
+    const uint32_t nseg = G.g >> G.log2L;
+    const uint32_t none = G.twok * ONES;
+    uint32_t chunks = 0;
+    for (uint32_t r0 = 0; r0 < nseg; r0 += 32u * SPC) {
+        uint32_t words[4] = {none, none, none, none};
+#pragma unroll
+        for (int q = 0; q < SPC; q++) {
+            const uint32_t sg = r0 + 32u * q + lane;
+            if (sg >= nseg) continue;
+            const uint8_t *at = G.pool + seg_base_k(G, hk, sg);     // first AT of the segment (SB-aligned)
+            if (SB == 2) {
+                const uint32_t v = __ldg(reinterpret_cast<const unsigned short *>(at));
+                const int sh = 16 * (q & 1);
+                words[q >> 1] = (words[q >> 1] & ~(0xFFFFu << sh)) | (v << sh);
+            } else if (SB == 4) {
+                words[q] = __ldg(reinterpret_cast<const uint32_t *>(at));
+            } else {
+                const uint2 v = __ldg(reinterpret_cast<const uint2 *>(at));
+                words[2 * q] = v.x;
+                words[2 * q + 1] = v.y;
+            }
+        }
+        ap.add_chunk(make_uint4(words[0], words[1], words[2], words[3]));
+        if (++chunks == 15u) {                                      // at most 240 ATs per lane per value
+            ap.fold(bact0, G.k, G.counter, lane, cd);
+            chunks = 0;
+        }
+    }
+}
+
 // The count of age d (d < k) of one host's VATs, in lane d; 0 in other lanes.
 __device__ __forceinline__ uint32_t host_age_counts(const Geom &G, uint32_t bact0, uint32_t aip, uint32_t lane) {
     AgePlanes ap;
@@ -119,6 +158,9 @@ __device__ __forceinline__ uint32_t host_age_counts(const Geom &G, uint32_t bact
     if (G.L == 16) age_counts_vec<0>(G, bact0, hk, lane, ap, cd);
     else if (G.L == 32) age_counts_vec<1>(G, bact0, hk, lane, ap, cd);
     else if (G.L == 64) age_counts_vec<2>(G, bact0, hk, lane, ap, cd);
+    else if (G.L == 2) age_counts_seg<2>(G, bact0, hk, lane, ap, cd);
+    else if (G.L == 4) age_counts_seg<4>(G, bact0, hk, lane, ap, cd);
+    else if (G.L == 8) age_counts_seg<8>(G, bact0, hk, lane, ap, cd);
     else {                      // one byte per VAT: sixteen VATs per lane make a chunk
         const uint32_t none = G.twok;
         for (uint32_t i0 = 0; i0 < G.g; i0 += 32u * 16u) {

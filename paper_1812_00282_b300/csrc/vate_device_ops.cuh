@@ -170,7 +170,7 @@ __device__ __forceinline__ uint64_t pool_inactive(const uint64_t *hist, uint64_t
 // after each batch.  u1..u3 are run-time ones.
 // SHARD: the pool holds only the positions [lo, hi) (64-aligned, so a
 // segment is wholly inside or outside); segments outside are not read.
-template <int CPSL, int RB, bool FULL, int W = 1, bool SHARD = false>
+template <int CPSL, int RB, bool FULL, int W = 1, bool SHARD = false, bool CG = false>
 __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, const RangeConsts &rc, uint32_t c2k, uint32_t aip,
                                                     uint32_t u1, uint32_t u2, uint32_t u3, uint32_t lane) {
     constexpr int CPS = 1 << CPSL;                      // 16-byte chunks per segment
@@ -202,7 +202,7 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, const RangeCo
                 valid[j] = FULL || c < (segs_here << CPSL);
                 if (SHARD) valid[j] = valid[j] && (q - q_lo) < q_n;
                 w[j] = make_uint4(0u, 0u, 0u, 0u);
-                if (valid[j]) w[j] = __ldg(pool16 + q);
+                if (valid[j]) w[j] = CG ? __ldcg(pool16 + q) : __ldg(pool16 + q);
             }
         }
         uint32_t acc = 0;
@@ -233,11 +233,18 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, const RangeCo
 }
 
 // Active VATs seen by this lane for one host of a frame-0 pool, one AT per
-// load (any L).
+// load (any L).  CG: loads cached in L2 only -- for a pool that other blocks
+// of the same launch have written (the monitor group's single launch), where
+// the read-only path could return a line this SM cached before those writes.
+template <bool CG = false>
 __device__ __forceinline__ uint32_t load_at(const Geom &G, uint32_t pid) {
+    if (CG)
+        return G.atw == 1u ? (uint32_t)__ldcg(G.pool + pid)
+                           : (uint32_t)__ldcg(reinterpret_cast<const uint16_t *>(G.pool) + pid);
     return G.atw == 1u ? (uint32_t)__ldg(G.pool + pid) : (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(G.pool) + pid);
 }
 
+template <bool CG = false>
 __device__ __forceinline__ uint32_t gather_host_scalar(const Geom &G, uint32_t bact0, uint32_t kprime, uint32_t aip,
                                                        uint32_t lane) {
     uint32_t cnt = 0;
@@ -246,12 +253,66 @@ __device__ __forceinline__ uint32_t gather_host_scalar(const Geom &G, uint32_t b
     for (uint32_t i = lane; i < G.g; i += 32u) {
         uint32_t pid = vat_pid_k(G, hk, i);
         if (pid < G.lo || pid >= G.hi) continue;             // another shard's AT
-        uint32_t v = load_at(G, pid);
+        uint32_t v = load_at<CG>(G, pid);
         if (G.counter == 1u) {
             cnt += check_dr(v, kprime) ? 1u : 0u;
             continue;
         }
         cnt += check_at(v, bact0, kprime, G.twok) ? 1u : 0u;
+    }
+    return cnt;
+}
+
+// Warp per host for segments of SB = L x AT-width bytes with SB in {2, 4, 8}
+// (L = 2, 4, 8 with byte ATs; L = 1, 2, 4 with 16-bit ones): lane j of a
+// round hashes segment 32 r + j of the host and loads the whole segment with
+// one 2-, 4- or 8-byte load (a segment is aligned to its size and never
+// crosses a 32-byte sector); RB rounds are loaded before any is tested, so
+// RB random sectors are in flight per lane.  CheckAT (ACT = BACT^0 in frame
+// 0) is the SWAR range test of the vector gather on the segment's word(s); a
+// 2-byte segment is widened to a word with inactive values (2k) in the other
+// half.  For these L a host's g VATs span g / L sectors, and the kernel is
+// bound by the L2's random-sector rate.
+template <int SB, int W, bool SHARD, bool CG = false>
+__device__ __forceinline__ uint32_t gather_host_seg(const Geom &G, const RangeConsts &rc, uint32_t c2k, uint32_t pad,
+                                                    uint32_t aip, uint32_t lane) {
+    constexpr int RB = SB == 8 ? 4 : 8;                  // segments in flight per lane
+    constexpr int NW = SB == 8 ? 2 : 1;                  // words per segment
+    const uint32_t nseg = G.g >> G.log2L;
+    const uint64_t hk = host_key(G, aip);
+    uint32_t cnt = 0;
+    for (uint32_t r0 = 0; r0 < nseg; r0 += 32u * RB) {
+        uint32_t w[RB][NW];
+#pragma unroll
+        for (int rb = 0; rb < RB; rb++) {
+            const uint32_t sg = r0 + 32u * rb + lane;
+            bool valid = sg < nseg;
+            const uint32_t pos = valid ? seg_base_k(G, hk, sg) : 0u;      // first AT of the segment
+            if (SHARD) valid = valid && pos >= G.lo && pos < G.hi;        // another shard's segment
+            const uint8_t *at = G.pool + (uint64_t)pos * W;
+#pragma unroll
+            for (int q = 0; q < NW; q++) w[rb][q] = pad;
+            if (valid) {
+                if (SB == 2) {
+                    const unsigned short *a16 = reinterpret_cast<const unsigned short *>(at);
+                    w[rb][0] = (uint32_t)(CG ? __ldcg(a16) : __ldg(a16)) | (pad & 0xFFFF0000u);
+                } else if (SB == 4) {
+                    const uint32_t *a32 = reinterpret_cast<const uint32_t *>(at);
+                    w[rb][0] = CG ? __ldcg(a32) : __ldg(a32);
+                } else {
+                    const uint2 *a64 = reinterpret_cast<const uint2 *>(at);
+                    const uint2 v = CG ? __ldcg(a64) : __ldg(a64);
+                    w[rb][0] = v.x;
+                    w[rb][NW - 1] = v.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int rb = 0; rb < RB; rb++) {
+#pragma unroll
+            for (int q = 0; q < NW; q++)
+                cnt += (uint32_t)__popc(W == 1 ? swar_active(w[rb][q], rc, c2k) : swar16_active(w[rb][q], rc, c2k));
+        }
     }
     return cnt;
 }

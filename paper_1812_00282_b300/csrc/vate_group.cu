@@ -1,20 +1,32 @@
 // vate_group.cu -- many independent monitors advanced together (include/vate_group.h).
 //
-// One slice of every monitor is five launches, each a persistent grid over a
-// work table that spans all monitors:
-//   group_begin_kernel     slice number + 1 (device-resident), clear the census
-//                          histograms and the work-queue counters
-//   group_preserve_kernel  PreserveAT (Algorithm 3) on each monitor's two blocks
-//                          whose ACT became 0 or k, as (monitor, 16-byte chunk) items
-//   group_ingest_kernel    SetAT for every pair, each pair's monitor found from
-//                          the CSR offsets of the batch
-//   group_census_kernel    census tiles (monitor, chunk range) from a work queue,
-//                          histograms accumulated per monitor
-//   group_gather_kernel    warp per host from a work queue, CheckAT gather and Eq. 11
-// The per-chunk and per-host arithmetic is the one of the single-pool kernels
-// (vate_device_ops.cuh).  Because the slice number, the batch offsets and k'
-// are read on the device, the five launches can be captured once as a CUDA
-// graph and replayed every slice.
+// One slice of every monitor is ONE persistent launch, group_step_kernel.  Its
+// blocks take work items in order from a device queue.  The item list is
+// laid out monitor after monitor, each monitor's items in the order of
+// Algorithm 4's per-slice pipeline:
+//   B  begin: clear the monitor's census histogram                  (1 item)
+//   P  PreserveAT (Algorithm 3) on the two blocks whose ACT became
+//      0 or k, in tiles of 16-byte chunks                          (none at slice 0)
+//   I  SetAT for the monitor's pairs, in tiles of pairs
+//   C  pool census, in tiles of 16-byte chunks
+//   G  CheckAT gather + Eq. 11 for the monitor's hosts, in tiles of hosts
+// An item of one phase of monitor m starts once every item of the earlier
+// phases of m has finished: a per-monitor count of finished items, waited on
+// by the block's first thread with a bounded spin.  Every item waits only on
+// items earlier in the list, and an item is handed out only to a running
+// block, so the smallest unfinished item can always proceed: no wait can
+// depend on a block that is not running, and the launch needs no
+// co-residency guarantee.  A wait that runs past its spin limit marks the
+// step as timed out in the group's status word (VATE_GROUP_TIMEOUT) and every
+// later wait of the launch gives up at once, so the kernel always returns.
+//
+// Monitor-major order keeps a monitor's pool hot in L2 from its SetATs to its
+// census and gather while the pools of the group as a whole exceed L2; items
+// of the next monitors fill the blocks that wait.  The per-chunk and per-host
+// arithmetic is the one of the single-pool kernels (vate_device_ops.cuh), so
+// every monitor is bit-identical to a vate_handle run alone.  The slice
+// number, the batch offsets and k' are read on the device, so the one launch
+// is captured once as a CUDA graph and replayed every slice.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -36,19 +48,40 @@ namespace {
 
 constexpr uint32_t MAX_MONITORS = 256;
 constexpr int G_THREADS = 256;
+constexpr int G_WARPS = G_THREADS / 32;
+constexpr int NPHASE = 5;                 // B, P, I, C, G
+constexpr unsigned long long DEFAULT_SPIN_LIMIT = 1ull << 23;   // x ~128 ns of sleep: about a second
 
-struct GroupState {                 // device-resident
-    unsigned long long step;        // slides since slice 0
-    unsigned int started;           // set by the first step
-    unsigned int status;            // VATE_GROUP_* bits
-    unsigned int q_census;          // census tiles handed out
-    unsigned int q_gather;          // hosts handed out
+struct GroupState {                       // device-resident
+    unsigned long long step;              // the slice last processed (valid once started)
+    unsigned int started;                 // set by the first step
+    unsigned int status;                  // VATE_GROUP_* bits (sticky)
+    unsigned int q_items;                 // work items handed out in the running launch
+    unsigned int blocks_done;             // blocks of the running launch that have finished
+    unsigned int poisoned;                // a wait of the running launch gave up
+    unsigned int pad;
 };
 
-struct CensusTile {
-    uint32_t mon;
-    uint32_t nchunks;
-    uint64_t chunk0;
+struct StepArgs {
+    const Geom *descs;
+    GroupState *st;
+    unsigned int *done;                   // [M]: items of the monitor finished in the running launch
+    const uint32_t *pairs;
+    const uint64_t *poff;
+    uint64_t pcap;
+    const uint32_t *hosts;
+    const uint64_t *hoff;
+    uint64_t hcap;
+    const uint32_t *kprimes;
+    uint64_t *hist;                       // [M][maxbins]
+    float *out;
+    uint8_t *flags;
+    unsigned long long spin_limit;
+    uint32_t M, maxbins;
+    uint32_t census_tile, ingest_tile, gather_tile, preserve_tile;
+    uint32_t advance;                     // 1: the next slice; 0: repeat the last slice (autotuner)
+    uint32_t missing;                     // added to every wait's target (tests of the timeout path)
+    uint32_t u1, u2, u3;                  // run-time ones (the vector gather's multiply-adds)
 };
 
 // census_chunk_raw (vate_device_ops.cuh) into columns of counter pairs:
@@ -73,291 +106,298 @@ __device__ __forceinline__ uint32_t bact0_of(unsigned long long step, uint32_t t
     return (uint32_t)(step % twok);
 }
 
-// index of the monitor whose [off[m], off[m+1]) holds i (off non-decreasing, off[0] <= i < off[M])
-__device__ __forceinline__ uint32_t find_monitor(const uint64_t *off, uint32_t M, uint64_t i) {
-    uint32_t lo = 0, hi = M;            // invariant: off[lo] <= i < off[hi]
+// index of the monitor m with pre[m] <= i < pre[m+1] (pre strictly increasing, pre[0] <= i < pre[M])
+template <typename T>
+__device__ __forceinline__ uint32_t find_monitor(const T *pre, uint32_t M, uint64_t i) {
+    uint32_t lo = 0, hi = M;
     while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (off[mid] <= i) lo = mid;
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint64_t)pre[mid] <= i) lo = mid;
         else hi = mid;
     }
     return lo;
 }
 
-// Load M+1 offsets into shared memory, clamped to [0, cap] and made
-// non-decreasing; a repair sets `bad` in the status word.
-__device__ void load_offsets(const uint64_t *__restrict__ off, uint32_t M, uint64_t cap, uint64_t *s,
-                             GroupState *st, unsigned bad) {
-    for (uint32_t t = threadIdx.x; t <= M; t += blockDim.x) s[t] = off[t];
+// The 16-byte chunks PreserveAT visits for the slide to `step`: the chunks
+// covering [s0, e0) (the block whose ACT became 0) then those covering
+// [s1, e1) (ACT k), as in the single-pool preserve_kernel.
+struct PreserveSpan {
+    uint64_t s0, e0, s1, e1, c0s, c0e, c1s, n0, n;
+    uint32_t b0;
+};
+__device__ __forceinline__ PreserveSpan preserve_span(const Geom &G, unsigned long long step) {
+    PreserveSpan p;
+    p.b0 = bact0_of(step, G.twok);
+    const uint32_t i0 = (G.twok - p.b0) % G.twok, i1 = (G.k + G.twok - p.b0) % G.twok;
+    block_range_of(G, i0, &p.s0, &p.e0);
+    block_range_of(G, i1, &p.s1, &p.e1);
+    p.c0s = p.s0 >> 4;
+    p.c0e = (p.e0 + 15) >> 4;
+    p.c1s = p.s1 >> 4;
+    const uint64_t c1e = (p.e1 + 15) >> 4;
+    p.n0 = p.e0 > p.s0 ? p.c0e - p.c0s : 0;
+    p.n = p.n0 + (p.e1 > p.s1 ? c1e - p.c1s : 0);
+    return p;
+}
+
+// Thread 0 of a block: wait until *done >= target, with at most `limit`
+// sleeps of ~128 ns.  A wait that gives up marks the launch (poisoned) and
+// the group (VATE_GROUP_TIMEOUT); a wait in a marked launch gives up at once.
+__device__ bool wait_done(const unsigned int *done, unsigned int target, GroupState *st, unsigned long long limit) {
+    for (unsigned long long spins = 0;; spins++) {
+        if (*reinterpret_cast<const volatile unsigned int *>(done) >= target) {
+            __threadfence();                      // the finished items' writes before ours
+            return true;
+        }
+        if (*reinterpret_cast<volatile unsigned int *>(&st->poisoned)) return false;
+        if (spins >= limit) {
+            atomicOr(&st->status, VATE_GROUP_TIMEOUT);
+            atomicExch(&st->poisoned, 1u);
+            return false;
+        }
+        __nanosleep(128);
+    }
+}
+
+// GK: the gather of the group's segment length: 0, 1, 2 = 16, 32, 64-byte
+// segments (gather_host_vec); 3, 4, 5 = 2, 4, 8-byte segments
+// (gather_host_seg); 6 = one byte per VAT (gather_host_scalar).
+template <int GK>
+__device__ __forceinline__ uint32_t gather_one(const Geom &G, const RangeConsts &rc, uint32_t c2k, uint32_t bact0,
+                                               uint32_t kp, uint32_t aip, uint32_t lane, const StepArgs &a) {
+    // L2-only loads (CG): the pool was written by other blocks of this launch
+    if constexpr (GK <= 2) {
+        const uint32_t nseg = G.g >> G.log2L;
+        if (nseg % (32u * 2u) == 0)
+            return gather_host_vec<GK, 2, true, 1, false, true>(G, rc, c2k, aip, a.u1, a.u2, a.u3, lane);
+        return gather_host_vec<GK, 2, false, 1, false, true>(G, rc, c2k, aip, a.u1, a.u2, a.u3, lane);
+    } else if constexpr (GK <= 5) {
+        constexpr int SB = GK == 3 ? 2 : (GK == 4 ? 4 : 8);
+        return gather_host_seg<SB, 1, false, true>(G, rc, c2k, G.twok * ONES, aip, lane);
+    } else {
+        return gather_host_scalar<true>(G, bact0, kp, aip, lane);
+    }
+}
+
+template <int GK>
+__global__ void __launch_bounds__(G_THREADS) group_step_kernel(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t M = a.M;
+    uint64_t *po = reinterpret_cast<uint64_t *>(smem);              // M + 1 pair offsets (clamped)
+    uint64_t *ho = po + (M + 1);                                      // M + 1 host offsets (clamped)
+    uint32_t *cum = reinterpret_cast<uint32_t *>(ho + (M + 1));       // [M][NPHASE + 1]: items before each phase
+    uint32_t *pre = cum + M * (NPHASE + 1);                           // M + 1: items before each monitor
+    uint32_t *kp = pre + (M + 1);                                     // M: k' (clamped)
+    uint32_t *cols = kp + M;                                          // census lane columns [warps][pairs][32]
+    const uint32_t maxpairs = (a.maxbins + 1u) / 2u;
+
+    __shared__ unsigned long long s_step;
+    __shared__ uint32_t s_j, s_m, s_p, s_t, s_ok;
+    __shared__ uint64_t s_n0;
+    __shared__ Geom sG;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    GroupState *st = a.st;
+
+    if (tid == 0) {
+        // a group whose earlier step timed out (poisoned stays set) does no more work
+        s_ok = *reinterpret_cast<volatile unsigned int *>(&st->poisoned) ? 0u : 1u;
+        s_step = a.advance ? (st->started ? st->step + 1ull : 0ull) : st->step;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        bool repaired = false;
-        uint64_t prev = 0;
+    const unsigned long long step = s_step;
+    if (s_ok) {
+
+    // ---- per-block set-up: offsets, k', the item counts of every monitor ----
+    for (uint32_t t = tid; t <= M; t += blockDim.x) {
+        po[t] = a.poff[t];
+        ho[t] = a.hoff[t];
+    }
+    __syncthreads();
+    if (tid == 0) {                           // clamp to the capacities, make non-decreasing
+        bool bad = false;
+        uint64_t pp = 0, hp = 0;
         for (uint32_t t = 0; t <= M; t++) {
-            uint64_t v = s[t];
-            if (v > cap) { v = cap; repaired = true; }
-            if (t && v < prev) { v = prev; repaired = true; }
-            s[t] = v;
-            prev = v;
+            uint64_t v = po[t], w = ho[t];
+            if (v > a.pcap) { v = a.pcap; bad = true; }
+            if (t && v < pp) { v = pp; bad = true; }
+            if (w > a.hcap) { w = a.hcap; bad = true; }
+            if (t && w < hp) { w = hp; bad = true; }
+            po[t] = pp = v;
+            ho[t] = hp = w;
         }
-        if (repaired && blockIdx.x == 0) atomicOr(&st->status, bad);
+        if (bad && blockIdx.x == 0) atomicOr(&st->status, VATE_GROUP_BAD_OFFSETS);
     }
     __syncthreads();
-}
-
-__global__ void group_begin_kernel(GroupState *st, uint64_t *__restrict__ hist_all, uint32_t hist_words) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (st->started) st->step += 1ull;
-        else st->started = 1u;
-        st->q_census = 0u;
-        st->q_gather = 0u;
-    }
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < hist_words; i += gridDim.x * blockDim.x)
-        hist_all[i] = 0ull;
-}
-
-// Clears the queue counters (and optionally the histograms) without moving
-// the slice: used when the autotuner repeats a phase of the same slice.
-__global__ void group_reset_kernel(GroupState *st, uint64_t *__restrict__ hist_all, uint32_t hist_words) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->q_census = 0u;
-        st->q_gather = 0u;
-    }
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < hist_words; i += gridDim.x * blockDim.x)
-        hist_all[i] = 0ull;
-}
-
-__global__ void __launch_bounds__(G_THREADS) group_preserve_kernel(const Geom *__restrict__ descs, uint32_t M,
-                                                                   const GroupState *__restrict__ st) {
-    __shared__ uint64_t r[MAX_MONITORS][4];      // s0, e0, s1, e1
-    __shared__ uint64_t pre[MAX_MONITORS + 1];   // prefix of chunk counts
-    __shared__ uint64_t n0s[MAX_MONITORS];
-    const unsigned long long step = st->step;
-    if (step == 0ull) return;                    // slice 0: nothing to maintain
-    for (uint32_t m = threadIdx.x; m < M; m += blockDim.x) {
-        const Geom &G = descs[m];
-        uint32_t b0 = bact0_of(step, G.twok);
-        uint32_t i0 = (G.twok - b0) % G.twok, i1 = (G.k + G.twok - b0) % G.twok;
-        uint64_t s0, e0, s1, e1;
-        block_range_of(G, i0, &s0, &e0);
-        block_range_of(G, i1, &s1, &e1);
-        r[m][0] = s0; r[m][1] = e0; r[m][2] = s1; r[m][3] = e1;
-        uint64_t c0s = s0 >> 4, c0e = (e0 + 15) >> 4, c1s = s1 >> 4, c1e = (e1 + 15) >> 4;
-        n0s[m] = (e0 > s0) ? c0e - c0s : 0;
-        pre[m + 1] = n0s[m] + ((e1 > s1) ? c1e - c1s : 0);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        pre[0] = 0;
-        for (uint32_t m = 0; m < M; m++) pre[m + 1] += pre[m];
-    }
-    __syncthreads();
-    const uint64_t total = pre[M];
-    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t m = find_monitor(pre, M, t);
-        uint64_t local = t - pre[m];
-        const uint64_t s0 = r[m][0], e0 = r[m][1], s1 = r[m][2], e1 = r[m][3];
-        uint64_t c0s = s0 >> 4, c0e = (e0 + 15) >> 4, c1s = s1 >> 4;
-        uint64_t n0 = n0s[m];
-        uint64_t chunk = local < n0 ? c0s + local : c1s + (local - n0);
-        if (local >= n0 && n0 && chunk >= c0s && chunk < c0e) continue;   // enumerated with range 0
-        const uint32_t k = descs[m].k;
-        preserve_chunk(descs[m].pool, chunk << 4, preserve_consts_frame0(bact0_of(step, 2u * k), k), 2u * k, s0, e0,
-                       s1, e1);
-    }
-}
-
-__global__ void __launch_bounds__(G_THREADS) group_ingest_kernel(const Geom *__restrict__ descs, uint32_t M,
-                                                                 GroupState *st,
-                                                                 const uint32_t *__restrict__ pairs,
-                                                                 const uint64_t *__restrict__ off, uint64_t cap) {
-    extern __shared__ uint64_t dyn[];
-    uint64_t *so = dyn;                                          // M + 1 offsets
-    Geom *sd = reinterpret_cast<Geom *>(so + ((M + 2) & ~1u));   // M descriptors
-    load_offsets(off, M, cap, so, st, VATE_GROUP_BAD_OFFSETS);
-    for (uint32_t m = threadIdx.x; m < M; m += blockDim.x) sd[m] = descs[m];
-    __syncthreads();
-    const unsigned long long step = st->step;
-    const uint64_t lo = so[0], hi = so[M];
-    const uint2 *p2 = reinterpret_cast<const uint2 *>(pairs);          // 8-byte aligned (checked on the host)
-    __shared__ uint32_t tile_mon[2];
-    // Tiles of INGEST_TILE consecutive pairs, in order across the grid, so the
-    // pools being written at any time are those of the few monitors whose
-    // pairs are in flight.  A tile inside one monitor runs with that monitor's
-    // descriptor in registers; only a tile that straddles monitors looks up
-    // the monitor of each pair.
-    constexpr uint32_t INGEST_TILE = G_THREADS * 8;
-    const uint64_t ntiles = (hi - lo + INGEST_TILE - 1) / INGEST_TILE;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t t0 = lo + tile * INGEST_TILE, t1 = min(t0 + INGEST_TILE, hi);
-        __syncthreads();                        // the previous tile's tile_mon has been read
-        if (threadIdx.x == 0) {
-            tile_mon[0] = find_monitor(so, M, t0);
-            tile_mon[1] = find_monitor(so, M, t1 - 1);
-        }
-        __syncthreads();
-        const uint32_t m0 = tile_mon[0];
-        if (m0 == tile_mon[1]) {
-            const Geom G = sd[m0];
-            const uint8_t v = (uint8_t)bact0_of(step, G.twok);        // SetAT in frame 0
-#pragma unroll 4
-            for (uint64_t i = t0 + threadIdx.x; i < t1; i += G_THREADS) {
-                const uint2 q = __ldcs(p2 + i);
-                G.pool[vat_pid(G, q.x, bh(G, q.y))] = v;
-            }
-        } else {
-            for (uint64_t i = t0 + threadIdx.x; i < t1; i += G_THREADS) {
-                const uint32_t m = find_monitor(so, M, i);
-                const Geom &G = sd[m];
-                const uint2 q = __ldcs(p2 + i);
-                G.pool[vat_pid(G, q.x, bh(G, q.y))] = (uint8_t)bact0_of(step, G.twok);
-            }
-        }
-    }
-}
-
-__global__ void __launch_bounds__(G_THREADS) group_census_kernel(const Geom *__restrict__ descs, GroupState *st,
-                                                                 const CensusTile *__restrict__ tiles, uint32_t ntiles,
-                                                                 uint64_t *__restrict__ hist_all, uint32_t maxbins) {
-    extern __shared__ uint32_t sh[];             // [warps][maxpairs][32]: lane columns of 16-bit counter pairs
-    __shared__ Geom G;
-    __shared__ CensusTile tile;
-    __shared__ unsigned int ticket;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t maxpairs = (maxbins + 1u) / 2u;
-    uint32_t *col = sh + (size_t)warp * maxpairs * 32u + lane;
-    const unsigned long long step = st->step;
-    for (;;) {
-        if (threadIdx.x == 0) ticket = atomicAdd(&st->q_census, 1u);
-        __syncthreads();
-        if (ticket >= ntiles) break;
-        if (threadIdx.x == 0) {
-            tile = tiles[ticket];
-            G = descs[tile.mon];
-        }
-        __syncthreads();
-        const uint32_t nbins = G.twok + 1u, npairs = (nbins + 1u) / 2u;
-        for (uint32_t b = 0; b < npairs; b++) col[b * 32u] = 0u;
-        const uint32_t pat = G.twok * ONES;
-        const uint32_t bact0 = bact0_of(step, G.twok);
-        uint32_t inactive_runs = 0;
-        const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
-        // eight chunks in flight per thread: the pools of a group exceed L2, so the loads wait on memory;
-        // frame-0 pools: the stored values are counted and relabelled as bins below.  A tile holds at
-        // most 65,536 chunks, so a lane counts at most 4,096 ATs and every 16-bit counter stays exact.
-        constexpr int U = 8;
-        const uint64_t qend = tile.chunk0 + tile.nchunks;
-        for (uint64_t q = tile.chunk0 + threadIdx.x; q < qend; q += (uint64_t)U * blockDim.x) {
-            uint4 w[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const uint64_t qu = q + (uint64_t)u * blockDim.x;
-                w[u] = qu < qend ? __ldcg(pool16 + qu) : make_uint4(pat, pat, pat, pat);
-            }
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const uint64_t qu = q + (uint64_t)u * blockDim.x;
-                if (qu < qend) census_chunk_raw_pairs(w[u], pat, G.twok, col, inactive_runs);
-            }
-        }
-        col[(G.twok >> 1) * 32u] += 16u * inactive_runs;     // 2k is even: the low half of pair k
-        __syncthreads();
-        for (uint32_t r = warp; r < npairs; r += nwarps) {
-            uint32_t lo = 0, hi = 0;
-            for (uint32_t wv = 0; wv < nwarps; wv++) {
-                const uint32_t x = sh[((size_t)wv * maxpairs + r) * 32u + lane];
-                lo += x & 0xFFFFu;
-                hi += x >> 16;
-            }
-            lo = __reduce_add_sync(0xFFFFFFFFu, lo);
-            hi = __reduce_add_sync(0xFFFFFFFFu, hi);
-            unsigned long long *h = reinterpret_cast<unsigned long long *>(hist_all) + (size_t)tile.mon * maxbins;
-            if (lane == 0 && lo) atomicAdd(h + census_raw_bin(G, bact0, 2u * r), (unsigned long long)lo);
-            if (lane == 0 && hi && 2u * r + 1u < nbins)
-                atomicAdd(h + census_raw_bin(G, bact0, 2u * r + 1u), (unsigned long long)hi);
-        }
-        __syncthreads();
-    }
-}
-
-template <int CPSL, int RB>
-__global__ void __launch_bounds__(G_THREADS) group_gather_kernel(const Geom *__restrict__ descs, uint32_t M,
-                                                                 GroupState *st, const uint32_t *__restrict__ hosts,
-                                                                 const uint64_t *__restrict__ off, uint64_t cap,
-                                                                 const uint32_t *__restrict__ kprimes,
-                                                                 const uint64_t *__restrict__ hist_all,
-                                                                 uint32_t maxbins, float *__restrict__ out,
-                                                                 uint8_t *__restrict__ flags, uint32_t grab,
-                                                                 uint32_t u1, uint32_t u2, uint32_t u3) {
-    extern __shared__ uint64_t dyn[];
-    uint64_t *so = dyn;                                          // M + 1 host offsets
-    uint64_t *n0 = so + M + 1;                                   // N0 per monitor
-    uint32_t *kp = reinterpret_cast<uint32_t *>(n0 + M);         // k' per monitor
-    Geom *sd = reinterpret_cast<Geom *>(so + ((2 * M + 1 + (M + 1) / 2 + 1) & ~1u));
-    load_offsets(off, M, cap, so, st, VATE_GROUP_BAD_OFFSETS);
-    for (uint32_t m = threadIdx.x; m < M; m += blockDim.x) {
-        sd[m] = descs[m];
-        uint32_t k = descs[m].k, x = kprimes[m];
-        if (x < 1u || x > k) {
+    for (uint32_t m = tid; m < M; m += blockDim.x) {
+        const Geom &G = a.descs[m];
+        uint32_t x = a.kprimes[m];
+        if (x < 1u || x > G.k) {
             if (blockIdx.x == 0) atomicOr(&st->status, VATE_GROUP_BAD_KPRIME);
-            x = k;
+            x = G.k;
         }
         kp[m] = x;
-        n0[m] = pool_inactive(hist_all + (size_t)m * maxbins, descs[m].P, x);
+        uint32_t n[NPHASE];
+        n[0] = 1u;
+        n[1] = step == 0ull ? 0u
+                            : (uint32_t)((preserve_span(G, step).n + a.preserve_tile - 1) / a.preserve_tile);
+        n[2] = (uint32_t)((po[m + 1] - po[m] + a.ingest_tile - 1) / a.ingest_tile);
+        n[3] = (uint32_t)(((G.P >> 4) + a.census_tile - 1) / a.census_tile);
+        n[4] = (uint32_t)((ho[m + 1] - ho[m] + a.gather_tile - 1) / a.gather_tile);
+        uint32_t c = 0;
+        for (int p = 0; p < NPHASE; p++) {
+            cum[m * (NPHASE + 1) + p] = c;
+            c += n[p];
+        }
+        cum[m * (NPHASE + 1) + NPHASE] = c;
     }
     __syncthreads();
-    const unsigned long long step = st->step;
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t lo = so[0], hi = so[M];
-    // the monitor of the last host and its host range [cur_lo, cur_hi): hosts
-    // come in runs of one monitor, so the binary search runs once per run
-    uint32_t cur = 0;
-    uint64_t cur_lo = 1, cur_hi = 0;
-    RangeConsts rc = {};
+    if (tid == 0) {
+        pre[0] = 0;
+        for (uint32_t m = 0; m < M; m++) pre[m + 1] = pre[m] + cum[m * (NPHASE + 1) + NPHASE];
+    }
+    __syncthreads();
+    const uint32_t total = pre[M];
+
+    // ---- the items ----
     for (;;) {
-        uint64_t base = 0;
-        if (lane == 0) base = lo + (uint64_t)atomicAdd(&st->q_gather, grab);
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
-        if (base >= hi) break;
-        const uint64_t end = min(base + grab, hi);
-        // up to 32 hosts at a time: lane j keeps host b0 + j's count and
-        // monitor, and the warp's lanes evaluate their Eq. 11 side by side
-        for (uint64_t b0 = base; b0 < end; b0 += 32) {
-            const uint64_t b1 = min(b0 + 32, end);
-            uint32_t myA = 0, mym = 0;
-            for (uint64_t h = b0; h < b1; h++) {
-                if (h < cur_lo || h >= cur_hi) {   // CheckAT of monitor m: ACT = BACT^0 for every AT in frame 0
-                    cur = find_monitor(so, M, h);
-                    cur_lo = so[cur];
-                    cur_hi = so[cur + 1];
-                    rc = range_consts(bact0_of(step, sd[cur].twok), kp[cur], sd[cur].twok);
-                }
-                const Geom &G = sd[cur];
-                const uint32_t aip = hosts[h];
-                uint32_t cnt;
-                if (CPSL >= 0) {
-                    const uint32_t nseg = G.g >> G.log2L;
-                    const uint32_t c2k = (128u - G.twok) * ONES;
-                    if (nseg % (32u * RB) == 0)
-                        cnt = gather_host_vec<(CPSL < 0 ? 0 : CPSL), RB, true>(G, rc, c2k, aip, u1, u2, u3, lane);
-                    else
-                        cnt = gather_host_vec<(CPSL < 0 ? 0 : CPSL), RB, false>(G, rc, c2k, aip, u1, u2, u3, lane);
-                } else {
-                    cnt = gather_host_scalar(G, bact0_of(step, G.twok), kp[cur], aip, lane);
-                }
-                const uint32_t A = __reduce_add_sync(0xFFFFFFFFu, cnt);
-                if (lane == (uint32_t)(h - b0)) {
-                    myA = A;
-                    mym = cur;
+        if (tid == 0) {
+            const uint32_t j = atomicAdd(&st->q_items, 1u);
+            s_j = j;
+            if (j < total) {
+                const uint32_t m = find_monitor(pre, M, j);
+                const uint32_t local = j - pre[m];
+                const uint32_t *cm = cum + m * (NPHASE + 1);
+                uint32_t p = 0;
+                while (local >= cm[p + 1]) p++;
+                s_m = m;
+                s_p = p;
+                s_t = local - cm[p];
+                s_ok = wait_done(a.done + m, cm[p] + a.missing, st, a.spin_limit) ? 1u : 0u;
+                sG = a.descs[m];
+                if (p == 4) {                       // N0 of Eq. 11 from the census (written in this launch)
+                    uint64_t act = 0;
+                    for (uint32_t d = 0; d < kp[m]; d++) act += __ldcg(a.hist + (size_t)m * a.maxbins + d);
+                    s_n0 = a.descs[m].P - act;
                 }
             }
-            if (b0 + lane < b1) {
-                const Geom &G = sd[mym];
-                uint8_t f;
-                out[b0 + lane] = estimate_eq11(G.g, G.P, n0[mym], myA, f);
-                if (flags) flags[b0 + lane] = f;
+        }
+        __syncthreads();
+        if (s_j >= total) break;
+        if (s_ok) {
+            const uint32_t m = s_m, p = s_p, t = s_t;
+            const Geom G = sG;
+            const uint32_t bact0 = bact0_of(step, G.twok);
+            if (p == 0) {                                        // B: clear the monitor's census
+                for (uint32_t b = tid; b <= G.twok; b += blockDim.x) a.hist[(size_t)m * a.maxbins + b] = 0ull;
+            } else if (p == 1) {                                 // P: PreserveAT, chunks [t*T, (t+1)*T)
+                const PreserveSpan ps = preserve_span(G, step);
+                const RangeConsts pc = preserve_consts_frame0(ps.b0, G.k);
+                const uint64_t u1 = min((uint64_t)(t + 1) * a.preserve_tile, ps.n);
+                for (uint64_t u = (uint64_t)t * a.preserve_tile + tid; u < u1; u += blockDim.x) {
+                    const uint64_t chunk = u < ps.n0 ? ps.c0s + u : ps.c1s + (u - ps.n0);
+                    if (u >= ps.n0 && ps.n0 && chunk >= ps.c0s && chunk < ps.c0e) continue;   // range 0's chunk
+                    preserve_chunk(G.pool, chunk << 4, pc, G.twok, ps.s0, ps.e0, ps.s1, ps.e1);
+                }
+            } else if (p == 2) {                                 // I: SetAT (frame 0: the value BACT^0)
+                const uint2 *p2 = reinterpret_cast<const uint2 *>(a.pairs);   // 8-byte aligned (host check)
+                const uint64_t i0 = po[m] + (uint64_t)t * a.ingest_tile;
+                const uint64_t i1 = min(i0 + a.ingest_tile, po[m + 1]);
+                const uint8_t v = (uint8_t)bact0;
+#pragma unroll 4
+                for (uint64_t i = i0 + tid; i < i1; i += G_THREADS) {
+                    const uint2 q = __ldcs(p2 + i);
+                    G.pool[vat_pid(G, q.x, bh(G, q.y))] = v;
+                }
+            } else if (p == 3) {                                 // C: census tile into lane columns
+                uint32_t *col = cols + (size_t)warp * maxpairs * 32u + lane;
+                const uint32_t nbins = G.twok + 1u, npairs = (nbins + 1u) / 2u;
+                for (uint32_t b = 0; b < npairs; b++) col[b * 32u] = 0u;
+                const uint32_t pat = G.twok * ONES;
+                uint32_t runs = 0;
+                const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
+                // a tile holds at most 65,536 chunks: a lane counts at most 4,096 ATs, every
+                // 16-bit counter stays exact
+                constexpr int U = 8;
+                const uint64_t q0 = (uint64_t)t * a.census_tile;
+                const uint64_t qend = min(q0 + a.census_tile, G.P >> 4);
+                for (uint64_t q = q0 + tid; q < qend; q += (uint64_t)U * blockDim.x) {
+                    uint4 w[U];
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const uint64_t qu = q + (uint64_t)u * blockDim.x;
+                        w[u] = qu < qend ? __ldcg(pool16 + qu) : make_uint4(pat, pat, pat, pat);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const uint64_t qu = q + (uint64_t)u * blockDim.x;
+                        if (qu < qend) census_chunk_raw_pairs(w[u], pat, G.twok, col, runs);
+                    }
+                }
+                col[(G.twok >> 1) * 32u] += 16u * runs;          // 2k is even: the low half of pair k
+                __syncthreads();
+                unsigned long long *h = reinterpret_cast<unsigned long long *>(a.hist) + (size_t)m * a.maxbins;
+                for (uint32_t r = warp; r < npairs; r += G_WARPS) {
+                    uint32_t lo = 0, hi = 0;
+                    for (uint32_t wv = 0; wv < (uint32_t)G_WARPS; wv++) {
+                        const uint32_t x = cols[((size_t)wv * maxpairs + r) * 32u + lane];
+                        lo += x & 0xFFFFu;
+                        hi += x >> 16;
+                    }
+                    lo = __reduce_add_sync(0xFFFFFFFFu, lo);
+                    hi = __reduce_add_sync(0xFFFFFFFFu, hi);
+                    if (lane == 0 && lo) atomicAdd(h + census_raw_bin(G, bact0, 2u * r), (unsigned long long)lo);
+                    if (lane == 0 && hi && 2u * r + 1u < nbins)
+                        atomicAdd(h + census_raw_bin(G, bact0, 2u * r + 1u), (unsigned long long)hi);
+                }
+            } else {                                             // G: gather + Eq. 11, warp per host
+                const uint32_t k1 = kp[m];
+                const RangeConsts rc = range_consts(bact0, k1, G.twok);   // frame 0: ACT = BACT^0
+                const uint32_t c2k = (128u - G.twok) * ONES;
+                const uint64_t N0 = s_n0;
+                const uint64_t h0 = ho[m] + (uint64_t)t * a.gather_tile;
+                const uint64_t h1 = min(h0 + a.gather_tile, ho[m + 1]);
+                // 32 hosts per warp at a time: lane j keeps host b0 + j's count, the 32 Eq. 11
+                // epilogues run side by side
+                for (uint64_t b0 = h0 + (uint64_t)warp * 32u; b0 < h1; b0 += (uint64_t)G_WARPS * 32u) {
+                    const uint64_t b1 = min(b0 + 32u, h1);
+                    const uint32_t my_aip = b0 + lane < b1 ? a.hosts[b0 + lane] : 0u;
+                    uint32_t myA = 0;
+                    for (uint32_t j = 0; j < (uint32_t)(b1 - b0); j++) {
+                        const uint32_t aip = __shfl_sync(0xFFFFFFFFu, my_aip, j);
+                        const uint32_t A =
+                            __reduce_add_sync(0xFFFFFFFFu, gather_one<GK>(G, rc, c2k, bact0, k1, aip, lane, a));
+                        if (lane == j) myA = A;
+                    }
+                    if (b0 + lane < b1) {
+                        uint8_t f;
+                        a.out[b0 + lane] = estimate_eq11(G.g, G.P, N0, myA, f);
+                        if (a.flags) a.flags[b0 + lane] = f;
+                    }
+                }
             }
+        }
+        // the item's writes, then its completion (release to the waits of later items)
+        __threadfence();
+        __syncthreads();
+        if (tid == 0 && s_ok) atomicAdd(a.done + s_m, 1u);
+    }
+    }   // s_ok
+
+    // ---- the last block to finish closes the launch ----
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned int t = atomicAdd(&st->blocks_done, 1u);
+        if (t == gridDim.x - 1u) {
+            __threadfence();
+            for (uint32_t m = 0; m < M; m++) a.done[m] = 0u;
+            st->q_items = 0u;
+            st->blocks_done = 0u;
+            if (!*reinterpret_cast<volatile unsigned int *>(&st->poisoned)) {   // a timed-out step is not one
+                st->step = step;
+                st->started = 1u;
+            }
+            __threadfence();
         }
     }
 }
@@ -379,113 +419,112 @@ struct vate_group {
     uint64_t arena_bytes = 0;
     Geom *d_descs = nullptr;
     GroupState *d_state = nullptr;
+    unsigned int *d_done = nullptr;  // M
     uint64_t *d_hist = nullptr;      // M x maxbins
     uint32_t maxbins = 0;
-    CensusTile *d_tiles = nullptr;
-    uint32_t ntiles = 0, tiles_capacity = 0;
-    uint32_t L = 1, log2L = 0;
+    uint32_t L = 1;
+    int gk = 1;                      // gather form (group_step_kernel<GK>)
     int sms = 148;
+    int max_blocks_per_sm = 1;       // occupancy of group_step_kernel
     uint32_t steps = 0;              // steps queued so far (host count)
     vate_group_tuning tuning;
+    unsigned long long spin_limit = DEFAULT_SPIN_LIMIT;
+    uint32_t missing = 0;
     bool persist_l2 = false;         // VATE_OPT_PERSIST_L2 in some monitor's options
     // CUDA graph of one step
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
-    uint64_t graph_key[12] = {};
+    uint32_t graph_nodes = 0;
+    uint64_t graph_key[14] = {};
 };
 
 namespace {
 
-int rebuild_tiles(vate_group *g, cudaStream_t st) {
-    std::vector<CensusTile> t;
-    const uint64_t per = g->tuning.census_tile_chunks;
-    for (uint32_t m = 0; m < g->M; m++) {
-        uint64_t nch = g->geoms[m].P >> 4;          // chunks of monitor m's own pool
-        for (uint64_t c = 0; c < nch; c += per) {
-            CensusTile x;
-            x.mon = m;
-            x.nchunks = (uint32_t)std::min(per, nch - c);
-            x.chunk0 = c;                           // relative to monitor m's pool
-            t.push_back(x);
-        }
+// dynamic shared memory of group_step_kernel: two uint64 offset arrays, then
+// cum, pre and kp (uint32), then the census lane columns
+size_t step_smem(uint32_t M, uint32_t maxbins) {
+    const size_t words = 4 * (size_t)(M + 1) + (size_t)M * (NPHASE + 1) + (M + 1) + M;
+    return words * 4 + (size_t)G_WARPS * ((maxbins + 1) / 2) * 32 * sizeof(uint32_t);
+}
+
+void *kernel_of(int gk) {
+    switch (gk) {
+    case 0: return (void *)group_step_kernel<0>;
+    case 1: return (void *)group_step_kernel<1>;
+    case 2: return (void *)group_step_kernel<2>;
+    case 3: return (void *)group_step_kernel<3>;
+    case 4: return (void *)group_step_kernel<4>;
+    case 5: return (void *)group_step_kernel<5>;
+    default: return (void *)group_step_kernel<6>;
     }
-    if (t.size() > g->tiles_capacity) return vate::set_error(VATE_EINVAL, "census tile table overflow");
-    g->ntiles = (uint32_t)t.size();
-    cudaError_t e = cudaMemcpyAsync(g->d_tiles, t.data(), t.size() * sizeof(CensusTile), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return vate::set_error(VATE_ECUDA, cudaGetErrorString(e));
-    return VATE_OK;
 }
 
-int check_tuning(const vate_group_tuning *t) {
+int gather_form(uint32_t L) {
+    switch (L) {
+    case 16: return 0;
+    case 32: return 1;
+    case 64: return 2;
+    case 2: return 3;
+    case 4: return 4;
+    case 8: return 5;
+    default: return 6;
+    }
+}
+
+int check_tuning(const vate_group_tuning *t, int max_bps) {
     if (!t) return vate::set_error(VATE_EINVAL, "tuning is NULL");
-    uint32_t c = t->census_tile_chunks;
-    if (c < 256 || c > 65536 || (c & (c - 1))) return vate::set_error(VATE_EINVAL, "census_tile_chunks: power of two in [256, 65536]");
-    for (uint32_t v : {t->gather_blocks_per_sm, t->ingest_blocks_per_sm, t->preserve_blocks_per_sm})
-        if (v < 1 || v > 32) return vate::set_error(VATE_EINVAL, "blocks per SM must be in [1, 32]");
-    if (t->gather_hosts_per_grab < 1 || t->gather_hosts_per_grab > 64) return vate::set_error(VATE_EINVAL, "gather_hosts_per_grab in [1, 64]");
+    const uint32_t c = t->census_tile_chunks;
+    if (c < 256 || c > 65536 || (c & (c - 1)))
+        return vate::set_error(VATE_EINVAL, "census_tile_chunks: a power of two in [256, 65536]");
+    if (t->blocks_per_sm < 1 || (int)t->blocks_per_sm > max_bps) {
+        static thread_local char msg[96];
+        snprintf(msg, sizeof msg, "blocks_per_sm must be in [1, %d] (the step kernel's occupancy)", max_bps);
+        return vate::set_error(VATE_EINVAL, msg);
+    }
+    for (uint32_t v : {t->gather_tile_hosts, t->ingest_tile_pairs, t->preserve_tile_chunks})
+        if (v < 256 || v > 65536 || v % 256)
+            return vate::set_error(VATE_EINVAL, "gather, ingest and preserve tiles: multiples of 256 in [256, 65536]");
     return VATE_OK;
-}
-
-size_t ingest_smem(uint32_t M) { return (size_t)((M + 2) & ~1u) * 8 + (size_t)M * sizeof(Geom); }
-size_t gather_smem(uint32_t M) { return (size_t)((2 * M + 1 + (M + 1) / 2 + 1) & ~1u) * 8 + (size_t)M * sizeof(Geom); }
-size_t census_smem(uint32_t maxbins) { return (size_t)(G_THREADS / 32) * ((maxbins + 1) / 2) * 32 * sizeof(uint32_t); }
-
-template <int CPSL, int RB>
-cudaError_t launch_group_gather(vate_group *g, const uint32_t *hosts, const uint64_t *hoff, uint64_t hcap,
-                                const uint32_t *kprime, float *out, uint8_t *flags, cudaStream_t st) {
-    auto kern = group_gather_kernel<CPSL, RB>;
-    size_t smem = gather_smem(g->M);
-    if (cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
-        return e;
-    return vate::launch_pool(g->arena_geom, kern, g->sms * g->tuning.gather_blocks_per_sm, G_THREADS, smem, st,
-                             (const Geom *)g->d_descs, g->M, g->d_state, hosts, hoff, hcap, kprime,
-                             (const uint64_t *)g->d_hist, g->maxbins, out, flags, g->tuning.gather_hosts_per_grab, 1u,
-                             1u, 1u);
-}
-
-cudaError_t enqueue_gather(vate_group *g, const uint32_t *hosts, const uint64_t *hoff, uint64_t hcap,
-                           const uint32_t *kprime, float *out, uint8_t *flags, cudaStream_t st) {
-    if (g->L == 16) return launch_group_gather<0, 2>(g, hosts, hoff, hcap, kprime, out, flags, st);
-    if (g->L == 32) return launch_group_gather<1, 2>(g, hosts, hoff, hcap, kprime, out, flags, st);
-    if (g->L == 64) return launch_group_gather<2, 2>(g, hosts, hoff, hcap, kprime, out, flags, st);
-    return launch_group_gather<-1, 1>(g, hosts, hoff, hcap, kprime, out, flags, st);
-}
-
-cudaError_t enqueue_ingest(vate_group *g, const vate_pair *pairs, const uint64_t *poff, uint64_t pcap,
-                           cudaStream_t st) {
-    size_t smem = ingest_smem(g->M);
-    if (cudaError_t e = cudaFuncSetAttribute(group_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
-        return e;
-    return vate::launch_pool(g->arena_geom, group_ingest_kernel, g->sms * g->tuning.ingest_blocks_per_sm, G_THREADS,
-                             smem, st, (const Geom *)g->d_descs, g->M, g->d_state,
-                             reinterpret_cast<const uint32_t *>(pairs), poff, pcap);
-}
-
-cudaError_t enqueue_census(vate_group *g, cudaStream_t st) {
-    size_t smem = census_smem(g->maxbins);
-    if (cudaError_t e = cudaFuncSetAttribute(group_census_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
-        return e;
-    // as many blocks per SM as their columns fit in about 200 KiB, up to four
-    const int per_sm = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)(200u << 10) / smem));
-    return vate::launch_pool(g->arena_geom, group_census_kernel, g->sms * per_sm, G_THREADS, smem, st,
-                             (const Geom *)g->d_descs, g->d_state, (const CensusTile *)g->d_tiles, g->ntiles, g->d_hist,
-                             g->maxbins);
 }
 
 cudaError_t enqueue_step(vate_group *g, const vate_pair *pairs, const uint64_t *poff, uint64_t pcap,
                          const uint32_t *hosts, const uint64_t *hoff, uint64_t hcap, const uint32_t *kprime,
-                         float *out, uint8_t *flags, cudaStream_t st) {
-    const uint32_t hist_words = g->M * g->maxbins;
-    cudaError_t e = vate::launch_pool(g->arena_geom, group_begin_kernel, 8, G_THREADS, 0, st, g->d_state, g->d_hist,
-                                      hist_words);
-    if (e == cudaSuccess)
-        e = vate::launch_pool(g->arena_geom, group_preserve_kernel, g->sms * g->tuning.preserve_blocks_per_sm,
-                              G_THREADS, 0, st, (const Geom *)g->d_descs, g->M, (const GroupState *)g->d_state);
-    if (e == cudaSuccess) e = enqueue_ingest(g, pairs, poff, pcap, st);
-    if (e == cudaSuccess) e = enqueue_census(g, st);
-    if (e == cudaSuccess) e = enqueue_gather(g, hosts, hoff, hcap, kprime, out, flags, st);
-    return e;
+                         float *out, uint8_t *flags, uint32_t advance, cudaStream_t st) {
+    StepArgs a;
+    a.descs = g->d_descs;
+    a.st = g->d_state;
+    a.done = g->d_done;
+    a.pairs = reinterpret_cast<const uint32_t *>(pairs);
+    a.poff = poff;
+    a.pcap = pcap;
+    a.hosts = hosts;
+    a.hoff = hoff;
+    a.hcap = hcap;
+    a.kprimes = kprime;
+    a.hist = g->d_hist;
+    a.out = out;
+    a.flags = flags;
+    a.spin_limit = g->spin_limit;
+    a.M = g->M;
+    a.maxbins = g->maxbins;
+    a.census_tile = g->tuning.census_tile_chunks;
+    a.ingest_tile = g->tuning.ingest_tile_pairs;
+    a.gather_tile = g->tuning.gather_tile_hosts;
+    a.preserve_tile = g->tuning.preserve_tile_chunks;
+    a.advance = advance;
+    a.missing = g->missing;
+    a.u1 = a.u2 = a.u3 = 1u;
+    const size_t smem = step_smem(g->M, g->maxbins);
+    const int grid = g->sms * (int)g->tuning.blocks_per_sm;
+    switch (g->gk) {
+    case 0: return vate::launch_pool(g->arena_geom, group_step_kernel<0>, grid, G_THREADS, smem, st, a);
+    case 1: return vate::launch_pool(g->arena_geom, group_step_kernel<1>, grid, G_THREADS, smem, st, a);
+    case 2: return vate::launch_pool(g->arena_geom, group_step_kernel<2>, grid, G_THREADS, smem, st, a);
+    case 3: return vate::launch_pool(g->arena_geom, group_step_kernel<3>, grid, G_THREADS, smem, st, a);
+    case 4: return vate::launch_pool(g->arena_geom, group_step_kernel<4>, grid, G_THREADS, smem, st, a);
+    case 5: return vate::launch_pool(g->arena_geom, group_step_kernel<5>, grid, G_THREADS, smem, st, a);
+    default: return vate::launch_pool(g->arena_geom, group_step_kernel<6>, grid, G_THREADS, smem, st, a);
+    }
 }
 
 int check_step_args(vate_group *g, const vate_pair *pairs, const uint64_t *poff, uint64_t pcap, const uint32_t *hosts,
@@ -534,20 +573,30 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
         off += g->geoms[m].P;
     }
     g->L = params[0].seg_len;
+    g->gk = gather_form(g->L);
     g->arena_bytes = (off + 255) & ~255ull;
     g->sms = sm_count_current();
-    g->tuning.census_tile_chunks = 4096;
-    g->tuning.gather_blocks_per_sm = 5;
-    g->tuning.gather_hosts_per_grab = 4;
-    g->tuning.ingest_blocks_per_sm = 16;
-    g->tuning.preserve_blocks_per_sm = 8;
+    const size_t smem = step_smem(g->M, g->maxbins);
+    cudaError_t ea = cudaFuncSetAttribute(kernel_of(g->gk), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    if (ea == cudaSuccess) ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_of(g->gk), G_THREADS, smem);
+    if (ea != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        delete g;
+        return vate::set_error(VATE_ECUDA, "group step kernel: shared-memory attribute or occupancy query failed");
+    }
+    g->max_blocks_per_sm = occ;
+    g->tuning.census_tile_chunks = 16384;
+    g->tuning.blocks_per_sm = (uint32_t)std::min(occ, 3);
+    g->tuning.gather_tile_hosts = 256;
+    g->tuning.ingest_tile_pairs = 4096;
+    g->tuning.preserve_tile_chunks = 4096;
     g->tuning.reserved = 0;
-    for (uint32_t m = 0; m < n_monitors; m++) g->tiles_capacity += (uint32_t)(((g->geoms[m].P >> 4) + 255) / 256);
     bool ok = cudaMalloc(&g->arena, g->arena_bytes) == cudaSuccess &&
               cudaMalloc(&g->d_descs, n_monitors * sizeof(Geom)) == cudaSuccess &&
               cudaMalloc(&g->d_state, sizeof(GroupState)) == cudaSuccess &&
+              cudaMalloc(&g->d_done, n_monitors * sizeof(unsigned int)) == cudaSuccess &&
               cudaMalloc(&g->d_hist, (size_t)n_monitors * g->maxbins * sizeof(uint64_t)) == cudaSuccess &&
-              cudaMalloc(&g->d_tiles, (size_t)g->tiles_capacity * sizeof(CensusTile)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -583,6 +632,8 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
     memset(&s0, 0, sizeof s0);
     cudaError_t e = cudaMemcpyAsync(g->d_descs, g->geoms.data(), n_monitors * sizeof(Geom), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_state, &s0, sizeof s0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_done, 0, n_monitors * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_hist, 0, (size_t)n_monitors * g->maxbins * sizeof(uint64_t), st);
     for (uint32_t m = 0; m < n_monitors && e == cudaSuccess; m++) {
         Geom G = g->geoms[m];
         G.l2_window_bytes = 0;
@@ -592,11 +643,6 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
     if (e != cudaSuccess) {
         vate_group_destroy(g);
         return vate::set_error(VATE_ECUDA, cudaGetErrorString(e));
-    }
-    int rc = rebuild_tiles(g, st);
-    if (rc) {
-        vate_group_destroy(g);
-        return rc;
     }
     *out = g;
     return VATE_OK;
@@ -610,8 +656,8 @@ int vate_group_destroy(vate_group *g) {
     cudaFree(g->arena);
     cudaFree(g->d_descs);
     cudaFree(g->d_state);
+    cudaFree(g->d_done);
     cudaFree(g->d_hist);
-    cudaFree(g->d_tiles);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     cudaGetLastError();
     delete g;
@@ -625,7 +671,7 @@ int vate_group_step(vate_group *g, const vate_pair *d_pairs, const uint64_t *d_p
                                  d_kprime, d_out))
         return rc;
     cudaError_t e = enqueue_step(g, d_pairs, d_pair_offsets, pair_capacity, d_hosts, d_host_offsets, host_capacity,
-                                 d_kprime, d_out, d_flags, (cudaStream_t)stream);
+                                 d_kprime, d_out, d_flags, 1u, (cudaStream_t)stream);
     if (e != cudaSuccess) return vate::set_error(VATE_ECUDA, cudaGetErrorString(e));
     g->steps++;
     return VATE_OK;
@@ -639,11 +685,11 @@ int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_
                                  d_kprime, d_out))
         return rc;
     const vate_group_tuning &t = g->tuning;
-    uint64_t key[12] = {(uint64_t)d_pairs, (uint64_t)d_pair_offsets, pair_capacity, (uint64_t)d_hosts,
+    uint64_t key[14] = {(uint64_t)d_pairs, (uint64_t)d_pair_offsets, pair_capacity, (uint64_t)d_hosts,
                         (uint64_t)d_host_offsets, host_capacity, (uint64_t)d_kprime, (uint64_t)d_out,
-                        (uint64_t)d_flags,
-                        ((uint64_t)t.census_tile_chunks << 32) | t.gather_blocks_per_sm,
-                        ((uint64_t)t.gather_hosts_per_grab << 32) | t.ingest_blocks_per_sm, t.preserve_blocks_per_sm};
+                        (uint64_t)d_flags, ((uint64_t)t.census_tile_chunks << 32) | t.blocks_per_sm,
+                        ((uint64_t)t.gather_tile_hosts << 32) | t.ingest_tile_pairs, t.preserve_tile_chunks,
+                        g->spin_limit, g->missing};
     if (!g->exec || memcmp(key, g->graph_key, sizeof key) != 0) {
         if (g->exec) {
             cudaGraphExecDestroy(g->exec);
@@ -653,16 +699,19 @@ int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_
         cudaError_t e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t le = enqueue_step(g, d_pairs, d_pair_offsets, pair_capacity, d_hosts, d_host_offsets,
-                                          host_capacity, d_kprime, d_out, d_flags, g->cap_stream);
+                                          host_capacity, d_kprime, d_out, d_flags, 1u, g->cap_stream);
             e = cudaStreamEndCapture(g->cap_stream, &graph);
             if (e == cudaSuccess) e = le;
         }
+        size_t nodes = 0;
+        if (e == cudaSuccess) e = cudaGraphGetNodes(graph, nullptr, &nodes);
         if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             g->exec = nullptr;
             return vate::set_error(VATE_ECUDA, cudaGetErrorString(e));
         }
+        g->graph_nodes = (uint32_t)nodes;
         memcpy(g->graph_key, key, sizeof key);
     }
     cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
@@ -671,13 +720,24 @@ int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_
     return VATE_OK;
 }
 
+int vate_group_graph_nodes(const vate_group *g, uint32_t *nodes) {
+    if (!g || !nodes) return vate::set_error(VATE_EINVAL, "NULL argument");
+    *nodes = g->exec ? g->graph_nodes : 0u;
+    return VATE_OK;
+}
+
+int vate_group_set_wait(vate_group *g, uint64_t spin_limit, uint32_t missing) {
+    if (!g) return vate::set_error(VATE_EINVAL, "group is NULL");
+    g->spin_limit = spin_limit;
+    g->missing = missing;
+    return VATE_OK;
+}
+
 int vate_group_set_tuning(vate_group *g, const vate_group_tuning *t) {
     if (!g) return vate::set_error(VATE_EINVAL, "group is NULL");
-    if (int rc = check_tuning(t)) return rc;
-    bool tiles = t->census_tile_chunks != g->tuning.census_tile_chunks;
+    if (int rc = check_tuning(t, g->max_blocks_per_sm)) return rc;
     g->tuning = *t;
     g->tuning.reserved = 0;
-    if (tiles) return rebuild_tiles(g, g->cap_stream);
     return VATE_OK;
 }
 
@@ -702,77 +762,51 @@ int vate_group_autotune(vate_group *g, const vate_pair *d_pairs, const uint64_t 
         return vate::set_error(VATE_ECUDA, "autotune: cudaEventCreate failed");
     }
     const vate_group_tuning entry = g->tuning;
-    // every return after this point destroys the events; an error restores the
-    // tiling the group had on entry
-    auto fail = [&](int rc) {
+    auto done = [&](int rc) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        g->tuning = entry;
-        rebuild_tiles(g, st);
+        if (rc) g->tuning = entry;               // an error restores the tiling in force on entry
         return rc;
     };
-    const uint32_t hist_words = g->M * g->maxbins;
-    auto reset = [&](bool hist) {
-        return vate::launch_pool(g->arena_geom, group_reset_kernel, 8, G_THREADS, 0, st, g->d_state, g->d_hist,
-                                 hist ? hist_words : 0u);
-    };
-    auto timed = [&](auto &&fn) -> float {
-        float best = 1e30f;
-        for (int r = 0; r < 3; r++) {
-            cudaEventRecord(e0, st);
-            fn();
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            best = std::min(best, ms);
-        }
-        return best;
+    // the last step repeated: PreserveAT of the same slide changes nothing more,
+    // SetAT of the same pairs writes the same values, the census and the gather
+    // recompute the same outputs
+    auto replay = [&]() {
+        return enqueue_step(g, d_pairs, d_pair_offsets, pair_capacity, d_hosts, d_host_offsets, host_capacity,
+                            d_kprime, d_out, d_flags, 0u, st);
     };
     vate_group_tuning best = g->tuning;
-    // ingest: repeating the last step's SetATs rewrites the values they wrote
-    // (d_pairs and d_pair_offsets must be that step's inputs, see the header)
     float bt = 1e30f;
-    for (uint32_t b : {4u, 8u, 16u, 24u}) {
-        g->tuning.ingest_blocks_per_sm = b;
-        float ms = timed([&] { enqueue_ingest(g, d_pairs, d_pair_offsets, pair_capacity, st); });
-        if (ms < bt) { bt = ms; best.ingest_blocks_per_sm = b; }
-    }
-    g->tuning.ingest_blocks_per_sm = best.ingest_blocks_per_sm;
-    // census (histograms cleared before each run)
-    bt = 1e30f;
-    for (uint32_t c : {1024u, 4096u, 16384u, 65536u}) {
-        g->tuning.census_tile_chunks = c;
-        if (int rc = rebuild_tiles(g, st)) return fail(rc);
-        float ms = timed([&] { reset(true); enqueue_census(g, st); });
-        if (ms < bt) { bt = ms; best.census_tile_chunks = c; }
-    }
-    g->tuning.census_tile_chunks = best.census_tile_chunks;
-    if (int rc = rebuild_tiles(g, st)) return fail(rc);
-    reset(true);
-    enqueue_census(g, st);                       // leave the slice's census in place
-    // gather (queue counter cleared before each run)
-    bt = 1e30f;
-    for (uint32_t b : {3u, 4u, 5u, 6u}) {
-        for (uint32_t grab : {1u, 4u, 16u}) {
-            g->tuning.gather_blocks_per_sm = b;
-            g->tuning.gather_hosts_per_grab = grab;
-            float ms = timed([&] {
-                reset(false);
-                enqueue_gather(g, d_hosts, d_host_offsets, host_capacity, d_kprime, d_out, d_flags, st);
-            });
-            if (ms < bt) { bt = ms; best.gather_blocks_per_sm = b; best.gather_hosts_per_grab = grab; }
-        }
-    }
+    for (uint32_t bps = 1; bps <= (uint32_t)std::min(g->max_blocks_per_sm, 4); bps++)
+        for (uint32_t ct : {4096u, 16384u, 65536u})
+            for (uint32_t it : {2048u, 8192u})
+                for (uint32_t gt : {256u, 1024u}) {
+                    g->tuning.blocks_per_sm = bps;
+                    g->tuning.census_tile_chunks = ct;
+                    g->tuning.ingest_tile_pairs = it;
+                    g->tuning.gather_tile_hosts = gt;
+                    float ms_best = 1e30f;
+                    for (int r = 0; r < 3; r++) {
+                        cudaEventRecord(e0, st);
+                        cudaError_t e = replay();
+                        cudaEventRecord(e1, st);
+                        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                        if (e != cudaSuccess) return done(vate::set_error(VATE_ECUDA, cudaGetErrorString(e)));
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        ms_best = std::min(ms_best, ms);
+                    }
+                    if (ms_best < bt) {
+                        bt = ms_best;
+                        best = g->tuning;
+                    }
+                }
     g->tuning = best;
-    reset(false);
-    cudaError_t e = enqueue_gather(g, d_hosts, d_host_offsets, host_capacity, d_kprime, d_out, d_flags, st);
+    cudaError_t e = replay();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return fail(vate::set_error(VATE_ECUDA, cudaGetErrorString(e)));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return done(vate::set_error(VATE_ECUDA, cudaGetErrorString(e)));
     if (chosen) *chosen = best;
-    return VATE_OK;
+    return done(VATE_OK);
 }
 
 int vate_group_status(vate_group *g, uint32_t *status, int clear, void *stream) {
@@ -782,7 +816,7 @@ int vate_group_status(vate_group *g, uint32_t *status, int clear, void *stream) 
     cudaError_t e = cudaMemcpyAsync(&s, g->d_state, sizeof s, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && clear) {
-        unsigned int z = 0;
+        unsigned int z = s.status & VATE_GROUP_TIMEOUT;    // a timeout stays: the group is unusable
         e = cudaMemcpyAsync(&g->d_state->status, &z, sizeof z, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }

@@ -602,57 +602,8 @@ __global__ void __launch_bounds__(GATHER_THREADS, VATE_GATHER_MINB) gather_vec_k
     }
 }
 
-// Warp per host for segments of SB = L x AT-width bytes with SB in {2, 4, 8}
-// (L = 2, 4, 8 with byte ATs; L = 1, 2, 4 with 16-bit ones): lane j of a
-// round hashes segment 32 r + j of the host and loads the whole segment with
-// one 2-, 4- or 8-byte load (a segment is aligned to its size and never
-// crosses a 32-byte sector); RB rounds are loaded before any is tested, so
-// RB random sectors are in flight per lane.  CheckAT (ACT = BACT^0 in frame
-// 0) is the SWAR range test of the vector gather on the segment's word(s); a
-// 2-byte segment is widened to a word with inactive values (2k) in the other
-// half.  For these L a host's g VATs span g / L sectors, and the kernel is
-// bound by the L2's random-sector rate.
-template <int SB, int W, bool SHARD>
-__device__ __forceinline__ uint32_t gather_host_seg(const Geom &G, const RangeConsts &rc, uint32_t c2k, uint32_t pad,
-                                                    uint32_t aip, uint32_t lane) {
-    constexpr int RB = SB == 8 ? 4 : 8;                  // segments in flight per lane
-    constexpr int NW = SB == 8 ? 2 : 1;                  // words per segment
-    const uint32_t nseg = G.g >> G.log2L;
-    const uint64_t hk = host_key(G, aip);
-    uint32_t cnt = 0;
-    for (uint32_t r0 = 0; r0 < nseg; r0 += 32u * RB) {
-        uint32_t w[RB][NW];
-#pragma unroll
-        for (int rb = 0; rb < RB; rb++) {
-            const uint32_t sg = r0 + 32u * rb + lane;
-            bool valid = sg < nseg;
-            const uint32_t pos = valid ? seg_base_k(G, hk, sg) : 0u;      // first AT of the segment
-            if (SHARD) valid = valid && pos >= G.lo && pos < G.hi;        // another shard's segment
-            const uint8_t *at = G.pool + (uint64_t)pos * W;
-#pragma unroll
-            for (int q = 0; q < NW; q++) w[rb][q] = pad;
-            if (valid) {
-                if (SB == 2) {
-                    w[rb][0] = (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(at)) | (pad & 0xFFFF0000u);
-                } else if (SB == 4) {
-                    w[rb][0] = __ldg(reinterpret_cast<const uint32_t *>(at));
-                } else {
-                    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(at));
-                    w[rb][0] = v.x;
-                    w[rb][NW - 1] = v.y;
-                }
-            }
-        }
-#pragma unroll
-        for (int rb = 0; rb < RB; rb++) {
-#pragma unroll
-            for (int q = 0; q < NW; q++)
-                cnt += (uint32_t)__popc(W == 1 ? swar_active(w[rb][q], rc, c2k) : swar16_active(w[rb][q], rc, c2k));
-        }
-    }
-    return cnt;
-}
-
+// Warp per host for segments of 2, 4 or 8 bytes (gather_host_seg,
+// vate_device_ops.cuh), 32 hosts per warp at a time as in gather_vec_kernel.
 template <int MODE, int SB, int W, bool SHARD>
 __global__ void __launch_bounds__(GATHER_THREADS) gather_seg_kernel(Geom G, uint32_t bact0, uint32_t kprime,
                                                                     const uint64_t *__restrict__ hist,

@@ -18,6 +18,8 @@ from typing import Dict, List
 
 import numpy as np
 
+SEG_LEN = 2          # VATs per pool segment of the served monitors (as the 40 Gb/s workload)
+
 
 @dataclass
 class Arrival:
@@ -70,7 +72,7 @@ def run(V, duration: float = 5.0, budget_bytes: int = 8 << 30, max_monitors: int
         # every fourth candidate has the pool the learned model was trained for
         c = model_log2_pool if i % 4 == 0 else int(rng.integers(24, 32))
         try:
-            mid = V.vate_server_admit(srv, V.make_params(c, 10, 4096, 32, 0, seed * 100 + i, options=V.VATE_OPT_PERSIST_L2))
+            mid = V.vate_server_admit(srv, V.make_params(c, 10, 4096, SEG_LEN, 0, seed * 100 + i, options=V.VATE_OPT_PERSIST_L2))
         except V.VateError as e:
             if e.code != V.VATE_ENOMEM:
                 raise

@@ -45,15 +45,15 @@ class vate_info(C.Structure):
 
 
 class vate_group_tuning(C.Structure):
-    _fields_ = [("census_tile_chunks", C.c_uint32), ("gather_blocks_per_sm", C.c_uint32),
-                ("gather_hosts_per_grab", C.c_uint32), ("ingest_blocks_per_sm", C.c_uint32),
-                ("preserve_blocks_per_sm", C.c_uint32), ("reserved", C.c_uint32)]
+    _fields_ = [("census_tile_chunks", C.c_uint32), ("blocks_per_sm", C.c_uint32),
+                ("gather_tile_hosts", C.c_uint32), ("ingest_tile_pairs", C.c_uint32),
+                ("preserve_tile_chunks", C.c_uint32), ("reserved", C.c_uint32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
 
 
-VATE_GROUP_BAD_OFFSETS, VATE_GROUP_BAD_KPRIME = 1, 2
+VATE_GROUP_BAD_OFFSETS, VATE_GROUP_BAD_KPRIME, VATE_GROUP_TIMEOUT = 1, 2, 4
 
 
 class vate_server_config(C.Structure):
@@ -106,6 +106,8 @@ def _load() -> C.CDLL:
         "vate_group_step_graph": (i, [vp, vp, vp, u64, vp, vp, u64, vp, vp, vp, vp]),
         "vate_group_autotune": (i, [vp, vp, vp, u64, vp, vp, u64, vp, vp, vp, P(vate_group_tuning), vp]),
         "vate_group_set_tuning": (i, [vp, P(vate_group_tuning)]),
+        "vate_group_set_wait": (i, [vp, u64, u32]),
+        "vate_group_graph_nodes": (i, [vp, P(C.c_uint32)]),
         "vate_group_get_tuning": (i, [vp, P(vate_group_tuning)]),
         "vate_group_status": (i, [vp, P(u32), i, vp]),
         "vate_group_copy_pool": (i, [vp, u32, vp, vp]),
@@ -461,6 +463,16 @@ def vate_group_autotune(g, pairs, pair_offsets, hosts, host_offsets, kprime, out
 
 def vate_group_set_tuning(g, t: vate_group_tuning) -> None:
     _check(_lib.vate_group_set_tuning(g, C.byref(t)))
+
+
+def vate_group_set_wait(g, spin_limit: int, missing: int = 0) -> None:
+    _check(_lib.vate_group_set_wait(g, spin_limit, missing))
+
+
+def vate_group_graph_nodes(g) -> int:
+    n = C.c_uint32()
+    _check(_lib.vate_group_graph_nodes(g, C.byref(n)))
+    return int(n.value)
 
 
 def vate_group_get_tuning(g) -> vate_group_tuning:

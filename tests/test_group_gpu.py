@@ -1,14 +1,16 @@
 """Monitor groups (include/vate_group.h): many independent VATE monitors
-advanced together in one set of persistent launches per slice.
+advanced together in one persistent launch per slice.
 
 Every monitor of a group must compute exactly what a single vate_handle with
 the same parameters computes on the same pairs and hosts: the pool byte for
 byte, the census, and the estimates and flags bit for bit (same device
 arithmetic).  One monitor is also checked against the CPU oracle.  The CUDA
-graph form must equal the plain form, the autotuner must leave state and
-outputs unchanged, and malformed device-side offsets and k' must be clamped
-and reported, never read out of bounds.  The 64-monitor configuration is run
-at full size as the benchmark drives it.
+graph form must equal the plain form and hold one node, the autotuner must
+leave state and outputs unchanged, malformed device-side offsets and k' must
+be clamped and reported, never read out of bounds, and a device-side wait
+that cannot be satisfied must give up within its limit and report
+VATE_GROUP_TIMEOUT (the kernel returns; nothing hangs).  The 64-monitor
+configuration is run at full size as the benchmark drives it.
 """
 import numpy as np
 import pytest
@@ -134,7 +136,7 @@ def test_group_equals_single_handles(V):
     run_group_vs_single(V, MONITORS_L32, nslices=14)
 
 
-@pytest.mark.parametrize("L", [1, 16, 64])
+@pytest.mark.parametrize("L", [1, 2, 4, 8, 16, 64])
 def test_group_other_segment_lengths(V, L):
     mons = [(14, 2, 128, L, 0, 11), (15, 5, 256, L, 1, 12), (16, 7, 64 * max(1, L // 16), L, 0, 13)]
     run_group_vs_single(V, mons, nslices=12)
@@ -142,6 +144,80 @@ def test_group_other_segment_lengths(V, L):
 
 def test_group_graph_replay_equals_single_handles(V):
     run_group_vs_single(V, MONITORS_L32[:5], nslices=12, graph=True)
+
+
+def test_group_step_graph_is_one_kernel_node(V):
+    mons = MONITORS_L32[:3]
+    grp = V.VateGroup([V.make_params(*m) for m in mons])
+    assert V.vate_group_graph_nodes(grp.g) == 0
+    tr = Traffic(SMALL, pkts_per_slice=1000)
+    P = as_i32(tr.slice_pairs(0, n=300))
+    PO = torch.tensor([0, 100, 200, 300], dtype=torch.int64, device="cuda")
+    H = as_i32(tr.aips[:30])
+    HO = torch.tensor([0, 10, 20, 30], dtype=torch.int64, device="cuda")
+    KP = torch.tensor([m[1] for m in mons], dtype=torch.int32, device="cuda")
+    out = torch.zeros(30, dtype=torch.float32, device="cuda")
+    grp.step(P, PO, H, HO, KP, out, graph=True)
+    grp.step(P, PO, H, HO, KP, out, graph=True)
+    assert V.vate_group_graph_nodes(grp.g) == 1
+    assert grp.status() == 0
+    grp.close()
+
+
+@pytest.mark.parametrize("spin_limit", [0, 1000])
+def test_group_unsatisfiable_wait_times_out_and_returns(V, spin_limit):
+    # Every wait of the step is made unsatisfiable (its target raised by one
+    # item); with a limit of 0 or 1,000 looks the kernel gives up, sets
+    # VATE_GROUP_TIMEOUT and returns.  The timed-out group then does no more
+    # work: a later step changes no pool byte.  Then it is destroyed.
+    import time
+    mons = MONITORS_L32[:3]
+    grp = V.VateGroup([V.make_params(*m) for m in mons])
+    tr = Traffic(SMALL, pkts_per_slice=1000)
+    P = as_i32(tr.slice_pairs(0, n=300))
+    PO = torch.tensor([0, 100, 200, 300], dtype=torch.int64, device="cuda")
+    H = as_i32(tr.aips[:30])
+    HO = torch.tensor([0, 10, 20, 30], dtype=torch.int64, device="cuda")
+    KP = torch.tensor([m[1] for m in mons], dtype=torch.int32, device="cuda")
+    out = torch.zeros(30, dtype=torch.float32, device="cuda")
+    grp.step(P, PO, H, HO, KP, out)                  # a normal step first
+    assert grp.status() == 0
+    V.vate_group_set_wait(grp.g, spin_limit, 1)
+    t0 = time.perf_counter()
+    grp.step(P, PO, H, HO, KP, out)
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 5.0
+    assert grp.status() & V.VATE_GROUP_TIMEOUT
+    before = []
+    for m, mon in enumerate(mons):
+        t = torch.empty(1 << mon[0], dtype=torch.uint8, device="cuda")
+        grp.copy_pool(m, t)
+        before.append(t)
+    V.vate_group_set_wait(grp.g, 1 << 23, 0)
+    grp.step(as_i32(tr.slice_pairs(1, n=300)), PO, H, HO, KP, out)
+    torch.cuda.synchronize()
+    for m, mon in enumerate(mons):
+        t = torch.empty(1 << mon[0], dtype=torch.uint8, device="cuda")
+        grp.copy_pool(m, t)
+        assert torch.equal(t, before[m]), "a timed-out group changed monitor %d's pool" % m
+    assert grp.status(clear=True) & V.VATE_GROUP_TIMEOUT
+    assert grp.status() & V.VATE_GROUP_TIMEOUT       # not cleared
+    grp.close()
+
+
+def test_group_tuning_is_checked(V):
+    grp = V.VateGroup([V.make_params(*m) for m in MONITORS_L32[:2]])
+    t = V.vate_group_get_tuning(grp.g)
+    assert t.blocks_per_sm >= 1 and t.census_tile_chunks >= 256
+    for field, bad in (("blocks_per_sm", 0), ("blocks_per_sm", 99), ("census_tile_chunks", 3000),
+                       ("gather_tile_hosts", 100), ("ingest_tile_pairs", 70000), ("preserve_tile_chunks", 0)):
+        u = V.vate_group_tuning.from_buffer_copy(t)
+        setattr(u, field, bad)
+        with pytest.raises(V.VateError) as e:
+            V.vate_group_set_tuning(grp.g, u)
+        assert e.value.code == V.VATE_EINVAL, field
+    V.vate_group_set_tuning(grp.g, t)
+    grp.close()
 
 
 def test_group_autotune_keeps_state_and_outputs(V):
