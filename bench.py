@@ -89,7 +89,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator train/evaluate run")
     ap.add_argument("--workload", default="link40g",
                     choices=["link40g", "monitors64", "serving", "pt", "learned-kernels", "probes", "ingest-mix",
-                             "placement"],
+                             "placement", "close-kernels"],
                     help="link40g: the headline single-monitor workload; monitors64: 64 independent monitors "
                          "advanced together (vate_group, CUDA graph per slice); learned-kernels: the learned "
                          "estimator's kernels timed one by one at 2^20 hosts; probes: random 32-byte sector "
@@ -1187,8 +1187,53 @@ def run_placement(args, seg_lens=(1, 4, 8, 16, 32, 64), n_slices=40):
                      "exact distinct peers in the last k slices", "rows": rows}
 
 
+def run_close_kernels(args):
+    """The slice step's kernels one by one at the 40 Gb/s shape (this run's k,
+    L and pool; 2^20 hosts): 12 slices of 5M pairs are ingested and closed,
+    then each of 10 more slices is timed piece by piece with CUDA events --
+    vate_ingest (slide + SetAT), vate_close_slice (census), vate_estimate
+    (gather + Eq. 11) -- with L2 flushed before the ingest.  Small enough to
+    run under ncu (about 0.6 GB on the device)."""
+    import torch
+    import paper_1812_00282_b300 as V
+    from traffic import LINK40G, DeviceTraffic, Traffic
+    torch.cuda.set_device(0)
+    dt = DeviceTraffic(Traffic(LINK40G, pkts_per_slice=args.pkts))
+    hosts = dt.hosts()[: args.aips].contiguous()
+    mon = V.Vate(C, args.k, G, args.seg_len, args.partition, seed=0xC2, at_bits=args.at_bits,
+                 options=V.VATE_OPT_PERSIST_L2)
+    out = torch.empty(hosts.numel(), dtype=torch.float32, device="cuda")
+    fl = torch.empty(hosts.numel(), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t = {"ingest": [], "census": [], "gather": []}
+    for s in range(22):
+        p = dt.slice_pairs(s)
+        flush.fill_(s & 0xFF)
+        ev[0].record()
+        mon.ingest(p, s)
+        ev[1].record()
+        mon.close_slice(s)
+        ev[2].record()
+        mon.estimate(hosts, args.k, out, fl)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if s >= 12:
+            t["ingest"].append(ev[0].elapsed_time(ev[1]))
+            t["census"].append(ev[1].elapsed_time(ev[2]))
+            t["gather"].append(ev[2].elapsed_time(ev[3]))
+    mon.close()
+    return {"workload": "slice step kernels at the 40 Gb/s shape: 2^26-AT pool, k = %d, g = 4096, L = %d, %d pairs, "
+                        "%d hosts" % (args.k, args.seg_len, args.pkts, hosts.numel()),
+            "unit": "ms (CUDA events, mean of 10 slices after 12)",
+            "ms": {n: round(statistics.mean(v), 4) for n, v in t.items()}}
+
+
 def main():
     args = parse()
+    if args.workload == "close-kernels":
+        print(json.dumps(run_close_kernels(args)), flush=True)
+        return
     if args.workload == "placement":
         print(json.dumps(run_placement(args)), flush=True)
         return
