@@ -53,6 +53,8 @@ extern "C" {
 #define VATE_ECUDA     4   /* a CUDA runtime call failed (no device, bad stream,
                               launch failure); see vate_last_error()           */
 #define VATE_ETIMEOUT  5   /* a bounded device-side wait gave up               */
+#define VATE_EDROPPED  6   /* a serving request dropped by an injected fault
+                              (vate_server_inject, include/vate_server.h)      */
 
 /* ---- per-host flags written by vate_estimate ------------------------- */
 #define VATE_FLAG_SAT       1u  /* every VAT of the host active: V0 read as 1  */
@@ -273,6 +275,35 @@ int vate_host_block(const vate_params *params, uint64_t pid, uint32_t *block);
  * cudaMalloc, cudaFree or allocating library routine is called. */
 int vate_census_noalloc(const vate_params *params, const uint8_t *d_pool, uint32_t bact0, uint64_t *d_hist,
                         void *stream);
+
+/* ---- the checked build --------------------------------------------------
+ * The paper has no counterpart; these stand in for a memory checker, which
+ * this GPU pool does not offer.  Built with VATE_DEBUG defined (the library
+ * libvate_debug.so beside libvate.so), the kernels check what their indexing
+ * relies on -- every computed pool position below P, every AT value they read
+ * within the counter's range (2k for timestamps, k for recorders), every block
+ * index below 2k -- and on a violation record it in the handle's status words
+ * instead of trapping: a bad position's access is skipped, a bad value is read
+ * as it is (no kernel leaves its buffers whatever a value holds).  Without
+ * VATE_DEBUG the checks are compiled out and the status stays 0. */
+#define VATE_DBG_POSITION 1u   /* a computed pool position outside the pool (access skipped) */
+#define VATE_DBG_VALUE    2u   /* an AT value above the counter's range                        */
+#define VATE_DBG_BLOCK    4u   /* a block index outside [0, 2k)                                */
+
+/* 1 if this library was built with the checks, else 0. */
+int vate_debug_checks(void);
+
+/* The VATE_DBG_* bits recorded on the handle's device work so far (OR-ed) and,
+ * in *first (may be NULL), the first report: bit 63 set, the VATE_DBG_* bit in
+ * bits 56-62, the pool position (or 16-byte chunk, or segment) in bits 0-55.
+ * clear = 1 resets both.  Synchronises `stream`. */
+int vate_debug_status(vate_handle *h, uint32_t *bits, uint64_t *first, int clear, void *stream);
+
+/* Checked build only: overwrite the stored value of pool position pid with
+ * `value` as it is (no range check, no frame conversion) -- a deliberate
+ * corruption for tests of the checks.  Synchronises `stream`.  Elsewhere, and
+ * for packed pools, VATE_EINVAL. */
+int vate_debug_poke(vate_handle *h, uint64_t pid, uint32_t value, void *stream);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *vate_last_error(void);

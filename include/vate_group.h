@@ -125,6 +125,14 @@ int vate_group_get_tuning(const vate_group *g, vate_group_tuning *t);
  * apply to later steps (a graph is re-captured).  Errors: VATE_EINVAL. */
 int vate_group_set_wait(vate_group *g, uint64_t spin_limit, uint32_t missing);
 
+/* Trace of later steps, for tuning: work item j of a step writes four words
+ * at d_trace[4j..4j+3] (j < capacity; device uint64): the %globaltimer
+ * nanoseconds when it was handed out, when its wait for the earlier phases of
+ * its monitor ended and when it finished, then (SM << 32) | (monitor << 8) |
+ * phase (0 begin, 1 PreserveAT, 2 SetAT, 3 census, 4 gather).  capacity 0
+ * stops tracing.  Errors: VATE_EINVAL. */
+int vate_group_set_trace(vate_group *g, uint64_t *d_trace, uint32_t capacity);
+
 /* Kernel nodes of the captured step graph (0 before the first
  * vate_group_step_graph): one, the step's persistent launch. */
 int vate_group_graph_nodes(const vate_group *g, uint32_t *nodes);

@@ -19,7 +19,9 @@
  *     monitor has a model, with the closed form of Eq. 11 as its fallback, and
  *     the closed form otherwise;
  *   - latency: per request, from submission to completion seen by the
- *     scheduler (queueing included); p50/p99 per request kind.
+ *     scheduler (queueing included); p50/p99 per request kind;
+ *   - order: requests go to the device in arrival order per monitor (a
+ *     monitor whose next request is held back does not hold up the others).
  * A monitor's results do not depend on the other monitors or on the timing of
  * the requests: every monitor computes what its vate_handle computes alone.
  *
@@ -94,6 +96,33 @@ int vate_server_wait(vate_server *s, uint64_t ticket, uint32_t timeout_ms);
 
 /* Wait up to timeout_ms for every submitted request. */
 int vate_server_drain(vate_server *s, uint32_t timeout_ms);
+
+/* Host-side fault injection, for tests of failure handling that need no GPU
+ * fault (the paper has no counterpart).  Faults act in the scheduler:
+ *   VATE_FAULT_STALL  the scheduler neither retires nor dispatches anything for
+ *                     `ms` milliseconds (a stalled host thread); requests queue.
+ *   VATE_FAULT_DROP   the next `count` ingest requests of monitor `mon` are
+ *                     dropped when their turn comes: they complete with
+ *                     VATE_EDROPPED through vate_server_wait and never reach
+ *                     the device (lost batches); the monitor's state is that
+ *                     of a stream without them.
+ *   VATE_FAULT_HOLD   the next `count` requests of monitor `mon` are each held
+ *                     back `ms` milliseconds when they reach the front of the
+ *                     monitor's line (late batches); the monitor's later
+ *                     requests wait behind them, other monitors' pass them.
+ * Requests are dispatched in arrival order per monitor, so no fault changes
+ * the results of a monitor it does not drop batches of.  Errors: VATE_EINVAL
+ * (unknown kind or monitor). */
+#define VATE_FAULT_STALL 1u
+#define VATE_FAULT_DROP  2u
+#define VATE_FAULT_HOLD  3u
+typedef struct {
+    uint32_t kind;
+    int32_t mon;
+    uint32_t count;
+    uint32_t ms;
+} vate_server_fault;
+int vate_server_inject(vate_server *s, const vate_server_fault *f);
 
 /* Counters and latency percentiles since creation or the last reset. */
 int vate_server_get_stats(vate_server *s, vate_server_stats *out, int reset);

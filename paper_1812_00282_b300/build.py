@@ -21,6 +21,7 @@ LIB = os.path.join(HERE, "libvate.so")
 SOURCES = ["vate_api.cu", "vate_kernels.cu", "vate_packed.cu", "vate_noalloc.cu", "vate_group.cu", "vate_learned.cu",
            "vate_server.cu"]
 PROBE_LIB = os.path.join(HERE, "libvate_probe.so")   # memory-system probes for the benchmark (include/vate_probe.h)
+DEBUG_LIB = os.path.join(HERE, "libvate_debug.so")   # the checked build: the same sources with VATE_DEBUG
 PROBE_SOURCES = ["vate_probe.cu"]
 HEADERS = ["vate_device.cuh", "vate_device_ops.cuh", "vate_ages.cuh", "vate_launch.cuh", "vate_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -42,9 +43,9 @@ def _stale(lib, sources) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(lib, sources, verbose):
+def _compile(lib, sources, verbose, defines=()):
     tmp = lib + ".tmp%d" % os.getpid()
-    extra = os.environ.get("VATE_NVCC_DEFINES", "").split()
+    extra = os.environ.get("VATE_NVCC_DEFINES", "").split() + list(defines)
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-shared", *extra,
            "-I", INCLUDE, "-I", CSRC, "-o", tmp] + [os.path.join(CSRC, f) for f in sources]
     if verbose:
@@ -55,9 +56,10 @@ def _compile(lib, sources, verbose):
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    for lib, sources in ((LIB, SOURCES), (PROBE_LIB, PROBE_SOURCES)):
+    for lib, sources, defines in ((LIB, SOURCES, ()), (PROBE_LIB, PROBE_SOURCES, ()),
+                                  (DEBUG_LIB, SOURCES, ("-DVATE_DEBUG",))):
         if force or _stale(lib, sources):
-            _compile(lib, sources, verbose)
+            _compile(lib, sources, verbose, defines)
     return LIB
 
 

@@ -126,6 +126,7 @@ struct vate_handle {
     uint64_t *d_hist = nullptr;       // census of the last close, 2k+1 counters
     uint64_t *d_acc = nullptr;        // census scratch: 2k+1 counters the blocks add into, zero between calls
     unsigned int *d_ticket = nullptr; // census scratch: blocks finished
+    unsigned long long *d_dbg = nullptr;   // checked build: [VATE_DBG_* bits, first report]
     // host-copy staging (allocated on first use)
     // pairs: a ring of staging buffers filled on their own stream, so that the
     // pairs of the next slice are copied while this slice is estimated
@@ -372,12 +373,15 @@ static int create_range(const vate_params *params, uint64_t lo, uint64_t hi, voi
     if (cudaMalloc(&mem, held_bytes) == cudaSuccess) h->G.pool = mem - G.lo * G.atw;   // position 0's address
     if (!mem || cudaMalloc(&h->d_hist, nbins * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&h->d_acc, nbins * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMalloc(&h->d_ticket, sizeof(unsigned int)) != cudaSuccess) {
+        cudaMalloc(&h->d_ticket, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc(&h->d_dbg, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         vate_destroy(h);
         return fail(VATE_ENOMEM, "out of device memory for a pool of 2^%u ATs", G.c);
     }
+    h->G.dbg = h->d_dbg;
     e = cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_dbg, 0, 2 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_hist, 0, nbins * sizeof(uint64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_acc, 0, nbins * sizeof(uint64_t), st);
     if (e == cudaSuccess) e = vate::launch_init(h->G, st, h->sms);
@@ -420,6 +424,7 @@ int vate_destroy(vate_handle *h) {
     cudaFree(h->d_hist);
     cudaFree(h->d_acc);
     cudaFree(h->d_ticket);
+    cudaFree(h->d_dbg);
     for (int i = 0; i < 2; i++) {
         cudaFree(h->d_stage[i]);
         cudaFree(h->d_stage_out[i]);
@@ -438,6 +443,50 @@ int vate_destroy(vate_handle *h) {
     if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
     delete h;
     return VATE_OK;
+}
+
+int vate_debug_checks(void) {
+#ifdef VATE_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int vate_debug_status(vate_handle *h, uint32_t *bits, uint64_t *first, int clear, void *stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!bits) return fail(VATE_EINVAL, "bits is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long w[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(w, h->d_dbg, sizeof w, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && clear) {
+        e = cudaMemsetAsync(h->d_dbg, 0, sizeof w, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "debug status");
+    *bits = (uint32_t)w[0];
+    if (first) *first = w[1];
+    return VATE_OK;
+}
+
+int vate_debug_poke(vate_handle *h, uint64_t pid, uint32_t value, void *stream) {
+#ifndef VATE_DEBUG
+    (void)h; (void)pid; (void)value; (void)stream;
+    return fail(VATE_EINVAL, "vate_debug_poke exists in the checked build (VATE_DEBUG) only");
+#else
+    if (int rc = check_handle(h)) return rc;
+    if (h->G.packed) return fail(VATE_EINVAL, "a packed pool cannot be poked");
+    if (pid < h->G.lo || pid >= h->G.hi) return fail(VATE_EINVAL, "pid outside the positions held");
+    if (value > (h->G.atw == 1u ? 0xFFu : 0xFFFFu)) return fail(VATE_EINVAL, "value wider than an AT");
+    const uint16_t v16 = (uint16_t)value;
+    const uint8_t v8 = (uint8_t)value;
+    cudaError_t e = cudaMemcpyAsync(h->G.pool + pid * h->G.atw, h->G.atw == 1u ? (const void *)&v8 : (const void *)&v16,
+                                    h->G.atw, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "poke");
+    return VATE_OK;
+#endif
 }
 
 int vate_get_info(const vate_handle *h, vate_info *out) {

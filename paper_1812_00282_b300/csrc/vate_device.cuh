@@ -53,6 +53,7 @@ struct Geom {
     uint32_t atb, pn;    // packed: bits per AT and fields per word
     uint64_t mpn;        // packed: ceil(2^64 / pn)
     uint64_t lo, hi;     // pool positions held: [0, P) for a whole pool, a 64-aligned range for a shard
+    unsigned long long *dbg;   // checked build (VATE_DEBUG): device status [bits, first report]; may be NULL
     // host side only: L2 access-policy window over the pool for every launch
     // that touches it (l2_window_bytes = 0: none)
     uint64_t l2_window_bytes;
@@ -154,6 +155,48 @@ VATE_HD uint32_t act_of_block(uint32_t bact0, uint32_t blk, uint32_t twok) {
 // ---- SWAR helpers (bytes < 128) -------------------------------------------
 constexpr uint32_t ONES = 0x01010101u;
 constexpr uint32_t HIGH = 0x80808080u;
+
+// ---- checked build ---------------------------------------------------------
+// Compiled with VATE_DEBUG, the kernels check what their indexing relies on --
+// a computed pool position below P, every AT value read within the counter's
+// range, every block index below 2k -- and report a violation into the
+// handle's status words (G.dbg[0]: VATE_DBG_* bits, OR-ed; G.dbg[1]: the first
+// report, bit 63 set, the position or chunk in the low bits and the bit in
+// bits 56-62) instead of trapping: a bad position's access is skipped, a bad
+// value is read as it is (every kernel stays in bounds whatever a value
+// holds).  Without VATE_DEBUG the checks compile to nothing.
+#define VATE_DBG_POSITION 1u
+#define VATE_DBG_VALUE 2u
+#define VATE_DBG_BLOCK 4u
+
+__device__ __forceinline__ void debug_report(const Geom &G, uint32_t bit, uint64_t where) {
+    if (!G.dbg) return;
+    atomicOr(G.dbg, (unsigned long long)bit);
+    atomicCAS(G.dbg + 1, 0ull, (1ull << 63) | ((unsigned long long)bit << 56) | (where & ((1ull << 56) - 1)));
+}
+
+// a word of stored values (bytes, or 16-bit halves for k >= 64) with a value
+// above the counter's range (2k for timestamps, k for recorders)
+__device__ __forceinline__ bool word_out_of_range(const Geom &G, uint32_t w) {
+    const uint32_t top = G.counter == 1u ? G.k : G.twok;
+    if (G.atw == 1u) return ((((w & ~HIGH) + (127u - top) * ONES) | w) & HIGH) != 0u;
+    return (w & 0xFFFFu) > top || (w >> 16) > top;
+}
+
+#ifdef VATE_DEBUG
+#define VATE_CHECK_POSITION(G, pid) ((pid) < (G).P ? true : (debug_report((G), VATE_DBG_POSITION, (pid)), false))
+#define VATE_CHECK_WORD(G, w, where) \
+    do { if (word_out_of_range((G), (w))) debug_report((G), VATE_DBG_VALUE, (where)); } while (0)
+#define VATE_CHECK_VALUE(G, v, where) \
+    do { if ((v) > ((G).counter == 1u ? (G).k : (G).twok)) debug_report((G), VATE_DBG_VALUE, (where)); } while (0)
+#define VATE_CHECK_BLOCK(G, blk, where) \
+    do { if ((blk) >= (G).twok) debug_report((G), VATE_DBG_BLOCK, (where)); } while (0)
+#else
+#define VATE_CHECK_POSITION(G, pid) true
+#define VATE_CHECK_WORD(G, w, where) do { } while (0)
+#define VATE_CHECK_VALUE(G, v, where) do { } while (0)
+#define VATE_CHECK_BLOCK(G, blk, where) do { } while (0)
+#endif
 
 // Algorithm 1 on four ATs of one word.  For an AT whose ACT is act, the
 // values active in W(t-k'+1, k') are {act, act-1, ..., act-k'+1} mod 2k.

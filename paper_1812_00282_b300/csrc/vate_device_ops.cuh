@@ -202,7 +202,13 @@ __device__ __forceinline__ uint32_t gather_host_vec(const Geom &G, const RangeCo
                 valid[j] = FULL || c < (segs_here << CPSL);
                 if (SHARD) valid[j] = valid[j] && (q - q_lo) < q_n;
                 w[j] = make_uint4(0u, 0u, 0u, 0u);
-                if (valid[j]) w[j] = CG ? __ldcg(pool16 + q) : __ldg(pool16 + q);
+                if (valid[j]) {
+                    w[j] = CG ? __ldcg(pool16 + q) : __ldg(pool16 + q);
+                    VATE_CHECK_WORD(G, w[j].x, q);
+                    VATE_CHECK_WORD(G, w[j].y, q);
+                    VATE_CHECK_WORD(G, w[j].z, q);
+                    VATE_CHECK_WORD(G, w[j].w, q);
+                }
             }
         }
         uint32_t acc = 0;
@@ -254,6 +260,7 @@ __device__ __forceinline__ uint32_t gather_host_scalar(const Geom &G, uint32_t b
         uint32_t pid = vat_pid_k(G, hk, i);
         if (pid < G.lo || pid >= G.hi) continue;             // another shard's AT
         uint32_t v = load_at<CG>(G, pid);
+        VATE_CHECK_VALUE(G, v, pid);
         if (G.counter == 1u) {
             cnt += check_dr(v, kprime) ? 1u : 0u;
             continue;
@@ -310,8 +317,10 @@ __device__ __forceinline__ uint32_t gather_host_seg(const Geom &G, const RangeCo
 #pragma unroll
         for (int rb = 0; rb < RB; rb++) {
 #pragma unroll
-            for (int q = 0; q < NW; q++)
+            for (int q = 0; q < NW; q++) {
+                VATE_CHECK_WORD(G, w[rb][q], r0 + 32u * rb + lane);
                 cnt += (uint32_t)__popc(W == 1 ? swar_active(w[rb][q], rc, c2k) : swar16_active(w[rb][q], rc, c2k));
+            }
         }
     }
     return cnt;

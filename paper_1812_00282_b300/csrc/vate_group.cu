@@ -79,6 +79,8 @@ struct StepArgs {
     unsigned long long spin_limit;
     uint32_t M, maxbins;
     uint32_t census_tile, ingest_tile, gather_tile, preserve_tile;
+    unsigned long long *trace;            // NULL, or 4 words per item (vate_group_set_trace)
+    uint32_t trace_cap;                   // items the trace buffer holds
     uint32_t advance;                     // 1: the next slice; 0: repeat the last slice (autotuner)
     uint32_t missing;                     // added to every wait's target (tests of the timeout path)
     uint32_t u1, u2, u3;                  // run-time ones (the vector gather's multiply-adds)
@@ -143,6 +145,18 @@ __device__ __forceinline__ PreserveSpan preserve_span(const Geom &G, unsigned lo
 // Thread 0 of a block: wait until *done >= target, with at most `limit`
 // sleeps of ~128 ns.  A wait that gives up marks the launch (poisoned) and
 // the group (VATE_GROUP_TIMEOUT); a wait in a marked launch gives up at once.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t sm_id() {
+    uint32_t id;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+    return id;
+}
+
 __device__ bool wait_done(const unsigned int *done, unsigned int target, GroupState *st, unsigned long long limit) {
     for (unsigned long long spins = 0;; spins++) {
         if (*reinterpret_cast<const volatile unsigned int *>(done) >= target) {
@@ -191,7 +205,7 @@ __global__ void __launch_bounds__(G_THREADS) group_step_kernel(StepArgs a) {
     uint32_t *cols = kp + M;                                          // census lane columns [warps][pairs][32]
     const uint32_t maxpairs = (a.maxbins + 1u) / 2u;
 
-    __shared__ unsigned long long s_step;
+    __shared__ unsigned long long s_step, s_t0, s_t1;
     __shared__ uint32_t s_j, s_m, s_p, s_t, s_ok;
     __shared__ uint64_t s_n0;
     __shared__ Geom sG;
@@ -263,6 +277,7 @@ __global__ void __launch_bounds__(G_THREADS) group_step_kernel(StepArgs a) {
         if (tid == 0) {
             const uint32_t j = atomicAdd(&st->q_items, 1u);
             s_j = j;
+            if (a.trace) s_t0 = global_ns();
             if (j < total) {
                 const uint32_t m = find_monitor(pre, M, j);
                 const uint32_t local = j - pre[m];
@@ -273,6 +288,7 @@ __global__ void __launch_bounds__(G_THREADS) group_step_kernel(StepArgs a) {
                 s_p = p;
                 s_t = local - cm[p];
                 s_ok = wait_done(a.done + m, cm[p] + a.missing, st, a.spin_limit) ? 1u : 0u;
+                if (a.trace) s_t1 = global_ns();
                 sG = a.descs[m];
                 if (p == 4) {                       // N0 of Eq. 11 from the census (written in this launch)
                     uint64_t act = 0;
@@ -306,7 +322,8 @@ __global__ void __launch_bounds__(G_THREADS) group_step_kernel(StepArgs a) {
 #pragma unroll 4
                 for (uint64_t i = i0 + tid; i < i1; i += G_THREADS) {
                     const uint2 q = __ldcs(p2 + i);
-                    G.pool[vat_pid(G, q.x, bh(G, q.y))] = v;
+                    const uint32_t pid = vat_pid(G, q.x, bh(G, q.y));
+                    if (VATE_CHECK_POSITION(G, pid)) G.pool[pid] = v;
                 }
             } else if (p == 3) {                                 // C: census tile into lane columns
                 uint32_t *col = cols + (size_t)warp * maxpairs * 32u + lane;
@@ -380,6 +397,13 @@ __global__ void __launch_bounds__(G_THREADS) group_step_kernel(StepArgs a) {
         __threadfence();
         __syncthreads();
         if (tid == 0 && s_ok) atomicAdd(a.done + s_m, 1u);
+        if (tid == 0 && a.trace && s_j < a.trace_cap) {        // handed out, started, finished, what and where
+            unsigned long long *tr = a.trace + 4ull * s_j;
+            tr[0] = s_t0;
+            tr[1] = s_t1;
+            tr[2] = global_ns();
+            tr[3] = ((unsigned long long)sm_id() << 32) | ((unsigned long long)s_m << 8) | s_p;
+        }
     }
     }   // s_ok
 
@@ -430,12 +454,14 @@ struct vate_group {
     vate_group_tuning tuning;
     unsigned long long spin_limit = DEFAULT_SPIN_LIMIT;
     uint32_t missing = 0;
+    unsigned long long *trace = nullptr;   // vate_group_set_trace
+    uint32_t trace_cap = 0;
     bool persist_l2 = false;         // VATE_OPT_PERSIST_L2 in some monitor's options
     // CUDA graph of one step
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint32_t graph_nodes = 0;
-    uint64_t graph_key[14] = {};
+    uint64_t graph_key[16] = {};
 };
 
 namespace {
@@ -513,6 +539,8 @@ cudaError_t enqueue_step(vate_group *g, const vate_pair *pairs, const uint64_t *
     a.preserve_tile = g->tuning.preserve_tile_chunks;
     a.advance = advance;
     a.missing = g->missing;
+    a.trace = g->trace;
+    a.trace_cap = g->trace_cap;
     a.u1 = a.u2 = a.u3 = 1u;
     const size_t smem = step_smem(g->M, g->maxbins);
     const int grid = g->sms * (int)g->tuning.blocks_per_sm;
@@ -685,11 +713,11 @@ int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_
                                  d_kprime, d_out))
         return rc;
     const vate_group_tuning &t = g->tuning;
-    uint64_t key[14] = {(uint64_t)d_pairs, (uint64_t)d_pair_offsets, pair_capacity, (uint64_t)d_hosts,
+    uint64_t key[16] = {(uint64_t)d_pairs, (uint64_t)d_pair_offsets, pair_capacity, (uint64_t)d_hosts,
                         (uint64_t)d_host_offsets, host_capacity, (uint64_t)d_kprime, (uint64_t)d_out,
                         (uint64_t)d_flags, ((uint64_t)t.census_tile_chunks << 32) | t.blocks_per_sm,
                         ((uint64_t)t.gather_tile_hosts << 32) | t.ingest_tile_pairs, t.preserve_tile_chunks,
-                        g->spin_limit, g->missing};
+                        g->spin_limit, g->missing, (uint64_t)g->trace, g->trace_cap};
     if (!g->exec || memcmp(key, g->graph_key, sizeof key) != 0) {
         if (g->exec) {
             cudaGraphExecDestroy(g->exec);
@@ -723,6 +751,13 @@ int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_
 int vate_group_graph_nodes(const vate_group *g, uint32_t *nodes) {
     if (!g || !nodes) return vate::set_error(VATE_EINVAL, "NULL argument");
     *nodes = g->exec ? g->graph_nodes : 0u;
+    return VATE_OK;
+}
+
+int vate_group_set_trace(vate_group *g, uint64_t *d_trace, uint32_t capacity) {
+    if (!g || (capacity && !d_trace)) return vate::set_error(VATE_EINVAL, "bad group or trace buffer");
+    g->trace = capacity ? reinterpret_cast<unsigned long long *>(d_trace) : nullptr;
+    g->trace_cap = capacity;
     return VATE_OK;
 }
 

@@ -57,6 +57,7 @@ __global__ void init_pool_kernel(uint8_t *__restrict__ pool, uint64_t nbytes, ui
 __device__ __forceinline__ void set_at(const Geom &G, uint32_t bact0, uint32_t aip, uint32_t bip) {
     uint32_t vid = bh(G, bip);
     uint32_t pid = vat_pid(G, aip, vid);
+    if (!VATE_CHECK_POSITION(G, pid)) return;           // checked build: a position outside the pool
     if (pid < G.lo || pid >= G.hi) return;              // another shard's AT
     uint32_t v = G.counter == 1u ? 0u : bact0;
     if (G.packed) {                  // clear the field, then set it (see vate_packed.cu)
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(256) frame_convert_kernel(Geom G, const uint8_
         const bool one = b0 == block_of(G, (uint32_t)(pid0 + o1 - 1));
         for (uint64_t o = o0; o < o1; o++) {
             const uint32_t blk = one ? b0 : block_of(G, (uint32_t)(pid0 + o));
+            VATE_CHECK_BLOCK(G, blk, pid0 + o);
             const uint32_t x = W == 1u ? (uint32_t)src[o] : (uint32_t)reinterpret_cast<const uint16_t *>(src)[o];
             uint32_t y;
             if (G.counter == 1u)          // distance recorders have one frame; out-of-range values become inactive
@@ -267,6 +269,12 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32
         for (int c = 0; c < U; c++) {
             const uint4 w = ws[c];
             const bool real = q + (uint64_t)c * stride < end;
+            if (real) {
+                VATE_CHECK_WORD(G, w.x, q + (uint64_t)c * stride);
+                VATE_CHECK_WORD(G, w.y, q + (uint64_t)c * stride);
+                VATE_CHECK_WORD(G, w.z, q + (uint64_t)c * stride);
+                VATE_CHECK_WORD(G, w.w, q + (uint64_t)c * stride);
+            }
             if (w.x == pat && w.y == pat && w.z == pat && w.w == pat) {
                 inactive += real ? 8u : 0u;
                 continue;
@@ -306,10 +314,6 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census16_kernel(Geom G, uint32
 // Eight 16-byte chunks are in flight per thread; the block's sums go into acc
 // with 64-bit atomics and the last block publishes them (census_publish).
 // --------------------------------------------------------------------------
-#ifndef VATE_CENSUS_PLANES_BPS
-#define VATE_CENSUS_PLANES_BPS 2
-#endif
-
 template <int RAW>
 __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ acc,
                                                                 uint64_t *__restrict__ hist,
@@ -340,6 +344,10 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
         for (int u = 0; u < U; u++) {
             const uint64_t qu = q + (uint64_t)u * stride;
             if (qu >= n16) continue;
+            VATE_CHECK_WORD(G, w[u].x, qu);
+            VATE_CHECK_WORD(G, w[u].y, qu);
+            VATE_CHECK_WORD(G, w[u].z, qu);
+            VATE_CHECK_WORD(G, w[u].w, qu);
             if (RAW) census_chunk_raw(w[u], pat, inact, col, runs);
             else census_chunk(G, bact0, (uint32_t)(qu << 4), w[u], pat, col, runs);
         }
@@ -381,8 +389,14 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_kernel(Geom G, uint32_t
 // a caller); a frame-0 timestamp pool of the library never holds them.
 // --------------------------------------------------------------------------
 constexpr int CP_THREADS = 256;
-constexpr int CP_BATCH = 8;                    // chunks loaded per thread per trip (all issued before any use)
-constexpr int CP_FOLD_BATCHES = 31;            // 31 batches x 8 chunks x 16 ATs = 3968 <= 4095 per value
+#ifndef VATE_CENSUS_BATCH
+#define VATE_CENSUS_BATCH 8
+#endif
+#ifndef VATE_CENSUS_PLANES_BPS
+#define VATE_CENSUS_PLANES_BPS 2
+#endif
+constexpr int CP_BATCH = VATE_CENSUS_BATCH;    // chunks loaded per thread per trip (4 or 8, all issued before any use)
+constexpr int CP_FOLD_BATCHES = 248 / CP_BATCH; // 248 chunks x 16 ATs = 3968 <= 4095 per value
 
 struct CensusPlanes {
     uint32_t lo[4] = {0, 0, 0, 0};             // weights 1, 2, 4, 8
@@ -392,8 +406,14 @@ struct CensusPlanes {
     __device__ __forceinline__ uint32_t add_chunk(uint4 w) {
         const uint32_t words[4] = {w.x, w.y, w.z, w.w};
         uint32_t m[16];
+        // byte b of a word moved down by a multiply-high (w >> 8b = umulhi(w, 2^(32 - 8b)), on the
+        // multiply-add pipe), then the funnel shift takes its low five bits as the amount
 #pragma unroll
-        for (int b = 0; b < 16; b++) m[b] = __funnelshift_l(0u, 1u, words[b >> 2] >> (8 * (b & 3)));
+        for (int b = 0; b < 16; b++) {
+            const uint32_t w = words[b >> 2];
+            const uint32_t x = (b & 3) == 0 ? w : __umulhi(w, 1u << (32 - 8 * (b & 3)));
+            m[b] = __funnelshift_l(0u, 1u, x);
+        }
         uint32_t twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;
         csa(twosA, lo[0], lo[0], m[0], m[1]);
         csa(twosB, lo[0], lo[0], m[2], m[3]);
@@ -412,19 +432,25 @@ struct CensusPlanes {
         csa(sixteens, lo[3], lo[3], eightsA, eightsB);
         return sixteens;
     }
-    // the eight carries of weight 16 of one batch into hi
+    // the carries of weight 16 of one batch (4 or 8 chunks) into hi
     __device__ __forceinline__ void add_batch_carries(const uint32_t (&s)[CP_BATCH]) {
-        uint32_t t32A, t32B, t64A, t64B, t128;
+        uint32_t t32A, t32B, t64A, t64B, c;
         csa(t32A, hi[0], hi[0], s[0], s[1]);
         csa(t32B, hi[0], hi[0], s[2], s[3]);
-        csa(t64A, hi[1], hi[1], t32A, t32B);
-        csa(t32A, hi[0], hi[0], s[4], s[5]);
-        csa(t32B, hi[0], hi[0], s[6], s[7]);
-        csa(t64B, hi[1], hi[1], t32A, t32B);
-        csa(t128, hi[2], hi[2], t64A, t64B);
-        uint32_t c = t128;                          // ripple into 128 .. 2048
+        if (CP_BATCH == 8) {
+            csa(t64A, hi[1], hi[1], t32A, t32B);
+            csa(t32A, hi[0], hi[0], s[CP_BATCH > 4 ? 4 : 0], s[CP_BATCH > 5 ? 5 : 0]);
+            csa(t32B, hi[0], hi[0], s[CP_BATCH > 6 ? 6 : 0], s[CP_BATCH > 7 ? 7 : 0]);
+            csa(t64B, hi[1], hi[1], t32A, t32B);
+            csa(c, hi[2], hi[2], t64A, t64B);            // carry of weight 128
+        } else {
+            csa(c, hi[1], hi[1], t32A, t32B);            // carry of weight 64
+            const uint32_t t = hi[2] & c;                // into 64, carry 128 on
+            hi[2] ^= c;
+            c = t;
+        }
 #pragma unroll
-        for (int j = 3; j < 8; j++) {
+        for (int j = 3; j < 8; j++) {                   // ripple into 128 .. 2048
             const uint32_t t = hi[j] & c;
             hi[j] ^= c;
             c = t;
@@ -467,7 +493,7 @@ __device__ __forceinline__ uint32_t warp_fold(const CensusPlanes &cp, uint32_t l
 }
 
 template <bool CLAMP>
-__global__ void __launch_bounds__(CP_THREADS) census_planes_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ acc,
+__global__ void __launch_bounds__(CP_THREADS, VATE_CENSUS_PLANES_BPS) census_planes_kernel(Geom G, uint32_t bact0, uint64_t *__restrict__ acc,
                                                                    uint64_t *__restrict__ hist,
                                                                    unsigned int *__restrict__ ticket) {
     __shared__ uint32_t blk[32];                                // the block's count of each stored value
@@ -499,6 +525,10 @@ __global__ void __launch_bounds__(CP_THREADS) census_planes_kernel(Geom G, uint3
             s[b] = 0u;
             if (q + (uint64_t)b * stride >= n16) continue;      // beyond the pool: not counted
             uint4 c = w[b];
+            VATE_CHECK_WORD(G, c.x, q + (uint64_t)b * stride);
+            VATE_CHECK_WORD(G, c.y, q + (uint64_t)b * stride);
+            VATE_CHECK_WORD(G, c.z, q + (uint64_t)b * stride);
+            VATE_CHECK_WORD(G, c.w, q + (uint64_t)b * stride);
             if (CLAMP) {
                 c.x = swar_clamp(c.x, inact);
                 c.y = swar_clamp(c.y, inact);

@@ -13,6 +13,13 @@
 //      (or Eq. 11) and copies the results back, all on the monitor's stream.
 // Requests of different monitors therefore overlap on the device, and new
 // requests enter as soon as slots free up.
+//
+// Host-side fault injection (vate_server_inject) exercises failure handling
+// without touching a GPU: the scheduler can be stalled, a monitor's next
+// ingest batches dropped (they complete with VATE_EDROPPED and never reach the
+// device), or a monitor's next requests held back for a while (late batches).
+// Requests are dispatched in arrival order per monitor: a held request holds
+// up the later requests of its own monitor only.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -43,6 +50,7 @@ constexpr int PENDING = -1;
 
 struct Req {
     uint64_t ticket = 0;
+    Clock::time_point hold_until{};   // a held (late) request is not dispatched before this
     int kind = REQ_INGEST;
     int32_t mon = -1;
     int64_t slice = 0;
@@ -79,6 +87,9 @@ struct Mon {
     uint32_t k = 0;
     bool alive = false;
     uint64_t pending = 0;          // queued + in flight
+    uint32_t drop_next = 0;        // injected: ingest batches still to drop
+    uint32_t hold_next = 0;        // injected: requests still to hold back ...
+    uint32_t hold_ms = 0;          // ... for this long each
 };
 
 double pct(std::vector<double> v, double p) {
@@ -103,6 +114,7 @@ struct vate_server {
     uint64_t next_ticket = 1;
     uint64_t mem_in_use = 0;
     bool stop = false;
+    Clock::time_point stall_until{};   // injected: the scheduler does nothing before this
     std::thread th;
     // statistics
     std::vector<double> lat_ingest, lat_close;
@@ -153,10 +165,11 @@ bool retire(vate_server *s) {
     return any;
 }
 
-// Dispatch one request (plus mergeable followers) into slot `sl` (lock held).
-void dispatch(vate_server *s, Slot &sl) {
-    Req *r = s->queue.front();
-    s->queue.pop_front();
+// Dispatch queued request number i (plus mergeable followers) into slot `sl`
+// (lock held).
+void dispatch(vate_server *s, Slot &sl, size_t i) {
+    Req *r = s->queue[i];
+    s->queue.erase(s->queue.begin() + (long)i);
     Mon &m = s->mons[r->mon];
     sl.reqs.clear();
     sl.reqs.push_back(r);
@@ -166,10 +179,12 @@ void dispatch(vate_server *s, Slot &sl) {
     cudaError_t e = cudaSuccess;
     if (r->kind == REQ_INGEST) {
         uint64_t total = r->n;
-        while (!s->queue.empty()) {        // merge consecutive ingests of the same monitor and slice
-            Req *q = s->queue.front();
-            if (q->kind != REQ_INGEST || q->mon != r->mon || q->slice != r->slice || total + q->n > cap) break;
-            s->queue.pop_front();
+        while (i < s->queue.size()) {      // merge consecutive ingests of the same monitor and slice
+            Req *q = s->queue[i];
+            if (q->kind != REQ_INGEST || q->mon != r->mon || q->slice != r->slice || total + q->n > cap ||
+                m.drop_next || m.hold_next || q->hold_until > Clock::now())
+                break;
+            s->queue.erase(s->queue.begin() + (long)i);
             sl.reqs.push_back(q);
             total += q->n;
             s->merged++;
@@ -221,26 +236,76 @@ void dispatch(vate_server *s, Slot &sl) {
     sl.busy = true;
 }
 
+// The first queued request that may go now (lock held): requests of one
+// monitor go in arrival order, so a monitor whose earliest queued request is
+// held back waits, while other monitors' requests pass it.  An injected hold
+// is stamped on a monitor's request when it first reaches the front of that
+// monitor's line.  Returns the queue size when nothing may go.
+size_t next_dispatchable(vate_server *s, Clock::time_point now) {
+    std::vector<char> blocked(s->mons.size(), 0);
+    for (size_t i = 0; i < s->queue.size(); i++) {
+        Req *r = s->queue[i];
+        if (blocked[r->mon]) continue;
+        Mon &m = s->mons[r->mon];
+        if (r->hold_until == Clock::time_point{} && m.hold_next) {
+            m.hold_next--;
+            r->hold_until = now + std::chrono::milliseconds(m.hold_ms);
+        }
+        if (r->hold_until > now) {
+            blocked[r->mon] = 1;
+            continue;
+        }
+        return i;
+    }
+    return s->queue.size();
+}
+
+// An injected drop: the monitor's next ingest completes with VATE_EDROPPED
+// without reaching the device (lock held).  Returns true if it dropped r.
+bool drop_injected(vate_server *s, Req *r) {
+    Mon &m = s->mons[r->mon];
+    if (r->kind != REQ_INGEST || !m.drop_next) return false;
+    m.drop_next--;
+    complete(s, r, VATE_EDROPPED, "ingest batch dropped (injected fault)");
+    return true;
+}
+
 void scheduler(vate_server *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
+        const Clock::time_point now = Clock::now();
+        if (now < s->stall_until) {             // injected stall: neither retire nor dispatch
+            lk.unlock();
+            std::this_thread::sleep_until(std::min(s->stall_until, now + std::chrono::milliseconds(5)));
+            lk.lock();
+            continue;
+        }
         retire(s);
         uint32_t busy = 0;
         for (Slot &sl : s->slots) busy += sl.busy ? 1u : 0u;
+        bool dropped = false;
         while (!s->queue.empty()) {
+            const size_t i = next_dispatchable(s, Clock::now());
+            if (i == s->queue.size()) break;
+            if (drop_injected(s, s->queue[i])) {
+                s->queue.erase(s->queue.begin() + (long)i);
+                dropped = true;
+                continue;
+            }
             Slot *free_slot = nullptr;
             for (Slot &sl : s->slots)
                 if (!sl.busy) { free_slot = &sl; break; }
             if (!free_slot) break;
-            dispatch(s, *free_slot);
+            dispatch(s, *free_slot, i);
             busy++;
         }
+        if (dropped) s->cv_done.notify_all();
         s->max_in_flight = std::max(s->max_in_flight, busy);
         if (s->stop && s->queue.empty() && busy == 0) break;
         if (busy == 0 && s->queue.empty())
             s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
-        else {                               // work on the GPU: poll its events briskly
+        else {                               // work on the GPU or held requests: poll briskly
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(20));
             lk.lock();
@@ -452,6 +517,27 @@ int vate_server_drain(vate_server *s, uint32_t timeout_ms) {
     };
     if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), idle))
         return vate::set_error(VATE_ETIMEOUT, "requests still in flight");
+    return VATE_OK;
+}
+
+int vate_server_inject(vate_server *s, const vate_server_fault *f) {
+    if (!s || !f) return vate::set_error(VATE_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> g(s->mu);
+    if (f->kind == VATE_FAULT_STALL) {
+        s->stall_until = Clock::now() + std::chrono::milliseconds(f->ms);
+        return VATE_OK;
+    }
+    if (f->kind != VATE_FAULT_DROP && f->kind != VATE_FAULT_HOLD) return vate::set_error(VATE_EINVAL, "unknown fault kind");
+    if (f->mon < 0 || f->mon >= (int32_t)s->mons.size() || !s->mons[f->mon].alive)
+        return vate::set_error(VATE_EINVAL, "unknown monitor");
+    Mon &m = s->mons[f->mon];
+    if (f->kind == VATE_FAULT_DROP) {
+        m.drop_next += f->count;
+    } else {
+        m.hold_next += f->count;
+        m.hold_ms = f->ms;
+    }
+    s->cv_work.notify_one();
     return VATE_OK;
 }
 

@@ -19,11 +19,14 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvate.so")
+DEBUG_LIB_PATH = os.path.join(_HERE, "libvate_debug.so")   # the checked build (VATE_DEBUG)
 
-VATE_OK, VATE_EINVAL, VATE_ENOMEM, VATE_ESLICE, VATE_ECUDA, VATE_ETIMEOUT = 0, 1, 2, 3, 4, 5
+VATE_OK, VATE_EINVAL, VATE_ENOMEM, VATE_ESLICE, VATE_ECUDA, VATE_ETIMEOUT, VATE_EDROPPED = 0, 1, 2, 3, 4, 5, 6
 VATE_FLAG_SAT, VATE_FLAG_POOLFULL = 1, 2
+VATE_DBG_POSITION, VATE_DBG_VALUE, VATE_DBG_BLOCK = 1, 2, 4
 VATE_OPT_PERSIST_L2 = 1
-ERROR_NAMES = {1: "VATE_EINVAL", 2: "VATE_ENOMEM", 3: "VATE_ESLICE", 4: "VATE_ECUDA", 5: "VATE_ETIMEOUT"}
+ERROR_NAMES = {1: "VATE_EINVAL", 2: "VATE_ENOMEM", 3: "VATE_ESLICE", 4: "VATE_ECUDA", 5: "VATE_ETIMEOUT",
+               6: "VATE_EDROPPED"}
 
 
 class VateError(RuntimeError):
@@ -72,12 +75,18 @@ class vate_server_stats(C.Structure):
 
 
 VATE_SUBMIT_PINNED = 1
+VATE_FAULT_STALL, VATE_FAULT_DROP, VATE_FAULT_HOLD = 1, 2, 3
 
 
-def _load() -> C.CDLL:
-    if not os.path.exists(LIB_PATH):
-        raise ImportError("libvate.so is not built (run `python -m paper_1812_00282_b300.build`): " + LIB_PATH)
-    lib = C.CDLL(LIB_PATH)
+class vate_server_fault(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("mon", C.c_int32), ("count", C.c_uint32), ("ms", C.c_uint32)]
+
+
+def _load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError("%s is not built (run `python -m paper_1812_00282_b300.build`): %s"
+                          % (os.path.basename(path), path))
+    lib = C.CDLL(path)
     vp, u32, u64, i64, i = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64, C.c_int
     P = C.POINTER
     sig = {
@@ -107,6 +116,7 @@ def _load() -> C.CDLL:
         "vate_group_autotune": (i, [vp, vp, vp, u64, vp, vp, u64, vp, vp, vp, P(vate_group_tuning), vp]),
         "vate_group_set_tuning": (i, [vp, P(vate_group_tuning)]),
         "vate_group_set_wait": (i, [vp, u64, u32]),
+        "vate_group_set_trace": (i, [vp, vp, u32]),
         "vate_group_graph_nodes": (i, [vp, P(C.c_uint32)]),
         "vate_group_get_tuning": (i, [vp, P(vate_group_tuning)]),
         "vate_group_status": (i, [vp, P(u32), i, vp]),
@@ -130,11 +140,15 @@ def _load() -> C.CDLL:
         "vate_server_wait": (i, [vp, u64, u32]),
         "vate_server_drain": (i, [vp, u32]),
         "vate_server_get_stats": (i, [vp, P(vate_server_stats), i]),
+        "vate_server_inject": (i, [vp, P(vate_server_fault)]),
         "vate_create_shard": (i, [P(vate_params), u64, u64, vp, P(vp)]),
         "vate_estimate_from_counts": (i, [P(vate_params), vp, vp, u64, u32, vp, vp, vp]),
         "vate_checkpoint_size": (i, [vp, P(u64)]),
         "vate_checkpoint": (i, [vp, vp, u64, vp]),
         "vate_restore": (i, [vp, u64, vp, P(vp)]),
+        "vate_debug_checks": (i, []),
+        "vate_debug_status": (i, [vp, P(u32), P(u64), i, vp]),
+        "vate_debug_poke": (i, [vp, u64, u32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -144,6 +158,42 @@ def _load() -> C.CDLL:
 
 
 _lib = _load()
+
+
+class use_library:
+    """Route every function of this binding to another build of the library
+    while the block runs -- `with use_library(DEBUG_LIB_PATH): ...` runs the
+    same calls on the checked build.  Handles belong to the library that made
+    them: create and destroy them inside the block."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self._saved = _lib
+        _lib = _load(self.path)
+        return _lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
+
+
+def vate_debug_checks() -> bool:
+    return bool(_lib.vate_debug_checks())
+
+
+def vate_debug_status(h, clear: bool = False, stream=None):
+    """(VATE_DBG_* bits, first report) of the handle (include/vate.h)."""
+    bits, first = C.c_uint32(), C.c_uint64()
+    _check(_lib.vate_debug_status(h, C.byref(bits), C.byref(first), 1 if clear else 0, _stream(stream)))
+    return int(bits.value), int(first.value)
+
+
+def vate_debug_poke(h, pid: int, value: int, stream=None) -> None:
+    _check(_lib.vate_debug_poke(h, pid, value, _stream(stream)))
 
 
 def _check(rc: int) -> None:
@@ -469,6 +519,15 @@ def vate_group_set_wait(g, spin_limit: int, missing: int = 0) -> None:
     _check(_lib.vate_group_set_wait(g, spin_limit, missing))
 
 
+def vate_group_set_trace(g, trace=None) -> None:
+    """trace: a CUDA int64 tensor of 4 x items, or None to stop tracing."""
+    import torch
+    if trace is None:
+        _check(_lib.vate_group_set_trace(g, None, 0))
+    else:
+        _check(_lib.vate_group_set_trace(g, _dev(trace, torch.int64, "trace"), trace.numel() // 4))
+
+
 def vate_group_graph_nodes(g) -> int:
     n = C.c_uint32()
     _check(_lib.vate_group_graph_nodes(g, C.byref(n)))
@@ -613,6 +672,11 @@ def vate_server_get_stats(s, reset: bool = False) -> vate_server_stats:
     st = vate_server_stats()
     _check(_lib.vate_server_get_stats(s, C.byref(st), 1 if reset else 0))
     return st
+
+
+def vate_server_inject(s, kind: int, mon: int = 0, count: int = 0, ms: int = 0) -> None:
+    """Host-side fault injection in the serving loop (include/vate_server.h)."""
+    _check(_lib.vate_server_inject(s, C.byref(vate_server_fault(kind, mon, count, ms))))
 
 
 def vate_create_shard(params: vate_params, pid_lo: int, pid_hi: int, stream=None) -> C.c_void_p:
