@@ -52,14 +52,18 @@ typedef struct vate_group vate_group;
  *   blocks_per_sm         persistent grid: blocks of 256 threads per SM (1 .. the kernel's occupancy)
  *   gather_tile_hosts     hosts per gather work item (multiple of 256, 256..65536)
  *   ingest_tile_pairs     pairs per SetAT work item (multiple of 256, 256..65536)
- *   preserve_tile_chunks  16-byte chunks per PreserveAT work item (multiple of 256, 256..65536) */
+ *   preserve_tile_chunks  16-byte chunks per PreserveAT work item (multiple of 256, 256..65536)
+ *   wave_pool_mib         work order: consecutive monitors whose pools add up to at most this many MiB
+ *                         form a wave, and a wave's items go phase by phase (every monitor's
+ *                         PreserveAT, then SetAT, census, gather), so that its pools stay in L2;
+ *                         0: one wave of all monitors (0..65536) */
 typedef struct {
     uint32_t census_tile_chunks;
     uint32_t blocks_per_sm;
     uint32_t gather_tile_hosts;
     uint32_t ingest_tile_pairs;
     uint32_t preserve_tile_chunks;
-    uint32_t reserved;
+    uint32_t wave_pool_mib;
 } vate_group_tuning;
 
 /* Create a group of n_monitors (1..256) monitors; params[m] as for

@@ -17,9 +17,17 @@
  * Model: y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3, hidden width 64, FP32
  * weights and accumulation.  y corrects the closed form in log space: the
  * estimate is expm1(8 y + log1p(max(Eq. 11 estimate, 0))), so a model that
- * outputs 0 reproduces the closed form (clamped at 0).
- * Parameter layout (floats): W1[n_in][64], b1[64], W2[64][64], b2[64], w3[64], b3
- * (vate_mlp_param_count(n_in) = 64 n_in + 4288 + 1).
+ * outputs 0 reproduces the closed form (clamped at 0).  A gate tau completes
+ * the model: where the closed form is >= tau (large hosts, for which Eq. 11
+ * is already accurate) the closed form itself is returned.
+ * Output rule for a host, in order: no active VAT in the window -> the closed
+ * form, VATE_FLAG_FALLBACK; closed form >= tau -> the closed form,
+ * VATE_FLAG_GATED; the corrected value not finite -> the closed form,
+ * VATE_FLAG_FALLBACK; otherwise the corrected value.
+ * Parameter layout (floats): W1[n_in][64], b1[64], W2[64][64], b2[64], w3[64], b3,
+ * tau (vate_mlp_param_count(n_in) = 64 n_in + 4288 + 2).  Training leaves tau
+ * alone (its gradient is 0); it is chosen after training (vate_mlp_apply lets
+ * a caller score candidates on its training rows) -- +infinity never gates.
  *
  * Conventions are those of vate.h.
  */
@@ -34,7 +42,8 @@ extern "C" {
 #endif
 
 #define VATE_MLP_HIDDEN 64
-#define VATE_FLAG_FALLBACK 4u   /* the closed form was returned (see vate_estimate_learned) */
+#define VATE_FLAG_FALLBACK 4u   /* the closed form was returned: no active VAT, or no finite correction */
+#define VATE_FLAG_GATED    8u   /* the closed form was returned: it is at or above the model's gate tau */
 
 /* Number of parameters of the model for n_in inputs. */
 uint64_t vate_mlp_param_count(uint32_t n_in);
@@ -45,11 +54,20 @@ uint64_t vate_mlp_param_count(uint32_t n_in);
 int vate_features(vate_handle *h, const uint32_t *d_aips, uint64_t n, float *d_x, void *stream);
 
 /* Deterministic initialisation: weights uniform in +-sqrt(6 / (fan_in +
- * fan_out)) (Glorot) from a counter-based hash of (seed, index); biases 0. */
+ * fan_out)) (Glorot) from a counter-based hash of (seed, index); biases 0;
+ * the gate tau = +infinity. */
 int vate_mlp_init(float *d_params, uint32_t n_in, uint64_t seed, void *stream);
 
 /* y[i] = model(x[i]) for n rows of x (device float[n * n_in]) into d_y (device float[n]). */
 int vate_mlp_forward(const float *d_params, uint32_t n_in, const float *d_x, uint64_t n, float *d_y, void *stream);
+
+/* The output rule (above) on n feature rows d_x (device float[n * n_in],
+ * n_in = 2k + 2) with their closed-form estimates d_plain (device float[n]):
+ * d_out (device float[n]) and, if not NULL, d_flags (device uint8[n]: the
+ * FALLBACK / GATED bits) -- what vate_estimate_learned returns for hosts with
+ * these features.  A row has no active VAT when its first k features are 0. */
+int vate_mlp_apply(const float *d_params, uint32_t n_in, const float *d_x, const float *d_plain, uint64_t n,
+                   float *d_out, uint8_t *d_flags, void *stream);
 
 /* Scratch floats that vate_mlp_train_step needs for a batch of n rows. */
 uint64_t vate_mlp_train_scratch(uint32_t n_in, uint64_t n);
@@ -73,10 +91,9 @@ int vate_mlp_train_step(float *d_params, float *d_m, float *d_v, uint32_t n_in, 
                         void *stream);
 
 /* Learned estimate of |OP(aip, t-k+1, k)| for n hosts at the end of the
- * closed slice, in one gather per host (features, MLP and the Eq. 11 fallback
- * fused).  The closed form is returned instead, with VATE_FLAG_FALLBACK, when
- * the host has no active VAT or the model's output is not finite.  d_flags
- * also carries VATE_FLAG_SAT / VATE_FLAG_POOLFULL of the closed form. */
+ * closed slice, in one gather per host (features, MLP, gate and the Eq. 11
+ * fallback fused), by the output rule above.  d_flags also carries
+ * VATE_FLAG_SAT / VATE_FLAG_POOLFULL of the closed form. */
 int vate_estimate_learned(vate_handle *h, const uint32_t *d_aips, uint64_t n, const float *d_params, float *d_out,
                           uint8_t *d_flags, void *stream);
 

@@ -2,13 +2,16 @@
 
 The model (not in the paper; the interface is fixed by include/vate_learned.h):
 y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 with hidden width 64, parameters
-laid out as W1[n_in][64], b1[64], W2[64][64], b2[64], w3[64], b3.  Loss: mean
+laid out as W1[n_in][64], b1[64], W2[64][64], b2[64], w3[64], b3, then the
+gate tau (not a weight of the network: the closed form is kept where it is
+>= tau).  Loss: mean
 squared error over the rows.  Features of a host: per-age VAT counts / g, the
 pool's per-age fractions, log2(g)/16, log1p(max(Eq. 11 estimate, 0))/16.
-Output rule at slice close (`estimate`): the model corrects the closed form
-of Eq. 11 in log space, estimate = expm1(8 y + log1p(max(Eq. 11, 0))); the
-closed form itself is returned, flagged FALLBACK, when the host has no active
-VAT in the window or the corrected value is not a finite FP32 number.
+Output rule at slice close (`estimate`), in order: the closed form of Eq. 11,
+flagged FALLBACK, when the host has no active VAT in the window; the closed
+form, flagged GATED, when it is >= tau; the closed form, flagged FALLBACK, when
+the corrected value expm1(8 y + log1p(max(Eq. 11, 0))) is not a finite FP32
+number; otherwise that corrected value.
 Written directly from those definitions with numpy; the gradient is pinned
 by finite differences, the forward pass and the output rule by hand-built
 networks whose outputs are known in closed form.
@@ -18,12 +21,13 @@ from __future__ import annotations
 import numpy as np
 
 HID = 64
-FALLBACK = 4          # flag bit: the closed form was returned instead of the model's value
+FALLBACK = 4          # flag bit: the closed form was returned (no active VAT, or no finite correction)
+GATED = 8             # flag bit: the closed form was returned (it is at or above the gate tau)
 FLT_MAX = float(np.finfo(np.float32).max)
 
 
 def n_params(n_in: int) -> int:
-    return n_in * HID + HID + HID * HID + HID + HID + 1
+    return n_in * HID + HID + HID * HID + HID + HID + 1 + 1      # ... b3, then the gate
 
 
 def unpack(p: np.ndarray, n_in: int):
@@ -36,6 +40,11 @@ def unpack(p: np.ndarray, n_in: int):
     w3 = p[o:o + HID]; o += HID
     b3 = p[o]
     return W1, b1, W2, b2, w3, b3
+
+
+def gate(p) -> float:
+    """The gate tau: the last parameter."""
+    return float(np.asarray(p, np.float64)[-1])
 
 
 def forward(p, n_in, X):
@@ -74,7 +83,7 @@ def loss_and_grad(p, n_in, X, t, w=None, absolute=False):
     dZ1 = (dZ2 @ W2.T) * (Z1 > 0)
     dW1 = X.T @ dZ1
     db1 = dZ1.sum(0)
-    g = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dw3, [db3]])
+    g = np.concatenate([dW1.ravel(), db1, dW2.ravel(), db2, dw3, [db3], [0.0]])   # the gate is not trained
     return loss, g
 
 
@@ -95,13 +104,9 @@ def features(o, hosts, k=None):
 
 def estimate(p, n_in, X, plain, k, plain_flags=None):
     """The learned estimate of each row and its flags (the closed form's
-    SAT/POOLFULL bits from `plain_flags`, plus FALLBACK).
-
-    y = forward(X); z = 8 y + log1p(max(plain, 0)); estimate = expm1(z).
-    FALLBACK (estimate = plain): the row's per-age counts X[:, :k] are all 0
-    (no active VAT in the window), or expm1(z) is not a finite FP32 number.
-    The finiteness decision is taken in FP32, the precision in which the
-    estimate is delivered."""
+    SAT/POOLFULL bits from `plain_flags`, plus FALLBACK / GATED), by the rule
+    in the module docstring.  The finiteness decision is taken in FP32, the
+    precision in which the estimate is delivered."""
     X = np.asarray(X, np.float64).reshape(-1, n_in)
     plain = np.asarray(plain, np.float64)
     y = forward(p, n_in, X)
@@ -110,8 +115,10 @@ def estimate(p, n_in, X, plain, k, plain_flags=None):
         est = np.expm1(z)
         finite32 = np.isfinite(est) & (np.abs(est) <= FLT_MAX)
     no_active = X[:, :k].sum(axis=1) == 0
-    fb = no_active | ~finite32
-    out = np.where(fb, plain, est)
+    gated = ~no_active & (plain >= gate(p))
+    fb = no_active | (~gated & ~finite32)
+    out = np.where(fb | gated, plain, est)
     flags = np.zeros(len(out), np.uint8) if plain_flags is None else np.asarray(plain_flags, np.uint8).copy()
     flags[fb] |= FALLBACK
+    flags[gated] |= GATED
     return out, flags, z

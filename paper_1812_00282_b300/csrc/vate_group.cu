@@ -1,9 +1,8 @@
 // vate_group.cu -- many independent monitors advanced together (include/vate_group.h).
 //
 // One slice of every monitor is ONE persistent launch, group_step_kernel.  Its
-// blocks take work items in order from a device queue.  The item list is
-// laid out monitor after monitor, each monitor's items in the order of
-// Algorithm 4's per-slice pipeline:
+// blocks take work items in order from a device queue.  Each monitor's items
+// follow Algorithm 4's per-slice pipeline:
 //   B  begin: clear the monitor's census histogram                  (1 item)
 //   P  PreserveAT (Algorithm 3) on the two blocks whose ACT became
 //      0 or k, in tiles of 16-byte chunks                          (none at slice 0)
@@ -20,9 +19,13 @@
 // step as timed out in the group's status word (VATE_GROUP_TIMEOUT) and every
 // later wait of the launch gives up at once, so the kernel always returns.
 //
-// Monitor-major order keeps a monitor's pool hot in L2 from its SetATs to its
-// census and gather while the pools of the group as a whole exceed L2; items
-// of the next monitors fill the blocks that wait.  The per-chunk and per-host
+// The list is cut into waves of consecutive monitors whose pools together fit a
+// byte budget (the tuning's wave_pool_mib; 0: one wave), and within a wave it
+// is phase-major: every monitor's B and P items, then every monitor's I
+// items, then C, then G.  So a wave's pools stay in L2 from their SetATs to
+// their census and gather, and an item's wait is for the tail of its own
+// monitor's previous phase while the other monitors' items of that phase keep
+// the blocks busy.  The per-chunk and per-host
 // arithmetic is the one of the single-pool kernels (vate_device_ops.cuh), so
 // every monitor is bit-identical to a vate_handle run alone.  The slice
 // number, the batch offsets and k' are read on the device, so the one launch
@@ -50,6 +53,8 @@ constexpr uint32_t MAX_MONITORS = 256;
 constexpr int G_THREADS = 256;
 constexpr int G_WARPS = G_THREADS / 32;
 constexpr int NPHASE = 5;                 // B, P, I, C, G
+constexpr int C_WARPS = 6;                // warps that count a census item (their lane columns fit 4 blocks per SM)
+constexpr int G_MIN_BLOCKS = 4;           // blocks per SM the step kernel is built for (at most 64 registers)
 constexpr unsigned long long DEFAULT_SPIN_LIMIT = 1ull << 23;   // x ~128 ns of sleep: about a second
 
 struct GroupState {                       // device-resident
@@ -79,6 +84,7 @@ struct StepArgs {
     unsigned long long spin_limit;
     uint32_t M, maxbins;
     uint32_t census_tile, ingest_tile, gather_tile, preserve_tile;
+    uint64_t wave_bytes;                  // pools per wave of monitors (0: one wave of all monitors)
     unsigned long long *trace;            // NULL, or 4 words per item (vate_group_set_trace)
     uint32_t trace_cap;                   // items the trace buffer holds
     uint32_t advance;                     // 1: the next slice; 0: repeat the last slice (autotuner)
@@ -108,7 +114,8 @@ __device__ __forceinline__ uint32_t bact0_of(unsigned long long step, uint32_t t
     return (uint32_t)(step % twok);
 }
 
-// index of the monitor m with pre[m] <= i < pre[m+1] (pre strictly increasing, pre[0] <= i < pre[M])
+// the last index m < M with pre[m] <= i (pre non-decreasing, pre[0] <= i < pre[M]): with runs of equal
+// entries (empty segments) that is the segment holding i
 template <typename T>
 __device__ __forceinline__ uint32_t find_monitor(const T *pre, uint32_t M, uint64_t i) {
     uint32_t lo = 0, hi = M;
@@ -194,15 +201,16 @@ __device__ __forceinline__ uint32_t gather_one(const Geom &G, const RangeConsts 
 }
 
 template <int GK>
-__global__ void __launch_bounds__(G_THREADS) group_step_kernel(StepArgs a) {
+__global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t M = a.M;
     uint64_t *po = reinterpret_cast<uint64_t *>(smem);              // M + 1 pair offsets (clamped)
     uint64_t *ho = po + (M + 1);                                      // M + 1 host offsets (clamped)
     uint32_t *cum = reinterpret_cast<uint32_t *>(ho + (M + 1));       // [M][NPHASE + 1]: items before each phase
-    uint32_t *pre = cum + M * (NPHASE + 1);                           // M + 1: items before each monitor
-    uint32_t *kp = pre + (M + 1);                                     // M: k' (clamped)
-    uint32_t *cols = kp + M;                                          // census lane columns [warps][pairs][32]
+    uint32_t *kp = cum + M * (NPHASE + 1);                            // M: k' (clamped)
+    uint32_t *seg_start = kp + M;                                     // NPHASE * M + 1: first item of each segment
+    uint32_t *seg_mp = seg_start + (NPHASE * M + 1);                  // NPHASE * M: (monitor << 3) | phase
+    uint32_t *cols = seg_mp + NPHASE * M;                             // census lane columns [C_WARPS][pairs][32]
     const uint32_t maxpairs = (a.maxbins + 1u) / 2u;
 
     __shared__ unsigned long long s_step, s_t0, s_t1;
@@ -266,11 +274,27 @@ __global__ void __launch_bounds__(G_THREADS) group_step_kernel(StepArgs a) {
     }
     __syncthreads();
     if (tid == 0) {
-        pre[0] = 0;
-        for (uint32_t m = 0; m < M; m++) pre[m + 1] = pre[m] + cum[m * (NPHASE + 1) + NPHASE];
+        // segments = (monitor, phase) runs of items, ordered wave by wave, phase-major inside a wave
+        uint32_t ns = 0, run = 0;
+        for (uint32_t m0 = 0; m0 < M;) {
+            uint32_t m1 = m0 + 1;
+            uint64_t bytes = a.descs[m0].P;
+            while (m1 < M && a.wave_bytes && bytes + a.descs[m1].P <= a.wave_bytes) bytes += a.descs[m1++].P;
+            if (!a.wave_bytes) m1 = M;
+            for (int p = 0; p < NPHASE; p++)
+                for (uint32_t m = m0; m < m1; m++) {
+                    seg_start[ns] = run;
+                    seg_mp[ns] = (m << 3) | (uint32_t)p;
+                    run += cum[m * (NPHASE + 1) + p + 1] - cum[m * (NPHASE + 1) + p];
+                    ns++;
+                }
+            m0 = m1;
+        }
+        seg_start[ns] = run;                  // ns = NPHASE * M: the total
     }
     __syncthreads();
-    const uint32_t total = pre[M];
+    const uint32_t nsegs = NPHASE * M;
+    const uint32_t total = seg_start[nsegs];
 
     // ---- the items ----
     for (;;) {
@@ -279,14 +303,12 @@ __global__ void __launch_bounds__(G_THREADS) group_step_kernel(StepArgs a) {
             s_j = j;
             if (a.trace) s_t0 = global_ns();
             if (j < total) {
-                const uint32_t m = find_monitor(pre, M, j);
-                const uint32_t local = j - pre[m];
+                const uint32_t sg = find_monitor(seg_start, nsegs, j);   // the segment holding item j
+                const uint32_t m = seg_mp[sg] >> 3, p = seg_mp[sg] & 7u;
                 const uint32_t *cm = cum + m * (NPHASE + 1);
-                uint32_t p = 0;
-                while (local >= cm[p + 1]) p++;
                 s_m = m;
                 s_p = p;
-                s_t = local - cm[p];
+                s_t = j - seg_start[sg];
                 s_ok = wait_done(a.done + m, cm[p] + a.missing, st, a.spin_limit) ? 1u : 0u;
                 if (a.trace) s_t1 = global_ns();
                 sG = a.descs[m];
@@ -326,36 +348,42 @@ __global__ void __launch_bounds__(G_THREADS) group_step_kernel(StepArgs a) {
                     if (VATE_CHECK_POSITION(G, pid)) G.pool[pid] = v;
                 }
             } else if (p == 3) {                                 // C: census tile into lane columns
-                uint32_t *col = cols + (size_t)warp * maxpairs * 32u + lane;
                 const uint32_t nbins = G.twok + 1u, npairs = (nbins + 1u) / 2u;
-                for (uint32_t b = 0; b < npairs; b++) col[b * 32u] = 0u;
+                const bool counts = warp < (uint32_t)C_WARPS;      // the counting warps (the others wait)
+                uint32_t *col = cols + (size_t)(counts ? warp : 0u) * maxpairs * 32u + lane;
+                if (counts)
+                    for (uint32_t b = 0; b < npairs; b++) col[b * 32u] = 0u;
                 const uint32_t pat = G.twok * ONES;
                 uint32_t runs = 0;
                 const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
                 // a tile holds at most 65,536 chunks: a lane counts at most 4,096 ATs, every
                 // 16-bit counter stays exact
+                // a tile holds at most 65,536 chunks, over C_WARPS * 32 lanes: at most 5,462 ATs a lane
                 constexpr int U = 8;
+                constexpr uint32_t CT = C_WARPS * 32u;           // counting threads
                 const uint64_t q0 = (uint64_t)t * a.census_tile;
                 const uint64_t qend = min(q0 + a.census_tile, G.P >> 4);
-                for (uint64_t q = q0 + tid; q < qend; q += (uint64_t)U * blockDim.x) {
-                    uint4 w[U];
+                if (counts) {
+                    for (uint64_t q = q0 + tid; q < qend; q += (uint64_t)U * CT) {
+                        uint4 w[U];
 #pragma unroll
-                    for (int u = 0; u < U; u++) {
-                        const uint64_t qu = q + (uint64_t)u * blockDim.x;
-                        w[u] = qu < qend ? __ldcg(pool16 + qu) : make_uint4(pat, pat, pat, pat);
-                    }
+                        for (int u = 0; u < U; u++) {
+                            const uint64_t qu = q + (uint64_t)u * CT;
+                            w[u] = qu < qend ? __ldcg(pool16 + qu) : make_uint4(pat, pat, pat, pat);
+                        }
 #pragma unroll
-                    for (int u = 0; u < U; u++) {
-                        const uint64_t qu = q + (uint64_t)u * blockDim.x;
-                        if (qu < qend) census_chunk_raw_pairs(w[u], pat, G.twok, col, runs);
+                        for (int u = 0; u < U; u++) {
+                            const uint64_t qu = q + (uint64_t)u * CT;
+                            if (qu < qend) census_chunk_raw_pairs(w[u], pat, G.twok, col, runs);
+                        }
                     }
+                    col[(G.twok >> 1) * 32u] += 16u * runs;      // 2k is even: the low half of pair k
                 }
-                col[(G.twok >> 1) * 32u] += 16u * runs;          // 2k is even: the low half of pair k
                 __syncthreads();
                 unsigned long long *h = reinterpret_cast<unsigned long long *>(a.hist) + (size_t)m * a.maxbins;
                 for (uint32_t r = warp; r < npairs; r += G_WARPS) {
                     uint32_t lo = 0, hi = 0;
-                    for (uint32_t wv = 0; wv < (uint32_t)G_WARPS; wv++) {
+                    for (uint32_t wv = 0; wv < (uint32_t)C_WARPS; wv++) {
                         const uint32_t x = cols[((size_t)wv * maxpairs + r) * 32u + lane];
                         lo += x & 0xFFFFu;
                         hi += x >> 16;
@@ -467,10 +495,10 @@ struct vate_group {
 namespace {
 
 // dynamic shared memory of group_step_kernel: two uint64 offset arrays, then
-// cum, pre and kp (uint32), then the census lane columns
+// cum, kp, seg_start and seg_mp (uint32), then the census lane columns
 size_t step_smem(uint32_t M, uint32_t maxbins) {
-    const size_t words = 4 * (size_t)(M + 1) + (size_t)M * (NPHASE + 1) + (M + 1) + M;
-    return words * 4 + (size_t)G_WARPS * ((maxbins + 1) / 2) * 32 * sizeof(uint32_t);
+    const size_t words = 4 * (size_t)(M + 1) + (size_t)M * (NPHASE + 1) + M + 2 * (size_t)NPHASE * M + 1;
+    return words * 4 + (size_t)C_WARPS * ((maxbins + 1) / 2) * 32 * sizeof(uint32_t);
 }
 
 void *kernel_of(int gk) {
@@ -510,6 +538,7 @@ int check_tuning(const vate_group_tuning *t, int max_bps) {
     for (uint32_t v : {t->gather_tile_hosts, t->ingest_tile_pairs, t->preserve_tile_chunks})
         if (v < 256 || v > 65536 || v % 256)
             return vate::set_error(VATE_EINVAL, "gather, ingest and preserve tiles: multiples of 256 in [256, 65536]");
+    if (t->wave_pool_mib > 65536) return vate::set_error(VATE_EINVAL, "wave_pool_mib must be in [0, 65536]");
     return VATE_OK;
 }
 
@@ -537,6 +566,7 @@ cudaError_t enqueue_step(vate_group *g, const vate_pair *pairs, const uint64_t *
     a.ingest_tile = g->tuning.ingest_tile_pairs;
     a.gather_tile = g->tuning.gather_tile_hosts;
     a.preserve_tile = g->tuning.preserve_tile_chunks;
+    a.wave_bytes = (uint64_t)g->tuning.wave_pool_mib << 20;
     a.advance = advance;
     a.missing = g->missing;
     a.trace = g->trace;
@@ -619,7 +649,7 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
     g->tuning.gather_tile_hosts = 256;
     g->tuning.ingest_tile_pairs = 4096;
     g->tuning.preserve_tile_chunks = 4096;
-    g->tuning.reserved = 0;
+    g->tuning.wave_pool_mib = 48;
     bool ok = cudaMalloc(&g->arena, g->arena_bytes) == cudaSuccess &&
               cudaMalloc(&g->d_descs, n_monitors * sizeof(Geom)) == cudaSuccess &&
               cudaMalloc(&g->d_state, sizeof(GroupState)) == cudaSuccess &&
@@ -716,7 +746,8 @@ int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_
     uint64_t key[16] = {(uint64_t)d_pairs, (uint64_t)d_pair_offsets, pair_capacity, (uint64_t)d_hosts,
                         (uint64_t)d_host_offsets, host_capacity, (uint64_t)d_kprime, (uint64_t)d_out,
                         (uint64_t)d_flags, ((uint64_t)t.census_tile_chunks << 32) | t.blocks_per_sm,
-                        ((uint64_t)t.gather_tile_hosts << 32) | t.ingest_tile_pairs, t.preserve_tile_chunks,
+                        ((uint64_t)t.gather_tile_hosts << 32) | t.ingest_tile_pairs,
+                        ((uint64_t)t.wave_pool_mib << 32) | t.preserve_tile_chunks,
                         g->spin_limit, g->missing, (uint64_t)g->trace, g->trace_cap};
     if (!g->exec || memcmp(key, g->graph_key, sizeof key) != 0) {
         if (g->exec) {
@@ -772,7 +803,6 @@ int vate_group_set_tuning(vate_group *g, const vate_group_tuning *t) {
     if (!g) return vate::set_error(VATE_EINVAL, "group is NULL");
     if (int rc = check_tuning(t, g->max_blocks_per_sm)) return rc;
     g->tuning = *t;
-    g->tuning.reserved = 0;
     return VATE_OK;
 }
 
@@ -812,13 +842,13 @@ int vate_group_autotune(vate_group *g, const vate_pair *d_pairs, const uint64_t 
     };
     vate_group_tuning best = g->tuning;
     float bt = 1e30f;
-    for (uint32_t bps = 1; bps <= (uint32_t)std::min(g->max_blocks_per_sm, 4); bps++)
-        for (uint32_t ct : {4096u, 16384u, 65536u})
-            for (uint32_t it : {2048u, 8192u})
+    for (uint32_t bps = 2; bps <= (uint32_t)std::min(g->max_blocks_per_sm, 4); bps++)
+        for (uint32_t wv : {0u, 32u, 64u})
+            for (uint32_t ct : {4096u, 16384u})
                 for (uint32_t gt : {256u, 1024u}) {
                     g->tuning.blocks_per_sm = bps;
+                    g->tuning.wave_pool_mib = wv;
                     g->tuning.census_tile_chunks = ct;
-                    g->tuning.ingest_tile_pairs = it;
                     g->tuning.gather_tile_hosts = gt;
                     float ms_best = 1e30f;
                     for (int r = 0; r < 3; r++) {

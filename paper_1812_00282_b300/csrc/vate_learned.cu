@@ -21,12 +21,13 @@ constexpr int WARPS = 8;                 // warps per block in the per-host kern
 constexpr int TR_ROWS = 64;              // rows per training tile
 constexpr int TR_THREADS = 256;
 
+// W1, b1, W2, b2, w3, b3, then the gate (not trained)
 __host__ __device__ inline uint64_t n_params(uint32_t n_in) {
-    return (uint64_t)n_in * HID + HID + (uint64_t)HID * HID + HID + HID + 1;
+    return (uint64_t)n_in * HID + HID + (uint64_t)HID * HID + HID + HID + 1 + 1;
 }
 
 struct Layout {                          // offsets of the parameter blocks
-    uint32_t W1, b1, W2, b2, w3, b3;
+    uint32_t W1, b1, W2, b2, w3, b3, gate;
 };
 __host__ __device__ inline Layout layout(uint32_t n_in) {
     Layout L;
@@ -36,6 +37,7 @@ __host__ __device__ inline Layout layout(uint32_t n_in) {
     L.b2 = L.W2 + HID * HID;
     L.w3 = L.b2 + HID;
     L.b3 = L.w3 + HID;
+    L.gate = L.b3 + 1;
     return L;
 }
 
@@ -144,6 +146,30 @@ __global__ void __launch_bounds__(WARPS * 32) features_kernel(Geom G, uint32_t b
     }
 }
 
+// The output rule of the learned estimator for one host: the closed form
+// `plain` (Eq. 11) is returned, flagged FALLBACK, when the host has no active
+// VAT in the window; flagged GATED when plain >= the model's gate; and,
+// flagged FALLBACK, when the corrected value is not finite.  Otherwise the
+// model's log-space correction: expm1(8 y + log1p(max(plain, 0))), where
+// x_last * 16 = log1p(max(plain, 0)) is the host's last feature.
+__device__ __forceinline__ float learned_rule(float plain, bool no_active, float y, float x_last, float gate,
+                                              uint8_t &flags) {
+    if (no_active) {
+        flags |= (uint8_t)VATE_FLAG_FALLBACK;
+        return plain;
+    }
+    if (plain >= gate) {
+        flags |= (uint8_t)VATE_FLAG_GATED;
+        return plain;
+    }
+    const float e = expm1f(8.0f * y + 16.0f * x_last);
+    if (!isfinite(e)) {
+        flags |= (uint8_t)VATE_FLAG_FALLBACK;
+        return plain;
+    }
+    return e;
+}
+
 // 32 hosts per warp: the warp extracts each host's features into its row of
 // xs (host_features), then lane j evaluates host j's model (mlp_eval_lane)
 // and the fallback.
@@ -183,12 +209,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) learned_estimate_kernel(Geom G,
         if (g0 + lane < n) {
             const float *x = xw + lane * XS;
             const float y = mlp_eval_lane(prm, w2t, n_in, x);
-            // the model corrects the closed form in log space: x[2k+1] * 16 = log1p(max(plain, 0))
-            float e = expm1f(8.0f * y + 16.0f * x[n_in - 1]);
-            if (myA == 0u || !isfinite(e)) {
-                e = myplain;
-                myf |= (uint8_t)VATE_FLAG_FALLBACK;
-            }
+            const float e = learned_rule(myplain, myA == 0u, y, x[n_in - 1], prm[layout(n_in).gate], myf);
             out[g0 + lane] = e;
             if (flags) flags[g0 + lane] = myf;
         }
@@ -218,6 +239,40 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_forward_kernel(const float *__
     }
 }
 
+// The output rule on feature rows (lane per row, as mlp_forward_kernel): a
+// row has no active VAT when its first k features (the per-age counts / g)
+// are all 0, k = (n_in - 2) / 2.
+__global__ void __launch_bounds__(WARPS * 32) mlp_apply_kernel(const float *__restrict__ params, uint32_t n_in,
+                                                               const float *__restrict__ x,
+                                                               const float *__restrict__ plain, uint64_t n,
+                                                               float *__restrict__ out, uint8_t *__restrict__ flags) {
+    extern __shared__ float4 dyn4[];
+    float *prm = reinterpret_cast<float *>(dyn4);
+    float *w2t = stage_model(prm, params, n_in);
+    float *xs = w2t + HID * HID;                       // [WARPS][32][XS]
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t k = (n_in - 2u) / 2u;
+    float *xw = xs + (size_t)warp * 32 * XS;
+    const uint64_t warp0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t r0 = warp0 * 32; r0 < n; r0 += nwarps * 32) {
+        const uint64_t rows = n - r0 < 32 ? n - r0 : 32;
+        for (uint32_t t = lane; t < rows * n_in; t += 32u) xw[(t / n_in) * XS + t % n_in] = x[r0 * n_in + t];
+        __syncwarp();
+        if (lane < rows) {
+            const float *xr = xw + lane * XS;
+            bool no_active = true;
+            for (uint32_t d = 0; d < k; d++) no_active = no_active && xr[d] == 0.0f;
+            const float y = mlp_eval_lane(prm, w2t, n_in, xr);
+            uint8_t f = 0;
+            out[r0 + lane] = learned_rule(plain[r0 + lane], no_active, y, xr[n_in - 1], prm[layout(n_in).gate], f);
+            if (flags) flags[r0 + lane] = f;
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void mlp_init_kernel(float *__restrict__ params, uint32_t n_in, uint64_t seed) {
     const Layout L = layout(n_in);
     const uint64_t np = n_params(n_in);
@@ -228,7 +283,7 @@ __global__ void mlp_init_kernel(float *__restrict__ params, uint32_t n_in, uint6
         else if (i >= L.w3 && i < L.b3) a = sqrtf(6.0f / (float)(HID + 1));
         const uint64_t r = mix64(seed ^ (i * 0x9E3779B97F4A7C15ull));
         const float u = (float)(r >> 40) * (1.0f / 16777216.0f);     // [0, 1), 24 bits
-        params[i] = a * (2.0f * u - 1.0f);
+        params[i] = i == L.gate ? INFINITY : a * (2.0f * u - 1.0f);  // the gate starts closed: never
     }
 }
 
@@ -318,9 +373,9 @@ __global__ void __launch_bounds__(TR_THREADS) mlp_grad_kernel(const float *__res
             for (uint32_t r = 0; r < TR_ROWS; r++) s += D2[r * HID + (p - L.b2)];
         } else if (p < L.b3) {                                  // dw3
             for (uint32_t r = 0; r < TR_ROWS; r++) s = fmaf(dy[r], H2[r * HID + (p - L.w3)], s);
-        } else {                                                // db3
+        } else if (p == L.b3) {                                 // db3
             for (uint32_t r = 0; r < TR_ROWS; r++) s += dy[r];
-        }
+        }                                                       // the gate: not trained (gradient 0)
         out[p] = s;
     }
 }
@@ -434,6 +489,22 @@ int vate_mlp_train_step(float *d_params, float *d_m, float *d_v, uint32_t n_in, 
     const float bc1 = 1.0f - powf(0.9f, (float)t), bc2 = 1.0f - powf(0.999f, (float)t);
     mlp_adam_kernel<<<(np + 255) / 256, 256, 0, st>>>(d_params, d_m, d_v, partial, loss_partial, tiles, np, lr, bc1,
                                                       bc2, d_grad, d_loss);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VATE_OK : set_error(VATE_ECUDA, cudaGetErrorString(e));
+}
+
+int vate_mlp_apply(const float *d_params, uint32_t n_in, const float *d_x, const float *d_plain, uint64_t n,
+                   float *d_out, uint8_t *d_flags, void *stream) {
+    if (!d_params || n_in < 4 || n_in > MAX_IN || (n_in & 1u))
+        return set_error(VATE_EINVAL, "bad parameters pointer or n_in (2k + 2 for 1 <= k <= 15)");
+    if (n && (!d_x || !d_plain || !d_out)) return set_error(VATE_EINVAL, "d_x, d_plain and d_out must not be NULL");
+    if (n == 0) return VATE_OK;
+    const size_t smem = sizeof(float) * (model_smem_floats(n_in) + (size_t)WARPS * 32 * XS);
+    if (cudaError_t e = cudaFuncSetAttribute(mlp_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+        return set_error(VATE_ECUDA, cudaGetErrorString(e));
+    int grid = (int)std::min<uint64_t>((n + WARPS * 32 - 1) / (WARPS * 32), (uint64_t)sms_now() * 8);
+    mlp_apply_kernel<<<grid, WARPS * 32, smem, (cudaStream_t)stream>>>(d_params, n_in, d_x, d_plain, n, d_out, d_flags);
     count_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VATE_OK : set_error(VATE_ECUDA, cudaGetErrorString(e));

@@ -132,6 +132,30 @@ def train(V, X, T, n_in, epochs=8, batch=4096, lr=2e-3, seed=1, weight=None, los
     return params
 
 
+GATE_CANDIDATES = [float("inf")] + [float(2 ** j) for j in range(21)]
+
+
+def choose_gate(V, params, X, plain, N, n_in):
+    """The gate tau of the model (include/vate_learned.h): the candidate that
+    minimises, on the TRAINING rows, the sum over the hosts with n >= 1 and
+    with n >= 100 of the learned estimator's mean relative error divided by
+    the closed form's.  Each candidate is scored on the estimates the library's
+    output rule returns (vate_mlp_apply); params[-1] is set to the choice."""
+    import torch
+    out = torch.empty_like(plain)
+    ref = {lo: mean_rel_err(plain, N, lo)[0] for lo in (1, 100)}
+    best, best_score, scores = None, float("inf"), {}
+    for tau in GATE_CANDIDATES:
+        params[-1] = tau
+        V.vate_mlp_apply(params, n_in, X, plain, out)
+        score = sum(mean_rel_err(out, N, lo)[0] / max(ref[lo], 1e-12) for lo in (1, 100) if ref[lo] == ref[lo])
+        scores[tau] = round(score, 5)
+        if score < best_score:
+            best, best_score = tau, score
+    params[-1] = best
+    return best, scores
+
+
 def mean_rel_err(est, n, lo=1):
     import torch
     sel = n >= lo
@@ -151,10 +175,11 @@ def run(V, spec=None, c=24, k=10, g=4096, seg_len=2, train_slices=200, eval_slic
     spec = LINK40G if spec is None else spec
     t0 = time.time()
     tr_train = DeviceTraffic(Traffic(spec))
-    X, T, _, N, _ = collect(V, tr_train, c, k, g, seg_len, seed, 0, train_slices + k, hosts_per_slice,
+    X, T, P, N, _ = collect(V, tr_train, c, k, g, seg_len, seed, 0, train_slices + k, hosts_per_slice,
                             large_share=large_share)
     t1 = time.time()
     params = train(V, X, T, 2 * k + 2, epochs=epochs, seed=seed, weight=balance_weights(N))
+    gate, gate_scores = choose_gate(V, params, X, P, N, 2 * k + 2)
     torch.cuda.synchronize()
     t2 = time.time()
     spec_eval = TrafficSpec(**{**spec.__dict__, "seed": spec.seed + 0x4E})
@@ -171,6 +196,8 @@ def run(V, spec=None, c=24, k=10, g=4096, seg_len=2, train_slices=200, eval_slic
     return {"mre": res, "accepted": bool(accepted), "train_rows": int(T.numel()), "eval_rows": int(Ne.numel()),
             "train_slices": train_slices, "eval_slices": eval_slices, "log2_pool": c, "k": k, "g": g,
             "learned_from": "vate_estimate_learned (the fused kernel that serves closes)",
+            "gate": gate, "gate_chosen_on": "the training rows (sum of learned / closed-form mean relative error "
+                                            "over n >= 1 and n >= 100)",
             "seconds": {"collect_train": round(t1 - t0, 2), "train": round(t2 - t1, 2),
                         "collect_eval": round(time.time() - t2, 2)},
             "params": params}

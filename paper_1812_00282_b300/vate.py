@@ -50,10 +50,10 @@ class vate_info(C.Structure):
 class vate_group_tuning(C.Structure):
     _fields_ = [("census_tile_chunks", C.c_uint32), ("blocks_per_sm", C.c_uint32),
                 ("gather_tile_hosts", C.c_uint32), ("ingest_tile_pairs", C.c_uint32),
-                ("preserve_tile_chunks", C.c_uint32), ("reserved", C.c_uint32)]
+                ("preserve_tile_chunks", C.c_uint32), ("wave_pool_mib", C.c_uint32)]
 
     def as_dict(self):
-        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 VATE_GROUP_BAD_OFFSETS, VATE_GROUP_BAD_KPRIME, VATE_GROUP_TIMEOUT = 1, 2, 4
@@ -128,6 +128,7 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
         "vate_features": (i, [vp, vp, u64, vp, vp]),
         "vate_mlp_init": (i, [vp, u32, u64, vp]),
         "vate_mlp_forward": (i, [vp, u32, vp, u64, vp, vp]),
+        "vate_mlp_apply": (i, [vp, u32, vp, vp, u64, vp, vp, vp]),
         "vate_mlp_train_step": (i, [vp, vp, vp, u32, vp, vp, vp, u32, u64, C.c_float, u32, vp, u64, vp, vp, vp]),
         "vate_estimate_learned": (i, [vp, vp, u64, vp, vp, vp, vp]),
         "vate_server_create": (i, [P(vate_server_config), P(vp)]),
@@ -403,7 +404,7 @@ def vate_census_noalloc(params: vate_params, pool, bact0: int, hist, stream=None
 
 # ---- learned estimator (include/vate_learned.h) -------------------------------
 
-VATE_FLAG_FALLBACK = 4
+VATE_FLAG_FALLBACK, VATE_FLAG_GATED = 4, 8
 VATE_MLP_LOSS_SQUARED, VATE_MLP_LOSS_ABSOLUTE = 0, 1
 
 
@@ -451,6 +452,18 @@ def vate_mlp_train_step(params, m, v, n_in: int, x, target, lr: float, t: int, s
         _dev(scratch, torch.float32, "scratch"),
         scratch.numel(), _dev(grad, torch.float32, "grad", npar) if grad is not None else None,
         _dev(loss, torch.float32, "loss", 1) if loss is not None else None, _stream(stream)))
+
+
+def vate_mlp_apply(params, n_in: int, x, plain, out, flags=None, stream=None) -> None:
+    """The learned estimator's output rule on feature rows (include/vate_learned.h)."""
+    import torch
+    n = plain.numel()
+    pp = _dev(params, torch.float32, "params", vate_mlp_param_count(n_in))
+    px = _dev(x, torch.float32, "x", n * n_in)
+    pl = _dev(plain, torch.float32, "plain", n)
+    po = _dev(out, torch.float32, "out", n)
+    pf = _dev(flags, torch.uint8, "flags", n) if flags is not None else None
+    _check(_lib.vate_mlp_apply(pp, n_in, px, pl, n, po, pf, _stream(stream)))
 
 
 def vate_estimate_learned(h, aips, params, out, flags=None, stream=None) -> None:

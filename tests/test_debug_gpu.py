@@ -40,7 +40,7 @@ def run(V, params, slices=5):
     for s in range(slices):
         d.ingest(as_i32(tr.slice_pairs(s)), s)
         d.close_slice(s)
-        pool = torch.empty(1 << params[0], dtype=torch.uint8, device="cuda")
+        pool = torch.empty(1 << params[0], dtype=torch.uint8 if params[1] <= 63 else torch.int16, device="cuda")
         hist = torch.empty(2 * params[1] + 1, dtype=torch.int64, device="cuda")
         e = torch.empty(hosts.numel(), dtype=torch.float32, device="cuda")
         f = torch.empty(hosts.numel(), dtype=torch.uint8, device="cuda")

@@ -61,11 +61,15 @@ def pack(pairs, hosts, kprime):
             torch.tensor(np.asarray(kprime, np.int32)).cuda())
 
 
-def run_group_vs_single(V, monitors, nslices, graph=False, autotune_at=None):
+def run_group_vs_single(V, monitors, nslices, graph=False, autotune_at=None, wave_mib=None):
     rng = np.random.default_rng(len(monitors) * 31 + nslices)
     trs = [Traffic(SMALL, pkts_per_slice=5000) for _ in monitors]
     params = [V.make_params(*m) for m in monitors]
     grp = V.VateGroup(params)
+    if wave_mib is not None:
+        t = V.vate_group_get_tuning(grp.g)
+        t.wave_pool_mib = wave_mib
+        V.vate_group_set_tuning(grp.g, t)
     singles = [V.Vate(*m) for m in monitors]
     kprime = [max(1, (m[1] + 1) // 2) if i % 2 else m[1] for i, m in enumerate(monitors)]
     cap_p, cap_h = 6000 * len(monitors), 700 * len(monitors)
@@ -132,8 +136,10 @@ def run_group_vs_single(V, monitors, nslices, graph=False, autotune_at=None):
         d.close()
 
 
-def test_group_equals_single_handles(V):
-    run_group_vs_single(V, MONITORS_L32, nslices=14)
+@pytest.mark.parametrize("wave_mib", [0, 1, 48])
+def test_group_equals_single_handles(V, wave_mib):
+    # waves of one monitor (1 MiB), of several, and one wave of all
+    run_group_vs_single(V, MONITORS_L32, nslices=14, wave_mib=wave_mib)
 
 
 @pytest.mark.parametrize("L", [1, 2, 4, 8, 16, 64])
@@ -210,7 +216,8 @@ def test_group_tuning_is_checked(V):
     t = V.vate_group_get_tuning(grp.g)
     assert t.blocks_per_sm >= 1 and t.census_tile_chunks >= 256
     for field, bad in (("blocks_per_sm", 0), ("blocks_per_sm", 99), ("census_tile_chunks", 3000),
-                       ("gather_tile_hosts", 100), ("ingest_tile_pairs", 70000), ("preserve_tile_chunks", 0)):
+                       ("gather_tile_hosts", 100), ("ingest_tile_pairs", 70000), ("preserve_tile_chunks", 0),
+                       ("wave_pool_mib", 70000)):
         u = V.vate_group_tuning.from_buffer_copy(t)
         setattr(u, field, bad)
         with pytest.raises(V.VateError) as e:

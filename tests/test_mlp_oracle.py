@@ -37,17 +37,17 @@ def test_forward_of_a_hand_built_network():
     W1 = np.zeros((n_in, 64)); W1[0, 0] = 1.0; W1[0, 1] = -1.0
     W2 = np.zeros((64, 64)); W2[0, 0] = 1.0; W2[1, 1] = 1.0
     w3 = np.zeros(64); w3[0] = w3[1] = 1.0
-    p = np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [0.25]])
+    p = np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [0.25], [np.inf]])
     X = np.array([[2.0, 5.0, -1.0], [-3.0, 0.0, 0.0], [0.0, 1.0, 1.0]])
     np.testing.assert_allclose(mlp.forward(p, n_in, X), [2.25, 3.25, 0.25])
 
 
-def _abs_net(n_in, b3):
-    # y = relu(x0) + relu(-x0) + b3 = |x0| + b3 (as in the forward pin)
+def _abs_net(n_in, b3, tau=np.inf):
+    # y = relu(x0) + relu(-x0) + b3 = |x0| + b3 (as in the forward pin); gate tau
     W1 = np.zeros((n_in, 64)); W1[0, 0] = 1.0; W1[0, 1] = -1.0
     W2 = np.zeros((64, 64)); W2[0, 0] = 1.0; W2[1, 1] = 1.0
     w3 = np.zeros(64); w3[0] = w3[1] = 1.0
-    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [b3]])
+    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [b3], [tau]])
 
 
 def test_learned_output_of_a_hand_built_network():
@@ -70,6 +70,7 @@ def test_learned_output_zero_model_reproduces_the_clamped_closed_form():
     # expm1(log1p(.)) round trip)
     k, n_in = 3, 8
     p = np.zeros(mlp.n_params(n_in))
+    p[-1] = np.inf                                        # no gate
     rng = np.random.default_rng(4)
     X = rng.uniform(0.01, 1, (50, n_in))
     plain = rng.normal(0, 300, 50)
@@ -91,3 +92,28 @@ def test_learned_output_falls_back_to_the_closed_form():
     assert est[1] == 100.0 and fl[1] == 1 | mlp.FALLBACK
     assert np.isclose(est[2], np.expm1(88.0), rtol=1e-15) and fl[2] == 0
     assert np.isclose(est[3], 41.0, rtol=1e-13) and fl[3] == 0
+
+
+def test_learned_output_gate_returns_the_closed_form_above_tau():
+    # tau = 100: hosts whose closed form is >= 100 keep it (GATED); below, the
+    # model's value; a host with no active VAT is FALLBACK whatever its plain
+    k, n_in = 2, 6
+    p = _abs_net(n_in, 0.25, tau=100.0)
+    X = np.array([[0.5, 0.0, 0, 0, 0.75, 0.1],
+                  [0.5, 0.0, 0, 0, 0.75, 0.1],
+                  [0.5, 0.0, 0, 0, 0.75, 0.1],
+                  [0.0, 0.0, 0, 0, 0.75, 0.1]])
+    plain = np.array([99.5, 100.0, 3000.0, 500.0])
+    est, fl, _ = mlp.estimate(p, n_in, X, plain, k)
+    assert np.isclose(est[0], np.expm1(6.0 + np.log1p(99.5)), rtol=1e-15) and fl[0] == 0
+    assert est[1] == 100.0 and fl[1] == mlp.GATED
+    assert est[2] == 3000.0 and fl[2] == mlp.GATED
+    assert est[3] == 500.0 and fl[3] == mlp.FALLBACK
+
+
+def test_gradient_of_the_gate_is_zero():
+    rng = np.random.default_rng(9)
+    n_in = 4
+    p = rng.normal(0, 0.3, mlp.n_params(n_in))
+    _, g = mlp.loss_and_grad(p, n_in, rng.normal(0, 1, (9, n_in)), rng.normal(0, 1, 9))
+    assert g.shape == p.shape and g[-1] == 0.0
