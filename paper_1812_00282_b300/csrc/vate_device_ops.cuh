@@ -10,10 +10,14 @@ namespace vate {
 // frame-0 pool, for the bytes inside [s0, e0) (block with ACT 0) or [s1, e1)
 // (block with ACT k): both clear the values selected by pc
 // (preserve_consts_frame0 of the new BACT^0).
+// CG: the chunk is read with an L2-only load, so that the SM keeps no L1 copy
+// of it (the monitor group's single launch later reads the pool through the
+// read-only path after other blocks have written it).
+template <bool CG = false>
 __device__ __forceinline__ void preserve_chunk(uint8_t *pool, uint64_t base, const RangeConsts &pc, uint32_t twok,
                                                uint64_t s0, uint64_t e0, uint64_t s1, uint64_t e1) {
     uint4 *p = reinterpret_cast<uint4 *>(pool + base);
-    uint4 w = *p;
+    uint4 w = CG ? __ldcg(p) : *p;
     uint4 r;
     r.x = swar_preserve_frame0(w.x, pc, twok);
     r.y = swar_preserve_frame0(w.y, pc, twok);

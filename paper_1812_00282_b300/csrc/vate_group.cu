@@ -20,12 +20,18 @@
 // later wait of the launch gives up at once, so the kernel always returns.
 //
 // The list is cut into waves of consecutive monitors whose pools together fit a
-// byte budget (the tuning's wave_pool_mib; 0: one wave), and within a wave it
-// is phase-major: every monitor's B and P items, then every monitor's I
-// items, then C, then G.  So a wave's pools stay in L2 from their SetATs to
-// their census and gather, and an item's wait is for the tail of its own
-// monitor's previous phase while the other monitors' items of that phase keep
-// the blocks busy.  The per-chunk and per-host
+// byte budget (the tuning's wave_pool_mib; 0: one wave of all monitors), and
+// the waves are software-pipelined: step s lists the B, P and I items of wave
+// s, then the C items of wave s - 1, then the G items of wave s - 2, each
+// phase monitor after monitor.  So the pools of at most three waves are live
+// in L2 at a time, and between any item and the items it waits for lie whole
+// phases of other waves, which keep the blocks busy.  With one wave the order
+// is phase-major: every B, P and I item, then every C, then every G.
+//
+// Loads: PreserveAT reads its chunks L2-only, SetAT only stores and the
+// census reads L2-only, so no SM holds an L1 copy of a pool line when the
+// gather reads it through the read-only path after the writes of other
+// blocks (L1 starts empty at every launch).  The per-chunk and per-host
 // arithmetic is the one of the single-pool kernels (vate_device_ops.cuh), so
 // every monitor is bit-identical to a vate_handle run alone.  The slice
 // number, the batch offsets and k' are read on the device, so the one launch
@@ -186,17 +192,17 @@ __device__ bool wait_done(const unsigned int *done, unsigned int target, GroupSt
 template <int GK>
 __device__ __forceinline__ uint32_t gather_one(const Geom &G, const RangeConsts &rc, uint32_t c2k, uint32_t bact0,
                                                uint32_t kp, uint32_t aip, uint32_t lane, const StepArgs &a) {
-    // L2-only loads (CG): the pool was written by other blocks of this launch
+    // the read-only path: no L1 copy of the pool predates this launch's writes (see the top of the file)
     if constexpr (GK <= 2) {
         const uint32_t nseg = G.g >> G.log2L;
         if (nseg % (32u * 2u) == 0)
-            return gather_host_vec<GK, 2, true, 1, false, true>(G, rc, c2k, aip, a.u1, a.u2, a.u3, lane);
-        return gather_host_vec<GK, 2, false, 1, false, true>(G, rc, c2k, aip, a.u1, a.u2, a.u3, lane);
+            return gather_host_vec<GK, 2, true>(G, rc, c2k, aip, a.u1, a.u2, a.u3, lane);
+        return gather_host_vec<GK, 2, false>(G, rc, c2k, aip, a.u1, a.u2, a.u3, lane);
     } else if constexpr (GK <= 5) {
         constexpr int SB = GK == 3 ? 2 : (GK == 4 ? 4 : 8);
-        return gather_host_seg<SB, 1, false, true>(G, rc, c2k, G.twok * ONES, aip, lane);
+        return gather_host_seg<SB, 1, false>(G, rc, c2k, G.twok * ONES, aip, lane);
     } else {
-        return gather_host_scalar<true>(G, bact0, kp, aip, lane);
+        return gather_host_scalar(G, bact0, kp, aip, lane);
     }
 }
 
@@ -210,7 +216,8 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
     uint32_t *kp = cum + M * (NPHASE + 1);                            // M: k' (clamped)
     uint32_t *seg_start = kp + M;                                     // NPHASE * M + 1: first item of each segment
     uint32_t *seg_mp = seg_start + (NPHASE * M + 1);                  // NPHASE * M: (monitor << 3) | phase
-    uint32_t *cols = seg_mp + NPHASE * M;                             // census lane columns [C_WARPS][pairs][32]
+    uint32_t *wave_lo = seg_mp + NPHASE * M;                          // M + 1: first monitor of each wave
+    uint32_t *cols = wave_lo + (M + 1);                               // census lane columns [C_WARPS][pairs][32]
     const uint32_t maxpairs = (a.maxbins + 1u) / 2u;
 
     __shared__ unsigned long long s_step, s_t0, s_t1;
@@ -274,21 +281,33 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
     }
     __syncthreads();
     if (tid == 0) {
-        // segments = (monitor, phase) runs of items, ordered wave by wave, phase-major inside a wave
-        uint32_t ns = 0, run = 0;
-        for (uint32_t m0 = 0; m0 < M;) {
+        // waves of consecutive monitors whose pools add up to at most wave_bytes (one monitor at least)
+        uint32_t nw = 0;
+        for (uint32_t m0 = 0; m0 < M; nw++) {
+            wave_lo[nw] = m0;
             uint32_t m1 = m0 + 1;
             uint64_t bytes = a.descs[m0].P;
-            while (m1 < M && a.wave_bytes && bytes + a.descs[m1].P <= a.wave_bytes) bytes += a.descs[m1++].P;
             if (!a.wave_bytes) m1 = M;
-            for (int p = 0; p < NPHASE; p++)
-                for (uint32_t m = m0; m < m1; m++) {
+            while (m1 < M && bytes + a.descs[m1].P <= a.wave_bytes) bytes += a.descs[m1++].P;
+            m0 = m1;
+        }
+        wave_lo[nw] = M;
+        // segments = (monitor, phase) runs of items: step s lists B, P, I of wave s, C of wave s - 1,
+        // G of wave s - 2, each phase monitor after monitor
+        uint32_t ns = 0, run = 0;
+        auto emit = [&](uint32_t w, int p0, int p1) {
+            for (int p = p0; p <= p1; p++)
+                for (uint32_t m = wave_lo[w]; m < wave_lo[w + 1]; m++) {
                     seg_start[ns] = run;
                     seg_mp[ns] = (m << 3) | (uint32_t)p;
                     run += cum[m * (NPHASE + 1) + p + 1] - cum[m * (NPHASE + 1) + p];
                     ns++;
                 }
-            m0 = m1;
+        };
+        for (uint32_t st2 = 0; st2 < nw + 2; st2++) {
+            if (st2 < nw) emit(st2, 0, 2);
+            if (st2 >= 1 && st2 <= nw) emit(st2 - 1, 3, 3);
+            if (st2 >= 2) emit(st2 - 2, 4, 4);
         }
         seg_start[ns] = run;                  // ns = NPHASE * M: the total
     }
@@ -311,16 +330,21 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                 s_t = j - seg_start[sg];
                 s_ok = wait_done(a.done + m, cm[p] + a.missing, st, a.spin_limit) ? 1u : 0u;
                 if (a.trace) s_t1 = global_ns();
-                sG = a.descs[m];
                 if (p == 4) {                       // N0 of Eq. 11 from the census (written in this launch)
                     uint64_t act = 0;
                     for (uint32_t d = 0; d < kp[m]; d++) act += __ldcg(a.hist + (size_t)m * a.maxbins + d);
-                    s_n0 = a.descs[m].P - act;
+                    s_n0 = (1ull << a.descs[m].c) - act;
                 }
             }
         }
         __syncthreads();
         if (s_j >= total) break;
+        if (warp == 0 && s_ok) {                                 // the item's descriptor, copied by one warp
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(a.descs + s_m);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&sG);
+            for (uint32_t w = lane; w < sizeof(Geom) / 4; w += 32u) dst[w] = src[w];
+        }
+        __syncthreads();
         if (s_ok) {
             const uint32_t m = s_m, p = s_p, t = s_t;
             const Geom G = sG;
@@ -334,7 +358,7 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                 for (uint64_t u = (uint64_t)t * a.preserve_tile + tid; u < u1; u += blockDim.x) {
                     const uint64_t chunk = u < ps.n0 ? ps.c0s + u : ps.c1s + (u - ps.n0);
                     if (u >= ps.n0 && ps.n0 && chunk >= ps.c0s && chunk < ps.c0e) continue;   // range 0's chunk
-                    preserve_chunk(G.pool, chunk << 4, pc, G.twok, ps.s0, ps.e0, ps.s1, ps.e1);
+                    preserve_chunk<true>(G.pool, chunk << 4, pc, G.twok, ps.s0, ps.e0, ps.s1, ps.e1);
                 }
             } else if (p == 2) {                                 // I: SetAT (frame 0: the value BACT^0)
                 const uint2 *p2 = reinterpret_cast<const uint2 *>(a.pairs);   // 8-byte aligned (host check)
@@ -495,9 +519,9 @@ struct vate_group {
 namespace {
 
 // dynamic shared memory of group_step_kernel: two uint64 offset arrays, then
-// cum, kp, seg_start and seg_mp (uint32), then the census lane columns
+// cum, kp, seg_start, seg_mp and wave_lo (uint32), then the census lane columns
 size_t step_smem(uint32_t M, uint32_t maxbins) {
-    const size_t words = 4 * (size_t)(M + 1) + (size_t)M * (NPHASE + 1) + M + 2 * (size_t)NPHASE * M + 1;
+    const size_t words = 4 * (size_t)(M + 1) + (size_t)M * (NPHASE + 1) + M + 2 * (size_t)NPHASE * M + 1 + (M + 1);
     return words * 4 + (size_t)C_WARPS * ((maxbins + 1) / 2) * 32 * sizeof(uint32_t);
 }
 

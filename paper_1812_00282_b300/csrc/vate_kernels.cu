@@ -59,14 +59,6 @@ __device__ __forceinline__ void set_at(const Geom &G, uint32_t bact0, uint32_t a
     uint32_t pid = vat_pid(G, aip, vid);
     if (!VATE_CHECK_POSITION(G, pid)) return;           // checked build: a position outside the pool
     if (pid < G.lo || pid >= G.hi) return;              // another shard's AT
-#ifdef VATE_INGEST_DEDUP
-    // warp-aggregated SetAT (a measured variant, off by default): the lanes
-    // holding the same position let the lowest of them store it
-    if (!G.packed) {
-        const uint32_t same = __match_any_sync(__activemask(), pid);
-        if ((threadIdx.x & 31u) != (uint32_t)(__ffs(same) - 1)) return;
-    }
-#endif
     uint32_t v = G.counter == 1u ? 0u : bact0;
     if (G.packed) {                  // clear the field, then set it (see vate_packed.cu)
         uint32_t q = (uint32_t)mulhi64(G.mpn, pid), sh = (pid - q * G.pn) * G.atb;

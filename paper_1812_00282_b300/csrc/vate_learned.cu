@@ -148,23 +148,24 @@ __global__ void __launch_bounds__(WARPS * 32) features_kernel(Geom G, uint32_t b
 
 // The output rule of the learned estimator for one host: the closed form
 // `plain` (Eq. 11) is returned, flagged FALLBACK, when the host has no active
-// VAT in the window; flagged GATED when plain >= the model's gate; and,
-// flagged FALLBACK, when the corrected value is not finite.  Otherwise the
-// model's log-space correction: expm1(8 y + log1p(max(plain, 0))), where
-// x_last * 16 = log1p(max(plain, 0)) is the host's last feature.
+// VAT in the window or when the corrected value expm1(8 y + log1p(max(plain,
+// 0))) is not finite (x_last * 16 = log1p(max(plain, 0)) is the host's last
+// feature); flagged GATED when the corrected value is >= the model's gate (a
+// large host, for which the closed form is the better estimate); otherwise
+// the corrected value.
 __device__ __forceinline__ float learned_rule(float plain, bool no_active, float y, float x_last, float gate,
                                               uint8_t &flags) {
     if (no_active) {
         flags |= (uint8_t)VATE_FLAG_FALLBACK;
         return plain;
     }
-    if (plain >= gate) {
-        flags |= (uint8_t)VATE_FLAG_GATED;
-        return plain;
-    }
     const float e = expm1f(8.0f * y + 16.0f * x_last);
     if (!isfinite(e)) {
         flags |= (uint8_t)VATE_FLAG_FALLBACK;
+        return plain;
+    }
+    if (e >= gate) {
+        flags |= (uint8_t)VATE_FLAG_GATED;
         return plain;
     }
     return e;

@@ -136,8 +136,9 @@ GATE_CANDIDATES = [float("inf")] + [float(2 ** j) for j in range(21)]
 
 
 def choose_gate(V, params, X, plain, N, n_in):
-    """The gate tau of the model (include/vate_learned.h), chosen on the
-    TRAINING rows: among the candidates whose mean relative error is no worse
+    """The gate tau of the model (include/vate_learned.h: the closed form is
+    returned where the corrected value is >= tau), chosen on the TRAINING
+    rows: among the candidates whose mean relative error is no worse
     than the closed form's over the hosts with n >= 1 and over those with
     n >= 100 (the acceptance criterion), the one with the smallest error over
     n >= 1; if none is, the one with the smallest sum of the two errors, each

@@ -96,12 +96,14 @@ def test_mlp_apply_matches_the_oracle_rule(V):
     V.vate_mlp_apply(torch.from_numpy(p).cuda(), n_in, torch.from_numpy(X).cuda(), torch.from_numpy(plain).cuda(),
                      out, fl)
     est, flags, z = mlp.estimate(p.astype(np.float64), n_in, X.astype(np.float64), plain.astype(np.float64), k)
-    np.testing.assert_array_equal(fl.cpu().numpy(), flags)
+    with np.errstate(over="ignore"):
+        amb = np.abs(np.expm1(z) - 300.0) <= 0.03            # either side of the gate in FP32
+    np.testing.assert_array_equal(fl.cpu().numpy()[~amb], flags[~amb])
     assert (flags & mlp.GATED).any() and (flags & mlp.FALLBACK).any() and (flags == 0).any()
     dev = out.cpu().numpy().astype(np.float64)
-    closed = flags != 0
+    closed = (flags != 0) & ~amb
     assert np.array_equal(dev[closed], plain[closed].astype(np.float64))
-    m = ~closed
+    m = (flags == 0) & ~amb
     bound = learned_error_bound(p.astype(np.float64), n_in, X[m].astype(np.float64), plain[m].astype(np.float64),
                                 z[m], est[m], plain_rtol=0.0)
     assert np.all(np.abs(dev[m] - est[m]) <= bound)
@@ -153,10 +155,12 @@ def check_fused_against_oracle(V, d, o, hosts, params, out=None, fl=None, idx=No
     p64 = params.cpu().numpy().astype(np.float64)
     est, flags, z = mlp.estimate(p64, n_in, X, plain, k, pflags)
     dev = out.cpu().numpy()[idx].astype(np.float64)
-    # a closed form within 1e-5 of the gate may fall on either side of it (FP32 on the device)
+    # a corrected value within 1e-4 of the gate may fall on either side of it (FP32 on the device)
     tau = mlp.gate(p64)
-    amb = np.isfinite(tau) & (np.abs(plain - tau) <= 1e-5 * max(abs(tau), 1.0))
-    assert amb.sum() <= 2, amb.sum()
+    with np.errstate(invalid="ignore", over="ignore"):
+        e_all = np.expm1(z)
+        amb = np.isfinite(tau) & (np.abs(e_all - tau) <= 1e-4 * max(abs(tau), 1.0))
+    assert amb.sum() <= max(2, len(idx) // 100), amb.sum()
     np.testing.assert_array_equal(fl.cpu().numpy()[idx][~amb], flags[~amb],
                                   err_msg="flags (SAT, POOLFULL, FALLBACK, GATED)")
     closed = ((flags & (mlp.FALLBACK | mlp.GATED)) != 0) & ~amb
@@ -238,9 +242,7 @@ def test_fused_estimate_matches_oracle_small(V, L, scenario):
     gated = trained.clone()
     plain = torch.empty(len(hosts), dtype=torch.float32, device="cuda")
     d.estimate(as_i32(hosts), 5, plain)
-    u = torch.unique(plain)                                          # the closed form takes discrete values:
-    i = int(0.7 * (u.numel() - 1))                                   # a gate half way between two of them
-    gated[-1] = float((u[i].double() + u[i + 1].double()) / 2)       # sends about 30 % of the hosts to it
+    gated[-1] = float(torch.quantile(plain.double().clamp(min=0), 0.7)) + 0.5   # gates roughly the top 30 %
     for params in (trained, glorot, gated):
         rel, share, nfb = check_fused_against_oracle(V, d, o, hosts, params)
         if scenario == "sparse":

@@ -95,19 +95,21 @@ def test_learned_output_falls_back_to_the_closed_form():
 
 
 def test_learned_output_gate_returns_the_closed_form_above_tau():
-    # tau = 100: hosts whose closed form is >= 100 keep it (GATED); below, the
-    # model's value; a host with no active VAT is FALLBACK whatever its plain
+    # tau = 100: where the corrected value expm1(8 y + log1p(plain)) is >= 100
+    # the closed form is kept (GATED) -- even a closed form below tau (row 2);
+    # below, the corrected value; a host with no active VAT is FALLBACK
     k, n_in = 2, 6
-    p = _abs_net(n_in, 0.25, tau=100.0)
-    X = np.array([[0.5, 0.0, 0, 0, 0.75, 0.1],
-                  [0.5, 0.0, 0, 0, 0.75, 0.1],
-                  [0.5, 0.0, 0, 0, 0.75, 0.1],
-                  [0.0, 0.0, 0, 0, 0.75, 0.1]])
-    plain = np.array([99.5, 100.0, 3000.0, 500.0])
-    est, fl, _ = mlp.estimate(p, n_in, X, plain, k)
-    assert np.isclose(est[0], np.expm1(6.0 + np.log1p(99.5)), rtol=1e-15) and fl[0] == 0
-    assert est[1] == 100.0 and fl[1] == mlp.GATED
-    assert est[2] == 3000.0 and fl[2] == mlp.GATED
+    p = _abs_net(n_in, 0.25, tau=100.0)           # y = |x0| + 0.25
+    X = np.array([[0.25, 0.1, 0, 0, 0.75, 0.1],     # y = 0.5:  z = 4 + 0.5 = 4.5, e = 89
+                  [0.5, 0.0, 0, 0, 0.75, 0.1],      # y = 0.75: z = 6 + log1p(3000)
+                  [0.0, 0.25, 0, 0, 0.75, 0.1],     # y = 0.25: z = 2 + 3 = 5, e = 147
+                  [0.0, 0.0, 0, 0, 0.75, 0.1]])     # no active VAT
+    plain = np.array([np.expm1(0.5), 3000.0, np.expm1(3.0), 500.0])
+    est, fl, z = mlp.estimate(p, n_in, X, plain, k)
+    np.testing.assert_allclose(z[[0, 2]], [4.5, 5.0], rtol=1e-15)
+    assert np.isclose(est[0], np.expm1(4.5), rtol=1e-15) and fl[0] == 0
+    assert est[1] == 3000.0 and fl[1] == mlp.GATED
+    assert est[2] == plain[2] and fl[2] == mlp.GATED
     assert est[3] == 500.0 and fl[3] == mlp.FALLBACK
 
 
