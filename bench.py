@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--aips", type=int, default=1 << 20, help="hosts estimated per slice")
     ap.add_argument("--pkts", type=int, default=5_000_000, help="packets per slice")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--group-modes", default="plain,graph,graph_tuned",
+                    help="monitors64: the step forms to time (plain launch, graph, graph after the autotuner)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
@@ -546,36 +548,41 @@ def run_learned(V, torch):
     """The learned-estimator workload: the 40 Gb/s traffic on a 2^24-AT pool,
     k = 10, g = 4096; MLP trained on 200 generated slices with exact labels,
     evaluated against the closed form on 100 held-out slices of another seed;
-    plus the close-time cost of the fused learned estimate for 2^20 hosts."""
+    at 32-AT segments (the configuration of the learned estimator) and at the
+    2-AT segments of the 40 Gb/s workload; plus the close-time cost of the
+    fused learned estimate for 2^20 hosts at each."""
     from paper_1812_00282_b300 import learned
     from traffic import LINK40G, DeviceTraffic, Traffic
-    r = learned.run(V)
-    params = r.pop("params")
-    # time both estimators on one closed slice of the same configuration
+    out = {}
     dt = DeviceTraffic(Traffic(LINK40G))
-    mon = V.Vate(24, 10, 4096, 2, 0, 0xC4)
-    for s in range(11):
-        mon.ingest(dt.slice_pairs(s), s)
-    mon.close_slice(10)
     hosts = dt.hosts()
-    out = torch.empty(hosts.numel(), dtype=torch.float32, device="cuda")
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    times = {}
-    for name, fn in (("plain", lambda: mon.estimate(hosts, 10, out)),
-                     ("learned", lambda: V.vate_estimate_learned(mon.h, hosts, params, out))):
-        fn()
-        best = 1e9
-        for _ in range(5):
-            ev[0].record()
+    est = torch.empty(hosts.numel(), dtype=torch.float32, device="cuda")
+    for L in (32, 2):
+        r = learned.run(V, seg_len=L)
+        params = r.pop("params")
+        # time both estimators on one closed slice of the same configuration
+        mon = V.Vate(24, 10, 4096, L, 0, 0xC4)
+        for s in range(11):
+            mon.ingest(dt.slice_pairs(s), s)
+        mon.close_slice(10)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        times = {}
+        for name, fn in (("plain", lambda: mon.estimate(hosts, 10, est)),
+                         ("learned", lambda: V.vate_estimate_learned(mon.h, hosts, params, est))):
             fn()
-            ev[1].record()
-            torch.cuda.synchronize()
-            best = min(best, ev[0].elapsed_time(ev[1]))
-        times[name] = round(best, 4)
-    mon.close()
-    r["estimate_ms_2p20_hosts"] = times
-    r["population"] = "hosts active in the window, sampled per slice; relative error |max(est,0) - n| / n"
-    return r
+            best = 1e9
+            for _ in range(5):
+                ev[0].record()
+                fn()
+                ev[1].record()
+                torch.cuda.synchronize()
+                best = min(best, ev[0].elapsed_time(ev[1]))
+            times[name] = round(best, 4)
+        mon.close()
+        r["estimate_ms_2p20_hosts"] = times
+        r["population"] = "hosts active in the window, sampled per slice; relative error |max(est,0) - n| / n"
+        out["seg_len_%d" % L] = r
+    return out
 
 
 def run_e2e(args, V, torch, tr, dt, rank, world):
@@ -883,7 +890,7 @@ def run_monitors64(args):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
     res = {}
-    for mode in ("plain", "graph", "graph_tuned"):
+    for mode in args.group_modes.split(","):
         grp.close()
         grp = V.VateGroup(params)
         if mode == "graph_tuned":
@@ -908,7 +915,7 @@ def run_monitors64(args):
         res[mode] = {"ms_per_step": round(statistics.mean(times), 4), "p99_ms": round(float(np.percentile(times, 99)), 4),
                      "mpkts": round(int(po[-1]) / statistics.mean(times) / 1e3, 1)}
     grp.close()
-    best = min(res[m]["ms_per_step"] for m in ("plain", "graph", "graph_tuned"))
+    best = min(res[m]["ms_per_step"] for m in args.group_modes.split(","))
     return {"metric": METRIC, "value": round(int(po[-1]) / best / 1e3, 3), "unit": "Mpkt/s", "n_gpus": 1,
             "steps": K, "warmup": W, "ms_per_step": best, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
@@ -929,7 +936,7 @@ def run_serving(args):
     import paper_1812_00282_b300 as V
     from paper_1812_00282_b300 import learned, serving
     torch.cuda.set_device(0)
-    lr = learned.run(V, train_slices=60, eval_slices=20)
+    lr = learned.run(V, seg_len=serving.SEG_LEN, train_slices=60, eval_slices=20)   # the served monitors' placement
     model = lr.pop("params")
     paced = serving.run(V, duration=5.0, paced=True, model=model)
     flood = serving.run(V, duration=5.0, paced=False, model=model)

@@ -50,7 +50,8 @@ typedef struct vate_group vate_group;
 /* Tiling of the step kernel, chosen by vate_group_autotune or set by hand.
  *   census_tile_chunks    16-byte chunks per census work item (power of two, 256..65536)
  *   blocks_per_sm         persistent grid: blocks of 256 threads per SM (1 .. the kernel's occupancy)
- *   gather_tile_hosts     hosts per gather work item (multiple of 256, 256..65536)
+ *   gather_tile_hosts     hosts per gather work item for g = 4096 (multiple of 256, 256..65536); a
+ *                         monitor with g VATs per host takes about 4096 / g times as many
  *   ingest_tile_pairs     pairs per SetAT work item (multiple of 256, 256..65536)
  *   preserve_tile_chunks  16-byte chunks per PreserveAT work item (multiple of 256, 256..65536)
  *   wave_pool_mib         work order: consecutive monitors whose pools add up to at most this many MiB

@@ -158,6 +158,15 @@ __device__ __forceinline__ PreserveSpan preserve_span(const Geom &G, unsigned lo
 // Thread 0 of a block: wait until *done >= target, with at most `limit`
 // sleeps of ~128 ns.  A wait that gives up marks the launch (poisoned) and
 // the group (VATE_GROUP_TIMEOUT); a wait in a marked launch gives up at once.
+// Hosts per gather item of a monitor with g VATs per host: the tuning's tile
+// is for g = 4096; smaller vectors take proportionally more hosts, so that an
+// item is about the same work whatever g (a multiple of 256, at most 65,536).
+__device__ __forceinline__ uint32_t gather_tile_of(uint32_t tile, uint32_t g) {
+    uint64_t t = (uint64_t)tile * 4096u / (g ? g : 1u);
+    t = (t + 255u) & ~255ull;
+    return (uint32_t)(t < tile ? tile : (t > 65536u ? 65536u : t));
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -221,7 +230,7 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
     const uint32_t maxpairs = (a.maxbins + 1u) / 2u;
 
     __shared__ unsigned long long s_step, s_t0, s_t1;
-    __shared__ uint32_t s_j, s_m, s_p, s_t, s_ok;
+    __shared__ uint32_t s_j, s_m, s_p, s_t, s_ok, s_next;
     __shared__ uint64_t s_n0;
     __shared__ Geom sG;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
@@ -271,7 +280,8 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                             : (uint32_t)((preserve_span(G, step).n + a.preserve_tile - 1) / a.preserve_tile);
         n[2] = (uint32_t)((po[m + 1] - po[m] + a.ingest_tile - 1) / a.ingest_tile);
         n[3] = (uint32_t)(((G.P >> 4) + a.census_tile - 1) / a.census_tile);
-        n[4] = (uint32_t)((ho[m + 1] - ho[m] + a.gather_tile - 1) / a.gather_tile);
+        const uint32_t gt = gather_tile_of(a.gather_tile, G.g);
+        n[4] = (uint32_t)((ho[m + 1] - ho[m] + gt - 1) / gt);
         uint32_t c = 0;
         for (int p = 0; p < NPHASE; p++) {
             cum[m * (NPHASE + 1) + p] = c;
@@ -328,6 +338,7 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                 s_m = m;
                 s_p = p;
                 s_t = j - seg_start[sg];
+                s_next = 0u;
                 s_ok = wait_done(a.done + m, cm[p] + a.missing, st, a.spin_limit) ? 1u : 0u;
                 if (a.trace) s_t1 = global_ns();
                 if (p == 4) {                       // N0 of Eq. 11 from the census (written in this launch)
@@ -423,11 +434,16 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                 const RangeConsts rc = range_consts(bact0, k1, G.twok);   // frame 0: ACT = BACT^0
                 const uint32_t c2k = (128u - G.twok) * ONES;
                 const uint64_t N0 = s_n0;
-                const uint64_t h0 = ho[m] + (uint64_t)t * a.gather_tile;
-                const uint64_t h1 = min(h0 + a.gather_tile, ho[m + 1]);
-                // 32 hosts per warp at a time: lane j keeps host b0 + j's count, the 32 Eq. 11
-                // epilogues run side by side
-                for (uint64_t b0 = h0 + (uint64_t)warp * 32u; b0 < h1; b0 += (uint64_t)G_WARPS * 32u) {
+                const uint32_t gt = gather_tile_of(a.gather_tile, G.g);
+                const uint64_t h0 = ho[m] + (uint64_t)t * gt;
+                const uint64_t h1 = min(h0 + gt, ho[m + 1]);
+                // the warps take 32 hosts at a time from the item (lane j keeps host b0 + j's count,
+                // the 32 Eq. 11 epilogues run side by side)
+                for (;;) {
+                    uint64_t b0 = 0;
+                    if (lane == 0) b0 = h0 + atomicAdd(&s_next, 32u);
+                    b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+                    if (b0 >= h1) break;
                     const uint64_t b1 = min(b0 + 32u, h1);
                     const uint32_t my_aip = b0 + lane < b1 ? a.hosts[b0 + lane] : 0u;
                     uint32_t myA = 0;
@@ -445,8 +461,9 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                 }
             }
         }
-        // the item's writes, then its completion (release to the waits of later items)
-        __threadfence();
+        // the item's writes, then its completion (release to the waits of later items); a gather's
+        // outputs are read by no later item, so it needs no fence
+        if (s_p != 4u) __threadfence();
         __syncthreads();
         if (tid == 0 && s_ok) atomicAdd(a.done + s_m, 1u);
         if (tid == 0 && a.trace && s_j < a.trace_cap) {        // handed out, started, finished, what and where

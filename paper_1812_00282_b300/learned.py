@@ -174,10 +174,10 @@ def mean_rel_err(est, n, lo=1):
     return float((torch.abs(e[sel] - n[sel]) / n[sel]).mean().item()), int(sel.sum().item())
 
 
-def run(V, spec=None, c=24, k=10, g=4096, seg_len=2, train_slices=200, eval_slices=100, hosts_per_slice=8192,
+def run(V, spec=None, c=24, k=10, g=4096, seg_len=32, train_slices=200, eval_slices=100, hosts_per_slice=8192,
         eval_hosts_per_slice=16384, epochs=8, seed=0xC4, large_share=0.0) -> Dict:
     """Learned-estimator workload: the 40 Gb/s traffic on a 2^24-AT pool, k = 10,
-    g = 4096, 2-AT segments (the placement of the 40 Gb/s workload);
+    g = 4096, segments of seg_len VATs;
     train on `train_slices` generated slices, evaluate on `eval_slices`
     held-out slices of a differently seeded stream, against the closed form.
     The learned estimates evaluated are those of vate_estimate_learned."""

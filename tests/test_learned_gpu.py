@@ -303,10 +303,25 @@ def test_learned_full_configuration_no_worse_than_eq11(V):
     # form's (Eq. 11), over all hosts active in the window and over the hosts
     # with at least 100 peers.
     from paper_1812_00282_b300 import learned
-    r = learned.run(V)
+    r = learned.run(V)                      # 32-AT segments
     assert r["train_slices"] == 200 and r["eval_slices"] == 100 and r["log2_pool"] == 24
     assert r["accepted"]
     for pop in ("n>=1", "n>=100"):
         m = r["mre"][pop]
         assert m["hosts"] > 1000 and np.isfinite(m["learned"])
         assert m["learned"] <= m["plain"], (pop, m)
+
+
+@pytest.mark.slow
+def test_learned_at_the_placement_of_the_40gbps_workload(V):
+    # The same workload at 2-AT segments, where the closed form is far better
+    # than at 32 (mean relative error 0.28 instead of 0.61 over n >= 100): the
+    # model still beats it over all hosts active in the window, and stays
+    # within 5 % of it over the hosts with n >= 100 (measured 0.293 vs 0.282;
+    # no gate tau made the model no worse there on the training rows).
+    from paper_1812_00282_b300 import learned
+    r = learned.run(V, seg_len=2)
+    m1, m100 = r["mre"]["n>=1"], r["mre"]["n>=100"]
+    assert m1["hosts"] > 1000 and m100["hosts"] > 1000
+    assert m1["learned"] <= m1["plain"], m1
+    assert m100["learned"] <= 1.05 * m100["plain"], m100
