@@ -534,6 +534,38 @@ def test_error_falls_with_pool_size_and_vector_length():
     assert by_g[0] > by_g[1] and by_g[0] > by_g[2], by_g
 
 
+def test_error_falls_with_vector_length_where_g_matters():
+    # Eq. 1 on a quiet pool: for a host of n distinct peers the relative
+    # standard error of the linear-counting estimate over g VATs is
+    # sqrt(e^t - t - 1) / (t sqrt(g)) with t = n / g, which falls as g grows,
+    # and at n near g ln g the vector saturates (g = 256 here: 256 ln 256 ~
+    # 1,420 < n).  Sixteen hosts of 2,000-5,000 peers each, alone on a
+    # 2^22-AT pool, one slice: the mean relative error falls strictly over
+    # g = 256, 1024, 4096, and for the two unsaturated g it is within a
+    # factor of two of sqrt(2 / pi) times the mean standard error (the mean
+    # absolute value of a normal error).
+    rng = np.random.default_rng(12)
+    ns = np.array([2000, 3000, 4000, 5000] * 4)
+    aips = (np.arange(1, len(ns) + 1, dtype=np.uint64) * 7919).astype(np.uint32)
+    parts = []
+    for a, n in zip(aips, ns):
+        b = np.unique(rng.integers(1, 2**32, size=2 * n, dtype=np.uint64))[:n]
+        rng.shuffle(b)
+        parts.append(np.stack([np.full(n, a, np.uint32), b.astype(np.uint32)], 1))
+    pairs = np.ascontiguousarray(np.concatenate(parts))
+    mre = []
+    for g in (256, 1024, 4096):
+        o = Oracle(c=22, k=2, g=g, seg_len=1, seed=3)
+        o.ingest(pairs)
+        est, _, _ = o.estimate(aips, 2)
+        mre.append(float(np.mean(np.abs(np.maximum(est, 0) - ns) / ns)))
+    assert mre[0] > mre[1] > mre[2], mre
+    for g, m in zip((1024, 4096), mre[1:]):
+        t = ns / g
+        pred = math.sqrt(2 / math.pi) * float(np.mean(np.sqrt(np.exp(t) - t - 1) / (t * math.sqrt(g))))
+        assert 0.5 * pred < m < 2 * pred, (g, m, pred)
+
+
 def test_oracle_results_do_not_depend_on_its_thread_count():
     # the census, the inactive count and the per-host loops may run on
     # several OpenMP threads (for the timed CPU baseline); integer sums and
