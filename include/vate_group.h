@@ -7,10 +7,13 @@
  * PreserveAT on the two blocks whose ACT became 0 or k), SetAT for every pair,
  * pool census, CheckAT gather and Eq. 11 for every host -- for all of them in
  * ONE persistent launch per slice.  Its blocks take (monitor, phase, tile)
- * work items in order from a device queue, monitor after monitor; an item
- * starts once the earlier phases of its monitor have finished (a bounded
- * device-side wait on a per-monitor count of finished items, which can only
- * wait on items already handed to running blocks).  Every monitor computes
+ * work items -- begin, PreserveAT, SetAT, census -- in order from a device
+ * queue, monitor after monitor; an item starts once the earlier phases of its
+ * monitor have finished (a bounded device-side wait on a per-monitor count of
+ * finished items, which can only wait on items already handed to running
+ * blocks).  A block that finds the queue empty gathers: each of its warps
+ * takes a few hosts at a time, monitor after monitor, once every item of the
+ * monitor has finished (the same bounded wait).  Every monitor computes
  * exactly what a single vate_handle with the same parameters computes (the
  * same device arithmetic); a monitor's result does not depend on the other
  * monitors in the group.
@@ -50,18 +53,18 @@ typedef struct vate_group vate_group;
 /* Tiling of the step kernel, chosen by vate_group_autotune or set by hand.
  *   census_tile_chunks    16-byte chunks per census work item (power of two, 256..65536)
  *   blocks_per_sm         persistent grid: blocks of 256 threads per SM (1 .. the kernel's occupancy)
- *   gather_tile_hosts     hosts per gather work item for g = 4096 (multiple of 256, 256..65536); a
- *                         monitor with g VATs per host takes about 4096 / g times as many
+ *   gather_grab_hosts     hosts a warp takes at a time for g = 4096 (1..32); a monitor with g VATs
+ *                         per host gives 4096 / g times as many (at least 1, at most 32)
  *   ingest_tile_pairs     pairs per SetAT work item (multiple of 256, 256..65536)
  *   preserve_tile_chunks  16-byte chunks per PreserveAT work item (multiple of 256, 256..65536)
  *   wave_pool_mib         work order: consecutive monitors whose pools add up to at most this many MiB
- *                         form a wave, and a wave's items go phase by phase (every monitor's
- *                         PreserveAT, then SetAT, census, gather), so that its pools stay in L2;
- *                         0: one wave of all monitors (0..65536) */
+ *                         form a wave; the SetAT items of wave s are listed before the census
+ *                         items of wave s - 1, so that a census reads pools SetAT has just
+ *                         written; 0: one wave of all monitors (0..65536) */
 typedef struct {
     uint32_t census_tile_chunks;
     uint32_t blocks_per_sm;
-    uint32_t gather_tile_hosts;
+    uint32_t gather_grab_hosts;
     uint32_t ingest_tile_pairs;
     uint32_t preserve_tile_chunks;
     uint32_t wave_pool_mib;
@@ -104,8 +107,10 @@ int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_
 /* Project-written autotuner: after at least one step, repeats that step (same
  * slice: a second PreserveAT of the same slide changes nothing, a repeat of
  * the same SetATs writes the same values, the census and the gather recompute
- * the same outputs) under candidate tilings -- blocks per SM, census, ingest
- * and gather tiles -- times each with CUDA events on `stream` (synchronising
+ * the same outputs) under candidate tilings -- blocks per SM {2 .. 4} within
+ * the kernel's occupancy, waves {0, 32 MiB}, census tiles {4,096, 16,384},
+ * gather grabs {2, 4, 8}, ingest tiles {4,096, 16,384, 65,536} -- times each
+ * as the best of three replays with CUDA events on `stream` (synchronising
  * it), keeps the fastest and writes it to *chosen (may be NULL).  The
  * monitors' state and the outputs end exactly as the last step left them.
  * The inputs MUST be exactly those of the last vate_group_step (same pairs,
@@ -131,11 +136,14 @@ int vate_group_get_tuning(const vate_group *g, vate_group_tuning *t);
 int vate_group_set_wait(vate_group *g, uint64_t spin_limit, uint32_t missing);
 
 /* Trace of later steps, for tuning: work item j of a step writes four words
- * at d_trace[4j..4j+3] (j < capacity; device uint64): the %globaltimer
- * nanoseconds when it was handed out, when its wait for the earlier phases of
- * its monitor ended and when it finished, then (SM << 32) | (monitor << 8) |
- * phase (0 begin, 1 PreserveAT, 2 SetAT, 3 census, 4 gather).  capacity 0
- * stops tracing.  Errors: VATE_EINVAL. */
+ * at d_trace[4j..4j+3] (device uint64): the %globaltimer nanoseconds when it
+ * was handed out, when its wait for the earlier phases of its monitor ended
+ * and when it finished, then (SM << 32) | (monitor << 8) | phase (0 begin,
+ * 1 PreserveAT, 2 SetAT, 3 census).  Then, with n the step's item count,
+ * block b writes its gather at d_trace[4(n + b)..]: the start twice, the
+ * end, then (SM << 32) | (0xFFFFFF << 8) | 4.  Only entries below capacity
+ * are written (clear the buffer first to tell them apart); capacity 0 stops
+ * tracing.  Errors: VATE_EINVAL. */
 int vate_group_set_trace(vate_group *g, uint64_t *d_trace, uint32_t capacity);
 
 /* Kernel nodes of the captured step graph (0 before the first

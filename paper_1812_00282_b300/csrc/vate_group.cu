@@ -8,7 +8,6 @@
 //      0 or k, in tiles of 16-byte chunks                          (none at slice 0)
 //   I  SetAT for the monitor's pairs, in tiles of pairs
 //   C  pool census, in tiles of 16-byte chunks
-//   G  CheckAT gather + Eq. 11 for the monitor's hosts, in tiles of hosts
 // An item of one phase of monitor m starts once every item of the earlier
 // phases of m has finished: a per-monitor count of finished items, waited on
 // by the block's first thread with a bounded spin.  Every item waits only on
@@ -22,11 +21,19 @@
 // The list is cut into waves of consecutive monitors whose pools together fit a
 // byte budget (the tuning's wave_pool_mib; 0: one wave of all monitors), and
 // the waves are software-pipelined: step s lists the B, P and I items of wave
-// s, then the C items of wave s - 1, then the G items of wave s - 2, each
-// phase monitor after monitor.  So the pools of at most three waves are live
-// in L2 at a time, and between any item and the items it waits for lie whole
-// phases of other waves, which keep the blocks busy.  With one wave the order
-// is phase-major: every B, P and I item, then every C, then every G.
+// s, then the C items of wave s - 1, each phase monitor after monitor.  With
+// one wave the order is phase-major: every B, P and I item, then every C.
+//
+//   G  CheckAT gather + Eq. 11 is not an item: a block that finds the list
+//      exhausted turns its warps loose on the hosts, monitor after monitor,
+//      each warp taking a few hosts at a time from the monitor's host
+//      counter (the tuning's gather_grab_hosts, scaled by g).  A warp's first
+//      batch of a monitor waits (its first lane, bounded as above) until
+//      every item of the monitor has finished.  Warps never wait for one
+//      another, and the hosts in flight at any time are those of one or two
+//      monitors, whose pools then stay in L2 (blocks of whole tiles of hosts
+//      would spread the reads over many pools).  The waits depend only on
+//      items, all of which are held by running blocks by then.
 //
 // Loads: PreserveAT reads its chunks L2-only, SetAT only stores and the
 // census reads L2-only, so no SM holds an L1 copy of a pool line when the
@@ -59,8 +66,27 @@ constexpr uint32_t MAX_MONITORS = 256;
 constexpr int G_THREADS = 256;
 constexpr int G_WARPS = G_THREADS / 32;
 constexpr int NPHASE = 5;                 // B, P, I, C, G
-constexpr int C_WARPS = 6;                // warps that count a census item (their lane columns fit 4 blocks per SM)
-constexpr int G_MIN_BLOCKS = 4;           // blocks per SM the step kernel is built for (at most 64 registers)
+// Compile-time shape of the step kernel, measured on the 64-monitor workload
+// (44.2 M pairs, 1.86 M hosts, 0.58 GiB of pools, no persisting L2): at most
+// 64 registers (4 blocks per SM) and six census warps 3.50 ms; 80 registers
+// (3 blocks per SM) 2.56 ms with six census warps, 2.55 with four, 2.68 with
+// two (the gather phase 1.96 -> 1.19 ms: its loads in flight); 96 registers
+// (2 blocks per SM) 2.90 ms.
+#ifndef VATE_GROUP_CWARPS
+#define VATE_GROUP_CWARPS 4
+#endif
+#ifndef VATE_GROUP_MINB
+#define VATE_GROUP_MINB 3
+#endif
+#ifndef VATE_GROUP_INGEST_U
+#define VATE_GROUP_INGEST_U 8
+#endif
+#ifndef VATE_GROUP_GATHER_CG
+#define VATE_GROUP_GATHER_CG 0
+#endif
+constexpr int C_WARPS = VATE_GROUP_CWARPS;      // warps that count a census item (lane columns in shared memory)
+constexpr int G_MIN_BLOCKS = VATE_GROUP_MINB;   // blocks per SM the step kernel is built for (3: at most 80 registers)
+constexpr int I_BATCH = VATE_GROUP_INGEST_U;    // pairs a thread loads before its SetATs
 constexpr unsigned long long DEFAULT_SPIN_LIMIT = 1ull << 23;   // x ~128 ns of sleep: about a second
 
 struct GroupState {                       // device-resident
@@ -89,9 +115,10 @@ struct StepArgs {
     uint8_t *flags;
     unsigned long long spin_limit;
     uint32_t M, maxbins;
-    uint32_t census_tile, ingest_tile, gather_tile, preserve_tile;
+    uint32_t census_tile, ingest_tile, gather_grab, preserve_tile;
+    unsigned long long *qhost;            // [M]: hosts of the monitor handed out in the running launch
     uint64_t wave_bytes;                  // pools per wave of monitors (0: one wave of all monitors)
-    unsigned long long *trace;            // NULL, or 4 words per item (vate_group_set_trace)
+    unsigned long long *trace;            // NULL, or 4 words per item and per block (vate_group_set_trace)
     uint32_t trace_cap;                   // items the trace buffer holds
     uint32_t advance;                     // 1: the next slice; 0: repeat the last slice (autotuner)
     uint32_t missing;                     // added to every wait's target (tests of the timeout path)
@@ -158,13 +185,12 @@ __device__ __forceinline__ PreserveSpan preserve_span(const Geom &G, unsigned lo
 // Thread 0 of a block: wait until *done >= target, with at most `limit`
 // sleeps of ~128 ns.  A wait that gives up marks the launch (poisoned) and
 // the group (VATE_GROUP_TIMEOUT); a wait in a marked launch gives up at once.
-// Hosts per gather item of a monitor with g VATs per host: the tuning's tile
-// is for g = 4096; smaller vectors take proportionally more hosts, so that an
-// item is about the same work whatever g (a multiple of 256, at most 65,536).
-__device__ __forceinline__ uint32_t gather_tile_of(uint32_t tile, uint32_t g) {
-    uint64_t t = (uint64_t)tile * 4096u / (g ? g : 1u);
-    t = (t + 255u) & ~255ull;
-    return (uint32_t)(t < tile ? tile : (t > 65536u ? 65536u : t));
+// Hosts a warp takes at a time from a monitor with g VATs per host: the
+// tuning's figure is for g = 4096, scaled by 4096 / g so that a batch is
+// about the same work whatever g, in [1, 32] (a lane keeps one host's count).
+__device__ __forceinline__ uint32_t gather_grab_of(uint32_t grab, uint32_t g) {
+    const uint64_t t = (uint64_t)grab * 4096u / (g ? g : 1u);
+    return (uint32_t)(t < 1u ? 1u : (t > 32u ? 32u : t));
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -204,9 +230,10 @@ __device__ __forceinline__ uint32_t gather_one(const Geom &G, const RangeConsts 
     // the read-only path: no L1 copy of the pool predates this launch's writes (see the top of the file)
     if constexpr (GK <= 2) {
         const uint32_t nseg = G.g >> G.log2L;
+        constexpr bool CG = VATE_GROUP_GATHER_CG != 0;
         if (nseg % (32u * 2u) == 0)
-            return gather_host_vec<GK, 2, true>(G, rc, c2k, aip, a.u1, a.u2, a.u3, lane);
-        return gather_host_vec<GK, 2, false>(G, rc, c2k, aip, a.u1, a.u2, a.u3, lane);
+            return gather_host_vec<GK, 2, true, 1, false, CG>(G, rc, c2k, aip, a.u1, a.u2, a.u3, lane);
+        return gather_host_vec<GK, 2, false, 1, false, CG>(G, rc, c2k, aip, a.u1, a.u2, a.u3, lane);
     } else if constexpr (GK <= 5) {
         constexpr int SB = GK == 3 ? 2 : (GK == 4 ? 4 : 8);
         return gather_host_seg<SB, 1, false>(G, rc, c2k, G.twok * ONES, aip, lane);
@@ -230,9 +257,8 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
     const uint32_t maxpairs = (a.maxbins + 1u) / 2u;
 
     __shared__ unsigned long long s_step, s_t0, s_t1;
-    __shared__ uint32_t s_j, s_m, s_p, s_t, s_ok, s_next;
-    __shared__ uint64_t s_n0;
-    __shared__ Geom sG;
+    __shared__ uint32_t s_j, s_m, s_p, s_t, s_ok, s_gm;
+    __shared__ Geom sG, sGw[G_WARPS];
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     GroupState *st = a.st;
 
@@ -280,8 +306,7 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                             : (uint32_t)((preserve_span(G, step).n + a.preserve_tile - 1) / a.preserve_tile);
         n[2] = (uint32_t)((po[m + 1] - po[m] + a.ingest_tile - 1) / a.ingest_tile);
         n[3] = (uint32_t)(((G.P >> 4) + a.census_tile - 1) / a.census_tile);
-        const uint32_t gt = gather_tile_of(a.gather_tile, G.g);
-        n[4] = (uint32_t)((ho[m + 1] - ho[m] + gt - 1) / gt);
+        n[4] = 0u;                            // G runs after the list, warp by warp
         uint32_t c = 0;
         for (int p = 0; p < NPHASE; p++) {
             cum[m * (NPHASE + 1) + p] = c;
@@ -303,7 +328,7 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
         }
         wave_lo[nw] = M;
         // segments = (monitor, phase) runs of items: step s lists B, P, I of wave s, C of wave s - 1,
-        // G of wave s - 2, each phase monitor after monitor
+        // each phase monitor after monitor
         uint32_t ns = 0, run = 0;
         auto emit = [&](uint32_t w, int p0, int p1) {
             for (int p = p0; p <= p1; p++)
@@ -314,15 +339,14 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                     ns++;
                 }
         };
-        for (uint32_t st2 = 0; st2 < nw + 2; st2++) {
+        for (uint32_t st2 = 0; st2 < nw + 1; st2++) {
             if (st2 < nw) emit(st2, 0, 2);
-            if (st2 >= 1 && st2 <= nw) emit(st2 - 1, 3, 3);
-            if (st2 >= 2) emit(st2 - 2, 4, 4);
+            if (st2 >= 1) emit(st2 - 1, 3, 3);
         }
-        seg_start[ns] = run;                  // ns = NPHASE * M: the total
+        seg_start[ns] = run;                  // ns = 4 M: the total
     }
     __syncthreads();
-    const uint32_t nsegs = NPHASE * M;
+    const uint32_t nsegs = 4u * M;
     const uint32_t total = seg_start[nsegs];
 
     // ---- the items ----
@@ -338,14 +362,8 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                 s_m = m;
                 s_p = p;
                 s_t = j - seg_start[sg];
-                s_next = 0u;
                 s_ok = wait_done(a.done + m, cm[p] + a.missing, st, a.spin_limit) ? 1u : 0u;
                 if (a.trace) s_t1 = global_ns();
-                if (p == 4) {                       // N0 of Eq. 11 from the census (written in this launch)
-                    uint64_t act = 0;
-                    for (uint32_t d = 0; d < kp[m]; d++) act += __ldcg(a.hist + (size_t)m * a.maxbins + d);
-                    s_n0 = (1ull << a.descs[m].c) - act;
-                }
             }
         }
         __syncthreads();
@@ -376,13 +394,23 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                 const uint64_t i0 = po[m] + (uint64_t)t * a.ingest_tile;
                 const uint64_t i1 = min(i0 + a.ingest_tile, po[m + 1]);
                 const uint8_t v = (uint8_t)bact0;
-#pragma unroll 4
-                for (uint64_t i = i0 + tid; i < i1; i += G_THREADS) {
-                    const uint2 q = __ldcs(p2 + i);
-                    const uint32_t pid = vat_pid(G, q.x, bh(G, q.y));
-                    if (VATE_CHECK_POSITION(G, pid)) G.pool[pid] = v;
+                // I_BATCH pairs loaded before any store: a byte store may alias the pairs, so the
+                // compiler would not move a later load above it
+                for (uint64_t i = i0 + tid; i < i1; i += (uint64_t)I_BATCH * G_THREADS) {
+                    uint2 q[I_BATCH];
+#pragma unroll
+                    for (int u = 0; u < I_BATCH; u++) {
+                        const uint64_t j = i + (uint64_t)u * G_THREADS;
+                        q[u] = j < i1 ? __ldcs(p2 + j) : make_uint2(0u, 0u);
+                    }
+#pragma unroll
+                    for (int u = 0; u < I_BATCH; u++) {
+                        if (i + (uint64_t)u * G_THREADS >= i1) break;
+                        const uint32_t pid = vat_pid(G, q[u].x, bh(G, q[u].y));
+                        if (VATE_CHECK_POSITION(G, pid)) G.pool[pid] = v;
+                    }
                 }
-            } else if (p == 3) {                                 // C: census tile into lane columns
+            } else {                                             // C: census tile into lane columns
                 const uint32_t nbins = G.twok + 1u, npairs = (nbins + 1u) / 2u;
                 const bool counts = warp < (uint32_t)C_WARPS;      // the counting warps (the others wait)
                 uint32_t *col = cols + (size_t)(counts ? warp : 0u) * maxpairs * 32u + lane;
@@ -391,9 +419,9 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                 const uint32_t pat = G.twok * ONES;
                 uint32_t runs = 0;
                 const uint4 *pool16 = reinterpret_cast<const uint4 *>(G.pool);
-                // a tile holds at most 65,536 chunks: a lane counts at most 4,096 ATs, every
-                // 16-bit counter stays exact
-                // a tile holds at most 65,536 chunks, over C_WARPS * 32 lanes: at most 5,462 ATs a lane
+                // a tile holds at most 65,536 chunks, over C_WARPS * 32 lanes: at most 2^20 / (32 C_WARPS)
+                // ATs a lane (8,192 for four warps), so every 16-bit counter stays exact
+                static_assert(C_WARPS >= 1 && (1u << 20) / (32u * C_WARPS) < 65536u, "16-bit census counters");
                 constexpr int U = 8;
                 constexpr uint32_t CT = C_WARPS * 32u;           // counting threads
                 const uint64_t q0 = (uint64_t)t * a.census_tile;
@@ -429,41 +457,10 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
                     if (lane == 0 && hi && 2u * r + 1u < nbins)
                         atomicAdd(h + census_raw_bin(G, bact0, 2u * r + 1u), (unsigned long long)hi);
                 }
-            } else {                                             // G: gather + Eq. 11, warp per host
-                const uint32_t k1 = kp[m];
-                const RangeConsts rc = range_consts(bact0, k1, G.twok);   // frame 0: ACT = BACT^0
-                const uint32_t c2k = (128u - G.twok) * ONES;
-                const uint64_t N0 = s_n0;
-                const uint32_t gt = gather_tile_of(a.gather_tile, G.g);
-                const uint64_t h0 = ho[m] + (uint64_t)t * gt;
-                const uint64_t h1 = min(h0 + gt, ho[m + 1]);
-                // the warps take 32 hosts at a time from the item (lane j keeps host b0 + j's count,
-                // the 32 Eq. 11 epilogues run side by side)
-                for (;;) {
-                    uint64_t b0 = 0;
-                    if (lane == 0) b0 = h0 + atomicAdd(&s_next, 32u);
-                    b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
-                    if (b0 >= h1) break;
-                    const uint64_t b1 = min(b0 + 32u, h1);
-                    const uint32_t my_aip = b0 + lane < b1 ? a.hosts[b0 + lane] : 0u;
-                    uint32_t myA = 0;
-                    for (uint32_t j = 0; j < (uint32_t)(b1 - b0); j++) {
-                        const uint32_t aip = __shfl_sync(0xFFFFFFFFu, my_aip, j);
-                        const uint32_t A =
-                            __reduce_add_sync(0xFFFFFFFFu, gather_one<GK>(G, rc, c2k, bact0, k1, aip, lane, a));
-                        if (lane == j) myA = A;
-                    }
-                    if (b0 + lane < b1) {
-                        uint8_t f;
-                        a.out[b0 + lane] = estimate_eq11(G.g, G.P, N0, myA, f);
-                        if (a.flags) a.flags[b0 + lane] = f;
-                    }
-                }
             }
         }
-        // the item's writes, then its completion (release to the waits of later items); a gather's
-        // outputs are read by no later item, so it needs no fence
-        if (s_p != 4u) __threadfence();
+        // the item's writes, then its completion (release to the waits of later items)
+        __threadfence();
         __syncthreads();
         if (tid == 0 && s_ok) atomicAdd(a.done + s_m, 1u);
         if (tid == 0 && a.trace && s_j < a.trace_cap) {        // handed out, started, finished, what and where
@@ -474,6 +471,82 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
             tr[3] = ((unsigned long long)sm_id() << 32) | ((unsigned long long)s_m << 8) | s_p;
         }
     }
+
+    // ---- G: CheckAT gather + Eq. 11, warp by warp over the hosts ----
+    if (tid == 0) {
+        s_gm = 0u;                            // monitors below s_gm: this block has seen their hosts run out
+        if (a.trace) s_t0 = global_ns();
+    }
+    __syncthreads();
+    {
+        Geom &G = sGw[warp];                  // the descriptor of the warp's monitor
+        uint32_t m = 0, have = 0xFFFFFFFFu;
+        bool ready = false;                   // every item of monitor `have` has finished
+        RangeConsts rc = {};
+        uint32_t c2k = 0, k1 = 1, bact0 = 0, grab = 1;
+        uint64_t N0 = 0;
+        for (;;) {
+            m = max(m, *reinterpret_cast<volatile uint32_t *>(&s_gm));
+            if (m >= M) break;
+            if (m != have) {
+                __syncwarp();
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(a.descs + m);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(&G);
+                for (uint32_t w = lane; w < sizeof(Geom) / 4; w += 32u) dst[w] = src[w];
+                __syncwarp();
+                have = m;
+                ready = false;
+                k1 = kp[m];
+                bact0 = bact0_of(step, G.twok);
+                rc = range_consts(bact0, k1, G.twok);            // frame 0: ACT = BACT^0
+                c2k = (128u - G.twok) * ONES;
+                grab = gather_grab_of(a.gather_grab, G.g);
+            }
+            const uint64_t nh = ho[m + 1] - ho[m];
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(a.qhost + m, (unsigned long long)grab);
+            b = __shfl_sync(0xFFFFFFFFu, b, 0);
+            if (b >= nh) {                                       // the monitor's hosts are all handed out
+                if (lane == 0) atomicMax(&s_gm, m + 1u);
+                m++;
+                continue;
+            }
+            if (!ready) {
+                uint32_t ok = 0;
+                if (lane == 0)
+                    ok = wait_done(a.done + m, cum[m * (NPHASE + 1) + NPHASE] + a.missing, st, a.spin_limit) ? 1u : 0u;
+                if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) break;
+                // N0 of Eq. 11 from the census (written in this launch: read from L2)
+                unsigned long long act = 0;
+                for (uint32_t d = lane; d < k1; d += 32u) act += __ldcg(a.hist + (size_t)m * a.maxbins + d);
+                for (int o = 16; o; o >>= 1) act += __shfl_xor_sync(0xFFFFFFFFu, act, o);
+                N0 = (1ull << G.c) - act;
+                ready = true;
+            }
+            // lane j keeps host b0 + j's count; the Eq. 11 epilogues run side by side
+            const uint64_t b0 = ho[m] + b, b1 = ho[m] + min((uint64_t)b + grab, nh);
+            const uint32_t my_aip = b0 + lane < b1 ? a.hosts[b0 + lane] : 0u;
+            uint32_t myA = 0;
+            for (uint32_t j = 0; j < (uint32_t)(b1 - b0); j++) {
+                const uint32_t aip = __shfl_sync(0xFFFFFFFFu, my_aip, j);
+                const uint32_t A = __reduce_add_sync(0xFFFFFFFFu, gather_one<GK>(G, rc, c2k, bact0, k1, aip, lane, a));
+                if (lane == j) myA = A;
+            }
+            if (b0 + lane < b1) {
+                uint8_t f;
+                a.out[b0 + lane] = estimate_eq11(G.g, G.P, N0, myA, f);
+                if (a.flags) a.flags[b0 + lane] = f;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && a.trace && total + blockIdx.x < a.trace_cap) {   // the block's gather: entry n_items + block
+        unsigned long long *tr = a.trace + 4ull * (total + blockIdx.x);
+        tr[0] = s_t0;
+        tr[1] = s_t0;
+        tr[2] = global_ns();
+        tr[3] = ((unsigned long long)sm_id() << 32) | (0xFFFFFFull << 8) | 4u;
+    }
     }   // s_ok
 
     // ---- the last block to finish closes the launch ----
@@ -483,7 +556,10 @@ __global__ void __launch_bounds__(G_THREADS, G_MIN_BLOCKS) group_step_kernel(Ste
         const unsigned int t = atomicAdd(&st->blocks_done, 1u);
         if (t == gridDim.x - 1u) {
             __threadfence();
-            for (uint32_t m = 0; m < M; m++) a.done[m] = 0u;
+            for (uint32_t m = 0; m < M; m++) {
+                a.done[m] = 0u;
+                a.qhost[m] = 0ull;
+            }
             st->q_items = 0u;
             st->blocks_done = 0u;
             if (!*reinterpret_cast<volatile unsigned int *>(&st->poisoned)) {   // a timed-out step is not one
@@ -513,6 +589,7 @@ struct vate_group {
     Geom *d_descs = nullptr;
     GroupState *d_state = nullptr;
     unsigned int *d_done = nullptr;  // M
+    unsigned long long *d_qhost = nullptr;   // M: host counters of the gather
     uint64_t *d_hist = nullptr;      // M x maxbins
     uint32_t maxbins = 0;
     uint32_t L = 1;
@@ -576,9 +653,11 @@ int check_tuning(const vate_group_tuning *t, int max_bps) {
         snprintf(msg, sizeof msg, "blocks_per_sm must be in [1, %d] (the step kernel's occupancy)", max_bps);
         return vate::set_error(VATE_EINVAL, msg);
     }
-    for (uint32_t v : {t->gather_tile_hosts, t->ingest_tile_pairs, t->preserve_tile_chunks})
+    for (uint32_t v : {t->ingest_tile_pairs, t->preserve_tile_chunks})
         if (v < 256 || v > 65536 || v % 256)
-            return vate::set_error(VATE_EINVAL, "gather, ingest and preserve tiles: multiples of 256 in [256, 65536]");
+            return vate::set_error(VATE_EINVAL, "ingest and preserve tiles: multiples of 256 in [256, 65536]");
+    if (t->gather_grab_hosts < 1 || t->gather_grab_hosts > 32)
+        return vate::set_error(VATE_EINVAL, "gather_grab_hosts must be in [1, 32]");
     if (t->wave_pool_mib > 65536) return vate::set_error(VATE_EINVAL, "wave_pool_mib must be in [0, 65536]");
     return VATE_OK;
 }
@@ -605,7 +684,8 @@ cudaError_t enqueue_step(vate_group *g, const vate_pair *pairs, const uint64_t *
     a.maxbins = g->maxbins;
     a.census_tile = g->tuning.census_tile_chunks;
     a.ingest_tile = g->tuning.ingest_tile_pairs;
-    a.gather_tile = g->tuning.gather_tile_hosts;
+    a.gather_grab = g->tuning.gather_grab_hosts;
+    a.qhost = g->d_qhost;
     a.preserve_tile = g->tuning.preserve_tile_chunks;
     a.wave_bytes = (uint64_t)g->tuning.wave_pool_mib << 20;
     a.advance = advance;
@@ -687,14 +767,15 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
     g->max_blocks_per_sm = occ;
     g->tuning.census_tile_chunks = 16384;
     g->tuning.blocks_per_sm = (uint32_t)std::min(occ, 3);
-    g->tuning.gather_tile_hosts = 256;
-    g->tuning.ingest_tile_pairs = 4096;
+    g->tuning.gather_grab_hosts = 8;
+    g->tuning.ingest_tile_pairs = 16384;
     g->tuning.preserve_tile_chunks = 4096;
-    g->tuning.wave_pool_mib = 48;
+    g->tuning.wave_pool_mib = 0;
     bool ok = cudaMalloc(&g->arena, g->arena_bytes) == cudaSuccess &&
               cudaMalloc(&g->d_descs, n_monitors * sizeof(Geom)) == cudaSuccess &&
               cudaMalloc(&g->d_state, sizeof(GroupState)) == cudaSuccess &&
               cudaMalloc(&g->d_done, n_monitors * sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc(&g->d_qhost, n_monitors * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMalloc(&g->d_hist, (size_t)n_monitors * g->maxbins * sizeof(uint64_t)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
@@ -732,6 +813,7 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
     cudaError_t e = cudaMemcpyAsync(g->d_descs, g->geoms.data(), n_monitors * sizeof(Geom), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_state, &s0, sizeof s0, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_done, 0, n_monitors * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_qhost, 0, n_monitors * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_hist, 0, (size_t)n_monitors * g->maxbins * sizeof(uint64_t), st);
     for (uint32_t m = 0; m < n_monitors && e == cudaSuccess; m++) {
         Geom G = g->geoms[m];
@@ -756,6 +838,7 @@ int vate_group_destroy(vate_group *g) {
     cudaFree(g->d_descs);
     cudaFree(g->d_state);
     cudaFree(g->d_done);
+    cudaFree(g->d_qhost);
     cudaFree(g->d_hist);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     cudaGetLastError();
@@ -787,7 +870,7 @@ int vate_group_step_graph(vate_group *g, const vate_pair *d_pairs, const uint64_
     uint64_t key[16] = {(uint64_t)d_pairs, (uint64_t)d_pair_offsets, pair_capacity, (uint64_t)d_hosts,
                         (uint64_t)d_host_offsets, host_capacity, (uint64_t)d_kprime, (uint64_t)d_out,
                         (uint64_t)d_flags, ((uint64_t)t.census_tile_chunks << 32) | t.blocks_per_sm,
-                        ((uint64_t)t.gather_tile_hosts << 32) | t.ingest_tile_pairs,
+                        ((uint64_t)t.gather_grab_hosts << 32) | t.ingest_tile_pairs,
                         ((uint64_t)t.wave_pool_mib << 32) | t.preserve_tile_chunks,
                         g->spin_limit, g->missing, (uint64_t)g->trace, g->trace_cap};
     if (!g->exec || memcmp(key, g->graph_key, sizeof key) != 0) {
@@ -883,30 +966,39 @@ int vate_group_autotune(vate_group *g, const vate_pair *d_pairs, const uint64_t 
     };
     vate_group_tuning best = g->tuning;
     float bt = 1e30f;
+    // the candidates, each timed as the best of three replays
+    std::vector<vate_group_tuning> cand;
     for (uint32_t bps = 2; bps <= (uint32_t)std::min(g->max_blocks_per_sm, 4); bps++)
-        for (uint32_t wv : {0u, 32u, 64u})
+        for (uint32_t wv : {0u, 32u})
             for (uint32_t ct : {4096u, 16384u})
-                for (uint32_t gt : {256u, 1024u}) {
-                    g->tuning.blocks_per_sm = bps;
-                    g->tuning.wave_pool_mib = wv;
-                    g->tuning.census_tile_chunks = ct;
-                    g->tuning.gather_tile_hosts = gt;
-                    float ms_best = 1e30f;
-                    for (int r = 0; r < 3; r++) {
-                        cudaEventRecord(e0, st);
-                        cudaError_t e = replay();
-                        cudaEventRecord(e1, st);
-                        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                        if (e != cudaSuccess) return done(vate::set_error(VATE_ECUDA, cudaGetErrorString(e)));
-                        float ms = 0;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        ms_best = std::min(ms_best, ms);
+                for (uint32_t gr : {2u, 4u, 8u})
+                    for (uint32_t it : {4096u, 16384u, 65536u}) {
+                        vate_group_tuning t = entry;
+                        t.blocks_per_sm = bps;
+                        t.wave_pool_mib = wv;
+                        t.census_tile_chunks = ct;
+                        t.gather_grab_hosts = gr;
+                        t.ingest_tile_pairs = it;
+                        cand.push_back(t);
                     }
-                    if (ms_best < bt) {
-                        bt = ms_best;
-                        best = g->tuning;
-                    }
-                }
+    for (const vate_group_tuning &t : cand) {
+        g->tuning = t;
+        float ms_best = 1e30f;
+        for (int r = 0; r < 3; r++) {
+            cudaEventRecord(e0, st);
+            cudaError_t e = replay();
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) return done(vate::set_error(VATE_ECUDA, cudaGetErrorString(e)));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms_best = std::min(ms_best, ms);
+        }
+        if (ms_best < bt) {
+            bt = ms_best;
+            best = t;
+        }
+    }
     g->tuning = best;
     cudaError_t e = replay();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -49,7 +49,7 @@ class vate_info(C.Structure):
 
 class vate_group_tuning(C.Structure):
     _fields_ = [("census_tile_chunks", C.c_uint32), ("blocks_per_sm", C.c_uint32),
-                ("gather_tile_hosts", C.c_uint32), ("ingest_tile_pairs", C.c_uint32),
+                ("gather_grab_hosts", C.c_uint32), ("ingest_tile_pairs", C.c_uint32),
                 ("preserve_tile_chunks", C.c_uint32), ("wave_pool_mib", C.c_uint32)]
 
     def as_dict(self):

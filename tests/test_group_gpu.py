@@ -216,7 +216,7 @@ def test_group_tuning_is_checked(V):
     t = V.vate_group_get_tuning(grp.g)
     assert t.blocks_per_sm >= 1 and t.census_tile_chunks >= 256
     for field, bad in (("blocks_per_sm", 0), ("blocks_per_sm", 99), ("census_tile_chunks", 3000),
-                       ("gather_tile_hosts", 100), ("ingest_tile_pairs", 70000), ("preserve_tile_chunks", 0),
+                       ("gather_grab_hosts", 33), ("ingest_tile_pairs", 70000), ("preserve_tile_chunks", 0),
                        ("wave_pool_mib", 70000)):
         u = V.vate_group_tuning.from_buffer_copy(t)
         setattr(u, field, bad)
