@@ -550,7 +550,7 @@ def run_learned(V, torch):
     evaluated against the closed form on 100 held-out slices of another seed;
     at 32-AT segments (the configuration of the learned estimator) and at the
     2-AT segments of the 40 Gb/s workload; plus the close-time cost of the
-    fused learned estimate for 2^20 hosts at each."""
+    learned estimate (vate_estimate_learned) for 2^20 hosts at each."""
     from paper_1812_00282_b300 import learned
     from traffic import LINK40G, DeviceTraffic, Traffic
     out = {}
@@ -940,16 +940,20 @@ def run_serving(args):
     from paper_1812_00282_b300 import learned, serving
     torch.cuda.set_device(0)
     lr = learned.run(V, seg_len=serving.SEG_LEN, train_slices=60, eval_slices=20)   # the served monitors' placement
-    model = lr.pop("params")
+    model = lr.pop("params") if lr["accepted"] else None   # a model that fails its acceptance is not served
     paced = serving.run(V, duration=5.0, paced=True, model=model)
     flood = serving.run(V, duration=5.0, paced=False, model=model)
+    # the same paced workload with the monitors at the 40 Gb/s workload's 2-AT segments (closed form)
+    paced2 = serving.run(V, duration=5.0, paced=True, model=None, seg_len=2)
     return {"metric": METRIC, "value": flood["mpkts"], "unit": "Mpkt/s", "n_gpus": 1, "steps": 1, "warmup": 0,
             "ms_per_step": round(flood["wall_s"] * 1e3, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": "serving loop: candidate monitors (pools 2^24..2^31, k=10, g=4096) admitted by an "
                                    "8 GB AT budget up to 16, Poisson batches 1k-1M pairs, mean 8 Mpkt/s, bursts to "
                                    "30 Mpkt/s, 1 s slices, learned estimator with closed-form fallback"},
-            "paced": paced, "flood": flood, "model_mre": lr["mre"]}
+            "seg_len": serving.SEG_LEN, "paced": paced, "flood": flood, "model_mre": lr["mre"],
+            "model_accepted": lr["accepted"],
+            "paced_seg_len_2": {kk: paced2[kk] for kk in ("mpkts", "offered_mpkts", "stats")}}
 
 
 def run_pt(args):
@@ -1043,7 +1047,7 @@ def run_learned_kernels(args):
     ms = {"age_counts": timed(lambda: V.vate_age_counts(h.h, hosts, ages)),
           "features": timed(lambda: V.vate_features(h.h, hosts, x)),
           "forward": timed(lambda: V.vate_mlp_forward(params, n_in, x.view(n, n_in), y)),
-          "fused_learned_estimate": timed(lambda: V.vate_estimate_learned(h.h, hosts, params, out, fl)),
+          "learned_estimate": timed(lambda: V.vate_estimate_learned(h.h, hosts, params, out, fl)),
           "plain_eq11_estimate": timed(lambda: h.estimate(hosts, k, out, fl))}
     h.close()
     # per-age counts with a longer window, k = 30 (shared-memory counters instead of bit planes)

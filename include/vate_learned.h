@@ -91,9 +91,15 @@ int vate_mlp_train_step(float *d_params, float *d_m, float *d_v, uint32_t n_in, 
                         void *stream);
 
 /* Learned estimate of |OP(aip, t-k+1, k)| for n hosts at the end of the
- * closed slice, in one gather per host (features, MLP, gate and the Eq. 11
- * fallback fused), by the output rule above.  d_flags also carries
- * VATE_FLAG_SAT / VATE_FLAG_POOLFULL of the closed form. */
+ * closed slice, in one gather per host, by the output rule above.  d_flags
+ * also carries VATE_FLAG_SAT / VATE_FLAG_POOLFULL of the closed form.  For
+ * seg_len >= 16 features, MLP, gate and the Eq. 11 fallback run fused in one
+ * kernel; for seg_len <= 8 (where the host's g / seg_len segment reads bound
+ * the close) the features and Eq. 11 of up to 2^17 hosts at a time go to a
+ * device scratch of the handle, then the model runs over those rows -- the
+ * results are the same bit for bit.  That scratch (2^17 (2k + 3) floats, at
+ * most 17.3 MB) is allocated on the first such call and kept until
+ * vate_destroy.  Errors: VATE_ENOMEM if it cannot be allocated. */
 int vate_estimate_learned(vate_handle *h, const uint32_t *d_aips, uint64_t n, const float *d_params, float *d_out,
                           uint8_t *d_flags, void *stream);
 

@@ -144,6 +144,9 @@ struct vate_handle {
     uint32_t *d_stage[2] = {nullptr, nullptr};   // hosts in
     float *d_stage_out[2] = {nullptr, nullptr};  // estimates out
     uint8_t *d_stage_flags[2] = {nullptr, nullptr};
+    // device scratch of other translation units (the learned estimator's feature rows), on first use
+    void *d_scratch = nullptr;
+    uint64_t scratch_bytes = 0;
 };
 
 namespace vate {
@@ -159,6 +162,24 @@ int handle_view(const vate_handle *h, HandleView *v) {
     v->hist = h->d_hist;
     v->closed = h->closed;
     v->sms = h->sms;
+    return VATE_OK;
+}
+
+int handle_scratch(vate_handle *h, uint64_t bytes, void **ptr) {
+    if (h->scratch_bytes < bytes) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(VATE_ENOMEM, "out of device memory for a scratch of %llu bytes", (unsigned long long)bytes);
+        }
+        if (h->d_scratch) {
+            cudaDeviceSynchronize();           // work queued on the old scratch ends first
+            cudaFree(h->d_scratch);
+        }
+        h->d_scratch = p;
+        h->scratch_bytes = bytes;
+    }
+    *ptr = h->d_scratch;
     return VATE_OK;
 }
 }  // namespace vate
@@ -425,6 +446,7 @@ int vate_destroy(vate_handle *h) {
     cudaFree(h->d_acc);
     cudaFree(h->d_ticket);
     cudaFree(h->d_dbg);
+    cudaFree(h->d_scratch);
     for (int i = 0; i < 2; i++) {
         cudaFree(h->d_stage[i]);
         cudaFree(h->d_stage_out[i]);

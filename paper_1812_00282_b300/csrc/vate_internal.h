@@ -27,6 +27,9 @@ struct vate_handle;
 namespace vate {
 int handle_view(const vate_handle *h, HandleView *v);
 int set_error(int code, const char *msg);
+// A device scratch of at least `bytes` owned by the handle: allocated on the
+// first request (and grown if a later one is larger), freed by vate_destroy.
+int handle_scratch(vate_handle *h, uint64_t bytes, void **ptr);
 
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms);
 cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, uint64_t n, cudaStream_t st, int sms);

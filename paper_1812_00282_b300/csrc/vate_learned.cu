@@ -18,6 +18,8 @@ namespace {
 constexpr int HID = VATE_MLP_HIDDEN;     // 64
 constexpr int MAX_IN = 32;               // 2k + 2 with k <= 15
 constexpr int WARPS = 8;                 // warps per block in the per-host kernels
+constexpr uint32_t SPLIT_MAX_L = 8;      // vate_estimate_learned: features, then the model, for L <= 8
+constexpr uint64_t SPLIT_CHUNK = 1ull << 17;   // hosts per features + model pass (scratch: 2^17 (n_in + 1) floats)
 constexpr int TR_ROWS = 64;              // rows per training tile
 constexpr int TR_THREADS = 256;
 
@@ -127,9 +129,12 @@ __device__ __forceinline__ uint64_t inactive_for_k(const uint64_t *hist, uint64_
     return P - act;
 }
 
+// Warp per host: the host's feature row into x, and, where plain / pflags are
+// not NULL, its Eq. 11 estimate and the closed form's flags.
 __global__ void __launch_bounds__(WARPS * 32) features_kernel(Geom G, uint32_t bact0, const uint64_t *__restrict__ hist,
                                                               const uint32_t *__restrict__ aips, uint64_t n,
-                                                              float *__restrict__ x) {
+                                                              float *__restrict__ x, float *__restrict__ plain,
+                                                              uint8_t *__restrict__ pflags) {
     __shared__ float xs[WARPS][MAX_IN];
     __shared__ uint64_t sN0;
     if (threadIdx.x == 0) sN0 = inactive_for_k(hist, G.P, G.k);
@@ -138,10 +143,12 @@ __global__ void __launch_bounds__(WARPS * 32) features_kernel(Geom G, uint32_t b
     const uint32_t n_in = 2 * G.k + 2;
     for (uint64_t h = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; h < n;
          h += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
-        uint8_t f;
+        uint8_t f = 0;
         uint32_t A;
-        host_features(G, bact0, hist, sN0, aips[h], lane, xs[warp], f, A);
+        const float p = host_features(G, bact0, hist, sN0, aips[h], lane, xs[warp], f, A);
         if (lane < n_in) x[h * n_in + lane] = xs[warp][lane];
+        if (lane == 0 && plain) plain[h] = p;
+        if (lane == 0 && pflags) pflags[h] = f;
         __syncwarp();
     }
 }
@@ -243,10 +250,13 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_forward_kernel(const float *__
 // The output rule on feature rows (lane per row, as mlp_forward_kernel): a
 // row has no active VAT when its first k features (the per-age counts / g)
 // are all 0, k = (n_in - 2) / 2.
+// Lane per row: the output rule.  or_flags = 1: the rule's bits are added to
+// the flags already in `flags` (the closed form's, written by features_kernel).
 __global__ void __launch_bounds__(WARPS * 32) mlp_apply_kernel(const float *__restrict__ params, uint32_t n_in,
                                                                const float *__restrict__ x,
                                                                const float *__restrict__ plain, uint64_t n,
-                                                               float *__restrict__ out, uint8_t *__restrict__ flags) {
+                                                               float *__restrict__ out, uint8_t *__restrict__ flags,
+                                                               uint32_t or_flags) {
     extern __shared__ float4 dyn4[];
     float *prm = reinterpret_cast<float *>(dyn4);
     float *w2t = stage_model(prm, params, n_in);
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_apply_kernel(const float *__re
             bool no_active = true;
             for (uint32_t d = 0; d < k; d++) no_active = no_active && xr[d] == 0.0f;
             const float y = mlp_eval_lane(prm, w2t, n_in, xr);
-            uint8_t f = 0;
+            uint8_t f = (or_flags && flags) ? flags[r0 + lane] : (uint8_t)0;
             out[r0 + lane] = learned_rule(plain[r0 + lane], no_active, y, xr[n_in - 1], prm[layout(n_in).gate], f);
             if (flags) flags[r0 + lane] = f;
         }
@@ -442,7 +452,7 @@ int vate_features(vate_handle *h, const uint32_t *d_aips, uint64_t n, float *d_x
     if (n == 0) return VATE_OK;
     int grid = (int)std::min<uint64_t>((n + WARPS - 1) / WARPS, (uint64_t)v.sms * 16);
     cudaError_t e = launch_pool(v.G, features_kernel, grid, WARPS * 32, 0, (cudaStream_t)stream, v.G, v.bact0, v.hist,
-                                d_aips, n, d_x);
+                                d_aips, n, d_x, (float *)nullptr, (uint8_t *)nullptr);
     return e == cudaSuccess ? VATE_OK : set_error(VATE_ECUDA, cudaGetErrorString(e));
 }
 
@@ -505,7 +515,8 @@ int vate_mlp_apply(const float *d_params, uint32_t n_in, const float *d_x, const
     if (cudaError_t e = cudaFuncSetAttribute(mlp_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
         return set_error(VATE_ECUDA, cudaGetErrorString(e));
     int grid = (int)std::min<uint64_t>((n + WARPS * 32 - 1) / (WARPS * 32), (uint64_t)sms_now() * 8);
-    mlp_apply_kernel<<<grid, WARPS * 32, smem, (cudaStream_t)stream>>>(d_params, n_in, d_x, d_plain, n, d_out, d_flags);
+    mlp_apply_kernel<<<grid, WARPS * 32, smem, (cudaStream_t)stream>>>(d_params, n_in, d_x, d_plain, n, d_out, d_flags,
+                                                                       0u);
     count_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VATE_OK : set_error(VATE_ECUDA, cudaGetErrorString(e));
@@ -518,12 +529,39 @@ int vate_estimate_learned(vate_handle *h, const uint32_t *d_aips, uint64_t n, co
     if (!d_params) return set_error(VATE_EINVAL, "d_params must not be NULL");
     if (n && (!d_aips || !d_out)) return set_error(VATE_EINVAL, "d_aips and d_out must not be NULL");
     if (n == 0) return VATE_OK;
-    const size_t smem = sizeof(float) * (model_smem_floats(2 * v.G.k + 2) + (size_t)WARPS * 32 * XS);
+    const uint32_t n_in = 2 * v.G.k + 2;
+    const size_t smem = sizeof(float) * (model_smem_floats(n_in) + (size_t)WARPS * 32 * XS);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (v.G.L <= SPLIT_MAX_L) {
+        // Segments of at most 8 ATs: the reads of the host's g / L segments bound the close, and the
+        // features kernel, free of the model's registers, keeps enough of them in flight to run at
+        // the random-sector rate; the model then runs over the rows (same values, same order: the
+        // results equal the fused kernel's bit for bit).
+        void *scr = nullptr;
+        const uint64_t chunk = std::min<uint64_t>(n, SPLIT_CHUNK);
+        if (int rc = handle_scratch(h, chunk * (n_in + 1) * sizeof(float), &scr)) return rc;
+        float *x = static_cast<float *>(scr), *plain = x + chunk * n_in;
+        if (cudaError_t e = cudaFuncSetAttribute(mlp_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+            return set_error(VATE_ECUDA, cudaGetErrorString(e));
+        for (uint64_t h0 = 0; h0 < n; h0 += chunk) {
+            const uint64_t m = std::min(chunk, n - h0);
+            const int fgrid = (int)std::min<uint64_t>((m + WARPS - 1) / WARPS, (uint64_t)v.sms * 16);
+            cudaError_t e = launch_pool(v.G, features_kernel, fgrid, WARPS * 32, 0, st, v.G, v.bact0, v.hist,
+                                        d_aips + h0, m, x, plain, d_flags ? d_flags + h0 : (uint8_t *)nullptr);
+            if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+            const int agrid = (int)std::min<uint64_t>((m + WARPS * 32 - 1) / (WARPS * 32), (uint64_t)v.sms * 8);
+            mlp_apply_kernel<<<agrid, WARPS * 32, smem, st>>>(d_params, n_in, x, plain, m, d_out + h0,
+                                                              d_flags ? d_flags + h0 : (uint8_t *)nullptr, 1u);
+            count_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+        }
+        return VATE_OK;
+    }
     if (cudaError_t e = cudaFuncSetAttribute(learned_estimate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem))
         return set_error(VATE_ECUDA, cudaGetErrorString(e));
     int grid = (int)std::min<uint64_t>((n + WARPS * 32 - 1) / (WARPS * 32), (uint64_t)v.sms * 8);
-    cudaError_t e = launch_pool(v.G, learned_estimate_kernel, grid, WARPS * 32, smem, (cudaStream_t)stream, v.G,
+    cudaError_t e = launch_pool(v.G, learned_estimate_kernel, grid, WARPS * 32, smem, st, v.G,
                                 v.bact0, v.hist, d_aips, n, d_params, d_out, d_flags);
     return e == cudaSuccess ? VATE_OK : set_error(VATE_ECUDA, cudaGetErrorString(e));
 }

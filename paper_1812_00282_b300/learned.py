@@ -1,14 +1,16 @@
 """Training and evaluation of the learned estimator (include/vate_learned.h).
 
-The model's arithmetic -- features, forward pass, gradient, Adam, the fused
+The model's arithmetic -- features, forward pass, gradient, Adam, the
 estimate with its closed-form fallback -- runs in the library's kernels; this
 module only moves data: it drives a VATE handle through generated slices,
 labels sampled hosts with their exact window cardinality (distinct (aip, bip)
 keys of the last k slices, by sort-unique on the device), feeds batches to
 vate_mlp_train_step, and on held-out slices takes the estimates that
 vate_estimate_learned -- the kernel that serves closes -- returns.  The closed
-form of Eq. 11 is kept as the yardstick: a model whose mean relative error on
-held-out slices is worse than the closed form's is not accepted.
+form of Eq. 11 is kept as the yardstick: a model is accepted when its mean
+relative error on held-out slices is no worse than the closed form's over all
+active hosts and within 5 % of it over hosts with at least 100 peers (where
+the closed form is already near the pool's noise floor).
 """
 from __future__ import annotations
 
@@ -45,7 +47,7 @@ def collect(V, dev_traffic, c, k, g, seg_len, seed, first_slice, n_slices, hosts
     """Run one handle over n_slices generated slices and, after `warm` slices,
     sample hosts active in the window: features, targets (log1p(n) -
     log1p(max(closed form, 0))) / 8, closed-form estimates, exact counts and,
-    when `params` is given, the fused learned estimates of vate_estimate_learned
+    when `params` is given, the learned estimates of vate_estimate_learned
     (device tensors, one row per sampled host; None without params).
     `large_share` of each slice's sample is drawn from hosts with at least
     `large_from` peers (training only; evaluation samples uniformly)."""
@@ -198,7 +200,7 @@ def run(V, spec=None, c=24, k=10, g=4096, seg_len=32, train_slices=200, eval_sli
     t2 = time.time()
     spec_eval = TrafficSpec(**{**spec.__dict__, "seed": spec.seed + 0x4E})
     tr_eval = DeviceTraffic(Traffic(spec_eval))
-    # held-out slices: the estimates come from the fused kernel that serves closes
+    # held-out slices: the estimates come from vate_estimate_learned, which serves closes
     _, _, Pe, Ne, Le = collect(V, tr_eval, c, k, g, seg_len, seed + 1, 0, eval_slices + k, eval_hosts_per_slice,
                                params=params)
     res = {}
@@ -206,10 +208,12 @@ def run(V, spec=None, c=24, k=10, g=4096, seg_len=32, train_slices=200, eval_sli
         ml, cnt = mean_rel_err(Le, Ne, lo)
         mp, _ = mean_rel_err(Pe, Ne, lo)
         res["n>=%d" % lo] = {"learned": round(ml, 5), "plain": round(mp, 5), "hosts": cnt}
-    accepted = res["n>=1"]["learned"] <= res["n>=1"]["plain"]
-    return {"mre": res, "accepted": bool(accepted), "train_rows": int(T.numel()), "eval_rows": int(Ne.numel()),
+    accepted = (res["n>=1"]["learned"] <= res["n>=1"]["plain"]
+                and res["n>=100"]["learned"] <= 1.05 * res["n>=100"]["plain"])
+    return {"mre": res, "accepted": bool(accepted),
+            "acceptance": "no worse than the closed form over n >= 1, within 5 % of it over n >= 100", "train_rows": int(T.numel()), "eval_rows": int(Ne.numel()),
             "train_slices": train_slices, "eval_slices": eval_slices, "log2_pool": c, "k": k, "g": g,
-            "learned_from": "vate_estimate_learned (the fused kernel that serves closes)",
+            "learned_from": "vate_estimate_learned (what serves closes)",
             "gate": gate, "gate_on_training_rows": gate_train,
             "gate_chosen_on": "the training rows: no worse than the closed form over n >= 1 and n >= 100, then the "
                               "smallest error over n >= 1",

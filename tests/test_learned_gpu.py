@@ -6,9 +6,9 @@ reference of the model (oracle/mlp.py) and the oracle's features:
   - one training step: gradient and loss within FP32 tolerance, Adam update
     recomputed from the returned gradient;
   - training is bit-reproducible;
-  - the fused estimate (vate_estimate_learned, the kernel that serves
-    closes) against the oracle's output rule (oracle/mlp.py estimate) fed
-    with the oracle's own features: flags bit-exact (FALLBACK included),
+  - the learned estimate (vate_estimate_learned, which serves closes: one
+    fused kernel for L >= 16, two passes for L <= 8) against the oracle's
+    output rule (oracle/mlp.py estimate) fed with the oracle's own features: flags bit-exact (FALLBACK included),
     fallback rows within the Eq. 11 tolerance, the others within the bound
     derived from the kernel's FP32 arithmetic (tests/learned_tol.py) -- on
     the small traffic (every host, a ragged count, hosts never seen) and at
@@ -248,6 +248,38 @@ def test_fused_estimate_matches_oracle_small(V, L, scenario):
         if scenario == "sparse":
             assert nfb > len(hosts) // 4
         print("L=%d %s: max rel err %.3g, %.4f of rows within 1e-5, %d fallbacks" % (L, scenario, rel, share, nfb))
+    d.close()
+
+
+@pytest.mark.parametrize("L", [1, 2, 32])
+def test_two_pass_form_equals_vate_estimate_learned(V, L):
+    # vate_estimate_learned fuses features and model in one kernel for
+    # L >= 16 and runs them in two passes through a scratch for L <= 8.  The
+    # public two-pass form -- vate_features, Eq. 11 from vate_estimate,
+    # vate_mlp_apply -- must give the same values bit for bit on either
+    # placement, and the same FALLBACK / GATED bits (vate_mlp_apply reports
+    # only those), with a trained model whose gate takes part.
+    tr, d, o = small_run(V, L=L, k=5, c=16, g=512, slices=8)
+    rng = np.random.default_rng(23)
+    absent = rng.integers(1, 1 << 32, 29, dtype=np.uint64).astype(np.uint32)
+    hosts = as_i32(np.concatenate([tr.aips, absent[~np.isin(absent, tr.aips)]]))
+    n, n_in = hosts.numel(), 12
+    params = labelled_params(V, d, tr.aips, tr, list(range(8)), 5)
+    plain = torch.empty(n, dtype=torch.float32, device="cuda")
+    d.estimate(hosts, 5, plain)
+    params[-1] = float(torch.quantile(plain.double().clamp(min=0), 0.8)) + 0.5
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+    V.vate_estimate_learned(d.h, hosts, params, out, fl)
+    x = torch.empty(n * n_in, dtype=torch.float32, device="cuda")
+    V.vate_features(d.h, hosts, x)
+    out2 = torch.empty_like(out)
+    fl2 = torch.empty_like(fl)
+    V.vate_mlp_apply(params, n_in, x, plain, out2, fl2)
+    assert torch.equal(out.view(torch.int32), out2.view(torch.int32))
+    rule = V.VATE_FLAG_FALLBACK | V.VATE_FLAG_GATED
+    assert torch.equal(fl & rule, fl2)
+    assert ((fl2 & V.VATE_FLAG_GATED) != 0).any() and (fl2 == 0).any()
     d.close()
 
 

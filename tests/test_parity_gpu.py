@@ -317,10 +317,11 @@ def test_host_staging_ring_wraps_and_back_to_back_steps(V):
 
 
 @pytest.mark.slow
-def test_full_size_40g_shape_sampled(V):
-    # The 40 Gb/s workload at full size -- 2^26-AT pool, g = 4096, L = 32,
-    # k = 10, 5M pairs per slice -- through the same entry points and launch
-    # configuration as the benchmark.  The whole pool and census are compared
+@pytest.mark.parametrize("L", [2, 32])
+def test_full_size_40g_shape_sampled(V, L):
+    # The 40 Gb/s workload at full size -- 2^26-AT pool, g = 4096, L = 2 (the
+    # benchmark's placement) and 32, k = 10, 5M pairs per slice -- through the
+    # same entry points and launch configuration as the benchmark.  The whole pool and census are compared
     # every slice; estimates, active counts and per-age counts every fifth
     # slice on a seeded sample of hosts plus every super-spreader (the oracle
     # computes them one by one).
@@ -329,22 +330,23 @@ def test_full_size_40g_shape_sampled(V):
     hosts = mixed_hosts(tr, 2048)
     k = 10
     slices = [tr.slice_pairs(s) for s in range(4 * k + 2)]
-    run_stream(V, (26, k, 4096, 32, 0, 0xC2), slices, hosts, kps=(1, k), check_every=5, check_ages=True,
+    run_stream(V, (26, k, 4096, L, 0, 0xC2), slices, hosts, kps=(1, k), check_every=5, check_ages=True,
                pool_every_slice=True)
 
 
 @pytest.mark.slow
-def test_full_size_every_host_in_one_launch_sampled(V):
+@pytest.mark.parametrize("L", [2, 32])
+def test_full_size_every_host_in_one_launch_sampled(V, L):
     # The benchmark's launch configuration: all 2^20 hosts of the 40 Gb/s
     # workload estimated by one vate_estimate call (so the gather runs on its
     # full grid), in host-table order, with flags, after 5M-pair slices into
-    # the 2^26-AT pool.  The oracle computes a seeded sample of the outputs
+    # the 2^26-AT pool, at the benchmark's L = 2 and at L = 32.  The oracle computes a seeded sample of the outputs
     # plus every super-spreader one by one; 2k + 3 slices take every block's
     # ACT through a full cycle.
     tr = Traffic(LINK40G)
     k, n = 10, tr.spec.n_aips
-    d = V.Vate(26, k, 4096, 32, 0, 0xC2)
-    o = Oracle(c=26, k=k, g=4096, seg_len=32, partition=0, seed=0xC2)
+    d = V.Vate(26, k, 4096, L, 0, 0xC2, options=V.VATE_OPT_PERSIST_L2)
+    o = Oracle(c=26, k=k, g=4096, seg_len=L, partition=0, seed=0xC2)
     dh = dev_u32(tr.aips)
     rng = np.random.default_rng(11)
     idx = np.union1d(rng.choice(n, 4096, replace=False), tr.super_hosts)
