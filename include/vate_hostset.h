@@ -1,0 +1,86 @@
+/*
+ * vate_hostset.h -- the close of a fixed list of hosts through a prebuilt
+ * index of their VAT positions.
+ *
+ * A host's virtual vector is fixed: VAT i of host aip always sits at pool
+ * position H(aip, i) (Sec. 4.1), whatever the traffic.  A monitor that
+ * estimates the same hosts at every close (every host of a link, say) can
+ * therefore sort the positions of all their VATs once, by pool region, and
+ * at each close compute the same counts A (Algorithm 1 over each host's g
+ * VATs) region by region:
+ *   1. the pool's CheckAT bitmap for k' -- one bit per AT, set when the AT is
+ *      active (Eq. 5 distance below k'), 2^c / 8 bytes -- in one pass over the
+ *      pool;
+ *   2. for every region of the bitmap that fits in one SM's shared memory
+ *      (1.5 M ATs), the region is loaded into shared memory and the index
+ *      entries of every host's VATs in that region are streamed from HBM,
+ *      each looked up in shared memory; a host's count is the sum over the
+ *      regions;
+ *   3. Eq. 11 from the counts and the census (vate_estimate_from_counts).
+ * The counts are the same integers the per-host gather computes, so the
+ * estimates and flags equal vate_estimate's bit for bit.  The gather reads
+ * g / L random 32-byte sectors per host, and for segments of at most 8 ATs
+ * its speed is set by the SMs' random-sector rate; the index is read in
+ * order instead, at HBM streaming rate, and the random lookups go to shared
+ * memory.  The index holds one 4-byte entry per segment of every host (g / L
+ * per host, each host's entries of a region padded to a multiple of four),
+ * about 4 n g / L bytes: 16 GiB for 2^20 hosts with g = 4096 and L = 1.
+ *
+ * Conventions are those of vate.h.  A hostset belongs to the handle it was
+ * built for and to the device that was current then.
+ */
+#ifndef VATE_HOSTSET_H
+#define VATE_HOSTSET_H
+
+#include <stdint.h>
+#include "vate.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vate_hostset vate_hostset;
+
+/* Build the index of the n hosts d_aips (device uint32[n], any order,
+ * repeats allowed) for the pool of handle h: their positions depend only on
+ * the handle's parameters, so the handle's state (slice, pool contents) does
+ * not matter and the index stays valid for the handle's whole life.  Needs a
+ * handle of byte ATs (k <= 63, at_bits 0 or 8) over the whole pool, seg_len
+ * 1, 2, 4 or 8, and at most 2^32 - 1 hosts.  Device memory: the index (about
+ * 4 n g / seg_len bytes), 4 (n + 1) bytes per region of offsets, the bitmap
+ * (2^c / 8 bytes) and 4 n bytes of counts; vate_hostset_bytes reports the
+ * total.  Synchronises `stream`.  Errors: VATE_EINVAL (handle, parameters,
+ * NULL pointers), VATE_ENOMEM, VATE_ECUDA. */
+int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *stream, vate_hostset **out);
+
+/* Free everything of the hostset (after its queued work).  NULL is accepted. */
+int vate_hostset_destroy(vate_hostset *s);
+
+/* Device bytes held by the hostset, and its number of hosts and regions. */
+int vate_hostset_info(const vate_hostset *s, uint64_t *bytes, uint64_t *n_hosts, uint32_t *regions);
+
+/* The estimates of Eq. 11 for window kprime (1 <= kprime <= k) of the
+ * hostset's hosts, in their order, at the end of the closed slice: the same
+ * values and flags as vate_estimate(h, d_aips, n, kprime, d_out, d_flags) for
+ * the list the hostset was built from.
+ *   d_out     device float[n]; d_flags device uint8[n] or NULL;
+ *   d_active  device uint32[n] or NULL: the counts A as vate_active_counts.
+ * Asynchronous on `stream`; calls on one hostset must not overlap on the GPU
+ * (they share its bitmap and counts).  Errors: VATE_EINVAL (another handle's
+ * hostset, kprime), VATE_ESLICE (slice not closed), VATE_ECUDA. */
+int vate_estimate_hostset(vate_handle *h, vate_hostset *s, uint32_t kprime, float *d_out, uint8_t *d_flags,
+                          uint32_t *d_active, void *stream);
+
+/* vate_estimate_hostset with the results in host memory: h_out (float[n])
+ * and h_flags (uint8[n], may be NULL) are written by copies queued on
+ * `stream` after the kernels (page-locked buffers make them asynchronous;
+ * the caller synchronises `stream` before reading).  The device side goes
+ * through buffers of the hostset (5 n bytes, allocated on the first call).
+ * Errors: as vate_estimate_hostset, and VATE_ENOMEM. */
+int vate_estimate_hostset_host(vate_handle *h, vate_hostset *s, uint32_t kprime, float *h_out, uint8_t *h_flags,
+                               void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VATE_HOSTSET_H */

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libvate.so")
 SOURCES = ["vate_api.cu", "vate_kernels.cu", "vate_packed.cu", "vate_noalloc.cu", "vate_group.cu", "vate_learned.cu",
-           "vate_server.cu"]
+           "vate_server.cu", "vate_hostset.cu"]
 PROBE_LIB = os.path.join(HERE, "libvate_probe.so")   # memory-system probes for the benchmark (include/vate_probe.h)
 DEBUG_LIB = os.path.join(HERE, "libvate_debug.so")   # the checked build: the same sources with VATE_DEBUG
 PROBE_SOURCES = ["vate_probe.cu"]

@@ -150,6 +150,11 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
         "vate_debug_checks": (i, []),
         "vate_debug_status": (i, [vp, P(u32), P(u64), i, vp]),
         "vate_debug_poke": (i, [vp, u64, u32, vp]),
+        "vate_hostset_create": (i, [vp, vp, u64, vp, P(vp)]),
+        "vate_hostset_destroy": (i, [vp]),
+        "vate_hostset_info": (i, [vp, P(u64), P(u64), P(u32)]),
+        "vate_estimate_hostset": (i, [vp, vp, u32, vp, vp, vp, vp]),
+        "vate_estimate_hostset_host": (i, [vp, vp, u32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -690,6 +695,48 @@ def vate_server_get_stats(s, reset: bool = False) -> vate_server_stats:
 def vate_server_inject(s, kind: int, mon: int = 0, count: int = 0, ms: int = 0) -> None:
     """Host-side fault injection in the serving loop (include/vate_server.h)."""
     _check(_lib.vate_server_inject(s, C.byref(vate_server_fault(kind, mon, count, ms))))
+
+
+def vate_hostset_create(h, aips, stream=None) -> C.c_void_p:
+    """The index of the hosts `aips` for handle h (include/vate_hostset.h)."""
+    import torch
+    pa = _dev(aips, aips.dtype if aips.dtype in (torch.int32, torch.uint32) else torch.int32, "aips")
+    s = C.c_void_p()
+    _check(_lib.vate_hostset_create(h, pa, aips.numel(), _stream(stream), C.byref(s)))
+    return s
+
+
+def vate_hostset_destroy(s) -> None:
+    _check(_lib.vate_hostset_destroy(s))
+
+
+def vate_hostset_info(s):
+    """(device bytes, hosts, regions) of a hostset."""
+    b, n, r = C.c_uint64(), C.c_uint64(), C.c_uint32()
+    _check(_lib.vate_hostset_info(s, C.byref(b), C.byref(n), C.byref(r)))
+    return int(b.value), int(n.value), int(r.value)
+
+
+def vate_estimate_hostset(h, s, kprime: int, out, flags=None, active=None, stream=None) -> None:
+    """vate_estimate for the hostset's hosts, through its index (include/vate_hostset.h)."""
+    import torch
+    n = vate_hostset_info(s)[1]
+    po = _dev(out, torch.float32, "out", n)
+    pf = _dev(flags, torch.uint8, "flags", n) if flags is not None else None
+    pc = _dev(active, active.dtype if active.dtype in (torch.int32, torch.uint32) else torch.int32, "active", n) \
+        if active is not None else None
+    _check(_lib.vate_estimate_hostset(h, s, kprime, po, pf, pc, _stream(stream)))
+
+
+def vate_estimate_hostset_host(h, s, kprime: int, out, flags=None, stream=None) -> None:
+    """vate_estimate_hostset into host tensors (page-locked for asynchronous copies)."""
+    import torch
+    n = vate_hostset_info(s)[1]
+    for t, dt, name in ((out, torch.float32, "out"), (flags, torch.uint8, "flags")):
+        if t is not None and (t.is_cuda or t.dtype != dt or not t.is_contiguous() or t.numel() < n):
+            raise ValueError("%s must be a contiguous host %s tensor of at least %d elements" % (name, dt, n))
+    _check(_lib.vate_estimate_hostset_host(h, s, kprime, out.data_ptr(),
+                                           flags.data_ptr() if flags is not None else None, _stream(stream)))
 
 
 def vate_create_shard(params: vate_params, pid_lo: int, pid_hi: int, stream=None) -> C.c_void_p:
