@@ -51,6 +51,12 @@ def workload_name(args, n_h):
             "4,096 ({}-AT segments), Zipf(1.05), 0.1% super-spreaders".format(n_h, args.pkts, args.k, args.seg_len))
 
 
+def use_index(args) -> bool:
+    """The close goes through the host list's index (vate_hostset) when asked
+    and the pool is one the index serves: byte ATs, segments of 1 to 8 ATs."""
+    return args.close == "index" and args.seg_len in (1, 2, 4, 8) and not args.at_bits and args.k <= 63
+
+
 def make_config(args, n_h, world):
     """The `config` of both arms' JSON lines (the same dict in each)."""
     from traffic import MEAN_PKT_BYTES
@@ -72,9 +78,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=295)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--seg-len", type=int, default=2,
-                    help="VATs per pool segment: 2 is the smallest that meets the 10 ms close target at 2^20 "
-                         "hosts (1 is the paper's random H; 32 is 14x faster at 2.4x the error, --workload placement)")
+    ap.add_argument("--close", default="index", choices=["index", "gather"],
+                    help="index: the estimates of the fixed host list through its prebuilt index of VAT positions "
+                         "(vate_hostset, seg_len 1-8); gather: the per-host gather (vate_estimate)")
+    ap.add_argument("--seg-len", type=int, default=1,
+                    help="VATs per pool segment: 1 is the paper's random H (the default; with --close index its "
+                         "close of 2^20 hosts takes ~4.4 ms); with --close gather 2 is the smallest L that meets the "
+                         "10 ms close target (--workload placement)")
     ap.add_argument("--partition", type=int, default=0)
     ap.add_argument("--k", type=int, default=K_WIN,
                     help="window in slices (the 40 Gb/s workload uses 10; the paper's long window is 300)")
@@ -226,7 +236,7 @@ def traffic_sha() -> str:
     """Checksum of the code (comments aside) of the sources a committed ncu
     traffic figure depends on."""
     h = hashlib.sha256()
-    for f in ("vate_kernels.cu", "vate_device.cuh", "vate_device_ops.cuh"):
+    for f in ("vate_kernels.cu", "vate_device.cuh", "vate_device_ops.cuh", "vate_hostset.cu"):
         with open(os.path.join(ROOT, "paper_1812_00282_b300", "csrc", f), encoding="utf-8") as fh:
             h.update(code_of(fh.read()).encode())
     return h.hexdigest()[:16]
@@ -347,7 +357,7 @@ def accuracy_at_closes(torch, V, dt, hosts, args, first_slice, n_closes=3):
     return res
 
 
-def close_latency_loop(torch, mon, dt, hosts, out, flags, k, first_slice, flush, no_flush, n=200):
+def close_latency_loop(torch, mon, dt, estimate, first_slice, n_hosts, flush, no_flush, n=200):
     """Slice-close latency over n closes in a loop of their own (independent of
     --steps): each close follows the ingest of a fresh slice (generated and
     ingested before the close's events, L2 flushed before the ingest) and is
@@ -363,15 +373,15 @@ def close_latency_loop(torch, mon, dt, hosts, out, flags, k, first_slice, flush,
         mon.ingest(p, s)
         e0[i].record()
         mon.close_slice(s)
-        mon.estimate(hosts, k, out, flags)
+        estimate()
         e1[i].record()
         del p
     torch.cuda.synchronize()
     ms = [e0[i].elapsed_time(e1[i]) for i in range(n)]
-    return {"closes": n, "hosts": int(hosts.numel()), "p50_ms": round(float(np.percentile(ms, 50)), 4),
+    return {"closes": n, "hosts": int(n_hosts), "p50_ms": round(float(np.percentile(ms, 50)), 4),
             "p99_ms": round(float(np.percentile(ms, 99)), 4), "max_ms": round(max(ms), 4),
             "how": "a loop of its own: every close after a fresh slice's ingest, from the vate_close_slice enqueue "
-                   "to the completion of vate_estimate for every host"}
+                   "to the completion of the estimates of every host"}
 
 
 def run_ours(args, rank, world, local):
@@ -395,11 +405,28 @@ def run_ours(args, rank, world, local):
     peaks = probe_peaks(torch, 1 << C)
     mon = V.Vate(C, args.k, G, args.seg_len, args.partition, seed=0xC2 + rank, at_bits=args.at_bits,
                  options=V.VATE_OPT_PERSIST_L2)
+    index = None
+    if use_index(args):
+        # the host list's index of VAT positions: built once (positions depend only on the
+        # monitor's parameters), outside the timed steps
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
+        hs = V.vate_hostset_create(mon.h, hosts)
+        torch.cuda.synchronize()
+        ib, _, regions = V.vate_hostset_info(hs)
+        index = {"build_s": round(time.perf_counter() - tb, 3), "bytes": ib, "regions": regions,
+                 "entries_bytes": ib - 8 * (regions + 1) - (1 << C) // 8 - 4 * n_h}
+
+        def estimate():
+            V.vate_estimate_hostset(mon.h, hs, args.k, out, flags)
+    else:
+        def estimate():
+            mon.estimate(hosts, args.k, out, flags)
 
     def step(s):
         mon.ingest(pairs[s], s)
         mon.close_slice(s)
-        mon.estimate(hosts, args.k, out, flags)
+        estimate()
 
     for s in range(W):
         if not args.no_flush:
@@ -426,7 +453,7 @@ def run_ours(args, rank, world, local):
         e1[i].record()
         mon.close_slice(s)
         e2[i].record()
-        mon.estimate(hosts, args.k, out, flags)
+        estimate()
         e3[i].record()
     torch.cuda.synchronize()
     barrier(world)
@@ -434,8 +461,7 @@ def run_ours(args, rank, world, local):
     clocks.mark_off()
     launches = V.vate_launch_count() - launches0
     clock_info = clocks.stop()
-    close_loop = close_latency_loop(torch, mon, dt, hosts, out, flags, args.k, W + K, flush, args.no_flush,
-                                    n=max(200, K))
+    close_loop = close_latency_loop(torch, mon, dt, estimate, W + K, n_h, flush, args.no_flush, n=max(200, K))
     accuracy = accuracy_at_closes(torch, V, dt, hosts, args, W + K + max(200, K)) if rank == 0 else None
 
     step_ms = [e0[i].elapsed_time(e3[i]) for i in range(K)]
@@ -460,10 +486,11 @@ def run_ours(args, rank, world, local):
     sectors = n_h * (G // args.seg_len) * seg_sectors
     gkernel = ("gather_seg_kernel" if args.seg_len * atb in (2, 4, 8) else
                "gather_vec_kernel" if args.seg_len * atb >= 16 else "gather_scalar_kernel")
-    # the committed ncu figure is for the default 40 Gb/s workload only
-    default_shape = (args.k == K_WIN and not args.at_bits and args.seg_len == 2 and args.partition == 0
+    # the committed ncu figures are for the 40 Gb/s workload's shape (any L, either close path)
+    default_shape = (args.k == K_WIN and not args.at_bits and args.partition == 0
                      and n_h == 1 << 20 and args.pkts == 5_000_000)
-    traffic = committed_traffic(gkernel) if default_shape else None
+    ekernel = "hs_active_kernel" if index else gkernel
+    traffic = committed_traffic("%s@L%d" % (ekernel, args.seg_len)) if default_shape else None
     ingest_avg = statistics.mean(ingest_ms)
     mp = measured_peaks()
     hbm = mp.get("hbm_gbs", 6400.0)
@@ -479,21 +506,31 @@ def run_ours(args, rank, world, local):
     if args.at_bits:
         roofline_note += "; packed fields: a segment's words may span more sectors than counted here"
 
-    result = {
-        "metric": METRIC, "value": round(value, 3), "unit": "Mpkt/s", "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": round(dev_ms_max / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u%d" % at_width if not args.at_bits else "%d-bit fields in u32 words" % args.at_bits,
-        "data": "synthetic",
-        "config": make_config(args, n_h, world),
-        "close_p50_ms": close_loop["p50_ms"],
-        "close_p99_ms": close_loop["p99_ms"],
-        "close_latency": {**close_loop, "in_timed_steps": {"p50_ms": round(float(np.percentile(close_ms, 50)), 4),
-                                                           "max_ms": round(max(close_ms), 4), "closes": K}},
-        "accuracy": accuracy,
-        "ingest_mpkts": round(args.pkts / ingest_avg / 1e3, 1),
-        "kernels_ms": {"ingest+preserve": round(ingest_avg, 4), "census": round(statistics.mean(census_ms), 4),
-                       "gather+estimate": round(gather_avg, 4)},
-        "roofline": {"bound": "l2_sector_rate", "achieved": round(achieved_sectors, 2),
+    if index:
+        # the index pass streams the index once from HBM (far above L2): its bound is HBM bandwidth.
+        # Timed: the whole estimate call (the pool's CheckAT bitmap, the index pass, Eq. 11).
+        ib = index["entries_bytes"]
+        achieved = ib / gather_avg / 1e6                          # GB/s
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 3), "traffic": traffic, "kernel": "hs_active_kernel",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                    "algorithmic": "the host list's index streamed once per close: %d bytes (one 4-byte entry per "
+                                   "segment of every host, a header per host and pool region, cells padded to "
+                                   "16 bytes); the estimate call's time, which also writes the pool's CheckAT "
+                                   "bitmap (%d bytes) and evaluates Eq. 11" % (ib, (1 << C) // 8),
+                    "vs_gather": {"sectors_equivalent": sectors,
+                                  "equivalent_gsector_s": round(achieved_sectors, 1),
+                                  "sector_probe": round(sector_peak, 2),
+                                  "note": "the per-host gather reads the same VATs as %d random 32-byte sectors, "
+                                          "bound by the SMs' sector rate (the probe); the index pass gives the "
+                                          "same counts at %.2f times that rate"
+                                          % (sectors, achieved_sectors / sector_peak)},
+                    "note": "index built once for the fixed host list in %.3f s (%.2f GB, %d pool regions), outside "
+                            "the timed steps; traffic = DRAM bytes of one launch of the index pass (ncu, "
+                            "profiles/traffic.json), null once the kernel sources change"
+                            % (index["build_s"], index["bytes"] / 1e9, index["regions"])}
+    else:
+        roofline = {"bound": "l2_sector_rate", "achieved": round(achieved_sectors, 2),
                      "peak": round(sector_peak, 2), "unit": "Gsector/s",
                      "frac": round(achieved_sectors / sector_peak, 3), "traffic": traffic, "kernel": gkernel,
                      "peak_source": "random 32-B sector reads from a 64 MiB L2-resident buffer, two threads per "
@@ -507,7 +544,24 @@ def run_ours(args, rank, world, local):
                                 "frac": round(vat_bytes / gather_avg / 1e6 / hbm, 3),
                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured); VAT bytes per launch / "
                                                "launch time"},
-                     "note": roofline_note},
+                     "note": roofline_note}
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mpkt/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(dev_ms_max / K, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u%d" % at_width if not args.at_bits else "%d-bit fields in u32 words" % args.at_bits,
+        "data": "synthetic",
+        "config": make_config(args, n_h, world),
+        "close_p50_ms": close_loop["p50_ms"],
+        "close_p99_ms": close_loop["p99_ms"],
+        "close_latency": {**close_loop, "in_timed_steps": {"p50_ms": round(float(np.percentile(close_ms, 50)), 4),
+                                                           "max_ms": round(max(close_ms), 4), "closes": K}},
+        "accuracy": accuracy,
+        "ingest_mpkts": round(args.pkts / ingest_avg / 1e3, 1),
+        "close_path": ("index (vate_estimate_hostset)" if index else "gather (vate_estimate)"),
+        "kernels_ms": {"ingest+preserve": round(ingest_avg, 4), "census": round(statistics.mean(census_ms), 4),
+                       "estimate": round(gather_avg, 4)},
+        "roofline": roofline,
         "roofline_ingest": {"bound": "l2_random_store", "achieved": round(args.pkts / ingest_avg / 1e6, 2),
                             "peak": round(peaks["l2_byte_store_gps"], 2), "unit": "Gstore/s",
                             "frac": round(args.pkts / ingest_avg / 1e6 / peaks["l2_byte_store_gps"], 3),
@@ -531,6 +585,9 @@ def run_ours(args, rank, world, local):
         "wall_bracket_s": round(t1 - t0, 4),
         "device": props.name,
     }
+    if index:
+        V.vate_hostset_destroy(hs)
+        result["index"] = index
     mon.close()
     del pairs
     torch.cuda.empty_cache()
@@ -600,11 +657,18 @@ def run_e2e(args, V, torch, tr, dt, rank, world):
     mon = V.Vate(C, args.k, G, args.seg_len, args.partition, seed=0xE2E + rank, at_bits=args.at_bits,
                  options=V.VATE_OPT_PERSIST_L2)
     st = torch.cuda.current_stream()
+    hs = V.vate_hostset_create(mon.h, dt.hosts()[: args.aips].contiguous()) if use_index(args) else None
+
+    def estimate_host(o, f):
+        if hs is not None:                 # the fixed host list is in the index: only the results cross PCIe
+            V.vate_estimate_hostset_host(mon.h, hs, args.k, o, f)
+        else:
+            V.vate_estimate_host(mon.h, hosts, args.k, o.numpy(), f.numpy())
 
     def step(s):
         V.vate_ingest_host(mon.h, host_pairs[s % nbuf], s)
         mon.close_slice(s)
-        V.vate_estimate_host(mon.h, hosts, args.k, out.numpy(), fl.numpy())
+        estimate_host(out, fl)
         st.synchronize()
 
     for s in range(W):
@@ -624,9 +688,11 @@ def run_e2e(args, V, torch, tr, dt, rank, world):
         o, f = outs[s & 1]
         V.vate_ingest_host(mon.h, host_pairs[s % nbuf], s)
         mon.close_slice(s)
-        V.vate_estimate_host(mon.h, hosts, args.k, o.numpy(), f.numpy())
+        estimate_host(o, f)
     st.synchronize()
     t3 = time.perf_counter()
+    if hs is not None:
+        V.vate_hostset_destroy(hs)
     mon.close()
     # the ceiling of the back-to-back form: the same steps' input copies alone
     # (pairs in 2^20-pair chunks and the host list, from the same pinned
@@ -646,7 +712,8 @@ def run_e2e(args, V, torch, tr, dt, rank, world):
             for j, off in enumerate(range(0, hp.shape[0], chunk)):
                 n = min(chunk, hp.shape[0] - off)
                 d_pairs[j & 1][:n].copy_(hp[off:off + n], non_blocking=True)
-            d_hosts.copy_(hosts, non_blocking=True)
+            if hs is None:
+                d_hosts.copy_(hosts, non_blocking=True)
         with torch.cuda.stream(ds):
             o.copy_(d_out, non_blocking=True)
             f.copy_(d_fl, non_blocking=True)
@@ -656,13 +723,17 @@ def run_e2e(args, V, torch, tr, dt, rank, world):
     el_pipe = max_over_ranks(t3 - t2, world)
     el_copy = max_over_ranks(t5 - t4, world)
     pk = sum_over_ranks(float(E * args.pkts), world)
-    h2d = args.pkts * 8 + hosts.numel() * 4
+    h2d = args.pkts * 8 + (hosts.numel() * 4 if hs is None else 0)
     return {"value": round(pk / el_pipe / 1e6, 3), "unit": "Mpkt/s", "steps": E,
-            "h2d_bytes_per_step": int(args.pkts * 8 + hosts.numel() * 4),
+            "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(hosts.numel() * 5),
-            "path": "vate_ingest_host / vate_close_slice / vate_estimate_host from pinned host memory, every step's "
-                    "pairs and hosts copied in and its estimates and flags copied out; slices issued back to back "
-                    "as a monitor streaming them would, one synchronisation after the last step",
+            "path": ("vate_ingest_host / vate_close_slice / vate_estimate_hostset_host from pinned host memory: every "
+                     "step's pairs copied in and its estimates and flags copied out (the fixed host list lives in "
+                     "the index)" if hs is not None else
+                     "vate_ingest_host / vate_close_slice / vate_estimate_host from pinned host memory, every step's "
+                     "pairs and hosts copied in and its estimates and flags copied out") +
+                    "; slices issued back to back as a monitor streaming them would, one synchronisation after the "
+                    "last step",
             "synchronised": {"value": round(pk / el / 1e6, 3), "unit": "Mpkt/s",
                              "how": "the same calls with the stream synchronised after every step"},
             "copy_only": {"value": round(pk / el_copy / 1e6, 3), "unit": "Mpkt/s",
