@@ -41,7 +41,12 @@ constexpr uint32_t REGION_ATS = 1536u * 1024u;         // one region's bitmap: 1
 constexpr uint32_t REGION_WORDS = REGION_ATS / 32u;
 constexpr uint32_t PAD = REGION_ATS;                    // points at a zero word kept past the region's bitmap
 constexpr uint32_t HDR = 0x80000000u;                   // a cell's first entry: HDR | host index
-constexpr int HB = 4;                                   // slabs of 32 quads a warp has in flight
+// slabs of 32 quads a warp loads before it counts them; measured at 2^20 hosts, 2^26 ATs: 2 slabs 5.04 /
+// 2.70 ms (L = 1 / 2), 4 slabs 4.40 / 2.42 ms, 8 slabs 4.22 / 2.32 ms
+#ifndef VATE_HS_SLABS
+#define VATE_HS_SLABS 8
+#endif
+constexpr int HB = VATE_HS_SLABS;                       // slabs of 32 quads a warp has in flight
 constexpr int HS_THREADS = 1024;                        // hs_active_kernel: one block of 32 warps per SM
 constexpr int BUILD_THREADS = 256;
 constexpr uint32_t MAX_REGIONS = 1024;
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_fill_kernel(Geom G, const ui
 // The active ATs of one segment whose first AT is bit e of the region's bitmap.
 template <int L>
 __device__ __forceinline__ uint32_t seg_count(const uint32_t *bm, uint32_t e) {
-    const uint32_t w = bm[e >> 5] >> (e & 31u);
+    const uint32_t w = __funnelshift_r(bm[e >> 5], 0u, e);      // the word shifted right by e mod 32
     if (L == 1) return w & 1u;
     return __popc(w & ((1u << L) - 1u));
 }
@@ -225,18 +230,22 @@ __global__ void __launch_bounds__(HS_THREADS, 1) hs_active_kernel(const uint32_t
         const uint64_t ws = next_cell(ent, p + len * warp / nw, pe, lane);
         const uint64_t we = next_cell(ent, p + len * (warp + 1) / nw, pe, lane);
         uint32_t carry_h = 0u, carry_s = 0u;             // the cell open at the end of the last slab
-        for (uint64_t q0 = ws; q0 < we; q0 += 32u * HB) {
+        const uint32_t nq = (uint32_t)(we - ws);          // quads of the warp's run (a region holds < 2^30)
+        const uint4 *wp = ent4 + ws;
+        for (uint32_t b0 = 0; b0 < nq; b0 += 32u * HB) {
             uint4 v[HB];
 #pragma unroll
             for (int u = 0; u < HB; u++) {
-                const uint64_t qq = q0 + 32u * u + lane;
-                v[u] = qq < we ? __ldcs(ent4 + qq) : make_uint4(PAD, PAD, PAD, PAD);
+                const uint32_t i = b0 + 32u * u + lane;
+                v[u] = i < nq ? __ldcs(wp + i) : make_uint4(PAD, PAD, PAD, PAD);
             }
 #pragma unroll
             for (int u = 0; u < HB; u++) {
                 const bool head = (v[u].x & HDR) != 0u;
-                const uint32_t val = (head ? 0u : seg_count<L>(bm, v[u].x)) + seg_count<L>(bm, v[u].y) +
-                                     seg_count<L>(bm, v[u].z) + seg_count<L>(bm, v[u].w);
+                // a header is looked up as PAD (the zero word past the bitmap), never as an address
+                const uint32_t x = head ? PAD : v[u].x;
+                const uint32_t val = seg_count<L>(bm, x) + seg_count<L>(bm, v[u].y) + seg_count<L>(bm, v[u].z) +
+                                     seg_count<L>(bm, v[u].w);
                 const uint32_t heads = __ballot_sync(0xFFFFFFFFu, head);
                 if (heads == 0u) {                       // the open cell runs through the slab
                     carry_s += __reduce_add_sync(0xFFFFFFFFu, val);
