@@ -226,3 +226,17 @@ def test_damaged_checkpoint_rejected_on_host(V, damage):
     with pytest.raises(V.VateError) as ei:
         V.vate_restore(img, stream=0)
     assert ei.value.code == V.VATE_EINVAL, V.vate_last_error()
+
+
+def test_hostset_calls_refuse_null_arguments_on_host(V):
+    # include/vate_hostset.h: a NULL handle, hostset or output is refused before any device work
+    lib = V._lib
+    s = ctypes.c_void_p()
+    buf = (ctypes.c_uint32 * 4)()
+    assert lib.vate_hostset_create(None, ctypes.addressof(buf), 4, None, ctypes.byref(s)) == V.VATE_EINVAL
+    assert lib.vate_hostset_create(None, ctypes.addressof(buf), 4, None, None) == V.VATE_EINVAL
+    b, n, r = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint32()
+    assert lib.vate_hostset_info(None, ctypes.byref(b), ctypes.byref(n), ctypes.byref(r)) == V.VATE_EINVAL
+    assert lib.vate_hostset_destroy(None) == V.VATE_OK
+    assert lib.vate_estimate_hostset(None, None, 1, None, None, None, None) == V.VATE_EINVAL
+    assert lib.vate_estimate_hostset_host(None, None, 1, None, None, None) == V.VATE_EINVAL
