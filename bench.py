@@ -232,11 +232,17 @@ def code_of(text: str) -> str:
     return " ".join(text.split())
 
 
-def traffic_sha() -> str:
+TRAFFIC_SOURCES = {                      # the sources each committed ncu traffic figure depends on
+    "hs_active_kernel": ("vate_hostset.cu", "vate_device.cuh"),
+}
+DEFAULT_TRAFFIC_SOURCES = ("vate_kernels.cu", "vate_device.cuh", "vate_device_ops.cuh")
+
+
+def traffic_sha(kernel: str = "") -> str:
     """Checksum of the code (comments aside) of the sources a committed ncu
-    traffic figure depends on."""
+    traffic figure of `kernel` depends on."""
     h = hashlib.sha256()
-    for f in ("vate_kernels.cu", "vate_device.cuh", "vate_device_ops.cuh", "vate_hostset.cu"):
+    for f in TRAFFIC_SOURCES.get(kernel.split("@")[0], DEFAULT_TRAFFIC_SOURCES):
         with open(os.path.join(ROOT, "paper_1812_00282_b300", "csrc", f), encoding="utf-8") as fh:
             h.update(code_of(fh.read()).encode())
     return h.hexdigest()[:16]
@@ -250,7 +256,7 @@ def committed_traffic(kernel: str):
     except (OSError, ValueError):
         return None
     e = d.get(kernel)
-    if not e or e.get("source_sha") != traffic_sha():
+    if not e or e.get("source_sha") != traffic_sha(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -605,16 +611,17 @@ def run_learned(V, torch):
     """The learned-estimator workload: the 40 Gb/s traffic on a 2^24-AT pool,
     k = 10, g = 4096; MLP trained on 200 generated slices with exact labels,
     evaluated against the closed form on 100 held-out slices of another seed;
-    at 32-AT segments (the configuration of the learned estimator) and at the
-    2-AT segments of the 40 Gb/s workload; plus the close-time cost of the
-    learned estimate (vate_estimate_learned) for 2^20 hosts at each."""
+    at 32-AT segments (the configuration of the learned estimator), at 2-AT
+    segments and at the paper's placement (L = 1, the 40 Gb/s workload's);
+    plus the close-time cost of the learned estimate (vate_estimate_learned)
+    for 2^20 hosts at each."""
     from paper_1812_00282_b300 import learned
     from traffic import LINK40G, DeviceTraffic, Traffic
     out = {}
     dt = DeviceTraffic(Traffic(LINK40G))
     hosts = dt.hosts()
     est = torch.empty(hosts.numel(), dtype=torch.float32, device="cuda")
-    for L in (32, 2):
+    for L in (32, 2, 1):
         r = learned.run(V, seg_len=L)
         params = r.pop("params")
         # time both estimators on one closed slice of the same configuration

@@ -3,10 +3,12 @@
 //
 // Index.  The pool is cut into regions of REGION_ATS positions (a multiple of
 // every segment length, so no segment straddles two).  For region r and host
-// h of the list, the entries of cell (r, h) are the offsets, within the
-// region, of the first AT of each of h's segments that lie in r (one entry
-// per segment, so a segment met twice by one host counts twice, as in the
-// gather), padded with PAD to a multiple of four so that every cell starts on
+// h of the list, the entries of cell (r, h) locate, in the region's bitmap,
+// the first AT of each of h's segments that lie in r (one entry per segment,
+// so a segment met twice by one host counts twice, as in the gather): the
+// byte offset of its 32-bit word shifted left by 5, plus its bit (the form
+// the lookup uses as it is).  A cell opens with a header HDR | h and is
+// padded with PAD to a multiple of four entries, so that every cell starts on
 // a 16-byte boundary.  Cells are stored region-major, host-minor;
 // off[r][h] is the first entry of cell (r, h) relative to the region's first
 // entry rbase[r], and off[r][n] the region's total.  Built in two passes over
@@ -39,7 +41,7 @@ namespace {
 
 constexpr uint32_t REGION_ATS = 1536u * 1024u;         // one region's bitmap: 192 KiB of shared memory
 constexpr uint32_t REGION_WORDS = REGION_ATS / 32u;
-constexpr uint32_t PAD = REGION_ATS;                    // points at a zero word kept past the region's bitmap
+constexpr uint32_t PAD = REGION_WORDS << 7;             // the entry of a zero word kept past the region's bitmap
 constexpr uint32_t HDR = 0x80000000u;                   // a cell's first entry: HDR | host index
 // slabs of 32 quads a warp loads before it counts them; measured at 2^20 hosts, 2^26 ATs: 2 slabs 5.04 /
 // 2.70 ms (L = 1 / 2), 4 slabs 4.40 / 2.42 ms, 8 slabs 4.22 / 2.32 ms
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(1024) hs_scan_kernel(uint32_t *__restrict__ of
 }
 
 // Warp per host: in each region where it has segments, its cell -- the
-// header HDR | h, then each segment's offset within the region, then PAD up
+// header HDR | h, then each segment's entry (its word's byte offset << 5 | its bit), then PAD up
 // to the cell's size.
 __global__ void __launch_bounds__(BUILD_THREADS) hs_fill_kernel(Geom G, const uint32_t *__restrict__ aips, uint64_t n,
                                                                 uint32_t nr, const uint32_t *__restrict__ off,
@@ -146,7 +148,8 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_fill_kernel(Geom G, const ui
             const uint32_t pos = seg_base_k(G, hk, j);
             const uint32_t r = pos / REGION_ATS;
             const uint32_t k = atomicAdd(&wh[r], 1u);
-            entries[rbase[r] + off[(uint64_t)r * (n + 1) + h] + 1u + k] = pos - r * REGION_ATS;
+            const uint32_t o = pos - r * REGION_ATS;                 // the AT's bit in the region's bitmap
+            entries[rbase[r] + off[(uint64_t)r * (n + 1) + h] + 1u + k] = ((o & ~31u) << 2) | (o & 31u);
         }
         __syncwarp();
         for (uint32_t r = lane; r < nr; r += 32u) {
@@ -159,10 +162,11 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_fill_kernel(Geom G, const ui
     }
 }
 
-// The active ATs of one segment whose first AT is bit e of the region's bitmap.
+// The active ATs of the segment of entry e: e >> 5 is the byte offset of its
+// word in the region's bitmap, e mod 32 the bit of its first AT.
 template <int L>
-__device__ __forceinline__ uint32_t seg_count(const uint32_t *bm, uint32_t e) {
-    const uint32_t w = __funnelshift_r(bm[e >> 5], 0u, e);      // the word shifted right by e mod 32
+__device__ __forceinline__ uint32_t seg_count(const unsigned char *bmb, uint32_t e) {
+    const uint32_t w = __funnelshift_r(*reinterpret_cast<const uint32_t *>(bmb + (e >> 5)), 0u, e);
     if (L == 1) return w & 1u;
     return __popc(w & ((1u << L) - 1u));
 }
@@ -194,6 +198,7 @@ __global__ void __launch_bounds__(HS_THREADS, 1) hs_active_kernel(const uint32_t
                                                                   uint32_t *__restrict__ active) {
     extern __shared__ uint4 bm4[];                       // REGION_WORDS words of bitmap, then one zero word (PAD)
     uint32_t *bm = reinterpret_cast<uint32_t *>(bm4);
+    const unsigned char *bmb = reinterpret_cast<const unsigned char *>(bm4);
     const uint32_t *ent = reinterpret_cast<const uint32_t *>(ent4);
     __shared__ unsigned long long s_b[2];
     __shared__ uint32_t s_r;
@@ -244,8 +249,8 @@ __global__ void __launch_bounds__(HS_THREADS, 1) hs_active_kernel(const uint32_t
                 const bool head = (v[u].x & HDR) != 0u;
                 // a header is looked up as PAD (the zero word past the bitmap), never as an address
                 const uint32_t x = head ? PAD : v[u].x;
-                const uint32_t val = seg_count<L>(bm, x) + seg_count<L>(bm, v[u].y) + seg_count<L>(bm, v[u].z) +
-                                     seg_count<L>(bm, v[u].w);
+                const uint32_t val = seg_count<L>(bmb, x) + seg_count<L>(bmb, v[u].y) + seg_count<L>(bmb, v[u].z) +
+                                     seg_count<L>(bmb, v[u].w);
                 const uint32_t heads = __ballot_sync(0xFFFFFFFFu, head);
                 if (heads == 0u) {                       // the open cell runs through the slab
                     carry_s += __reduce_add_sync(0xFFFFFFFFu, val);

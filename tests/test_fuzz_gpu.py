@@ -13,7 +13,8 @@ groups of random size and make-up (one segment length per group), stepped
 plainly or by graph replay, equal a single handle per monitor bit for bit.
 Position shards at random 64-aligned cut points hold the undivided pool
 between them and reduce to its census and estimates.  A handle checkpointed
-after a random slice and restored continues exactly as the original.
+after a random slice and restored continues exactly as the original.  The
+close of a random host list through its index equals the per-host gather.
 The draws are seeded, so a failing case is reproduced by its id.
 """
 import math
@@ -231,3 +232,43 @@ def test_random_checkpoint_resume_continues_exactly(V, case):
             assert torch.equal(e1, e2)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("case", range(16))
+def test_random_hostset_equals_per_host_gather(V, case):
+    # the close of a fixed host list through its index (include/vate_hostset.h)
+    # equals the per-host gather bit for bit, for random byte-AT configurations
+    # with L <= 8 (pools of up to three regions), timestamps or recorders, a
+    # random host list (repeats, hosts never seen) and the drawn slice sequence
+    rng = np.random.default_rng(70_000 + case)
+    params, _, ids, kps, pkts = draw(80_000 + case)
+    c, k, g, L, part, seed = params
+    k = min(k, 63)
+    L = int(rng.choice([1, 2, 4, 8]))
+    g = int(min(L * rng.integers(2, 129), 4096))
+    c = max(c, int(rng.choice([c, 22])))
+    kps = sorted({1, int(rng.integers(1, k + 1)), k})
+    counter = int(rng.integers(0, 2))
+    d = V.Vate(c, k, g, L, part, seed, counter=counter)
+    tr = Traffic(SMALL, pkts_per_slice=pkts)
+    n = int(rng.integers(1, 3000))
+    hosts = rng.choice(tr.aips, n)
+    hosts[: n // 10] = rng.integers(1, 1 << 32, n // 10, dtype=np.uint64).astype(np.uint32)
+    dh = dev_u32(hosts)
+    s = V.vate_hostset_create(d.h, dh)
+    e1 = torch.empty(n, dtype=torch.float32, device="cuda")
+    f1 = torch.empty(n, dtype=torch.uint8, device="cuda")
+    a1 = torch.empty(n, dtype=torch.int32, device="cuda")
+    e2, f2, a2 = torch.empty_like(e1), torch.empty_like(f1), torch.empty_like(a1)
+    for sid in ids:
+        d.ingest(dev_pairs(tr.slice_pairs(sid % 64)), sid)
+        d.close_slice(sid)
+        for kp in kps:
+            d.estimate(dh, kp, e1, f1)
+            V.vate_active_counts(d.h, dh, kp, a1)
+            V.vate_estimate_hostset(d.h, s, kp, e2, f2, a2)
+            assert torch.equal(a1, a2), (case, sid, kp)
+            assert torch.equal(f1, f2), (case, sid, kp)
+            assert torch.equal(e1.view(torch.int32), e2.view(torch.int32)), (case, sid, kp)
+    V.vate_hostset_destroy(s)
+    d.close()
