@@ -27,7 +27,8 @@
  * about 4 n g / L bytes: 16 GiB for 2^20 hosts with g = 4096 and L = 1.
  *
  * Conventions are those of vate.h.  A hostset belongs to the handle it was
- * built for and to the device that was current then.
+ * built for and to the device that was current then; destroy it before that
+ * handle (it keeps the handle's address to refuse other handles).
  */
 #ifndef VATE_HOSTSET_H
 #define VATE_HOSTSET_H
