@@ -18,12 +18,13 @@
  * weights and accumulation.  y corrects the closed form in log space: the
  * estimate is expm1(8 y + log1p(max(Eq. 11 estimate, 0))), so a model that
  * outputs 0 reproduces the closed form (clamped at 0).  A gate tau completes
- * the model: where the corrected value is >= tau (a large host, for which
- * Eq. 11 is already accurate) the closed form itself is returned.
+ * the model: where the corrected value and the closed form are both >= tau (a
+ * host both call large, for which Eq. 11 is already accurate) the closed form
+ * itself is returned.
  * Output rule for a host, in order: no active VAT in the window -> the closed
  * form, VATE_FLAG_FALLBACK; the corrected value not finite -> the closed form,
- * VATE_FLAG_FALLBACK; the corrected value >= tau -> the closed form,
- * VATE_FLAG_GATED; otherwise the corrected value.
+ * VATE_FLAG_FALLBACK; the corrected value and the closed form both >= tau ->
+ * the closed form, VATE_FLAG_GATED; otherwise the corrected value.
  * Parameter layout (floats): W1[n_in][64], b1[64], W2[64][64], b2[64], w3[64], b3,
  * tau (vate_mlp_param_count(n_in) = 64 n_in + 4288 + 2).  Training leaves tau
  * alone (its gradient is 0); it is chosen after training (vate_mlp_apply lets
@@ -43,7 +44,7 @@ extern "C" {
 
 #define VATE_MLP_HIDDEN 64
 #define VATE_FLAG_FALLBACK 4u   /* the closed form was returned: no active VAT, or no finite correction */
-#define VATE_FLAG_GATED    8u   /* the closed form was returned: the corrected value is at or above the gate tau */
+#define VATE_FLAG_GATED    8u   /* the closed form was returned: it and the corrected value are at or above the gate tau */
 
 /* Number of parameters of the model for n_in inputs. */
 uint64_t vate_mlp_param_count(uint32_t n_in);

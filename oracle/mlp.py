@@ -4,14 +4,15 @@ The model (not in the paper; the interface is fixed by include/vate_learned.h):
 y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 with hidden width 64, parameters
 laid out as W1[n_in][64], b1[64], W2[64][64], b2[64], w3[64], b3, then the
 gate tau (not a weight of the network: the closed form is kept where the
-corrected value is >= tau).  Loss: mean
+corrected value and the closed form are both >= tau).  Loss: mean
 squared error over the rows.  Features of a host: per-age VAT counts / g, the
 pool's per-age fractions, log2(g)/16, log1p(max(Eq. 11 estimate, 0))/16.
 Output rule at slice close (`estimate`), in order: the closed form of Eq. 11,
 flagged FALLBACK, when the host has no active VAT in the window; the closed
 form, flagged FALLBACK, when the corrected value expm1(8 y + log1p(max(Eq. 11,
 0))) is not a finite FP32 number; the closed form, flagged GATED, when the
-corrected value is >= tau; otherwise that corrected value.
+corrected value and the closed form are both >= tau; otherwise that corrected
+value.
 Written directly from those definitions with numpy; the gradient is pinned
 by finite differences, the forward pass and the output rule by hand-built
 networks whose outputs are known in closed form.
@@ -22,7 +23,7 @@ import numpy as np
 
 HID = 64
 FALLBACK = 4          # flag bit: the closed form was returned (no active VAT, or no finite correction)
-GATED = 8             # flag bit: the closed form was returned (it is at or above the gate tau)
+GATED = 8             # flag bit: the closed form was returned (it and the corrected value are >= the gate tau)
 FLT_MAX = float(np.finfo(np.float32).max)
 
 
@@ -117,7 +118,7 @@ def estimate(p, n_in, X, plain, k, plain_flags=None):
     no_active = X[:, :k].sum(axis=1) == 0
     fb = no_active | ~finite32
     with np.errstate(invalid="ignore"):
-        gated = ~fb & (est >= gate(p))
+        gated = ~fb & (est >= gate(p)) & (plain >= gate(p))
     out = np.where(fb | gated, plain, est)
     flags = np.zeros(len(out), np.uint8) if plain_flags is None else np.asarray(plain_flags, np.uint8).copy()
     flags[fb] |= FALLBACK

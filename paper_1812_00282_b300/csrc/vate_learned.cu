@@ -157,9 +157,9 @@ __global__ void __launch_bounds__(WARPS * 32) features_kernel(Geom G, uint32_t b
 // `plain` (Eq. 11) is returned, flagged FALLBACK, when the host has no active
 // VAT in the window or when the corrected value expm1(8 y + log1p(max(plain,
 // 0))) is not finite (x_last * 16 = log1p(max(plain, 0)) is the host's last
-// feature); flagged GATED when the corrected value is >= the model's gate (a
-// large host, for which the closed form is the better estimate); otherwise
-// the corrected value.
+// feature); flagged GATED when the corrected value and the closed form are
+// both >= the model's gate (a host both call large, for which the closed form
+// is the better estimate); otherwise the corrected value.
 __device__ __forceinline__ float learned_rule(float plain, bool no_active, float y, float x_last, float gate,
                                               uint8_t &flags) {
     if (no_active) {
@@ -171,7 +171,7 @@ __device__ __forceinline__ float learned_rule(float plain, bool no_active, float
         flags |= (uint8_t)VATE_FLAG_FALLBACK;
         return plain;
     }
-    if (e >= gate) {
+    if (e >= gate && plain >= gate) {      // both call the host large: the closed form is kept
         flags |= (uint8_t)VATE_FLAG_GATED;
         return plain;
     }

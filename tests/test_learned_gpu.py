@@ -155,11 +155,13 @@ def check_fused_against_oracle(V, d, o, hosts, params, out=None, fl=None, idx=No
     p64 = params.cpu().numpy().astype(np.float64)
     est, flags, z = mlp.estimate(p64, n_in, X, plain, k, pflags)
     dev = out.cpu().numpy()[idx].astype(np.float64)
-    # a corrected value within 1e-4 of the gate may fall on either side of it (FP32 on the device)
+    # a corrected value or a closed form within 1e-4 of the gate may fall on either side of it (FP32 on
+    # the device, and the closed form there is within 1e-5 of the oracle's)
     tau = mlp.gate(p64)
     with np.errstate(invalid="ignore", over="ignore"):
         e_all = np.expm1(z)
-        amb = np.isfinite(tau) & (np.abs(e_all - tau) <= 1e-4 * max(abs(tau), 1.0))
+        band = 1e-4 * max(abs(tau), 1.0)
+        amb = np.isfinite(tau) & ((np.abs(e_all - tau) <= band) | (np.abs(plain - tau) <= band))
     assert amb.sum() <= max(2, len(idx) // 100), amb.sum()
     np.testing.assert_array_equal(fl.cpu().numpy()[idx][~amb], flags[~amb],
                                   err_msg="flags (SAT, POOLFULL, FALLBACK, GATED)")
@@ -345,15 +347,19 @@ def test_learned_full_configuration_no_worse_than_eq11(V):
 
 
 @pytest.mark.slow
-def test_learned_at_the_placement_of_the_40gbps_workload(V):
-    # The same workload at 2-AT segments, where the closed form is far better
-    # than at 32 (mean relative error 0.28 instead of 0.61 over n >= 100): the
-    # model still beats it over all hosts active in the window, and stays
-    # within 5 % of it over the hosts with n >= 100 (measured 0.293 vs 0.282;
-    # no gate tau made the model no worse there on the training rows).
+@pytest.mark.parametrize("L", [2, 1])
+def test_learned_at_short_segments_meets_its_acceptance(V, L):
+    # The same workload at 2-AT segments and at the paper's placement (L = 1,
+    # the 40 Gb/s workload's), where the closed form is far better than at 32
+    # (mean relative error 0.28 / 0.25 instead of 0.61 over n >= 100): the
+    # model, with its gate chosen on the training rows, beats it over all
+    # hosts active in the window and stays within 5 % of it over the hosts with
+    # n >= 100 (measured at L = 2, ungated: 5.63 vs 9.31 and 0.293 vs 0.282; at
+    # L = 1, gated at 16: 7.27 vs 8.46 and 0.260 vs 0.254).
     from paper_1812_00282_b300 import learned
-    r = learned.run(V, seg_len=2)
+    r = learned.run(V, seg_len=L)
     m1, m100 = r["mre"]["n>=1"], r["mre"]["n>=100"]
     assert m1["hosts"] > 1000 and m100["hosts"] > 1000
     assert m1["learned"] <= m1["plain"], m1
-    assert m100["learned"] <= 1.05 * m100["plain"], m100
+    assert m100["learned"] <= learned.ACCEPT_LARGE * m100["plain"], m100
+    assert r["accepted"]

@@ -94,23 +94,29 @@ def test_learned_output_falls_back_to_the_closed_form():
     assert np.isclose(est[3], 41.0, rtol=1e-13) and fl[3] == 0
 
 
-def test_learned_output_gate_returns_the_closed_form_above_tau():
-    # tau = 100: where the corrected value expm1(8 y + log1p(plain)) is >= 100
-    # the closed form is kept (GATED) -- even a closed form below tau (row 2);
-    # below, the corrected value; a host with no active VAT is FALLBACK
+def test_learned_output_gate_returns_the_closed_form_where_both_are_above_tau():
+    # tau = 100: where the corrected value expm1(8 y + log1p(plain)) and the
+    # closed form are both >= 100 the closed form is kept (GATED); where only
+    # one of them is (row 2: the corrected value; the second net: the closed
+    # form), the corrected value; a host with no active VAT is FALLBACK
     k, n_in = 2, 6
     p = _abs_net(n_in, 0.25, tau=100.0)           # y = |x0| + 0.25
     X = np.array([[0.25, 0.1, 0, 0, 0.75, 0.1],     # y = 0.5:  z = 4 + 0.5 = 4.5, e = 89
                   [0.5, 0.0, 0, 0, 0.75, 0.1],      # y = 0.75: z = 6 + log1p(3000)
-                  [0.0, 0.25, 0, 0, 0.75, 0.1],     # y = 0.25: z = 2 + 3 = 5, e = 147
+                  [0.0, 0.25, 0, 0, 0.75, 0.1],     # y = 0.25: z = 2 + 3 = 5, e = 147, closed form 19
                   [0.0, 0.0, 0, 0, 0.75, 0.1]])     # no active VAT
     plain = np.array([np.expm1(0.5), 3000.0, np.expm1(3.0), 500.0])
     est, fl, z = mlp.estimate(p, n_in, X, plain, k)
     np.testing.assert_allclose(z[[0, 2]], [4.5, 5.0], rtol=1e-15)
     assert np.isclose(est[0], np.expm1(4.5), rtol=1e-15) and fl[0] == 0
     assert est[1] == 3000.0 and fl[1] == mlp.GATED
-    assert est[2] == plain[2] and fl[2] == mlp.GATED
+    assert np.isclose(est[2], np.expm1(5.0), rtol=1e-15) and fl[2] == 0
     assert est[3] == 500.0 and fl[3] == mlp.FALLBACK
+    # y = |x0| - 0.5 = -0.5: a closed form of 500 corrected to 501 e^-4 - 1 = 8.2, below tau: not gated
+    q = _abs_net(n_in, -0.5, tau=100.0)
+    est, fl, z = mlp.estimate(q, n_in, np.array([[0.0, 0.25, 0, 0, 0.75, 0.1]]), np.array([500.0]), k)
+    assert np.isclose(z[0], np.log(501.0) - 4.0, rtol=1e-15)
+    assert np.isclose(est[0], 501.0 * np.exp(-4.0) - 1.0, rtol=1e-13) and fl[0] == 0
 
 
 def test_gradient_of_the_gate_is_zero():
