@@ -6,8 +6,9 @@ small case.
 
   - every segment length the index serves (L = 1, 2, 4, 8), both partitions,
     timestamps and distance recorders, several k';
-  - pools of one region (2^16 ATs, a partial region) and of several (2^22:
-    three regions, the last partial);
+  - pools of one region (2^16 ATs, a partial region), of several (2^22:
+    three regions, the last partial) and of many (2^30: 683 regions, most
+    of them empty for a single host);
   - host lists with repeats, hosts never seen, and a ragged count;
   - the benchmark's configuration at full size: the 2^26-AT pool, all 2^20
     hosts of the 40 Gb/s traffic, L = 1 and L = 2;
@@ -176,3 +177,24 @@ def test_hostset_refusals(V):
     V.vate_hostset_destroy(s)
     for x in (d, other, wide):
         x.close()
+
+
+@pytest.mark.parametrize("L", [1, 8])
+def test_hostset_many_regions_and_tiny_lists(V, L):
+    # a 2^30-AT pool (683 regions, most of them empty for a short vector), a
+    # single host and a list of 300: cells of one or two segments, empty
+    # regions between them, against the per-host gather
+    c, k, g = 30, 4, 64
+    tr = Traffic(SMALL, pkts_per_slice=8_000)
+    d = V.Vate(c, k, g, L, 0, 77)
+    lists = [tr.aips[:1], tr.aips[:300]]
+    sets = [V.vate_hostset_create(d.h, as_i32(h)) for h in lists]
+    assert V.vate_hostset_info(sets[0])[2] == 683
+    for sl in range(4):
+        d.ingest(as_i32(tr.slice_pairs(sl)), sl)
+        d.close_slice(sl)
+        for h, s in zip(lists, sets):
+            compare(V, d, s, h, k)
+    for s in sets:
+        V.vate_hostset_destroy(s)
+    d.close()
