@@ -233,7 +233,7 @@ def code_of(text: str) -> str:
 
 
 TRAFFIC_SOURCES = {                      # the sources each committed ncu traffic figure depends on
-    "hs_active_kernel": ("vate_hostset.cu", "vate_device.cuh"),
+    "hs_tile_kernel": ("vate_hostset.cu", "vate_device.cuh"),
 }
 DEFAULT_TRAFFIC_SOURCES = ("vate_kernels.cu", "vate_device.cuh", "vate_device_ops.cuh")
 
@@ -421,7 +421,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         ib, _, regions = V.vate_hostset_info(hs)
         index = {"build_s": round(time.perf_counter() - tb, 3), "bytes": ib, "regions": regions,
-                 "entries_bytes": ib - 8 * (regions + 1) - (1 << C) // 8 - 4 * n_h}
+                 "entries_bytes": ib - 4 * (regions + 1) - (1 << C) // 8 - 4 * n_h}
 
         def estimate():
             V.vate_estimate_hostset(mon.h, hs, args.k, out, flags)
@@ -495,7 +495,7 @@ def run_ours(args, rank, world, local):
     # the committed ncu figures are for the 40 Gb/s workload's shape (any L, either close path)
     default_shape = (args.k == K_WIN and not args.at_bits and args.partition == 0
                      and n_h == 1 << 20 and args.pkts == 5_000_000)
-    ekernel = "hs_active_kernel" if index else gkernel
+    ekernel = "hs_tile_kernel" if index else gkernel
     traffic = committed_traffic("%s@L%d" % (ekernel, args.seg_len)) if default_shape else None
     ingest_avg = statistics.mean(ingest_ms)
     mp = measured_peaks()
@@ -518,12 +518,14 @@ def run_ours(args, rank, world, local):
         ib = index["entries_bytes"]
         achieved = ib / gather_avg / 1e6                          # GB/s
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                    "frac": round(achieved / hbm, 3), "traffic": traffic, "kernel": "hs_active_kernel",
+                    "frac": round(achieved / hbm, 3), "traffic": traffic, "kernel": "hs_tile_kernel",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                     "algorithmic": "the host list's index streamed once per close: %d bytes (one 4-byte entry per "
-                                   "segment of every host, a header per host and pool region, cells padded to "
-                                   "16 bytes); the estimate call's time, which also writes the pool's CheckAT "
-                                   "bitmap (%d bytes) and evaluates Eq. 11" % (ib, (1 << C) // 8),
+                                   "segment of every host, %d bytes, in rows of 32-cell tiles whose columns are "
+                                   "padded to the tile's largest cell, a 4-byte host per cell and a 4-byte first "
+                                   "row per tile); the estimate call's time, which also writes the pool's "
+                                   "CheckAT bitmap (%d bytes) and evaluates Eq. 11"
+                                   % (ib, 4 * n_h * (G // args.seg_len), (1 << C) // 8),
                     "vs_gather": {"sectors_equivalent": sectors,
                                   "equivalent_gsector_s": round(achieved_sectors, 1),
                                   "sector_probe": round(sector_peak, 2),

@@ -2,28 +2,33 @@
 // VAT positions (include/vate_hostset.h).
 //
 // Index.  The pool is cut into regions of REGION_ATS positions (a multiple of
-// every segment length, so no segment straddles two).  For region r and host
-// h of the list, the entries of cell (r, h) locate, in the region's bitmap,
-// the first AT of each of h's segments that lie in r (one entry per segment,
-// so a segment met twice by one host counts twice, as in the gather): the
-// byte offset of its 32-bit word shifted left by 5, plus its bit (the form
-// the lookup uses as it is).  A cell opens with a header HDR | h and is
-// padded with PAD to a multiple of four entries, so that every cell starts on
-// a 16-byte boundary.  Cells are stored region-major, host-minor;
-// off[r][h] is the first entry of cell (r, h) relative to the region's first
-// entry rbase[r], and off[r][n] the region's total.  Built in two passes over
-// the hosts' segments (count per cell, then place), with an exclusive scan of
-// the counts between them.
+// every segment length, so no segment straddles two).  Cell (r, h) holds one
+// entry per segment of host h that lies in region r (a segment met twice by
+// one host counts twice, as in the gather): the byte offset of the segment's
+// 32-bit word in the block's shared-memory copy of the region's bitmap,
+// shifted left by 5, plus the bit of its first AT.  The shared-memory copy
+// starts with a zero quad, so the entry 0 looks up a zero word: it pads.
+// The cells of a region are sorted by their number of quads (four entries),
+// largest first, and dealt in that order to tiles of 32 cells.  Tile t holds
+// M_t rows of 32 quads; row i holds quad i of each of the tile's cells, lane j
+// reading cell j's column; M_t is the quads of its first, largest, cell and
+// the rest of every column is 0.  Tiles are stored region-major: rt[r] is the
+// first tile of region r, row0[t] the first row of tile t (row0[T] the number
+// of rows), host[32 t + j] the host of cell j of tile t, NONE for an empty
+// lane of a region's last tile.  Built in passes over the hosts' segments:
+// count per cell, a histogram of cell sizes per region and its scan, the
+// placement of every cell in its region's order, a scan of the tiles' rows,
+// then the entries.
 //
 // Close (per call).  hs_bitmap_kernel writes the pool's CheckAT bitmap for k'
 // (bit p set when AT p is active: the SWAR range test of CheckAT in the frame
-// of block 0, as in the gather).  hs_active_kernel runs one block per SM;
-// block b takes an equal share of the cells, in order, so it meets one or two
-// regions; for each it loads the region's bitmap into shared memory and its
-// warps run through the cells, four at a time (eight lanes each), streaming
-// each cell's entries as 16-byte loads and summing the popcounts of the
-// segments' bits; a cell's sum is added to its host's count.  Eq. 11 then
-// comes from the counts and the census (the kernel of vate_estimate_from_counts).
+// of block 0, as in the gather).  hs_tile_kernel runs one block per SM; block
+// b takes an equal share of the rows (whole tiles, in order), so it meets one
+// or two regions; for each it loads the region's bitmap into shared memory,
+// and each warp streams an equal share of the region's rows: lane j sums the
+// bits its column's entries point at, and at the end of a tile -- the same row
+// for every lane -- adds the sum to its cell's host.  Eq. 11 then comes from
+// the counts and the census (the kernel of vate_estimate_from_counts).
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -39,19 +44,28 @@ using namespace vate;
 
 namespace {
 
-constexpr uint32_t REGION_ATS = 1536u * 1024u;         // one region's bitmap: 192 KiB of shared memory
-constexpr uint32_t REGION_WORDS = REGION_ATS / 32u;
-constexpr uint32_t PAD = REGION_WORDS << 7;             // the entry of a zero word kept past the region's bitmap
-constexpr uint32_t HDR = 0x80000000u;                   // a cell's first entry: HDR | host index
-// slabs of 32 quads a warp loads before it counts them; measured at 2^20 hosts, 2^26 ATs: 2 slabs 5.04 /
-// 2.70 ms (L = 1 / 2), 4 slabs 4.40 / 2.42 ms, 8 slabs 4.22 / 2.32 ms
-#ifndef VATE_HS_SLABS
-#define VATE_HS_SLABS 8
+// A region's bitmap sits in shared memory (REGION_ATS / 8 bytes); the rest of the SM's 256 KB of L1 and shared
+// memory stays L1, which holds the index loads in flight.  Measured at 2^20 hosts, 2^26 ATs, L = 1: see the
+// benchmark notes beside the kernel.
+#ifndef VATE_HS_REGION_KATS
+#define VATE_HS_REGION_KATS 1536
 #endif
-constexpr int HB = VATE_HS_SLABS;                       // slabs of 32 quads a warp has in flight
-constexpr int HS_THREADS = 1024;                        // hs_active_kernel: one block of 32 warps per SM
+constexpr uint32_t REGION_ATS = VATE_HS_REGION_KATS * 1024u;
+constexpr uint32_t REGION_WORDS = REGION_ATS / 32u;
+static_assert(REGION_WORDS % 4u == 0u && REGION_ATS % 8u == 0u, "a region holds whole quads of words and segments");
+constexpr uint32_t BM_SKIP = 16u;                       // bytes of zeros before the bitmap in shared memory
+constexpr uint32_t NONE = 0xFFFFFFFFu;                  // the host of an empty lane
+// rows of 32 quads a warp has in flight
+#ifndef VATE_HS_ROWS
+#define VATE_HS_ROWS 8
+#endif
+constexpr int HB = VATE_HS_ROWS;
+constexpr int HS_THREADS = 1024;                        // hs_tile_kernel: one block of 32 warps per SM
 constexpr int BUILD_THREADS = 256;
 constexpr uint32_t MAX_REGIONS = 1024;
+
+// The entry of pool offset o within its region.
+__host__ __device__ constexpr uint32_t entry_of(uint32_t o) { return (((o & ~31u) >> 3) + BM_SKIP) << 5 | (o & 31u); }
 
 // Thread per 32 ATs: bit (p mod 32) of word p / 32 is set when AT p is active.
 __global__ void __launch_bounds__(256) hs_bitmap_kernel(Geom G, RangeConsts rc, uint32_t c2k, uint64_t words,
@@ -75,11 +89,9 @@ __global__ void __launch_bounds__(256) hs_bitmap_kernel(Geom G, RangeConsts rc, 
     }
 }
 
-// Warp per host: the size of its cell in each region -- a header and one
-// entry per segment, rounded up to a multiple of four; 0 where the host has no
-// segment.
+// Warp per host: cnt[r][h] = the host's segments in region r.
 __global__ void __launch_bounds__(BUILD_THREADS) hs_count_kernel(Geom G, const uint32_t *__restrict__ aips, uint64_t n,
-                                                                 uint32_t nr, uint32_t *__restrict__ off) {
+                                                                 uint32_t nr, uint32_t *__restrict__ cnt) {
     extern __shared__ uint32_t wh_all[];                 // [warps][nr]
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t *wh = wh_all + (size_t)warp * nr;
@@ -91,14 +103,24 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_count_kernel(Geom G, const u
         const uint64_t hk = host_key(G, aips[h]);
         for (uint32_t j = lane; j < nseg; j += 32u) atomicAdd(&wh[seg_base_k(G, hk, j) / REGION_ATS], 1u);
         __syncwarp();
-        for (uint32_t r = lane; r < nr; r += 32u)
-            off[(uint64_t)r * (n + 1) + h] = wh[r] ? (wh[r] + 1u + 3u) & ~3u : 0u;
+        for (uint32_t r = lane; r < nr; r += 32u) cnt[(uint64_t)r * n + h] = wh[r];
         __syncwarp();
     }
 }
 
-// Block per region: off[r][0..n) from cell sizes to exclusive offsets,
-// off[r][n] and total[r] the region's entries (in 64 bits, to catch overflow).
+// Cells by size, per region: qh[r][qm - q] += 1 for a cell of q quads (row r of qh has qm + 1 counters).
+__global__ void __launch_bounds__(BUILD_THREADS) hs_qhist_kernel(const uint32_t *__restrict__ cnt, uint64_t n,
+                                                                 uint32_t qm, uint32_t *__restrict__ qh) {
+    const uint32_t r = blockIdx.y;
+    for (uint64_t h = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t q = (cnt[(uint64_t)r * n + h] + 3u) >> 2;
+        if (q) atomicAdd(&qh[(uint64_t)r * (qm + 1) + (qm - q)], 1u);
+    }
+}
+
+// Block per row of `off` (rows of n counters at a stride of n + 1): the row
+// from counts to exclusive offsets, off[n] and total[row] its sum (in 64
+// bits, to catch overflow).
 __global__ void __launch_bounds__(1024) hs_scan_kernel(uint32_t *__restrict__ off, uint64_t n,
                                                        unsigned long long *__restrict__ total) {
     __shared__ unsigned long long part[1024];
@@ -128,12 +150,35 @@ __global__ void __launch_bounds__(1024) hs_scan_kernel(uint32_t *__restrict__ of
     }
 }
 
-// Warp per host: in each region where it has segments, its cell -- the
-// header HDR | h, then each segment's entry (its word's byte offset << 5 | its bit), then PAD up
-// to the cell's size.
+// Every cell its place: the next slot of its size class in its region's order
+// (qh holds the classes' first slots and advances), so that the cells of a
+// region run from the most quads to the fewest.  Slot s of region r is lane
+// s mod 32 of tile rt[r] + s / 32; the first cell of a tile is its largest and
+// gives the tile's rows.  cnt[r][h] becomes the cell's tile lane 32 t + j.
+__global__ void __launch_bounds__(BUILD_THREADS) hs_place_kernel(uint32_t *__restrict__ cnt, uint64_t n, uint32_t qm,
+                                                                 uint32_t *__restrict__ qh,
+                                                                 const uint32_t *__restrict__ rt,
+                                                                 uint32_t *__restrict__ host,
+                                                                 uint32_t *__restrict__ rows) {
+    const uint32_t r = blockIdx.y;
+    for (uint64_t h = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = (uint64_t)r * n + h;
+        const uint32_t q = (cnt[i] + 3u) >> 2;
+        if (!q) continue;
+        const uint32_t s = atomicAdd(&qh[(uint64_t)r * (qm + 1) + (qm - q)], 1u);
+        const uint32_t tl = rt[r] * 32u + s;
+        host[tl] = (uint32_t)h;
+        if ((s & 31u) == 0u) rows[tl >> 5] = q;
+        cnt[i] = tl;
+    }
+}
+
+// Warp per host: each segment's entry at its slot of the host's cell in its
+// region -- entry k of the cell in lane j = tl mod 32 of tile t = tl / 32 is
+// word k mod 4 of that lane's quad in row row0[t] + k / 4.
 __global__ void __launch_bounds__(BUILD_THREADS) hs_fill_kernel(Geom G, const uint32_t *__restrict__ aips, uint64_t n,
-                                                                uint32_t nr, const uint32_t *__restrict__ off,
-                                                                const unsigned long long *__restrict__ rbase,
+                                                                uint32_t nr, const uint32_t *__restrict__ tlpos,
+                                                                const uint32_t *__restrict__ row0,
                                                                 uint32_t *__restrict__ entries) {
     extern __shared__ uint32_t wh_all[];                 // [warps][nr]: entries placed so far per region
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -148,22 +193,16 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_fill_kernel(Geom G, const ui
             const uint32_t pos = seg_base_k(G, hk, j);
             const uint32_t r = pos / REGION_ATS;
             const uint32_t k = atomicAdd(&wh[r], 1u);
-            const uint32_t o = pos - r * REGION_ATS;                 // the AT's bit in the region's bitmap
-            entries[rbase[r] + off[(uint64_t)r * (n + 1) + h] + 1u + k] = ((o & ~31u) << 2) | (o & 31u);
-        }
-        __syncwarp();
-        for (uint32_t r = lane; r < nr; r += 32u) {
-            if (!wh[r]) continue;
-            const uint64_t cell = rbase[r] + off[(uint64_t)r * (n + 1) + h];
-            entries[cell] = HDR | (uint32_t)h;
-            for (uint32_t k = 1u + wh[r]; k & 3u; k++) entries[cell + k] = PAD;
+            const uint32_t tl = tlpos[(uint64_t)r * n + h];
+            const uint64_t row = (uint64_t)row0[tl >> 5] + (k >> 2);
+            entries[row * 128u + (tl & 31u) * 4u + (k & 3u)] = entry_of(pos - r * REGION_ATS);
         }
         __syncwarp();
     }
 }
 
 // The active ATs of the segment of entry e: e >> 5 is the byte offset of its
-// word in the region's bitmap, e mod 32 the bit of its first AT.
+// word in the shared-memory bitmap, e mod 32 the bit of its first AT.
 template <int L>
 __device__ __forceinline__ uint32_t seg_count(const unsigned char *bmb, uint32_t e) {
     const uint32_t w = __funnelshift_r(*reinterpret_cast<const uint32_t *>(bmb + (e >> 5)), 0u, e);
@@ -171,120 +210,123 @@ __device__ __forceinline__ uint32_t seg_count(const unsigned char *bmb, uint32_t
     return __popc(w & ((1u << L) - 1u));
 }
 
-// The first quad at or after x (below limit) that starts a cell, else limit.
-__device__ __forceinline__ uint64_t next_cell(const uint32_t *__restrict__ ent, uint64_t x, uint64_t limit,
-                                              uint32_t lane) {
-    for (uint64_t q = x; q < limit; q += 32u) {
-        const uint64_t qq = q + lane;
-        const bool head = qq < limit && (__ldcg(ent + 4 * qq) & HDR) != 0u;
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, head);
-        if (m) return q + (uint64_t)(__ffs(m) - 1);
-    }
-    return limit;
+template <int L>
+__device__ __forceinline__ uint32_t quad_count(const unsigned char *bmb, uint4 v) {
+    return seg_count<L>(bmb, v.x) + seg_count<L>(bmb, v.y) + seg_count<L>(bmb, v.z) + seg_count<L>(bmb, v.w);
 }
 
-// The block's share of the index (whole cells), region by region: the
-// region's bitmap into shared memory, then each warp a run of whole cells,
-// read as slabs of 32 quads (one per lane, HB slabs in flight).  A cell
-// starts a quad, so a quad holds at most one header, in its first entry; a
-// lane's quad adds to the cell of the nearest header at or before it, found
-// with a prefix sum over the slab and the ballot of its headers; a cell that
-// runs past the slab carries into the next.
+// The first tile t in [lo, hi] whose first row is at or past x (row0
+// ascending; hi when none below it is): a 32-way search, each lane probing
+// one point per round.  Called by all 32 lanes.
+__device__ __forceinline__ uint32_t tile_at_row(const uint32_t *__restrict__ row0, uint32_t lo, uint32_t hi, uint32_t x,
+                                                uint32_t lane) {
+    while (hi - lo > 31u) {                              // the answer lies in [lo, hi]
+        const uint32_t step = (hi - lo + 31u) >> 5;
+        const uint32_t p = lo + lane * step;
+        const bool past = p >= hi || __ldcg(row0 + p) >= x;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, past);
+        if (m & 1u) return lo;
+        if (m == 0u) {
+            lo += 31u * step;
+        } else {
+            const uint32_t f = __ffs(m) - 1u;
+            hi = min(hi, lo + f * step);
+            lo += (f - 1u) * step;
+        }
+    }
+    const uint32_t p = lo + lane;
+    const bool past = p >= hi || __ldcg(row0 + p) >= x;
+    return lo + (uint32_t)__ffs(__ballot_sync(0xFFFFFFFFu, past)) - 1u;
+}
+
+// The block's share of the rows (whole tiles), region by region: the region's
+// bitmap into shared memory, then each warp an equal share of the region's
+// rows (whole tiles), HB rows of 32 quads in flight, lane j summing column j.
+// A tile's rows end at the same row for every lane, where each lane adds its
+// sum to its cell's host; the next tile's first row and hosts are loaded one
+// tile ahead.
 template <int L>
-__global__ void __launch_bounds__(HS_THREADS, 1) hs_active_kernel(const uint32_t *__restrict__ bitmap, uint64_t bm_words,
-                                                                  uint32_t nr,
-                                                                  const unsigned long long *__restrict__ rbase,
-                                                                  const uint4 *__restrict__ ent4, uint64_t quads,
-                                                                  uint32_t *__restrict__ active) {
-    extern __shared__ uint4 bm4[];                       // REGION_WORDS words of bitmap, then one zero word (PAD)
-    uint32_t *bm = reinterpret_cast<uint32_t *>(bm4);
+__global__ void __launch_bounds__(HS_THREADS, 1) hs_tile_kernel(const uint32_t *__restrict__ bitmap, uint64_t bm_words,
+                                                                uint32_t nr, const uint32_t *__restrict__ rt,
+                                                                const uint32_t *__restrict__ row0,
+                                                                const uint32_t *__restrict__ hosts,
+                                                                const uint4 *__restrict__ ent4, uint32_t T, uint32_t R,
+                                                                uint32_t *__restrict__ active) {
+    extern __shared__ uint4 bm4[];                       // a zero quad, then REGION_WORDS words of bitmap
+    uint32_t *bm = reinterpret_cast<uint32_t *>(bm4 + 1);
     const unsigned char *bmb = reinterpret_cast<const unsigned char *>(bm4);
-    const uint32_t *ent = reinterpret_cast<const uint32_t *>(ent4);
-    __shared__ unsigned long long s_b[2];
+    __shared__ uint32_t s_t[2];
     __shared__ uint32_t s_r;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nw = blockDim.x >> 5;
-    if (tid == 0) bm[REGION_WORDS] = 0u;
+    if (tid == 0) bm4[0] = make_uint4(0u, 0u, 0u, 0u);
     if (warp < 2) {
-        const uint64_t a = quads * (blockIdx.x + warp) / gridDim.x;
-        const uint64_t b = next_cell(ent, a, quads, lane);
-        if (lane == 0) s_b[warp] = b;
+        const uint32_t x = (uint32_t)((uint64_t)R * (blockIdx.x + warp) / gridDim.x);
+        const uint32_t t = tile_at_row(row0, 0u, T, x, lane);
+        if (lane == 0) s_t[warp] = t;
     }
     __syncthreads();
-    const uint64_t b0 = s_b[0], b1 = s_b[1];
-    for (uint64_t p = b0; p < b1;) {
-        if (tid == 0) {                                  // the region holding quad p
+    const uint32_t ta = s_t[0], tb = s_t[1];
+    for (uint32_t t0 = ta; t0 < tb;) {
+        if (tid == 0) {                                  // the region holding tile t0
             uint32_t lo = 0, hi = nr;
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if ((rbase[mid] >> 2) <= p) lo = mid;
+                if (rt[mid] <= t0) lo = mid;
                 else hi = mid;
             }
             s_r = lo;
         }
         __syncthreads();                                 // also: the previous region's lookups are done
         const uint32_t r = s_r;
-        const uint64_t pe = min(b1, (uint64_t)(rbase[r + 1] >> 2));
+        const uint32_t t1 = min(tb, rt[r + 1]);
         const uint64_t w0 = (uint64_t)r * REGION_WORDS, left = bm_words - w0;
         const uint32_t nwords = left < (uint64_t)REGION_WORDS ? (uint32_t)left : REGION_WORDS;
         const uint4 *src = reinterpret_cast<const uint4 *>(bitmap + w0);   // w0 is a multiple of 4 words
-        for (uint32_t i = tid; i < nwords / 4u; i += blockDim.x) bm4[i] = __ldcg(src + i);
+        for (uint32_t i = tid; i < nwords / 4u; i += blockDim.x) bm4[1 + i] = __ldcg(src + i);
         for (uint32_t i = (nwords & ~3u) + tid; i < nwords; i += blockDim.x) bm[i] = __ldcg(bitmap + w0 + i);
         __syncthreads();
-        const uint64_t len = pe - p;
-        const uint64_t ws = next_cell(ent, p + len * warp / nw, pe, lane);
-        const uint64_t we = next_cell(ent, p + len * (warp + 1) / nw, pe, lane);
-        uint32_t carry_h = 0u, carry_s = 0u;             // the cell open at the end of the last slab
-        const uint32_t nq = (uint32_t)(we - ws);          // quads of the warp's run (a region holds < 2^30)
-        const uint4 *wp = ent4 + ws;
-        for (uint32_t b0 = 0; b0 < nq; b0 += 32u * HB) {
-            uint4 v[HB];
+        const uint32_t xa = __ldcg(row0 + t0), xb = __ldcg(row0 + t1);
+        const uint32_t wa = tile_at_row(row0, t0, t1, xa + (uint32_t)((uint64_t)(xb - xa) * warp / nw), lane);
+        const uint32_t wb = tile_at_row(row0, t0, t1, xa + (uint32_t)((uint64_t)(xb - xa) * (warp + 1u) / nw), lane);
+        if (wa < wb) {
+            const uint32_t rowA = __ldcg(row0 + wa), rowB = __ldcg(row0 + wb);
+            uint32_t t = wa;
+            uint32_t end = __ldcg(row0 + t + 1u);         // first row past tile t
+            uint32_t host = __ldcg(hosts + (uint64_t)t * 32u + lane);
+            const bool more = t + 1u < wb;
+            uint32_t end2 = more ? __ldcg(row0 + t + 2u) : rowB;
+            uint32_t host2 = more ? __ldcg(hosts + (uint64_t)(t + 1u) * 32u + lane) : NONE;
+            uint32_t sum = 0;
+            for (uint32_t row = rowA; row < rowB; row += HB) {
+                const uint4 *rp = ent4 + (uint64_t)row * 32u + lane;
+                uint4 v[HB];
 #pragma unroll
-            for (int u = 0; u < HB; u++) {
-                const uint32_t i = b0 + 32u * u + lane;
-                v[u] = i < nq ? __ldcs(wp + i) : make_uint4(PAD, PAD, PAD, PAD);
+                for (int u = 0; u < HB; u++)
+                    v[u] = row + u < rowB ? __ldcs(rp + 32u * u) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int u = 0; u < HB; u++) {
+                    if (row + u >= rowB) break;
+                    if (row + u == end) {                // tile t ends here, for every lane
+                        if (host != NONE && sum) atomicAdd(active + host, sum);
+                        sum = 0;
+                        t++;
+                        end = end2;
+                        host = host2;
+                        if (t + 1u < wb) {
+                            end2 = __ldcg(row0 + t + 2u);
+                            host2 = __ldcg(hosts + (uint64_t)(t + 1u) * 32u + lane);
+                        } else {
+                            end2 = rowB;
+                            host2 = NONE;
+                        }
+                    }
+                    sum += quad_count<L>(bmb, v[u]);
+                }
             }
-#pragma unroll
-            for (int u = 0; u < HB; u++) {
-                const bool head = (v[u].x & HDR) != 0u;
-                // a header is looked up as PAD (the zero word past the bitmap), never as an address
-                const uint32_t x = head ? PAD : v[u].x;
-                const uint32_t val = seg_count<L>(bmb, x) + seg_count<L>(bmb, v[u].y) + seg_count<L>(bmb, v[u].z) +
-                                     seg_count<L>(bmb, v[u].w);
-                const uint32_t heads = __ballot_sync(0xFFFFFFFFu, head);
-                if (heads == 0u) {                       // the open cell runs through the slab
-                    carry_s += __reduce_add_sync(0xFFFFFFFFu, val);
-                    continue;
-                }
-                // the open cell ends before the first header: its part in this slab is the sum below it
-                const uint32_t first = __ffs(heads) - 1u;
-                const uint32_t head_sum = __reduce_add_sync(0xFFFFFFFFu, lane < first ? val : 0u);
-                if (lane == 0 && carry_s + head_sum) atomicAdd(active + carry_h, carry_s + head_sum);
-                if ((heads & (heads - 1u)) == 0u) {      // one header: the cell it starts stays open
-                    carry_h = __shfl_sync(0xFFFFFFFFu, v[u].x & ~HDR, first);
-                    carry_s = __reduce_add_sync(0xFFFFFFFFu, lane >= first ? val : 0u);
-                    continue;
-                }
-                // several headers: the cells between them close here, the last one stays open
-                uint32_t P = val;                        // inclusive prefix sum over the slab
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, P, d);
-                    if (lane >= (uint32_t)d) P += y;
-                }
-                const uint32_t upto = heads & (0xFFFFFFFFu >> (31u - lane));   // headers at or below this lane
-                const uint32_t hl = upto ? 31u - __clz(upto) : 0u;             // the lane of the nearest one
-                const uint32_t before = __shfl_sync(0xFFFFFFFFu, P, (hl + 31u) & 31u);
-                const uint32_t host = __shfl_sync(0xFFFFFFFFu, v[u].x & ~HDR, hl);
-                const uint32_t sum = hl ? P - before : P;
-                // lanes from the first header on: a cell that ends here (the next lane starts one) adds its sum
-                if (upto && lane < 31u && ((heads >> (lane + 1u)) & 1u) && sum) atomicAdd(active + host, sum);
-                carry_h = __shfl_sync(0xFFFFFFFFu, host, 31);
-                carry_s = __shfl_sync(0xFFFFFFFFu, sum, 31);
-            }
+            if (host != NONE && sum) atomicAdd(active + host, sum);
         }
-        if (lane == 0 && ws < we && carry_s) atomicAdd(active + carry_h, carry_s);
-        p = pe;
+        t0 = t1;
     }
 }
 
@@ -303,10 +345,13 @@ struct vate_hostset {
     uint64_t n = 0;
     uint32_t nr = 0;
     uint32_t L = 1;
-    uint64_t entries = 0;                  // index entries (with padding)
+    uint32_t T = 0;                        // tiles
+    uint32_t R = 0;                        // rows of 32 quads
     uint64_t bm_words = 0;
-    uint32_t *d_entries = nullptr;
-    unsigned long long *d_rbase = nullptr; // [nr + 1]
+    uint32_t *d_entries = nullptr;         // [R][32][4]
+    uint32_t *d_rt = nullptr;              // [nr + 1]: first tile of each region
+    uint32_t *d_row0 = nullptr;            // [T + 1]: first row of each tile
+    uint32_t *d_host = nullptr;            // [T][32]: host of each cell, NONE for an empty lane
     uint32_t *d_bitmap = nullptr;
     uint32_t *d_active = nullptr;          // [n]
     float *d_out = nullptr;                // [n], vate_estimate_hostset_host (on first use)
@@ -319,7 +364,9 @@ namespace {
 void free_hostset(vate_hostset *s) {
     if (!s) return;
     cudaFree(s->d_entries);
-    cudaFree(s->d_rbase);
+    cudaFree(s->d_rt);
+    cudaFree(s->d_row0);
+    cudaFree(s->d_host);
     cudaFree(s->d_bitmap);
     cudaFree(s->d_active);
     cudaFree(s->d_out);
@@ -330,14 +377,28 @@ void free_hostset(vate_hostset *s) {
 
 void *kernel_for(uint32_t L) {
     switch (L) {
-    case 1: return (void *)hs_active_kernel<1>;
-    case 2: return (void *)hs_active_kernel<2>;
-    case 4: return (void *)hs_active_kernel<4>;
-    default: return (void *)hs_active_kernel<8>;
+    case 1: return (void *)hs_tile_kernel<1>;
+    case 2: return (void *)hs_tile_kernel<2>;
+    case 4: return (void *)hs_tile_kernel<4>;
+    default: return (void *)hs_tile_kernel<8>;
     }
 }
 
-constexpr size_t ACTIVE_SMEM = (size_t)REGION_WORDS * 4 + 16;
+constexpr size_t TILE_SMEM = (size_t)REGION_WORDS * 4 + BM_SKIP;
+
+// Shared memory for the region's bitmap and no more: the carveout (in percent
+// of the SM's shared memory) that holds one block, so that the rest stays L1.
+int tile_carveout() {
+#ifdef VATE_HS_CARVEOUT
+    return VATE_HS_CARVEOUT;
+#endif
+    int dev = 0, smem_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess || smem_sm <= 0)
+        return 100;
+    const size_t need = TILE_SMEM + 64 + 1024;          // dynamic, static and the block's reserved kilobyte
+    return (int)std::min<size_t>(100, (need * 100 + smem_sm - 1) / smem_sm);
+}
 
 }  // namespace
 
@@ -350,13 +411,14 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
     if (int rc = handle_view(h, &v)) return rc;
     const Geom &G = v.G;
     if (n == 0 || !d_aips) return set_error(VATE_EINVAL, "a hostset needs at least one host (d_aips not NULL)");
-    if (n >= HDR) return set_error(VATE_EINVAL, "at most 2^31 - 1 hosts");
+    if (n >= 0x80000000ull) return set_error(VATE_EINVAL, "at most 2^31 - 1 hosts");
     if (G.atw != 1u || G.packed || (G.counter == VATE_COUNTER_AT && !G.frame0))
         return set_error(VATE_EINVAL, "a hostset needs a pool of byte ATs (k <= 63)");
     if (G.lo != 0 || G.hi != G.P) return set_error(VATE_EINVAL, "a hostset needs the whole pool, not a shard");
     if (G.L != 1 && G.L != 2 && G.L != 4 && G.L != 8) return set_error(VATE_EINVAL, "a hostset needs seg_len 1, 2, 4 or 8");
     const uint32_t nr = (uint32_t)((G.P + REGION_ATS - 1) / REGION_ATS);
     if (nr > MAX_REGIONS) return set_error(VATE_EINVAL, "pool too large for a hostset (more than 1024 regions)");
+    const uint32_t qm = ((G.g >> G.log2L) + 3u) / 4u;   // the most quads a cell can have
     cudaStream_t st = (cudaStream_t)stream;
     vate_hostset *s = new (std::nothrow) vate_hostset();
     if (!s) return set_error(VATE_ENOMEM, "host allocation failed");
@@ -367,74 +429,101 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
     s->nr = nr;
     s->L = G.L;
     s->bm_words = G.P / 32u;
-    const size_t off_words = (size_t)nr * (n + 1);
+    // build-only buffers: cnt[r][h] (segments per cell, then the cell's tile lane), qh[r][qm + 1] (cells by size,
+    // then each size's next slot), total[] (sums of the scans)
+    uint32_t *d_cnt = nullptr, *d_qh = nullptr;
     unsigned long long *d_total = nullptr;
-    uint32_t *d_off = nullptr;             // [nr][n + 1]: cell offsets within each region (build only)
-    bool ok = cudaMalloc(&d_off, off_words * sizeof(uint32_t)) == cudaSuccess &&
-              cudaMalloc(&s->d_rbase, (nr + 1) * sizeof(unsigned long long)) == cudaSuccess &&
-              cudaMalloc(&s->d_bitmap, s->bm_words * sizeof(uint32_t)) == cudaSuccess &&
-              cudaMalloc(&s->d_active, n * sizeof(uint32_t)) == cudaSuccess &&
-              cudaMalloc(&d_total, nr * sizeof(unsigned long long)) == cudaSuccess;
-    if (!ok) {
+    auto release = [&]() {
+        cudaFree(d_cnt);
+        cudaFree(d_qh);
         cudaFree(d_total);
-        cudaFree(d_off);
         free_hostset(s);
-        return set_error(VATE_ENOMEM, "out of device memory for the hostset's offsets");
-    }
+    };
     auto fail_cuda = [&](cudaError_t e) {
-        cudaFree(d_total);
-        cudaFree(d_off);
-        free_hostset(s);
+        release();
         return set_error(VATE_ECUDA, cudaGetErrorString(e));
     };
+    auto fail_mem = [&](const char *what) {
+        cudaGetLastError();
+        release();
+        return set_error(VATE_ENOMEM, what);
+    };
+    if (cudaMalloc(&d_cnt, (size_t)nr * n * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&d_qh, (size_t)nr * (qm + 1) * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&d_total, nr * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&s->d_rt, (nr + 1) * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&s->d_bitmap, s->bm_words * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&s->d_active, n * sizeof(uint32_t)) != cudaSuccess)
+        return fail_mem("out of device memory for the hostset's build");
     const size_t build_smem = (size_t)(BUILD_THREADS / 32) * nr * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(hs_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(hs_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_qh, 0, (size_t)nr * (qm + 1) * sizeof(uint32_t), st);
     if (e != cudaSuccess) return fail_cuda(e);
     const int grid = (int)std::min<uint64_t>((n + BUILD_THREADS / 32 - 1) / (BUILD_THREADS / 32), (uint64_t)s->sms * 16);
-    hs_count_kernel<<<grid, BUILD_THREADS, build_smem, st>>>(G, d_aips, n, nr, d_off);
+    const dim3 rgrid((unsigned)std::min<uint64_t>((n + BUILD_THREADS - 1) / BUILD_THREADS, 256), nr);
+    hs_count_kernel<<<grid, BUILD_THREADS, build_smem, st>>>(G, d_aips, n, nr, d_cnt);
     count_launch();
-    hs_scan_kernel<<<nr, 1024, 0, st>>>(d_off, n, d_total);
+    hs_qhist_kernel<<<rgrid, BUILD_THREADS, 0, st>>>(d_cnt, n, qm, d_qh);
     count_launch();
-    std::vector<unsigned long long> total(nr), rbase(nr + 1);
+    hs_scan_kernel<<<nr, 1024, 0, st>>>(d_qh, qm, d_total);
+    count_launch();
+    std::vector<unsigned long long> cells(nr);
+    std::vector<uint32_t> rt(nr + 1);
     if ((e = cudaGetLastError()) != cudaSuccess ||
-        (e = cudaMemcpyAsync(total.data(), d_total, nr * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) !=
+        (e = cudaMemcpyAsync(cells.data(), d_total, nr * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) !=
             cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return fail_cuda(e);
-    rbase[0] = 0;
+    uint64_t tiles = 0;
     for (uint32_t r = 0; r < nr; r++) {
-        if (total[r] >= 0xFFFFFFFFull) {
-            cudaFree(d_total);
-            cudaFree(d_off);
-            free_hostset(s);
-            return set_error(VATE_EINVAL, "too many hosts for a hostset: a region would hold 2^32 or more entries");
+        rt[r] = (uint32_t)tiles;
+        tiles += (cells[r] + 31u) / 32u;
+        if (tiles > (0xFFFFFFFFull >> 5) - 1u) {
+            release();
+            return set_error(VATE_EINVAL, "too many hosts for a hostset: 2^27 or more tiles of 32 cells");
         }
-        rbase[r + 1] = rbase[r] + total[r];
     }
-    s->entries = rbase[nr];
-    if (cudaMalloc(&s->d_entries, std::max<uint64_t>(s->entries, 4) * sizeof(uint32_t)) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(d_total);
-        cudaFree(d_off);
-        free_hostset(s);
-        return set_error(VATE_ENOMEM, "out of device memory for the hostset's index");
-    }
-    if ((e = cudaMemcpyAsync(s->d_rbase, rbase.data(), (nr + 1) * sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                             st)) != cudaSuccess)
+    rt[nr] = (uint32_t)tiles;
+    s->T = (uint32_t)tiles;
+    if (cudaMalloc(&s->d_host, (size_t)s->T * 32u * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&s->d_row0, ((size_t)s->T + 1) * sizeof(uint32_t)) != cudaSuccess)
+        return fail_mem("out of device memory for the hostset's tiles");
+    if ((e = cudaMemcpyAsync(s->d_rt, rt.data(), (nr + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(s->d_host, 0xFF, (size_t)s->T * 32u * sizeof(uint32_t), st)) != cudaSuccess)
         return fail_cuda(e);
-    hs_fill_kernel<<<grid, BUILD_THREADS, build_smem, st>>>(G, d_aips, n, nr, d_off, s->d_rbase, s->d_entries);
+    hs_place_kernel<<<rgrid, BUILD_THREADS, 0, st>>>(d_cnt, n, qm, d_qh, s->d_rt, s->d_host, s->d_row0);
+    count_launch();
+    hs_scan_kernel<<<1, 1024, 0, st>>>(s->d_row0, s->T, d_total);
+    count_launch();
+    unsigned long long rows = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&rows, d_total, sizeof(rows), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail_cuda(e);
+    if (rows > 0xFFFFFFFFull - 64u) {
+        release();
+        return set_error(VATE_EINVAL, "too many hosts for a hostset: 2^32 or more rows of index");
+    }
+    s->R = (uint32_t)rows;
+    const size_t ebytes = (size_t)s->R * 512u;
+    if (cudaMalloc(&s->d_entries, ebytes) != cudaSuccess) return fail_mem("out of device memory for the hostset's index");
+    if ((e = cudaMemsetAsync(s->d_entries, 0, ebytes, st)) != cudaSuccess) return fail_cuda(e);
+    hs_fill_kernel<<<grid, BUILD_THREADS, build_smem, st>>>(G, d_aips, n, nr, d_cnt, s->d_row0, s->d_entries);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return fail_cuda(e);
+    cudaFree(d_cnt);
+    cudaFree(d_qh);
     cudaFree(d_total);
-    cudaFree(d_off);
-    if ((e = cudaFuncSetAttribute(kernel_for(s->L), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ACTIVE_SMEM)) !=
-        cudaSuccess) {
-        free_hostset(s);
-        return set_error(VATE_ECUDA, cudaGetErrorString(e));
-    }
-    s->bytes = std::max<uint64_t>(s->entries, 4) * 4 + (nr + 1) * 8 + s->bm_words * 4 + n * 4;
+    d_cnt = d_qh = nullptr;
+    d_total = nullptr;
+    void *kern = kernel_for(s->L);
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, tile_carveout())) != cudaSuccess)
+        return fail_cuda(e);
+    s->bytes = ebytes + (uint64_t)s->T * 32u * 4u + ((uint64_t)s->T + 1) * 4u + (nr + 1) * 4u + s->bm_words * 4 + n * 4;
     *out = s;
     return VATE_OK;
 }
@@ -473,13 +562,16 @@ int vate_estimate_hostset(vate_handle *h, vate_hostset *s, uint32_t kprime, floa
     e = launch_pool(G, hs_bitmap_kernel, bgrid, 256, 0, st, G, rc, c2k, s->bm_words, s->d_bitmap);
     if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
     const uint4 *ent4 = reinterpret_cast<const uint4 *>(s->d_entries);
-    const uint64_t quads = s->entries / 4;
+#define VATE_HS_LAUNCH(LL)                                                                                          \
+    hs_tile_kernel<LL><<<v.sms, HS_THREADS, TILE_SMEM, st>>>(s->d_bitmap, s->bm_words, s->nr, s->d_rt, s->d_row0,   \
+                                                             s->d_host, ent4, s->T, s->R, acc)
     switch (s->L) {
-    case 1: hs_active_kernel<1><<<v.sms, HS_THREADS, ACTIVE_SMEM, st>>>(s->d_bitmap, s->bm_words, s->nr, s->d_rbase, ent4, quads, acc); break;
-    case 2: hs_active_kernel<2><<<v.sms, HS_THREADS, ACTIVE_SMEM, st>>>(s->d_bitmap, s->bm_words, s->nr, s->d_rbase, ent4, quads, acc); break;
-    case 4: hs_active_kernel<4><<<v.sms, HS_THREADS, ACTIVE_SMEM, st>>>(s->d_bitmap, s->bm_words, s->nr, s->d_rbase, ent4, quads, acc); break;
-    default: hs_active_kernel<8><<<v.sms, HS_THREADS, ACTIVE_SMEM, st>>>(s->d_bitmap, s->bm_words, s->nr, s->d_rbase, ent4, quads, acc); break;
+    case 1: VATE_HS_LAUNCH(1); break;
+    case 2: VATE_HS_LAUNCH(2); break;
+    case 4: VATE_HS_LAUNCH(4); break;
+    default: VATE_HS_LAUNCH(8); break;
     }
+#undef VATE_HS_LAUNCH
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
     e = launch_estimate_from_counts(G, kprime, v.hist, acc, s->n, d_out, d_flags, st, v.sms);

@@ -24,13 +24,13 @@ def test_code_of_keeps_code_changes():
 
 
 def test_traffic_sha_is_the_committed_one_or_the_figure_is_null():
-    for kernel in ("hs_active_kernel@L1", "gather_seg_kernel@L2"):
+    for kernel in ("hs_tile_kernel@L1", "gather_seg_kernel@L2"):
         sha = bench.traffic_sha(kernel)
         assert len(sha) == 16 and all(c in "0123456789abcdef" for c in sha)
         t = bench.committed_traffic(kernel)
         assert t is None or t > 0
     # each figure depends on its own kernel's sources
-    assert bench.traffic_sha("hs_active_kernel@L1") != bench.traffic_sha("gather_seg_kernel@L2")
+    assert bench.traffic_sha("hs_tile_kernel@L1") != bench.traffic_sha("gather_seg_kernel@L2")
 
 
 def _args(*argv):
