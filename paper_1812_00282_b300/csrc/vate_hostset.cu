@@ -3,15 +3,16 @@
 //
 // Index.  The pool is cut into regions of REGION_ATS positions (a multiple of
 // every segment length, so no segment straddles two).  Cell (r, h) holds one
-// entry per segment of host h that lies in region r (a segment met twice by
-// one host counts twice, as in the gather): the byte offset of the segment's
-// 32-bit word in the block's shared-memory copy of the region's bitmap,
-// shifted left by 5, plus the bit of its first AT.  The shared-memory copy
-// starts with a zero quad, so the entry 0 looks up a zero word: it pads.
-// The cells of a region are sorted by their number of quads (four entries),
+// 21-bit entry per segment of host h that lies in region r (a segment met
+// twice by one host counts twice, as in the gather): the offset of the
+// segment's first AT in the region plus 128, i.e. its bit in the block's
+// shared-memory copy of the region's bitmap, which starts with a zero quad --
+// so the entry 0 looks up a zero word: it pads.  Six entries fill a 16-byte
+// unit (bits 21 s .. 21 s + 20 of its 128 bits for entry s; the top two bits
+// are 0).  The cells of a region are sorted by their number of units,
 // largest first, and dealt in that order to tiles of 32 cells.  Tile t holds
-// M_t rows of 32 quads; row i holds quad i of each of the tile's cells, lane j
-// reading cell j's column; M_t is the quads of its first, largest, cell and
+// M_t rows of 32 units; row i holds unit i of each of the tile's cells, lane j
+// reading cell j's column; M_t is the units of its first, largest, cell and
 // the rest of every column is 0.  Tiles are stored region-major: rt[r] is the
 // first tile of region r, row0[t] the first row of tile t (row0[T] the number
 // of rows), host[32 t + j] the host of cell j of tile t, NONE for an empty
@@ -53,9 +54,11 @@ namespace {
 constexpr uint32_t REGION_ATS = VATE_HS_REGION_KATS * 1024u;
 constexpr uint32_t REGION_WORDS = REGION_ATS / 32u;
 static_assert(REGION_WORDS % 4u == 0u && REGION_ATS % 8u == 0u, "a region holds whole quads of words and segments");
+static_assert(REGION_ATS + 128u <= (1u << 21), "an entry holds a region's offset + 128 in 21 bits");
 constexpr uint32_t BM_SKIP = 16u;                       // bytes of zeros before the bitmap in shared memory
+constexpr uint32_t PER_UNIT = 6u;                       // 21-bit entries in a 16-byte unit
 constexpr uint32_t NONE = 0xFFFFFFFFu;                  // the host of an empty lane
-// rows of 32 quads a warp has in flight
+// rows of 32 units a warp has in flight
 #ifndef VATE_HS_ROWS
 #define VATE_HS_ROWS 8
 #endif
@@ -64,8 +67,8 @@ constexpr int HS_THREADS = 1024;                        // hs_tile_kernel: one b
 constexpr int BUILD_THREADS = 256;
 constexpr uint32_t MAX_REGIONS = 1024;
 
-// The entry of pool offset o within its region.
-__host__ __device__ constexpr uint32_t entry_of(uint32_t o) { return (((o & ~31u) >> 3) + BM_SKIP) << 5 | (o & 31u); }
+// The entry of pool offset o within its region: its bit in the shared-memory bitmap.
+__host__ __device__ constexpr uint32_t entry_of(uint32_t o) { return o + BM_SKIP * 8u; }
 
 // Thread per 32 ATs: bit (p mod 32) of word p / 32 is set when AT p is active.
 __global__ void __launch_bounds__(256) hs_bitmap_kernel(Geom G, RangeConsts rc, uint32_t c2k, uint64_t words,
@@ -108,12 +111,12 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_count_kernel(Geom G, const u
     }
 }
 
-// Cells by size, per region: qh[r][qm - q] += 1 for a cell of q quads (row r of qh has qm + 1 counters).
+// Cells by size, per region: qh[r][qm - q] += 1 for a cell of q units (row r of qh has qm + 1 counters).
 __global__ void __launch_bounds__(BUILD_THREADS) hs_qhist_kernel(const uint32_t *__restrict__ cnt, uint64_t n,
                                                                  uint32_t qm, uint32_t *__restrict__ qh) {
     const uint32_t r = blockIdx.y;
     for (uint64_t h = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t q = (cnt[(uint64_t)r * n + h] + 3u) >> 2;
+        const uint32_t q = (cnt[(uint64_t)r * n + h] + PER_UNIT - 1u) / PER_UNIT;
         if (q) atomicAdd(&qh[(uint64_t)r * (qm + 1) + (qm - q)], 1u);
     }
 }
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(1024) hs_scan_kernel(uint32_t *__restrict__ of
 
 // Every cell its place: the next slot of its size class in its region's order
 // (qh holds the classes' first slots and advances), so that the cells of a
-// region run from the most quads to the fewest.  Slot s of region r is lane
+// region run from the most units to the fewest.  Slot s of region r is lane
 // s mod 32 of tile rt[r] + s / 32; the first cell of a tile is its largest and
 // gives the tile's rows.  cnt[r][h] becomes the cell's tile lane 32 t + j.
 __global__ void __launch_bounds__(BUILD_THREADS) hs_place_kernel(uint32_t *__restrict__ cnt, uint64_t n, uint32_t qm,
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_place_kernel(uint32_t *__res
     const uint32_t r = blockIdx.y;
     for (uint64_t h = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t i = (uint64_t)r * n + h;
-        const uint32_t q = (cnt[i] + 3u) >> 2;
+        const uint32_t q = (cnt[i] + PER_UNIT - 1u) / PER_UNIT;
         if (!q) continue;
         const uint32_t s = atomicAdd(&qh[(uint64_t)r * (qm + 1) + (qm - q)], 1u);
         const uint32_t tl = rt[r] * 32u + s;
@@ -175,7 +178,8 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_place_kernel(uint32_t *__res
 
 // Warp per host: each segment's entry at its slot of the host's cell in its
 // region -- entry k of the cell in lane j = tl mod 32 of tile t = tl / 32 is
-// word k mod 4 of that lane's quad in row row0[t] + k / 4.
+// field k mod 6 of that lane's unit in row row0[t] + k / 6, OR-ed into the
+// (zeroed) words it spans.
 __global__ void __launch_bounds__(BUILD_THREADS) hs_fill_kernel(Geom G, const uint32_t *__restrict__ aips, uint64_t n,
                                                                 uint32_t nr, const uint32_t *__restrict__ tlpos,
                                                                 const uint32_t *__restrict__ row0,
@@ -194,25 +198,32 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_fill_kernel(Geom G, const ui
             const uint32_t r = pos / REGION_ATS;
             const uint32_t k = atomicAdd(&wh[r], 1u);
             const uint32_t tl = tlpos[(uint64_t)r * n + h];
-            const uint64_t row = (uint64_t)row0[tl >> 5] + (k >> 2);
-            entries[row * 128u + (tl & 31u) * 4u + (k & 3u)] = entry_of(pos - r * REGION_ATS);
+            const uint64_t row = (uint64_t)row0[tl >> 5] + k / PER_UNIT;
+            const uint32_t e = entry_of(pos - r * REGION_ATS), b = 21u * (k % PER_UNIT);
+            uint32_t *u = entries + row * 128u + (tl & 31u) * 4u + (b >> 5);
+            atomicOr(u, e << (b & 31u));
+            if ((b & 31u) > 11u) atomicOr(u + 1, e >> (32u - (b & 31u)));
         }
         __syncwarp();
     }
 }
 
-// The active ATs of the segment of entry e: e >> 5 is the byte offset of its
-// word in the shared-memory bitmap, e mod 32 the bit of its first AT.
+// The active ATs of the segment whose entry is the low 21 bits of x (the
+// bits above are the next entry's): bits 5-20 give its word of the
+// shared-memory bitmap, bits 0-4 the bit of its first AT.
 template <int L>
-__device__ __forceinline__ uint32_t seg_count(const unsigned char *bmb, uint32_t e) {
-    const uint32_t w = __funnelshift_r(*reinterpret_cast<const uint32_t *>(bmb + (e >> 5)), 0u, e);
+__device__ __forceinline__ uint32_t seg_count(const unsigned char *bmb, uint32_t x) {
+    const uint32_t w = __funnelshift_r(*reinterpret_cast<const uint32_t *>(bmb + ((x >> 3) & 0x3FFFCu)), 0u, x);
     if (L == 1) return w & 1u;
     return __popc(w & ((1u << L) - 1u));
 }
 
+// The six entries of a unit: entry s starts at bit 21 s of its 128 bits.
 template <int L>
-__device__ __forceinline__ uint32_t quad_count(const unsigned char *bmb, uint4 v) {
-    return seg_count<L>(bmb, v.x) + seg_count<L>(bmb, v.y) + seg_count<L>(bmb, v.z) + seg_count<L>(bmb, v.w);
+__device__ __forceinline__ uint32_t unit_count(const unsigned char *bmb, uint4 v) {
+    return seg_count<L>(bmb, v.x) + seg_count<L>(bmb, __funnelshift_r(v.x, v.y, 21)) + seg_count<L>(bmb, v.y >> 10) +
+           seg_count<L>(bmb, __funnelshift_r(v.y, v.z, 31)) + seg_count<L>(bmb, __funnelshift_r(v.z, v.w, 20)) +
+           seg_count<L>(bmb, v.w >> 9);
 }
 
 // The first tile t in [lo, hi] whose first row is at or past x (row0
@@ -241,7 +252,7 @@ __device__ __forceinline__ uint32_t tile_at_row(const uint32_t *__restrict__ row
 
 // The block's share of the rows (whole tiles), region by region: the region's
 // bitmap into shared memory, then each warp an equal share of the region's
-// rows (whole tiles), HB rows of 32 quads in flight, lane j summing column j.
+// rows (whole tiles), HB rows of 32 units in flight, lane j summing column j.
 // A tile's rows end at the same row for every lane, where each lane adds its
 // sum to its cell's host; the next tile's first row and hosts are loaded one
 // tile ahead.
@@ -321,7 +332,7 @@ __global__ void __launch_bounds__(HS_THREADS, 1) hs_tile_kernel(const uint32_t *
                             host2 = NONE;
                         }
                     }
-                    sum += quad_count<L>(bmb, v[u]);
+                    sum += unit_count<L>(bmb, v[u]);
                 }
             }
             if (host != NONE && sum) atomicAdd(active + host, sum);
@@ -346,7 +357,7 @@ struct vate_hostset {
     uint32_t nr = 0;
     uint32_t L = 1;
     uint32_t T = 0;                        // tiles
-    uint32_t R = 0;                        // rows of 32 quads
+    uint32_t R = 0;                        // rows of 32 units
     uint64_t bm_words = 0;
     uint32_t *d_entries = nullptr;         // [R][32][4]
     uint32_t *d_rt = nullptr;              // [nr + 1]: first tile of each region
@@ -418,7 +429,7 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
     if (G.L != 1 && G.L != 2 && G.L != 4 && G.L != 8) return set_error(VATE_EINVAL, "a hostset needs seg_len 1, 2, 4 or 8");
     const uint32_t nr = (uint32_t)((G.P + REGION_ATS - 1) / REGION_ATS);
     if (nr > MAX_REGIONS) return set_error(VATE_EINVAL, "pool too large for a hostset (more than 1024 regions)");
-    const uint32_t qm = ((G.g >> G.log2L) + 3u) / 4u;   // the most quads a cell can have
+    const uint32_t qm = ((G.g >> G.log2L) + PER_UNIT - 1u) / PER_UNIT;   // the most units a cell can have
     cudaStream_t st = (cudaStream_t)stream;
     vate_hostset *s = new (std::nothrow) vate_hostset();
     if (!s) return set_error(VATE_ENOMEM, "host allocation failed");

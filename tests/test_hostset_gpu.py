@@ -72,7 +72,7 @@ def test_hostset_equals_per_host_gather(V, L, c, part):
     s = V.vate_hostset_create(d.h, as_i32(hosts))
     nbytes, nh, nr = V.vate_hostset_info(s)
     assert nh == len(hosts) and nr == (1 if c == 16 else 3)
-    assert nbytes >= 4 * len(hosts) * g // L
+    assert nbytes >= 16 * len(hosts) * (g // L) // 6          # six 21-bit entries per 16 bytes
     for sl in range(9):
         d.ingest(as_i32(tr.slice_pairs(sl)), sl)
         d.close_slice(sl)
