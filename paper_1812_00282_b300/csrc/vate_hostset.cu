@@ -179,30 +179,150 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_place_kernel(uint32_t *__res
 // Warp per host: each segment's entry at its slot of the host's cell in its
 // region -- entry k of the cell in lane j = tl mod 32 of tile t = tl / 32 is
 // field k mod 6 of that lane's unit in row row0[t] + k / 6, OR-ed into the
-// (zeroed) words it spans.
-__global__ void __launch_bounds__(BUILD_THREADS) hs_fill_kernel(Geom G, const uint32_t *__restrict__ aips, uint64_t n,
-                                                                uint32_t nr, const uint32_t *__restrict__ tlpos,
-                                                                const uint32_t *__restrict__ row0,
-                                                                uint32_t *__restrict__ entries) {
-    extern __shared__ uint32_t wh_all[];                 // [warps][nr]: entries placed so far per region
+// (zeroed) words it spans.  A cell's entries go in the order of their
+// shared-memory bank less the lane, mod 32 (a counting sort: a histogram per
+// region and key, its scan, then each entry to the next slot of its key), so
+// that at any step the 32 lanes of a tile -- cells of about the same size --
+// look up words in different banks rather than in 32 random ones.
+__global__ void hs_fill_kernel(Geom G, const uint32_t *__restrict__ aips, uint64_t n, uint32_t nr,
+                               const uint32_t *__restrict__ tlpos, const uint32_t *__restrict__ row0,
+                               uint32_t *__restrict__ entries) {
+    extern __shared__ uint32_t wk_all[];                 // [warps][nr][33]: per region and key, counts, then slots
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    uint32_t *wh = wh_all + (size_t)warp * nr;
+    uint32_t *wk = wk_all + (size_t)warp * nr * 33u;
     const uint32_t nseg = G.g >> G.log2L;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t h = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; h < n; h += nwarps) {
-        for (uint32_t r = lane; r < nr; r += 32u) wh[r] = 0u;
+        for (uint32_t i = lane; i < nr * 33u; i += 32u) wk[i] = 0u;
         __syncwarp();
         const uint64_t hk = host_key(G, aips[h]);
-        for (uint32_t j = lane; j < nseg; j += 32u) {
-            const uint32_t pos = seg_base_k(G, hk, j);
-            const uint32_t r = pos / REGION_ATS;
-            const uint32_t k = atomicAdd(&wh[r], 1u);
-            const uint32_t tl = tlpos[(uint64_t)r * n + h];
-            const uint64_t row = (uint64_t)row0[tl >> 5] + k / PER_UNIT;
-            const uint32_t e = entry_of(pos - r * REGION_ATS), b = 21u * (k % PER_UNIT);
-            uint32_t *u = entries + row * 128u + (tl & 31u) * 4u + (b >> 5);
-            atomicOr(u, e << (b & 31u));
-            if ((b & 31u) > 11u) atomicOr(u + 1, e >> (32u - (b & 31u)));
+        for (int pass = 0; pass < 2; pass++) {
+            for (uint32_t j = lane; j < nseg; j += 32u) {
+                const uint32_t pos = seg_base_k(G, hk, j);
+                const uint32_t r = pos / REGION_ATS;
+                const uint32_t e = entry_of(pos - r * REGION_ATS);
+                const uint32_t tl = tlpos[(uint64_t)r * n + h];
+                uint32_t *slot = wk + r * 33u + (((e >> 5) - tl) & 31u);
+                if (pass == 0) {
+                    atomicAdd(slot, 1u);
+                    continue;
+                }
+                const uint32_t k = atomicAdd(slot, 1u);
+                const uint64_t row = (uint64_t)row0[tl >> 5] + k / PER_UNIT;
+                const uint32_t b = 21u * (k % PER_UNIT);
+                uint32_t *u = entries + row * 128u + (tl & 31u) * 4u + (b >> 5);
+                atomicOr(u, e << (b & 31u));
+                if ((b & 31u) > 11u) atomicOr(u + 1, e >> (32u - (b & 31u)));
+            }
+            __syncwarp();
+            if (pass == 0) {
+                for (uint32_t r = lane; r < nr; r += 32u) {   // counts -> first slots, key by key
+                    uint32_t run = 0;
+                    for (uint32_t q = 0; q < 32u; q++) {
+                        const uint32_t c = wk[r * 33u + q];
+                        wk[r * 33u + q] = run;
+                        run += c;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
+constexpr uint32_t ORDER_ROWS = 24;                    // tiles of up to this many rows are dealt again
+constexpr uint32_t ORDER_CAP = ORDER_ROWS * PER_UNIT;  // entries of a column, at most
+constexpr int ORDER_WARPS = 4;                          // hs_order_kernel: warps per block, a tile each
+constexpr size_t ORDER_WARP_BYTES = (32u * ORDER_CAP + 2u * 32u * 33u) * 4u;
+
+// The six 21-bit entries of a unit (0 = pad).
+__device__ __forceinline__ void unit_entries(uint4 v, uint32_t (&x)[PER_UNIT]) {
+    x[0] = v.x & 0x1FFFFFu;
+    x[1] = __funnelshift_r(v.x, v.y, 21) & 0x1FFFFFu;
+    x[2] = (v.y >> 10) & 0x1FFFFFu;
+    x[3] = __funnelshift_r(v.y, v.z, 31) & 0x1FFFFFu;
+    x[4] = __funnelshift_r(v.z, v.w, 20) & 0x1FFFFFu;
+    x[5] = v.w >> 9;
+}
+
+// Warp per tile: the entries of each column dealt again, step by step (step
+// 6 i + s is field s of row i), so that at a step the 32 lanes look up words
+// in different shared-memory banks where they can.  At each step the lanes
+// choose in turn, the lane with the fewest banks left first (then the one
+// with the most entries left); a lane takes the bank, not yet taken at this
+// step, of which it holds the most entries (ties: the bank most entries of
+// the tile still wait for), or, when all of its banks are taken, the one of
+// which it holds the most.  A column keeps its entries, reordered, so every
+// count is unchanged.  Tiles of more than ORDER_ROWS rows keep the fill's
+// order.
+__global__ void __launch_bounds__(32 * ORDER_WARPS) hs_order_kernel(const uint32_t *__restrict__ row0, uint32_t T,
+                                                                    uint4 *__restrict__ ent4) {
+    extern __shared__ uint32_t order_smem[];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t *srt = order_smem + (size_t)warp * (ORDER_WARP_BYTES / 4u);   // [32][ORDER_CAP]: a column by bank
+    uint32_t *cnt = srt + 32u * ORDER_CAP;                                   // [32][33]: entries left per bank
+    uint32_t *mysrt = srt + lane * ORDER_CAP, *mycnt = cnt + lane * 33u;
+    uint32_t *mybeg = cnt + 32u * 33u + lane * 33u;                          // first entry of each bank
+    const uint32_t nwarps = gridDim.x * ORDER_WARPS;
+    for (uint32_t t = blockIdx.x * ORDER_WARPS + warp; t < T; t += nwarps) {
+        const uint32_t r0 = row0[t], M = row0[t + 1] - r0;
+        if (M > ORDER_ROWS) continue;
+        uint4 *col = ent4 + (uint64_t)r0 * 32u + lane;
+        for (uint32_t b = 0; b < 32u; b++) mycnt[b] = 0u;
+        for (uint32_t i = 0; i < M; i++) {
+            uint32_t x[PER_UNIT];
+            unit_entries(col[32u * i], x);
+#pragma unroll
+            for (int f = 0; f < (int)PER_UNIT; f++)
+                if (x[f]) mycnt[(x[f] >> 5) & 31u]++;
+        }
+        uint32_t rem = 0, nav = 0;
+        for (uint32_t b = 0; b < 32u; b++) {
+            mybeg[b] = rem;
+            rem += mycnt[b];
+            nav += mycnt[b] != 0u;
+        }
+        for (uint32_t i = 0; i < M; i++) {
+            uint32_t x[PER_UNIT];
+            unit_entries(col[32u * i], x);
+#pragma unroll
+            for (int f = 0; f < (int)PER_UNIT; f++)
+                if (x[f]) mysrt[mybeg[(x[f] >> 5) & 31u]++] = x[f];
+        }
+        for (uint32_t b = 0; b < 32u; b++) mybeg[b] -= mycnt[b];
+        __syncwarp();
+        uint32_t glob = 0;                               // lane b: entries of bank b the tile has left
+        for (uint32_t j = 0; j < 32u; j++) glob += cnt[j * 33u + lane];
+        for (uint32_t i = 0; i < M; i++) {
+            uint32_t y[PER_UNIT];
+#pragma unroll
+            for (int f = 0; f < (int)PER_UNIT; f++) {
+                uint32_t taken = 0u, done = 0u, mine = 0u;
+                for (int turn = 0; turn < 32; turn++) {
+                    const bool waiting = rem != 0u && !((done >> lane) & 1u);
+                    const uint32_t m = __reduce_min_sync(0xFFFFFFFFu, waiting ? ((nav << 8 | (255u - rem)) << 5 | lane) : 0xFFFFFFFFu);
+                    if (m == 0xFFFFFFFFu) break;
+                    const uint32_t j = m & 31u;
+                    const uint32_t c = cnt[j * 33u + lane];          // lane b looks at bank b of lane j
+                    const uint32_t sc = c ? ((c << 16 | glob) << 5 | lane) : 0u;
+                    uint32_t best = __reduce_max_sync(0xFFFFFFFFu, ((taken >> lane) & 1u) ? 0u : sc);
+                    if (!best) best = __reduce_max_sync(0xFFFFFFFFu, sc);
+                    const uint32_t b = best & 31u;
+                    taken |= 1u << b;
+                    done |= 1u << j;
+                    if (lane == b) glob--;
+                    if (lane == j) {
+                        const uint32_t left = --mycnt[b];
+                        mine = mysrt[mybeg[b] + left];
+                        rem--;
+                        nav -= left == 0u;
+                    }
+                    __syncwarp();
+                }
+                y[f] = mine;
+            }
+            col[32u * i] = make_uint4(y[0] | y[1] << 21, y[1] >> 11 | y[2] << 10 | y[3] << 31, y[3] >> 1 | y[4] << 20,
+                                      y[4] >> 12 | y[5] << 9);
         }
         __syncwarp();
     }
@@ -467,9 +587,12 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
         cudaMalloc(&s->d_active, n * sizeof(uint32_t)) != cudaSuccess)
         return fail_mem("out of device memory for the hostset's build");
     const size_t build_smem = (size_t)(BUILD_THREADS / 32) * nr * sizeof(uint32_t);
+    // the fill's warps each hold nr x 33 counters: as many warps per block (1-8) as fit in 200 KB
+    const uint32_t fill_warps = (uint32_t)std::max<size_t>(1, std::min<size_t>(8, (200u << 10) / ((size_t)nr * 132u)));
+    const size_t fill_smem = (size_t)fill_warps * nr * 132u;
     cudaError_t e = cudaFuncSetAttribute(hs_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(hs_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem);
+        e = cudaFuncSetAttribute(hs_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_qh, 0, (size_t)nr * (qm + 1) * sizeof(uint32_t), st);
     if (e != cudaSuccess) return fail_cuda(e);
     const int grid = (int)std::min<uint64_t>((n + BUILD_THREADS / 32 - 1) / (BUILD_THREADS / 32), (uint64_t)s->sms * 16);
@@ -522,7 +645,15 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
     const size_t ebytes = (size_t)s->R * 512u;
     if (cudaMalloc(&s->d_entries, ebytes) != cudaSuccess) return fail_mem("out of device memory for the hostset's index");
     if ((e = cudaMemsetAsync(s->d_entries, 0, ebytes, st)) != cudaSuccess) return fail_cuda(e);
-    hs_fill_kernel<<<grid, BUILD_THREADS, build_smem, st>>>(G, d_aips, n, nr, d_cnt, s->d_row0, s->d_entries);
+    const int fgrid = (int)std::min<uint64_t>((n + fill_warps - 1) / fill_warps, (uint64_t)s->sms * 16 * (8 / fill_warps));
+    hs_fill_kernel<<<fgrid, 32 * fill_warps, fill_smem, st>>>(G, d_aips, n, nr, d_cnt, s->d_row0, s->d_entries);
+    count_launch();
+    const size_t order_smem = ORDER_WARPS * ORDER_WARP_BYTES;
+    if ((e = cudaFuncSetAttribute(hs_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)order_smem)) !=
+        cudaSuccess)
+        return fail_cuda(e);
+    const int ogrid = (int)std::min<uint64_t>((s->T + ORDER_WARPS - 1) / ORDER_WARPS, (uint64_t)s->sms * 2);
+    hs_order_kernel<<<ogrid, 32 * ORDER_WARPS, order_smem, st>>>(s->d_row0, s->T, reinterpret_cast<uint4 *>(s->d_entries));
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return fail_cuda(e);
     cudaFree(d_cnt);
