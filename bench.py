@@ -520,12 +520,12 @@ def run_ours(args, rank, world, local):
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(achieved / hbm, 3), "traffic": traffic, "kernel": "hs_tile_kernel",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                    "algorithmic": "the host list's index streamed once per close: %d bytes (one 4-byte entry per "
-                                   "segment of every host, %d bytes, in rows of 32-cell tiles whose columns are "
-                                   "padded to the tile's largest cell, a 4-byte host per cell and a 4-byte first "
-                                   "row per tile); the estimate call's time, which also writes the pool's "
-                                   "CheckAT bitmap (%d bytes) and evaluates Eq. 11"
-                                   % (ib, 4 * n_h * (G // args.seg_len), (1 << C) // 8),
+                    "algorithmic": "the host list's index streamed once per close: %d bytes (one 21-bit entry per "
+                                   "segment of every host, %d segments, six to 16 bytes, in rows of 32-cell "
+                                   "tiles whose columns are padded to the tile's largest cell, a 4-byte host "
+                                   "per cell and a 4-byte first row per tile); the estimate call's time, which "
+                                   "also writes the pool's CheckAT bitmap (%d bytes) and evaluates Eq. 11"
+                                   % (ib, n_h * (G // args.seg_len), (1 << C) // 8),
                     "vs_gather": {"sectors_equivalent": sectors,
                                   "equivalent_gsector_s": round(achieved_sectors, 1),
                                   "sector_probe": round(sector_peak, 2),

@@ -13,7 +13,7 @@
  *      pool;
  *   2. for every region of the bitmap that fits in one SM's shared memory
  *      (1.5 M ATs), the region is loaded into shared memory and the index
- *      entries of every host's VATs in that region are streamed from HBM,
+ *      entries of every host's segments in that region are streamed from HBM,
  *      each looked up in shared memory; a host's count is the sum over the
  *      regions;
  *   3. Eq. 11 from the counts and the census (vate_estimate_from_counts).
@@ -22,9 +22,11 @@
  * g / L random 32-byte sectors per host, and for segments of at most 8 ATs
  * its speed is set by the SMs' random-sector rate; the index is read in
  * order instead, at HBM streaming rate, and the random lookups go to shared
- * memory.  The index holds one 4-byte entry per segment of every host (g / L
- * per host, each host's entries of a region padded to a multiple of four),
- * about 4 n g / L bytes: 16 GiB for 2^20 hosts with g = 4096 and L = 1.
+ * memory.  The index holds one 21-bit entry per segment of every host (the
+ * segment's offset in its region), six to 16 bytes, with a host's entries of
+ * a region (a cell) padded to whole 16-byte units and the cells of a region
+ * in tiles of 32 of about the same size, plus 4 bytes per cell: about
+ * 2.8 n g / L bytes, 11.9 GB for 2^20 hosts with g = 4096 and L = 1.
  *
  * Conventions are those of vate.h.  A hostset belongs to the handle it was
  * built for and to the device that was current then; destroy it before that
@@ -47,11 +49,13 @@ typedef struct vate_hostset vate_hostset;
  * the handle's parameters, so the handle's state (slice, pool contents) does
  * not matter and the index stays valid for the handle's whole life.  Needs a
  * handle of byte ATs (k <= 63, at_bits 0 or 8) over the whole pool, seg_len
- * 1, 2, 4 or 8, and at most 2^32 - 1 hosts.  Device memory: the index (about
- * 4 n g / seg_len bytes), 4 (n + 1) bytes per region of offsets, the bitmap
- * (2^c / 8 bytes) and 4 n bytes of counts; vate_hostset_bytes reports the
- * total.  Synchronises `stream`.  Errors: VATE_EINVAL (handle, parameters,
- * NULL pointers), VATE_ENOMEM, VATE_ECUDA. */
+ * 1, 2, 4 or 8, and at most 2^31 - 1 hosts.  Device memory: the index (about
+ * 2.8 n g / seg_len bytes with its tile tables), the bitmap (2^c / 8 bytes)
+ * and 4 n bytes of counts, which vate_hostset_info reports; while it builds,
+ * also 4 n bytes per region.  Synchronises `stream`; the build takes about a
+ * second for 2^20 hosts with g = 4096, seg_len 1.  Errors: VATE_EINVAL
+ * (handle, parameters, NULL pointers, more than 2^32 rows of index),
+ * VATE_ENOMEM, VATE_ECUDA. */
 int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *stream, vate_hostset **out);
 
 /* Free everything of the hostset (after its queued work).  NULL is accepted. */
