@@ -615,8 +615,10 @@ def run_learned(V, torch):
     evaluated against the closed form on 100 held-out slices of another seed;
     at 32-AT segments (the configuration of the learned estimator), at 2-AT
     segments and at the paper's placement (L = 1, the 40 Gb/s workload's);
-    plus the close-time cost of the learned estimate (vate_estimate_learned)
-    for 2^20 hosts at each."""
+    plus the close-time cost of the learned estimate for 2^20 hosts at each:
+    through the per-host gather (vate_estimate_learned) and, for L <= 8,
+    through the host list's age index (vate_estimate_learned_hostset, built
+    once; checked equal bit for bit here)."""
     from paper_1812_00282_b300 import learned
     from traffic import LINK40G, DeviceTraffic, Traffic
     out = {}
@@ -633,8 +635,23 @@ def run_learned(V, torch):
         mon.close_slice(10)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         times = {}
-        for name, fn in (("plain", lambda: mon.estimate(hosts, 10, est)),
-                         ("learned", lambda: V.vate_estimate_learned(mon.h, hosts, params, est))):
+        calls = [("plain", lambda: mon.estimate(hosts, 10, est)),
+                 ("learned", lambda: V.vate_estimate_learned(mon.h, hosts, params, est))]
+        ages = None
+        if L <= 8:
+            torch.cuda.synchronize()
+            tb = time.perf_counter()
+            ages = V.vate_hostset_create_ages(mon.h, hosts)
+            torch.cuda.synchronize()
+            r["age_index"] = {"build_s": round(time.perf_counter() - tb, 3), "bytes": V.vate_hostset_info(ages)[0]}
+            est2 = torch.empty_like(est)
+            V.vate_estimate_learned(mon.h, hosts, params, est)
+            V.vate_estimate_learned_hostset(mon.h, ages, params, est2)
+            torch.cuda.synchronize()
+            r["age_index"]["equal_to_gather"] = bool(torch.equal(est.view(torch.int32), est2.view(torch.int32)))
+            calls += [("plain_age_index", lambda: V.vate_estimate_hostset(mon.h, ages, 10, est)),
+                      ("learned_age_index", lambda: V.vate_estimate_learned_hostset(mon.h, ages, params, est))]
+        for name, fn in calls:
             fn()
             best = 1e9
             for _ in range(5):
@@ -644,6 +661,8 @@ def run_learned(V, torch):
                 torch.cuda.synchronize()
                 best = min(best, ev[0].elapsed_time(ev[1]))
             times[name] = round(best, 4)
+        if ages is not None:
+            V.vate_hostset_destroy(ages)
         mon.close()
         r["estimate_ms_2p20_hosts"] = times
         r["population"] = "hosts active in the window, sampled per slice; relative error |max(est,0) - n| / n"

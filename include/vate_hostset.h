@@ -85,6 +85,33 @@ int vate_estimate_hostset(vate_handle *h, vate_hostset *s, uint32_t kprime, floa
 int vate_estimate_hostset_host(vate_handle *h, vate_hostset *s, uint32_t kprime, float *h_out, uint8_t *h_flags,
                                void *stream);
 
+/* An age index: the same index over regions of 384 K ATs, looked up in the
+ * pool's age map (4 bits per AT: the AT's distance d when d < k, else 15;
+ * 192 KiB per region) instead of the CheckAT bitmap, so that one pass gives
+ * every host's per-age counts.  It serves vate_estimate_hostset (A for k' is
+ * the sum of the ages below k'), vate_age_counts_hostset and
+ * vate_estimate_learned_hostset.  Needs, beyond vate_hostset_create's
+ * conditions, k <= 15 and g <= 65535; device memory as vate_hostset_create's
+ * (with an age map of 2^c / 2 bytes) and 32 n bytes of counts.  Errors: as
+ * vate_hostset_create. */
+int vate_hostset_create_ages(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *stream, vate_hostset **out);
+
+/* vate_age_counts for an age index's hosts, in their order: d_counts device
+ * uint16[n * k], d_counts[i k + d] the host's VATs at distance d.
+ * Asynchronous on `stream`.  Errors: VATE_EINVAL (not an age index, another
+ * handle's hostset, NULL d_counts), VATE_ESLICE (slice not closed),
+ * VATE_ECUDA. */
+int vate_age_counts_hostset(vate_handle *h, vate_hostset *s, uint16_t *d_counts, void *stream);
+
+/* vate_estimate_learned (include/vate_learned.h) for an age index's hosts:
+ * the same values and flags bit for bit, from the per-age counts of one pass
+ * over the index; the feature rows of up to 2^17 hosts at a time go through
+ * the handle's scratch, as in vate_estimate_learned.  Errors: as
+ * vate_estimate_learned, and VATE_EINVAL for a hostset that is not an age
+ * index or was built for another handle. */
+int vate_estimate_learned_hostset(vate_handle *h, vate_hostset *s, const float *d_params, float *d_out,
+                                  uint8_t *d_flags, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

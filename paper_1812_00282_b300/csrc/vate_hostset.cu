@@ -67,8 +67,11 @@ constexpr int HS_THREADS = 1024;                        // hs_tile_kernel: one b
 constexpr int BUILD_THREADS = 256;
 constexpr uint32_t MAX_REGIONS = 1024;
 
-// The entry of pool offset o within its region: its bit in the shared-memory bitmap.
-__host__ __device__ constexpr uint32_t entry_of(uint32_t o) { return o + BM_SKIP * 8u; }
+// An index locates ATs in a shared-memory map of 2^(5 - wsh) bits per AT (wsh = 5: the CheckAT bitmap,
+// one bit per AT; wsh = 3: the age map, four bits per AT), so that entry e lies in word e >> wsh.  The entry
+// of pool offset o within its region: its place in the map, past the map's 16 leading zero bytes.
+__host__ __device__ constexpr uint32_t entry_of(uint32_t o, uint32_t wsh) { return o + (BM_SKIP << (wsh - 2u)); }
+constexpr uint32_t AGE_REGION_ATS = REGION_WORDS * 8u;  // the age map of a region (4 bits per AT) fills the same words
 
 // Thread per 32 ATs: bit (p mod 32) of word p / 32 is set when AT p is active.
 __global__ void __launch_bounds__(256) hs_bitmap_kernel(Geom G, RangeConsts rc, uint32_t c2k, uint64_t words,
@@ -94,7 +97,7 @@ __global__ void __launch_bounds__(256) hs_bitmap_kernel(Geom G, RangeConsts rc, 
 
 // Warp per host: cnt[r][h] = the host's segments in region r.
 __global__ void __launch_bounds__(BUILD_THREADS) hs_count_kernel(Geom G, const uint32_t *__restrict__ aips, uint64_t n,
-                                                                 uint32_t nr, uint32_t *__restrict__ cnt) {
+                                                                 uint32_t nr, uint32_t ra, uint32_t *__restrict__ cnt) {
     extern __shared__ uint32_t wh_all[];                 // [warps][nr]
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t *wh = wh_all + (size_t)warp * nr;
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_count_kernel(Geom G, const u
         for (uint32_t r = lane; r < nr; r += 32u) wh[r] = 0u;
         __syncwarp();
         const uint64_t hk = host_key(G, aips[h]);
-        for (uint32_t j = lane; j < nseg; j += 32u) atomicAdd(&wh[seg_base_k(G, hk, j) / REGION_ATS], 1u);
+        for (uint32_t j = lane; j < nseg; j += 32u) atomicAdd(&wh[seg_base_k(G, hk, j) / ra], 1u);
         __syncwarp();
         for (uint32_t r = lane; r < nr; r += 32u) cnt[(uint64_t)r * n + h] = wh[r];
         __syncwarp();
@@ -184,8 +187,8 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_place_kernel(uint32_t *__res
 // region and key, its scan, then each entry to the next slot of its key), so
 // that at any step the 32 lanes of a tile -- cells of about the same size --
 // look up words in different banks rather than in 32 random ones.
-__global__ void hs_fill_kernel(Geom G, const uint32_t *__restrict__ aips, uint64_t n, uint32_t nr,
-                               const uint32_t *__restrict__ tlpos, const uint32_t *__restrict__ row0,
+__global__ void hs_fill_kernel(Geom G, const uint32_t *__restrict__ aips, uint64_t n, uint32_t nr, uint32_t ra,
+                               uint32_t wsh, const uint32_t *__restrict__ tlpos, const uint32_t *__restrict__ row0,
                                uint32_t *__restrict__ entries) {
     extern __shared__ uint32_t wk_all[];                 // [warps][nr][33]: per region and key, counts, then slots
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -199,10 +202,10 @@ __global__ void hs_fill_kernel(Geom G, const uint32_t *__restrict__ aips, uint64
         for (int pass = 0; pass < 2; pass++) {
             for (uint32_t j = lane; j < nseg; j += 32u) {
                 const uint32_t pos = seg_base_k(G, hk, j);
-                const uint32_t r = pos / REGION_ATS;
-                const uint32_t e = entry_of(pos - r * REGION_ATS);
+                const uint32_t r = pos / ra;
+                const uint32_t e = entry_of(pos - r * ra, wsh);
                 const uint32_t tl = tlpos[(uint64_t)r * n + h];
-                uint32_t *slot = wk + r * 33u + (((e >> 5) - tl) & 31u);
+                uint32_t *slot = wk + r * 33u + (((e >> wsh) - tl) & 31u);
                 if (pass == 0) {
                     atomicAdd(slot, 1u);
                     continue;
@@ -256,7 +259,7 @@ __device__ __forceinline__ void unit_entries(uint4 v, uint32_t (&x)[PER_UNIT]) {
 // count is unchanged.  Tiles of more than ORDER_ROWS rows keep the fill's
 // order.
 __global__ void __launch_bounds__(32 * ORDER_WARPS) hs_order_kernel(const uint32_t *__restrict__ row0, uint32_t T,
-                                                                    uint4 *__restrict__ ent4) {
+                                                                    uint32_t wsh, uint4 *__restrict__ ent4) {
     extern __shared__ uint32_t order_smem[];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t *srt = order_smem + (size_t)warp * (ORDER_WARP_BYTES / 4u);   // [32][ORDER_CAP]: a column by bank
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(32 * ORDER_WARPS) hs_order_kernel(const uint32
             unit_entries(col[32u * i], x);
 #pragma unroll
             for (int f = 0; f < (int)PER_UNIT; f++)
-                if (x[f]) mycnt[(x[f] >> 5) & 31u]++;
+                if (x[f]) mycnt[(x[f] >> wsh) & 31u]++;
         }
         uint32_t rem = 0, nav = 0;
         for (uint32_t b = 0; b < 32u; b++) {
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(32 * ORDER_WARPS) hs_order_kernel(const uint32
             unit_entries(col[32u * i], x);
 #pragma unroll
             for (int f = 0; f < (int)PER_UNIT; f++)
-                if (x[f]) mysrt[mybeg[(x[f] >> 5) & 31u]++] = x[f];
+                if (x[f]) mysrt[mybeg[(x[f] >> wsh) & 31u]++] = x[f];
         }
         for (uint32_t b = 0; b < 32u; b++) mybeg[b] -= mycnt[b];
         __syncwarp();
@@ -461,6 +464,179 @@ __global__ void __launch_bounds__(HS_THREADS, 1) hs_tile_kernel(const uint32_t *
     }
 }
 
+// Thread per 8 ATs: nibble j of word w is the age of AT 8 w + j -- its
+// distance d (Eq. 5 in frame 0; a recorder's value) when d < k, else 15.
+__global__ void __launch_bounds__(256) hs_agemap_kernel(Geom G, uint32_t bact0, uint64_t words, uint32_t *__restrict__ map) {
+    const uint2 *pool8 = reinterpret_cast<const uint2 *>(G.pool);
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 v = __ldcg(pool8 + w);
+        VATE_CHECK_WORD(G, v.x, w >> 1);
+        uint32_t half[2];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const uint32_t raw = i ? v.y : v.x;
+            const uint32_t d = G.counter == 1u ? raw : swar_bins(raw, bact0, G.twok);    // a distance per byte
+            const uint32_t old = ((d + (128u - G.k) * ONES) & HIGH) >> 7;               // d >= k
+            const uint32_t nb = (d | (old * 0xFFu)) & 0x0F0F0F0Fu;                      // d, or 15
+            const uint32_t t = (nb | (nb >> 4)) & 0x00FF00FFu;                           // nibble pairs
+            half[i] = (t | (t >> 8)) & 0xFFFFu;
+        }
+        map[w] = half[0] | half[1] << 16;
+    }
+}
+
+// One AT age (a < 16) into four accumulators of 8-bit fields: field a mod 4
+// of accumulator a / 4 (a shift of 32 or more adds nothing).
+__device__ __forceinline__ void add_age(uint32_t (&acc)[4], uint32_t a, uint32_t nacc) {
+    const uint32_t s = a << 3;
+    acc[0] += __funnelshift_lc(0u, 1u, s);
+    acc[1] += __funnelshift_lc(0u, 1u, s - 32u);
+    if (nacc > 2u) acc[2] += __funnelshift_lc(0u, 1u, s - 64u);
+    if (nacc > 3u) acc[3] += __funnelshift_lc(0u, 1u, s - 96u);
+}
+
+// The lane's counts (8-bit fields, ages 4 i .. 4 i + 3 in acc[i]) added to its
+// host's 16-bit fields (ages 4 i .. 4 i + 3 in counts[i n + h]: a host's
+// fields in four arrays, so that its atomics meet different sectors); then zero.
+__device__ __forceinline__ void flush_ages(uint32_t (&acc)[4], uint32_t nacc, uint32_t host, uint64_t n,
+                                           unsigned long long *__restrict__ counts) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if ((uint32_t)i < nacc && acc[i] && host != NONE) {
+            const unsigned long long v = (unsigned long long)__byte_perm(acc[i], 0u, 0x4342u) << 32 |
+                                         __byte_perm(acc[i], 0u, 0x4140u);
+            atomicAdd(counts + (uint64_t)i * n + host, v);
+        }
+        acc[i] = 0u;
+    }
+}
+
+// hs_tile_kernel over the age map (4 bits per AT, 384 K ATs per region in the
+// same shared memory): lane j adds the age of every AT of its column's
+// segments to 8-bit fields, and adds them to its cell's host at the end of the
+// tile, and before any field can reach 256.  nacc = accumulators of four ages
+// in use (k <= 4 nacc; 2 at least).
+template <int L>
+__global__ void __launch_bounds__(HS_THREADS, 1) hs_age_kernel(const uint32_t *__restrict__ agemap, uint64_t map_words,
+                                                               uint32_t nr, const uint32_t *__restrict__ rt,
+                                                               const uint32_t *__restrict__ row0,
+                                                               const uint32_t *__restrict__ hosts,
+                                                               const uint4 *__restrict__ ent4, uint32_t T, uint32_t R,
+                                                               uint32_t nacc, uint64_t n,
+                                                               unsigned long long *__restrict__ counts) {
+    constexpr uint32_t FLUSH_ROWS = 255u / (PER_UNIT * L);   // rows a field can take before it could overflow
+    extern __shared__ uint4 bm4[];                       // a zero quad, then REGION_WORDS words of age map
+    uint32_t *bm = reinterpret_cast<uint32_t *>(bm4 + 1);
+    const unsigned char *bmb = reinterpret_cast<const unsigned char *>(bm4);
+    __shared__ uint32_t s_t[2];
+    __shared__ uint32_t s_r;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t nw = blockDim.x >> 5;
+    if (tid == 0) bm4[0] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);   // pads: age 15
+    if (warp < 2) {
+        const uint32_t x = (uint32_t)((uint64_t)R * (blockIdx.x + warp) / gridDim.x);
+        const uint32_t t = tile_at_row(row0, 0u, T, x, lane);
+        if (lane == 0) s_t[warp] = t;
+    }
+    __syncthreads();
+    const uint32_t ta = s_t[0], tb = s_t[1];
+    for (uint32_t t0 = ta; t0 < tb;) {
+        if (tid == 0) {
+            uint32_t lo = 0, hi = nr;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (rt[mid] <= t0) lo = mid;
+                else hi = mid;
+            }
+            s_r = lo;
+        }
+        __syncthreads();
+        const uint32_t r = s_r;
+        const uint32_t t1 = min(tb, rt[r + 1]);
+        const uint64_t w0 = (uint64_t)r * REGION_WORDS, left = map_words - w0;
+        const uint32_t nwords = left < (uint64_t)REGION_WORDS ? (uint32_t)left : REGION_WORDS;
+        const uint4 *src = reinterpret_cast<const uint4 *>(agemap + w0);
+        for (uint32_t i = tid; i < nwords / 4u; i += blockDim.x) bm4[1 + i] = __ldcg(src + i);
+        for (uint32_t i = (nwords & ~3u) + tid; i < nwords; i += blockDim.x) bm[i] = __ldcg(agemap + w0 + i);
+        __syncthreads();
+        const uint32_t xa = __ldcg(row0 + t0), xb = __ldcg(row0 + t1);
+        const uint32_t wa = tile_at_row(row0, t0, t1, xa + (uint32_t)((uint64_t)(xb - xa) * warp / nw), lane);
+        const uint32_t wb = tile_at_row(row0, t0, t1, xa + (uint32_t)((uint64_t)(xb - xa) * (warp + 1u) / nw), lane);
+        if (wa < wb) {
+            const uint32_t rowA = __ldcg(row0 + wa), rowB = __ldcg(row0 + wb);
+            uint32_t t = wa;
+            uint32_t end = __ldcg(row0 + t + 1u);
+            uint32_t host = __ldcg(hosts + (uint64_t)t * 32u + lane);
+            const bool more = t + 1u < wb;
+            uint32_t end2 = more ? __ldcg(row0 + t + 2u) : rowB;
+            uint32_t host2 = more ? __ldcg(hosts + (uint64_t)(t + 1u) * 32u + lane) : NONE;
+            uint32_t acc[4] = {0u, 0u, 0u, 0u};
+            uint32_t since = 0;                          // rows added since the last flush (the same in every lane)
+            for (uint32_t row = rowA; row < rowB; row += HB) {
+                const uint4 *rp = ent4 + (uint64_t)row * 32u + lane;
+                uint4 v[HB];
+#pragma unroll
+                for (int u = 0; u < HB; u++)
+                    v[u] = row + u < rowB ? __ldcs(rp + 32u * u) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int u = 0; u < HB; u++) {
+                    if (row + u >= rowB) break;
+                    if (row + u == end || since == FLUSH_ROWS) {
+                        flush_ages(acc, nacc, host, n, counts);
+                        since = 0;
+                    }
+                    if (row + u == end) {
+                        t++;
+                        end = end2;
+                        host = host2;
+                        if (t + 1u < wb) {
+                            end2 = __ldcg(row0 + t + 2u);
+                            host2 = __ldcg(hosts + (uint64_t)(t + 1u) * 32u + lane);
+                        } else {
+                            end2 = rowB;
+                            host2 = NONE;
+                        }
+                    }
+                    const uint32_t x[PER_UNIT] = {v[u].x, __funnelshift_r(v[u].x, v[u].y, 21), v[u].y >> 10,
+                                                  __funnelshift_r(v[u].y, v[u].z, 31),
+                                                  __funnelshift_r(v[u].z, v[u].w, 20), v[u].w >> 9};
+#pragma unroll
+                    for (int f = 0; f < (int)PER_UNIT; f++) {
+                        // bits 3-20 of the entry: its word of the map; bits 0-2: the nibble of the segment's first AT
+                        const uint32_t w = __funnelshift_r(
+                            *reinterpret_cast<const uint32_t *>(bmb + ((x[f] >> 1) & 0x3FFFCu)), 0u, x[f] << 2);
+#pragma unroll
+                        for (int a = 0; a < L; a++) add_age(acc, (w >> (4 * a)) & 15u, nacc);
+                    }
+                    since++;
+                }
+            }
+            flush_ages(acc, nacc, host, n, counts);
+        }
+        t0 = t1;
+    }
+}
+
+// Per-host sums of the 16-bit age fields (counts[i n + h]): active[h] = the ages below kprime.
+__global__ void hs_counts_active_kernel(const unsigned long long *__restrict__ counts, uint64_t n, uint32_t kprime,
+                                        uint32_t *__restrict__ active) {
+    for (uint64_t h = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t a = 0;
+        for (uint32_t d = 0; d < kprime; d++) a += (uint32_t)(counts[(d >> 2) * n + h] >> (16u * (d & 3u))) & 0xFFFFu;
+        active[h] = a;
+    }
+}
+
+// The 16-bit age fields as vate_age_counts writes them: out[h k + d], d < k.
+__global__ void hs_counts_u16_kernel(const unsigned long long *__restrict__ counts, uint64_t n, uint32_t k,
+                                     uint16_t *__restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n * k; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t h = i / k;
+        const uint32_t d = (uint32_t)(i - h * k);
+        out[i] = (uint16_t)(counts[(d >> 2) * n + h] >> (16u * (d & 3u)));
+    }
+}
+
 int sm_count_now() {
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -478,13 +654,17 @@ struct vate_hostset {
     uint32_t L = 1;
     uint32_t T = 0;                        // tiles
     uint32_t R = 0;                        // rows of 32 units
-    uint64_t bm_words = 0;
+    bool ages = false;                     // an age index (4-bit age map) rather than a CheckAT bitmap index
+    uint32_t ra = 0;                       // ATs per region
+    uint32_t wsh = 5;                      // entry e lies in word e >> wsh of the region's map
+    uint64_t bm_words = 0;                 // words of the pool's map (bitmap or age map)
     uint32_t *d_entries = nullptr;         // [R][32][4]
     uint32_t *d_rt = nullptr;              // [nr + 1]: first tile of each region
     uint32_t *d_row0 = nullptr;            // [T + 1]: first row of each tile
     uint32_t *d_host = nullptr;            // [T][32]: host of each cell, NONE for an empty lane
     uint32_t *d_bitmap = nullptr;
     uint32_t *d_active = nullptr;          // [n]
+    unsigned long long *d_ages = nullptr;  // [4][n]: an age index's per-age counts, 16-bit fields
     float *d_out = nullptr;                // [n], vate_estimate_hostset_host (on first use)
     uint8_t *d_flags = nullptr;            // [n]
     uint64_t bytes = 0;
@@ -500,18 +680,19 @@ void free_hostset(vate_hostset *s) {
     cudaFree(s->d_host);
     cudaFree(s->d_bitmap);
     cudaFree(s->d_active);
+    cudaFree(s->d_ages);
     cudaFree(s->d_out);
     cudaFree(s->d_flags);
     cudaGetLastError();
     delete s;
 }
 
-void *kernel_for(uint32_t L) {
+void *kernel_for(uint32_t L, bool ages) {
     switch (L) {
-    case 1: return (void *)hs_tile_kernel<1>;
-    case 2: return (void *)hs_tile_kernel<2>;
-    case 4: return (void *)hs_tile_kernel<4>;
-    default: return (void *)hs_tile_kernel<8>;
+    case 1: return ages ? (void *)hs_age_kernel<1> : (void *)hs_tile_kernel<1>;
+    case 2: return ages ? (void *)hs_age_kernel<2> : (void *)hs_tile_kernel<2>;
+    case 4: return ages ? (void *)hs_age_kernel<4> : (void *)hs_tile_kernel<4>;
+    default: return ages ? (void *)hs_age_kernel<8> : (void *)hs_tile_kernel<8>;
     }
 }
 
@@ -533,9 +714,9 @@ int tile_carveout() {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *stream, vate_hostset **out) {
+int create_hostset(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *stream, vate_hostset **out, bool ages) {
     if (!out) return set_error(VATE_EINVAL, "out must not be NULL");
     *out = nullptr;
     HandleView v;
@@ -547,7 +728,10 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
         return set_error(VATE_EINVAL, "a hostset needs a pool of byte ATs (k <= 63)");
     if (G.lo != 0 || G.hi != G.P) return set_error(VATE_EINVAL, "a hostset needs the whole pool, not a shard");
     if (G.L != 1 && G.L != 2 && G.L != 4 && G.L != 8) return set_error(VATE_EINVAL, "a hostset needs seg_len 1, 2, 4 or 8");
-    const uint32_t nr = (uint32_t)((G.P + REGION_ATS - 1) / REGION_ATS);
+    if (ages && (G.k > 15u || G.g > 65535u))
+        return set_error(VATE_EINVAL, "an age index needs k <= 15 and g <= 65535");
+    const uint32_t ra = ages ? AGE_REGION_ATS : REGION_ATS, wsh = ages ? 3u : 5u;
+    const uint32_t nr = (uint32_t)((G.P + ra - 1) / ra);
     if (nr > MAX_REGIONS) return set_error(VATE_EINVAL, "pool too large for a hostset (more than 1024 regions)");
     const uint32_t qm = ((G.g >> G.log2L) + PER_UNIT - 1u) / PER_UNIT;   // the most units a cell can have
     cudaStream_t st = (cudaStream_t)stream;
@@ -559,7 +743,10 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
     s->n = n;
     s->nr = nr;
     s->L = G.L;
-    s->bm_words = G.P / 32u;
+    s->ages = ages;
+    s->ra = ra;
+    s->wsh = wsh;
+    s->bm_words = G.P >> wsh;
     // build-only buffers: cnt[r][h] (segments per cell, then the cell's tile lane), qh[r][qm + 1] (cells by size,
     // then each size's next slot), total[] (sums of the scans)
     uint32_t *d_cnt = nullptr, *d_qh = nullptr;
@@ -584,7 +771,8 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
         cudaMalloc(&d_total, nr * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&s->d_rt, (nr + 1) * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&s->d_bitmap, s->bm_words * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&s->d_active, n * sizeof(uint32_t)) != cudaSuccess)
+        cudaMalloc(&s->d_active, n * sizeof(uint32_t)) != cudaSuccess ||
+        (ages && cudaMalloc(&s->d_ages, n * 4 * sizeof(unsigned long long)) != cudaSuccess))
         return fail_mem("out of device memory for the hostset's build");
     const size_t build_smem = (size_t)(BUILD_THREADS / 32) * nr * sizeof(uint32_t);
     // the fill's warps each hold nr x 33 counters: as many warps per block (1-8) as fit in 200 KB
@@ -597,7 +785,7 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
     if (e != cudaSuccess) return fail_cuda(e);
     const int grid = (int)std::min<uint64_t>((n + BUILD_THREADS / 32 - 1) / (BUILD_THREADS / 32), (uint64_t)s->sms * 16);
     const dim3 rgrid((unsigned)std::min<uint64_t>((n + BUILD_THREADS - 1) / BUILD_THREADS, 256), nr);
-    hs_count_kernel<<<grid, BUILD_THREADS, build_smem, st>>>(G, d_aips, n, nr, d_cnt);
+    hs_count_kernel<<<grid, BUILD_THREADS, build_smem, st>>>(G, d_aips, n, nr, ra, d_cnt);
     count_launch();
     hs_qhist_kernel<<<rgrid, BUILD_THREADS, 0, st>>>(d_cnt, n, qm, d_qh);
     count_launch();
@@ -646,14 +834,16 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
     if (cudaMalloc(&s->d_entries, ebytes) != cudaSuccess) return fail_mem("out of device memory for the hostset's index");
     if ((e = cudaMemsetAsync(s->d_entries, 0, ebytes, st)) != cudaSuccess) return fail_cuda(e);
     const int fgrid = (int)std::min<uint64_t>((n + fill_warps - 1) / fill_warps, (uint64_t)s->sms * 16 * (8 / fill_warps));
-    hs_fill_kernel<<<fgrid, 32 * fill_warps, fill_smem, st>>>(G, d_aips, n, nr, d_cnt, s->d_row0, s->d_entries);
+    hs_fill_kernel<<<fgrid, 32 * fill_warps, fill_smem, st>>>(G, d_aips, n, nr, ra, wsh, d_cnt, s->d_row0,
+                                                              s->d_entries);
     count_launch();
     const size_t order_smem = ORDER_WARPS * ORDER_WARP_BYTES;
     if ((e = cudaFuncSetAttribute(hs_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)order_smem)) !=
         cudaSuccess)
         return fail_cuda(e);
     const int ogrid = (int)std::min<uint64_t>((s->T + ORDER_WARPS - 1) / ORDER_WARPS, (uint64_t)s->sms * 2);
-    hs_order_kernel<<<ogrid, 32 * ORDER_WARPS, order_smem, st>>>(s->d_row0, s->T, reinterpret_cast<uint4 *>(s->d_entries));
+    hs_order_kernel<<<ogrid, 32 * ORDER_WARPS, order_smem, st>>>(s->d_row0, s->T, wsh,
+                                                                  reinterpret_cast<uint4 *>(s->d_entries));
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return fail_cuda(e);
     cudaFree(d_cnt);
@@ -661,13 +851,26 @@ int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void
     cudaFree(d_total);
     d_cnt = d_qh = nullptr;
     d_total = nullptr;
-    void *kern = kernel_for(s->L);
+    void *kern = kernel_for(s->L, ages);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, tile_carveout())) != cudaSuccess)
         return fail_cuda(e);
-    s->bytes = ebytes + (uint64_t)s->T * 32u * 4u + ((uint64_t)s->T + 1) * 4u + (nr + 1) * 4u + s->bm_words * 4 + n * 4;
+    s->bytes = ebytes + (uint64_t)s->T * 32u * 4u + ((uint64_t)s->T + 1) * 4u + (nr + 1) * 4u + s->bm_words * 4 + n * 4 +
+               (ages ? n * 32 : 0);
     *out = s;
     return VATE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vate_hostset_create(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *stream, vate_hostset **out) {
+    return create_hostset(h, d_aips, n, stream, out, false);
+}
+
+int vate_hostset_create_ages(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *stream, vate_hostset **out) {
+    return create_hostset(h, d_aips, n, stream, out, true);
 }
 
 int vate_hostset_destroy(vate_hostset *s) {
@@ -685,6 +888,45 @@ int vate_hostset_info(const vate_hostset *s, uint64_t *bytes, uint64_t *n_hosts,
     return VATE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The per-age counts of an age index's hosts into s->d_ages: the pool's age map, then the tile pass.
+cudaError_t age_pass(const HandleView &v, vate_hostset *s, cudaStream_t st) {
+    const Geom &G = v.G;
+    cudaError_t e = cudaMemsetAsync(s->d_ages, 0, s->n * 4 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const int mgrid = (int)std::min<uint64_t>((s->bm_words + 255) / 256, (uint64_t)v.sms * 16);
+    if ((e = launch_pool(G, hs_agemap_kernel, mgrid, 256, 0, st, G, v.bact0, s->bm_words, s->d_bitmap)) != cudaSuccess)
+        return e;
+    const uint4 *ent4 = reinterpret_cast<const uint4 *>(s->d_entries);
+    const uint32_t nacc = std::max(2u, (G.k + 3u) / 4u);
+#define VATE_HS_AGES(LL)                                                                                           \
+    hs_age_kernel<LL><<<v.sms, HS_THREADS, TILE_SMEM, st>>>(s->d_bitmap, s->bm_words, s->nr, s->d_rt, s->d_row0,   \
+                                                            s->d_host, ent4, s->T, s->R, nacc, s->n, s->d_ages)
+    switch (s->L) {
+    case 1: VATE_HS_AGES(1); break;
+    case 2: VATE_HS_AGES(2); break;
+    case 4: VATE_HS_AGES(4); break;
+    default: VATE_HS_AGES(8); break;
+    }
+#undef VATE_HS_AGES
+    count_launch();
+    return cudaGetLastError();
+}
+
+int check_call(vate_handle *h, vate_hostset *s, HandleView &v) {
+    if (int rc = handle_view(h, &v)) return rc;
+    if (!s || s->owner != h) return set_error(VATE_EINVAL, "the hostset was not built for this handle");
+    if (!v.closed) return set_error(VATE_ESLICE, "the current slice has not been closed");
+    return VATE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int vate_estimate_hostset(vate_handle *h, vate_hostset *s, uint32_t kprime, float *d_out, uint8_t *d_flags,
                           uint32_t *d_active, void *stream) {
     HandleView v;
@@ -696,29 +938,68 @@ int vate_estimate_hostset(vate_handle *h, vate_hostset *s, uint32_t kprime, floa
     if (kprime < 1 || kprime > G.k) return set_error(VATE_EINVAL, "kprime must be in [1, k]");
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t *acc = d_active ? d_active : s->d_active;
-    cudaError_t e = cudaMemsetAsync(acc, 0, s->n * sizeof(uint32_t), st);
-    if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
-    const RangeConsts rc = G.counter == 1u ? dr_range_consts(kprime) : range_consts(v.bact0, kprime, G.twok);
-    const uint32_t c2k = (128u - G.twok) * ONES;
-    const int bgrid = (int)std::min<uint64_t>((s->bm_words + 255) / 256, (uint64_t)v.sms * 16);
-    e = launch_pool(G, hs_bitmap_kernel, bgrid, 256, 0, st, G, rc, c2k, s->bm_words, s->d_bitmap);
-    if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
-    const uint4 *ent4 = reinterpret_cast<const uint4 *>(s->d_entries);
+    cudaError_t e;
+    if (s->ages) {
+        // the active count for k' is the sum of the ages below k'
+        if ((e = age_pass(v, s, st)) != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+        const int cgrid = (int)std::min<uint64_t>((s->n + 255) / 256, (uint64_t)v.sms * 8);
+        hs_counts_active_kernel<<<cgrid, 256, 0, st>>>(s->d_ages, s->n, kprime, acc);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+    } else {
+        if ((e = cudaMemsetAsync(acc, 0, s->n * sizeof(uint32_t), st)) != cudaSuccess)
+            return set_error(VATE_ECUDA, cudaGetErrorString(e));
+        const RangeConsts rc = G.counter == 1u ? dr_range_consts(kprime) : range_consts(v.bact0, kprime, G.twok);
+        const uint32_t c2k = (128u - G.twok) * ONES;
+        const int bgrid = (int)std::min<uint64_t>((s->bm_words + 255) / 256, (uint64_t)v.sms * 16);
+        e = launch_pool(G, hs_bitmap_kernel, bgrid, 256, 0, st, G, rc, c2k, s->bm_words, s->d_bitmap);
+        if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+        const uint4 *ent4 = reinterpret_cast<const uint4 *>(s->d_entries);
 #define VATE_HS_LAUNCH(LL)                                                                                          \
     hs_tile_kernel<LL><<<v.sms, HS_THREADS, TILE_SMEM, st>>>(s->d_bitmap, s->bm_words, s->nr, s->d_rt, s->d_row0,   \
                                                              s->d_host, ent4, s->T, s->R, acc)
-    switch (s->L) {
-    case 1: VATE_HS_LAUNCH(1); break;
-    case 2: VATE_HS_LAUNCH(2); break;
-    case 4: VATE_HS_LAUNCH(4); break;
-    default: VATE_HS_LAUNCH(8); break;
-    }
+        switch (s->L) {
+        case 1: VATE_HS_LAUNCH(1); break;
+        case 2: VATE_HS_LAUNCH(2); break;
+        case 4: VATE_HS_LAUNCH(4); break;
+        default: VATE_HS_LAUNCH(8); break;
+        }
 #undef VATE_HS_LAUNCH
-    count_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+    }
     e = launch_estimate_from_counts(G, kprime, v.hist, acc, s->n, d_out, d_flags, st, v.sms);
     if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
     return VATE_OK;
+}
+
+int vate_age_counts_hostset(vate_handle *h, vate_hostset *s, uint16_t *d_counts, void *stream) {
+    HandleView v;
+    if (int rc = check_call(h, s, v)) return rc;
+    if (!s->ages) return set_error(VATE_EINVAL, "per-age counts need an age index (vate_hostset_create_ages)");
+    if (!d_counts) return set_error(VATE_EINVAL, "d_counts must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = age_pass(v, s, st);
+    if (e == cudaSuccess) {
+        const int cgrid = (int)std::min<uint64_t>((s->n * v.G.k + 255) / 256, (uint64_t)v.sms * 8);
+        hs_counts_u16_kernel<<<cgrid, 256, 0, st>>>(s->d_ages, s->n, v.G.k, d_counts);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? VATE_OK : set_error(VATE_ECUDA, cudaGetErrorString(e));
+}
+
+int vate_estimate_learned_hostset(vate_handle *h, vate_hostset *s, const float *d_params, float *d_out,
+                                  uint8_t *d_flags, void *stream) {
+    HandleView v;
+    if (int rc = check_call(h, s, v)) return rc;
+    if (!s->ages) return set_error(VATE_EINVAL, "the learned close needs an age index (vate_hostset_create_ages)");
+    if (!d_params || !d_out) return set_error(VATE_EINVAL, "d_params and d_out must not be NULL");
+    if (int rc = learned_handle_ok(h)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = age_pass(v, s, st);
+    if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+    return learned_from_age_counts(h, v, s->d_ages, s->n, d_params, d_out, d_flags, st);   // fields counts[i n + h]
 }
 
 int vate_estimate_hostset_host(vate_handle *h, vate_hostset *s, uint32_t kprime, float *h_out, uint8_t *h_flags,

@@ -30,6 +30,15 @@ int set_error(int code, const char *msg);
 // A device scratch of at least `bytes` owned by the handle: allocated on the
 // first request (and grown if a later one is larger), freed by vate_destroy.
 int handle_scratch(vate_handle *h, uint64_t bytes, void **ptr);
+// VATE_OK when the handle can serve the learned estimator (its checks and
+// error messages), else the error (vate_learned.cu).
+int learned_handle_ok(const vate_handle *h);
+// The learned estimate (vate_estimate_learned) of n hosts from their per-age
+// counts, given as 16-bit fields (ages 4 i .. 4 i + 3 in counts[i n + h]):
+// feature rows, Eq. 11 and the output rule, in chunks through the handle's
+// scratch (vate_learned.cu).
+int learned_from_age_counts(vate_handle *h, const HandleView &v, const unsigned long long *counts, uint64_t n,
+                            const float *d_params, float *d_out, uint8_t *d_flags, cudaStream_t st);
 
 cudaError_t launch_init(const Geom &G, cudaStream_t st, int sms);
 cudaError_t launch_ingest(const Geom &G, uint32_t bact0, const uint32_t *pairs, uint64_t n, cudaStream_t st, int sms);

@@ -155,6 +155,9 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
         "vate_hostset_info": (i, [vp, P(u64), P(u64), P(u32)]),
         "vate_estimate_hostset": (i, [vp, vp, u32, vp, vp, vp, vp]),
         "vate_estimate_hostset_host": (i, [vp, vp, u32, vp, vp, vp]),
+        "vate_hostset_create_ages": (i, [vp, vp, u64, vp, P(vp)]),
+        "vate_age_counts_hostset": (i, [vp, vp, vp, vp]),
+        "vate_estimate_learned_hostset": (i, [vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -704,6 +707,35 @@ def vate_hostset_create(h, aips, stream=None) -> C.c_void_p:
     s = C.c_void_p()
     _check(_lib.vate_hostset_create(h, pa, aips.numel(), _stream(stream), C.byref(s)))
     return s
+
+
+def vate_hostset_create_ages(h, aips, stream=None) -> C.c_void_p:
+    """The age index of the hosts `aips` for handle h (include/vate_hostset.h)."""
+    import torch
+    pa = _dev(aips, aips.dtype if aips.dtype in (torch.int32, torch.uint32) else torch.int32, "aips")
+    s = C.c_void_p()
+    _check(_lib.vate_hostset_create_ages(h, pa, aips.numel(), _stream(stream), C.byref(s)))
+    return s
+
+
+def vate_age_counts_hostset(h, s, counts, stream=None) -> None:
+    """vate_age_counts for an age index's hosts (include/vate_hostset.h)."""
+    import torch
+    n = vate_hostset_info(s)[1]
+    k = vate_get_info_k(h)
+    pc = _dev(counts, counts.dtype if counts.dtype in (torch.int16, torch.uint16) else torch.int16, "counts", n * k)
+    _check(_lib.vate_age_counts_hostset(h, s, pc, _stream(stream)))
+
+
+def vate_estimate_learned_hostset(h, s, params, out, flags=None, stream=None) -> None:
+    """vate_estimate_learned for an age index's hosts (include/vate_hostset.h)."""
+    import torch
+    n = vate_hostset_info(s)[1]
+    k = vate_get_info_k(h)
+    pp = _dev(params, torch.float32, "params", vate_mlp_param_count(2 * k + 2))
+    po = _dev(out, torch.float32, "out", n)
+    pf = _dev(flags, torch.uint8, "flags", n) if flags is not None else None
+    _check(_lib.vate_estimate_learned_hostset(h, s, pp, po, pf, _stream(stream)))
 
 
 def vate_hostset_destroy(s) -> None:
