@@ -1157,8 +1157,25 @@ def run_learned_kernels(args):
     ages30 = torch.empty(n * 30, dtype=torch.int16, device="cuda")
     ms["age_counts_k30"] = timed(lambda: V.vate_age_counts(h30.h, hosts, ages30))
     h30.close()
-    return {"workload": "learned estimator kernels at close: %d hosts, 2^24-AT pool, k = 10, g = 4096" % n,
-            "unit": "ms per call", "ms": ms}
+    # the same hosts through their age index (vate_hostset_create_ages), at L = 1 and 2: per-age counts, A
+    # and the learned close from one pass over the index, beside the per-host gathers
+    for L in (1, 2):
+        hl = V.Vate(c, k, g, L, 0, 7)
+        for s in range(12):
+            hl.ingest(dt.slice_pairs(s), s)
+        hl.close_slice(11)
+        ai = V.vate_hostset_create_ages(hl.h, hosts)
+        ms["L%d" % L] = {
+            "age_counts_gather": timed(lambda: V.vate_age_counts(hl.h, hosts, ages)),
+            "age_counts_age_index": timed(lambda: V.vate_age_counts_hostset(hl.h, ai, ages)),
+            "learned_gather": timed(lambda: V.vate_estimate_learned(hl.h, hosts, params, out, fl)),
+            "learned_age_index": timed(lambda: V.vate_estimate_learned_hostset(hl.h, ai, params, out, fl)),
+            "plain_age_index": timed(lambda: V.vate_estimate_hostset(hl.h, ai, k, out, fl)),
+            "age_index_bytes": V.vate_hostset_info(ai)[0]}
+        V.vate_hostset_destroy(ai)
+        hl.close()
+    return {"workload": "learned estimator kernels at close: %d hosts, 2^24-AT pool, k = 10, g = 4096 (L = 2, "
+                        "and the age index at L = 1 and 2)" % n, "unit": "ms per call", "ms": ms}
 
 
 def run_probes(args):
