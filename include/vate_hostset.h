@@ -105,8 +105,8 @@ int vate_age_counts_hostset(vate_handle *h, vate_hostset *s, uint16_t *d_counts,
 
 /* vate_estimate_learned (include/vate_learned.h) for an age index's hosts:
  * the same values and flags bit for bit, from the per-age counts of one pass
- * over the index; the feature rows of up to 2^17 hosts at a time go through
- * the handle's scratch, as in vate_estimate_learned.  Errors: as
+ * over the index; each host's feature row is built from its counts in shared
+ * memory, beside the model (no scratch).  Errors: as
  * vate_estimate_learned, and VATE_EINVAL for a hostset that is not an age
  * index or was built for another handle. */
 int vate_estimate_learned_hostset(vate_handle *h, vate_hostset *s, const float *d_params, float *d_out,

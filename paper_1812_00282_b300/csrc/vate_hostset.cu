@@ -4,10 +4,11 @@
 // Index.  The pool is cut into regions of REGION_ATS positions (a multiple of
 // every segment length, so no segment straddles two).  Cell (r, h) holds one
 // 21-bit entry per segment of host h that lies in region r (a segment met
-// twice by one host counts twice, as in the gather): the offset of the
-// segment's first AT in the region plus 128, i.e. its bit in the block's
-// shared-memory copy of the region's bitmap, which starts with a zero quad --
-// so the entry 0 looks up a zero word: it pads.  Six entries fill a 16-byte
+// twice by one host counts twice, as in the gather): the first bit of its
+// first AT's field in the block's shared-memory copy of the region's map
+// (the offset in the region plus 128 for the bitmap; 4 times the offset plus
+// 128 for an age map), which starts with a quad that reads as nothing (zero
+// bits; ages 15) -- so the entry 0 pads.  Six entries fill a 16-byte
 // unit (bits 21 s .. 21 s + 20 of its 128 bits for entry s; the top two bits
 // are 0).  The cells of a region are sorted by their number of units,
 // largest first, and dealt in that order to tiles of 32 cells.  Tile t holds
@@ -67,10 +68,10 @@ constexpr int HS_THREADS = 1024;                        // hs_tile_kernel: one b
 constexpr int BUILD_THREADS = 256;
 constexpr uint32_t MAX_REGIONS = 1024;
 
-// An index locates ATs in a shared-memory map of 2^(5 - wsh) bits per AT (wsh = 5: the CheckAT bitmap,
-// one bit per AT; wsh = 3: the age map, four bits per AT), so that entry e lies in word e >> wsh.  The entry
-// of pool offset o within its region: its place in the map, past the map's 16 leading zero bytes.
-__host__ __device__ constexpr uint32_t entry_of(uint32_t o, uint32_t wsh) { return o + (BM_SKIP << (wsh - 2u)); }
+// An index locates ATs in a shared-memory map of bpa bits per AT (1: the CheckAT bitmap; 4: the age map).
+// The entry of pool offset o within its region is the first bit of its field in the map, past the map's 16
+// leading bytes: bits 5-20 give the map word, bits 0-4 the field's first bit in it.
+__host__ __device__ constexpr uint32_t entry_of(uint32_t o, uint32_t bpa) { return o * bpa + BM_SKIP * 8u; }
 constexpr uint32_t AGE_REGION_ATS = REGION_WORDS * 8u;  // the age map of a region (4 bits per AT) fills the same words
 
 // Thread per 32 ATs: bit (p mod 32) of word p / 32 is set when AT p is active.
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) hs_place_kernel(uint32_t *__res
 // that at any step the 32 lanes of a tile -- cells of about the same size --
 // look up words in different banks rather than in 32 random ones.
 __global__ void hs_fill_kernel(Geom G, const uint32_t *__restrict__ aips, uint64_t n, uint32_t nr, uint32_t ra,
-                               uint32_t wsh, const uint32_t *__restrict__ tlpos, const uint32_t *__restrict__ row0,
+                               uint32_t bpa, const uint32_t *__restrict__ tlpos, const uint32_t *__restrict__ row0,
                                uint32_t *__restrict__ entries) {
     extern __shared__ uint32_t wk_all[];                 // [warps][nr][33]: per region and key, counts, then slots
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -203,9 +204,9 @@ __global__ void hs_fill_kernel(Geom G, const uint32_t *__restrict__ aips, uint64
             for (uint32_t j = lane; j < nseg; j += 32u) {
                 const uint32_t pos = seg_base_k(G, hk, j);
                 const uint32_t r = pos / ra;
-                const uint32_t e = entry_of(pos - r * ra, wsh);
+                const uint32_t e = entry_of(pos - r * ra, bpa);
                 const uint32_t tl = tlpos[(uint64_t)r * n + h];
-                uint32_t *slot = wk + r * 33u + (((e >> wsh) - tl) & 31u);
+                uint32_t *slot = wk + r * 33u + (((e >> 5) - tl) & 31u);
                 if (pass == 0) {
                     atomicAdd(slot, 1u);
                     continue;
@@ -259,7 +260,7 @@ __device__ __forceinline__ void unit_entries(uint4 v, uint32_t (&x)[PER_UNIT]) {
 // count is unchanged.  Tiles of more than ORDER_ROWS rows keep the fill's
 // order.
 __global__ void __launch_bounds__(32 * ORDER_WARPS) hs_order_kernel(const uint32_t *__restrict__ row0, uint32_t T,
-                                                                    uint32_t wsh, uint4 *__restrict__ ent4) {
+                                                                    uint4 *__restrict__ ent4) {
     extern __shared__ uint32_t order_smem[];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t *srt = order_smem + (size_t)warp * (ORDER_WARP_BYTES / 4u);   // [32][ORDER_CAP]: a column by bank
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(32 * ORDER_WARPS) hs_order_kernel(const uint32
             unit_entries(col[32u * i], x);
 #pragma unroll
             for (int f = 0; f < (int)PER_UNIT; f++)
-                if (x[f]) mycnt[(x[f] >> wsh) & 31u]++;
+                if (x[f]) mycnt[(x[f] >> 5) & 31u]++;
         }
         uint32_t rem = 0, nav = 0;
         for (uint32_t b = 0; b < 32u; b++) {
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(32 * ORDER_WARPS) hs_order_kernel(const uint32
             unit_entries(col[32u * i], x);
 #pragma unroll
             for (int f = 0; f < (int)PER_UNIT; f++)
-                if (x[f]) mysrt[mybeg[(x[f] >> wsh) & 31u]++] = x[f];
+                if (x[f]) mysrt[mybeg[(x[f] >> 5) & 31u]++] = x[f];
         }
         for (uint32_t b = 0; b < 32u; b++) mybeg[b] -= mycnt[b];
         __syncwarp();
@@ -485,46 +486,61 @@ __global__ void __launch_bounds__(256) hs_agemap_kernel(Geom G, uint32_t bact0, 
     }
 }
 
-// One AT age (a < 16) into four accumulators of 8-bit fields: field a mod 4
-// of accumulator a / 4 (a shift of 32 or more adds nothing).
-__device__ __forceinline__ void add_age(uint32_t (&acc)[4], uint32_t a, uint32_t nacc) {
-    const uint32_t s = a << 3;
-    acc[0] += __funnelshift_lc(0u, 1u, s);
-    acc[1] += __funnelshift_lc(0u, 1u, s - 32u);
-    if (nacc > 2u) acc[2] += __funnelshift_lc(0u, 1u, s - 64u);
-    if (nacc > 3u) acc[3] += __funnelshift_lc(0u, 1u, s - 96u);
+// One AT age (a < 16) into accumulators of 6-bit fields: one is added to
+// field a mod 5 of accumulator a / 5 (bits 6 (a mod 5) ..); ages 15 and, past
+// the accumulators in use, ages at or above 5 NACC add nothing (a shift of 32
+// or more), and an age that lands on the top two bits of an accumulator is one
+// no window counts.
+template <int NACC>
+__device__ __forceinline__ void add_age(uint32_t (&acc)[3], uint32_t a) {
+    acc[0] += __funnelshift_lc(0u, 1u, a * 6u);
+    if (NACC > 1) acc[1] += __funnelshift_lc(0u, 1u, a * 6u - 30u);
+    if (NACC > 2) acc[2] += __funnelshift_lc(0u, 1u, a * 6u - 60u);
 }
 
-// The lane's counts (8-bit fields, ages 4 i .. 4 i + 3 in acc[i]) added to its
-// host's 16-bit fields (ages 4 i .. 4 i + 3 in counts[i n + h]: a host's
-// fields in four arrays, so that its atomics meet different sectors); then zero.
-__device__ __forceinline__ void flush_ages(uint32_t (&acc)[4], uint32_t nacc, uint32_t host, uint64_t n,
-                                           unsigned long long *__restrict__ counts) {
+// The 6-bit fields into 16-bit ones (ages 2 j, 2 j + 1 in wide[j]); then zero.
+template <int NACC>
+__device__ __forceinline__ void spill_ages(uint32_t (&acc)[3], uint32_t (&wide)[8]) {
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        if ((uint32_t)i < nacc && acc[i] && host != NONE) {
-            const unsigned long long v = (unsigned long long)__byte_perm(acc[i], 0u, 0x4342u) << 32 |
-                                         __byte_perm(acc[i], 0u, 0x4140u);
-            atomicAdd(counts + (uint64_t)i * n + host, v);
+    for (int j = 0; j < NACC; j++) {
+#pragma unroll
+        for (int f = 0; f < 5; f++) {
+            const int a = 5 * j + f;
+            wide[a >> 1] += ((acc[j] >> (6 * f)) & 63u) << (16 * (a & 1));
         }
-        acc[i] = 0u;
+        acc[j] = 0u;
+    }
+}
+
+// The lane's counts added to its host's 16-bit fields (ages 4 i .. 4 i + 3 in
+// counts[i n + h]: a host's fields in separate arrays, so that its atomics
+// meet different sectors); then zero.
+template <int NACC>
+__device__ __forceinline__ void flush_ages(uint32_t (&acc)[3], uint32_t (&wide)[8], uint32_t host, uint64_t n,
+                                           unsigned long long *__restrict__ counts) {
+    spill_ages<NACC>(acc, wide);
+    constexpr int NW = (5 * NACC + 3) / 4;              // 64-bit words of four ages
+#pragma unroll
+    for (int i = 0; i < NW; i++) {
+        const unsigned long long v = (unsigned long long)wide[2 * i + 1] << 32 | wide[2 * i];
+        if (v && host != NONE) atomicAdd(counts + (uint64_t)i * n + host, v);
+        wide[2 * i] = wide[2 * i + 1] = 0u;
     }
 }
 
 // hs_tile_kernel over the age map (4 bits per AT, 384 K ATs per region in the
 // same shared memory): lane j adds the age of every AT of its column's
-// segments to 8-bit fields, and adds them to its cell's host at the end of the
-// tile, and before any field can reach 256.  nacc = accumulators of four ages
-// in use (k <= 4 nacc; 2 at least).
-template <int L>
+// segments to 6-bit fields, moves them into 16-bit fields in registers before
+// any could reach 64, and adds those to its cell's host at the end of the
+// tile.  NACC = accumulators of five ages in use (k <= 5 NACC).
+template <int L, int NACC>
 __global__ void __launch_bounds__(HS_THREADS, 1) hs_age_kernel(const uint32_t *__restrict__ agemap, uint64_t map_words,
                                                                uint32_t nr, const uint32_t *__restrict__ rt,
                                                                const uint32_t *__restrict__ row0,
                                                                const uint32_t *__restrict__ hosts,
                                                                const uint4 *__restrict__ ent4, uint32_t T, uint32_t R,
-                                                               uint32_t nacc, uint64_t n,
-                                                               unsigned long long *__restrict__ counts) {
-    constexpr uint32_t FLUSH_ROWS = 255u / (PER_UNIT * L);   // rows a field can take before it could overflow
+                                                               uint64_t n, unsigned long long *__restrict__ counts) {
+    constexpr uint32_t SPILL_ROWS = 63u / (PER_UNIT * L);    // rows a 6-bit field can take before it could overflow
     extern __shared__ uint4 bm4[];                       // a zero quad, then REGION_WORDS words of age map
     uint32_t *bm = reinterpret_cast<uint32_t *>(bm4 + 1);
     const unsigned char *bmb = reinterpret_cast<const unsigned char *>(bm4);
@@ -570,7 +586,8 @@ __global__ void __launch_bounds__(HS_THREADS, 1) hs_age_kernel(const uint32_t *_
             const bool more = t + 1u < wb;
             uint32_t end2 = more ? __ldcg(row0 + t + 2u) : rowB;
             uint32_t host2 = more ? __ldcg(hosts + (uint64_t)(t + 1u) * 32u + lane) : NONE;
-            uint32_t acc[4] = {0u, 0u, 0u, 0u};
+            uint32_t acc[3] = {0u, 0u, 0u};
+            uint32_t wide[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
             uint32_t since = 0;                          // rows added since the last flush (the same in every lane)
             for (uint32_t row = rowA; row < rowB; row += HB) {
                 const uint4 *rp = ent4 + (uint64_t)row * 32u + lane;
@@ -581,8 +598,11 @@ __global__ void __launch_bounds__(HS_THREADS, 1) hs_age_kernel(const uint32_t *_
 #pragma unroll
                 for (int u = 0; u < HB; u++) {
                     if (row + u >= rowB) break;
-                    if (row + u == end || since == FLUSH_ROWS) {
-                        flush_ages(acc, nacc, host, n, counts);
+                    if (row + u == end) {
+                        flush_ages<NACC>(acc, wide, host, n, counts);
+                        since = 0;
+                    } else if (since == SPILL_ROWS) {
+                        spill_ages<NACC>(acc, wide);
                         since = 0;
                     }
                     if (row + u == end) {
@@ -602,16 +622,16 @@ __global__ void __launch_bounds__(HS_THREADS, 1) hs_age_kernel(const uint32_t *_
                                                   __funnelshift_r(v[u].z, v[u].w, 20), v[u].w >> 9};
 #pragma unroll
                     for (int f = 0; f < (int)PER_UNIT; f++) {
-                        // bits 3-20 of the entry: its word of the map; bits 0-2: the nibble of the segment's first AT
+                        // bits 5-20 of the entry: its word of the map; bits 0-4: the first bit of the segment's nibbles
                         const uint32_t w = __funnelshift_r(
-                            *reinterpret_cast<const uint32_t *>(bmb + ((x[f] >> 1) & 0x3FFFCu)), 0u, x[f] << 2);
+                            *reinterpret_cast<const uint32_t *>(bmb + ((x[f] >> 3) & 0x3FFFCu)), 0u, x[f]);
 #pragma unroll
-                        for (int a = 0; a < L; a++) add_age(acc, (w >> (4 * a)) & 15u, nacc);
+                        for (int a = 0; a < L; a++) add_age<NACC>(acc, (w >> (4 * a)) & 15u);
                     }
                     since++;
                 }
             }
-            flush_ages(acc, nacc, host, n, counts);
+            flush_ages<NACC>(acc, wide, host, n, counts);
         }
         t0 = t1;
     }
@@ -656,7 +676,7 @@ struct vate_hostset {
     uint32_t R = 0;                        // rows of 32 units
     bool ages = false;                     // an age index (4-bit age map) rather than a CheckAT bitmap index
     uint32_t ra = 0;                       // ATs per region
-    uint32_t wsh = 5;                      // entry e lies in word e >> wsh of the region's map
+    uint32_t bpa = 1;                      // bits per AT of the region's map (1: bitmap, 4: age map)
     uint64_t bm_words = 0;                 // words of the pool's map (bitmap or age map)
     uint32_t *d_entries = nullptr;         // [R][32][4]
     uint32_t *d_rt = nullptr;              // [nr + 1]: first tile of each region
@@ -687,12 +707,29 @@ void free_hostset(vate_hostset *s) {
     delete s;
 }
 
-void *kernel_for(uint32_t L, bool ages) {
+// accumulators of five ages an age pass needs for window k
+uint32_t nacc_for(uint32_t k) { return std::max(1u, (k + 4u) / 5u); }
+
+template <int NACC>
+void *age_kernel_for(uint32_t L) {
     switch (L) {
-    case 1: return ages ? (void *)hs_age_kernel<1> : (void *)hs_tile_kernel<1>;
-    case 2: return ages ? (void *)hs_age_kernel<2> : (void *)hs_tile_kernel<2>;
-    case 4: return ages ? (void *)hs_age_kernel<4> : (void *)hs_tile_kernel<4>;
-    default: return ages ? (void *)hs_age_kernel<8> : (void *)hs_tile_kernel<8>;
+    case 1: return (void *)hs_age_kernel<1, NACC>;
+    case 2: return (void *)hs_age_kernel<2, NACC>;
+    case 4: return (void *)hs_age_kernel<4, NACC>;
+    default: return (void *)hs_age_kernel<8, NACC>;
+    }
+}
+
+// The index pass for segment length L: the bitmap's (nacc 0) or the age map's with nacc accumulators.
+void *kernel_for(uint32_t L, uint32_t nacc) {
+    if (nacc == 1u) return age_kernel_for<1>(L);
+    if (nacc == 2u) return age_kernel_for<2>(L);
+    if (nacc >= 3u) return age_kernel_for<3>(L);
+    switch (L) {
+    case 1: return (void *)hs_tile_kernel<1>;
+    case 2: return (void *)hs_tile_kernel<2>;
+    case 4: return (void *)hs_tile_kernel<4>;
+    default: return (void *)hs_tile_kernel<8>;
     }
 }
 
@@ -730,7 +767,7 @@ int create_hostset(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *str
     if (G.L != 1 && G.L != 2 && G.L != 4 && G.L != 8) return set_error(VATE_EINVAL, "a hostset needs seg_len 1, 2, 4 or 8");
     if (ages && (G.k > 15u || G.g > 65535u))
         return set_error(VATE_EINVAL, "an age index needs k <= 15 and g <= 65535");
-    const uint32_t ra = ages ? AGE_REGION_ATS : REGION_ATS, wsh = ages ? 3u : 5u;
+    const uint32_t ra = ages ? AGE_REGION_ATS : REGION_ATS, bpa = ages ? 4u : 1u;
     const uint32_t nr = (uint32_t)((G.P + ra - 1) / ra);
     if (nr > MAX_REGIONS) return set_error(VATE_EINVAL, "pool too large for a hostset (more than 1024 regions)");
     const uint32_t qm = ((G.g >> G.log2L) + PER_UNIT - 1u) / PER_UNIT;   // the most units a cell can have
@@ -745,8 +782,8 @@ int create_hostset(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *str
     s->L = G.L;
     s->ages = ages;
     s->ra = ra;
-    s->wsh = wsh;
-    s->bm_words = G.P >> wsh;
+    s->bpa = bpa;
+    s->bm_words = G.P * bpa / 32u;
     // build-only buffers: cnt[r][h] (segments per cell, then the cell's tile lane), qh[r][qm + 1] (cells by size,
     // then each size's next slot), total[] (sums of the scans)
     uint32_t *d_cnt = nullptr, *d_qh = nullptr;
@@ -834,7 +871,7 @@ int create_hostset(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *str
     if (cudaMalloc(&s->d_entries, ebytes) != cudaSuccess) return fail_mem("out of device memory for the hostset's index");
     if ((e = cudaMemsetAsync(s->d_entries, 0, ebytes, st)) != cudaSuccess) return fail_cuda(e);
     const int fgrid = (int)std::min<uint64_t>((n + fill_warps - 1) / fill_warps, (uint64_t)s->sms * 16 * (8 / fill_warps));
-    hs_fill_kernel<<<fgrid, 32 * fill_warps, fill_smem, st>>>(G, d_aips, n, nr, ra, wsh, d_cnt, s->d_row0,
+    hs_fill_kernel<<<fgrid, 32 * fill_warps, fill_smem, st>>>(G, d_aips, n, nr, ra, bpa, d_cnt, s->d_row0,
                                                               s->d_entries);
     count_launch();
     const size_t order_smem = ORDER_WARPS * ORDER_WARP_BYTES;
@@ -842,7 +879,7 @@ int create_hostset(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *str
         cudaSuccess)
         return fail_cuda(e);
     const int ogrid = (int)std::min<uint64_t>((s->T + ORDER_WARPS - 1) / ORDER_WARPS, (uint64_t)s->sms * 2);
-    hs_order_kernel<<<ogrid, 32 * ORDER_WARPS, order_smem, st>>>(s->d_row0, s->T, wsh,
+    hs_order_kernel<<<ogrid, 32 * ORDER_WARPS, order_smem, st>>>(s->d_row0, s->T,
                                                                   reinterpret_cast<uint4 *>(s->d_entries));
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return fail_cuda(e);
@@ -851,7 +888,7 @@ int create_hostset(vate_handle *h, const uint32_t *d_aips, uint64_t n, void *str
     cudaFree(d_total);
     d_cnt = d_qh = nullptr;
     d_total = nullptr;
-    void *kern = kernel_for(s->L, ages);
+    void *kern = kernel_for(s->L, ages ? nacc_for(G.k) : 0u);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, tile_carveout())) != cudaSuccess)
         return fail_cuda(e);
@@ -900,20 +937,16 @@ cudaError_t age_pass(const HandleView &v, vate_hostset *s, cudaStream_t st) {
     const int mgrid = (int)std::min<uint64_t>((s->bm_words + 255) / 256, (uint64_t)v.sms * 16);
     if ((e = launch_pool(G, hs_agemap_kernel, mgrid, 256, 0, st, G, v.bact0, s->bm_words, s->d_bitmap)) != cudaSuccess)
         return e;
+    // the arguments of hs_age_kernel<L, NACC>, in its parameters' types
+    const uint32_t *map = s->d_bitmap, *rt = s->d_rt, *row0 = s->d_row0, *hosts = s->d_host;
     const uint4 *ent4 = reinterpret_cast<const uint4 *>(s->d_entries);
-    const uint32_t nacc = std::max(2u, (G.k + 3u) / 4u);
-#define VATE_HS_AGES(LL)                                                                                           \
-    hs_age_kernel<LL><<<v.sms, HS_THREADS, TILE_SMEM, st>>>(s->d_bitmap, s->bm_words, s->nr, s->d_rt, s->d_row0,   \
-                                                            s->d_host, ent4, s->T, s->R, nacc, s->n, s->d_ages)
-    switch (s->L) {
-    case 1: VATE_HS_AGES(1); break;
-    case 2: VATE_HS_AGES(2); break;
-    case 4: VATE_HS_AGES(4); break;
-    default: VATE_HS_AGES(8); break;
-    }
-#undef VATE_HS_AGES
+    uint64_t words = s->bm_words, n = s->n;
+    uint32_t nr = s->nr, T = s->T, R = s->R;
+    unsigned long long *counts = s->d_ages;
+    void *args[] = {&map, &words, &nr, &rt, &row0, &hosts, &ent4, &T, &R, &n, &counts};
+    e = cudaLaunchKernel(kernel_for(s->L, nacc_for(G.k)), dim3(v.sms), dim3(HS_THREADS), args, TILE_SMEM, st);
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 int check_call(vate_handle *h, vate_hostset *s, HandleView &v) {

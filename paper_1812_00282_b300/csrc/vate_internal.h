@@ -35,8 +35,7 @@ int handle_scratch(vate_handle *h, uint64_t bytes, void **ptr);
 int learned_handle_ok(const vate_handle *h);
 // The learned estimate (vate_estimate_learned) of n hosts from their per-age
 // counts, given as 16-bit fields (ages 4 i .. 4 i + 3 in counts[i n + h]):
-// feature rows, Eq. 11 and the output rule, in chunks through the handle's
-// scratch (vate_learned.cu).
+// feature rows, Eq. 11 and the output rule in one kernel (vate_learned.cu).
 int learned_from_age_counts(vate_handle *h, const HandleView &v, const unsigned long long *counts, uint64_t n,
                             const float *d_params, float *d_out, uint8_t *d_flags, cudaStream_t st);
 

@@ -153,36 +153,6 @@ __global__ void __launch_bounds__(WARPS * 32) features_kernel(Geom G, uint32_t b
     }
 }
 
-// Thread per host: host_features from per-age counts given as 16-bit fields
-// (age d of host h in counts[(d / 4) stride + h] >> 16 (d mod 4)): the same
-// feature row, Eq. 11 and flags.
-__global__ void __launch_bounds__(256) features_from_counts_kernel(Geom G, const uint64_t *__restrict__ hist,
-                                                                   const unsigned long long *__restrict__ counts,
-                                                                   uint64_t stride, uint64_t n, float *__restrict__ x,
-                                                                   float *__restrict__ plain,
-                                                                   uint8_t *__restrict__ pflags) {
-    __shared__ uint64_t sN0;
-    if (threadIdx.x == 0) sN0 = inactive_for_k(hist, G.P, G.k);
-    __syncthreads();
-    const uint32_t n_in = 2 * G.k + 2;
-    for (uint64_t h = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
-        float *xr = x + h * n_in;
-        uint32_t A = 0;
-        for (uint32_t d = 0; d < G.k; d++) {
-            const uint32_t c = (uint32_t)(counts[(d >> 2) * stride + h] >> (16u * (d & 3u))) & 0xFFFFu;
-            A += c;
-            xr[d] = (float)c / (float)G.g;
-            xr[G.k + d] = (float)((double)hist[d] / (double)G.P);
-        }
-        uint8_t f = 0;
-        const float p = estimate_eq11(G.g, G.P, sN0, A, f);
-        xr[2 * G.k] = log2f((float)G.g) / 16.0f;
-        xr[2 * G.k + 1] = log1pf(fmaxf(p, 0.0f)) / 16.0f;
-        plain[h] = p;
-        if (pflags) pflags[h] = f;
-    }
-}
-
 // The output rule of the learned estimator for one host: the closed form
 // `plain` (Eq. 11) is returned, flagged FALLBACK, when the host has no active
 // VAT in the window or when the corrected value expm1(8 y + log1p(max(plain,
@@ -311,6 +281,47 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_apply_kernel(const float *__re
             if (flags) flags[r0 + lane] = f;
         }
         __syncwarp();
+    }
+}
+
+// mlp_apply_kernel fed from per-age counts instead of feature rows: lane j
+// builds host j's row in shared memory from its counts (16-bit fields, age d
+// of host h in counts[(d / 4) stride + h] >> 16 (d mod 4)) with the
+// expressions of host_features, evaluates Eq. 11 and the model, and applies
+// the output rule -- what vate_estimate_learned returns for the host, bit for
+// bit, without a row in global memory.
+__global__ void __launch_bounds__(WARPS * 32) learned_from_counts_kernel(Geom G, const uint64_t *__restrict__ hist,
+                                                                         const unsigned long long *__restrict__ counts,
+                                                                         uint64_t stride, uint64_t n,
+                                                                         const float *__restrict__ params,
+                                                                         float *__restrict__ out,
+                                                                         uint8_t *__restrict__ flags) {
+    extern __shared__ float4 dyn4[];
+    const uint32_t n_in = 2 * G.k + 2;
+    float *prm = reinterpret_cast<float *>(dyn4);
+    float *w2t = stage_model(prm, params, n_in);
+    float *xs = w2t + HID * HID;                       // [WARPS][32][XS]
+    __shared__ uint64_t sN0;
+    if (threadIdx.x == 0) sN0 = inactive_for_k(hist, G.P, G.k);
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    float *xr = xs + (size_t)warp * 32 * XS + lane * XS;
+    const float lg = log2f((float)G.g) / 16.0f;
+    for (uint64_t h = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; h < n; h += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t A = 0;
+        for (uint32_t d = 0; d < G.k; d++) {
+            const uint32_t c = (uint32_t)(counts[(d >> 2) * stride + h] >> (16u * (d & 3u))) & 0xFFFFu;
+            A += c;
+            xr[d] = (float)c / (float)G.g;
+            xr[G.k + d] = (float)((double)hist[d] / (double)G.P);
+        }
+        uint8_t f = 0;
+        const float plain = estimate_eq11(G.g, G.P, sN0, A, f);
+        xr[2 * G.k] = lg;
+        xr[2 * G.k + 1] = log1pf(fmaxf(plain, 0.0f)) / 16.0f;
+        const float y = mlp_eval_lane(prm, w2t, n_in, xr);
+        out[h] = learned_rule(plain, A == 0u, y, xr[n_in - 1], prm[layout(n_in).gate], f);
+        if (flags) flags[h] = f;
     }
 }
 
@@ -475,28 +486,16 @@ int learned_handle_ok(const vate_handle *h) {
 
 int learned_from_age_counts(vate_handle *h, const HandleView &v, const unsigned long long *counts, uint64_t n,
                             const float *d_params, float *d_out, uint8_t *d_flags, cudaStream_t st) {
-    HandleView w;
-    if (int rc = check_learned_handle(h, &w)) return rc;
+    if (int rc = learned_handle_ok(h)) return rc;
     const uint32_t n_in = 2 * v.G.k + 2;
     const size_t smem = sizeof(float) * (model_smem_floats(n_in) + (size_t)WARPS * 32 * XS);
-    void *scr = nullptr;
-    const uint64_t chunk = std::min<uint64_t>(n, SPLIT_CHUNK);
-    if (int rc = handle_scratch(h, chunk * (n_in + 1) * sizeof(float), &scr)) return rc;
-    float *x = static_cast<float *>(scr), *plain = x + chunk * n_in;
-    if (cudaError_t e = cudaFuncSetAttribute(mlp_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+    if (cudaError_t e = cudaFuncSetAttribute(learned_from_counts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem))
         return set_error(VATE_ECUDA, cudaGetErrorString(e));
-    for (uint64_t h0 = 0; h0 < n; h0 += chunk) {
-        const uint64_t m = std::min(chunk, n - h0);
-        const int fgrid = (int)std::min<uint64_t>((m + 255) / 256, (uint64_t)v.sms * 8);
-        features_from_counts_kernel<<<fgrid, 256, 0, st>>>(v.G, v.hist, counts + h0, n, m, x, plain,
-                                                           d_flags ? d_flags + h0 : (uint8_t *)nullptr);
-        count_launch();
-        const int agrid = (int)std::min<uint64_t>((m + WARPS * 32 - 1) / (WARPS * 32), (uint64_t)v.sms * 8);
-        mlp_apply_kernel<<<agrid, WARPS * 32, smem, st>>>(d_params, n_in, x, plain, m, d_out + h0,
-                                                          d_flags ? d_flags + h0 : (uint8_t *)nullptr, 1u);
-        count_launch();
-        if (cudaError_t e = cudaGetLastError()) return set_error(VATE_ECUDA, cudaGetErrorString(e));
-    }
+    const int grid = (int)std::min<uint64_t>((n + WARPS * 32 - 1) / (WARPS * 32), (uint64_t)v.sms * 8);
+    learned_from_counts_kernel<<<grid, WARPS * 32, smem, st>>>(v.G, v.hist, counts, n, n, d_params, d_out, d_flags);
+    count_launch();
+    if (cudaError_t e = cudaGetLastError()) return set_error(VATE_ECUDA, cudaGetErrorString(e));
     return VATE_OK;
 }
 
