@@ -98,15 +98,17 @@ typedef struct {
  *              counts and the learned estimator need b = 8 or 16.
  *   options    bit set, 0 by default:
  *              VATE_OPT_PERSIST_L2  keep the pool resident in L2 across
- *                slices: vate_create raises the PROCESS-WIDE persisting-L2
- *                limit (cudaLimitPersistingL2CacheSize) to the device maximum
- *                if it is lower, and vate_destroy resets the persisting lines
- *                (cudaCtxResetPersistingL2Cache).  Both change L2 behaviour
- *                for every kernel of the calling process, so the library
- *                does neither unless asked.  Without the bit no process-wide
- *                setting is touched; the pool's kernels still carry a
- *                persisting access-policy window over it, which takes effect
- *                only if the process has set a persisting limit itself.
+ *                slices: the pool's kernels carry a persisting access-policy
+ *                window over it, and the handle holds the device's
+ *                PROCESS-WIDE persisting-L2 limit (cudaLimitPersistingL2-
+ *                CacheSize) at the device maximum: the first such handle (or
+ *                monitor group) raises it, the last one destroyed resets the
+ *                persisting lines (cudaCtxResetPersistingL2Cache) and puts
+ *                back the limit it found.  While held, the set-aside changes
+ *                L2 behaviour for every kernel of the calling process, so
+ *                the library does it only when asked.  Without the bit no
+ *                process-wide setting is touched and the pool's kernels carry
+ *                no window.
  *              Other bits must be 0.
  *   seed       keys the hash functions H and BH.
  * The hash functions (Sec. 4.1 leaves them open):

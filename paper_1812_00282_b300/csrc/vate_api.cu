@@ -117,7 +117,7 @@ int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
 struct vate_handle {
     vate_params prm;
     Geom G;
-    bool persist_l2 = false;         // this handle raised the process's persisting-L2 limit
+    bool persist_l2 = false;         // VATE_OPT_PERSIST_L2: holds the device's persisting-L2 limit (persist_acquire)
     int device = 0;
     int sms = 148;
     int64_t slice = -1;
@@ -181,6 +181,43 @@ int handle_scratch(vate_handle *h, uint64_t bytes, void **ptr) {
     }
     *ptr = h->d_scratch;
     return VATE_OK;
+}
+
+// Handles and groups made with VATE_OPT_PERSIST_L2, per device: the first one
+// raises the device's persisting-L2 limit to `want` (remembering the limit it
+// found), the last one released puts that limit back, so that no L2 stays set
+// aside once none of them is left.
+namespace {
+constexpr int PERSIST_DEVICES = 64;
+std::mutex g_persist_mu;
+int g_persist_users[PERSIST_DEVICES];
+size_t g_persist_prev[PERSIST_DEVICES];
+}  // namespace
+
+bool persist_acquire(int dev, size_t want) {
+    std::lock_guard<std::mutex> lock(g_persist_mu);
+    if (dev < 0 || dev >= PERSIST_DEVICES) return false;
+    if (g_persist_users[dev]++ == 0) {
+        size_t cur = 0;
+        if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) cur = 0;
+        g_persist_prev[dev] = cur;
+        if (cur < want) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+        cudaGetLastError();
+    }
+    return true;
+}
+
+void persist_release(int dev) {
+    std::lock_guard<std::mutex> lock(g_persist_mu);
+    if (dev < 0 || dev >= PERSIST_DEVICES || g_persist_users[dev] == 0) return;
+    int cur_dev = 0;
+    cudaGetDevice(&cur_dev);
+    if (cur_dev != dev) cudaSetDevice(dev);
+    cudaDeviceSynchronize();
+    cudaCtxResetPersistingL2Cache();                   // lines of the freed memory must not stay set aside
+    if (--g_persist_users[dev] == 0) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_persist_prev[dev]);
+    if (cur_dev != dev) cudaSetDevice(cur_dev);
+    cudaGetLastError();
 }
 }  // namespace vate
 
@@ -369,21 +406,17 @@ static int create_range(const vate_params *params, uint64_t lo, uint64_t hi, voi
         delete h;
         return cuda_fail(e, "kernel attributes");
     }
-    // The pool's kernels launch with a persisting access-policy window over
-    // it (hit ratio = persisting capacity / pool).  Only with
-    // VATE_OPT_PERSIST_L2 does the handle raise the process-wide persisting
-    // limit that gives the window its effect.
-    {
+    // With VATE_OPT_PERSIST_L2 the pool's kernels launch with a persisting
+    // access-policy window over it (hit ratio = persisting capacity / pool),
+    // and the handle holds the device's persisting limit that gives the window
+    // its effect (persist_acquire); without it, neither.
+    if (params->options & VATE_OPT_PERSIST_L2) {
         int persist_max = 0, window_max = 0;
         cudaDeviceGetAttribute(&persist_max, cudaDevAttrMaxPersistingL2CacheSize, h->device);
         cudaDeviceGetAttribute(&window_max, cudaDevAttrMaxAccessPolicyWindowSize, h->device);
-        size_t cur = 0;
-        if (persist_max > 0 && window_max > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
-            if ((params->options & VATE_OPT_PERSIST_L2) && cur < (size_t)persist_max) {
-                cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist_max);
-                h->persist_l2 = true;
-            }
-            cudaGetLastError();
+        cudaGetLastError();
+        if (persist_max > 0 && window_max > 0 && vate::persist_acquire(h->device, (size_t)persist_max)) {
+            h->persist_l2 = true;
             h->G.l2_window_bytes = held_bytes < (uint64_t)window_max ? held_bytes : (uint64_t)window_max;
             double ratio = (double)persist_max / (double)h->G.l2_window_bytes;
             h->G.l2_hit_ratio = ratio >= 1.0 ? 1.0f : (float)ratio;
@@ -435,12 +468,7 @@ int vate_destroy(vate_handle *h) {
     if (h->pairs_stream) cudaStreamSynchronize(h->pairs_stream);
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
     if (h->d2h_stream) cudaStreamSynchronize(h->d2h_stream);
-    if (h->G.l2_window_bytes && (h->prm.options & VATE_OPT_PERSIST_L2)) {
-        // lines of the freed pool must not keep the persisting carve-out
-        cudaDeviceSynchronize();
-        cudaCtxResetPersistingL2Cache();
-        cudaGetLastError();
-    }
+    if (h->persist_l2) vate::persist_release(h->device);
     if (h->G.pool) cudaFree(vate::pool_mem(h->G));
     cudaFree(h->d_hist);
     cudaFree(h->d_acc);

@@ -602,7 +602,8 @@ struct vate_group {
     uint32_t missing = 0;
     unsigned long long *trace = nullptr;   // vate_group_set_trace
     uint32_t trace_cap = 0;
-    bool persist_l2 = false;         // VATE_OPT_PERSIST_L2 in some monitor's options
+    bool persist_l2 = false;         // holds the persisting limit (VATE_OPT_PERSIST_L2 in some monitor's options)
+    int device = 0;
     // CUDA graph of one step
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -727,8 +728,9 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
     if (!g) return vate::set_error(VATE_ENOMEM, "host allocation failed");
     g->M = n_monitors;
     g->prm.assign(params, params + n_monitors);
+    bool want_persist = false;
     for (uint32_t m = 0; m < n_monitors; m++)
-        if (params[m].options & VATE_OPT_PERSIST_L2) g->persist_l2 = true;
+        if (params[m].options & VATE_OPT_PERSIST_L2) want_persist = true;
     g->geoms.resize(n_monitors);
     uint64_t off = 0;
     for (uint32_t m = 0; m < n_monitors; m++) {
@@ -792,17 +794,16 @@ int vate_group_create(const vate_params *params, uint32_t n_monitors, void *stre
     // L2 window over the whole arena for every group launch
     memset(&g->arena_geom, 0, sizeof g->arena_geom);
     g->arena_geom.pool = g->arena;
-    {
-        int dev = 0, persist_max = 0, window_max = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&persist_max, cudaDevAttrMaxPersistingL2CacheSize, dev);
-        cudaDeviceGetAttribute(&window_max, cudaDevAttrMaxAccessPolicyWindowSize, dev);
-        size_t cur = 0;
-        if (persist_max > 0 && window_max > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
-            // the process-wide limit only on request (VATE_OPT_PERSIST_L2 in any monitor's options)
-            if (g->persist_l2 && cur < (size_t)persist_max)
-                cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)persist_max);
-            cudaGetLastError();
+    if (want_persist) {
+        // the arena's window and the device's persisting limit only on request (VATE_OPT_PERSIST_L2 in any
+        // monitor's options); the limit is held until the group is destroyed
+        int persist_max = 0, window_max = 0;
+        cudaGetDevice(&g->device);
+        cudaDeviceGetAttribute(&persist_max, cudaDevAttrMaxPersistingL2CacheSize, g->device);
+        cudaDeviceGetAttribute(&window_max, cudaDevAttrMaxAccessPolicyWindowSize, g->device);
+        cudaGetLastError();
+        g->persist_l2 = persist_max > 0 && window_max > 0 && vate::persist_acquire(g->device, (size_t)persist_max);
+        if (g->persist_l2) {
             g->arena_geom.l2_window_bytes = std::min<uint64_t>(g->arena_bytes, (uint64_t)window_max);
             double ratio = (double)persist_max / (double)g->arena_geom.l2_window_bytes;
             g->arena_geom.l2_hit_ratio = ratio >= 1.0 ? 1.0f : (float)ratio;
@@ -833,7 +834,7 @@ int vate_group_destroy(vate_group *g) {
     if (!g) return VATE_OK;
     cudaDeviceSynchronize();
     if (g->exec) cudaGraphExecDestroy(g->exec);
-    if (g->arena_geom.l2_window_bytes && g->persist_l2) cudaCtxResetPersistingL2Cache();
+    if (g->persist_l2) vate::persist_release(g->device);
     cudaFree(g->arena);
     cudaFree(g->d_descs);
     cudaFree(g->d_state);

@@ -30,6 +30,12 @@ int set_error(int code, const char *msg);
 // A device scratch of at least `bytes` owned by the handle: allocated on the
 // first request (and grown if a later one is larger), freed by vate_destroy.
 int handle_scratch(vate_handle *h, uint64_t bytes, void **ptr);
+// The device's persisting-L2 limit, held by the handles and groups made with
+// VATE_OPT_PERSIST_L2: the first raises it to `want`, the last released puts
+// back the limit it found (vate_api.cu).  acquire returns false when the
+// device index is out of range (nothing changed).
+bool persist_acquire(int dev, size_t want);
+void persist_release(int dev);
 // VATE_OK when the handle can serve the learned estimator (its checks and
 // error messages), else the error (vate_learned.cu).
 int learned_handle_ok(const vate_handle *h);
