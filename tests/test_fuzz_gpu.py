@@ -272,3 +272,49 @@ def test_random_hostset_equals_per_host_gather(V, case):
             assert torch.equal(e1.view(torch.int32), e2.view(torch.int32)), (case, sid, kp)
     V.vate_hostset_destroy(s)
     d.close()
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_random_age_index_equals_per_host_gathers(V, case):
+    # the age index (vate_hostset_create_ages): per-age counts and A for several
+    # k' equal the per-host gathers bit for bit, for random configurations with
+    # k <= 15, L <= 8 (pools of up to eleven 384 K-AT regions), timestamps or
+    # recorders, a random host list (repeats, hosts never seen) and the drawn
+    # slice sequence
+    rng = np.random.default_rng(90_000 + case)
+    params, _, ids, kps, pkts = draw(95_000 + case)
+    c, k, g, L, part, seed = params
+    k = int(rng.integers(1, 16))
+    L = int(rng.choice([1, 2, 4, 8]))
+    g = int(min(L * rng.integers(2, 129), 4096))
+    c = max(c, int(rng.choice([c, 22])))
+    kps = sorted({1, int(rng.integers(1, k + 1)), k})
+    counter = int(rng.integers(0, 2))
+    d = V.Vate(c, k, g, L, part, seed, counter=counter)
+    tr = Traffic(SMALL, pkts_per_slice=pkts)
+    n = int(rng.integers(1, 3000))
+    hosts = rng.choice(tr.aips, n)
+    hosts[: n // 10] = rng.integers(1, 1 << 32, n // 10, dtype=np.uint64).astype(np.uint32)
+    dh = dev_u32(hosts)
+    s = V.vate_hostset_create_ages(d.h, dh)
+    c1 = torch.empty(n * k, dtype=torch.int16, device="cuda")
+    c2 = torch.empty_like(c1)
+    e1 = torch.empty(n, dtype=torch.float32, device="cuda")
+    f1 = torch.empty(n, dtype=torch.uint8, device="cuda")
+    a1 = torch.empty(n, dtype=torch.int32, device="cuda")
+    e2, f2, a2 = torch.empty_like(e1), torch.empty_like(f1), torch.empty_like(a1)
+    for sid in ids:
+        d.ingest(dev_pairs(tr.slice_pairs(sid % 64)), sid)
+        d.close_slice(sid)
+        V.vate_age_counts(d.h, dh, c1)
+        V.vate_age_counts_hostset(d.h, s, c2)
+        assert torch.equal(c1, c2), (case, sid)
+        for kp in kps:
+            d.estimate(dh, kp, e1, f1)
+            V.vate_active_counts(d.h, dh, kp, a1)
+            V.vate_estimate_hostset(d.h, s, kp, e2, f2, a2)
+            assert torch.equal(a1, a2), (case, sid, kp)
+            assert torch.equal(f1, f2), (case, sid, kp)
+            assert torch.equal(e1.view(torch.int32), e2.view(torch.int32)), (case, sid, kp)
+    V.vate_hostset_destroy(s)
+    d.close()
