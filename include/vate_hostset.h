@@ -85,6 +85,23 @@ int vate_estimate_hostset(vate_handle *h, vate_hostset *s, uint32_t kprime, floa
 int vate_estimate_hostset_host(vate_handle *h, vate_hostset *s, uint32_t kprime, float *h_out, uint8_t *h_flags,
                                void *stream);
 
+/* vate_estimate_hostset_host whose copies overlap the caller's next work:
+ * the kernels run on `stream` into one of two device buffers of the hostset
+ * (in turn), and the copies to h_out / h_flags are queued on a stream of the
+ * hostset after them, so that work queued next on `stream` (the next slice's
+ * ingest and close) does not wait for them.  The host buffers hold the
+ * results once vate_hostset_wait returns (synchronising `stream` is not
+ * enough); a call waits on the device for the copies of the call before last,
+ * whose buffer it reuses.  The buffers of two calls in flight must differ.
+ * Device memory: 10 n bytes, allocated on the first call.  Errors: as
+ * vate_estimate_hostset_host. */
+int vate_estimate_hostset_host_async(vate_handle *h, vate_hostset *s, uint32_t kprime, float *h_out, uint8_t *h_flags,
+                                     void *stream);
+
+/* Block until every copy queued by vate_estimate_hostset_host_async on this
+ * hostset is in host memory.  Errors: VATE_EINVAL (NULL), VATE_ECUDA. */
+int vate_hostset_wait(vate_hostset *s);
+
 /* An age index: the same index over regions of 384 K ATs, looked up in the
  * pool's age map (4 bits per AT: the AT's distance d when d < k, else 15;
  * 192 KiB per region) instead of the CheckAT bitmap, so that one pass gives

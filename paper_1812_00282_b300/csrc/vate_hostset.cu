@@ -687,6 +687,15 @@ struct vate_hostset {
     unsigned long long *d_ages = nullptr;  // [4][n]: an age index's per-age counts, 16-bit fields
     float *d_out = nullptr;                // [n], vate_estimate_hostset_host (on first use)
     uint8_t *d_flags = nullptr;            // [n]
+    // vate_estimate_hostset_host_async (on first use): results of two calls in turn, copied on a stream of
+    // the hostset; done[b]: the copy out of buffer b; ready: the kernels of the last call
+    float *d_out2[2] = {nullptr, nullptr};
+    uint8_t *d_flags2[2] = {nullptr, nullptr};
+    cudaStream_t d2h = nullptr;
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    cudaEvent_t ready = nullptr;
+    bool used[2] = {false, false};
+    uint32_t flip = 0;
     uint64_t bytes = 0;
 };
 
@@ -703,6 +712,13 @@ void free_hostset(vate_hostset *s) {
     cudaFree(s->d_ages);
     cudaFree(s->d_out);
     cudaFree(s->d_flags);
+    for (int b = 0; b < 2; b++) {
+        cudaFree(s->d_out2[b]);
+        cudaFree(s->d_flags2[b]);
+        if (s->done[b]) cudaEventDestroy(s->done[b]);
+    }
+    if (s->ready) cudaEventDestroy(s->ready);
+    if (s->d2h) cudaStreamDestroy(s->d2h);
     cudaGetLastError();
     delete s;
 }
@@ -1054,6 +1070,45 @@ int vate_estimate_hostset_host(vate_handle *h, vate_hostset *s, uint32_t kprime,
     if (e == cudaSuccess && h_flags) e = cudaMemcpyAsync(h_flags, s->d_flags, s->n, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
     return VATE_OK;
+}
+
+int vate_estimate_hostset_host_async(vate_handle *h, vate_hostset *s, uint32_t kprime, float *h_out, uint8_t *h_flags,
+                                     void *stream) {
+    if (!s || !h_out) return set_error(VATE_EINVAL, "hostset and h_out must not be NULL");
+    if (!s->d2h) {
+        bool ok = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&s->ready, cudaEventDisableTiming) == cudaSuccess;
+        for (int b = 0; b < 2 && ok; b++)
+            ok = cudaEventCreateWithFlags(&s->done[b], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaMalloc(&s->d_out2[b], s->n * sizeof(float)) == cudaSuccess &&
+                 cudaMalloc(&s->d_flags2[b], s->n) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return set_error(VATE_ENOMEM, "out of device memory (or streams) for the hostset's copies");
+        }
+        s->bytes += 2 * s->n * 5;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t b = s->flip;
+    // the kernels of this call rewrite buffer b: after the copy that read it two calls ago
+    cudaError_t e = s->used[b] ? cudaStreamWaitEvent(st, s->done[b], 0) : cudaSuccess;
+    if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+    if (int rc = vate_estimate_hostset(h, s, kprime, s->d_out2[b], s->d_flags2[b], nullptr, stream)) return rc;
+    if ((e = cudaEventRecord(s->ready, st)) == cudaSuccess && (e = cudaStreamWaitEvent(s->d2h, s->ready, 0)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(h_out, s->d_out2[b], s->n * sizeof(float), cudaMemcpyDeviceToHost, s->d2h)) == cudaSuccess &&
+        (!h_flags || (e = cudaMemcpyAsync(h_flags, s->d_flags2[b], s->n, cudaMemcpyDeviceToHost, s->d2h)) == cudaSuccess))
+        e = cudaEventRecord(s->done[b], s->d2h);
+    if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+    s->used[b] = true;
+    s->flip = b ^ 1u;
+    return VATE_OK;
+}
+
+int vate_hostset_wait(vate_hostset *s) {
+    if (!s) return set_error(VATE_EINVAL, "hostset is NULL");
+    if (!s->d2h) return VATE_OK;
+    cudaError_t e = cudaStreamSynchronize(s->d2h);
+    return e == cudaSuccess ? VATE_OK : set_error(VATE_ECUDA, cudaGetErrorString(e));
 }
 
 }  // extern "C"

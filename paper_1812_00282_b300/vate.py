@@ -156,6 +156,8 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
         "vate_estimate_hostset": (i, [vp, vp, u32, vp, vp, vp, vp]),
         "vate_estimate_hostset_host": (i, [vp, vp, u32, vp, vp, vp]),
         "vate_hostset_create_ages": (i, [vp, vp, u64, vp, P(vp)]),
+        "vate_estimate_hostset_host_async": (i, [vp, vp, u32, vp, vp, vp]),
+        "vate_hostset_wait": (i, [vp]),
         "vate_age_counts_hostset": (i, [vp, vp, vp, vp]),
         "vate_estimate_learned_hostset": (i, [vp, vp, vp, vp, vp, vp]),
     }
@@ -769,6 +771,22 @@ def vate_estimate_hostset_host(h, s, kprime: int, out, flags=None, stream=None) 
             raise ValueError("%s must be a contiguous host %s tensor of at least %d elements" % (name, dt, n))
     _check(_lib.vate_estimate_hostset_host(h, s, kprime, out.data_ptr(),
                                            flags.data_ptr() if flags is not None else None, _stream(stream)))
+
+
+def vate_estimate_hostset_host_async(h, s, kprime: int, out, flags=None, stream=None) -> None:
+    """vate_estimate_hostset_host with its copies on a stream of the hostset;
+    the host tensors hold the results after vate_hostset_wait(s)."""
+    import torch
+    n = vate_hostset_info(s)[1]
+    for t, dt, name in ((out, torch.float32, "out"), (flags, torch.uint8, "flags")):
+        if t is not None and (t.is_cuda or t.dtype != dt or not t.is_contiguous() or t.numel() < n):
+            raise ValueError("%s must be a contiguous host %s tensor of at least %d elements" % (name, dt, n))
+    _check(_lib.vate_estimate_hostset_host_async(h, s, kprime, out.data_ptr(),
+                                                 flags.data_ptr() if flags is not None else None, _stream(stream)))
+
+
+def vate_hostset_wait(s) -> None:
+    _check(_lib.vate_hostset_wait(s))
 
 
 def vate_create_shard(params: vate_params, pid_lo: int, pid_hi: int, stream=None) -> C.c_void_p:

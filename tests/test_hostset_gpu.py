@@ -198,3 +198,38 @@ def test_hostset_many_regions_and_tiny_lists(V, L):
     for s in sets:
         V.vate_hostset_destroy(s)
     d.close()
+
+
+@pytest.mark.parametrize("ages", [False, True])
+def test_async_host_copies_equal_the_device_results(V, ages):
+    # vate_estimate_hostset_host_async: calls back to back, the results of two
+    # calls in flight in two host buffers, read after vate_hostset_wait; each
+    # equal to vate_estimate_hostset on the device bit for bit
+    k, c, g, L = 5, 20, 512, 1
+    tr = Traffic(SMALL, pkts_per_slice=20_000)
+    hosts = tr.aips
+    n = len(hosts)
+    d = V.Vate(c, k, g, L, 0, 61)
+    s = (V.vate_hostset_create_ages if ages else V.vate_hostset_create)(d.h, as_i32(hosts))
+    outs = [(torch.empty(n, dtype=torch.float32).pin_memory(), torch.empty(n, dtype=torch.uint8).pin_memory())
+            for _ in range(2)]
+    refs = []
+    for sl in range(7):
+        d.ingest(as_i32(tr.slice_pairs(sl)), sl)
+        d.close_slice(sl)
+        o, f = outs[sl & 1]
+        V.vate_estimate_hostset_host_async(d.h, s, k, o, f)
+        e = torch.empty(n, dtype=torch.float32, device="cuda")
+        fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+        V.vate_estimate_hostset(d.h, s, k, e, fl)
+        refs.append((e.cpu(), fl.cpu()))
+        if sl >= 1:                                  # the call before this one: its copies are done after the wait
+            V.vate_hostset_wait(s)
+            po, pf = outs[(sl - 1) & 1]
+            ro, rf = refs[sl - 1]
+            assert torch.equal(po.view(torch.int32), ro.view(torch.int32)) and torch.equal(pf, rf), sl - 1
+    V.vate_hostset_wait(s)
+    po, pf = outs[6 & 1]
+    assert torch.equal(po.view(torch.int32), refs[6][0].view(torch.int32)) and torch.equal(pf, refs[6][1])
+    V.vate_hostset_destroy(s)
+    d.close()
