@@ -233,7 +233,7 @@ def code_of(text: str) -> str:
 
 
 TRAFFIC_SOURCES = {                      # the sources each committed ncu traffic figure depends on
-    "hs_tile_kernel": ("vate_hostset.cu", "vate_device.cuh"),
+    "hs_tile_kernel": ("vate_hostset_pass.cuh", "vate_device.cuh", "vate_device_ops.cuh"),
 }
 DEFAULT_TRAFFIC_SOURCES = ("vate_kernels.cu", "vate_device.cuh", "vate_device_ops.cuh")
 

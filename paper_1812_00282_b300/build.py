@@ -23,7 +23,8 @@ SOURCES = ["vate_api.cu", "vate_kernels.cu", "vate_packed.cu", "vate_noalloc.cu"
 PROBE_LIB = os.path.join(HERE, "libvate_probe.so")   # memory-system probes for the benchmark (include/vate_probe.h)
 DEBUG_LIB = os.path.join(HERE, "libvate_debug.so")   # the checked build: the same sources with VATE_DEBUG
 PROBE_SOURCES = ["vate_probe.cu"]
-HEADERS = ["vate_device.cuh", "vate_device_ops.cuh", "vate_ages.cuh", "vate_launch.cuh", "vate_internal.h"]
+HEADERS = ["vate_device.cuh", "vate_device_ops.cuh", "vate_ages.cuh", "vate_launch.cuh", "vate_internal.h",
+           "vate_hostset_pass.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
