@@ -102,6 +102,18 @@ int vate_estimate_hostset_host_async(vate_handle *h, vate_hostset *s, uint32_t k
  * hostset is in host memory.  Errors: VATE_EINVAL (NULL), VATE_ECUDA. */
 int vate_hostset_wait(vate_hostset *s);
 
+/* Time the index pass (the tile pass over the bitmap, or the age pass) of
+ * the next n calls that close through this hostset (n <= 4096; 0 stops):
+ * CUDA events recorded on the caller's stream before and after it, so that
+ * the pass's own duration is known beside the whole call's.  Restarts the
+ * count.  Errors: VATE_EINVAL, VATE_ENOMEM (events). */
+int vate_hostset_time_passes(vate_hostset *s, uint32_t n);
+
+/* The pass durations recorded since vate_hostset_time_passes, in ms, in the
+ * order of the calls: min(max, recorded) of them into ms[], their number in
+ * *count.  Waits for the recorded events.  Errors: VATE_EINVAL, VATE_ECUDA. */
+int vate_hostset_pass_times(vate_hostset *s, float *ms, uint32_t max, uint32_t *count);
+
 /* An age index: the same index over regions of 384 K ATs, looked up in the
  * pool's age map (4 bits per AT: the AT's distance d when d < k, else 15;
  * 192 KiB per region) instead of the CheckAT bitmap, so that one pass gives

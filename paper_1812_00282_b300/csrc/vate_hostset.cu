@@ -514,6 +514,9 @@ struct vate_hostset {
     cudaEvent_t ready = nullptr;
     bool used[2] = {false, false};
     uint32_t flip = 0;
+    // vate_hostset_time_passes: event pairs around the index pass of the next calls
+    std::vector<cudaEvent_t> pass_ev;      // [2 * n]
+    uint32_t pass_want = 0, pass_done = 0;
     uint64_t bytes = 0;
 };
 
@@ -536,6 +539,7 @@ void free_hostset(vate_hostset *s) {
         if (s->done[b]) cudaEventDestroy(s->done[b]);
     }
     if (s->ready) cudaEventDestroy(s->ready);
+    for (cudaEvent_t e : s->pass_ev) cudaEventDestroy(e);
     if (s->d2h) cudaStreamDestroy(s->d2h);
     cudaGetLastError();
     delete s;
@@ -808,7 +812,10 @@ int vate_estimate_hostset(vate_handle *h, vate_hostset *s, uint32_t kprime, floa
     cudaError_t e;
     if (s->ages) {
         // the active count for k' is the sum of the ages below k'
+        const bool timed = s->pass_done < s->pass_want;
+        if (timed) cudaEventRecord(s->pass_ev[2 * s->pass_done], st);
         if ((e = age_pass(v, s, st)) != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+        if (timed) cudaEventRecord(s->pass_ev[2 * s->pass_done++ + 1], st);
         const int cgrid = (int)std::min<uint64_t>((s->n + 255) / 256, (uint64_t)v.sms * 8);
         hs_counts_active_kernel<<<cgrid, 256, 0, st>>>(s->d_ages, s->n, kprime, acc);
         count_launch();
@@ -822,6 +829,8 @@ int vate_estimate_hostset(vate_handle *h, vate_hostset *s, uint32_t kprime, floa
         e = launch_pool(G, hs_bitmap_kernel, bgrid, 256, 0, st, G, rc, c2k, s->bm_words, s->d_bitmap);
         if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
         const uint4 *ent4 = reinterpret_cast<const uint4 *>(s->d_entries);
+        const bool timed = s->pass_done < s->pass_want;
+        if (timed) cudaEventRecord(s->pass_ev[2 * s->pass_done], st);
 #define VATE_HS_LAUNCH(LL)                                                                                          \
     hs_tile_kernel<LL><<<v.sms, HS_THREADS, TILE_SMEM, st>>>(s->d_bitmap, s->bm_words, s->nr, s->d_rt, s->d_row0,   \
                                                              s->d_host, ent4, s->T, s->R, acc)
@@ -833,6 +842,7 @@ int vate_estimate_hostset(vate_handle *h, vate_hostset *s, uint32_t kprime, floa
         }
 #undef VATE_HS_LAUNCH
         count_launch();
+        if (timed) cudaEventRecord(s->pass_ev[2 * s->pass_done++ + 1], st);
         if ((e = cudaGetLastError()) != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
     }
     e = launch_estimate_from_counts(G, kprime, v.hist, acc, s->n, d_out, d_flags, st, v.sms);
@@ -927,6 +937,34 @@ int vate_hostset_wait(vate_hostset *s) {
     if (!s->d2h) return VATE_OK;
     cudaError_t e = cudaStreamSynchronize(s->d2h);
     return e == cudaSuccess ? VATE_OK : set_error(VATE_ECUDA, cudaGetErrorString(e));
+}
+
+int vate_hostset_time_passes(vate_hostset *s, uint32_t n) {
+    if (!s) return set_error(VATE_EINVAL, "hostset is NULL");
+    if (n > 4096u) return set_error(VATE_EINVAL, "at most 4096 passes are timed at once");
+    while (s->pass_ev.size() < 2u * n) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(VATE_ENOMEM, "CUDA events for the pass timings");
+        }
+        s->pass_ev.push_back(e);
+    }
+    s->pass_want = n;
+    s->pass_done = 0;
+    return VATE_OK;
+}
+
+int vate_hostset_pass_times(vate_hostset *s, float *ms, uint32_t max, uint32_t *count) {
+    if (!s || (!ms && max) || !count) return set_error(VATE_EINVAL, "hostset, ms and count must not be NULL");
+    const uint32_t n = std::min(max, s->pass_done);
+    for (uint32_t i = 0; i < n; i++) {
+        cudaError_t e = cudaEventSynchronize(s->pass_ev[2 * i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms + i, s->pass_ev[2 * i], s->pass_ev[2 * i + 1]);
+        if (e != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
+    }
+    *count = n;
+    return VATE_OK;
 }
 
 }  // extern "C"

@@ -158,6 +158,8 @@ def _load(path: str = LIB_PATH) -> C.CDLL:
         "vate_hostset_create_ages": (i, [vp, vp, u64, vp, P(vp)]),
         "vate_estimate_hostset_host_async": (i, [vp, vp, u32, vp, vp, vp]),
         "vate_hostset_wait": (i, [vp]),
+        "vate_hostset_time_passes": (i, [vp, u32]),
+        "vate_hostset_pass_times": (i, [vp, vp, u32, P(u32)]),
         "vate_age_counts_hostset": (i, [vp, vp, vp, vp]),
         "vate_estimate_learned_hostset": (i, [vp, vp, vp, vp, vp, vp]),
     }
@@ -787,6 +789,19 @@ def vate_estimate_hostset_host_async(h, s, kprime: int, out, flags=None, stream=
 
 def vate_hostset_wait(s) -> None:
     _check(_lib.vate_hostset_wait(s))
+
+
+def vate_hostset_time_passes(s, n: int) -> None:
+    """Time the index pass of the next n closes through hostset s (include/vate_hostset.h)."""
+    _check(_lib.vate_hostset_time_passes(s, n))
+
+
+def vate_hostset_pass_times(s, max_n: int = 4096):
+    """The recorded index-pass durations, in ms, in call order."""
+    buf = (C.c_float * max(1, max_n))()
+    cnt = C.c_uint32()
+    _check(_lib.vate_hostset_pass_times(s, C.cast(buf, C.c_void_p), max_n, C.byref(cnt)))
+    return [float(buf[i]) for i in range(cnt.value)]
 
 
 def vate_create_shard(params: vate_params, pid_lo: int, pid_hi: int, stream=None) -> C.c_void_p:

@@ -233,3 +233,32 @@ def test_async_host_copies_equal_the_device_results(V, ages):
     assert torch.equal(po.view(torch.int32), refs[6][0].view(torch.int32)) and torch.equal(pf, refs[6][1])
     V.vate_hostset_destroy(s)
     d.close()
+
+
+def test_pass_timings(V):
+    # vate_hostset_time_passes: the next n closes record their index pass with
+    # CUDA events; later calls are not recorded; a restart starts over
+    tr = Traffic(SMALL, pkts_per_slice=10_000)
+    d = V.Vate(20, 4, 512, 1, 0, 3)
+    for ages in (False, True):
+        s = (V.vate_hostset_create_ages if ages else V.vate_hostset_create)(d.h, as_i32(tr.aips))
+        out = torch.empty(len(tr.aips), dtype=torch.float32, device="cuda")
+        if not ages:
+            d.ingest(as_i32(tr.slice_pairs(0)), 0)
+            d.close_slice(0)
+        assert V.vate_hostset_pass_times(s) == []
+        V.vate_hostset_time_passes(s, 3)
+        for _ in range(5):
+            V.vate_estimate_hostset(d.h, s, 4, out)
+        ms = V.vate_hostset_pass_times(s)
+        assert len(ms) == 3 and all(0.0 < t < 1000.0 for t in ms)
+        V.vate_hostset_time_passes(s, 1)
+        V.vate_estimate_hostset(d.h, s, 4, out)
+        assert len(V.vate_hostset_pass_times(s)) == 1
+        V.vate_hostset_time_passes(s, 0)
+        V.vate_estimate_hostset(d.h, s, 4, out)
+        assert V.vate_hostset_pass_times(s) == []
+        with pytest.raises(V.VateError):
+            V.vate_hostset_time_passes(s, 5000)
+        V.vate_hostset_destroy(s)
+    d.close()
