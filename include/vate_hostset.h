@@ -103,7 +103,9 @@ int vate_estimate_hostset_host_async(vate_handle *h, vate_hostset *s, uint32_t k
 int vate_hostset_wait(vate_hostset *s);
 
 /* Time the index pass (the tile pass over the bitmap, or the age pass) of
- * the next n calls that close through this hostset (n <= 4096; 0 stops):
+ * the next n calls that run it through this hostset (vate_estimate_hostset
+ * and its host forms; vate_age_counts_hostset, vate_estimate_learned_hostset)
+ * (n <= 4096; 0 stops):
  * CUDA events recorded on the caller's stream before and after it, so that
  * the pass's own duration is known beside the whole call's.  Restarts the
  * count.  Errors: VATE_EINVAL, VATE_ENOMEM (events). */

@@ -782,8 +782,11 @@ cudaError_t age_pass(const HandleView &v, vate_hostset *s, cudaStream_t st) {
     uint32_t nr = s->nr, T = s->T, R = s->R;
     unsigned long long *counts = s->d_ages;
     void *args[] = {&map, &words, &nr, &rt, &row0, &hosts, &ent4, &T, &R, &n, &counts};
+    const bool timed = s->pass_done < s->pass_want;
+    if (timed) cudaEventRecord(s->pass_ev[2 * s->pass_done], st);
     e = cudaLaunchKernel(kernel_for(s->L, nacc_for(G.k)), dim3(v.sms), dim3(HS_THREADS), args, TILE_SMEM, st);
     count_launch();
+    if (timed && e == cudaSuccess) cudaEventRecord(s->pass_ev[2 * s->pass_done++ + 1], st);
     return e;
 }
 
@@ -812,10 +815,7 @@ int vate_estimate_hostset(vate_handle *h, vate_hostset *s, uint32_t kprime, floa
     cudaError_t e;
     if (s->ages) {
         // the active count for k' is the sum of the ages below k'
-        const bool timed = s->pass_done < s->pass_want;
-        if (timed) cudaEventRecord(s->pass_ev[2 * s->pass_done], st);
         if ((e = age_pass(v, s, st)) != cudaSuccess) return set_error(VATE_ECUDA, cudaGetErrorString(e));
-        if (timed) cudaEventRecord(s->pass_ev[2 * s->pass_done++ + 1], st);
         const int cgrid = (int)std::min<uint64_t>((s->n + 255) / 256, (uint64_t)v.sms * 8);
         hs_counts_active_kernel<<<cgrid, 256, 0, st>>>(s->d_ages, s->n, kprime, acc);
         count_launch();

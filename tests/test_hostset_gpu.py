@@ -258,6 +258,11 @@ def test_pass_timings(V):
         V.vate_hostset_time_passes(s, 0)
         V.vate_estimate_hostset(d.h, s, 4, out)
         assert V.vate_hostset_pass_times(s) == []
+        if ages:                                   # the age index's other entry points run the same pass
+            V.vate_hostset_time_passes(s, 2)
+            V.vate_age_counts_hostset(d.h, s, torch.empty(len(tr.aips) * 4, dtype=torch.int16, device="cuda"))
+            V.vate_estimate_hostset(d.h, s, 4, out)
+            assert len(V.vate_hostset_pass_times(s)) == 2
         with pytest.raises(V.VateError):
             V.vate_hostset_time_passes(s, 5000)
         V.vate_hostset_destroy(s)
