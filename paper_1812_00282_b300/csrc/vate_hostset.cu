@@ -910,7 +910,20 @@ int vate_estimate_hostset_host_async(vate_handle *h, vate_hostset *s, uint32_t k
             ok = cudaEventCreateWithFlags(&s->done[b], cudaEventDisableTiming) == cudaSuccess &&
                  cudaMalloc(&s->d_out2[b], s->n * sizeof(float)) == cudaSuccess &&
                  cudaMalloc(&s->d_flags2[b], s->n) == cudaSuccess;
-        if (!ok) {
+        if (!ok) {                                       // undo it all, so that a later call starts over
+            cudaGetLastError();
+            for (int b = 0; b < 2; b++) {
+                cudaFree(s->d_out2[b]);
+                cudaFree(s->d_flags2[b]);
+                if (s->done[b]) cudaEventDestroy(s->done[b]);
+                s->d_out2[b] = nullptr;
+                s->d_flags2[b] = nullptr;
+                s->done[b] = nullptr;
+            }
+            if (s->ready) cudaEventDestroy(s->ready);
+            if (s->d2h) cudaStreamDestroy(s->d2h);
+            s->ready = nullptr;
+            s->d2h = nullptr;
             cudaGetLastError();
             return set_error(VATE_ENOMEM, "out of device memory (or streams) for the hostset's copies");
         }
